@@ -1,0 +1,717 @@
+/*
+ * DDQMC oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU statement of one step of the
+ * driven-dissipative FCIQMC of Nagy & Savona (arXiv:1802.05931) for the
+ * spin-1/2 XYZ lattice with sigma^- decay on every site.  Only the test
+ * suite, the package smoke check and the benchmark's CPU-baseline leg may
+ * build, load or call this file.  The CUDA library never links it, and the
+ * two share no code, header, table or helper.
+ *
+ * What one step computes, in the paper's order (Sec. III.C):
+ *   (i)   spawning along the off-diagonal elements of the shifted Liouvillian
+ *         (Kronecker form and element equation of Sec. III.C), with the four
+ *         real/imaginary parent/child sign rules;
+ *   (ii)  clone/death from the real part of the diagonal element and the
+ *         on-site Re<->Im transfer from its imaginary part;
+ *   (iii) annihilation: all contributions to one configuration |i><j| are
+ *         summed, real and imaginary parts separately, under the initiator
+ *         survival rule of Sec. IV.A;
+ *   then the estimators of Sec. III.A (ratio of traces) and the shift update
+ *   of Sec. III.C.
+ *
+ * Fixed readings of what the paper leaves open (the CUDA path follows the same
+ * written rules, from its own code):
+ *   - basis: site k = x + Lx*y, bit k of a spin word set <=> spin up;
+ *     a configuration is (ket i, bra j); canonical order is (bra, ket);
+ *   - H = sum over bonds of Jx sx sx + Jy sy sy + Jz sz sz (Pauli matrices),
+ *     decay gamma * D[sigma^-] on every site (Sec. V, XYZ model);
+ *   - moves, in this order: ket bond flips b = 0..B-1, bra bond flips
+ *     b = 0..B-1, then jumps k = 0..N-1;
+ *   - per-walker categorical draws, which have the joint law of the
+ *     binomial + multinomial scheme of Sec. III.B; n_att = ceil(P_tot)
+ *     attempts when P_tot > 1;
+ *   - rates are fixed-point integers: q(x) = (uint64)(x * 2^32), truncated;
+ *   - Philox4x32-10 (Salmon et al., SC'11) with key (lo32(seed),
+ *     hi32(seed) ^ lo32(t)) and counter (ket, bra, walker, part<<16 | block);
+ *   - shift: S0 until the controlled weight first reaches the target, then
+ *     the log update of Sec. III.C every step with a series logarithm.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define OR_MAX_SITES 64
+#define OR_MAX_BONDS 128
+
+/* error codes returned by or_step / or_import */
+#define OR_OK 0
+#define OR_ERR_ARG (-1)
+#define OR_ERR_OOM (-2)
+#define OR_ERR_OVERFLOW (-4)
+
+typedef struct {
+    uint64_t ket, bra;
+    int64_t re, im;     /* 64-bit while summing; range-checked against int32 */
+} or_entry;
+
+typedef struct {
+    uint64_t ket, bra;
+    int32_t dre, dim;
+    int32_t init;       /* 1 if the parent was an initiator */
+} or_spawn;
+
+typedef struct {
+    /* lattice and model */
+    int Lx, Ly, periodic, N, B;
+    int bond_a[OR_MAX_BONDS], bond_b[OR_MAX_BONDS];
+    uint64_t bond_m[OR_MAX_BONDS];
+    double Jx, Jy, Jz, gamma, dt;
+    int64_t target;
+    int32_t n_a;
+    int control;            /* 0: N_w = sum |Re rho_ii| (paper); 1: sum |re|+|im| */
+    int guide_kind;         /* 0 none, 1 uniform w = exp(-p), 2 site product */
+    double guide_p;
+    double site_r[OR_MAX_SITES];
+    uint64_t seed;
+    double delta, S0;
+    int64_t n0;
+    int64_t t_eq_override;  /* < 0: derived */
+    /* fixed-point rate tables */
+    uint64_t rate_q[OR_MAX_BONDS][2][4];   /* [bond][aligned=0/anti=1][ratio class] */
+    uint64_t jump_q;
+    uint32_t cross_int[2 * OR_MAX_BONDS + 1];
+    uint64_t cross_frac[2 * OR_MAX_BONDS + 1];
+    double shift_gain;      /* delta / dt */
+    /* state */
+    or_entry *L;
+    int64_t M, capL;
+    double S;
+    int variable;
+    int64_t Qprev;
+    int64_t t, t_var, t_eq;
+    /* per-step estimator series */
+    int nobs;
+    int64_t *series;
+    int64_t nseries, capseries;
+    int64_t last_spawns;    /* child-walker records made in the last step */
+    /* uniform injection (hand-worked tests) */
+    const uint32_t *inj;
+    int64_t ninj, pinj;
+    int inj_short;
+} or_run;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from its definition in Salmon, Moraes, Dror & Shaw,        */
+/* "Parallel random numbers: as easy as 1, 2, 3" (SC'11).                    */
+/* ------------------------------------------------------------------------ */
+static uint32_t or_mulhi32(uint32_t a, uint32_t b) {
+    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+}
+
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint32_t hi0 = or_mulhi32(M0, c0), lo0 = M0 * c0;
+        uint32_t hi1 = or_mulhi32(M1, c2), lo1 = M1 * c2;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Deterministic natural logarithm: x = m 2^e with m in (1/sqrt2, sqrt2],     */
+/* log m = 2 atanh(s), s = (m-1)/(m+1), atanh by its odd power series.       */
+/* Every operation is a single IEEE-754 double operation in a fixed order.   */
+/* ------------------------------------------------------------------------ */
+double or_series_log(double x) {
+    const double LN2 = 0.6931471805599453;      /* nearest double to ln 2 */
+    const double SQRT2 = 1.4142135623730951;    /* nearest double to sqrt 2 */
+    if (!(x > 0.0)) return 0.0;
+    uint64_t bits;
+    memcpy(&bits, &x, 8);
+    int e = (int)((bits >> 52) & 0x7FF);
+    if (e == 0) return 0.0;     /* subnormals never occur: inputs are ratios of counts */
+    e -= 1023;
+    uint64_t mb = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    double m;
+    memcpy(&m, &mb, 8);
+    if (m > SQRT2) { m = m * 0.5; e += 1; }
+    double num = m - 1.0;
+    double den = m + 1.0;
+    double s = num / den;
+    double z = s * s;
+    /* sum_{k=0}^{14} z^k / (2k+1), Horner from the top term */
+    double p = 1.0 / 29.0;
+    for (int k = 13; k >= 0; --k) {
+        double c = 1.0 / (double)(2 * k + 1);
+        double pz = p * z;
+        p = pz + c;
+    }
+    double two_s = 2.0 * s;
+    double lm = two_s * p;
+    double el = (double)e * LN2;
+    return el + lm;
+}
+
+/* ------------------------------------------------------------------------ */
+/* helpers                                                                   */
+/* ------------------------------------------------------------------------ */
+static int or_popc(uint64_t x) { int c = 0; while (x) { x &= x - 1; ++c; } return c; }
+static int or_bit(uint64_t s, int k) { return (int)((s >> k) & 1u); }
+static uint64_t or_q(double x) { return (uint64_t)(x * 4294967296.0); }
+
+/* z-sum of a spin word: sum over bonds of z_a z_b (z = +1 up, -1 down) */
+static int or_zsum(const or_run *r, uint64_t s) {
+    int acc = 0;
+    for (int b = 0; b < r->B; ++b)
+        acc += (or_bit(s, r->bond_a[b]) == or_bit(s, r->bond_b[b])) ? 1 : -1;
+    return acc;
+}
+
+/* off-diagonal element of H between s and s ^ m_b: Jx - Jy if the bond is
+ * aligned in s (sy sy gives -1), Jx + Jy if anti-aligned (sy sy gives +1) */
+static double or_hb(const or_run *r, uint64_t s, int b) {
+    int aligned = or_bit(s, r->bond_a[b]) == or_bit(s, r->bond_b[b]);
+    return aligned ? (r->Jx - r->Jy) : (r->Jx + r->Jy);
+}
+
+/* ratio class of a bond move applied to configuration (i, j) -- see rate table */
+static int or_ratio_class(const or_run *r, uint64_t i, uint64_t j, int b) {
+    uint64_t d = i ^ j;
+    if (r->guide_kind == 1) {
+        if (d == 0) return 1;                 /* diagonal parent -> off-diagonal child */
+        if (d == r->bond_m[b]) return 2;      /* off-diagonal parent -> diagonal child */
+        return 0;
+    }
+    if (r->guide_kind == 2)
+        return 2 * or_bit(d, r->bond_a[b]) + or_bit(d, r->bond_b[b]);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* construction                                                              */
+/* ------------------------------------------------------------------------ */
+static int or_build_lattice(or_run *r) {
+    int Lx = r->Lx, Ly = r->Ly;
+    if (Lx < 1 || Ly < 1 || Lx * Ly > OR_MAX_SITES) return OR_ERR_ARG;
+    if (r->periodic && (Lx == 2 || Ly == 2)) return OR_ERR_ARG;
+    r->N = Lx * Ly;
+    int B = 0;
+    for (int y = 0; y < Ly; ++y) {
+        for (int x = 0; x < Lx; ++x) {
+            int a = x + Lx * y;
+            if (Lx > 1 && (x + 1 < Lx || r->periodic)) {
+                r->bond_a[B] = a; r->bond_b[B] = ((x + 1) % Lx) + Lx * y; ++B;
+            }
+            if (Ly > 1 && (y + 1 < Ly || r->periodic)) {
+                r->bond_a[B] = a; r->bond_b[B] = x + Lx * ((y + 1) % Ly); ++B;
+            }
+        }
+    }
+    r->B = B;
+    for (int b = 0; b < B; ++b)
+        r->bond_m[b] = (1ull << r->bond_a[b]) | (1ull << r->bond_b[b]);
+    return OR_OK;
+}
+
+/* Fixed-point rate tables.  A bond move has |A| = |h_b| (aligned or
+ * anti-aligned), times dt, times the importance-sampling ratio
+ * w(child)/w(parent) of Sec. IV.B.  A jump has |A| = gamma and ratio 1
+ * (it clears bit k on both sides, so i == j and the differing sites are
+ * unchanged). */
+static void or_build_rates(or_run *r) {
+    double hv[2];
+    hv[0] = fabs(r->Jx - r->Jy);
+    hv[1] = fabs(r->Jx + r->Jy);
+    double w_off = 1.0, w_inv = 1.0;
+    if (r->guide_kind == 1) { w_off = exp(-r->guide_p); w_inv = 1.0 / w_off; }
+    for (int b = 0; b < r->B; ++b) {
+        for (int h = 0; h < 2; ++h) {
+            double base = hv[h] * r->dt;
+            for (int c = 0; c < 4; ++c) {
+                double x = base;
+                if (r->guide_kind == 1) {
+                    if (c == 1) x = base * w_off;
+                    else if (c == 2) x = base * w_inv;
+                } else if (r->guide_kind == 2) {
+                    double ra = r->site_r[r->bond_a[b]], rb = r->site_r[r->bond_b[b]];
+                    double fa = (c & 2) ? (1.0 / ra) : ra;   /* site a differed -> becomes equal */
+                    double fb = (c & 1) ? (1.0 / rb) : rb;
+                    double ratio = fa * fb;
+                    x = base * ratio;
+                }
+                r->rate_q[b][h][c] = or_q(x);
+            }
+        }
+    }
+    r->jump_q = or_q(r->gamma * r->dt);
+    /* on-site cross term: q = dt |Jz| |zsum(i) - zsum(j)| */
+    double cbase = r->dt * fabs(r->Jz);
+    for (int c = 0; c <= 2 * r->B; ++c) {
+        double x = cbase * (double)c;
+        double ip = floor(x);
+        r->cross_int[c] = (uint32_t)ip;
+        r->cross_frac[c] = or_q(x - ip);
+    }
+    r->shift_gain = r->delta / r->dt;
+}
+
+void or_destroy(or_run *r) {
+    if (!r) return;
+    free(r->L);
+    free(r->series);
+    free(r);
+}
+
+or_run *or_create(int Lx, int Ly, int periodic, double Jx, double Jy, double Jz,
+                  double gamma, double dt, int64_t target, int32_t n_a,
+                  int guide_kind, double guide_p, const double *site_r,
+                  uint64_t seed, double delta, double S0, int64_t n0,
+                  int control, int64_t t_eq_override) {
+    or_run *r = (or_run *)calloc(1, sizeof(or_run));
+    if (!r) return NULL;
+    r->Lx = Lx; r->Ly = Ly; r->periodic = periodic;
+    r->Jx = Jx; r->Jy = Jy; r->Jz = Jz; r->gamma = gamma; r->dt = dt;
+    r->target = target; r->n_a = n_a; r->control = control;
+    r->guide_kind = guide_kind; r->guide_p = guide_p;
+    r->seed = seed; r->delta = delta; r->S0 = S0; r->n0 = n0;
+    r->t_eq_override = t_eq_override;
+    if (or_build_lattice(r) != OR_OK || !(dt > 0.0) || gamma < 0.0 || target <= 0 ||
+        n_a < 0 || guide_kind < 0 || guide_kind > 2 || n0 < 0 || n0 > 2147483647 ||
+        (control != 0 && control != 1)) {
+        free(r);
+        return NULL;
+    }
+    for (int k = 0; k < r->N; ++k) r->site_r[k] = 1.0;
+    if (guide_kind == 2) {
+        if (!site_r) { free(r); return NULL; }
+        for (int k = 0; k < r->N; ++k) {
+            if (!(site_r[k] > 0.0 && site_r[k] <= 1.0)) { free(r); return NULL; }
+            r->site_r[k] = site_r[k];
+        }
+    }
+    or_build_rates(r);
+    r->nobs = 5 + r->N + 3 * r->B + 4;
+    r->capL = 1024;
+    r->L = (or_entry *)malloc(sizeof(or_entry) * (size_t)r->capL);
+    if (!r->L) { free(r); return NULL; }
+    /* initial state: n0 real walkers on |down...down><down...down| */
+    r->M = 0;
+    if (n0 > 0) { r->L[0].ket = 0; r->L[0].bra = 0; r->L[0].re = n0; r->L[0].im = 0; r->M = 1; }
+    r->S = S0;
+    r->variable = 0;
+    r->t = 0;
+    r->t_var = -1;
+    r->t_eq = -1;
+    r->Qprev = (control == 0) ? n0 : n0;   /* both measures equal n0 initially */
+    return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* draws                                                                     */
+/* ------------------------------------------------------------------------ */
+static void or_draw_block(or_run *r, uint64_t ket, uint64_t bra, uint32_t w, int part,
+                          uint32_t block, uint32_t out[4]) {
+    if (r->inj) {
+        for (int q = 0; q < 4; ++q) {
+            if (r->pinj < r->ninj) out[q] = r->inj[r->pinj++];
+            else { out[q] = 0xFFFFFFFFu; r->inj_short = 1; }
+        }
+        return;
+    }
+    uint32_t ctr[4], key[2];
+    ctr[0] = (uint32_t)ket;          /* N <= 32: the words themselves are unique */
+    ctr[1] = (uint32_t)bra;
+    if (r->N > 32) {                 /* wider words: fold the high halves in */
+        ctr[0] ^= (uint32_t)(ket >> 32) * 0x9E3779B9u;
+        ctr[1] ^= (uint32_t)(bra >> 32) * 0x85EBCA6Bu;
+    }
+    ctr[2] = w;
+    ctr[3] = ((uint32_t)part << 16) | block;
+    key[0] = (uint32_t)r->seed;
+    key[1] = (uint32_t)(r->seed >> 32) ^ (uint32_t)r->t;
+    or_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* move enumeration (element rules derived from the Lindblad equation of     */
+/* Sec. III.A and its Kronecker form in Sec. III.C)                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t cket, cbra;
+    int kind;           /* 0 ket bond flip, 1 bra bond flip, 2 jump */
+    double Are, Aim;    /* complex element A = L~[child, parent] */
+    uint64_t rate;      /* q(|A| dt w_child / w_parent) */
+} or_move;
+
+static int or_moves_of(const or_run *r, uint64_t i, uint64_t j, or_move *mv) {
+    int K = 0;
+    for (int b = 0; b < r->B; ++b) {           /* -i H rho: child (i ^ m_b, j), A = -i h_b(i) */
+        double h = or_hb(r, i, b);
+        int al = or_bit(i, r->bond_a[b]) != or_bit(i, r->bond_b[b]);
+        mv[K].cket = i ^ r->bond_m[b]; mv[K].cbra = j; mv[K].kind = 0;
+        mv[K].Are = 0.0; mv[K].Aim = -h;
+        mv[K].rate = r->rate_q[b][al][or_ratio_class(r, i, j, b)];
+        ++K;
+    }
+    for (int b = 0; b < r->B; ++b) {           /* +i rho H: child (i, j ^ m_b), A = +i h_b(j) */
+        double h = or_hb(r, j, b);
+        int al = or_bit(j, r->bond_a[b]) != or_bit(j, r->bond_b[b]);
+        mv[K].cket = i; mv[K].cbra = j ^ r->bond_m[b]; mv[K].kind = 1;
+        mv[K].Are = 0.0; mv[K].Aim = h;
+        mv[K].rate = r->rate_q[b][al][or_ratio_class(r, i, j, b)];
+        ++K;
+    }
+    for (int k = 0; k < r->N; ++k) {           /* gamma sigma^- rho sigma^+: needs bit k up on both sides */
+        int ok = or_bit(i, k) && or_bit(j, k);
+        mv[K].cket = i & ~(1ull << k); mv[K].cbra = j & ~(1ull << k); mv[K].kind = 2;
+        mv[K].Are = ok ? r->gamma : 0.0; mv[K].Aim = 0.0;
+        mv[K].rate = ok ? r->jump_q : 0;
+        ++K;
+    }
+    return K;
+}
+
+/* ------------------------------------------------------------------------ */
+/* one step                                                                  */
+/* ------------------------------------------------------------------------ */
+static int or_cmp_key(uint64_t ka, uint64_t ba, uint64_t kb, uint64_t bb) {
+    if (ba != bb) return ba < bb ? -1 : 1;
+    if (ka != kb) return ka < kb ? -1 : 1;
+    return 0;
+}
+
+static int or_spawn_cmp(const void *pa, const void *pb) {
+    const or_spawn *a = (const or_spawn *)pa, *b = (const or_spawn *)pb;
+    return or_cmp_key(a->ket, a->bra, b->ket, b->bra);
+}
+
+typedef struct { or_spawn *v; int64_t n, cap; } or_spawn_vec;
+
+static int or_push(or_spawn_vec *sv, uint64_t ket, uint64_t bra, int32_t dre, int32_t dim, int init) {
+    if (sv->n == sv->cap) {
+        int64_t nc = sv->cap ? 2 * sv->cap : 4096;
+        or_spawn *nv = (or_spawn *)realloc(sv->v, sizeof(or_spawn) * (size_t)nc);
+        if (!nv) return OR_ERR_OOM;
+        sv->v = nv; sv->cap = nc;
+    }
+    or_spawn *s = &sv->v[sv->n++];
+    s->ket = ket; s->bra = bra; s->dre = dre; s->dim = dim; s->init = init;
+    return OR_OK;
+}
+
+static void or_estimate(or_run *r, int64_t *est);
+static int or_series_append(or_run *r, const int64_t *est);
+
+int or_step(or_run *r, int64_t nsteps) {
+    or_move mv[2 * OR_MAX_BONDS + OR_MAX_SITES];
+    for (int64_t it = 0; it < nsteps; ++it) {
+        /* death/clone table for this step: p_c = dt ((gamma/2) c + S), c = n(i) + n(j) */
+        uint32_t d_int[2 * OR_MAX_SITES + 1];
+        uint64_t d_frac[2 * OR_MAX_SITES + 1];
+        int d_sgn[2 * OR_MAX_SITES + 1];
+        double g2 = 0.5 * r->gamma;
+        for (int c = 0; c <= 2 * r->N; ++c) {
+            double a = g2 * (double)c;
+            double b = a + r->S;
+            double p = r->dt * b;
+            double ap = fabs(p);
+            double ip = floor(ap);
+            d_int[c] = (uint32_t)ip;
+            d_frac[c] = or_q(ap - ip);
+            d_sgn[c] = (p > 0.0) ? 1 : ((p < 0.0) ? -1 : 0);
+        }
+
+        or_spawn_vec sv = {0, 0, 0};
+        int err = OR_OK;
+        /* (i) spawning and (ii) death/clone, all from rho(t) and S(t) (Euler step) */
+        for (int64_t e = 0; e < r->M && err == OR_OK; ++e) {
+            uint64_t i = r->L[e].ket, j = r->L[e].bra;
+            int64_t re = r->L[e].re, im = r->L[e].im;
+            int64_t nre = re < 0 ? -re : re, nim = im < 0 ? -im : im;
+            int init = (r->n_a == 0) || (i == j) || (nre + nim > (int64_t)r->n_a);
+            int K = or_moves_of(r, i, j, mv);
+            uint64_t T = 0;
+            for (int k = 0; k < K; ++k) T += mv[k].rate;
+            uint64_t natt = (T + 0xFFFFFFFFull) >> 32;
+            if (natt < 1) natt = 1;
+            int cd = or_popc(i) + or_popc(j);
+            int dz = or_zsum(r, i) - or_zsum(r, j);
+            int adz = dz < 0 ? -dz : dz;
+            /* Im part of the diagonal element, d = -(E(i) - E(j)) = -Jz dz */
+            int sgn_d = 0;
+            if (dz != 0 && r->Jz != 0.0) sgn_d = ((r->Jz > 0.0) == (dz > 0)) ? -1 : 1;
+            int64_t dre = 0, dim = 0;
+            for (int part = 0; part < 2; ++part) {
+                int64_t pop = part == 0 ? re : im;
+                int64_t n = pop < 0 ? -pop : pop;
+                int sig = pop < 0 ? -1 : 1;
+                for (int64_t w = 0; w < n; ++w) {
+                    uint32_t x[4];
+                    or_draw_block(r, i, j, (uint32_t)w, part, 0, x);
+                    /* death (p > 0) or cloning (p < 0) on the walker's own part */
+                    int64_t cnt = (int64_t)d_int[cd] + ((uint64_t)x[1] < d_frac[cd] ? 1 : 0);
+                    if (part == 0) dre -= (int64_t)d_sgn[cd] * sig * cnt;
+                    else dim -= (int64_t)d_sgn[cd] * sig * cnt;
+                    /* on-site transfer from the imaginary part of the diagonal element */
+                    int64_t cc = (int64_t)r->cross_int[adz] + ((uint64_t)x[2] < r->cross_frac[adz] ? 1 : 0);
+                    if (part == 0) dim += (int64_t)sig * sgn_d * cc;
+                    else dre -= (int64_t)sig * sgn_d * cc;
+                    /* spawning attempts */
+                    uint32_t xb[4];
+                    uint32_t cur_block = 0;
+                    for (uint64_t a = 0; a < natt; ++a) {
+                        uint32_t u;
+                        if (a == 0) u = x[0];
+                        else if (a == 1) u = x[3];
+                        else {
+                            uint32_t blk = 1u + (uint32_t)((a - 2) / 4);
+                            if (blk != cur_block) { or_draw_block(r, i, j, (uint32_t)w, part, blk, xb); cur_block = blk; }
+                            u = xb[(a - 2) % 4];
+                        }
+                        uint64_t v = (uint64_t)u * natt;
+                        if (v >= T) continue;
+                        uint64_t cum = 0;
+                        int k = 0;
+                        for (; k < K; ++k) { cum += mv[k].rate; if (v < cum) break; }
+                        /* child type and sign: Delta rho_child = A * rho_parent (Sec. III.C rules) */
+                        int32_t cre = 0, cim = 0;
+                        double Ar = mv[k].Are, Ai = mv[k].Aim;
+                        if (part == 0) {            /* real parent of sign sig */
+                            if (Ar != 0.0) cre = sig * (Ar > 0.0 ? 1 : -1);
+                            else cim = sig * (Ai > 0.0 ? 1 : -1);
+                        } else {                    /* imaginary parent i*sig */
+                            if (Ar != 0.0) cim = sig * (Ar > 0.0 ? 1 : -1);
+                            else cre = -sig * (Ai > 0.0 ? 1 : -1);
+                        }
+                        err = or_push(&sv, mv[k].cket, mv[k].cbra, cre, cim, init);
+                        if (err != OR_OK) break;
+                    }
+                    if (err != OR_OK) break;
+                }
+                if (err != OR_OK) break;
+            }
+            r->L[e].re = re + dre;
+            r->L[e].im = im + dim;
+        }
+        if (err != OR_OK) { free(sv.v); return err; }
+        r->last_spawns = sv.n;
+
+        /* (iii) annihilation: sort the spawns, then one linear merge */
+        if (sv.n > 1) qsort(sv.v, (size_t)sv.n, sizeof(or_spawn), or_spawn_cmp);
+        int64_t cap = r->M + sv.n + 1;
+        or_entry *out = (or_entry *)malloc(sizeof(or_entry) * (size_t)cap);
+        if (!out) { free(sv.v); return OR_ERR_OOM; }
+        int64_t a = 0, b = 0, m = 0;
+        while (a < r->M || b < sv.n) {
+            uint64_t ket, bra;
+            if (b >= sv.n || (a < r->M && or_cmp_key(r->L[a].ket, r->L[a].bra, sv.v[b].ket, sv.v[b].bra) <= 0)) {
+                ket = r->L[a].ket; bra = r->L[a].bra;
+            } else {
+                ket = sv.v[b].ket; bra = sv.v[b].bra;
+            }
+            int occupied = (a < r->M && r->L[a].ket == ket && r->L[a].bra == bra);
+            int64_t sre = 0, sim = 0;
+            if (occupied) { sre = r->L[a].re; sim = r->L[a].im; ++a; }
+            /* initiator rule (Sec. IV.A): a non-initiator child survives only on an
+             * occupied or a diagonal configuration */
+            int open = occupied || (ket == bra) || (r->n_a == 0);
+            while (b < sv.n && sv.v[b].ket == ket && sv.v[b].bra == bra) {
+                if (open || sv.v[b].init) { sre += sv.v[b].dre; sim += sv.v[b].dim; }
+                ++b;
+            }
+            if (sre == 0 && sim == 0) continue;
+            if (sre > 2147483647LL || sre < -2147483647LL || sim > 2147483647LL || sim < -2147483647LL) {
+                free(out); free(sv.v); return OR_ERR_OVERFLOW;
+            }
+            out[m].ket = ket; out[m].bra = bra; out[m].re = sre; out[m].im = sim; ++m;
+        }
+        free(sv.v);
+        free(r->L);
+        r->L = out; r->M = m; r->capL = cap;
+
+        /* estimators on rho(t+1), then the shift update of Sec. III.C */
+        int64_t est[5 + OR_MAX_SITES + 3 * OR_MAX_BONDS + 4];
+        or_estimate(r, est);
+        int64_t Q = (r->control == 0) ? est[2] : est[3];
+        if (r->variable) {
+            if (Q > 0 && r->Qprev > 0) {
+                double ratio = (double)Q / (double)r->Qprev;
+                double lg = or_series_log(ratio);
+                double inc = r->shift_gain * lg;
+                r->S = r->S + inc;
+            }
+        } else if (Q >= r->target) {
+            r->variable = 1;
+            r->t_var = r->t + 1;
+            if (r->t_eq_override >= 0) r->t_eq = r->t_var + r->t_eq_override;
+            else {
+                double span = 10.0 / (r->gamma * r->dt);
+                r->t_eq = r->t_var + (int64_t)ceil(span);
+            }
+        }
+        r->Qprev = Q;
+        r->t += 1;
+        if (r->variable && r->t >= r->t_eq) {
+            int e2 = or_series_append(r, est);
+            if (e2 != OR_OK) return e2;
+        }
+    }
+    return OR_OK;
+}
+
+/* Estimator numerators over the current list, all integers (Sec. III.A):
+ *   [0] Tr Re rho, [1] Tr Im rho, [2] N_w = sum |Re rho_ii|, [3] W = sum |re|+|im|,
+ *   [4] M = occupied configurations,
+ *   [5 .. 5+N)        sum_i z_k(i) Re rho_ii            (per-site sigma^z)
+ *   [5+N .. +B)       sum_i z_a z_b Re rho_ii           (per-bond zz)
+ *   [.. +B)           sum over i^j == m_b of Re rho_ij  (per-bond xx)
+ *   [.. +B)           same with -1 if i is aligned on b, +1 if not (per-bond yy)
+ *   [.. +4)           sums over sites / bonds of the four blocks above.
+ * Importance weights divide the xx/yy numerators afterwards (Sec. IV.B). */
+static void or_estimate(or_run *r, int64_t *est) {
+    int N = r->N, B = r->B;
+    int nobs = r->nobs;
+    for (int k = 0; k < nobs; ++k) est[k] = 0;
+    int oz = 5, ozz = 5 + N, oxx = 5 + N + B, oyy = 5 + N + 2 * B, oag = 5 + N + 3 * B;
+    for (int64_t e = 0; e < r->M; ++e) {
+        uint64_t i = r->L[e].ket, j = r->L[e].bra;
+        int64_t re = r->L[e].re, im = r->L[e].im;
+        est[3] += (re < 0 ? -re : re) + (im < 0 ? -im : im);
+        est[4] += 1;
+        if (i == j) {
+            est[0] += re;
+            est[1] += im;
+            est[2] += re < 0 ? -re : re;
+            for (int k = 0; k < N; ++k) est[oz + k] += or_bit(i, k) ? re : -re;
+            for (int b = 0; b < B; ++b)
+                est[ozz + b] += (or_bit(i, r->bond_a[b]) == or_bit(i, r->bond_b[b])) ? re : -re;
+        } else {
+            uint64_t d = i ^ j;
+            if (or_popc(d) == 2) {
+                for (int b = 0; b < B; ++b) {
+                    if (r->bond_m[b] != d) continue;
+                    est[oxx + b] += re;
+                    int aligned = or_bit(i, r->bond_a[b]) == or_bit(i, r->bond_b[b]);
+                    est[oyy + b] += aligned ? -re : re;
+                }
+            }
+        }
+    }
+    for (int k = 0; k < N; ++k) est[oag + 0] += est[oz + k];
+    for (int b = 0; b < B; ++b) {
+        est[oag + 1] += est[ozz + b];
+        est[oag + 2] += est[oxx + b];
+        est[oag + 3] += est[oyy + b];
+    }
+}
+
+static int or_series_append(or_run *r, const int64_t *est) {
+    if (r->nseries == r->capseries) {
+        int64_t nc = r->capseries ? 2 * r->capseries : 1024;
+        int64_t *ns = (int64_t *)realloc(r->series, sizeof(int64_t) * (size_t)(nc * r->nobs));
+        if (!ns) return OR_ERR_OOM;
+        r->series = ns; r->capseries = nc;
+    }
+    memcpy(r->series + r->nseries * r->nobs, est, sizeof(int64_t) * (size_t)r->nobs);
+    r->nseries += 1;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* accessors for the tests                                                   */
+/* ------------------------------------------------------------------------ */
+int or_nobs(const or_run *r) { return r->nobs; }
+int or_nsites(const or_run *r) { return r->N; }
+int or_nbonds(const or_run *r) { return r->B; }
+int64_t or_size(const or_run *r) { return r->M; }
+int64_t or_last_spawns(const or_run *r) { return r->last_spawns; }
+
+void or_bonds(const or_run *r, int32_t *a, int32_t *b) {
+    for (int k = 0; k < r->B; ++k) { a[k] = r->bond_a[k]; b[k] = r->bond_b[k]; }
+}
+
+/* scalar state: t, S, variable, Qprev, t_var, t_eq */
+void or_get_state(const or_run *r, int64_t *t, double *S, int32_t *variable, int64_t *Qprev,
+                  int64_t *t_var, int64_t *t_eq) {
+    *t = r->t; *S = r->S; *variable = r->variable; *Qprev = r->Qprev; *t_var = r->t_var; *t_eq = r->t_eq;
+}
+
+void or_set_state(or_run *r, int64_t t, double S, int32_t variable, int64_t Qprev,
+                  int64_t t_var, int64_t t_eq) {
+    r->t = t; r->S = S; r->variable = variable; r->Qprev = Qprev; r->t_var = t_var; r->t_eq = t_eq;
+}
+
+int64_t or_export(const or_run *r, uint64_t *ket, uint64_t *bra, int32_t *re, int32_t *im, int64_t cap) {
+    int64_t n = r->M < cap ? r->M : cap;
+    for (int64_t e = 0; e < n; ++e) {
+        ket[e] = r->L[e].ket; bra[e] = r->L[e].bra;
+        re[e] = (int32_t)r->L[e].re; im[e] = (int32_t)r->L[e].im;
+    }
+    return r->M;
+}
+
+/* Replace the walker list; entries must be sorted by (bra, ket), unique and non-zero. */
+int or_import(or_run *r, const uint64_t *ket, const uint64_t *bra, const int32_t *re,
+              const int32_t *im, int64_t n) {
+    for (int64_t e = 0; e < n; ++e) {
+        if (re[e] == 0 && im[e] == 0) return OR_ERR_ARG;
+        if (e > 0 && or_cmp_key(ket[e - 1], bra[e - 1], ket[e], bra[e]) >= 0) return OR_ERR_ARG;
+        if (r->N < 64 && ((ket[e] >> r->N) || (bra[e] >> r->N))) return OR_ERR_ARG;
+    }
+    or_entry *L = (or_entry *)malloc(sizeof(or_entry) * (size_t)(n > 0 ? n : 1));
+    if (!L) return OR_ERR_OOM;
+    for (int64_t e = 0; e < n; ++e) { L[e].ket = ket[e]; L[e].bra = bra[e]; L[e].re = re[e]; L[e].im = im[e]; }
+    free(r->L);
+    r->L = L; r->M = n; r->capL = n > 0 ? n : 1;
+    return OR_OK;
+}
+
+void or_estimates_now(or_run *r, int64_t *est) { or_estimate(r, est); }
+
+int64_t or_series(const or_run *r, int64_t *out, int64_t cap_rows) {
+    int64_t n = r->nseries < cap_rows ? r->nseries : cap_rows;
+    if (out && n > 0) memcpy(out, r->series, sizeof(int64_t) * (size_t)(n * r->nobs));
+    return r->nseries;
+}
+
+/* All moves of configuration (i, j) in move order, with the complex element
+ * A = L~[child, parent] and the fixed-point rate.  Returns the move count. */
+int or_moves(const or_run *r, uint64_t i, uint64_t j, uint64_t *cket, uint64_t *cbra,
+             int32_t *kind, double *Are, double *Aim, uint64_t *rate) {
+    or_move mv[2 * OR_MAX_BONDS + OR_MAX_SITES];
+    int K = or_moves_of(r, i, j, mv);
+    for (int k = 0; k < K; ++k) {
+        cket[k] = mv[k].cket; cbra[k] = mv[k].cbra; kind[k] = mv[k].kind;
+        Are[k] = mv[k].Are; Aim[k] = mv[k].Aim; rate[k] = mv[k].rate;
+    }
+    return K;
+}
+
+/* Diagonal element of the shifted Liouvillian at (i, j):
+ * -(gamma/2)(n(i)+n(j)) - S - i (E(i) - E(j)),  E(s) = Jz zsum(s). */
+void or_diag(const or_run *r, uint64_t i, uint64_t j, double *Dre, double *Dim) {
+    double g2 = 0.5 * r->gamma;
+    *Dre = -(g2 * (double)(or_popc(i) + or_popc(j))) - r->S;
+    *Dim = -(r->Jz * (double)(or_zsum(r, i) - or_zsum(r, j)));
+}
+
+/* Inject a uniform stream: each Philox block draw takes the next four words
+ * instead (in the order the step makes its draws).  NULL restores Philox.
+ * Returns 1 if the last step ran past the end of the stream. */
+int or_inject(or_run *r, const uint32_t *u, int64_t n) {
+    int short_ = r->inj_short;
+    r->inj = u; r->ninj = n; r->pinj = 0; r->inj_short = 0;
+    return short_;
+}
+int64_t or_injected_used(const or_run *r) { return r->pinj; }

@@ -1,0 +1,49 @@
+"""Write the stored exact values the tests compare against.
+
+Calls only ``oracle/exact.py`` (Kronecker Liouvillian and its null vector),
+never the CUDA path.  Run from the repository root:
+
+    python tests/golden/make_golden.py
+
+Outputs (JSON, one file per lattice):
+  ness_2x2_open.json       dense SVD null vector, 256 x 256 Liouvillian
+  ness_3x3_periodic.json   Runge-Kutta fixed point, 262144-dim Liouvillian
+Both use the XYZ couplings Jx = 0.9, Jy = 1.0, Jz = 1.0 and gamma = 1 with
+Pauli matrices in H and sigma^- decay on every site (Nagy & Savona, Sec. V).
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import exact  # noqa: E402
+
+
+def dump(name, Lx, Ly, periodic, rho, resid, method):
+    ob = exact.observables(rho, Lx, Ly, periodic)
+    rec = dict(lattice=[Lx, Ly, periodic], Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0,
+               method=method, residual=float(resid), mz=ob["mz"],
+               z=ob["z"].tolist(), x=ob["x"].tolist(), y=ob["y"].tolist(),
+               xx=ob["xx"].tolist(), yy=ob["yy"].tolist(), zz=ob["zz"].tolist(),
+               bonds=exact.lattice_bonds(Lx, Ly, periodic))
+    with open(os.path.join(HERE, name), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(name, "mz", ob["mz"], "residual", resid)
+
+
+def main():
+    L = exact.liouvillian(2, 2, 0, 0.9, 1.0, 1.0, 1.0)
+    rho, s_min, _ = exact.ness_dense(L, 16)
+    resid = np.linalg.norm(L @ rho.reshape(-1, order="F"))
+    dump("ness_2x2_open.json", 2, 2, 0, rho, resid, "dense SVD null vector")
+    L = exact.liouvillian(3, 3, 1, 0.9, 1.0, 1.0, 1.0)
+    rho, resid = exact.ness_sparse(L, 512)
+    dump("ness_3x3_periodic.json", 3, 3, 1, rho, resid, "RK4 fixed point, sector popcount(i)+popcount(j) even")
+
+
+if __name__ == "__main__":
+    main()
