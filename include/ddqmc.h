@@ -1,0 +1,192 @@
+/*
+ * ddqmc.h -- C-ABI of libddqmc.so, a GB300 (sm_103a) implementation of one
+ * step of driven-dissipative quantum Monte Carlo (DDQMC): real-time FCIQMC
+ * sampling of the vectorised density matrix of an open spin-1/2 XYZ lattice
+ * under the shifted Liouvillian (Nagy & Savona, arXiv:1802.05931).
+ *
+ * Conventions shared by every call
+ *   - Return value: 0 (DDQMC_OK) on success, a negative DDQMC_ERR_* code
+ *     otherwise.  Errors found on the device (capacity, int32 overflow,
+ *     bounded-wait timeout) are sticky: once set, every later call on the run
+ *     returns the same code.  No C++ exception crosses this interface.
+ *   - Pointers named host_* or passed as plain arrays are HOST memory owned by
+ *     the caller; the run owns all of its device memory.
+ *   - A run is not thread-safe; separate runs may be driven from separate host
+ *     threads.  All device work of a run is issued on its CUDA stream.
+ *   - Basis: site k = x + Lx*y; bit k of a spin word is 1 when spin k is up.
+ *     A configuration |i><j| is the pair (ket i, bra j).  Walker lists are in
+ *     canonical order: by bra word, then by ket word.
+ *   - Model (Sec. V): H = sum over nearest-neighbour bonds of
+ *     Jx sx sx + Jy sy sy + Jz sz sz with Pauli matrices, and decay at rate
+ *     gamma through sigma^- on every site (Lindblad equation, Sec. III.A).
+ */
+#ifndef DDQMC_H
+#define DDQMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DDQMC_OK 0
+#define DDQMC_ERR_INVALID_ARG (-1)   /* a parameter or pointer is invalid */
+#define DDQMC_ERR_OOM (-2)           /* device or host allocation failed */
+#define DDQMC_ERR_CAPACITY (-3)      /* walker list or spawn buffer capacity exceeded (sticky) */
+#define DDQMC_ERR_OVERFLOW (-4)      /* a population left the int32 range (sticky) */
+#define DDQMC_ERR_TIMEOUT (-5)       /* a bounded device wait gave up (sticky) */
+#define DDQMC_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define DDQMC_ERR_UNSUPPORTED (-7)   /* valid parameters this build does not handle (N > 31) */
+
+#define DDQMC_MAX_SITES 31
+#define DDQMC_MAX_BONDS 64
+
+/* Lattice: Lx x Ly sites; periodic = 1 wraps both directions (then each
+ * periodic extent must be 1 or >= 3, since L = 2 would repeat bonds). */
+typedef struct {
+    int32_t Lx, Ly, periodic;
+} ddqmc_lattice;
+
+/* Importance sampling (Sec. IV.B): the population on |i><j| represents
+ * w_ij rho_ij and every off-diagonal rate is multiplied by w_child/w_parent.
+ *   kind 0: none (w = 1);
+ *   kind 1: uniform, w_ij = exp(-p) for every i != j, w_ii = 1 (the paper's
+ *           single-parameter scheme);
+ *   kind 2: site product, w_ij = prod over sites k where i and j differ of
+ *           site_ratio[k] (N values in (0, 1]), w_ii = 1.  site_ratio is read
+ *           during ddqmc_create only. */
+typedef struct {
+    int32_t kind;
+    double p;
+    const double *site_ratio;
+} ddqmc_guide;
+
+/* Options; fill with ddqmc_default_options() and override fields. */
+typedef struct {
+    uint64_t seed;             /* Philox key; default 1 */
+    double damping;            /* delta of the shift update (Sec. III.C); default 0.05 */
+    double shift0;             /* S before the target is reached; default -1.0 */
+    int64_t n0;                /* initial real walkers on |down..down><down..down|; default 1000 */
+    int32_t control;           /* 0: N_w = sum |Re rho_ii| (the paper's rule); 1: total sum |re|+|im| */
+    int64_t t_eq;              /* steps after the shift switches on before estimates
+                                  accumulate; < 0: ceil(10 / (gamma dt)) */
+    int64_t capacity_entries;  /* walker-list capacity (entries); <= 0: derived from the target */
+    int64_t capacity_spawns;   /* spawn-record capacity per step; <= 0: derived from the target */
+    void *cuda_stream;         /* cudaStream_t to issue work on; NULL: the run creates its own */
+} ddqmc_options;
+
+typedef struct ddqmc_run ddqmc_run;
+
+/* Steady-state estimates (ratios of time averages, Sec. III.A) with blocked
+ * standard errors, over the steps t >= t_eq.  Sigma^x and sigma^y are zero by
+ * the Z2 parity of the dynamics (every move flips an even number of spins
+ * across ket and bra), so they are not reported separately. */
+typedef struct {
+    int64_t t;                 /* completed steps */
+    double shift;              /* current S */
+    int32_t variable;          /* 1 once the shift update is on */
+    int64_t t_var, t_eq;       /* first variable-shift step; first accumulated step */
+    int64_t n_samples;         /* steps accumulated */
+    int64_t walkers;           /* sum |re|+|im| of the current list */
+    int64_t entries;           /* occupied configurations */
+    int64_t nw;                /* sum |Re rho_ii| of the current list */
+    int64_t trace_re, trace_im;
+    int32_t nsites, nbonds;
+    double walker_steps;       /* sum over completed steps of the walkers stepped */
+    double mz, mz_err;         /* M_z = (1/N) sum_k <sigma^z_k> (Sec. V.A) */
+    double xx, xx_err, yy, yy_err, zz, zz_err;     /* bond averages of <s s> */
+    double sz[DDQMC_MAX_SITES], sz_err[DDQMC_MAX_SITES];
+    double bond_xx[DDQMC_MAX_BONDS], bond_yy[DDQMC_MAX_BONDS], bond_zz[DDQMC_MAX_BONDS];
+} ddqmc_estimates;
+
+/* Scalar state of a run (for checkpoints and single-step comparisons). */
+typedef struct {
+    int64_t t;
+    double shift;
+    int32_t variable;
+    int64_t q_prev;            /* controlled weight after the last step */
+    int64_t t_var, t_eq;
+    int64_t entries;
+    int32_t status;            /* sticky device status (0 or a DDQMC_ERR_* code) */
+} ddqmc_state;
+
+/* Defaults for every option field.  Returns DDQMC_OK, or INVALID_ARG for NULL. */
+int ddqmc_default_options(ddqmc_options *opt);
+
+/* Create a run (Sec. III.C problem statement: lattice, couplings, gamma, dt,
+ * target population, initiator threshold I_limit = n_a (Sec. IV.A, 0 = none),
+ * importance guide).  Allocates all device memory, writes the initial list
+ * of opt->n0 real walkers on |down..down><down..down| and S = opt->shift0.
+ * guide and opt may be NULL (no importance sampling / defaults).
+ * Errors: INVALID_ARG (N > 64, dt <= 0, gamma < 0, target <= 0, n_a < 0,
+ * bad guide), UNSUPPORTED (N > 31), OOM, CUDA.  *out is NULL on error. */
+int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz,
+                 double gamma, double dt, int64_t target_walkers,
+                 int32_t initiator_threshold, const ddqmc_guide *guide,
+                 const ddqmc_options *opt, ddqmc_run **out);
+
+/* Advance nsteps DDQMC steps (Sec. III.C, one step = spawn + death/clone,
+ * annihilation under the initiator rule, estimators, shift update), issued
+ * on the run's stream; waits for completion and returns the sticky device
+ * status.  nsteps = 0 only reports the status. */
+int ddqmc_step(ddqmc_run *run, int64_t nsteps);
+
+/* Same as ddqmc_step but does not wait: returns after enqueueing the work;
+ * the device status is reported by the next waiting call. */
+int ddqmc_step_async(ddqmc_run *run, int64_t nsteps);
+
+/* Wait for the run's stream and return the sticky device status. */
+int ddqmc_sync(ddqmc_run *run);
+
+/* Steady-state estimates with blocked errors (waits for the stream). */
+int ddqmc_estimators(ddqmc_run *run, ddqmc_estimates *out);
+
+/* Integer estimator numerators of the current list (Sec. III.A):
+ * [0] Tr Re, [1] Tr Im, [2] N_w, [3] sum |re|+|im|, [4] entries,
+ * [5, 5+N) sum z_k Re rho_ii, then per bond zz, xx, yy numerators (B each),
+ * then the sums over sites/bonds of those four blocks.  Writes
+ * min(cap, nobs) values to host_out and nobs to *nobs. */
+int ddqmc_raw_estimators(ddqmc_run *run, int64_t *host_out, int32_t cap, int32_t *nobs);
+
+/* Exact integer blocking moments (Flyvbjerg-Petersen levels) of observable
+ * k against the trace: for each level l < levels, n (blocks), sum X,
+ * sum X^2, sum X*Y (Y = Tr Re block sums).  The 128-bit sums are returned as
+ * (lo, hi) pairs of 64-bit words, two's complement.  Arrays hold `levels`
+ * (resp. 2*levels) entries. */
+int ddqmc_blocking_moments(ddqmc_run *run, int32_t k, int32_t levels, int64_t *host_n,
+                           int64_t *host_sx, int64_t *host_sxx, int64_t *host_sxy);
+
+/* Copy the current walker list (canonical order) to host arrays of capacity
+ * cap; *n receives the list length (call with cap = 0 to query it). */
+int ddqmc_export_walkers(ddqmc_run *run, uint64_t *ket, uint64_t *bra, int32_t *re,
+                         int32_t *im, int64_t cap, int64_t *n);
+
+/* Replace the walker list with n host entries (strictly increasing canonical
+ * order, no all-zero entry, spin words within N bits) and set the step
+ * counter t and shift S; the shift stays in its variable phase iff
+ * variable != 0, with q_prev as the last controlled weight.  Clears the
+ * accumulated estimates and any sticky error. */
+int ddqmc_import_walkers(ddqmc_run *run, const uint64_t *ket, const uint64_t *bra,
+                         const int32_t *re, const int32_t *im, int64_t n, int64_t t,
+                         double S, int32_t variable, int64_t q_prev, int64_t t_var,
+                         int64_t t_eq);
+
+/* Scalar state (waits for the stream). */
+int ddqmc_get_state(ddqmc_run *run, ddqmc_state *out);
+
+/* Last step's spawn-record count and the list/spawn capacities (diagnostics
+ * and roofline accounting). */
+int ddqmc_get_counts(ddqmc_run *run, int64_t *spawn_records, int64_t *capacity_entries,
+                     int64_t *capacity_spawns);
+
+/* Free every resource of the run (NULL is ignored). */
+void ddqmc_destroy(ddqmc_run *run);
+
+/* Static description of a status code. */
+const char *ddqmc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDQMC_H */

@@ -556,7 +556,8 @@ int or_step(or_run *r, int64_t nsteps) {
             r->t_var = r->t + 1;
             if (r->t_eq_override >= 0) r->t_eq = r->t_var + r->t_eq_override;
             else {
-                double span = 10.0 / (r->gamma * r->dt);
+                double rate = r->gamma > 0.0 ? r->gamma : 1.0;
+                double span = 10.0 / (rate * r->dt);
                 r->t_eq = r->t_var + (int64_t)ceil(span);
             }
         }

@@ -1,0 +1,156 @@
+// Shared definitions of the DDQMC GPU path: record layout, per-run constant
+// tables, the device-resident step state, Philox4x32-10 and the series
+// logarithm.  Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ddq {
+
+constexpr int MAXN = 31;                      // sites: ket and bra words pack into 62 key bits
+constexpr int MAXB = 64;                      // bonds (2N for a periodic 2D lattice)
+constexpr int MAXK = 2 * MAXB + MAXN;         // moves per configuration
+constexpr int NOBS_MAX = 5 + MAXN + 3 * MAXB + 4;
+constexpr int LEVELS = 32;                    // blocking levels (block length 2^l)
+constexpr int MAXPASS = 8;                    // radix passes of 8 bits over 2N <= 62 key bits
+
+constexpr uint32_t ST_CAPACITY = 1u, ST_OVERFLOW = 2u, ST_TIMEOUT = 4u;
+
+// Spawn records carry the parent's initiator flag in bit 63; list keys never do.
+constexpr uint64_t FLAG_BIT = 1ull << 63;
+constexpr uint64_t KEY_MASK = ~FLAG_BIT;
+
+// One occupied configuration or one spawn record: packed key (bra << N | ket)
+// and the signed real / imaginary walker populations.  16 bytes, so a whole
+// record moves with one 128-bit load or store.
+struct __align__(16) Rec {
+    uint64_t key;
+    int32_t re;
+    int32_t im;
+};
+
+// Look-back status words: [epoch:30][flag:2][value:32].
+constexpr uint64_t LB_AGG = 1ull, LB_INC = 2ull;
+__device__ __forceinline__ uint64_t lb_pack(uint32_t epoch, uint64_t flag, uint32_t value) {
+    return ((uint64_t)(epoch & 0x3FFFFFFFu) << 34) | (flag << 32) | (uint64_t)value;
+}
+
+// Per-run constants, computed on the host at create time.
+struct RunParams {
+    int32_t N, B, K, nobs, npass, n_a, guide_kind, control;
+    int32_t sgn_h[2];          // sign of Jx - Jy (aligned bond) and Jx + Jy (anti-aligned)
+    int32_t sgn_jz;
+    int32_t pad0;
+    uint64_t nmask;            // (1 << N) - 1
+    uint64_t seed;
+    int64_t target;
+    int64_t t_eq_span;         // steps from the first variable-shift step to the first sample
+    double gamma_half, dt, shift_gain;
+    uint64_t jump_q;
+    uint64_t bond_m[MAXB];
+    int32_t bond_a[MAXB], bond_b[MAXB];
+    uint64_t rate_q[MAXB][2][4];      // [bond][anti-aligned][importance class]
+    uint32_t cross_int[2 * MAXB + 1];
+    uint64_t cross_frac[2 * MAXB + 1];
+    int8_t pair_bond[MAXN * MAXN];    // bond index of an (a, b) site pair, -1 if none
+};
+
+// Device-resident state of a run, updated by the kernels of each step.
+struct DevState {
+    int64_t t, t_var, t_eq, q_prev;
+    double S;
+    int32_t variable;
+    uint32_t status;
+    int64_t M;                 // entries of the current list
+    int64_t M_next;            // entries of the merged list (written by the last merge tile)
+    int64_t R;                 // spawn records of the step in progress
+    int64_t R_last;            // spawn records of the last completed step
+    uint32_t epoch;            // look-back epoch of the step in progress
+    uint32_t pad1;
+    uint32_t tickets[16];      // tile tickets: [0, 8) radix passes, 8 merge
+    int64_t walker_steps;      // sum over completed steps of the walkers stepped
+    int64_t W_cur;             // sum |re| + |im| of the current list
+    int64_t n_app;             // samples accumulated for blocking
+    uint32_t d_int[2 * MAXN + 1];
+    uint64_t d_frac[2 * MAXN + 1];
+    int32_t d_sgn[2 * MAXN + 1];
+    int64_t est[NOBS_MAX];     // estimator numerators of the step in progress
+    int64_t last_est[NOBS_MAX];
+    uint32_t hist[MAXPASS][256];
+};
+
+// One blocking cell: observable k at level l (block length 2^l).
+struct BlkCell {
+    int64_t n;                 // completed blocks
+    int64_t sx;                // sum of block sums
+    __int128 sxx;              // sum of squared block sums
+    __int128 sxy;              // sum of block sum x trace block sum
+    int64_t pend_x, pend_y;    // pending half-block
+    int32_t has_pend;
+    int32_t pad;
+};
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies with a Weyl-sequence key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t p0 = 0xD2511F53u * c.x, h0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t p1 = 0xCD9E8D57u * c.z, h1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(h1 ^ c.y ^ k0, p1, h0 ^ c.w ^ k1, p0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Natural logarithm from log x = e ln2 + 2 atanh((m-1)/(m+1)), x = m 2^e,
+// m in (1/sqrt2, sqrt2], atanh by its odd power series (15 terms), every
+// operation an explicitly rounded IEEE double operation in a fixed order.
+__device__ __forceinline__ double series_log(double x) {
+    if (!(x > 0.0)) return 0.0;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    int e = (int)((bits >> 52) & 0x7FFull);
+    if (e == 0) return 0.0;
+    e -= 1023;
+    double m = __longlong_as_double((long long)((bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+    if (m > 1.4142135623730951) { m = __dmul_rn(m, 0.5); e += 1; }
+    const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double z = __dmul_rn(s, s);
+    double p = __ddiv_rn(1.0, 29.0);
+    for (int k = 13; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, z), __ddiv_rn(1.0, (double)(2 * k + 1)));
+    return __dadd_rn(__dmul_rn((double)e, 0.6931471805599453), __dmul_rn(__dmul_rn(2.0, s), p));
+}
+
+__device__ __forceinline__ int64_t iabs64(int64_t v) { return v < 0 ? -v : v; }
+
+// Block-uniform read of the sticky status: every thread of the block takes the
+// same early exit, so no barrier is ever left waiting for an exited thread.
+__device__ __forceinline__ bool block_stopped(const DevState *st) {
+    __shared__ uint32_t s_stop;
+    if (threadIdx.x == 0) s_stop = *(volatile const uint32_t *)&st->status;
+    __syncthreads();
+    const bool stop = s_stop != 0u;
+    __syncthreads();
+    return stop;
+}
+
+// Bounded spin on a look-back status word; returns the word or 0 on timeout
+// (and records ST_TIMEOUT).
+__device__ __forceinline__ uint64_t lb_wait(const uint64_t *p, uint32_t epoch, uint32_t *status) {
+    const uint64_t want = (uint64_t)(epoch & 0x3FFFFFFFu);
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        const uint64_t w = *(volatile const uint64_t *)p;
+        if ((w >> 34) == want && ((w >> 32) & 3ull) != 0ull) return w;
+        if (it > 64) __nanosleep(64);
+    }
+    atomicOr(status, ST_TIMEOUT);
+    return 0;
+}
+
+__device__ __forceinline__ void lb_store(uint64_t *p, uint64_t w) {
+    *(volatile uint64_t *)p = w;
+}
+
+}  // namespace ddq

@@ -1,0 +1,691 @@
+// libddqmc.so: the C-ABI of the DDQMC GPU path (declared in include/ddqmc.h).
+//
+// One step (Sec. III.C) is five kinds of launch on the run's stream, none of
+// which needs a host round trip: spawn + death/clone, npass onesweep radix
+// passes, merge-path partition, merge + annihilation + estimators, finalize
+// (shift update, blocking, resets).  Every size a kernel needs is read from
+// the device-resident DevState.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ddqmc.h"
+#include "common.cuh"
+#include "finalize.cuh"
+#include "merge.cuh"
+#include "radix.cuh"
+#include "spawn.cuh"
+
+using namespace ddq;
+
+struct ddqmc_run {
+    RunParams hp;
+    RunParams *dP = nullptr;
+    DevState *dS = nullptr;
+    BlkCell *dBlk = nullptr;
+    Rec *L[2] = {nullptr, nullptr};
+    Rec *Sp[2] = {nullptr, nullptr};
+    uint64_t *lb_radix = nullptr;
+    uint64_t *lb_merge = nullptr;
+    int64_t *splits = nullptr;
+    int64_t mcap = 0, rcap = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int cur = 0;                 // which L buffer holds the current list
+    int g_spawn = 0, g_radix = 0, g_part = 0, g_merge = 0;
+    int guide_kind = 0;
+    double w_bond[MAXB];         // importance weight of a configuration differing on bond b only
+    int host_status = 0;         // sticky host-visible status
+};
+
+namespace {
+
+int status_code(uint32_t st) {
+    if (st & ST_TIMEOUT) return DDQMC_ERR_TIMEOUT;
+    if (st & ST_OVERFLOW) return DDQMC_ERR_OVERFLOW;
+    if (st & ST_CAPACITY) return DDQMC_ERR_CAPACITY;
+    return DDQMC_OK;
+}
+
+uint64_t fixed_rate(double x) { return (uint64_t)(x * 4294967296.0); }
+
+// Host-side death table for the shift S (same operation order as the device's).
+void host_death_table(const RunParams &P, double S, DevState &st) {
+    for (int c = 0; c <= 2 * P.N; ++c) {
+        const double a = P.gamma_half * (double)c;
+        const double b = a + S;
+        const double p = P.dt * b;
+        const double ap = std::fabs(p);
+        const double ip = std::floor(ap);
+        st.d_int[c] = (uint32_t)ip;
+        st.d_frac[c] = (uint64_t)((ap - ip) * 4294967296.0);
+        st.d_sgn[c] = p > 0.0 ? 1 : (p < 0.0 ? -1 : 0);
+    }
+}
+
+int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, double Jz, double gamma,
+                 double dt, int64_t target, int32_t n_a, const ddqmc_guide *guide, const ddqmc_options &o) {
+    RunParams &P = r->hp;
+    std::memset(&P, 0, sizeof(P));
+    const int Lx = lat->Lx, Ly = lat->Ly, per = lat->periodic ? 1 : 0;
+    if (Lx < 1 || Ly < 1 || (int64_t)Lx * Ly > 64) return DDQMC_ERR_INVALID_ARG;
+    if (per && (Lx == 2 || Ly == 2)) return DDQMC_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !(gamma >= 0.0) || target <= 0 || n_a < 0) return DDQMC_ERR_INVALID_ARG;
+    if (!std::isfinite(Jx) || !std::isfinite(Jy) || !std::isfinite(Jz) || !std::isfinite(gamma) || !std::isfinite(dt))
+        return DDQMC_ERR_INVALID_ARG;
+    if (o.n0 < 0 || o.n0 > 2147483647ll || (o.control != 0 && o.control != 1)) return DDQMC_ERR_INVALID_ARG;
+    const int N = Lx * Ly;
+    if (N > MAXN) return DDQMC_ERR_UNSUPPORTED;
+    P.N = N;
+    int B = 0;
+    // bonds: for each site in (y, x) order, the bond to the right, then the bond below
+    for (int y = 0; y < Ly; ++y)
+        for (int x = 0; x < Lx; ++x) {
+            const int a = x + Lx * y;
+            if (Lx > 1 && (x + 1 < Lx || per)) { P.bond_a[B] = a; P.bond_b[B] = (x + 1) % Lx + Lx * y; ++B; }
+            if (Ly > 1 && (y + 1 < Ly || per)) { P.bond_a[B] = a; P.bond_b[B] = x + Lx * ((y + 1) % Ly); ++B; }
+        }
+    P.B = B;
+    P.K = 2 * B + N;
+    P.nobs = 5 + N + 3 * B + 4;
+    P.npass = (2 * N + 7) / 8;
+    P.n_a = n_a;
+    P.control = o.control;
+    P.nmask = (1ull << N) - 1ull;
+    P.seed = o.seed;
+    P.target = target;
+    const double span_rate = gamma > 0.0 ? gamma : 1.0;
+    P.t_eq_span = o.t_eq >= 0 ? o.t_eq : (int64_t)std::ceil(10.0 / (span_rate * dt));
+    P.gamma_half = 0.5 * gamma;
+    P.dt = dt;
+    P.shift_gain = o.damping / dt;
+    P.sgn_h[0] = (Jx - Jy) > 0.0 ? 1 : ((Jx - Jy) < 0.0 ? -1 : 0);
+    P.sgn_h[1] = (Jx + Jy) > 0.0 ? 1 : ((Jx + Jy) < 0.0 ? -1 : 0);
+    P.sgn_jz = Jz > 0.0 ? 1 : (Jz < 0.0 ? -1 : 0);
+    for (int q = 0; q < N * N; ++q) P.pair_bond[q] = -1;
+    for (int b = 0; b < B; ++b) {
+        P.bond_m[b] = (1ull << P.bond_a[b]) | (1ull << P.bond_b[b]);
+        const int lo = P.bond_a[b] < P.bond_b[b] ? P.bond_a[b] : P.bond_b[b];
+        const int hi = P.bond_a[b] < P.bond_b[b] ? P.bond_b[b] : P.bond_a[b];
+        P.pair_bond[lo * N + hi] = (int8_t)b;
+    }
+    // importance sampling (Sec. IV.B)
+    int gk = guide ? guide->kind : 0;
+    if (gk < 0 || gk > 2) return DDQMC_ERR_INVALID_ARG;
+    double site_r[MAXN];
+    for (int k = 0; k < N; ++k) site_r[k] = 1.0;
+    double w_off = 1.0, w_inv = 1.0;
+    if (gk == 1) {
+        if (!std::isfinite(guide->p)) return DDQMC_ERR_INVALID_ARG;
+        w_off = std::exp(-guide->p);
+        w_inv = 1.0 / w_off;
+    }
+    if (gk == 2) {
+        if (!guide->site_ratio) return DDQMC_ERR_INVALID_ARG;
+        for (int k = 0; k < N; ++k) {
+            const double v = guide->site_ratio[k];
+            if (!(v > 0.0 && v <= 1.0)) return DDQMC_ERR_INVALID_ARG;
+            site_r[k] = v;
+        }
+    }
+    P.guide_kind = gk;
+    r->guide_kind = gk;
+    const double hval[2] = {std::fabs(Jx - Jy), std::fabs(Jx + Jy)};
+    for (int b = 0; b < B; ++b) {
+        r->w_bond[b] = gk == 1 ? w_off : (gk == 2 ? site_r[P.bond_a[b]] * site_r[P.bond_b[b]] : 1.0);
+        for (int h = 0; h < 2; ++h) {
+            const double base = hval[h] * dt;
+            for (int c = 0; c < 4; ++c) {
+                double x = base;
+                if (gk == 1) {
+                    if (c == 1) x = base * w_off;
+                    else if (c == 2) x = base * w_inv;
+                } else if (gk == 2) {
+                    const double ra = site_r[P.bond_a[b]], rb = site_r[P.bond_b[b]];
+                    const double fa = (c & 2) ? (1.0 / ra) : ra;
+                    const double fb = (c & 1) ? (1.0 / rb) : rb;
+                    const double ratio = fa * fb;
+                    x = base * ratio;
+                }
+                P.rate_q[b][h][c] = fixed_rate(x);
+            }
+        }
+    }
+    P.jump_q = fixed_rate(gamma * dt);
+    const double cbase = dt * std::fabs(Jz);
+    for (int c = 0; c <= 2 * B; ++c) {
+        const double x = cbase * (double)c;
+        const double ip = std::floor(x);
+        P.cross_int[c] = (uint32_t)ip;
+        P.cross_frac[c] = fixed_rate(x - ip);
+    }
+    return DDQMC_OK;
+}
+
+template <typename T>
+int dalloc(T **p, size_t n) {
+    if (n == 0) n = 1;
+    if (cudaMalloc((void **)p, n * sizeof(T)) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return DDQMC_ERR_OOM;
+    }
+    return DDQMC_OK;
+}
+
+int occupancy_grid(const void *fn, int tpb, size_t smem, int sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tpb, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * sms;
+}
+
+void free_run(ddqmc_run *r) {
+    if (!r) return;
+    cudaFree(r->dP);
+    cudaFree(r->dS);
+    cudaFree(r->dBlk);
+    cudaFree(r->L[0]);
+    cudaFree(r->L[1]);
+    cudaFree(r->Sp[0]);
+    cudaFree(r->Sp[1]);
+    cudaFree(r->lb_radix);
+    cudaFree(r->lb_merge);
+    cudaFree(r->splits);
+    if (r->own_stream && r->stream) cudaStreamDestroy(r->stream);
+    delete r;
+}
+
+int read_status(ddqmc_run *r) {
+    if (r->host_status) return r->host_status;
+    uint32_t st = 0;
+    if (cudaMemcpyAsync(&st, &r->dS->status, sizeof(st), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        r->host_status = DDQMC_ERR_CUDA;
+        return r->host_status;
+    }
+    r->host_status = status_code(st);
+    return r->host_status;
+}
+
+constexpr size_t SP_SMEM = sizeof(SpawnShared);
+constexpr size_t RX_SMEM = sizeof(RadixShared);
+constexpr size_t MG_SMEM = sizeof(MergeShared);
+
+int enqueue_steps(ddqmc_run *r, int64_t nsteps) {
+    const RunParams &P = r->hp;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        Rec *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
+        k_spawn_death<<<r->g_spawn, SP_TPB, SP_SMEM, r->stream>>>(r->dP, r->dS, Lc, r->Sp[0], r->rcap);
+        for (int p = 0; p < P.npass; ++p)
+            k_radix_pass<<<r->g_radix, RX_TPB, RX_SMEM, r->stream>>>(r->Sp[p & 1], r->Sp[(p + 1) & 1], r->dS,
+                                                                     r->lb_radix, p, 8 * p, r->rcap);
+        const Rec *sorted = r->Sp[P.npass & 1];
+        k_merge_partition<<<r->g_part, 256, 0, r->stream>>>(Lc, sorted, r->dS, r->splits, r->rcap);
+        k_merge<<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits, r->lb_merge,
+                                                            r->rcap, r->mcap);
+        k_finalize<<<1, FN_TPB, 0, r->stream>>>(r->dP, r->dS, r->dBlk);
+        r->cur ^= 1;
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+        r->host_status = DDQMC_ERR_CUDA;
+        return r->host_status;
+    }
+    return DDQMC_OK;
+}
+
+struct LevelStat {
+    int64_t n;
+    double R, err;
+};
+
+// Delta-method variance of sum X / sum Y from exact integer moments of one level.
+LevelStat level_stat(const BlkCell &cx, const BlkCell &cy) {
+    LevelStat o;
+    o.n = cx.n;
+    o.R = cy.sx != 0 ? (double)cx.sx / (double)cy.sx : NAN;
+    o.err = NAN;
+    if (cx.n < 2 || cy.sx == 0) return o;
+    const __int128 n = cx.n;
+    const __int128 A = n * cx.sxx - (__int128)cx.sx * cx.sx;
+    const __int128 C = n * cx.sxy - (__int128)cx.sx * cy.sx;
+    const __int128 D = n * cy.sxx - (__int128)cy.sx * cy.sx;
+    const long double X = (long double)cx.sx, Y = (long double)cy.sx;
+    const long double num = (long double)A * Y * Y - 2.0L * X * Y * (long double)C + X * X * (long double)D;
+    const long double den = (long double)(cx.n - 1) * Y * Y * Y * Y;
+    const long double var = num / den;
+    o.err = var >= 0 ? (double)std::sqrt(var) : NAN;
+    return o;
+}
+
+// Blocked ratio estimate: R over all samples and the plateau error.
+void blocked_ratio(const std::vector<BlkCell> &cells, int k, double &R, double &err) {
+    std::vector<LevelStat> lv;
+    for (int l = 0; l < LEVELS; ++l) {
+        const BlkCell &cx = cells[(size_t)k * LEVELS + l];
+        if (cx.n < 1) break;
+        lv.push_back(level_stat(cx, cells[l]));
+    }
+    R = lv.empty() ? NAN : lv[0].R;
+    err = NAN;
+    std::vector<int> valid;
+    for (int l = 0; l < (int)lv.size(); ++l)
+        if (lv[l].n >= 16 && lv[l].err == lv[l].err) valid.push_back(l);
+    if (valid.empty()) return;
+    auto de = [&](int l) { return lv[l].err / std::sqrt(2.0 * (double)(lv[l].n - 1)); };
+    for (size_t a = 0; a < valid.size(); ++a) {
+        const int kk = valid[a];
+        bool ok = true;
+        for (size_t b = a + 1; b < valid.size() && ok; ++b) {
+            const int q = valid[b];
+            if (lv[q].err > lv[kk].err + 2.0 * std::sqrt(de(kk) * de(kk) + de(q) * de(q))) ok = false;
+        }
+        if (ok) { err = lv[kk].err; return; }
+    }
+    err = lv[valid.back()].err;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ddqmc_default_options(ddqmc_options *o) {
+    if (!o) return DDQMC_ERR_INVALID_ARG;
+    o->seed = 1;
+    o->damping = 0.05;
+    o->shift0 = -1.0;
+    o->n0 = 1000;
+    o->control = 0;
+    o->t_eq = -1;
+    o->capacity_entries = 0;
+    o->capacity_spawns = 0;
+    o->cuda_stream = nullptr;
+    return DDQMC_OK;
+}
+
+int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, double gamma, double dt,
+                 int64_t target_walkers, int32_t initiator_threshold, const ddqmc_guide *guide,
+                 const ddqmc_options *opt, ddqmc_run **out) {
+    if (!out) return DDQMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!lattice) return DDQMC_ERR_INVALID_ARG;
+    ddqmc_options o;
+    ddqmc_default_options(&o);
+    if (opt) o = *opt;
+    ddqmc_run *r = new (std::nothrow) ddqmc_run();
+    if (!r) return DDQMC_ERR_OOM;
+    int rc = build_params(r, lattice, Jx, Jy, Jz, gamma, dt, target_walkers, initiator_threshold, guide, o);
+    if (rc != DDQMC_OK) { delete r; return rc; }
+    if (cudaGetDevice(&r->device) != cudaSuccess) { cudaGetLastError(); delete r; return DDQMC_ERR_CUDA; }
+    // capacities
+    int64_t mcap = o.capacity_entries, rcap = o.capacity_spawns;
+    const int64_t scale = o.control == 1 ? 2 : 64;
+    if (mcap <= 0) mcap = target_walkers * scale + 1024;
+    if (rcap <= 0) rcap = target_walkers * scale + 1024;
+    if (mcap < 4096) mcap = 4096;
+    if (rcap < 4096) rcap = 4096;
+    const int64_t lim = (1ll << 31) - 1;
+    if (mcap > lim) mcap = lim;
+    if (rcap > lim) rcap = lim;
+    r->mcap = mcap;
+    r->rcap = rcap;
+    if (o.cuda_stream) {
+        r->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete r;
+            return DDQMC_ERR_CUDA;
+        }
+        r->own_stream = true;
+    }
+    const int64_t rtiles = rcap / RX_TILE + 2;
+    const int64_t mtiles = (mcap + rcap) / MG_TILE + 2;
+    rc = DDQMC_OK;
+    rc |= dalloc(&r->dP, 1);
+    rc |= dalloc(&r->dS, 1);
+    rc |= dalloc(&r->dBlk, (size_t)NOBS_MAX * LEVELS);
+    rc |= dalloc(&r->L[0], (size_t)mcap);
+    rc |= dalloc(&r->L[1], (size_t)mcap);
+    rc |= dalloc(&r->Sp[0], (size_t)rcap);
+    rc |= dalloc(&r->Sp[1], (size_t)rcap);
+    rc |= dalloc(&r->lb_radix, (size_t)rtiles * 256);
+    rc |= dalloc(&r->lb_merge, (size_t)mtiles);
+    rc |= dalloc(&r->splits, (size_t)mtiles + 1);
+    if (rc != DDQMC_OK) { free_run(r); return DDQMC_ERR_OOM; }
+    // kernel shapes
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device);
+    if (sms < 1) sms = 1;
+    bool ok = cudaFuncSetAttribute(k_spawn_death, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
+    r->g_spawn = occupancy_grid((const void *)k_spawn_death, SP_TPB, SP_SMEM, sms);
+    r->g_radix = occupancy_grid((const void *)k_radix_pass, RX_TPB, RX_SMEM, sms);
+    r->g_merge = occupancy_grid((const void *)k_merge, MG_TPB, MG_SMEM, sms);
+    r->g_part = 4 * sms;
+    // initial state
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.t = 0;
+    hs.t_var = -1;
+    hs.t_eq = -1;
+    hs.q_prev = o.n0;
+    hs.S = o.shift0;
+    hs.variable = 0;
+    hs.M = o.n0 > 0 ? 1 : 0;
+    hs.W_cur = o.n0;
+    hs.epoch = 16;
+    host_death_table(r->hp, o.shift0, hs);
+    Rec first;
+    first.key = 0;
+    first.re = (int32_t)o.n0;
+    first.im = 0;
+    bool okc = cudaMemcpyAsync(r->dP, &r->hp, sizeof(RunParams), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    okc = okc && cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    okc = okc && cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * (size_t)NOBS_MAX * LEVELS, r->stream) == cudaSuccess;
+    okc = okc && cudaMemsetAsync(r->lb_radix, 0, sizeof(uint64_t) * (size_t)rtiles * 256, r->stream) == cudaSuccess;
+    okc = okc && cudaMemsetAsync(r->lb_merge, 0, sizeof(uint64_t) * (size_t)mtiles, r->stream) == cudaSuccess;
+    okc = okc && cudaMemcpyAsync(r->L[0], &first, sizeof(Rec), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    okc = okc && cudaStreamSynchronize(r->stream) == cudaSuccess;
+    if (!okc) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
+    r->cur = 0;
+    *out = r;
+    return DDQMC_OK;
+}
+
+int ddqmc_step_async(ddqmc_run *r, int64_t nsteps) {
+    if (!r || nsteps < 0) return DDQMC_ERR_INVALID_ARG;
+    if (r->host_status) return r->host_status;
+    return enqueue_steps(r, nsteps);
+}
+
+int ddqmc_sync(ddqmc_run *r) {
+    if (!r) return DDQMC_ERR_INVALID_ARG;
+    return read_status(r);
+}
+
+int ddqmc_step(ddqmc_run *r, int64_t nsteps) {
+    const int rc = ddqmc_step_async(r, nsteps);
+    if (rc != DDQMC_OK) return rc;
+    return read_status(r);
+}
+
+int ddqmc_get_state(ddqmc_run *r, ddqmc_state *out) {
+    if (!r || !out) return DDQMC_ERR_INVALID_ARG;
+    DevState hs;
+    if (cudaMemcpyAsync(&hs, r->dS, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    out->t = hs.t;
+    out->shift = hs.S;
+    out->variable = hs.variable;
+    out->q_prev = hs.q_prev;
+    out->t_var = hs.t_var;
+    out->t_eq = hs.t_eq;
+    out->entries = hs.M;
+    out->status = r->host_status ? r->host_status : status_code(hs.status);
+    return DDQMC_OK;
+}
+
+int ddqmc_get_counts(ddqmc_run *r, int64_t *spawn_records, int64_t *capacity_entries, int64_t *capacity_spawns) {
+    if (!r) return DDQMC_ERR_INVALID_ARG;
+    int64_t R = 0;
+    if (cudaMemcpyAsync(&R, &r->dS->R_last, sizeof(R), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    if (spawn_records) *spawn_records = R;
+    if (capacity_entries) *capacity_entries = r->mcap;
+    if (capacity_spawns) *capacity_spawns = r->rcap;
+    return DDQMC_OK;
+}
+
+int ddqmc_raw_estimators(ddqmc_run *r, int64_t *host_out, int32_t cap, int32_t *nobs) {
+    if (!r || (cap > 0 && !host_out)) return DDQMC_ERR_INVALID_ARG;
+    const int n = r->hp.nobs;
+    if (nobs) *nobs = n;
+    const int m = cap < n ? cap : n;
+    if (m > 0) {
+        if (cudaMemcpyAsync(host_out, r->dS->last_est, sizeof(int64_t) * (size_t)m, cudaMemcpyDeviceToHost,
+                            r->stream) != cudaSuccess ||
+            cudaStreamSynchronize(r->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return DDQMC_ERR_CUDA;
+        }
+    }
+    return DDQMC_OK;
+}
+
+int ddqmc_blocking_moments(ddqmc_run *r, int32_t k, int32_t levels, int64_t *hn, int64_t *hsx, int64_t *hsxx,
+                           int64_t *hsxy) {
+    if (!r || k < 0 || k >= r->hp.nobs || levels < 0 || levels > LEVELS) return DDQMC_ERR_INVALID_ARG;
+    std::vector<BlkCell> cells(LEVELS);
+    if (cudaMemcpyAsync(cells.data(), r->dBlk + (size_t)k * LEVELS, sizeof(BlkCell) * LEVELS,
+                        cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    for (int l = 0; l < levels; ++l) {
+        if (hn) hn[l] = cells[l].n;
+        if (hsx) hsx[l] = cells[l].sx;
+        if (hsxx) {
+            hsxx[2 * l] = (int64_t)(uint64_t)(unsigned __int128)cells[l].sxx;
+            hsxx[2 * l + 1] = (int64_t)(uint64_t)((unsigned __int128)cells[l].sxx >> 64);
+        }
+        if (hsxy) {
+            hsxy[2 * l] = (int64_t)(uint64_t)(unsigned __int128)cells[l].sxy;
+            hsxy[2 * l + 1] = (int64_t)(uint64_t)((unsigned __int128)cells[l].sxy >> 64);
+        }
+    }
+    return DDQMC_OK;
+}
+
+int ddqmc_estimators(ddqmc_run *r, ddqmc_estimates *out) {
+    if (!r || !out) return DDQMC_ERR_INVALID_ARG;
+    const RunParams &P = r->hp;
+    DevState hs;
+    std::vector<BlkCell> cells((size_t)P.nobs * LEVELS);
+    if (cudaMemcpyAsync(&hs, r->dS, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaMemcpyAsync(cells.data(), r->dBlk, sizeof(BlkCell) * cells.size(), cudaMemcpyDeviceToHost,
+                        r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    std::memset(out, 0, sizeof(*out));
+    const int N = P.N, B = P.B, core = 5 + N + 3 * B;
+    out->t = hs.t;
+    out->shift = hs.S;
+    out->variable = hs.variable;
+    out->t_var = hs.t_var;
+    out->t_eq = hs.t_eq;
+    out->n_samples = hs.n_app;
+    out->walkers = hs.last_est[3];
+    out->entries = hs.M;
+    out->nw = hs.last_est[2];
+    out->trace_re = hs.last_est[0];
+    out->trace_im = hs.last_est[1];
+    out->nsites = N;
+    out->nbonds = B;
+    out->walker_steps = (double)hs.walker_steps;
+    if (hs.t == 0) {            // nothing stepped yet: report the initial list
+        out->walkers = hs.W_cur;
+        out->nw = hs.W_cur;
+        out->trace_re = hs.W_cur;
+    }
+    double R, e;
+    blocked_ratio(cells, core + 0, R, e);
+    out->mz = R / N;
+    out->mz_err = e / N;
+    for (int k = 0; k < N; ++k) {
+        blocked_ratio(cells, 5 + k, R, e);
+        out->sz[k] = R;
+        out->sz_err[k] = e;
+    }
+    bool uniform_w = true;
+    for (int b = 1; b < B; ++b) uniform_w = uniform_w && r->w_bond[b] == r->w_bond[0];
+    for (int b = 0; b < B; ++b) {
+        blocked_ratio(cells, 5 + N + b, R, e);
+        out->bond_zz[b] = R;
+        blocked_ratio(cells, 5 + N + B + b, R, e);
+        out->bond_xx[b] = R / r->w_bond[b];
+        blocked_ratio(cells, 5 + N + 2 * B + b, R, e);
+        out->bond_yy[b] = R / r->w_bond[b];
+    }
+    blocked_ratio(cells, core + 1, R, e);
+    out->zz = B ? R / B : NAN;
+    out->zz_err = B ? e / B : NAN;
+    const double w0 = B ? r->w_bond[0] : 1.0;
+    blocked_ratio(cells, core + 2, R, e);
+    out->xx = B ? R / (B * w0) : NAN;
+    out->xx_err = B ? e / (B * w0) : NAN;
+    blocked_ratio(cells, core + 3, R, e);
+    out->yy = B ? R / (B * w0) : NAN;
+    out->yy_err = B ? e / (B * w0) : NAN;
+    if (!uniform_w && B) {      // per-bond weights differ: average the per-bond estimates
+        double sx = 0, sy = 0, ex = 0, ey = 0;
+        for (int b = 0; b < B; ++b) {
+            sx += out->bond_xx[b];
+            sy += out->bond_yy[b];
+            double Rb, eb;
+            blocked_ratio(cells, 5 + N + B + b, Rb, eb);
+            ex += (eb / r->w_bond[b]) * (eb / r->w_bond[b]);
+            blocked_ratio(cells, 5 + N + 2 * B + b, Rb, eb);
+            ey += (eb / r->w_bond[b]) * (eb / r->w_bond[b]);
+        }
+        out->xx = sx / B;
+        out->yy = sy / B;
+        out->xx_err = std::sqrt(ex) / B;
+        out->yy_err = std::sqrt(ey) / B;
+    }
+    return r->host_status ? r->host_status : status_code(hs.status);
+}
+
+int ddqmc_export_walkers(ddqmc_run *r, uint64_t *ket, uint64_t *bra, int32_t *re, int32_t *im, int64_t cap,
+                         int64_t *n) {
+    if (!r || !n || (cap > 0 && (!ket || !bra || !re || !im))) return DDQMC_ERR_INVALID_ARG;
+    int64_t M = 0;
+    if (cudaMemcpyAsync(&M, &r->dS->M, sizeof(M), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    *n = M;
+    const int64_t m = cap < M ? cap : M;
+    if (m <= 0) return DDQMC_OK;
+    Rec *h = nullptr;
+    if (cudaMallocHost((void **)&h, sizeof(Rec) * (size_t)m) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_OOM;
+    }
+    int rc = DDQMC_OK;
+    if (cudaMemcpyAsync(h, r->L[r->cur], sizeof(Rec) * (size_t)m, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        rc = DDQMC_ERR_CUDA;
+    } else {
+        const int N = r->hp.N;
+        const uint64_t mask = r->hp.nmask;
+        for (int64_t q = 0; q < m; ++q) {
+            ket[q] = h[q].key & mask;
+            bra[q] = h[q].key >> N;
+            re[q] = h[q].re;
+            im[q] = h[q].im;
+        }
+    }
+    cudaFreeHost(h);
+    return rc;
+}
+
+int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra, const int32_t *re,
+                         const int32_t *im, int64_t n, int64_t t, double S, int32_t variable, int64_t q_prev,
+                         int64_t t_var, int64_t t_eq) {
+    if (!r || n < 0 || (n > 0 && (!ket || !bra || !re || !im)) || t < 0 || !std::isfinite(S))
+        return DDQMC_ERR_INVALID_ARG;
+    if (n > r->mcap) return DDQMC_ERR_CAPACITY;
+    const int N = r->hp.N;
+    const uint64_t mask = r->hp.nmask;
+    Rec *h = nullptr;
+    if (n > 0 && cudaMallocHost((void **)&h, sizeof(Rec) * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_OOM;
+    }
+    for (int64_t q = 0; q < n; ++q) {
+        const bool bad = (ket[q] & ~mask) || (bra[q] & ~mask) || (re[q] == 0 && im[q] == 0) ||
+                         (q > 0 && (bra[q - 1] > bra[q] || (bra[q - 1] == bra[q] && ket[q - 1] >= ket[q])));
+        if (bad) { cudaFreeHost(h); return DDQMC_ERR_INVALID_ARG; }
+        h[q].key = (bra[q] << N) | ket[q];
+        h[q].re = re[q];
+        h[q].im = im[q];
+    }
+    // make sure no earlier work of this run is in flight before rewriting its
+    // state; the look-back epoch keeps counting so that no status word left
+    // by an earlier step can match a later one
+    uint32_t old_epoch = 0;
+    if (cudaMemcpyAsync(&old_epoch, &r->dS->epoch, sizeof(old_epoch), cudaMemcpyDeviceToHost, r->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h);
+        return DDQMC_ERR_CUDA;
+    }
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.t = t;
+    hs.S = S;
+    hs.variable = variable ? 1 : 0;
+    hs.q_prev = q_prev;
+    hs.t_var = t_var;
+    hs.t_eq = t_eq;
+    hs.M = n;
+    int64_t W = 0;
+    for (int64_t q = 0; q < n; ++q) W += (int64_t)std::llabs(re[q]) + (int64_t)std::llabs(im[q]);
+    hs.W_cur = W;
+    hs.epoch = (old_epoch + 16u) & 0x3FFFFFFFu;
+    host_death_table(r->hp, S, hs);
+    bool ok = true;
+    if (n > 0)
+        ok = cudaMemcpyAsync(r->L[r->cur], h, sizeof(Rec) * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * (size_t)NOBS_MAX * LEVELS, r->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
+    if (h) cudaFreeHost(h);
+    if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    r->host_status = 0;
+    return DDQMC_OK;
+}
+
+void ddqmc_destroy(ddqmc_run *r) {
+    if (!r) return;
+    if (r->stream) cudaStreamSynchronize(r->stream);
+    free_run(r);
+}
+
+const char *ddqmc_strerror(int status) {
+    switch (status) {
+        case DDQMC_OK: return "success";
+        case DDQMC_ERR_INVALID_ARG: return "invalid argument";
+        case DDQMC_ERR_OOM: return "out of memory";
+        case DDQMC_ERR_CAPACITY: return "walker list or spawn buffer capacity exceeded";
+        case DDQMC_ERR_OVERFLOW: return "walker population left the int32 range";
+        case DDQMC_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case DDQMC_ERR_CUDA: return "CUDA runtime error";
+        case DDQMC_ERR_UNSUPPORTED: return "unsupported size (more than 31 sites)";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

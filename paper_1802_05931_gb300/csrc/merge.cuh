@@ -1,0 +1,291 @@
+// Annihilation, part 2, and the estimators (Sec. III.C annihilation; Sec. IV.A
+// initiator rule; Sec. III.A estimators).
+//
+// The sorted list L_t (unique keys, populations already updated by
+// death/clone) and the sorted spawn records S (repeated keys) are merged
+// along the merge path, L first on equal keys, in tiles of MG_TILE merged
+// positions.  In the merged order every configuration forms one run: its
+// L_t entry (if present) followed by all its spawn records.  The thread that
+// holds the first element of a run sums the run (reading past its own range,
+// and past the tile, when the run continues) under the initiator rule:
+// records whose parent was not an initiator count only when the configuration
+// is occupied in L_t or diagonal.  Non-zero sums are compacted into L_{t+1}
+// in order: a block scan gives offsets inside the tile and a decoupled
+// look-back over earlier tiles gives the tile's output offset.  Every kept
+// entry is added to the integer estimator numerators on the way out.
+#pragma once
+
+#include "common.cuh"
+
+namespace ddq {
+
+constexpr int MG_TPB = 256;
+constexpr int MG_WARPS = MG_TPB / 32;
+constexpr int MG_IPT = 8;
+constexpr int MG_TILE = MG_TPB * MG_IPT;
+
+// merge-path split of output diagonal `diag`: number of L elements among the
+// first `diag` merged elements (L before S on equal keys)
+__device__ __forceinline__ int64_t merge_split(const Rec *L, int64_t M, const Rec *S, int64_t R, int64_t diag) {
+    int64_t lo = diag > R ? diag - R : 0;
+    int64_t hi = diag < M ? diag : M;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (L[mid].key <= (S[diag - 1 - mid].key & KEY_MASK)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_merge_partition(const Rec *__restrict__ L, const Rec *__restrict__ S, DevState *__restrict__ st,
+                                  int64_t *__restrict__ splits, int64_t rcap) {
+    if (st->status) return;
+    const int64_t M = st->M;
+    int64_t R = st->R;
+    if (R > rcap) R = rcap;
+    const int64_t tot = M + R;
+    const int64_t ntiles = (tot + MG_TILE - 1) / MG_TILE;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t diag = t * MG_TILE;
+        if (diag > tot) diag = tot;
+        splits[t] = merge_split(L, M, S, R, diag);
+    }
+}
+
+struct MergeShared {
+    Rec buf[MG_TILE];                 // L part then S part of the tile; later the output staging
+    unsigned long long est[NOBS_MAX];
+    uint64_t bond_m[MAXB];
+    int8_t bond_a[MAXB], bond_b[MAXB];
+    int8_t pair_bond[MAXN * MAXN];
+    uint32_t scan_tmp[MG_WARPS];
+    int64_t tile, a0, a1, out_base;
+    uint64_t prev_key;
+    int32_t has_prev;
+};
+
+__device__ __forceinline__ void add_estimators(MergeShared &s, const RunParams &P, uint64_t key, int32_t re,
+                                               int32_t im) {
+    const int N = P.N, B = P.B;
+    const uint64_t i = key & P.nmask, j = key >> N;
+    if (i == j) {
+        atomicAdd(&s.est[0], (unsigned long long)(int64_t)re);
+        atomicAdd(&s.est[1], (unsigned long long)(int64_t)im);
+        atomicAdd(&s.est[2], (unsigned long long)(int64_t)(re < 0 ? -re : re));
+        for (int k = 0; k < N; ++k)
+            atomicAdd(&s.est[5 + k], (unsigned long long)(int64_t)(((i >> k) & 1ull) ? re : -re));
+        for (int b = 0; b < B; ++b) {
+            const bool al = ((i >> s.bond_a[b]) & 1ull) == ((i >> s.bond_b[b]) & 1ull);
+            atomicAdd(&s.est[5 + N + b], (unsigned long long)(int64_t)(al ? re : -re));
+        }
+    } else {
+        const uint64_t d = i ^ j;
+        if (__popcll(d) == 2) {
+            const int a = __ffsll((long long)d) - 1;
+            const int b2 = 63 - __clzll((long long)d);
+            const int b = s.pair_bond[a * N + b2];
+            if (b >= 0) {
+                const bool al = ((i >> s.bond_a[b]) & 1ull) == ((i >> s.bond_b[b]) & 1ull);
+                atomicAdd(&s.est[5 + N + B + b], (unsigned long long)(int64_t)re);
+                atomicAdd(&s.est[5 + N + 2 * B + b], (unsigned long long)(int64_t)(al ? -re : re));
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MG_TPB)
+k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const Rec *__restrict__ S,
+        Rec *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
+        uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MergeShared &s = *reinterpret_cast<MergeShared *>(smem_raw);
+    const RunParams &P = *Pp;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (block_stopped(st)) return;
+    const int64_t M = st->M;
+    int64_t R = st->R;
+    if (R > rcap) R = rcap;
+    const int64_t tot = M + R;
+    const int64_t ntiles = (tot + MG_TILE - 1) / MG_TILE;
+    const uint32_t epoch = st->epoch + (uint32_t)MAXPASS;
+    const int N = P.N;
+    const uint64_t nmask = P.nmask;
+    const bool no_init = P.n_a == 0;
+
+    for (int q = tid; q < NOBS_MAX; q += MG_TPB) s.est[q] = 0ull;
+    for (int q = tid; q < P.B; q += MG_TPB) {
+        s.bond_m[q] = P.bond_m[q];
+        s.bond_a[q] = (int8_t)P.bond_a[q];
+        s.bond_b[q] = (int8_t)P.bond_b[q];
+    }
+    for (int q = tid; q < N * N; q += MG_TPB) s.pair_bond[q] = P.pair_bond[q];
+    int64_t my_w = 0, my_m = 0;
+    uint32_t local_status = 0;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            const int64_t tile = (int64_t)atomicAdd(&st->tickets[8], 1u);
+            s.tile = tile;
+            if (tile < ntiles) {
+                const int64_t d0 = tile * MG_TILE;
+                s.a0 = splits[tile];
+                s.a1 = splits[tile + 1];
+                const int64_t b0 = d0 - s.a0;
+                uint64_t pk = 0;
+                int hp = 0;
+                if (s.a0 > 0) { pk = L[s.a0 - 1].key; hp = 1; }
+                if (b0 > 0) {
+                    const uint64_t k2 = S[b0 - 1].key & KEY_MASK;
+                    if (!hp || k2 > pk) pk = k2;
+                    hp = 1;
+                }
+                s.prev_key = pk;
+                s.has_prev = hp;
+            }
+        }
+        __syncthreads();
+        const int64_t tile = s.tile;
+        if (tile >= ntiles) break;
+        const int64_t d0 = tile * MG_TILE;
+        const int64_t d1 = (d0 + MG_TILE < tot) ? d0 + MG_TILE : tot;
+        const int64_t a0 = s.a0, a1 = s.a1;
+        const int64_t b0 = d0 - a0, b1 = d1 - a1;
+        const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
+        // load the tile's L and S elements (S keys keep their flag)
+        for (int q = tid; q < na; q += MG_TPB) s.buf[q] = L[a0 + q];
+        for (int q = tid; q < nb; q += MG_TPB) s.buf[na + q] = S[b0 + q];
+        __syncthreads();
+        const Rec *sL = s.buf;
+        const Rec *sS = s.buf + na;
+
+        // this thread's merge-path start inside the tile
+        const int dloc = tid * MG_IPT;
+        Rec outv[MG_IPT];
+        int nout = 0;
+        if (dloc < na + nb) {
+            int lo = dloc > nb ? dloc - nb : 0;
+            int hi = dloc < na ? dloc : na;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sL[mid].key <= (sS[dloc - 1 - mid].key & KEY_MASK)) lo = mid + 1;
+                else hi = mid;
+            }
+            int ia = lo, ib = dloc - lo;
+            // key of the merged element just before this thread's range
+            uint64_t prev = 0;
+            bool hprev = false;
+            if (dloc == 0) { prev = s.prev_key; hprev = s.has_prev != 0; }
+            else {
+                if (ia > 0) { prev = sL[ia - 1].key; hprev = true; }
+                if (ib > 0) {
+                    const uint64_t k2 = sS[ib - 1].key & KEY_MASK;
+                    if (!hprev || k2 > prev) prev = k2;
+                    hprev = true;
+                }
+            }
+            const int dend = (dloc + MG_IPT < na + nb) ? dloc + MG_IPT : na + nb;
+            for (int dpos = dloc; dpos < dend; ++dpos) {
+                bool fromL;
+                if (ia >= na) fromL = false;
+                else if (ib >= nb) fromL = true;
+                else fromL = sL[ia].key <= (sS[ib].key & KEY_MASK);
+                const uint64_t key = fromL ? sL[ia].key : (sS[ib].key & KEY_MASK);
+                const bool head = !hprev || key != prev;
+                prev = key;
+                hprev = true;
+                if (head) {
+                    int64_t sre = 0, sim = 0;
+                    const bool occupied = fromL;
+                    if (fromL) { sre = sL[ia].re; sim = sL[ia].im; }
+                    const bool open = occupied || no_init || ((key & nmask) == (key >> N));
+                    // walk the spawn records of this key (may run past the tile)
+                    int64_t q = ib;
+                    for (;;) {
+                        Rec v;
+                        if (q < nb) v = sS[q];
+                        else if (b0 + q < R) v = S[b0 + q];
+                        else break;
+                        if ((v.key & KEY_MASK) != key) break;
+                        if (open || (v.key & FLAG_BIT)) { sre += v.re; sim += v.im; }
+                        ++q;
+                    }
+                    if (sre != 0 || sim != 0) {
+                        if (iabs64(sre) > 2147483647ll || iabs64(sim) > 2147483647ll) local_status |= ST_OVERFLOW;
+                        outv[nout].key = key;
+                        outv[nout].re = (int32_t)sre;
+                        outv[nout].im = (int32_t)sim;
+                        ++nout;
+                    }
+                }
+                if (fromL) ++ia; else ++ib;
+            }
+        }
+        // block scan of output counts
+        int x = nout;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= off) x += y;
+        }
+        __syncthreads();                 // everyone is done reading s.buf
+        if (lane == 31) s.scan_tmp[warp] = (uint32_t)x;
+        __syncthreads();
+        uint32_t pre = 0, total = 0;
+        for (int w = 0; w < MG_WARPS; ++w) {
+            const uint32_t v = s.scan_tmp[w];
+            if (w < warp) pre += v;
+            total += v;
+        }
+        const uint32_t my_off = pre + (uint32_t)(x - nout);
+        for (int q = 0; q < nout; ++q) s.buf[my_off + q] = outv[q];
+        if (tid == 0) {
+            uint64_t *myw = lookback + tile;
+            uint64_t excl = 0;
+            if (tile == 0) {
+                lb_store(myw, lb_pack(epoch, LB_INC, total));
+            } else {
+                lb_store(myw, lb_pack(epoch, LB_AGG, total));
+                for (int64_t jt = tile - 1; jt >= 0; --jt) {
+                    const uint64_t w = lb_wait(lookback + jt, epoch, &st->status);
+                    excl += (uint32_t)w;
+                    if (((w >> 32) & 3ull) != LB_AGG) break;
+                }
+                lb_store(myw, lb_pack(epoch, LB_INC, (uint32_t)(excl + total)));
+            }
+            s.out_base = (int64_t)excl;
+            if (tile == ntiles - 1) st->M_next = (int64_t)(excl + total);
+        }
+        __syncthreads();
+        const int64_t ob = s.out_base;
+        if (ob + (int64_t)total > mcap) {
+            if (tid == 0) local_status |= ST_CAPACITY;
+        } else {
+            for (uint32_t q = tid; q < total; q += MG_TPB) {
+                const Rec v = s.buf[q];
+                out[ob + q] = v;
+                my_w += iabs64(v.re) + iabs64(v.im);
+                my_m += 1;
+                const uint64_t i = v.key & nmask, j = v.key >> N;
+                if (i == j || __popcll(i ^ j) == 2) add_estimators(s, P, v.key, v.re, v.im);
+            }
+        }
+    }
+    // flush the block's estimator partials
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        my_w += __shfl_xor_sync(0xFFFFFFFFu, my_w, off);
+        my_m += __shfl_xor_sync(0xFFFFFFFFu, my_m, off);
+    }
+    if (lane == 0) {
+        atomicAdd(&s.est[3], (unsigned long long)my_w);
+        atomicAdd(&s.est[4], (unsigned long long)my_m);
+    }
+    if (local_status) atomicOr(&st->status, local_status);
+    __syncthreads();
+    const int nobs_core = 5 + N + 3 * P.B;
+    for (int q = tid; q < nobs_core; q += MG_TPB)
+        if (s.est[q]) atomicAdd((unsigned long long *)&st->est[q], s.est[q]);
+}
+
+}  // namespace ddq

@@ -1,0 +1,156 @@
+// Annihilation, part 1: sort the spawn records of one step by configuration
+// key (Sec. III.C, annihilation; Sec. II rule (iii)).
+//
+// Least-significant-digit radix sort in the single-pass ("onesweep") style:
+// the digit histograms of every pass were counted by the spawn kernel, so a
+// pass reads each record once and writes it once.  A persistent grid takes
+// tiles in order from an atomic ticket; each tile ranks its records by digit
+// with warp match/ballot multisplit (stable), publishes its per-digit counts,
+// resolves its global per-digit offsets by decoupled look-back over earlier
+// tiles (bounded waits), stages the tile in digit order in shared memory and
+// writes runs of equal digits to consecutive global addresses.  The initiator
+// flag (bit 63) is carried, never sorted.
+#pragma once
+
+#include "common.cuh"
+
+namespace ddq {
+
+constexpr int RX_TPB = 256;                  // one thread per digit value
+constexpr int RX_WARPS = RX_TPB / 32;
+constexpr int RX_IPT = 8;                    // records per thread
+constexpr int RX_TILE = RX_TPB * RX_IPT;     // 2048 records per tile
+
+struct RadixShared {
+    Rec stage[RX_TILE];
+    uint32_t whist[RX_WARPS][256];
+    uint32_t bucket[256];      // start of each digit's bucket in the output
+    uint32_t dstart[256];      // start of each digit inside the staged tile
+    int64_t gbase[256];        // output index of staged position 0 of each digit
+    uint32_t scan_tmp[RX_WARPS];
+    int64_t tile;
+};
+
+__global__ void __launch_bounds__(RX_TPB)
+k_radix_pass(const Rec *__restrict__ in, Rec *__restrict__ out, DevState *__restrict__ st,
+             uint64_t *__restrict__ lookback, int pass, int shift, int64_t cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RadixShared &s = *reinterpret_cast<RadixShared *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (block_stopped(st)) return;
+    int64_t R = st->R;
+    if (R > cap) R = cap;
+    const int64_t ntiles = (R + RX_TILE - 1) / RX_TILE;
+    const uint32_t epoch = st->epoch + (uint32_t)pass;
+
+    // exclusive scan of this pass's global histogram -> bucket starts
+    {
+        const uint32_t v = st->hist[pass][tid];
+        uint32_t x = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) s.scan_tmp[warp] = x;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; ++w) pre += s.scan_tmp[w];
+        s.bucket[tid] = pre + x - v;
+        __syncthreads();
+    }
+
+    for (;;) {
+        if (tid == 0) s.tile = (int64_t)atomicAdd(&st->tickets[pass], 1u);
+        __syncthreads();
+        const int64_t tile = s.tile;
+        if (tile >= ntiles) break;
+        const int64_t t0 = tile * RX_TILE;
+        for (int q = tid; q < RX_WARPS * 256; q += RX_TPB) (&s.whist[0][0])[q] = 0u;
+        __syncthreads();
+
+        // load: warp w owns records [t0 + w*32*IPT, +32*IPT), item i at + i*32 + lane
+        Rec r[RX_IPT];
+        uint32_t dg[RX_IPT];
+        uint32_t rk[RX_IPT];
+        const int64_t wbase = t0 + (int64_t)warp * 32 * RX_IPT;
+#pragma unroll
+        for (int q = 0; q < RX_IPT; ++q) {
+            const int64_t idx = wbase + q * 32 + lane;
+            if (idx < R) {
+                r[q] = in[idx];
+                dg[q] = (uint32_t)(((r[q].key & KEY_MASK) >> shift) & 0xFFull);
+            } else {
+                r[q].key = 0; r[q].re = 0; r[q].im = 0;
+                dg[q] = 0x100u + lane;            // unique sentinel, never counted
+            }
+        }
+        // stable warp multisplit rank
+#pragma unroll
+        for (int q = 0; q < RX_IPT; ++q) {
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, dg[q]);
+            const unsigned below = peers & ((1u << lane) - 1u);
+            uint32_t base = 0;
+            if (dg[q] < 256u) base = s.whist[warp][dg[q]];
+            __syncwarp();
+            if (dg[q] < 256u && below == 0u) s.whist[warp][dg[q]] = base + (uint32_t)__popc(peers);
+            __syncwarp();
+            rk[q] = base + (uint32_t)__popc(below);
+        }
+        __syncthreads();
+
+        // per digit (thread tid = digit): warp offsets, tile count, tile-local start
+        uint32_t cnt = 0;
+        for (int w = 0; w < RX_WARPS; ++w) {
+            const uint32_t c = s.whist[w][tid];
+            s.whist[w][tid] = cnt;
+            cnt += c;
+        }
+        uint64_t *my = lookback + (size_t)tile * 256 + tid;
+        if (tile == 0) lb_store(my, lb_pack(epoch, LB_INC, cnt));
+        else lb_store(my, lb_pack(epoch, LB_AGG, cnt));
+        {
+            uint32_t x = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+                if (lane >= off) x += y;
+            }
+            if (lane == 31) s.scan_tmp[warp] = x;
+            __syncthreads();
+            uint32_t pre = 0;
+            for (int w = 0; w < warp; ++w) pre += s.scan_tmp[w];
+            s.dstart[tid] = pre + x - cnt;
+        }
+        // decoupled look-back for this digit
+        uint64_t excl = 0;
+        for (int64_t jt = tile - 1; jt >= 0; --jt) {
+            const uint64_t w = lb_wait(lookback + (size_t)jt * 256 + tid, epoch, &st->status);
+            excl += (uint32_t)w;
+            if (((w >> 32) & 3ull) != LB_AGG) break;       // inclusive (or timed out)
+        }
+        if (tile > 0) lb_store(my, lb_pack(epoch, LB_INC, (uint32_t)(excl + cnt)));
+        s.gbase[tid] = (int64_t)s.bucket[tid] + (int64_t)excl - (int64_t)s.dstart[tid];
+        __syncthreads();
+
+        // stage in digit order
+#pragma unroll
+        for (int q = 0; q < RX_IPT; ++q) {
+            if (dg[q] < 256u) {
+                const uint32_t pos = s.dstart[dg[q]] + s.whist[warp][dg[q]] + rk[q];
+                s.stage[pos] = r[q];
+            }
+        }
+        __syncthreads();
+        int64_t nvalid = R - t0;
+        if (nvalid > RX_TILE) nvalid = RX_TILE;
+        for (int q = tid; q < nvalid; q += RX_TPB) {
+            const Rec v = s.stage[q];
+            const uint32_t d = (uint32_t)(((v.key & KEY_MASK) >> shift) & 0xFFull);
+            out[s.gbase[d] + q] = v;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace ddq

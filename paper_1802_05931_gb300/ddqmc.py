@@ -1,0 +1,286 @@
+"""Python binding of libddqmc.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls (see
+include/ddqmc.h); every step of the DDQMC path runs in the library's CUDA
+kernels.  The binding raises if the library has not been built: there is no
+CPU fallback.  ``Run`` is a small convenience wrapper over the same calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libddqmc.so")
+
+MAX_SITES = 31
+MAX_BONDS = 64
+
+ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CAPACITY", -4: "OVERFLOW", -5: "TIMEOUT",
+          -6: "CUDA", -7: "UNSUPPORTED"}
+
+
+class DDQMCError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (what, ERRORS.get(code, "?"), code))
+
+
+class ddqmc_lattice(C.Structure):
+    _fields_ = [("Lx", C.c_int32), ("Ly", C.c_int32), ("periodic", C.c_int32)]
+
+
+class ddqmc_guide(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("p", C.c_double), ("site_ratio", C.POINTER(C.c_double))]
+
+
+class ddqmc_options(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("damping", C.c_double), ("shift0", C.c_double),
+                ("n0", C.c_int64), ("control", C.c_int32), ("t_eq", C.c_int64),
+                ("capacity_entries", C.c_int64), ("capacity_spawns", C.c_int64),
+                ("cuda_stream", C.c_void_p)]
+
+
+class ddqmc_estimates(C.Structure):
+    _fields_ = [("t", C.c_int64), ("shift", C.c_double), ("variable", C.c_int32),
+                ("t_var", C.c_int64), ("t_eq", C.c_int64), ("n_samples", C.c_int64),
+                ("walkers", C.c_int64), ("entries", C.c_int64), ("nw", C.c_int64),
+                ("trace_re", C.c_int64), ("trace_im", C.c_int64),
+                ("nsites", C.c_int32), ("nbonds", C.c_int32), ("walker_steps", C.c_double),
+                ("mz", C.c_double), ("mz_err", C.c_double),
+                ("xx", C.c_double), ("xx_err", C.c_double), ("yy", C.c_double), ("yy_err", C.c_double),
+                ("zz", C.c_double), ("zz_err", C.c_double),
+                ("sz", C.c_double * MAX_SITES), ("sz_err", C.c_double * MAX_SITES),
+                ("bond_xx", C.c_double * MAX_BONDS), ("bond_yy", C.c_double * MAX_BONDS),
+                ("bond_zz", C.c_double * MAX_BONDS)]
+
+
+class ddqmc_state(C.Structure):
+    _fields_ = [("t", C.c_int64), ("shift", C.c_double), ("variable", C.c_int32),
+                ("q_prev", C.c_int64), ("t_var", C.c_int64), ("t_eq", C.c_int64),
+                ("entries", C.c_int64), ("status", C.c_int32)]
+
+
+EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_async", "ddqmc_sync",
+           "ddqmc_estimators", "ddqmc_raw_estimators", "ddqmc_blocking_moments",
+           "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_get_state", "ddqmc_get_counts",
+           "ddqmc_destroy", "ddqmc_strerror"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libddqmc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libddqmc.so is not built (run __graft_entry__.build()); "
+                           "the DDQMC path has no CPU fallback")
+    lib = C.CDLL(path)
+    P = C.POINTER
+    i32, i64, u64, dbl, vp = C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_void_p
+    lib.ddqmc_default_options.argtypes = [P(ddqmc_options)]
+    lib.ddqmc_create.argtypes = [P(ddqmc_lattice), dbl, dbl, dbl, dbl, dbl, i64, i32, P(ddqmc_guide),
+                                 P(ddqmc_options), P(vp)]
+    lib.ddqmc_step.argtypes = [vp, i64]
+    lib.ddqmc_step_async.argtypes = [vp, i64]
+    lib.ddqmc_sync.argtypes = [vp]
+    lib.ddqmc_estimators.argtypes = [vp, P(ddqmc_estimates)]
+    lib.ddqmc_raw_estimators.argtypes = [vp, P(i64), i32, P(i32)]
+    lib.ddqmc_blocking_moments.argtypes = [vp, i32, i32, P(i64), P(i64), P(i64), P(i64)]
+    lib.ddqmc_export_walkers.argtypes = [vp, P(u64), P(u64), P(i32), P(i32), i64, P(i64)]
+    lib.ddqmc_import_walkers.argtypes = [vp, P(u64), P(u64), P(i32), P(i32), i64, i64, dbl, i32, i64,
+                                         i64, i64]
+    lib.ddqmc_get_state.argtypes = [vp, P(ddqmc_state)]
+    lib.ddqmc_get_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
+    lib.ddqmc_destroy.argtypes = [vp]
+    lib.ddqmc_destroy.restype = None
+    lib.ddqmc_strerror.argtypes = [C.c_int]
+    lib.ddqmc_strerror.restype = C.c_char_p
+    for n in EXPORTS:
+        if n not in ("ddqmc_destroy", "ddqmc_strerror"):
+            getattr(lib, n).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise DDQMCError(rc, what)
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+# --- thin wrappers with the C names -------------------------------------------------------
+def ddqmc_default_options():
+    o = ddqmc_options()
+    _check(load().ddqmc_default_options(C.byref(o)), "ddqmc_default_options")
+    return o
+
+
+def ddqmc_create(lattice, Jx, Jy, Jz, gamma, dt, target_walkers, initiator_threshold, guide=None,
+                 options=None):
+    lib = load()
+    h = C.c_void_p()
+    rc = lib.ddqmc_create(C.byref(lattice), Jx, Jy, Jz, gamma, dt, int(target_walkers),
+                          int(initiator_threshold), C.byref(guide) if guide is not None else None,
+                          C.byref(options) if options is not None else None, C.byref(h))
+    _check(rc, "ddqmc_create")
+    return h
+
+
+def ddqmc_step(run, nsteps):
+    return load().ddqmc_step(run, int(nsteps))
+
+
+def ddqmc_step_async(run, nsteps):
+    return load().ddqmc_step_async(run, int(nsteps))
+
+
+def ddqmc_sync(run):
+    return load().ddqmc_sync(run)
+
+
+def ddqmc_estimators(run):
+    e = ddqmc_estimates()
+    rc = load().ddqmc_estimators(run, C.byref(e))
+    return rc, e
+
+
+def ddqmc_raw_estimators(run, cap=512):
+    out = np.zeros(cap, dtype=np.int64)
+    n = C.c_int32()
+    _check(load().ddqmc_raw_estimators(run, _p(out, C.c_int64), cap, C.byref(n)), "ddqmc_raw_estimators")
+    return out[: n.value]
+
+
+def ddqmc_blocking_moments(run, k, levels=32):
+    n = np.zeros(levels, dtype=np.int64)
+    sx = np.zeros(levels, dtype=np.int64)
+    sxx = np.zeros(2 * levels, dtype=np.int64)
+    sxy = np.zeros(2 * levels, dtype=np.int64)
+    _check(load().ddqmc_blocking_moments(run, int(k), levels, _p(n, C.c_int64), _p(sx, C.c_int64),
+                                         _p(sxx, C.c_int64), _p(sxy, C.c_int64)), "ddqmc_blocking_moments")
+
+    def i128(a, l):
+        return (int(a[2 * l + 1]) << 64) + (int(a[2 * l]) & ((1 << 64) - 1))
+    return [dict(n=int(n[l]), sx=int(sx[l]), sxx=i128(sxx, l), sxy=i128(sxy, l)) for l in range(levels)]
+
+
+def ddqmc_export_walkers(run):
+    lib = load()
+    n = C.c_int64()
+    _check(lib.ddqmc_export_walkers(run, None, None, None, None, 0, C.byref(n)), "ddqmc_export_walkers")
+    m = n.value
+    ket = np.zeros(max(m, 1), dtype=np.uint64)
+    bra = np.zeros(max(m, 1), dtype=np.uint64)
+    re = np.zeros(max(m, 1), dtype=np.int32)
+    im = np.zeros(max(m, 1), dtype=np.int32)
+    _check(lib.ddqmc_export_walkers(run, _p(ket, C.c_uint64), _p(bra, C.c_uint64), _p(re, C.c_int32),
+                                    _p(im, C.c_int32), m, C.byref(n)), "ddqmc_export_walkers")
+    return ket[:m], bra[:m], re[:m], im[:m]
+
+
+def ddqmc_import_walkers(run, ket, bra, re, im, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-1):
+    ket = np.ascontiguousarray(ket, dtype=np.uint64)
+    bra = np.ascontiguousarray(bra, dtype=np.uint64)
+    re = np.ascontiguousarray(re, dtype=np.int32)
+    im = np.ascontiguousarray(im, dtype=np.int32)
+    rc = load().ddqmc_import_walkers(run, _p(ket, C.c_uint64), _p(bra, C.c_uint64), _p(re, C.c_int32),
+                                     _p(im, C.c_int32), len(ket), int(t), float(S), int(variable),
+                                     int(q_prev), int(t_var), int(t_eq))
+    _check(rc, "ddqmc_import_walkers")
+
+
+def ddqmc_get_state(run):
+    s = ddqmc_state()
+    _check(load().ddqmc_get_state(run, C.byref(s)), "ddqmc_get_state")
+    return s
+
+
+def ddqmc_get_counts(run):
+    r, mc, rc_ = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().ddqmc_get_counts(run, C.byref(r), C.byref(mc), C.byref(rc_)), "ddqmc_get_counts")
+    return r.value, mc.value, rc_.value
+
+
+def ddqmc_destroy(run):
+    load().ddqmc_destroy(run)
+
+
+def ddqmc_strerror(code):
+    return load().ddqmc_strerror(int(code)).decode()
+
+
+class Run:
+    """One DDQMC run on the GPU (all device memory owned by the library)."""
+
+    def __init__(self, Lx, Ly, periodic, Jx, Jy, Jz, gamma, dt, target, n_a=0, guide_kind=0,
+                 guide_p=0.0, site_ratio=None, seed=1, damping=0.05, shift0=-1.0, n0=1000, control=0,
+                 t_eq=-1, capacity_entries=0, capacity_spawns=0, stream=None):
+        o = ddqmc_default_options()
+        o.seed = int(seed) & ((1 << 64) - 1)
+        o.damping = damping
+        o.shift0 = shift0
+        o.n0 = int(n0)
+        o.control = int(control)
+        o.t_eq = int(t_eq)
+        o.capacity_entries = int(capacity_entries)
+        o.capacity_spawns = int(capacity_spawns)
+        o.cuda_stream = stream
+        g = ddqmc_guide()
+        g.kind = int(guide_kind)
+        g.p = float(guide_p)
+        self._site_r = None
+        if site_ratio is not None:
+            self._site_r = np.ascontiguousarray(site_ratio, dtype=np.float64)
+            g.site_ratio = _p(self._site_r, C.c_double)
+        lat = ddqmc_lattice(int(Lx), int(Ly), int(periodic))
+        self.h = ddqmc_create(lat, float(Jx), float(Jy), float(Jz), float(gamma), float(dt), int(target),
+                              int(n_a), g, o)
+        self.N = Lx * Ly
+
+    def close(self):
+        if getattr(self, "h", None):
+            ddqmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        _check(ddqmc_step(self.h, n), "ddqmc_step")
+
+    def step_async(self, n=1):
+        _check(ddqmc_step_async(self.h, n), "ddqmc_step_async")
+
+    def sync(self):
+        _check(ddqmc_sync(self.h), "ddqmc_sync")
+
+    def estimates(self):
+        rc, e = ddqmc_estimators(self.h)
+        _check(rc, "ddqmc_estimators")
+        return e
+
+    def raw_estimates(self):
+        return ddqmc_raw_estimators(self.h)
+
+    def export(self):
+        return ddqmc_export_walkers(self.h)
+
+    def import_(self, ket, bra, re, im, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-1):
+        ddqmc_import_walkers(self.h, ket, bra, re, im, t, S, variable, q_prev, t_var, t_eq)
+
+    def state(self):
+        return ddqmc_get_state(self.h)
+
+    def counts(self):
+        return ddqmc_get_counts(self.h)

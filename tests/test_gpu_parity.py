@@ -1,0 +1,169 @@
+"""GPU path (through the C-ABI) against the CPU oracle, element by element.
+
+Walker lists (keys and int32 populations) and the integer estimator
+numerators must be bit-identical after every step; the blocking moments are
+exact integers and must be identical too."""
+import numpy as np
+import pytest
+
+from oracle import blocking as Bk
+from oracle import oracle as O
+from tests import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ddqmc():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1802_05931_gb300 import ddqmc as d
+    return d
+
+
+def _pair(ddqmc, cfg, **over):
+    args, kw = W.run_kwargs(cfg, **over)
+    return ddqmc.Run(*args, **kw), O.OracleRun(*args, **kw)
+
+
+def _same(gpu, cpu, where):
+    g = gpu.export()
+    c = cpu.export()
+    assert len(g[0]) == len(c[0]), (where, len(g[0]), len(c[0]))
+    for name, a, b in zip(("ket", "bra", "re", "im"), g, c):
+        assert np.array_equal(a, b), (where, name)
+    assert np.array_equal(gpu.raw_estimates(), cpu.estimates_now()), where
+
+
+def test_first_steps_2x2(ddqmc):
+    gpu, cpu = _pair(ddqmc, W.C1)
+    for t in range(300):
+        gpu.step(1)
+        cpu.step(1)
+        _same(gpu, cpu, t)
+        s, o = gpu.state(), cpu.state()
+        assert s.t == o["t"] and s.shift == o["S"] and s.variable == o["variable"]
+
+
+def test_c1_all_steps_bitexact(ddqmc):
+    """2x2 open, seed 1: every one of the 2 x 10^4 steps."""
+    gpu, cpu = _pair(ddqmc, W.C1)
+    for t in range(W.C1["steps"]):
+        gpu.step(1)
+        cpu.step(1)
+        if t % 10 == 0 or t > W.C1["steps"] - 5:
+            _same(gpu, cpu, t)
+    st, o = gpu.state(), cpu.state()
+    assert (st.t, st.shift, st.variable, st.t_var, st.t_eq) == (o["t"], o["S"], o["variable"], o["t_var"], o["t_eq"])
+
+
+def test_c2_first_200_steps_bitexact(ddqmc):
+    """3x3 periodic, n_a = 3, seed 2: the first 200 steps."""
+    gpu, cpu = _pair(ddqmc, W.C2)
+    for t in range(200):
+        gpu.step(1)
+        cpu.step(1)
+        _same(gpu, cpu, t)
+
+
+@pytest.mark.parametrize("over", [
+    dict(guide_kind=1, guide_p=1.5, dt=0.05),                        # uniform guide, n_att > 1
+    dict(guide_kind=2, guide_p=0.7, n_a=2, dt=0.02),                 # site-product guide
+    dict(dt=0.2, shift0=-6.0, n0=300),                               # |p_death| > 1, several attempts
+    dict(Jx=0.3, Jy=-1.2, Jz=-0.7, gamma=0.6, n_a=1, seed=99),       # signs of every element flipped
+])
+def test_variants_bitexact(ddqmc, over):
+    cfg = dict(W.C2)
+    cfg.update(target=20000)
+    gpu, cpu = _pair(ddqmc, cfg, **over)
+    for t in range(120):
+        gpu.step(1)
+        cpu.step(1)
+        _same(gpu, cpu, t)
+
+
+def test_heavy_and_light_entries_4x4(ddqmc):
+    """4x4 periodic with many walkers per diagonal entry (warp-cooperative path)
+    and single walkers off the diagonal (lane-per-entry path)."""
+    cfg = dict(W.C3)
+    cfg.update(target=3 * 10 ** 5, n0=20000)
+    gpu, cpu = _pair(ddqmc, cfg)
+    for t in range(60):
+        gpu.step(1)
+        cpu.step(1)
+        _same(gpu, cpu, t)
+
+
+def test_single_step_from_imported_state(ddqmc):
+    """Grow a 4x4 population on the GPU, then step the exported state once on
+    both sides (the oracle imports the GPU's list and scalar state)."""
+    args, kw = W.run_kwargs(W.C3, target=2 * 10 ** 6)
+    gpu = ddqmc.Run(*args, **kw)
+    gpu.step(1400)
+    ket, bra, re, im = gpu.export()
+    s = gpu.state()
+    assert len(ket) > 10 ** 5
+    cpu = O.OracleRun(*args, **kw)
+    cpu.import_(ket, bra, re, im)
+    cpu.set_state(s.t, s.shift, s.variable, s.q_prev, s.t_var, s.t_eq)
+    for _ in range(2):
+        gpu.step(1)
+        cpu.step(1)
+        _same(gpu, cpu, "imported")
+
+
+def test_blocking_moments_are_exact(ddqmc):
+    """The device-resident blocking cells equal the exact block sums of the
+    oracle's per-step series (same samples, integer arithmetic)."""
+    gpu, cpu = _pair(ddqmc, W.C1, target=3000, t_eq=50)
+    gpu.step(3000)
+    cpu.step(3000)
+    ser = cpu.series()
+    assert len(ser) > 2000
+    est = gpu.estimates()
+    assert est.n_samples == len(ser)
+    for k in (0, 2, 5, cpu.nobs - 4, cpu.nobs - 1):
+        ref = Bk.level_moments(ser[:, k], ser[:, 0])
+        got = ddqmc.ddqmc_blocking_moments(gpu.h, k)
+        for l, lv in enumerate(ref):
+            if lv["n"] < 1:
+                break
+            g = got[l]
+            assert (g["n"], g["sx"], g["sxx"], g["sxy"]) == (lv["n"], lv["sx"], lv["sxx"], lv["sxy"]), (k, l)
+    lay = O.observable_layout(4, 4)
+    R, err, _ = Bk.blocked_ratio(ser[:, lay["sum_z"]], ser[:, 0])
+    assert abs(est.mz - R / 4) < 1e-12 and abs(est.mz_err - err / 4) < 1e-9 * err
+
+
+def test_empty_and_dark_states(ddqmc):
+    run = ddqmc.Run(2, 2, 0, 0.9, 1.0, 1.0, 1.0, 0.01, 1000, n0=0)
+    run.step(5)
+    assert len(run.export()[0]) == 0
+    run = ddqmc.Run(2, 2, 0, 1.0, 1.0, 0.7, 1.0, 0.01, 5000, seed=4)
+    cpu = O.OracleRun(2, 2, 0, 1.0, 1.0, 0.7, 1.0, 0.01, 5000, seed=4)
+    run.step(500)
+    cpu.step(500)
+    _same(run, cpu, "dark")
+    k, b, r, i = run.export()
+    assert list(k) == [0] and list(b) == [0]
+
+
+def test_capacity_error_is_reported_and_sticky(ddqmc):
+    run = ddqmc.Run(3, 3, 1, 0.9, 1.0, 1.0, 1.0, 0.005, 10 ** 6, capacity_entries=4096, capacity_spawns=4096)
+    with pytest.raises(ddqmc.DDQMCError) as e:
+        run.step(2000)
+    assert e.value.code == -3
+    with pytest.raises(ddqmc.DDQMCError):
+        run.step(1)
+
+
+def test_invalid_arguments_rejected(ddqmc):
+    with pytest.raises(ddqmc.DDQMCError) as e:
+        ddqmc.Run(2, 2, 1, 0.9, 1.0, 1.0, 1.0, 0.01, 100)       # L = 2 periodic
+    assert e.value.code == -1
+    with pytest.raises(ddqmc.DDQMCError) as e:
+        ddqmc.Run(8, 4, 0, 0.9, 1.0, 1.0, 1.0, 0.01, 100)       # 32 sites
+    assert e.value.code == -7
+    run = ddqmc.Run(2, 2, 0, 0.9, 1.0, 1.0, 1.0, 0.01, 100)
+    with pytest.raises(ddqmc.DDQMCError):
+        run.import_([1, 0], [0, 0], [1, 1], [0, 0], 0, 0.0)      # not in canonical order
