@@ -70,8 +70,10 @@ typedef struct {
     int32_t control;           /* 0: N_w = sum |Re rho_ii| (the paper's rule); 1: total sum |re|+|im| */
     int64_t t_eq;              /* steps after the shift switches on before estimates
                                   accumulate; < 0: ceil(10 / (gamma dt)) */
-    int64_t capacity_entries;  /* walker-list capacity (entries); <= 0: derived from the target */
-    int64_t capacity_spawns;   /* spawn-record capacity per step; <= 0: derived from the target */
+    int64_t capacity_entries;  /* walker-list capacity (entries); <= 0: 2*target (control 1)
+                                  or 64*target (control 0), plus 65536 */
+    int64_t capacity_spawns;   /* spawn-record capacity per step; <= 0: 4*target (control 1)
+                                  or 64*target (control 0), plus 65536 */
     void *cuda_stream;         /* cudaStream_t to issue work on; NULL: the run creates its own */
 } ddqmc_options;
 
@@ -108,6 +110,8 @@ typedef struct {
     int64_t t_var, t_eq;
     int64_t entries;
     int32_t status;            /* sticky device status (0 or a DDQMC_ERR_* code) */
+    int32_t status_bits;       /* device status bits: 1 capacity, 2 int32 overflow, 4 timeout,
+                                  8 walker-list capacity, 16 spawn-buffer capacity */
 } ddqmc_state;
 
 /* Defaults for every option field.  Returns DDQMC_OK, or INVALID_ARG for NULL. */

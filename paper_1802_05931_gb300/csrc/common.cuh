@@ -16,6 +16,7 @@ constexpr int LEVELS = 32;                    // blocking levels (block length 2
 constexpr int MAXPASS = 8;                    // radix passes of 8 bits over 2N <= 62 key bits
 
 constexpr uint32_t ST_CAPACITY = 1u, ST_OVERFLOW = 2u, ST_TIMEOUT = 4u;
+constexpr uint32_t ST_CAP_LIST = 8u, ST_CAP_SPAWN = 16u;   // which capacity ran out (with ST_CAPACITY)
 
 // Spawn records carry the parent's initiator flag in bit 63; list keys never do.
 constexpr uint64_t FLAG_BIT = 1ull << 63;
@@ -54,6 +55,15 @@ struct RunParams {
     uint32_t cross_int[2 * MAXB + 1];
     uint64_t cross_frac[2 * MAXB + 1];
     int8_t pair_bond[MAXN * MAXN];    // bond index of an (a, b) site pair, -1 if none
+    // square-lattice geometry for the mask formulation of the rates
+    int32_t Lx, shD;                  // row length; Lx * (Ly - 1)
+    uint32_t ER, ED;                  // sites owning a bond to the right / below
+    uint32_t LC, LR;                  // last column / last row
+    int8_t rn[MAXN], dn[MAXN];        // right / lower neighbour of each site
+    int32_t uniform;                  // 1 if every bond has the same rate table
+    int32_t pad1;
+    uint64_t Emorton;                 // bond-existence mask, bit 2k = right bond of k, 2k+1 = lower
+    uint64_t urate[2][3];             // [anti-aligned][class] rates when uniform
 };
 
 // Device-resident state of a run, updated by the kernels of each step.

@@ -156,6 +156,34 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
         }
     }
     P.jump_q = fixed_rate(gamma * dt);
+    // geometry masks and the bond-uniform rate table of the popcount formulation
+    P.Lx = Lx;
+    P.shD = Lx * (Ly - 1);
+    for (int k = 0; k < N; ++k) {
+        const int x = k % Lx, y = k / Lx;
+        P.rn[k] = (int8_t)((x + 1) % Lx + Lx * y);
+        P.dn[k] = (int8_t)(x + Lx * ((y + 1) % Ly));
+        if (Lx > 1 && (x + 1 < Lx || per)) P.ER |= 1u << k;
+        if (Ly > 1 && (y + 1 < Ly || per)) P.ED |= 1u << k;
+        if (x == Lx - 1) P.LC |= 1u << k;
+        if (y == Ly - 1) P.LR |= 1u << k;
+    }
+    for (int k = 0; k < N; ++k) {
+        if (P.ER >> k & 1u) P.Emorton |= 1ull << (2 * k);
+        if (P.ED >> k & 1u) P.Emorton |= 1ull << (2 * k + 1);
+    }
+    bool uni = true;
+    for (int b = 1; b < B; ++b)
+        for (int h = 0; h < 2; ++h)
+            for (int c = 0; c < 4; ++c) uni = uni && P.rate_q[b][h][c] == P.rate_q[0][h][c];
+    if (gk == 2)
+        for (int h = 0; h < 2; ++h) uni = uni && P.rate_q[0][h][1] == P.rate_q[0][h][2];
+    P.uniform = uni ? 1 : 0;
+    for (int h = 0; h < 2; ++h) {
+        P.urate[h][0] = P.rate_q[0][h][0];
+        P.urate[h][1] = P.rate_q[0][h][1];
+        P.urate[h][2] = gk == 2 ? P.rate_q[0][h][3] : P.rate_q[0][h][2];
+    }
     const double cbase = dt * std::fabs(Jz);
     for (int c = 0; c <= 2 * B; ++c) {
         const double x = cbase * (double)c;
@@ -326,9 +354,12 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     if (cudaGetDevice(&r->device) != cudaSuccess) { cudaGetLastError(); delete r; return DDQMC_ERR_CUDA; }
     // capacities
     int64_t mcap = o.capacity_entries, rcap = o.capacity_spawns;
-    const int64_t scale = o.control == 1 ? 2 : 64;
-    if (mcap <= 0) mcap = target_walkers * scale + 1024;
-    if (rcap <= 0) rcap = target_walkers * scale + 1024;
+    // defaults: with total-population control the list holds at most ~target
+    // entries and a step makes up to a few records per walker (P_tot > 1 under
+    // importance sampling); with diagonal control the off-diagonal population
+    // is not held, so leave a wide margin
+    if (mcap <= 0) mcap = (o.control == 1 ? 2 * target_walkers : 64 * target_walkers) + 65536;
+    if (rcap <= 0) rcap = (o.control == 1 ? 4 * target_walkers : 64 * target_walkers) + 65536;
     if (mcap < 4096) mcap = 4096;
     if (rcap < 4096) rcap = 4096;
     const int64_t lim = (1ll << 31) - 1;
@@ -435,6 +466,7 @@ int ddqmc_get_state(ddqmc_run *r, ddqmc_state *out) {
     out->t_eq = hs.t_eq;
     out->entries = hs.M;
     out->status = r->host_status ? r->host_status : status_code(hs.status);
+    out->status_bits = (int32_t)hs.status;
     return DDQMC_OK;
 }
 

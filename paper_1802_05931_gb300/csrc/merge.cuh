@@ -259,7 +259,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const Rec *
         __syncthreads();
         const int64_t ob = s.out_base;
         if (ob + (int64_t)total > mcap) {
-            if (tid == 0) local_status |= ST_CAPACITY;
+            if (tid == 0) local_status |= ST_CAPACITY | ST_CAP_LIST;
         } else {
             for (uint32_t q = tid; q < total; q += MG_TPB) {
                 const Rec v = s.buf[q];

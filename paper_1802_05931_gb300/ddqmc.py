@@ -60,7 +60,7 @@ class ddqmc_estimates(C.Structure):
 class ddqmc_state(C.Structure):
     _fields_ = [("t", C.c_int64), ("shift", C.c_double), ("variable", C.c_int32),
                 ("q_prev", C.c_int64), ("t_var", C.c_int64), ("t_eq", C.c_int64),
-                ("entries", C.c_int64), ("status", C.c_int32)]
+                ("entries", C.c_int64), ("status", C.c_int32), ("status_bits", C.c_int32)]
 
 
 EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_async", "ddqmc_sync",

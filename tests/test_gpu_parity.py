@@ -66,16 +66,21 @@ def test_c2_first_200_steps_bitexact(ddqmc):
         _same(gpu, cpu, t)
 
 
-@pytest.mark.parametrize("over", [
-    dict(guide_kind=1, guide_p=1.5, dt=0.05),                        # uniform guide, n_att > 1
-    dict(guide_kind=2, guide_p=0.7, n_a=2, dt=0.02),                 # site-product guide
-    dict(dt=0.2, shift0=-6.0, n0=300),                               # |p_death| > 1, several attempts
-    dict(Jx=0.3, Jy=-1.2, Jz=-0.7, gamma=0.6, n_a=1, seed=99),       # signs of every element flipped
-])
-def test_variants_bitexact(ddqmc, over):
-    cfg = dict(W.C2)
-    cfg.update(target=20000)
-    gpu, cpu = _pair(ddqmc, cfg, **over)
+VARIANTS = [
+    # (base config, overrides): every one keeps its population bounded
+    ("C1", dict(guide_kind=1, guide_p=3.0, dt=0.05, control=1, target=5000)),    # n_att up to 5
+    ("C2", dict(guide_kind=1, guide_p=1.5, dt=0.01, control=1, target=20000)),   # uniform guide
+    ("C2", dict(guide_kind=2, guide_p=0.7, n_a=2, dt=0.01, control=1, target=20000)),  # site product
+    ("C1", dict(dt=0.05, shift0=25.0, n0=20000, target=10 ** 12)),               # |p_death| > 1
+    ("C2", dict(Jx=0.3, Jy=-1.2, Jz=-0.7, gamma=0.6, n_a=1, seed=99, control=1, target=20000)),
+]
+
+
+@pytest.mark.parametrize("base,over", VARIANTS)
+def test_variants_bitexact(ddqmc, base, over):
+    args, kw = W.run_kwargs(getattr(W, base), **over)
+    gpu = ddqmc.Run(*args, capacity_entries=1 << 22, capacity_spawns=1 << 23, **kw)
+    cpu = O.OracleRun(*args, **kw)
     for t in range(120):
         gpu.step(1)
         cpu.step(1)
@@ -98,7 +103,7 @@ def test_single_step_from_imported_state(ddqmc):
     """Grow a 4x4 population on the GPU, then step the exported state once on
     both sides (the oracle imports the GPU's list and scalar state)."""
     args, kw = W.run_kwargs(W.C3, target=2 * 10 ** 6)
-    gpu = ddqmc.Run(*args, **kw)
+    gpu = ddqmc.Run(*args, capacity_entries=1 << 25, capacity_spawns=1 << 26, **kw)
     gpu.step(1400)
     ket, bra, re, im = gpu.export()
     s = gpu.state()
