@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""DDQMC throughput benchmark: walker-steps per second of one DDQMC step
+(spawn + death/clone, onesweep radix sort, merge-path annihilation with the
+initiator rule, estimators, shift update) on the 4x4 periodic XYZ lattice.
+
+Workload: 4x4 periodic XYZ lattice (N = 16, 32 bonds), Jx = 0.9, Jy = Jz = 1,
+gamma = 1, dt = 0.005, initiator threshold n_a = 3, site-product importance
+guide with uniform site ratio exp(-1.5), the shift switched on when the total
+population sum |re|+|im| first reaches 10^8, seed 3.  The run is grown from
+1000 walkers on |down..down><down..down| (untimed), settles, then W warm-up
+steps and K timed steps follow.  Every input is synthetic: the dynamics
+generate the walker lists.
+
+One JSON line on stdout (rank 0).  ``--impl reference`` times the CPU oracle
+(single-threaded C) on a bounded sample of the same workload instead.
+Under torchrun each rank runs an independent replica (seed + rank); the
+value is the walker-steps of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "walker-steps/s"
+UNIT = "walker-steps/s"
+WORKLOAD = dict(Lx=4, Ly=4, periodic=1, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, n_a=3,
+                guide_kind=2, guide_p=1.5, control=1, seed=3)
+WORKLOAD_NAME = "4x4 periodic XYZ, Jx=0.9 Jy=Jz=1 gamma=1, dt=0.005, n_a=3, site-product guide exp(-1.5), " \
+                "total-walker shift target 1e8, seed 3"
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--target", type=float, default=1e8, help="total walkers at which the shift switches on")
+    ap.add_argument("--settle", type=int, default=150, help="untimed steps after the shift switches on")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-target", type=float, default=2e4, help="shift target of the oracle sample")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_setup(n):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def reduce_max(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) < 9:
+                        continue
+                    try:
+                        sm.append(float(p[1]))
+                        mx.append(float(p[2]))
+                    except ValueError:
+                        continue
+                    for nm, v in zip(names, p[5:9]):
+                        if v.lower().startswith("active"):
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic():
+    """DRAM bytes per unit of work of each kernel from the committed ncu summary
+    (profiles/traffic_per_unit.txt: '<kernel> <bytes per unit> <unit>'), if present."""
+    out = {}
+    path = os.path.join(ROOT, "profiles", "traffic_per_unit.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.strip() and not line.startswith("#"):
+                    k, v, u = line.split()[:3]
+                    out[k] = (float(v), u)
+    except Exception:
+        pass
+    return out
+
+
+# ----------------------------------------------------------------------------- oracle sample
+def oracle_sample(target, seconds, warmup, steps=None):
+    """Time the CPU oracle (single-threaded) on the same workload at a smaller
+    shift target: grow and settle untimed, then time steps."""
+    from oracle import oracle as O
+    w = WORKLOAD
+    site_r = [math.exp(-w["guide_p"])] * (w["Lx"] * w["Ly"])
+    run = O.OracleRun(w["Lx"], w["Ly"], w["periodic"], w["Jx"], w["Jy"], w["Jz"], w["gamma"], w["dt"],
+                      int(target), n_a=w["n_a"], guide_kind=w["guide_kind"], guide_p=w["guide_p"],
+                      site_ratio=site_r, seed=w["seed"], control=w["control"])
+    while True:
+        run.step(25)
+        st = run.state()
+        if st["variable"] and st["t"] >= st["t_var"] + 100:
+            break
+    run.step(max(warmup, 1))
+    ws, n, t0 = 0, 0, time.perf_counter()
+    while True:
+        ws += int(run.estimates_now()[3])
+        run.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (steps is None and el >= seconds):
+            break
+    W = int(run.estimates_now()[3])
+    return ws / el, dict(steps=n, seconds=el, walkers=W, target=int(target))
+
+
+def cpu_cores_desc():
+    try:
+        import platform
+        return "%s, %d host cores" % (platform.processor() or platform.machine(), os.cpu_count() or 0)
+    except Exception:
+        return "%d host cores" % (os.cpu_count() or 0)
+
+
+def reference_arm(args, world, rank, pg):
+    if rank != 0:
+        return 0
+    rate, info = oracle_sample(args.cpu_target, args.cpu_seconds, args.warmup, steps=args.steps)
+    sample = ("oracle on the bench workload with shift target %d (about %d walkers): %d timed steps "
+              "after %d warm-up steps, %.1f s" % (info["target"], info["walkers"], info["steps"],
+                                                   args.warmup, info["seconds"]))
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": info["steps"], "warmup": args.warmup, "ms_per_step": 1e3 * info["seconds"] / info["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_target": info["target"]},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": cpu_cores_desc()},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def gpu_arm(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    barrier(pg)
+    from paper_1802_05931_gb300 import ddqmc
+    w = WORKLOAD
+    N = w["Lx"] * w["Ly"]
+    stream = torch.cuda.Stream()
+    target = int(args.target)
+    run = ddqmc.Run(w["Lx"], w["Ly"], w["periodic"], w["Jx"], w["Jy"], w["Jz"], w["gamma"], w["dt"], target,
+                    n_a=w["n_a"], guide_kind=w["guide_kind"], guide_p=w["guide_p"],
+                    site_ratio=[math.exp(-w["guide_p"])] * N, seed=w["seed"] + rank, control=w["control"],
+                    capacity_entries=int(3.2 * target) + (1 << 20), capacity_spawns=int(4.5 * target) + (1 << 20),
+                    stream=stream.cuda_stream)
+    # grow and settle (untimed)
+    while True:
+        run.step(25)
+        st = run.state()
+        if st.variable and st.t >= st.t_var + args.settle:
+            break
+    run.step(max(args.warmup, 3))
+    tot0 = ddqmc.ddqmc_get_totals(run.h)
+    ddqmc.ddqmc_set_timing(run.h, 1)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    tot1 = ddqmc.ddqmc_get_totals(run.h)
+    timing = ddqmc.ddqmc_get_timing(run.h)
+    ddqmc.ddqmc_set_timing(run.h, 0)
+    dws = tot1["walker_steps"] - tot0["walker_steps"]
+    dM = tot1["entry_steps"] - tot0["entry_steps"]
+    dR = tot1["spawn_records"] - tot0["spawn_records"]
+    dMn = tot1["merged_entries"] - tot0["merged_entries"]
+    K = args.steps
+    t_max = reduce_max(pg, ms)
+    ws_all = reduce_sum(pg, dws)
+    value = ws_all / (t_max / 1e3)
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / average launch time
+    alg = {"spawn_death": (24 * dM + 16 * dR) / K,
+           "radix_pass": 32 * dR / K,
+           "merge": 16 * (dM + dR + dMn) / K}
+    per_unit = {"spawn_death": (dM + dR) / K, "radix_pass": dR / K, "merge": (dM + dR) / K}
+    kern = {}
+    for k, (kms, n) in timing.items():
+        if n:
+            kern[k] = {"ms_per_launch": kms / n, "launches": n, "share": kms / max(sum(v[0] for v in timing.values()), 1e-30)}
+            if k in alg:
+                kern[k]["alg_bytes_per_launch"] = alg[k]
+                kern[k]["achieved_gbs"] = alg[k] / (kms / n / 1e3) / 1e9
+    dom = max((k for k in kern if k in alg), key=lambda k: timing[k][0])
+    peak, peak_src = peak_hbm()
+    achieved = kern[dom]["achieved_gbs"]
+    traffic = None
+    tr = profile_traffic().get(dom)
+    if tr is not None:
+        traffic = tr[0] * per_unit[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_src == "measured" else "fallback 6.8 TB/s"}
+    sortmerge_ms = sum(timing[k][0] for k in ("radix_pass", "merge_partition", "merge")) / K
+    sortmerge_bytes = alg["radix_pass"] * (timing["radix_pass"][1] / K) + alg["merge"]
+    # end to end through the C-ABI with host buffers: import, step, export, estimators
+    e2e = None
+    if args.e2e_steps > 0:
+        ket, bra, re, im = run.export()
+        st = run.state()
+        state = (st.t, st.shift, st.variable, st.q_prev, st.t_var, st.t_eq)
+        torch.cuda.synchronize()
+        barrier(pg)
+        t0 = time.perf_counter()
+        e_ws, h2d, d2h = 0, 0, 0
+        for _ in range(args.e2e_steps):
+            run.import_(ket, bra, re, im, *state)
+            h2d += 16 * len(ket)
+            e_ws += int(np.abs(re, dtype=np.int64).sum() + np.abs(im, dtype=np.int64).sum())
+            run.step(1)
+            ket, bra, re, im = run.export()
+            est = run.raw_estimates()
+            d2h += 16 * len(ket) + 8 * len(est)
+            st = run.state()
+            state = (st.t, st.shift, st.variable, st.q_prev, st.t_var, st.t_eq)
+        el = time.perf_counter() - t0
+        el = reduce_max(pg, el)
+        e_all = reduce_sum(pg, e_ws)
+        e2e = {"value": e_all / el, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
+               "d2h_bytes_per_step": d2h // args.e2e_steps, "steps": args.e2e_steps}
+    st = run.state()
+    est = run.raw_estimates()
+    run.close()
+    if rank != 0:
+        return 0
+    cpu = None
+    if args.cpu_seconds > 0:
+        rate, info = oracle_sample(args.cpu_target, args.cpu_seconds, 3)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "oracle on the bench workload with shift target %d (about %d walkers), %d steps in %.1f s"
+                         % (info["target"], info["walkers"], info["steps"], info["seconds"]),
+               "host": cpu_cores_desc()}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "walkers_per_step": dws / K, "entries_per_step": dM / K,
+                       "spawn_records_per_step": dR / K, "shift": st.shift, "t": st.t,
+                       "l2": "inputs larger than L2 (walker list and spawn buffer are GBs)",
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline,
+            "sort_merge": {"ms_per_step": sortmerge_ms, "alg_bytes_per_step": sortmerge_bytes,
+                           "achieved_gbs": sortmerge_bytes / (sortmerge_ms / 1e3) / 1e9,
+                           "frac": sortmerge_bytes / (sortmerge_ms / 1e3) / 1e9 / peak},
+            "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(sum(v[1] for v in timing.values())), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args.gpus)
+    try:
+        if args.impl == "reference":
+            return reference_arm(args, world, rank, pg)
+        return gpu_arm(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -183,6 +183,23 @@ int ddqmc_get_state(ddqmc_run *run, ddqmc_state *out);
 int ddqmc_get_counts(ddqmc_run *run, int64_t *spawn_records, int64_t *capacity_entries,
                      int64_t *capacity_spawns);
 
+/* Totals over all completed steps (device counters, exact): walkers stepped
+ * (sum over steps of sum |re|+|im| of the list being stepped), configurations
+ * stepped, spawn records written, and configurations of the merged lists.
+ * They give the algorithmic bytes of each kernel.  Any pointer may be NULL. */
+int ddqmc_get_totals(ddqmc_run *run, int64_t *walker_steps, int64_t *entry_steps,
+                     int64_t *spawn_records, int64_t *merged_entries);
+
+/* Per-kernel timing: with enable != 0 every later ddqmc_step brackets each
+ * kernel class with CUDA events on the run's stream (classes: 0 spawn+death,
+ * 1 radix passes, 2 merge partition, 3 merge+annihilation+estimators,
+ * 4 finalize) and accumulates the elapsed times; enabling or disabling resets
+ * the sums.  ddqmc_step_async does not record events. */
+int ddqmc_set_timing(ddqmc_run *run, int32_t enable);
+
+/* Accumulated milliseconds and launch counts per kernel class (cap >= 5). */
+int ddqmc_get_timing(ddqmc_run *run, double *ms, int64_t *launches, int32_t cap);
+
 /* Free every resource of the run (NULL is ignored). */
 void ddqmc_destroy(ddqmc_run *run);
 

@@ -82,6 +82,7 @@ struct DevState {
     int64_t walker_steps;      // sum over completed steps of the walkers stepped
     int64_t W_cur;             // sum |re| + |im| of the current list
     int64_t n_app;             // samples accumulated for blocking
+    int64_t sum_M, sum_R, sum_Mnext;   // totals over completed steps: entries stepped, spawn records, merged entries
     uint32_t d_int[2 * MAXN + 1];
     uint64_t d_frac[2 * MAXN + 1];
     int32_t d_sgn[2 * MAXN + 1];

@@ -40,6 +40,14 @@ struct ddqmc_run {
     int guide_kind = 0;
     double w_bond[MAXB];         // importance weight of a configuration differing on bond b only
     int host_status = 0;         // sticky host-visible status
+    // optional per-kernel timing (CUDA events on the run's stream)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;     // 2 * NKCLASS events per step
+    double kernel_ms[8] = {0};
+    int64_t kernel_launches[8] = {0};
+    // pinned host staging for import / export, kept between calls
+    Rec *hstage = nullptr;
+    int64_t hstage_cap = 0;
 };
 
 namespace {
@@ -216,6 +224,8 @@ int occupancy_grid(const void *fn, int tpb, size_t smem, int sms) {
 
 void free_run(ddqmc_run *r) {
     if (!r) return;
+    for (cudaEvent_t e : r->ev) cudaEventDestroy(e);
+    if (r->hstage) cudaFreeHost(r->hstage);
     cudaFree(r->dP);
     cudaFree(r->dS);
     cudaFree(r->dBlk);
@@ -243,23 +253,63 @@ int read_status(ddqmc_run *r) {
     return r->host_status;
 }
 
+// Pinned host staging of at least n records (grown on demand, never shrunk).
+Rec *host_stage(ddqmc_run *r, int64_t n) {
+    if (n <= r->hstage_cap) return r->hstage;
+    if (r->hstage) { cudaFreeHost(r->hstage); r->hstage = nullptr; r->hstage_cap = 0; }
+    const int64_t cap = n + n / 4 + 1024;
+    if (cudaMallocHost((void **)&r->hstage, sizeof(Rec) * (size_t)cap) != cudaSuccess) {
+        cudaGetLastError();
+        r->hstage = nullptr;
+        return nullptr;
+    }
+    r->hstage_cap = cap;
+    return r->hstage;
+}
+
 constexpr size_t SP_SMEM = sizeof(SpawnShared);
 constexpr size_t RX_SMEM = sizeof(RadixShared);
 constexpr size_t MG_SMEM = sizeof(MergeShared);
 
+// kernel classes of the per-kernel timing
+enum { KC_SPAWN = 0, KC_RADIX = 1, KC_PARTITION = 2, KC_MERGE = 3, KC_FINALIZE = 4, NKCLASS = 5 };
+
 int enqueue_steps(ddqmc_run *r, int64_t nsteps) {
     const RunParams &P = r->hp;
     for (int64_t s = 0; s < nsteps; ++s) {
+        cudaEvent_t *ev = nullptr;
+        if (r->timing) {
+            const size_t need = (size_t)(s + 1) * 2 * NKCLASS;
+            while (r->ev.size() < need) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+                r->ev.push_back(e);
+            }
+            ev = &r->ev[(size_t)s * 2 * NKCLASS];
+        }
+        auto mark = [&](int kc, int edge) {
+            if (ev) cudaEventRecord(ev[2 * kc + edge], r->stream);
+        };
         Rec *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
+        mark(KC_SPAWN, 0);
         k_spawn_death<<<r->g_spawn, SP_TPB, SP_SMEM, r->stream>>>(r->dP, r->dS, Lc, r->Sp[0], r->rcap);
+        mark(KC_SPAWN, 1);
+        mark(KC_RADIX, 0);
         for (int p = 0; p < P.npass; ++p)
             k_radix_pass<<<r->g_radix, RX_TPB, RX_SMEM, r->stream>>>(r->Sp[p & 1], r->Sp[(p + 1) & 1], r->dS,
                                                                      r->lb_radix, p, 8 * p, r->rcap);
+        mark(KC_RADIX, 1);
         const Rec *sorted = r->Sp[P.npass & 1];
+        mark(KC_PARTITION, 0);
         k_merge_partition<<<r->g_part, 256, 0, r->stream>>>(Lc, sorted, r->dS, r->splits, r->rcap);
+        mark(KC_PARTITION, 1);
+        mark(KC_MERGE, 0);
         k_merge<<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits, r->lb_merge,
                                                             r->rcap, r->mcap);
+        mark(KC_MERGE, 1);
+        mark(KC_FINALIZE, 0);
         k_finalize<<<1, FN_TPB, 0, r->stream>>>(r->dP, r->dS, r->dBlk);
+        mark(KC_FINALIZE, 1);
         r->cur ^= 1;
     }
     if (cudaGetLastError() != cudaSuccess) {
@@ -267,6 +317,23 @@ int enqueue_steps(ddqmc_run *r, int64_t nsteps) {
         return r->host_status;
     }
     return DDQMC_OK;
+}
+
+// Fold the recorded per-kernel times of the last nsteps steps into the totals
+// (the stream must have been synchronised).
+void collect_timing(ddqmc_run *r, int64_t nsteps) {
+    if (!r->timing) return;
+    for (int64_t s = 0; s < nsteps; ++s)
+        for (int kc = 0; kc < NKCLASS; ++kc) {
+            float ms = 0.f;
+            const size_t b = (size_t)s * 2 * NKCLASS + 2 * kc;
+            if (cudaEventElapsedTime(&ms, r->ev[b], r->ev[b + 1]) == cudaSuccess) {
+                r->kernel_ms[kc] += ms;
+                r->kernel_launches[kc] += (kc == KC_RADIX) ? r->hp.npass : 1;
+            } else {
+                cudaGetLastError();
+            }
+        }
 }
 
 struct LevelStat {
@@ -445,9 +512,49 @@ int ddqmc_sync(ddqmc_run *r) {
 }
 
 int ddqmc_step(ddqmc_run *r, int64_t nsteps) {
-    const int rc = ddqmc_step_async(r, nsteps);
-    if (rc != DDQMC_OK) return rc;
-    return read_status(r);
+    if (!r || nsteps < 0) return DDQMC_ERR_INVALID_ARG;
+    if (r->host_status) return r->host_status;
+    // with timing on, steps are issued in batches whose events are folded in after each batch
+    const int64_t batch = r->timing ? 256 : nsteps;
+    for (int64_t done = 0; done < nsteps || (nsteps == 0 && done == 0); done += batch) {
+        const int64_t n = nsteps - done < batch ? nsteps - done : batch;
+        int rc = enqueue_steps(r, n);
+        if (rc != DDQMC_OK) return rc;
+        rc = read_status(r);
+        collect_timing(r, n);
+        if (rc != DDQMC_OK || nsteps == 0) return rc;
+    }
+    return DDQMC_OK;
+}
+
+int ddqmc_set_timing(ddqmc_run *r, int32_t enable) {
+    if (!r) return DDQMC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    r->timing = enable != 0;
+    for (int k = 0; k < 8; ++k) { r->kernel_ms[k] = 0.0; r->kernel_launches[k] = 0; }
+    return DDQMC_OK;
+}
+
+int ddqmc_get_timing(ddqmc_run *r, double *ms, int64_t *launches, int32_t cap) {
+    if (!r || cap < 0 || (cap > 0 && (!ms || !launches))) return DDQMC_ERR_INVALID_ARG;
+    for (int k = 0; k < cap && k < NKCLASS; ++k) { ms[k] = r->kernel_ms[k]; launches[k] = r->kernel_launches[k]; }
+    return DDQMC_OK;
+}
+
+int ddqmc_get_totals(ddqmc_run *r, int64_t *walker_steps, int64_t *entry_steps, int64_t *spawn_records,
+                     int64_t *merged_entries) {
+    if (!r) return DDQMC_ERR_INVALID_ARG;
+    DevState hs;
+    if (cudaMemcpyAsync(&hs, r->dS, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    if (walker_steps) *walker_steps = hs.walker_steps;
+    if (entry_steps) *entry_steps = hs.sum_M;
+    if (spawn_records) *spawn_records = hs.sum_R;
+    if (merged_entries) *merged_entries = hs.sum_Mnext;
+    return DDQMC_OK;
 }
 
 int ddqmc_get_state(ddqmc_run *r, ddqmc_state *out) {
@@ -618,11 +725,8 @@ int ddqmc_export_walkers(ddqmc_run *r, uint64_t *ket, uint64_t *bra, int32_t *re
     *n = M;
     const int64_t m = cap < M ? cap : M;
     if (m <= 0) return DDQMC_OK;
-    Rec *h = nullptr;
-    if (cudaMallocHost((void **)&h, sizeof(Rec) * (size_t)m) != cudaSuccess) {
-        cudaGetLastError();
-        return DDQMC_ERR_OOM;
-    }
+    Rec *h = host_stage(r, m);
+    if (!h) return DDQMC_ERR_OOM;
     int rc = DDQMC_OK;
     if (cudaMemcpyAsync(h, r->L[r->cur], sizeof(Rec) * (size_t)m, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
@@ -638,7 +742,6 @@ int ddqmc_export_walkers(ddqmc_run *r, uint64_t *ket, uint64_t *bra, int32_t *re
             im[q] = h[q].im;
         }
     }
-    cudaFreeHost(h);
     return rc;
 }
 
@@ -650,15 +753,14 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     if (n > r->mcap) return DDQMC_ERR_CAPACITY;
     const int N = r->hp.N;
     const uint64_t mask = r->hp.nmask;
-    Rec *h = nullptr;
-    if (n > 0 && cudaMallocHost((void **)&h, sizeof(Rec) * (size_t)n) != cudaSuccess) {
-        cudaGetLastError();
-        return DDQMC_ERR_OOM;
-    }
+    // make sure no earlier transfer still reads the staging buffer
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    Rec *h = n > 0 ? host_stage(r, n) : nullptr;
+    if (n > 0 && !h) return DDQMC_ERR_OOM;
     for (int64_t q = 0; q < n; ++q) {
         const bool bad = (ket[q] & ~mask) || (bra[q] & ~mask) || (re[q] == 0 && im[q] == 0) ||
                          (q > 0 && (bra[q - 1] > bra[q] || (bra[q - 1] == bra[q] && ket[q - 1] >= ket[q])));
-        if (bad) { cudaFreeHost(h); return DDQMC_ERR_INVALID_ARG; }
+        if (bad) return DDQMC_ERR_INVALID_ARG;
         h[q].key = (bra[q] << N) | ket[q];
         h[q].re = re[q];
         h[q].im = im[q];
@@ -671,7 +773,6 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
             cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
         cudaGetLastError();
-        cudaFreeHost(h);
         return DDQMC_ERR_CUDA;
     }
     DevState hs;
@@ -694,7 +795,6 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     ok = ok && cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * (size_t)NOBS_MAX * LEVELS, r->stream) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
-    if (h) cudaFreeHost(h);
     if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
     r->host_status = 0;
     return DDQMC_OK;

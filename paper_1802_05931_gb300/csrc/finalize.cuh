@@ -62,6 +62,9 @@ k_finalize(const RunParams *__restrict__ Pp, DevState *__restrict__ st, BlkCell 
         st->S = S;
         st->q_prev = Q;
         st->walker_steps += st->W_cur;
+        st->sum_M += st->M;
+        st->sum_R += st->R;
+        st->sum_Mnext += st->M_next;
         st->W_cur = s_est[3];
         st->t += 1;
         st->M = st->M_next;

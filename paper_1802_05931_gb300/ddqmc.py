@@ -66,7 +66,8 @@ class ddqmc_state(C.Structure):
 EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_async", "ddqmc_sync",
            "ddqmc_estimators", "ddqmc_raw_estimators", "ddqmc_blocking_moments",
            "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_get_state", "ddqmc_get_counts",
-           "ddqmc_destroy", "ddqmc_strerror"]
+           "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_destroy", "ddqmc_strerror"]
+KERNEL_CLASSES = ["spawn_death", "radix_pass", "merge_partition", "merge", "finalize"]
 
 _lib = None
 
@@ -96,6 +97,9 @@ def load(path: str = LIB_PATH):
                                          i64, i64]
     lib.ddqmc_get_state.argtypes = [vp, P(ddqmc_state)]
     lib.ddqmc_get_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
+    lib.ddqmc_get_totals.argtypes = [vp, P(i64), P(i64), P(i64), P(i64)]
+    lib.ddqmc_set_timing.argtypes = [vp, i32]
+    lib.ddqmc_get_timing.argtypes = [vp, P(dbl), P(i64), i32]
     lib.ddqmc_destroy.argtypes = [vp]
     lib.ddqmc_destroy.restype = None
     lib.ddqmc_strerror.argtypes = [C.c_int]
@@ -207,6 +211,24 @@ def ddqmc_get_counts(run):
     r, mc, rc_ = C.c_int64(), C.c_int64(), C.c_int64()
     _check(load().ddqmc_get_counts(run, C.byref(r), C.byref(mc), C.byref(rc_)), "ddqmc_get_counts")
     return r.value, mc.value, rc_.value
+
+
+def ddqmc_get_totals(run):
+    a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().ddqmc_get_totals(run, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "ddqmc_get_totals")
+    return dict(walker_steps=a.value, entry_steps=b.value, spawn_records=c.value, merged_entries=d.value)
+
+
+def ddqmc_set_timing(run, enable):
+    _check(load().ddqmc_set_timing(run, int(bool(enable))), "ddqmc_set_timing")
+
+
+def ddqmc_get_timing(run):
+    ms = np.zeros(len(KERNEL_CLASSES), dtype=np.float64)
+    n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
+    _check(load().ddqmc_get_timing(run, _p(ms, C.c_double), _p(n, C.c_int64), len(KERNEL_CLASSES)),
+           "ddqmc_get_timing")
+    return {k: (float(ms[q]), int(n[q])) for q, k in enumerate(KERNEL_CLASSES)}
 
 
 def ddqmc_destroy(run):
