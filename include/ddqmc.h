@@ -200,6 +200,27 @@ int ddqmc_set_timing(ddqmc_run *run, int32_t enable);
 /* Accumulated milliseconds and launch counts per kernel class (cap >= 5). */
 int ddqmc_get_timing(ddqmc_run *run, double *ms, int64_t *launches, int32_t cap);
 
+/* Annihilation stage on its own (Sec. III.C rule (iii) with the initiator
+ * rule of Sec. IV.A): sort spawn records by configuration and merge them into
+ * a sorted list.  Records are 16 bytes, { uint64 key; int32 re; int32 im; },
+ * key = bra << N | ket; in spawn records bit 63 of the key is set when the
+ * parent was an initiator.
+ *   d_list   m records, strictly increasing keys, no flag bit (device memory);
+ *   d_spawns nsp records in any order (device memory, read only);
+ *   d_out    room for out_cap records (device memory, must not overlap the
+ *            inputs); receives the merged list, *m_out entries: every key keeps
+ *            its list population plus its spawns, except that spawns of
+ *            non-initiator parents count only on keys present in d_list or on
+ *            the diagonal (or always when the run's threshold is 0); zero sums
+ *            are dropped.
+ * Uses the run's lattice and initiator threshold and the run's spawn buffers
+ * as scratch (so it must not overlap a ddqmc_step_async of the same run);
+ * issued on the run's stream and waited for.  Errors: INVALID_ARG,
+ * CAPACITY (nsp above the run's spawn capacity, m above its list capacity,
+ * or more than out_cap merged entries), OVERFLOW, TIMEOUT, CUDA. */
+int ddqmc_annihilate(ddqmc_run *run, const void *d_list, int64_t m, const void *d_spawns, int64_t nsp,
+                     void *d_out, int64_t out_cap, int64_t *m_out);
+
 /* Free every resource of the run (NULL is ignored). */
 void ddqmc_destroy(ddqmc_run *run);
 

@@ -413,6 +413,49 @@ static int or_push(or_spawn_vec *sv, uint64_t ket, uint64_t bra, int32_t dre, in
 static void or_estimate(or_run *r, int64_t *est);
 static int or_series_append(or_run *r, const int64_t *est);
 
+/* Annihilation (Sec. III.C, rule (iii)) with the initiator rule of Sec. IV.A:
+ * sort the spawned children by configuration, then walk L (sorted, unique)
+ * and the children together; every configuration keeps the sum of its own
+ * population and its children, except that children of non-initiator parents
+ * count only on configurations occupied in L or on the diagonal (or when
+ * n_a = 0, where every parent is an initiator).  Zero sums are dropped.
+ * Sorts `sp` in place; *out is malloc'ed. */
+static int or_merge_spawns(const or_entry *L, int64_t M, or_spawn *sp, int64_t R, int32_t n_a,
+                           or_entry **out_p, int64_t *m_p) {
+    if (R > 1) qsort(sp, (size_t)R, sizeof(or_spawn), or_spawn_cmp);
+    int64_t cap = M + R + 1;
+    or_entry *out = (or_entry *)malloc(sizeof(or_entry) * (size_t)cap);
+    if (!out) return OR_ERR_OOM;
+    int64_t a = 0, b = 0, m = 0;
+    while (a < M || b < R) {
+        uint64_t ket, bra;
+        if (b >= R || (a < M && or_cmp_key(L[a].ket, L[a].bra, sp[b].ket, sp[b].bra) <= 0)) {
+            ket = L[a].ket; bra = L[a].bra;
+        } else {
+            ket = sp[b].ket; bra = sp[b].bra;
+        }
+        int occupied = (a < M && L[a].ket == ket && L[a].bra == bra);
+        int64_t sre = 0, sim = 0;
+        if (occupied) { sre = L[a].re; sim = L[a].im; ++a; }
+        int open = occupied || (ket == bra) || (n_a == 0);
+        while (b < R && sp[b].ket == ket && sp[b].bra == bra) {
+            if (open || sp[b].init) { sre += sp[b].dre; sim += sp[b].dim; }
+            ++b;
+        }
+        if (sre == 0 && sim == 0) continue;
+        if (sre > 2147483647LL || sre < -2147483647LL || sim > 2147483647LL || sim < -2147483647LL) {
+            free(out);
+            return OR_ERR_OVERFLOW;
+        }
+        out[m].ket = ket; out[m].bra = bra; out[m].re = sre; out[m].im = sim; ++m;
+    }
+    *out_p = out;
+    *m_p = m;
+    return OR_OK;
+}
+
+
+
 int or_step(or_run *r, int64_t nsteps) {
     or_move mv[2 * OR_MAX_BONDS + OR_MAX_SITES];
     for (int64_t it = 0; it < nsteps; ++it) {
@@ -508,37 +551,13 @@ int or_step(or_run *r, int64_t nsteps) {
         r->last_spawns = sv.n;
 
         /* (iii) annihilation: sort the spawns, then one linear merge */
-        if (sv.n > 1) qsort(sv.v, (size_t)sv.n, sizeof(or_spawn), or_spawn_cmp);
-        int64_t cap = r->M + sv.n + 1;
-        or_entry *out = (or_entry *)malloc(sizeof(or_entry) * (size_t)cap);
-        if (!out) { free(sv.v); return OR_ERR_OOM; }
-        int64_t a = 0, b = 0, m = 0;
-        while (a < r->M || b < sv.n) {
-            uint64_t ket, bra;
-            if (b >= sv.n || (a < r->M && or_cmp_key(r->L[a].ket, r->L[a].bra, sv.v[b].ket, sv.v[b].bra) <= 0)) {
-                ket = r->L[a].ket; bra = r->L[a].bra;
-            } else {
-                ket = sv.v[b].ket; bra = sv.v[b].bra;
-            }
-            int occupied = (a < r->M && r->L[a].ket == ket && r->L[a].bra == bra);
-            int64_t sre = 0, sim = 0;
-            if (occupied) { sre = r->L[a].re; sim = r->L[a].im; ++a; }
-            /* initiator rule (Sec. IV.A): a non-initiator child survives only on an
-             * occupied or a diagonal configuration */
-            int open = occupied || (ket == bra) || (r->n_a == 0);
-            while (b < sv.n && sv.v[b].ket == ket && sv.v[b].bra == bra) {
-                if (open || sv.v[b].init) { sre += sv.v[b].dre; sim += sv.v[b].dim; }
-                ++b;
-            }
-            if (sre == 0 && sim == 0) continue;
-            if (sre > 2147483647LL || sre < -2147483647LL || sim > 2147483647LL || sim < -2147483647LL) {
-                free(out); free(sv.v); return OR_ERR_OVERFLOW;
-            }
-            out[m].ket = ket; out[m].bra = bra; out[m].re = sre; out[m].im = sim; ++m;
-        }
+        or_entry *out = NULL;
+        int64_t m = 0;
+        int rc = or_merge_spawns(r->L, r->M, sv.v, sv.n, r->n_a, &out, &m);
         free(sv.v);
+        if (rc != OR_OK) return rc;
         free(r->L);
-        r->L = out; r->M = m; r->capL = cap;
+        r->L = out; r->M = m; r->capL = m > 0 ? m : 1;
 
         /* estimators on rho(t+1), then the shift update of Sec. III.C */
         int64_t est[5 + OR_MAX_SITES + 3 * OR_MAX_BONDS + 4];
@@ -716,3 +735,31 @@ int or_inject(or_run *r, const uint32_t *u, int64_t n) {
     return short_;
 }
 int64_t or_injected_used(const or_run *r) { return r->pinj; }
+
+/* Standalone annihilation of arrays: list (m entries, sorted by (bra, ket),
+ * unique) and spawn records (r entries, any order; init = parent initiator
+ * flag).  Writes up to cap merged entries; returns the merged length, or a
+ * negative error code. */
+int64_t or_annihilate(const uint64_t *lket, const uint64_t *lbra, const int32_t *lre, const int32_t *lim,
+                      int64_t m, const uint64_t *sket, const uint64_t *sbra, const int32_t *sre,
+                      const int32_t *sim, const int32_t *sinit, int64_t r, int32_t n_a,
+                      uint64_t *oket, uint64_t *obra, int32_t *ore, int32_t *oim, int64_t cap) {
+    or_entry *L = (or_entry *)malloc(sizeof(or_entry) * (size_t)(m > 0 ? m : 1));
+    or_spawn *sp = (or_spawn *)malloc(sizeof(or_spawn) * (size_t)(r > 0 ? r : 1));
+    if (!L || !sp) { free(L); free(sp); return OR_ERR_OOM; }
+    for (int64_t q = 0; q < m; ++q) { L[q].ket = lket[q]; L[q].bra = lbra[q]; L[q].re = lre[q]; L[q].im = lim[q]; }
+    for (int64_t q = 0; q < r; ++q) {
+        sp[q].ket = sket[q]; sp[q].bra = sbra[q]; sp[q].dre = sre[q]; sp[q].dim = sim[q]; sp[q].init = sinit[q] != 0;
+    }
+    or_entry *out = NULL;
+    int64_t mo = 0;
+    int rc = or_merge_spawns(L, m, sp, r, n_a, &out, &mo);
+    free(L);
+    free(sp);
+    if (rc != OR_OK) return rc;
+    for (int64_t q = 0; q < mo && q < cap; ++q) {
+        oket[q] = out[q].ket; obra[q] = out[q].bra; ore[q] = (int32_t)out[q].re; oim[q] = (int32_t)out[q].im;
+    }
+    free(out);
+    return mo;
+}

@@ -76,6 +76,9 @@ def _load():
         lib.or_inject.argtypes = [C.c_void_p, P(C.c_uint32), i64]
         lib.or_inject.restype = C.c_int
         lib.or_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+        lib.or_annihilate.argtypes = [P(u64), P(u64), P(i32), P(i32), i64, P(u64), P(u64), P(i32), P(i32),
+                                      P(i32), i64, i32, P(u64), P(u64), P(i32), P(i32), i64]
+        lib.or_annihilate.restype = i64
         lib.or_series_log.argtypes = [dbl]
         lib.or_series_log.restype = dbl
         _lib = lib
@@ -94,6 +97,25 @@ def philox4x32_10(ctr, key):
     out = np.zeros(4, dtype=np.uint32)
     lib.or_philox4x32_10(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(out, C.c_uint32))
     return [int(x) for x in out]
+
+
+def annihilate(lket, lbra, lre, lim, sket, sbra, sre, sim, sinit, n_a):
+    """Annihilation of a sorted list with unsorted spawn records under the
+    initiator rule (Sec. III.C rule (iii), Sec. IV.A); returns the merged list."""
+    lib = _load()
+    a = [np.ascontiguousarray(x, dtype=t) for x, t in ((lket, np.uint64), (lbra, np.uint64), (lre, np.int32),
+                                                     (lim, np.int32))]
+    b = [np.ascontiguousarray(x, dtype=t) for x, t in ((sket, np.uint64), (sbra, np.uint64), (sre, np.int32),
+                                                     (sim, np.int32), (sinit, np.int32))]
+    cap = len(a[0]) + len(b[0])
+    o = [np.zeros(max(cap, 1), dtype=t) for t in (np.uint64, np.uint64, np.int32, np.int32)]
+    cts = (C.c_uint64, C.c_uint64, C.c_int32, C.c_int32)
+    n = lib.or_annihilate(*[_ptr(x, ct) for x, ct in zip(a, cts)], len(a[0]),
+                          *[_ptr(x, ct) for x, ct in zip(b, cts + (C.c_int32,))], len(b[0]), int(n_a),
+                          *[_ptr(x, ct) for x, ct in zip(o, cts)], cap)
+    if n < 0:
+        raise RuntimeError("oracle annihilation failed (%d)" % n)
+    return tuple(x[:n] for x in o)
 
 
 def series_log(x: float) -> float:

@@ -48,6 +48,9 @@ struct ddqmc_run {
     // pinned host staging for import / export, kept between calls
     Rec *hstage = nullptr;
     int64_t hstage_cap = 0;
+    // counters of standalone annihilation calls (allocated on first use)
+    DevState *dAnn = nullptr;
+    uint32_t ann_calls = 0;
 };
 
 namespace {
@@ -236,6 +239,7 @@ void free_run(ddqmc_run *r) {
     cudaFree(r->lb_radix);
     cudaFree(r->lb_merge);
     cudaFree(r->splits);
+    cudaFree(r->dAnn);
     if (r->own_stream && r->stream) cudaStreamDestroy(r->stream);
     delete r;
 }
@@ -798,6 +802,47 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
     r->host_status = 0;
     return DDQMC_OK;
+}
+
+int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_spawns, int64_t nsp, void *d_out,
+                     int64_t out_cap, int64_t *m_out) {
+    if (!r || !m_out || m < 0 || nsp < 0 || out_cap < 0 || (m > 0 && !d_list) || (nsp > 0 && !d_spawns) ||
+        (out_cap > 0 && !d_out))
+        return DDQMC_ERR_INVALID_ARG;
+    if (nsp > r->rcap || m > r->mcap) return DDQMC_ERR_CAPACITY;
+    *m_out = 0;
+    if (!r->dAnn && dalloc(&r->dAnn, 1) != DDQMC_OK) return DDQMC_ERR_OOM;
+    const RunParams &P = r->hp;
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.M = m;
+    hs.R = nsp;
+    // epochs of standalone calls carry bit 29, those of the run's steps do not
+    hs.epoch = (1u << 29) | ((r->ann_calls++ * 16u) & ((1u << 29) - 1u));
+    if (cudaMemcpyAsync(r->dAnn, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    const Rec *list = (const Rec *)d_list;
+    const Rec *sp = (const Rec *)d_spawns;
+    k_digit_histogram<<<r->g_part, RX_TPB, 0, r->stream>>>(sp, r->dAnn, P.npass);
+    const Rec *src = sp;
+    for (int p = 0; p < P.npass; ++p) {
+        Rec *dst = r->Sp[p & 1];
+        k_radix_pass<<<r->g_radix, RX_TPB, RX_SMEM, r->stream>>>(src, dst, r->dAnn, r->lb_radix, p, 8 * p, r->rcap);
+        src = dst;
+    }
+    k_merge_partition<<<r->g_part, 256, 0, r->stream>>>(list, src, r->dAnn, r->splits, r->rcap);
+    k_merge<<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, list, src, (Rec *)d_out, r->dAnn, r->splits,
+                                                        r->lb_merge, r->rcap, out_cap);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&hs, r->dAnn, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    *m_out = hs.M_next;
+    return status_code(hs.status);
 }
 
 void ddqmc_destroy(ddqmc_run *r) {

@@ -31,6 +31,25 @@ struct RadixShared {
     int64_t tile;
 };
 
+// Digit histograms of every pass over st->R records (used when the records do
+// not come from the spawn kernel, which counts them as it writes them).
+__global__ void __launch_bounds__(RX_TPB)
+k_digit_histogram(const Rec *__restrict__ in, DevState *__restrict__ st, int npass) {
+    __shared__ uint32_t h[MAXPASS][256];
+    const int tid = threadIdx.x;
+    if (block_stopped(st)) return;
+    for (int q = tid; q < MAXPASS * 256; q += RX_TPB) (&h[0][0])[q] = 0u;
+    __syncthreads();
+    const int64_t R = st->R;
+    for (int64_t q = (int64_t)blockIdx.x * RX_TPB + tid; q < R; q += (int64_t)gridDim.x * RX_TPB) {
+        const uint64_t key = in[q].key & KEY_MASK;
+        for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 0xFFull], 1u);
+    }
+    __syncthreads();
+    for (int q = tid; q < npass * 256; q += RX_TPB)
+        if ((&h[0][0])[q]) atomicAdd(&st->hist[q >> 8][q & 255], (&h[0][0])[q]);
+}
+
 __global__ void __launch_bounds__(RX_TPB)
 k_radix_pass(const Rec *__restrict__ in, Rec *__restrict__ out, DevState *__restrict__ st,
              uint64_t *__restrict__ lookback, int pass, int shift, int64_t cap) {

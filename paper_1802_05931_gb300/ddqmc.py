@@ -66,7 +66,8 @@ class ddqmc_state(C.Structure):
 EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_async", "ddqmc_sync",
            "ddqmc_estimators", "ddqmc_raw_estimators", "ddqmc_blocking_moments",
            "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_get_state", "ddqmc_get_counts",
-           "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_destroy", "ddqmc_strerror"]
+           "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_annihilate",
+           "ddqmc_destroy", "ddqmc_strerror"]
 KERNEL_CLASSES = ["spawn_death", "radix_pass", "merge_partition", "merge", "finalize"]
 
 _lib = None
@@ -100,6 +101,7 @@ def load(path: str = LIB_PATH):
     lib.ddqmc_get_totals.argtypes = [vp, P(i64), P(i64), P(i64), P(i64)]
     lib.ddqmc_set_timing.argtypes = [vp, i32]
     lib.ddqmc_get_timing.argtypes = [vp, P(dbl), P(i64), i32]
+    lib.ddqmc_annihilate.argtypes = [vp, vp, i64, vp, i64, vp, i64, P(i64)]
     lib.ddqmc_destroy.argtypes = [vp]
     lib.ddqmc_destroy.restype = None
     lib.ddqmc_strerror.argtypes = [C.c_int]
@@ -229,6 +231,14 @@ def ddqmc_get_timing(run):
     _check(load().ddqmc_get_timing(run, _p(ms, C.c_double), _p(n, C.c_int64), len(KERNEL_CLASSES)),
            "ddqmc_get_timing")
     return {k: (float(ms[q]), int(n[q])) for q, k in enumerate(KERNEL_CLASSES)}
+
+
+def ddqmc_annihilate(run, d_list, m, d_spawns, nsp, d_out, out_cap):
+    """Device pointers (ints) in and out; returns the merged length."""
+    n = C.c_int64()
+    _check(load().ddqmc_annihilate(run, C.c_void_p(d_list), int(m), C.c_void_p(d_spawns), int(nsp),
+                                   C.c_void_p(d_out), int(out_cap), C.byref(n)), "ddqmc_annihilate")
+    return n.value
 
 
 def ddqmc_destroy(run):

@@ -1,0 +1,86 @@
+"""ddqmc_annihilate (onesweep radix sort + merge-path merge on caller-provided
+device records) against the oracle's annihilation, bit for bit."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import records as RC
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1802_05931_gb300 import ddqmc
+    return torch, ddqmc
+
+
+def _dev(torch, recs):
+    b = np.ascontiguousarray(recs).view(np.uint8)
+    t = torch.from_numpy(b.copy()).cuda() if len(b) else torch.empty(16, dtype=torch.uint8, device="cuda")
+    return t
+
+
+def run_case(env, run, N, n_a, L, S):
+    torch, ddqmc = env
+    dl, ds = _dev(torch, L), _dev(torch, S)
+    cap = len(L) + len(S) + 1
+    out = torch.empty(cap * 16, dtype=torch.uint8, device="cuda")
+    n = ddqmc.ddqmc_annihilate(run.h, dl.data_ptr(), len(L), ds.data_ptr(), len(S), out.data_ptr(), cap)
+    got = out[: n * 16].cpu().numpy().view(RC.REC)
+    lk, lb, lr, li, _ = RC.split(L, N)
+    sk, sb, sr, si, sf = RC.split(S, N)
+    ok, ob, orr, oi = O.annihilate(lk, lb, lr, li, sk, sb, sr, si, sf, n_a)
+    ref = np.zeros(len(ok), dtype=RC.REC)
+    ref["key"] = (ob << np.uint64(N)) | ok
+    ref["re"] = orr
+    ref["im"] = oi
+    return got, ref
+
+
+@pytest.mark.parametrize("n_a", [0, 3])
+@pytest.mark.parametrize("m,r", [(0, 0), (0, 7), (5, 0), (1, 1), (3000, 5000), (2047, 2049), (40000, 100000),
+                                 (250000, 700000)])
+def test_annihilate_matches_oracle(env, n_a, m, r):
+    torch, ddqmc = env
+    N = 16
+    run = ddqmc.Run(4, 4, 1, 0.9, 1.0, 1.0, 1.0, 0.005, 10 ** 6, n_a=n_a, control=1,
+                    capacity_entries=1 << 21, capacity_spawns=1 << 21)
+    L, S = RC.random_case(1000 * m + r + n_a, N, m, r)
+    got, ref = run_case(env, run, N, n_a, L, S)
+    assert len(got) == len(ref)
+    assert np.array_equal(got["key"], ref["key"])
+    assert np.array_equal(got["re"], ref["re"]) and np.array_equal(got["im"], ref["im"])
+
+
+def test_annihilate_twice_in_a_row_and_between_steps(env):
+    """Standalone calls interleaved with steps of the same run give the same
+    results and leave the run's own stepping untouched."""
+    torch, ddqmc = env
+    N = 9
+    args = (3, 3, 1, 0.9, 1.0, 1.0, 1.0, 0.005, 20000)
+    run = ddqmc.Run(*args, n_a=3, control=1)
+    ref_run = O.OracleRun(*args, n_a=3, control=1)
+    L, S = RC.random_case(5, N, 20000, 60000)
+    first = run_case(env, run, N, 3, L, S)
+    for _ in range(3):
+        run.step(40)
+        ref_run.step(40)
+        got, ref = run_case(env, run, N, 3, L, S)
+        assert np.array_equal(got, first[0]) and np.array_equal(got, ref)
+    g = run.export()
+    c = ref_run.export()
+    for a, b in zip(g, c):
+        assert np.array_equal(a, b)
+
+
+def test_annihilate_rejects_too_many_spawns(env):
+    torch, ddqmc = env
+    run = ddqmc.Run(2, 2, 0, 0.9, 1.0, 1.0, 1.0, 0.01, 100, capacity_entries=4096, capacity_spawns=4096)
+    x = torch.empty(16 * 8192, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ddqmc.DDQMCError) as e:
+        ddqmc.ddqmc_annihilate(run.h, x.data_ptr(), 0, x.data_ptr(), 8192, x.data_ptr(), 8192)
+    assert e.value.code == -3
