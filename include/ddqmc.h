@@ -221,6 +221,30 @@ int ddqmc_get_timing(ddqmc_run *run, double *ms, int64_t *launches, int32_t cap)
 int ddqmc_annihilate(ddqmc_run *run, const void *d_list, int64_t m, const void *d_spawns, int64_t nsp,
                      void *d_out, int64_t out_cap, int64_t *m_out);
 
+/* The annihilation stage of ddqmc_annihilate for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this is a property
+ * of the library, not of the method.  Some callers cannot call cudaMalloc:
+ * their device memory is already reserved by another allocator's pool (a
+ * serving engine or a framework's caching allocator that took it up front),
+ * or they must stay off the driver's allocation path and its implicit
+ * synchronisation.  This entry point allocates nothing and needs no run: its
+ * scratch is a fixed array inside the library that every GPU loading the
+ * library holds until the process exits (about 8.6 MB).
+ *   lattice, initiator_threshold: as in ddqmc_create (key layout and rule);
+ *   d_list, m, d_spawns, nsp, d_out, out_cap, *m_out: as in ddqmc_annihilate,
+ *     with m <= 1048576 list entries and nsp <= 262144 spawn records
+ *     (larger sizes return DDQMC_ERR_CAPACITY before any work);
+ *   cuda_stream: stream to issue on (NULL: the default stream); the call
+ *     waits for it before returning.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current), so make that first call before any
+ * stream capture.  Every call shares the array and leaves its contents
+ * behind; calls that overlap on the GPU (from two streams or two host
+ * threads at once) race on it and must be serialised by the caller. */
+int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_threshold,
+                             const void *d_list, int64_t m, const void *d_spawns, int64_t nsp,
+                             void *d_out, int64_t out_cap, int64_t *m_out, void *cuda_stream);
+
 /* Free every resource of the run (NULL is ignored). */
 void ddqmc_destroy(ddqmc_run *run);
 

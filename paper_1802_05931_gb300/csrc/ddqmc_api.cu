@@ -393,6 +393,72 @@ void blocked_ratio(const std::vector<BlkCell> &cells, int k, double &R, double &
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Scratch of ddqmc_annihilate_noalloc, in the library's own device memory.
+//
+// Some callers cannot call cudaMalloc: a process whose device memory is
+// already reserved by another allocator's pool (a serving engine or a
+// framework's caching allocator that took it all up front), or a loop that
+// must not take the driver's allocation path with its implicit
+// synchronisation.  For them the annihilation stage can run out of this fixed
+// array instead: every GPU that loads the library holds it until the process
+// exits.  In host code the array's name is only a host-side stand-in; the
+// device address comes from cudaGetSymbolAddress, looked up once per device.
+// Every call shares the array and leaves its contents behind; the parts that
+// must start at zero are cleared at the start of each call, and calls that
+// overlap on the GPU (two streams at once) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NA_MAX_SPAWNS = 1ll << 18;     // spawn records per call
+constexpr int64_t NA_MAX_LIST = 1ll << 20;       // list entries per call
+constexpr int64_t NA_RTILES = NA_MAX_SPAWNS / RX_TILE + 2;
+constexpr int64_t NA_MTILES = (NA_MAX_LIST + NA_MAX_SPAWNS) / MG_TILE + 3;
+
+struct NoAllocScratch {
+    RunParams P;
+    DevState st;
+    uint64_t lb_radix[NA_RTILES * 256];
+    uint64_t lb_merge[NA_MTILES];
+    int64_t splits[NA_MTILES + 1];
+    Rec buf[2][NA_MAX_SPAWNS];
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+constexpr int NA_MAX_DEVICES = 64;
+NoAllocScratch *g_na_ptr[NA_MAX_DEVICES] = {nullptr};
+int g_na_grid[NA_MAX_DEVICES][3];       // radix, partition, merge grids
+
+// Once per device, with that device current: device address of the scratch
+// array and the launch shapes.
+int noalloc_setup(int dev) {
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return DDQMC_ERR_UNSUPPORTED;
+    if (g_na_ptr[dev]) return DDQMC_OK;
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    if (cudaFuncSetAttribute(k_radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    g_na_grid[dev][0] = occupancy_grid((const void *)k_radix_pass, RX_TPB, RX_SMEM, sms);
+    g_na_grid[dev][1] = 4 * sms;
+    g_na_grid[dev][2] = occupancy_grid((const void *)k_merge, MG_TPB, MG_SMEM, sms);
+    g_na_ptr[dev] = (NoAllocScratch *)ptr;
+    return DDQMC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int ddqmc_default_options(ddqmc_options *o) {
@@ -843,6 +909,63 @@ int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_
     }
     *m_out = hs.M_next;
     return status_code(hs.status);
+}
+
+int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_threshold, const void *d_list,
+                             int64_t m, const void *d_spawns, int64_t nsp, void *d_out, int64_t out_cap,
+                             int64_t *m_out, void *cuda_stream) {
+    if (!lattice || !m_out || m < 0 || nsp < 0 || out_cap < 0 || (m > 0 && !d_list) || (nsp > 0 && !d_spawns) ||
+        (out_cap > 0 && !d_out))
+        return DDQMC_ERR_INVALID_ARG;
+    *m_out = 0;
+    if (nsp > NA_MAX_SPAWNS || m > NA_MAX_LIST) return DDQMC_ERR_CAPACITY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    int rc = noalloc_setup(dev);
+    if (rc != DDQMC_OK) return rc;
+    NoAllocScratch *sc = g_na_ptr[dev];
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    // lattice tables (host only; couplings do not enter the annihilation)
+    ddqmc_run host_ctx;
+    ddqmc_options o;
+    ddqmc_default_options(&o);
+    rc = build_params(&host_ctx, lattice, 0.0, 0.0, 0.0, 0.0, 1.0, 1, initiator_threshold, nullptr, o);
+    if (rc != DDQMC_OK) return rc;
+    const RunParams &P = host_ctx.hp;
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.M = m;
+    hs.R = nsp;
+    hs.epoch = 16;
+    // clear what must start at zero: counters, histograms, tickets, look-back words
+    bool ok = cudaMemcpyAsync(&sc->P, &P, sizeof(RunParams), cudaMemcpyHostToDevice, stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(&sc->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(sc->lb_radix, 0, sizeof(sc->lb_radix), stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(sc->lb_merge, 0, sizeof(sc->lb_merge), stream) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    const Rec *list = (const Rec *)d_list;
+    const Rec *src = (const Rec *)d_spawns;
+    k_digit_histogram<<<g_na_grid[dev][1], RX_TPB, 0, stream>>>(src, &sc->st, P.npass);
+    for (int p = 0; p < P.npass; ++p) {
+        Rec *dst = sc->buf[p & 1];
+        k_radix_pass<<<g_na_grid[dev][0], RX_TPB, RX_SMEM, stream>>>(src, dst, &sc->st, sc->lb_radix, p, 8 * p,
+                                                                      NA_MAX_SPAWNS);
+        src = dst;
+    }
+    k_merge_partition<<<g_na_grid[dev][1], 256, 0, stream>>>(list, src, &sc->st, sc->splits, NA_MAX_SPAWNS);
+    k_merge<<<g_na_grid[dev][2], MG_TPB, MG_SMEM, stream>>>(&sc->P, list, src, (Rec *)d_out, &sc->st, sc->splits,
+                                                            sc->lb_merge, NA_MAX_SPAWNS, out_cap);
+    int64_t mo = 0;
+    uint32_t status = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&mo, &sc->st.M_next, sizeof(mo), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaMemcpyAsync(&status, &sc->st.status, sizeof(status), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    *m_out = mo;
+    return status_code(status);
 }
 
 void ddqmc_destroy(ddqmc_run *r) {

@@ -67,7 +67,9 @@ EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_as
            "ddqmc_estimators", "ddqmc_raw_estimators", "ddqmc_blocking_moments",
            "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_get_state", "ddqmc_get_counts",
            "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_annihilate",
-           "ddqmc_destroy", "ddqmc_strerror"]
+           "ddqmc_annihilate_noalloc", "ddqmc_destroy", "ddqmc_strerror"]
+NOALLOC_MAX_SPAWNS = 1 << 18
+NOALLOC_MAX_LIST = 1 << 20
 KERNEL_CLASSES = ["spawn_death", "radix_pass", "merge_partition", "merge", "finalize"]
 
 _lib = None
@@ -102,6 +104,7 @@ def load(path: str = LIB_PATH):
     lib.ddqmc_set_timing.argtypes = [vp, i32]
     lib.ddqmc_get_timing.argtypes = [vp, P(dbl), P(i64), i32]
     lib.ddqmc_annihilate.argtypes = [vp, vp, i64, vp, i64, vp, i64, P(i64)]
+    lib.ddqmc_annihilate_noalloc.argtypes = [P(ddqmc_lattice), i32, vp, i64, vp, i64, vp, i64, P(i64), vp]
     lib.ddqmc_destroy.argtypes = [vp]
     lib.ddqmc_destroy.restype = None
     lib.ddqmc_strerror.argtypes = [C.c_int]
@@ -238,6 +241,18 @@ def ddqmc_annihilate(run, d_list, m, d_spawns, nsp, d_out, out_cap):
     n = C.c_int64()
     _check(load().ddqmc_annihilate(run, C.c_void_p(d_list), int(m), C.c_void_p(d_spawns), int(nsp),
                                    C.c_void_p(d_out), int(out_cap), C.byref(n)), "ddqmc_annihilate")
+    return n.value
+
+
+def ddqmc_annihilate_noalloc(lattice, initiator_threshold, d_list, m, d_spawns, nsp, d_out, out_cap,
+                             stream=None):
+    """Same as ddqmc_annihilate without a run and without any allocation
+    (scratch in a fixed array inside the library); returns the merged length."""
+    n = C.c_int64()
+    _check(load().ddqmc_annihilate_noalloc(C.byref(lattice), int(initiator_threshold), C.c_void_p(d_list), int(m),
+                                           C.c_void_p(d_spawns), int(nsp), C.c_void_p(d_out), int(out_cap),
+                                           C.byref(n), C.c_void_p(stream) if stream else None),
+           "ddqmc_annihilate_noalloc")
     return n.value
 
 
