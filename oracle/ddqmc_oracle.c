@@ -26,8 +26,9 @@
  *     a configuration is (ket i, bra j); canonical order is (bra, ket);
  *   - H = sum over bonds of Jx sx sx + Jy sy sy + Jz sz sz (Pauli matrices),
  *     decay gamma * D[sigma^-] on every site (Sec. V, XYZ model);
- *   - moves, in this order: ket bond flips b = 0..B-1, bra bond flips
- *     b = 0..B-1, then jumps k = 0..N-1;
+ *   - moves, in this order: ket bond flips, bra bond flips, then jumps by
+ *     site; inside a bond-flip segment grouped by (anti-aligned, importance
+ *     class) and in bond order inside a group;
  *   - per-walker categorical draws, which have the joint law of the
  *     binomial + multinomial scheme of Sec. III.B; n_att = ceil(P_tot)
  *     attempts when P_tot > 1;
@@ -354,24 +355,35 @@ typedef struct {
     uint64_t rate;      /* q(|A| dt w_child / w_parent) */
 } or_move;
 
+/* Move order: the ket bond flips, then the bra bond flips, then the jumps.
+ * Within each bond-flip segment the moves are grouped by g = 4*anti + class
+ * (anti = 1 if the bond is anti-aligned in the flipped word, class = the
+ * importance-sampling class of the bond), groups in increasing g, bonds in
+ * bond order inside a group; jumps go by site. */
 static int or_moves_of(const or_run *r, uint64_t i, uint64_t j, or_move *mv) {
     int K = 0;
-    for (int b = 0; b < r->B; ++b) {           /* -i H rho: child (i ^ m_b, j), A = -i h_b(i) */
-        double h = or_hb(r, i, b);
-        int al = or_bit(i, r->bond_a[b]) != or_bit(i, r->bond_b[b]);
-        mv[K].cket = i ^ r->bond_m[b]; mv[K].cbra = j; mv[K].kind = 0;
-        mv[K].Are = 0.0; mv[K].Aim = -h;
-        mv[K].rate = r->rate_q[b][al][or_ratio_class(r, i, j, b)];
-        ++K;
-    }
-    for (int b = 0; b < r->B; ++b) {           /* +i rho H: child (i, j ^ m_b), A = +i h_b(j) */
-        double h = or_hb(r, j, b);
-        int al = or_bit(j, r->bond_a[b]) != or_bit(j, r->bond_b[b]);
-        mv[K].cket = i; mv[K].cbra = j ^ r->bond_m[b]; mv[K].kind = 1;
-        mv[K].Are = 0.0; mv[K].Aim = h;
-        mv[K].rate = r->rate_q[b][al][or_ratio_class(r, i, j, b)];
-        ++K;
-    }
+    for (int g = 0; g < 8; ++g)                /* -i H rho: child (i ^ m_b, j), A = -i h_b(i) */
+        for (int b = 0; b < r->B; ++b) {
+            int al = or_bit(i, r->bond_a[b]) != or_bit(i, r->bond_b[b]);
+            int cl = or_ratio_class(r, i, j, b);
+            if (4 * al + cl != g) continue;
+            double h = or_hb(r, i, b);
+            mv[K].cket = i ^ r->bond_m[b]; mv[K].cbra = j; mv[K].kind = 0;
+            mv[K].Are = 0.0; mv[K].Aim = -h;
+            mv[K].rate = r->rate_q[b][al][cl];
+            ++K;
+        }
+    for (int g = 0; g < 8; ++g)                /* +i rho H: child (i, j ^ m_b), A = +i h_b(j) */
+        for (int b = 0; b < r->B; ++b) {
+            int al = or_bit(j, r->bond_a[b]) != or_bit(j, r->bond_b[b]);
+            int cl = or_ratio_class(r, i, j, b);
+            if (4 * al + cl != g) continue;
+            double h = or_hb(r, j, b);
+            mv[K].cket = i; mv[K].cbra = j ^ r->bond_m[b]; mv[K].kind = 1;
+            mv[K].Are = 0.0; mv[K].Aim = h;
+            mv[K].rate = r->rate_q[b][al][cl];
+            ++K;
+        }
     for (int k = 0; k < r->N; ++k) {           /* gamma sigma^- rho sigma^+: needs bit k up on both sides */
         int ok = or_bit(i, k) && or_bit(j, k);
         mv[K].cket = i & ~(1ull << k); mv[K].cbra = j & ~(1ull << k); mv[K].kind = 2;

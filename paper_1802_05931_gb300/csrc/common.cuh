@@ -63,7 +63,7 @@ struct RunParams {
     int32_t uniform;                  // 1 if every bond has the same rate table
     int32_t pad1;
     uint64_t Emorton;                 // bond-existence mask, bit 2k = right bond of k, 2k+1 = lower
-    uint64_t urate[2][3];             // [anti-aligned][class] rates when uniform
+    uint64_t urate8[8];               // rate of group 4*anti + class when every bond has the same table
 };
 
 // Device-resident state of a run, updated by the kernels of each step.

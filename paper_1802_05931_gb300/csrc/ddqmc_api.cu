@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -37,6 +38,8 @@ struct ddqmc_run {
     int device = 0;
     int cur = 0;                 // which L buffer holds the current list
     int g_spawn = 0, g_radix = 0, g_part = 0, g_merge = 0;
+    int g_radix_wide = 0;        // radix grid of 16-byte records (standalone annihilation)
+    bool packed = false;         // 8-byte spawn records (2N <= 32) on the step path
     int guide_kind = 0;
     double w_bond[MAXB];         // importance weight of a configuration differing on bond b only
     int host_status = 0;         // sticky host-visible status
@@ -187,14 +190,8 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
     for (int b = 1; b < B; ++b)
         for (int h = 0; h < 2; ++h)
             for (int c = 0; c < 4; ++c) uni = uni && P.rate_q[b][h][c] == P.rate_q[0][h][c];
-    if (gk == 2)
-        for (int h = 0; h < 2; ++h) uni = uni && P.rate_q[0][h][1] == P.rate_q[0][h][2];
     P.uniform = uni ? 1 : 0;
-    for (int h = 0; h < 2; ++h) {
-        P.urate[h][0] = P.rate_q[0][h][0];
-        P.urate[h][1] = P.rate_q[0][h][1];
-        P.urate[h][2] = gk == 2 ? P.rate_q[0][h][3] : P.rate_q[0][h][2];
-    }
+    for (int g = 0; g < 8; ++g) P.urate8[g] = P.rate_q[0][g >> 2][g & 3];
     const double cbase = dt * std::fabs(Jz);
     for (int c = 0; c <= 2 * B; ++c) {
         const double x = cbase * (double)c;
@@ -272,14 +269,39 @@ Rec *host_stage(ddqmc_run *r, int64_t n) {
 }
 
 constexpr size_t SP_SMEM = sizeof(SpawnShared);
-constexpr size_t RX_SMEM = sizeof(RadixShared);
+constexpr size_t RX_SMEM = sizeof(RadixShared<Rec>);
+constexpr size_t RXP_SMEM = sizeof(RadixShared<uint64_t>);
 constexpr size_t MG_SMEM = sizeof(MergeShared);
+
+// One step's launches for spawn records of type T (16-byte Rec or packed 8-byte).
+template <typename T>
+void launch_step(ddqmc_run *r, Rec *Lc, Rec *Ln, const std::function<void(int, int)> &mark) {
+    const RunParams &P = r->hp;
+    T *sp0 = reinterpret_cast<T *>(r->Sp[0]);
+    T *sp1 = reinterpret_cast<T *>(r->Sp[1]);
+    const size_t rx_smem = sizeof(RadixShared<T>);
+    mark(0, 0);
+    k_spawn_death<T><<<r->g_spawn, SP_TPB, SP_SMEM, r->stream>>>(r->dP, r->dS, Lc, sp0, r->rcap);
+    mark(0, 1);
+    mark(1, 0);
+    for (int p = 0; p < P.npass; ++p)
+        k_radix_pass<T><<<r->g_radix, RX_TPB, rx_smem, r->stream>>>((p & 1) ? sp1 : sp0, (p & 1) ? sp0 : sp1, r->dS,
+                                                                   r->lb_radix, p, 8 * p, r->rcap);
+    mark(1, 1);
+    const T *sorted = (P.npass & 1) ? sp1 : sp0;
+    mark(2, 0);
+    k_merge_partition<T><<<r->g_part, 256, 0, r->stream>>>(Lc, sorted, r->dS, r->splits, r->rcap);
+    mark(2, 1);
+    mark(3, 0);
+    k_merge<T><<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits, r->lb_merge,
+                                                           r->rcap, r->mcap);
+    mark(3, 1);
+}
 
 // kernel classes of the per-kernel timing
 enum { KC_SPAWN = 0, KC_RADIX = 1, KC_PARTITION = 2, KC_MERGE = 3, KC_FINALIZE = 4, NKCLASS = 5 };
 
 int enqueue_steps(ddqmc_run *r, int64_t nsteps) {
-    const RunParams &P = r->hp;
     for (int64_t s = 0; s < nsteps; ++s) {
         cudaEvent_t *ev = nullptr;
         if (r->timing) {
@@ -291,26 +313,12 @@ int enqueue_steps(ddqmc_run *r, int64_t nsteps) {
             }
             ev = &r->ev[(size_t)s * 2 * NKCLASS];
         }
-        auto mark = [&](int kc, int edge) {
+        std::function<void(int, int)> mark = [&](int kc, int edge) {
             if (ev) cudaEventRecord(ev[2 * kc + edge], r->stream);
         };
         Rec *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
-        mark(KC_SPAWN, 0);
-        k_spawn_death<<<r->g_spawn, SP_TPB, SP_SMEM, r->stream>>>(r->dP, r->dS, Lc, r->Sp[0], r->rcap);
-        mark(KC_SPAWN, 1);
-        mark(KC_RADIX, 0);
-        for (int p = 0; p < P.npass; ++p)
-            k_radix_pass<<<r->g_radix, RX_TPB, RX_SMEM, r->stream>>>(r->Sp[p & 1], r->Sp[(p + 1) & 1], r->dS,
-                                                                     r->lb_radix, p, 8 * p, r->rcap);
-        mark(KC_RADIX, 1);
-        const Rec *sorted = r->Sp[P.npass & 1];
-        mark(KC_PARTITION, 0);
-        k_merge_partition<<<r->g_part, 256, 0, r->stream>>>(Lc, sorted, r->dS, r->splits, r->rcap);
-        mark(KC_PARTITION, 1);
-        mark(KC_MERGE, 0);
-        k_merge<<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits, r->lb_merge,
-                                                            r->rcap, r->mcap);
-        mark(KC_MERGE, 1);
+        if (r->packed) launch_step<uint64_t>(r, Lc, Ln, mark);
+        else launch_step<Rec>(r, Lc, Ln, mark);
         mark(KC_FINALIZE, 0);
         k_finalize<<<1, FN_TPB, 0, r->stream>>>(r->dP, r->dS, r->dBlk);
         mark(KC_FINALIZE, 1);
@@ -412,7 +420,7 @@ namespace {
 
 constexpr int64_t NA_MAX_SPAWNS = 1ll << 18;     // spawn records per call
 constexpr int64_t NA_MAX_LIST = 1ll << 20;       // list entries per call
-constexpr int64_t NA_RTILES = NA_MAX_SPAWNS / RX_TILE + 2;
+constexpr int64_t NA_RTILES = NA_MAX_SPAWNS / RX_TILE_MIN + 2;
 constexpr int64_t NA_MTILES = (NA_MAX_LIST + NA_MAX_SPAWNS) / MG_TILE + 3;
 
 struct NoAllocScratch {
@@ -445,14 +453,14 @@ int noalloc_setup(int dev) {
         cudaGetLastError();
         return DDQMC_ERR_CUDA;
     }
-    if (cudaFuncSetAttribute(k_radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) != cudaSuccess ||
-        cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_radix_pass<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_merge<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) != cudaSuccess) {
         cudaGetLastError();
         return DDQMC_ERR_CUDA;
     }
-    g_na_grid[dev][0] = occupancy_grid((const void *)k_radix_pass, RX_TPB, RX_SMEM, sms);
+    g_na_grid[dev][0] = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
     g_na_grid[dev][1] = 4 * sms;
-    g_na_grid[dev][2] = occupancy_grid((const void *)k_merge, MG_TPB, MG_SMEM, sms);
+    g_na_grid[dev][2] = occupancy_grid((const void *)k_merge<Rec>, MG_TPB, MG_SMEM, sms);
     g_na_ptr[dev] = (NoAllocScratch *)ptr;
     return DDQMC_OK;
 }
@@ -514,7 +522,7 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
         }
         r->own_stream = true;
     }
-    const int64_t rtiles = rcap / RX_TILE + 2;
+    const int64_t rtiles = rcap / RX_TILE_MIN + 2;
     const int64_t mtiles = (mcap + rcap) / MG_TILE + 2;
     rc = DDQMC_OK;
     rc |= dalloc(&r->dP, 1);
@@ -532,13 +540,24 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device);
     if (sms < 1) sms = 1;
-    bool ok = cudaFuncSetAttribute(k_spawn_death, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_radix_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
+    r->packed = 2 * r->hp.N <= 32;
+    bool ok = cudaFuncSetAttribute(k_spawn_death<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_spawn_death<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_radix_pass<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_radix_pass<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RXP_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_merge<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_merge<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
-    r->g_spawn = occupancy_grid((const void *)k_spawn_death, SP_TPB, SP_SMEM, sms);
-    r->g_radix = occupancy_grid((const void *)k_radix_pass, RX_TPB, RX_SMEM, sms);
-    r->g_merge = occupancy_grid((const void *)k_merge, MG_TPB, MG_SMEM, sms);
+    if (r->packed) {
+        r->g_spawn = occupancy_grid((const void *)k_spawn_death<uint64_t>, SP_TPB, SP_SMEM, sms);
+        r->g_radix = occupancy_grid((const void *)k_radix_pass<uint64_t>, RX_TPB, RXP_SMEM, sms);
+        r->g_merge = occupancy_grid((const void *)k_merge<uint64_t>, MG_TPB, MG_SMEM, sms);
+    } else {
+        r->g_spawn = occupancy_grid((const void *)k_spawn_death<Rec>, SP_TPB, SP_SMEM, sms);
+        r->g_radix = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
+        r->g_merge = occupancy_grid((const void *)k_merge<Rec>, MG_TPB, MG_SMEM, sms);
+    }
+    r->g_radix_wide = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
     r->g_part = 4 * sms;
     // initial state
     DevState hs;
@@ -891,16 +910,17 @@ int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_
     }
     const Rec *list = (const Rec *)d_list;
     const Rec *sp = (const Rec *)d_spawns;
-    k_digit_histogram<<<r->g_part, RX_TPB, 0, r->stream>>>(sp, r->dAnn, P.npass);
+    k_digit_histogram<Rec><<<r->g_part, RX_TPB, 0, r->stream>>>(sp, r->dAnn, P.npass);
     const Rec *src = sp;
     for (int p = 0; p < P.npass; ++p) {
         Rec *dst = r->Sp[p & 1];
-        k_radix_pass<<<r->g_radix, RX_TPB, RX_SMEM, r->stream>>>(src, dst, r->dAnn, r->lb_radix, p, 8 * p, r->rcap);
+        k_radix_pass<Rec><<<r->g_radix_wide, RX_TPB, RX_SMEM, r->stream>>>(src, dst, r->dAnn, r->lb_radix, p, 8 * p,
+                                                                          r->rcap);
         src = dst;
     }
-    k_merge_partition<<<r->g_part, 256, 0, r->stream>>>(list, src, r->dAnn, r->splits, r->rcap);
-    k_merge<<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, list, src, (Rec *)d_out, r->dAnn, r->splits,
-                                                        r->lb_merge, r->rcap, out_cap);
+    k_merge_partition<Rec><<<r->g_part, 256, 0, r->stream>>>(list, src, r->dAnn, r->splits, r->rcap);
+    k_merge<Rec><<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, list, src, (Rec *)d_out, r->dAnn, r->splits,
+                                                             r->lb_merge, r->rcap, out_cap);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&hs, r->dAnn, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
@@ -945,16 +965,16 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
     if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
     const Rec *list = (const Rec *)d_list;
     const Rec *src = (const Rec *)d_spawns;
-    k_digit_histogram<<<g_na_grid[dev][1], RX_TPB, 0, stream>>>(src, &sc->st, P.npass);
+    k_digit_histogram<Rec><<<g_na_grid[dev][1], RX_TPB, 0, stream>>>(src, &sc->st, P.npass);
     for (int p = 0; p < P.npass; ++p) {
         Rec *dst = sc->buf[p & 1];
-        k_radix_pass<<<g_na_grid[dev][0], RX_TPB, RX_SMEM, stream>>>(src, dst, &sc->st, sc->lb_radix, p, 8 * p,
-                                                                      NA_MAX_SPAWNS);
+        k_radix_pass<Rec><<<g_na_grid[dev][0], RX_TPB, RX_SMEM, stream>>>(src, dst, &sc->st, sc->lb_radix, p, 8 * p,
+                                                                           NA_MAX_SPAWNS);
         src = dst;
     }
-    k_merge_partition<<<g_na_grid[dev][1], 256, 0, stream>>>(list, src, &sc->st, sc->splits, NA_MAX_SPAWNS);
-    k_merge<<<g_na_grid[dev][2], MG_TPB, MG_SMEM, stream>>>(&sc->P, list, src, (Rec *)d_out, &sc->st, sc->splits,
-                                                            sc->lb_merge, NA_MAX_SPAWNS, out_cap);
+    k_merge_partition<Rec><<<g_na_grid[dev][1], 256, 0, stream>>>(list, src, &sc->st, sc->splits, NA_MAX_SPAWNS);
+    k_merge<Rec><<<g_na_grid[dev][2], MG_TPB, MG_SMEM, stream>>>(&sc->P, list, src, (Rec *)d_out, &sc->st, sc->splits,
+                                                                 sc->lb_merge, NA_MAX_SPAWNS, out_cap);
     int64_t mo = 0;
     uint32_t status = 0;
     if (cudaGetLastError() != cudaSuccess ||

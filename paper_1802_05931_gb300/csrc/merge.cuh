@@ -10,34 +10,40 @@
 // and past the tile, when the run continues) under the initiator rule:
 // records whose parent was not an initiator count only when the configuration
 // is occupied in L_t or diagonal.  Non-zero sums are compacted into L_{t+1}
-// in order: a block scan gives offsets inside the tile and a decoupled
-// look-back over earlier tiles gives the tile's output offset.  Every kept
-// entry is added to the integer estimator numerators on the way out.
+// in order: a block scan gives offsets inside the tile and a warp-parallel
+// decoupled look-back over earlier tiles gives the tile's output offset.
+// Every kept entry is added to the integer estimator numerators on the way
+// out.  Keys and populations sit in separate shared arrays and every thread
+// merges an odd number of positions, so the threads' merge cursors spread
+// over the shared-memory banks.
 #pragma once
 
 #include "common.cuh"
+#include "radix.cuh"
 
 namespace ddq {
 
 constexpr int MG_TPB = 256;
 constexpr int MG_WARPS = MG_TPB / 32;
-constexpr int MG_IPT = 8;
+constexpr int MG_IPT = 7;
 constexpr int MG_TILE = MG_TPB * MG_IPT;
 
 // merge-path split of output diagonal `diag`: number of L elements among the
 // first `diag` merged elements (L before S on equal keys)
-__device__ __forceinline__ int64_t merge_split(const Rec *L, int64_t M, const Rec *S, int64_t R, int64_t diag) {
+template <typename T>
+__device__ __forceinline__ int64_t merge_split(const Rec *L, int64_t M, const T *S, int64_t R, int64_t diag) {
     int64_t lo = diag > R ? diag - R : 0;
     int64_t hi = diag < M ? diag : M;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if (L[mid].key <= (S[diag - 1 - mid].key & KEY_MASK)) lo = mid + 1;
+        if (L[mid].key <= RecTraits<T>::key(S[diag - 1 - mid])) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
-__global__ void k_merge_partition(const Rec *__restrict__ L, const Rec *__restrict__ S, DevState *__restrict__ st,
+template <typename T>
+__global__ void k_merge_partition(const Rec *__restrict__ L, const T *__restrict__ S, DevState *__restrict__ st,
                                   int64_t *__restrict__ splits, int64_t rcap) {
     if (st->status) return;
     const int64_t M = st->M;
@@ -53,7 +59,8 @@ __global__ void k_merge_partition(const Rec *__restrict__ L, const Rec *__restri
 }
 
 struct MergeShared {
-    Rec buf[MG_TILE];                 // L part then S part of the tile; later the output staging
+    uint64_t key[MG_TILE];            // L keys, then S keys with the flag bit; later the output keys
+    int2 val[MG_TILE];                // (re, im) of the same elements; later the output populations
     unsigned long long est[NOBS_MAX];
     uint64_t bond_m[MAXB];
     int8_t bond_a[MAXB], bond_b[MAXB];
@@ -93,10 +100,18 @@ __device__ __forceinline__ void add_estimators(MergeShared &s, const RunParams &
     }
 }
 
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+    return v;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(MG_TPB)
-k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const Rec *__restrict__ S,
+k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__restrict__ S,
         Rec *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
         uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
+    using TR = RecTraits<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MergeShared &s = *reinterpret_cast<MergeShared *>(smem_raw);
     const RunParams &P = *Pp;
@@ -136,7 +151,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const Rec *
                 int hp = 0;
                 if (s.a0 > 0) { pk = L[s.a0 - 1].key; hp = 1; }
                 if (b0 > 0) {
-                    const uint64_t k2 = S[b0 - 1].key & KEY_MASK;
+                    const uint64_t k2 = TR::key(S[b0 - 1]);
                     if (!hp || k2 > pk) pk = k2;
                     hp = 1;
                 }
@@ -152,23 +167,34 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const Rec *
         const int64_t a0 = s.a0, a1 = s.a1;
         const int64_t b0 = d0 - a0, b1 = d1 - a1;
         const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
-        // load the tile's L and S elements (S keys keep their flag)
-        for (int q = tid; q < na; q += MG_TPB) s.buf[q] = L[a0 + q];
-        for (int q = tid; q < nb; q += MG_TPB) s.buf[na + q] = S[b0 + q];
+        // load the tile's L and S elements (S keys keep their flag in bit 63)
+        for (int q = tid; q < na; q += MG_TPB) {
+            const Rec v = L[a0 + q];
+            s.key[q] = v.key;
+            s.val[q] = make_int2(v.re, v.im);
+        }
+        for (int q = tid; q < nb; q += MG_TPB) {
+            const T v = S[b0 + q];
+            s.key[na + q] = TR::key(v) | (TR::flag(v) ? FLAG_BIT : 0ull);
+            s.val[na + q] = make_int2(TR::re(v), TR::im(v));
+        }
         __syncthreads();
-        const Rec *sL = s.buf;
-        const Rec *sS = s.buf + na;
+        const uint64_t *kL = s.key;
+        const uint64_t *kS = s.key + na;
+        const int2 *vL = s.val;
+        const int2 *vS = s.val + na;
 
         // this thread's merge-path start inside the tile
         const int dloc = tid * MG_IPT;
-        Rec outv[MG_IPT];
+        uint64_t okey[MG_IPT];
+        int2 oval[MG_IPT];
         int nout = 0;
         if (dloc < na + nb) {
             int lo = dloc > nb ? dloc - nb : 0;
             int hi = dloc < na ? dloc : na;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (sL[mid].key <= (sS[dloc - 1 - mid].key & KEY_MASK)) lo = mid + 1;
+                if (kL[mid] <= (kS[dloc - 1 - mid] & KEY_MASK)) lo = mid + 1;
                 else hi = mid;
             }
             int ia = lo, ib = dloc - lo;
@@ -177,44 +203,53 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const Rec *
             bool hprev = false;
             if (dloc == 0) { prev = s.prev_key; hprev = s.has_prev != 0; }
             else {
-                if (ia > 0) { prev = sL[ia - 1].key; hprev = true; }
+                if (ia > 0) { prev = kL[ia - 1]; hprev = true; }
                 if (ib > 0) {
-                    const uint64_t k2 = sS[ib - 1].key & KEY_MASK;
+                    const uint64_t k2 = kS[ib - 1] & KEY_MASK;
                     if (!hprev || k2 > prev) prev = k2;
                     hprev = true;
                 }
             }
             const int dend = (dloc + MG_IPT < na + nb) ? dloc + MG_IPT : na + nb;
+#pragma unroll 1
             for (int dpos = dloc; dpos < dend; ++dpos) {
                 bool fromL;
                 if (ia >= na) fromL = false;
                 else if (ib >= nb) fromL = true;
-                else fromL = sL[ia].key <= (sS[ib].key & KEY_MASK);
-                const uint64_t key = fromL ? sL[ia].key : (sS[ib].key & KEY_MASK);
+                else fromL = kL[ia] <= (kS[ib] & KEY_MASK);
+                const uint64_t key = fromL ? kL[ia] : (kS[ib] & KEY_MASK);
                 const bool head = !hprev || key != prev;
                 prev = key;
                 hprev = true;
                 if (head) {
                     int64_t sre = 0, sim = 0;
-                    const bool occupied = fromL;
-                    if (fromL) { sre = sL[ia].re; sim = sL[ia].im; }
-                    const bool open = occupied || no_init || ((key & nmask) == (key >> N));
+                    if (fromL) { sre = vL[ia].x; sim = vL[ia].y; }
+                    const bool open = fromL || no_init || ((key & nmask) == (key >> N));
                     // walk the spawn records of this key (may run past the tile)
                     int64_t q = ib;
                     for (;;) {
-                        Rec v;
-                        if (q < nb) v = sS[q];
-                        else if (b0 + q < R) v = S[b0 + q];
-                        else break;
-                        if ((v.key & KEY_MASK) != key) break;
-                        if (open || (v.key & FLAG_BIT)) { sre += v.re; sim += v.im; }
+                        uint64_t kk;
+                        int32_t vr, vi;
+                        if (q < nb) {
+                            kk = kS[q];
+                            vr = vS[q].x;
+                            vi = vS[q].y;
+                        } else if (b0 + q < R) {
+                            const T g = S[b0 + q];
+                            kk = TR::key(g) | (TR::flag(g) ? FLAG_BIT : 0ull);
+                            vr = TR::re(g);
+                            vi = TR::im(g);
+                        } else {
+                            break;
+                        }
+                        if ((kk & KEY_MASK) != key) break;
+                        if (open || (kk & FLAG_BIT)) { sre += vr; sim += vi; }
                         ++q;
                     }
                     if (sre != 0 || sim != 0) {
                         if (iabs64(sre) > 2147483647ll || iabs64(sim) > 2147483647ll) local_status |= ST_OVERFLOW;
-                        outv[nout].key = key;
-                        outv[nout].re = (int32_t)sre;
-                        outv[nout].im = (int32_t)sim;
+                        okey[nout] = key;
+                        oval[nout] = make_int2((int32_t)sre, (int32_t)sim);
                         ++nout;
                     }
                 }
@@ -228,7 +263,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const Rec *
             const int y = __shfl_up_sync(0xFFFFFFFFu, x, off);
             if (lane >= off) x += y;
         }
-        __syncthreads();                 // everyone is done reading s.buf
+        __syncthreads();                 // everyone is done reading the tile
         if (lane == 31) s.scan_tmp[warp] = (uint32_t)x;
         __syncthreads();
         uint32_t pre = 0, total = 0;
@@ -238,23 +273,34 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const Rec *
             total += v;
         }
         const uint32_t my_off = pre + (uint32_t)(x - nout);
-        for (int q = 0; q < nout; ++q) s.buf[my_off + q] = outv[q];
-        if (tid == 0) {
+        for (int q = 0; q < nout; ++q) {
+            s.key[my_off + q] = okey[q];
+            s.val[my_off + q] = oval[q];
+        }
+        // output offset of the tile: warp-parallel decoupled look-back
+        if (warp == 0) {
             uint64_t *myw = lookback + tile;
+            if (lane == 0) lb_store(myw, lb_pack(epoch, tile == 0 ? LB_INC : LB_AGG, total));
             uint64_t excl = 0;
-            if (tile == 0) {
-                lb_store(myw, lb_pack(epoch, LB_INC, total));
-            } else {
-                lb_store(myw, lb_pack(epoch, LB_AGG, total));
-                for (int64_t jt = tile - 1; jt >= 0; --jt) {
-                    const uint64_t w = lb_wait(lookback + jt, epoch, &st->status);
-                    excl += (uint32_t)w;
-                    if (((w >> 32) & 3ull) != LB_AGG) break;
+            if (tile > 0) {
+                for (int64_t jt = tile - 1;; jt -= 32) {
+                    const int64_t jj = jt - lane;
+                    const uint64_t w = jj >= 0 ? lb_wait(lookback + jj, epoch, &st->status)
+                                               : lb_pack(epoch, LB_INC, 0u);
+                    const unsigned inc = __ballot_sync(0xFFFFFFFFu, ((w >> 32) & 3ull) != LB_AGG);
+                    if (inc) {
+                        const int first = __ffs(inc) - 1;
+                        excl += warp_sum_u64(lane <= first ? (uint64_t)(uint32_t)w : 0ull);
+                        break;
+                    }
+                    excl += warp_sum_u64((uint64_t)(uint32_t)w);
                 }
-                lb_store(myw, lb_pack(epoch, LB_INC, (uint32_t)(excl + total)));
+                if (lane == 0) lb_store(myw, lb_pack(epoch, LB_INC, (uint32_t)(excl + total)));
             }
-            s.out_base = (int64_t)excl;
-            if (tile == ntiles - 1) st->M_next = (int64_t)(excl + total);
+            if (lane == 0) {
+                s.out_base = (int64_t)excl;
+                if (tile == ntiles - 1) st->M_next = (int64_t)(excl + total);
+            }
         }
         __syncthreads();
         const int64_t ob = s.out_base;
@@ -262,7 +308,10 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const Rec *
             if (tid == 0) local_status |= ST_CAPACITY | ST_CAP_LIST;
         } else {
             for (uint32_t q = tid; q < total; q += MG_TPB) {
-                const Rec v = s.buf[q];
+                Rec v;
+                v.key = s.key[q];
+                v.re = s.val[q].x;
+                v.im = s.val[q].y;
                 out[ob + q] = v;
                 my_w += iabs64(v.re) + iabs64(v.im);
                 my_m += 1;

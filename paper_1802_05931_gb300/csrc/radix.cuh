@@ -9,20 +9,53 @@
 // resolves its global per-digit offsets by decoupled look-back over earlier
 // tiles (bounded waits), stages the tile in digit order in shared memory and
 // writes runs of equal digits to consecutive global addresses.  The initiator
-// flag (bit 63) is carried, never sorted.
+// flag is carried, never sorted.
+//
+// Two record layouts: 16-byte Rec (any key width), and 8-byte packed records
+// for keys of at most 32 bits (2N <= 32):
+//   bits 63..32 key, bit 31 initiator flag, bits 29..15 Delta im, 14..0 Delta re
+// (15-bit two's complement each), which halves the bytes every pass moves.
 #pragma once
 
 #include "common.cuh"
 
 namespace ddq {
 
+template <typename T> struct RecTraits;
+
+template <> struct RecTraits<Rec> {
+    static constexpr int IPT = 8;      // records per thread in a radix tile
+    __device__ __forceinline__ static uint64_t key(const Rec &r) { return r.key & KEY_MASK; }
+    __device__ __forceinline__ static bool flag(const Rec &r) { return (r.key & FLAG_BIT) != 0ull; }
+    __device__ __forceinline__ static int32_t re(const Rec &r) { return r.re; }
+    __device__ __forceinline__ static int32_t im(const Rec &r) { return r.im; }
+    __device__ __forceinline__ static Rec empty() { Rec r; r.key = 0; r.re = 0; r.im = 0; return r; }
+};
+
+constexpr int PK_LIM = 16383;          // largest |Delta| of one packed record
+
+template <> struct RecTraits<uint64_t> {
+    static constexpr int IPT = 16;
+    __device__ __forceinline__ static uint64_t key(uint64_t r) { return r >> 32; }
+    __device__ __forceinline__ static bool flag(uint64_t r) { return ((r >> 31) & 1ull) != 0ull; }
+    __device__ __forceinline__ static int32_t re(uint64_t r) { return ((int32_t)((uint32_t)r << 17)) >> 17; }
+    __device__ __forceinline__ static int32_t im(uint64_t r) { return ((int32_t)((uint32_t)(r >> 15) << 17)) >> 17; }
+    __device__ __forceinline__ static uint64_t empty() { return 0ull; }
+};
+
+// packed record; |re|, |im| <= PK_LIM
+__device__ __forceinline__ uint64_t pack_rec(uint64_t key, bool flag, int re, int im) {
+    return (key << 32) | (flag ? (1ull << 31) : 0ull) | ((uint64_t)((uint32_t)im & 0x7FFFu) << 15) |
+           (uint64_t)((uint32_t)re & 0x7FFFu);
+}
+
 constexpr int RX_TPB = 256;                  // one thread per digit value
 constexpr int RX_WARPS = RX_TPB / 32;
-constexpr int RX_IPT = 8;                    // records per thread
-constexpr int RX_TILE = RX_TPB * RX_IPT;     // 2048 records per tile
+constexpr int RX_TILE_MIN = RX_TPB * 8;      // smallest tile (sizes the look-back words)
 
+template <typename T>
 struct RadixShared {
-    Rec stage[RX_TILE];
+    T stage[RX_TPB * RecTraits<T>::IPT];
     uint32_t whist[RX_WARPS][256];
     uint32_t bucket[256];      // start of each digit's bucket in the output
     uint32_t dstart[256];      // start of each digit inside the staged tile
@@ -33,8 +66,9 @@ struct RadixShared {
 
 // Digit histograms of every pass over st->R records (used when the records do
 // not come from the spawn kernel, which counts them as it writes them).
+template <typename T>
 __global__ void __launch_bounds__(RX_TPB)
-k_digit_histogram(const Rec *__restrict__ in, DevState *__restrict__ st, int npass) {
+k_digit_histogram(const T *__restrict__ in, DevState *__restrict__ st, int npass) {
     __shared__ uint32_t h[MAXPASS][256];
     const int tid = threadIdx.x;
     if (block_stopped(st)) return;
@@ -42,7 +76,7 @@ k_digit_histogram(const Rec *__restrict__ in, DevState *__restrict__ st, int npa
     __syncthreads();
     const int64_t R = st->R;
     for (int64_t q = (int64_t)blockIdx.x * RX_TPB + tid; q < R; q += (int64_t)gridDim.x * RX_TPB) {
-        const uint64_t key = in[q].key & KEY_MASK;
+        const uint64_t key = RecTraits<T>::key(in[q]);
         for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 0xFFull], 1u);
     }
     __syncthreads();
@@ -50,16 +84,20 @@ k_digit_histogram(const Rec *__restrict__ in, DevState *__restrict__ st, int npa
         if ((&h[0][0])[q]) atomicAdd(&st->hist[q >> 8][q & 255], (&h[0][0])[q]);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(RX_TPB)
-k_radix_pass(const Rec *__restrict__ in, Rec *__restrict__ out, DevState *__restrict__ st,
+k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict__ st,
              uint64_t *__restrict__ lookback, int pass, int shift, int64_t cap) {
+    using TR = RecTraits<T>;
+    constexpr int IPT = TR::IPT;
+    constexpr int TILE = RX_TPB * IPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    RadixShared &s = *reinterpret_cast<RadixShared *>(smem_raw);
+    RadixShared<T> &s = *reinterpret_cast<RadixShared<T> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (block_stopped(st)) return;
     int64_t R = st->R;
     if (R > cap) R = cap;
-    const int64_t ntiles = (R + RX_TILE - 1) / RX_TILE;
+    const int64_t ntiles = (R + TILE - 1) / TILE;
     const uint32_t epoch = st->epoch + (uint32_t)pass;
 
     // exclusive scan of this pass's global histogram -> bucket starts
@@ -84,29 +122,29 @@ k_radix_pass(const Rec *__restrict__ in, Rec *__restrict__ out, DevState *__rest
         __syncthreads();
         const int64_t tile = s.tile;
         if (tile >= ntiles) break;
-        const int64_t t0 = tile * RX_TILE;
+        const int64_t t0 = tile * TILE;
         for (int q = tid; q < RX_WARPS * 256; q += RX_TPB) (&s.whist[0][0])[q] = 0u;
         __syncthreads();
 
-        // load: warp w owns records [t0 + w*32*IPT, +32*IPT), item i at + i*32 + lane
-        Rec r[RX_IPT];
-        uint32_t dg[RX_IPT];
-        uint32_t rk[RX_IPT];
-        const int64_t wbase = t0 + (int64_t)warp * 32 * RX_IPT;
+        // load: warp w owns records [t0 + w*32*IPT, +32*IPT), item q at + q*32 + lane
+        T r[IPT];
+        uint32_t dg[IPT];
+        uint32_t rk[IPT];
+        const int64_t wbase = t0 + (int64_t)warp * 32 * IPT;
 #pragma unroll
-        for (int q = 0; q < RX_IPT; ++q) {
+        for (int q = 0; q < IPT; ++q) {
             const int64_t idx = wbase + q * 32 + lane;
             if (idx < R) {
                 r[q] = in[idx];
-                dg[q] = (uint32_t)(((r[q].key & KEY_MASK) >> shift) & 0xFFull);
+                dg[q] = (uint32_t)((TR::key(r[q]) >> shift) & 0xFFull);
             } else {
-                r[q].key = 0; r[q].re = 0; r[q].im = 0;
+                r[q] = TR::empty();
                 dg[q] = 0x100u + lane;            // unique sentinel, never counted
             }
         }
         // stable warp multisplit rank
 #pragma unroll
-        for (int q = 0; q < RX_IPT; ++q) {
+        for (int q = 0; q < IPT; ++q) {
             const unsigned peers = __match_any_sync(0xFFFFFFFFu, dg[q]);
             const unsigned below = peers & ((1u << lane) - 1u);
             uint32_t base = 0;
@@ -154,7 +192,7 @@ k_radix_pass(const Rec *__restrict__ in, Rec *__restrict__ out, DevState *__rest
 
         // stage in digit order
 #pragma unroll
-        for (int q = 0; q < RX_IPT; ++q) {
+        for (int q = 0; q < IPT; ++q) {
             if (dg[q] < 256u) {
                 const uint32_t pos = s.dstart[dg[q]] + s.whist[warp][dg[q]] + rk[q];
                 s.stage[pos] = r[q];
@@ -162,10 +200,10 @@ k_radix_pass(const Rec *__restrict__ in, Rec *__restrict__ out, DevState *__rest
         }
         __syncthreads();
         int64_t nvalid = R - t0;
-        if (nvalid > RX_TILE) nvalid = RX_TILE;
+        if (nvalid > TILE) nvalid = TILE;
         for (int q = tid; q < nvalid; q += RX_TPB) {
-            const Rec v = s.stage[q];
-            const uint32_t d = (uint32_t)(((v.key & KEY_MASK) >> shift) & 0xFFull);
+            const T v = s.stage[q];
+            const uint32_t d = (uint32_t)((TR::key(v) >> shift) & 0xFFull);
             out[s.gbase[d] + q] = v;
         }
         __syncthreads();

@@ -11,31 +11,35 @@
 //
 // Moves, in order: ket bond flips (child (i ^ m_b, j), A = -i h_b(i)), bra
 // bond flips (child (i, j ^ m_b), A = +i h_b(j)), jumps (child (i - 2^k,
-// j - 2^k), A = gamma, needs spin k up on both sides).  Rates are fixed-point
-// integers (rate * 2^32, truncated), so the move selection is integer-only.
+// j - 2^k), A = gamma, needs spin k up on both sides).  Inside a bond-flip
+// segment the moves are grouped by g = 4*anti + class (anti-aligned bond in
+// the flipped word; importance class of the bond), groups in increasing g and
+// bonds in bond order inside a group.  Rates are fixed-point integers
+// (rate * 2^32, truncated), so the move selection is integer-only.
 //
 // Children follow Delta rho_child = A rho_parent (the four sign rules of
 // Sec. III.C); death / clone and the Re <-> Im transfer act on the parent's
 // own entry, which is updated in place.
 //
 // Two paths share the work of a chunk of 32 configurations per warp:
-//  * light configurations (few walkers): the walkers of the whole chunk are
-//    spread over the 32 lanes, so every lane does the same per-walker work.
-//    Rate totals and the move search use bond masks: with bit 2k the bond
-//    from site k to its right neighbour and bit 2k+1 the bond to the one
-//    below, bit order is move order, each bond's rate is a function of
-//    (anti-aligned, importance class), and the cumulative rate up to a bit
-//    position is a sum of popcounts times the six rates.  The selected move
-//    is found by binary search over the 64 bit positions.
+//  * light configurations (few walkers, every bond with the same rate
+//    table): the walkers of the whole chunk are spread over the 32 lanes, so
+//    every lane does the same per-walker work.  Bonds are bits of a mask
+//    (bit 2k the bond from site k to its right neighbour, 2k+1 the one
+//    below, which is bond order); a group is a mask, its rate total a popcount
+//    times the group's rate, and a draw is resolved in O(1): the group from
+//    eight running totals, the bond as the r-th set bit of the group's mask.
 //  * heavy configurations (many walkers, or rate tables that differ per
 //    bond): the whole warp on one configuration, with the cumulative rate
-//    table in shared memory and the children aggregated per move.
+//    table of the group-ordered moves in shared memory and the children
+//    aggregated per move.
 // Spawn records are appended through per-warp shared-memory staging
-// (coalesced 16-byte stores) and counted into the radix histograms of every
-// digit pass.
+// (coalesced stores) and counted into the radix histograms of every digit
+// pass.
 #pragma once
 
 #include "common.cuh"
+#include "radix.cuh"
 
 namespace ddq {
 
@@ -43,15 +47,17 @@ constexpr int SP_TPB = 256;
 constexpr int SP_WARPS = SP_TPB / 32;
 constexpr int SP_STAGE = 128;      // staged records per warp
 constexpr int SP_FLUSH = 32;       // flush threshold at warp-uniform points
-constexpr int SP_HEAVY = 48;       // configurations with more walkers use the warp-cooperative path
+constexpr int SP_HEAVY = 1024;     // configurations with more walkers use the warp-cooperative path
 
-// Parameters of one light configuration, staged for the lanes that run its walkers.
-struct LightEntry {
-    uint64_t Ai, Aj, C1, C2;   // anti-aligned (ket, bra) and importance-class bond masks
-    uint64_t T_ket, T_bra, T;  // rate totals: ket moves, bra moves, all moves
-    uint32_t i, j, natt;
-    int32_t re, im, nre;
-    int32_t cd, adz, sgn_d, init;
+// Parameters of the light configurations of one warp's chunk, one array per
+// field (lanes that read different configurations hit different banks).
+struct LightSoA {
+    uint64_t Ai[32], Aj[32], X1[32], X2[32];   // anti-aligned bond masks (ket, bra), importance-class masks
+    uint64_t Tket[32], Tbra[32], T[32];        // rate totals: ket moves, bra moves, all moves
+    uint64_t gk[32], gb[32];                   // bonds per group (8 bytes), ket and bra
+    uint32_t i[32], j[32], natt[32];
+    int32_t re[32], im[32], nre[32];
+    int32_t cd[32], adz[32], sgn_d[32], init[32];
 };
 
 struct SpawnShared {
@@ -59,7 +65,7 @@ struct SpawnShared {
     uint64_t bond_m[MAXB];
     uint64_t cross_frac[2 * MAXB + 1];
     uint64_t d_frac[2 * MAXN + 1];
-    uint64_t urate[2][3];
+    uint64_t urate8[8];
     uint32_t cross_int[2 * MAXB + 1];
     uint32_t d_int[2 * MAXN + 1];
     int32_t d_sgn[2 * MAXN + 1];
@@ -68,10 +74,11 @@ struct SpawnShared {
     uint32_t hist[MAXPASS][256];
     int32_t stage_n[SP_WARPS];
     Rec stage[SP_WARPS][SP_STAGE];
-    LightEntry le[SP_WARPS][32];
+    LightSoA le[SP_WARPS];
     int32_t incl[SP_WARPS][32];
     int32_t dre[SP_WARPS][32], dim[SP_WARPS][32];
     uint64_t cum[SP_WARPS][MAXK];
+    int16_t mv[SP_WARPS][MAXK];       // move index (ket b, bra B + b, jump 2B + k) of each table slot
     int32_t cnt_re[SP_WARPS][MAXK];
     int32_t cnt_im[SP_WARPS][MAXK];
 };
@@ -120,68 +127,74 @@ __device__ __forceinline__ uint64_t anti_mask(const SpawnCtx &c, uint32_t s) {
     return bond_mask((s ^ nb_right(c, s)) & c.ER, (s ^ nb_down(c, s)) & c.ED);
 }
 
-// cumulative rate of the bonds selected by `low` (a prefix of bit positions)
-__device__ __forceinline__ uint64_t seg_cum(uint64_t A, uint64_t E, uint64_t C1, uint64_t C2,
-                                            const uint64_t (&R)[2][3], uint64_t low) {
-    const uint64_t e = E & low, a = A & low, c1 = C1 & low, c2 = C2 & low;
-    const uint64_t n = e & ~a, c0 = ~(c1 | c2);
-    return R[1][0] * (uint64_t)__popcll(a & c0) + R[1][1] * (uint64_t)__popcll(a & c1) +
-           R[1][2] * (uint64_t)__popcll(a & c2) + R[0][0] * (uint64_t)__popcll(n & c0) +
-           R[0][1] * (uint64_t)__popcll(n & c1) + R[0][2] * (uint64_t)__popcll(n & c2);
-}
-
-// largest bit position p with seg_cum(prefix p) <= v (the selected bond), given v < segment total
-__device__ __forceinline__ int seg_search(uint64_t A, uint64_t E, uint64_t C1, uint64_t C2,
-                                          const uint64_t (&R)[2][3], uint64_t v) {
-    int lo = 0, hi = 64;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (seg_cum(A, E, C1, C2, R, (1ull << mid) - 1ull) <= v) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// importance classes of every bond of configuration (i, j): C1, C2 bond masks
-__device__ __forceinline__ void class_masks(const SpawnCtx &c, uint32_t i, uint32_t j, uint64_t &C1,
-                                            uint64_t &C2) {
+// importance-class masks of configuration (i, j): for the site-product guide
+// X1 / X2 = bonds whose first / second site differs between i and j; for the
+// uniform guide X1 = every bond when i == j, X2 = the bond whose flip makes
+// the child diagonal
+__device__ __forceinline__ void class_masks(const SpawnCtx &c, uint32_t i, uint32_t j, uint64_t &X1,
+                                            uint64_t &X2) {
     const uint32_t d = i ^ j;
-    C1 = 0;
-    C2 = 0;
+    X1 = 0;
+    X2 = 0;
     if (c.gk == 1) {
-        if (d == 0) { C1 = c.Emorton; return; }
+        if (d == 0) { X1 = c.Emorton; return; }
         if (__popc(d) != 2) return;
         const int a = __ffs(d) - 1, b = 31 - __clz(d);
         const SpawnShared &s = *c.sh;
-        // the bond whose two sites are exactly a and b (child diagonal)
-        if ((c.ER >> a & 1u) && s.rn[a] == b) C2 = 1ull << (2 * a);
-        else if ((c.ED >> a & 1u) && s.dn[a] == b) C2 = 1ull << (2 * a + 1);
-        else if ((c.ER >> b & 1u) && s.rn[b] == a) C2 = 1ull << (2 * b);
-        else if ((c.ED >> b & 1u) && s.dn[b] == a) C2 = 1ull << (2 * b + 1);
+        if ((c.ER >> a & 1u) && s.rn[a] == b) X2 = 1ull << (2 * a);
+        else if ((c.ED >> a & 1u) && s.dn[a] == b) X2 = 1ull << (2 * a + 1);
+        else if ((c.ER >> b & 1u) && s.rn[b] == a) X2 = 1ull << (2 * b);
+        else if ((c.ED >> b & 1u) && s.dn[b] == a) X2 = 1ull << (2 * b + 1);
     } else if (c.gk == 2) {
-        // class = number of the bond's two sites on which i and j differ
-        const uint32_t ar = d & c.ER, br = nb_right(c, d) & c.ER;
-        const uint32_t ad = d & c.ED, bd = nb_down(c, d) & c.ED;
-        C1 = bond_mask(ar ^ br, ad ^ bd);
-        C2 = bond_mask(ar & br, ad & bd);
+        X1 = bond_mask(d & c.ER, d & c.ED);
+        X2 = bond_mask(nb_right(c, d) & c.ER, nb_down(c, d) & c.ED);
     }
+}
+
+// bonds of group g = 4*anti + class, given the anti mask A of the flipped word
+__device__ __forceinline__ uint64_t group_mask(const SpawnCtx &c, uint64_t A, uint64_t X1, uint64_t X2, int g) {
+    const int cls = g & 3;
+    uint64_t cm;
+    if (c.gk == 2) cm = ((cls & 2) ? X1 : ~X1) & ((cls & 1) ? X2 : ~X2);
+    else if (c.gk == 1) cm = cls == 0 ? ~(X1 | X2) : (cls == 1 ? X1 : (cls == 2 ? X2 : 0ull));
+    else cm = cls == 0 ? ~0ull : 0ull;
+    return ((g & 4) ? A : ~A) & cm & c.Emorton;
+}
+
+// position of the r-th set bit (r from 0) of m, given r < popcount(m)
+__device__ __forceinline__ int select_bit(uint64_t m, uint32_t r) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 32; w >= 1; w >>= 1) {
+        const uint32_t c = (uint32_t)__popcll((m >> pos) & ((1ull << w) - 1ull));
+        if (r >= c) { r -= c; pos += w; }
+    }
+    return pos;
+}
+
+// floor(v / q) for a quotient below 64, by integer bisection (no division:
+// the FP64 and 64-bit integer division paths are slow on this GPU)
+__device__ __forceinline__ uint32_t small_quotient(uint64_t v, uint64_t q) {
+    uint32_t r = 0;
+#pragma unroll
+    for (uint32_t b = 32; b >= 1; b >>= 1)
+        if ((uint64_t)(r + b) * q <= v) r += b;
+    return r;
+}
+
+// bond bit of the draw v (0 <= v < segment total) in a segment with group counts cnt
+__device__ __forceinline__ int seg_select(const SpawnCtx &c, const uint64_t *rate8, uint64_t cnt,
+                                          uint64_t A, uint64_t X1, uint64_t X2, uint64_t v) {
+    int g = 0;
+    for (; g < 7; ++g) {
+        const uint64_t w = rate8[g] * ((cnt >> (8 * g)) & 0xFFull);
+        if (v < w) break;
+        v -= w;
+    }
+    return select_bit(group_mask(c, A, X1, X2, g), small_quotient(v, rate8[g]));
 }
 
 // ---- per-move tables (heavy path) -------------------------------------------
-
-// Rate of move m of configuration (i, j).
-__device__ __forceinline__ uint64_t move_rate(const SpawnCtx &c, uint64_t i, uint64_t j, int m) {
-    const SpawnShared &s = *c.sh;
-    if (m < 2 * c.B) {
-        const int b = m < c.B ? m : m - c.B;
-        const uint64_t w = m < c.B ? i : j;
-        const int a0 = s.bond_a[b], a1 = s.bond_b[b];
-        const int anti = (int)(((w >> a0) ^ (w >> a1)) & 1ull);
-        return s.rate_q[b][anti][imp_class(c.gk, i ^ j, s.bond_m[b], a0, a1)];
-    }
-    const int k = m - 2 * c.B;
-    return (((i & j) >> k) & 1ull) ? c.jump_q : 0ull;
-}
 
 // Child key of move m of configuration (i, j) and the sign factor g of the
 // move: a real parent of sign s makes an imaginary child of sign s*g and an
@@ -210,31 +223,72 @@ __device__ __forceinline__ void move_key(const SpawnCtx &c, const RunParams &P, 
 
 // ---- record output ----------------------------------------------------------
 
+template <typename T> __device__ __forceinline__ T make_spawn(uint64_t key, bool flag, int re, int im);
+template <> __device__ __forceinline__ Rec make_spawn<Rec>(uint64_t key, bool flag, int re, int im) {
+    Rec r;
+    r.key = key | (flag ? FLAG_BIT : 0ull);
+    r.re = re;
+    r.im = im;
+    return r;
+}
+template <> __device__ __forceinline__ uint64_t make_spawn<uint64_t>(uint64_t key, bool flag, int re, int im) {
+    return pack_rec(key, flag, re, im);
+}
+
 __device__ __forceinline__ void count_digits(SpawnShared &s, uint64_t key, int npass) {
     for (int p = 0; p < npass; ++p) atomicAdd(&s.hist[p][(key >> (8 * p)) & 0xFFull], 1u);
 }
 
 // Append one record from a (possibly divergent) lane.
-__device__ __forceinline__ void emit(SpawnShared &s, int warp, const Rec &r, Rec *out, int64_t cap,
+template <typename T>
+__device__ __forceinline__ void emit(SpawnShared &s, int warp, const T &r, T *out, int64_t cap,
                                      DevState *st, int npass) {
-    const int pos = atomicAdd(&s.stage_n[warp], 1);
+    T *stage = reinterpret_cast<T *>(&s.stage[warp][0]);
+    // one staging-counter update for all the lanes that emit together
+    const unsigned am = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(am) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&s.stage_n[warp], __popc(am));
+    base = __shfl_sync(am, base, leader);
+    const int pos = base + __popc(am & ((1u << lane) - 1u));
     if (pos < SP_STAGE) {
-        s.stage[warp][pos] = r;
+        stage[pos] = r;
     } else {
         const unsigned long long idx = atomicAdd((unsigned long long *)&st->R, 1ull);
         if ((int64_t)idx < cap) {
             out[idx] = r;
-            count_digits(s, r.key & KEY_MASK, npass);
+            count_digits(s, RecTraits<T>::key(r), npass);
         } else {
             atomicOr(&st->status, ST_CAPACITY | ST_CAP_SPAWN);
         }
     }
 }
 
+// Append an aggregated child (any int32 counts): packed records carry at most
+// PK_LIM walkers per part, so large counts become several records.
+template <typename T>
+__device__ __forceinline__ void emit_counts(SpawnShared &s, int warp, uint64_t key, bool flag, int cre, int cim,
+                                            T *out, int64_t cap, DevState *st, int npass) {
+    if constexpr (sizeof(T) == sizeof(Rec)) {
+        emit(s, warp, make_spawn<T>(key, flag, cre, cim), out, cap, st, npass);
+    } else {
+        while (cre != 0 || cim != 0) {
+            const int pr = cre > PK_LIM ? PK_LIM : (cre < -PK_LIM ? -PK_LIM : cre);
+            const int pi = cim > PK_LIM ? PK_LIM : (cim < -PK_LIM ? -PK_LIM : cim);
+            emit(s, warp, make_spawn<T>(key, flag, pr, pi), out, cap, st, npass);
+            cre -= pr;
+            cim -= pi;
+        }
+    }
+}
+
 // Warp-uniform flush of the warp's staged records.
-__device__ __forceinline__ void flush(SpawnShared &s, int warp, int lane, Rec *out, int64_t cap,
+template <typename T>
+__device__ __forceinline__ void flush(SpawnShared &s, int warp, int lane, T *out, int64_t cap,
                                       DevState *st, int npass, int min_n) {
     __syncwarp();
+    const T *stage = reinterpret_cast<const T *>(&s.stage[warp][0]);
     int n = s.stage_n[warp];
     if (n > SP_STAGE) n = SP_STAGE;
     if (n >= min_n && n > 0) {
@@ -242,10 +296,10 @@ __device__ __forceinline__ void flush(SpawnShared &s, int warp, int lane, Rec *o
         if (lane == 0) base = atomicAdd((unsigned long long *)&st->R, (unsigned long long)n);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         for (int k = lane; k < n; k += 32) {
-            const Rec r = s.stage[warp][k];
+            const T r = stage[k];
             if ((int64_t)(base + k) < cap) {
                 out[base + k] = r;
-                count_digits(s, r.key & KEY_MASK, npass);
+                count_digits(s, RecTraits<T>::key(r), npass);
             }
         }
         if (lane == 0 && (int64_t)(base + n) > cap) atomicOr(&st->status, ST_CAPACITY | ST_CAP_SPAWN);
@@ -273,9 +327,10 @@ __device__ __forceinline__ uint32_t attempt_word(uint4 x0, uint4 &xb, uint32_t &
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(SP_TPB)
 k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *__restrict__ L,
-              Rec *__restrict__ out, int64_t cap) {
+              T *__restrict__ out, int64_t cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpawnShared &s = *reinterpret_cast<SpawnShared *>(smem_raw);
     const RunParams &P = *Pp;
@@ -290,7 +345,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
         s.bond_b[q] = (int8_t)P.bond_b[q];
     }
     for (int q = tid; q < N; q += SP_TPB) { s.rn[q] = P.rn[q]; s.dn[q] = P.dn[q]; }
-    if (tid < 6) (&s.urate[0][0])[tid] = (&P.urate[0][0])[tid];
+    if (tid < 8) s.urate8[tid] = P.urate8[tid];
     for (int q = tid; q <= 2 * B; q += SP_TPB) { s.cross_int[q] = P.cross_int[q]; s.cross_frac[q] = P.cross_frac[q]; }
     for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_frac[q] = st->d_frac[q]; s.d_sgn[q] = st->d_sgn[q]; }
     for (int q = tid; q < MAXPASS * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
@@ -300,7 +355,6 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
     SpawnCtx c;
     c.sh = &s; c.N = N; c.B = B; c.K = K; c.gk = P.guide_kind; c.jump_q = P.jump_q;
     c.ER = P.ER; c.ED = P.ED; c.LC = P.LC; c.LR = P.LR; c.Lx = P.Lx; c.shD = P.shD; c.Emorton = P.Emorton;
-    const uint64_t(&R)[2][3] = s.urate;
     const bool uniform = P.uniform != 0;
     const int64_t M = st->M;
     const uint64_t t = (uint64_t)st->t;
@@ -327,27 +381,43 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
         // ---- light configurations: per-configuration setup, one lane each ----
         int nl = 0;
         if (light) {
-            LightEntry q;
+            LightSoA &q = s.le[warp];
             const uint32_t i32 = (uint32_t)i, j32 = (uint32_t)j;
-            q.Ai = anti_mask(c, i32);
-            q.Aj = anti_mask(c, j32);
-            class_masks(c, i32, j32, q.C1, q.C2);
-            q.T_ket = seg_cum(q.Ai, c.Emorton, q.C1, q.C2, R, ~0ull);
-            q.T_bra = seg_cum(q.Aj, c.Emorton, q.C1, q.C2, R, ~0ull);
-            q.T = q.T_ket + q.T_bra + (uint64_t)__popc(i32 & j32) * c.jump_q;
-            uint64_t natt = (q.T + 0xFFFFFFFFull) >> 32;
-            q.natt = natt == 0 ? 1u : (uint32_t)natt;
-            q.i = i32;
-            q.j = j32;
-            q.re = rec.re;
-            q.im = rec.im;
-            q.nre = (int32_t)nre;
-            q.cd = __popc(i32) + __popc(j32);
-            const int dz = 2 * (__popcll(q.Aj) - __popcll(q.Ai));     // zsum(i) - zsum(j)
-            q.adz = dz < 0 ? -dz : dz;
-            q.sgn_d = (dz == 0) ? 0 : -sgn_jz * (dz > 0 ? 1 : -1);
-            q.init = init ? 1 : 0;
-            s.le[warp][lane] = q;
+            const uint64_t Ai = anti_mask(c, i32), Aj = anti_mask(c, j32);
+            uint64_t X1, X2;
+            class_masks(c, i32, j32, X1, X2);
+            uint64_t Tket = 0, Tbra = 0, gkp = 0, gbp = 0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const int ck = __popcll(group_mask(c, Ai, X1, X2, g));
+                const int cb = __popcll(group_mask(c, Aj, X1, X2, g));
+                gkp |= (uint64_t)ck << (8 * g);
+                gbp |= (uint64_t)cb << (8 * g);
+                Tket += s.urate8[g] * (uint64_t)ck;
+                Tbra += s.urate8[g] * (uint64_t)cb;
+            }
+            const uint64_t Tall = Tket + Tbra + (uint64_t)__popc(i32 & j32) * c.jump_q;
+            const uint64_t natt = (Tall + 0xFFFFFFFFull) >> 32;
+            q.Ai[lane] = Ai;
+            q.Aj[lane] = Aj;
+            q.X1[lane] = X1;
+            q.X2[lane] = X2;
+            q.Tket[lane] = Tket;
+            q.Tbra[lane] = Tbra;
+            q.T[lane] = Tall;
+            q.gk[lane] = gkp;
+            q.gb[lane] = gbp;
+            q.natt[lane] = natt == 0 ? 1u : (uint32_t)natt;
+            q.i[lane] = i32;
+            q.j[lane] = j32;
+            q.re[lane] = rec.re;
+            q.im[lane] = rec.im;
+            q.nre[lane] = (int32_t)nre;
+            q.cd[lane] = __popc(i32) + __popc(j32);
+            const int dz = 2 * (__popcll(Aj) - __popcll(Ai));     // zsum(i) - zsum(j)
+            q.adz[lane] = dz < 0 ? -dz : dz;
+            q.sgn_d[lane] = (dz == 0) ? 0 : -sgn_jz * (dz > 0 ? 1 : -1);
+            q.init[lane] = init ? 1 : 0;
             nl = (int)nw;
         }
         s.dre[warp][lane] = 0;
@@ -372,17 +442,21 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                     if (s.incl[warp][mid] > g) hi = mid; else lo = mid + 1;
                 }
                 const int owner = lo;
-                const LightEntry &q = s.le[warp][owner];
+                const LightSoA &q = s.le[warp];
+                const int o = owner;
+                const uint32_t qi = q.i[o], qj = q.j[o];
+                const int nre_o = q.nre[o];
                 const int local = g - (owner ? s.incl[warp][owner - 1] : 0);
-                const int part = local < q.nre ? 0 : 1;
-                const uint32_t w = (uint32_t)(part ? local - q.nre : local);
-                const int sig = (part ? q.im : q.re) < 0 ? -1 : 1;
-                const uint4 ctr = make_uint4(q.i, q.j, w, (uint32_t)part << 16);
+                const int part = local < nre_o ? 0 : 1;
+                const uint32_t w = (uint32_t)(part ? local - nre_o : local);
+                const int sig = (part ? q.im[o] : q.re[o]) < 0 ? -1 : 1;
+                const uint4 ctr = make_uint4(qi, qj, w, (uint32_t)part << 16);
                 const uint4 x = philox4x32_10(ctr, k0, k1);
-                const int cnt = (int)s.d_int[q.cd] + ((uint64_t)x.y < s.d_frac[q.cd] ? 1 : 0);
-                const int cc = (int)s.cross_int[q.adz] + ((uint64_t)x.z < s.cross_frac[q.adz] ? 1 : 0);
-                const int ddeath = -s.d_sgn[q.cd] * sig * cnt;
-                const int dcross = sig * q.sgn_d * cc;
+                const int cd = q.cd[o], adz = q.adz[o];
+                const int cnt = (int)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
+                const int cc = (int)s.cross_int[adz] + ((uint64_t)x.z < s.cross_frac[adz] ? 1 : 0);
+                const int ddeath = -s.d_sgn[cd] * sig * cnt;
+                const int dcross = sig * q.sgn_d[o] * cc;
                 if (part == 0) {
                     if (ddeath) atomicAdd(&s.dre[warp][owner], ddeath);
                     if (dcross) atomicAdd(&s.dim[warp][owner], dcross);
@@ -392,17 +466,20 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                 }
                 uint4 xb = x;
                 uint32_t blk = 0;
-                const uint64_t natt = q.natt;
+                const uint64_t natt = q.natt[o];
+                const uint64_t qT = q.T[o], qTket = q.Tket[o], qTbra = q.Tbra[o];
+                const bool qinit = q.init[o] != 0;
                 for (uint64_t a = 0; a < natt; ++a) {
                     const uint32_t u = attempt_word(x, xb, blk, a, ctr, k0, k1);
                     const uint64_t v = (uint64_t)u * natt;
-                    if (v >= q.T) continue;
-                    uint32_t ci = q.i, cj = q.j;
+                    if (v >= qT) continue;
+                    uint32_t ci = qi, cj = qj;
                     int cre = 0, cim = 0;
-                    if (v < q.T_ket + q.T_bra) {
-                        const bool ket = v < q.T_ket;
-                        const uint64_t A = ket ? q.Ai : q.Aj;
-                        const int p = seg_search(A, c.Emorton, q.C1, q.C2, R, ket ? v : v - q.T_ket);
+                    if (v < qTket + qTbra) {
+                        const bool ket = v < qTket;
+                        const uint64_t A = ket ? q.Ai[o] : q.Aj[o];
+                        const int p = seg_select(c, s.urate8, ket ? q.gk[o] : q.gb[o], A, q.X1[o], q.X2[o],
+                                                 ket ? v : v - qTket);
                         const int k = p >> 1;
                         const int other = (p & 1) ? s.dn[k] : s.rn[k];
                         const uint32_t m = (1u << k) | (1u << other);
@@ -411,19 +488,14 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                         if (ket) ci ^= m; else cj ^= m;
                         if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
                     } else {
-                        uint64_t idx = (v - q.T_ket - q.T_bra) / c.jump_q;
-                        uint32_t jm = q.i & q.j;
-                        for (; idx > 0; --idx) jm &= jm - 1u;
-                        const int k = __ffs(jm) - 1;
+                        const uint32_t idx = small_quotient(v - qTket - qTbra, c.jump_q);
+                        const int k = select_bit((uint64_t)(qi & qj), idx);
                         ci &= ~(1u << k);
                         cj &= ~(1u << k);
                         if (part == 0) cre = sig; else cim = sig;
                     }
-                    Rec r;
-                    r.key = ((uint64_t)cj << N) | (uint64_t)ci | (q.init ? FLAG_BIT : 0ull);
-                    r.re = cre;
-                    r.im = cim;
-                    emit(s, warp, r, out, cap, st, npass);
+                    emit(s, warp, make_spawn<T>(((uint64_t)cj << N) | (uint64_t)ci, qinit, cre, cim), out,
+                         cap, st, npass);
                 }
             }
         }
@@ -445,12 +517,56 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
             const int32_t hre = __shfl_sync(0xFFFFFFFFu, rec.re, h);
             const int32_t him = __shfl_sync(0xFFFFFFFFu, rec.im, h);
             const bool hinit = __shfl_sync(0xFFFFFFFFu, init, h);
-            const uint64_t hfl = hinit ? FLAG_BIT : 0ull;
-            // cumulative thresholds over the K moves (warp scan)
+            // rates of the K moves in move order (group-major inside each bond
+            // segment, via ballots over the bonds), then their running sums
+            {
+                const uint64_t hd = hi ^ hj;
+                const unsigned lt = (1u << lane) - 1u;
+                int base = 0;
+                for (int seg = 0; seg < 2; ++seg) {
+                    const uint64_t w = seg == 0 ? hi : hj;
+                    int g0 = -1, g1 = -1;
+                    uint64_t r0 = 0, r1 = 0;
+                    if (lane < B) {
+                        const int a0 = s.bond_a[lane], a1 = s.bond_b[lane];
+                        const int anti = (int)(((w >> a0) ^ (w >> a1)) & 1ull);
+                        const int cl = imp_class(c.gk, hd, s.bond_m[lane], a0, a1);
+                        g0 = 4 * anti + cl;
+                        r0 = s.rate_q[lane][anti][cl];
+                    }
+                    if (lane + 32 < B) {
+                        const int a0 = s.bond_a[lane + 32], a1 = s.bond_b[lane + 32];
+                        const int anti = (int)(((w >> a0) ^ (w >> a1)) & 1ull);
+                        const int cl = imp_class(c.gk, hd, s.bond_m[lane + 32], a0, a1);
+                        g1 = 4 * anti + cl;
+                        r1 = s.rate_q[lane + 32][anti][cl];
+                    }
+                    for (int g = 0; g < 8; ++g) {
+                        const unsigned m0 = __ballot_sync(0xFFFFFFFFu, g0 == g);
+                        const unsigned m1 = __ballot_sync(0xFFFFFFFFu, g1 == g);
+                        if (g0 == g) {
+                            const int pos = base + __popc(m0 & lt);
+                            s.cum[warp][pos] = r0;
+                            s.mv[warp][pos] = (int16_t)(seg * B + lane);
+                        }
+                        if (g1 == g) {
+                            const int pos = base + __popc(m0) + __popc(m1 & lt);
+                            s.cum[warp][pos] = r1;
+                            s.mv[warp][pos] = (int16_t)(seg * B + lane + 32);
+                        }
+                        base += __popc(m0) + __popc(m1);
+                    }
+                }
+                if (lane < N) {
+                    s.cum[warp][2 * B + lane] = (((hi & hj) >> lane) & 1ull) ? c.jump_q : 0ull;
+                    s.mv[warp][2 * B + lane] = (int16_t)(2 * B + lane);
+                }
+                __syncwarp();
+            }
             uint64_t carry = 0;
             for (int base = 0; base < K; base += 32) {
                 const int m = base + lane;
-                uint64_t r = m < K ? move_rate(c, hi, hj, m) : 0ull;
+                uint64_t r = m < K ? s.cum[warp][m] : 0ull;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
                     const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, r, off);
@@ -461,8 +577,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
             }
             for (int m = lane; m < K; m += 32) { s.cnt_re[warp][m] = 0; s.cnt_im[warp][m] = 0; }
             __syncwarp();
-            const uint64_t T = carry;
-            uint64_t natt = (T + 0xFFFFFFFFull) >> 32;
+            const uint64_t Ttot = carry;
+            uint64_t natt = (Ttot + 0xFFFFFFFFull) >> 32;
             if (natt == 0) natt = 1;
             int na_i = 0, na_j = 0;
             for (int b = 0; b < B; ++b) {
@@ -490,7 +606,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                     for (uint64_t a = 0; a < natt; ++a) {
                         const uint32_t u = attempt_word(x, xb, blk, a, ctr, k0, k1);
                         const uint64_t v = (uint64_t)u * natt;
-                        if (v >= T) continue;
+                        if (v >= Ttot) continue;
                         int lo = 0, hi2 = K - 1;
                         while (lo < hi2) {
                             const int mid = (lo + hi2) >> 1;
@@ -499,7 +615,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                         uint64_t ck;
                         int gsg;
                         bool jump;
-                        move_key(c, P, hi, hj, lo, ck, gsg, jump);
+                        move_key(c, P, hi, hj, s.mv[warp][lo], ck, gsg, jump);
                         if (jump) {
                             if (part == 0) atomicAdd(&s.cnt_re[warp][lo], sig);
                             else atomicAdd(&s.cnt_im[warp][lo], sig);
@@ -525,14 +641,11 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
             for (int m = lane; m < K; m += 32) {
                 const int32_t cre = s.cnt_re[warp][m], cim = s.cnt_im[warp][m];
                 if (cre == 0 && cim == 0) continue;
-                Rec r;
+                uint64_t ck;
                 int gsg;
                 bool jump;
-                move_key(c, P, hi, hj, m, r.key, gsg, jump);
-                r.key |= hfl;
-                r.re = cre;
-                r.im = cim;
-                emit(s, warp, r, out, cap, st, npass);
+                move_key(c, P, hi, hj, s.mv[warp][m], ck, gsg, jump);
+                emit_counts(s, warp, ck, hinit, cre, cim, out, cap, st, npass);
             }
             flush(s, warp, lane, out, cap, st, npass, SP_FLUSH);
         }

@@ -87,6 +87,21 @@ def test_variants_bitexact(ddqmc, base, over):
         _same(gpu, cpu, t)
 
 
+def test_site_dependent_guide_bitexact(ddqmc):
+    """Site-product guide with a different ratio on every site: every bond has
+    its own rate table, so every configuration takes the warp-per-configuration
+    path with the group-ordered cumulative table."""
+    r = [0.35 + 0.07 * k for k in range(9)]
+    args = (3, 3, 1, 0.9, 1.0, 1.0, 1.0, 0.01, 20000)
+    kw = dict(n_a=2, control=1, seed=5, guide_kind=2, site_ratio=r)
+    gpu = ddqmc.Run(*args, **kw)
+    cpu = O.OracleRun(*args, **kw)
+    for t in range(120):
+        gpu.step(1)
+        cpu.step(1)
+        _same(gpu, cpu, t)
+
+
 def test_heavy_and_light_entries_4x4(ddqmc):
     """4x4 periodic with many walkers per diagonal entry (warp-cooperative path)
     and single walkers off the diagonal (lane-per-entry path)."""
@@ -94,6 +109,20 @@ def test_heavy_and_light_entries_4x4(ddqmc):
     cfg.update(target=3 * 10 ** 5, n0=20000)
     gpu, cpu = _pair(ddqmc, cfg)
     for t in range(60):
+        gpu.step(1)
+        cpu.step(1)
+        _same(gpu, cpu, t)
+
+
+@pytest.mark.parametrize("Lx,Ly,per", [(4, 5, 0), (3, 6, 1)])
+def test_wide_keys_bitexact(ddqmc, Lx, Ly, per):
+    """More than 16 sites: 16-byte spawn records (the packed 8-byte layout
+    needs 2N <= 32), open and periodic."""
+    args = (Lx, Ly, per, 0.9, 1.0, 1.0, 1.0, 0.005, 30000)
+    kw = dict(n_a=3, control=1, seed=7)
+    gpu = ddqmc.Run(*args, **kw)
+    cpu = O.OracleRun(*args, **kw)
+    for t in range(150):
         gpu.step(1)
         cpu.step(1)
         _same(gpu, cpu, t)

@@ -106,3 +106,27 @@ def test_initiator_keeps_child_on_diagonal():
     run.inject([1000, FULL, FULL, FULL])
     run.step(1)
     assert _list(run) == [(0, 0, -1, 0), (3, 0, 0, 1)]
+
+
+def test_move_groups_order_aligned_before_anti_aligned():
+    # 3-site open chain, one real walker on (ket 1, bra 1): in ket 1 (site 0 up)
+    # bond b0 = (0,1) is anti-aligned and b1 = (1,2) aligned, so the ket moves
+    # come as b1 (aligned group) then b0 (anti-aligned group), although b0
+    # comes first in bond order; the same holds for the bra moves.
+    # dt = 0.01: aligned rate 0.1*0.01*2^32 -> 4294967, anti-aligned
+    # 1.9*0.01*2^32 -> 81604378; cumulative ket: 4294967, 85899345.
+    # u0 = 1000 < 4294967 selects the ket move on b1: child (1 ^ 6, 1) = (7, 1),
+    # A = -i (Jx - Jy) = +0.1 i -> imaginary child, sign +.
+    # Death (c = 2, S = 0): p = 0.01; all-ones words: no death, no transfer.
+    run = _run(3, 1, 0.01, 0.0)
+    run.import_([1], [1], [1], [0])
+    run.inject([1000, FULL, FULL, FULL])
+    run.step(1)
+    assert _list(run) == [(1, 1, 1, 0), (7, 1, 0, 1)]
+    # u0 = 4294967 selects the first anti-aligned move: b0, child (1 ^ 3, 1) = (2, 1),
+    # A = -i (Jx + Jy) = -1.9 i -> imaginary child, sign -.
+    run = _run(3, 1, 0.01, 0.0)
+    run.import_([1], [1], [1], [0])
+    run.inject([4294967, FULL, FULL, FULL])
+    run.step(1)
+    assert _list(run) == [(1, 1, 1, 0), (2, 1, 0, -1)]
