@@ -60,6 +60,23 @@ struct LightSoA {
     int32_t cd[32], adz[32], sgn_d[32], init[32];
 };
 
+// Tables of one warp-cooperative configuration: running rate sums of the
+// moves in move order, the move index of each slot (ket b, bra B + b, jump
+// 2B + k) and the children counted per slot.
+struct HeavyTables {
+    uint64_t cum[MAXK];
+    int32_t cnt_re[MAXK];
+    int32_t cnt_im[MAXK];
+    int16_t mv[MAXK];
+};
+
+// A warp's light-configuration parameters are dead before its heavy
+// configurations start, so the two share storage.
+union WarpScratch {
+    LightSoA le;
+    HeavyTables hv;
+};
+
 struct SpawnShared {
     uint64_t rate_q[MAXB][2][4];
     uint64_t bond_m[MAXB];
@@ -74,13 +91,9 @@ struct SpawnShared {
     uint32_t hist[MAXPASS][256];
     int32_t stage_n[SP_WARPS];
     Rec stage[SP_WARPS][SP_STAGE];
-    LightSoA le[SP_WARPS];
+    WarpScratch ws[SP_WARPS];
     int32_t incl[SP_WARPS][32];
     int32_t dre[SP_WARPS][32], dim[SP_WARPS][32];
-    uint64_t cum[SP_WARPS][MAXK];
-    int16_t mv[SP_WARPS][MAXK];       // move index (ket b, bra B + b, jump 2B + k) of each table slot
-    int32_t cnt_re[SP_WARPS][MAXK];
-    int32_t cnt_im[SP_WARPS][MAXK];
 };
 
 struct SpawnCtx {
@@ -328,7 +341,7 @@ __device__ __forceinline__ uint32_t attempt_word(uint4 x0, uint4 &xb, uint32_t &
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SP_TPB)
+__global__ void __launch_bounds__(SP_TPB, 3)
 k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *__restrict__ L,
               T *__restrict__ out, int64_t cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -381,7 +394,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
         // ---- light configurations: per-configuration setup, one lane each ----
         int nl = 0;
         if (light) {
-            LightSoA &q = s.le[warp];
+            LightSoA &q = s.ws[warp].le;
             const uint32_t i32 = (uint32_t)i, j32 = (uint32_t)j;
             const uint64_t Ai = anti_mask(c, i32), Aj = anti_mask(c, j32);
             uint64_t X1, X2;
@@ -442,7 +455,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                     if (s.incl[warp][mid] > g) hi = mid; else lo = mid + 1;
                 }
                 const int owner = lo;
-                const LightSoA &q = s.le[warp];
+                const LightSoA &q = s.ws[warp].le;
                 const int o = owner;
                 const uint32_t qi = q.i[o], qj = q.j[o];
                 const int nre_o = q.nre[o];
@@ -546,36 +559,36 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                         const unsigned m1 = __ballot_sync(0xFFFFFFFFu, g1 == g);
                         if (g0 == g) {
                             const int pos = base + __popc(m0 & lt);
-                            s.cum[warp][pos] = r0;
-                            s.mv[warp][pos] = (int16_t)(seg * B + lane);
+                            s.ws[warp].hv.cum[pos] = r0;
+                            s.ws[warp].hv.mv[pos] = (int16_t)(seg * B + lane);
                         }
                         if (g1 == g) {
                             const int pos = base + __popc(m0) + __popc(m1 & lt);
-                            s.cum[warp][pos] = r1;
-                            s.mv[warp][pos] = (int16_t)(seg * B + lane + 32);
+                            s.ws[warp].hv.cum[pos] = r1;
+                            s.ws[warp].hv.mv[pos] = (int16_t)(seg * B + lane + 32);
                         }
                         base += __popc(m0) + __popc(m1);
                     }
                 }
                 if (lane < N) {
-                    s.cum[warp][2 * B + lane] = (((hi & hj) >> lane) & 1ull) ? c.jump_q : 0ull;
-                    s.mv[warp][2 * B + lane] = (int16_t)(2 * B + lane);
+                    s.ws[warp].hv.cum[2 * B + lane] = (((hi & hj) >> lane) & 1ull) ? c.jump_q : 0ull;
+                    s.ws[warp].hv.mv[2 * B + lane] = (int16_t)(2 * B + lane);
                 }
                 __syncwarp();
             }
             uint64_t carry = 0;
             for (int base = 0; base < K; base += 32) {
                 const int m = base + lane;
-                uint64_t r = m < K ? s.cum[warp][m] : 0ull;
+                uint64_t r = m < K ? s.ws[warp].hv.cum[m] : 0ull;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
                     const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, r, off);
                     if (lane >= off) r += y;
                 }
-                if (m < K) s.cum[warp][m] = carry + r;
+                if (m < K) s.ws[warp].hv.cum[m] = carry + r;
                 carry += __shfl_sync(0xFFFFFFFFu, r, 31);
             }
-            for (int m = lane; m < K; m += 32) { s.cnt_re[warp][m] = 0; s.cnt_im[warp][m] = 0; }
+            for (int m = lane; m < K; m += 32) { s.ws[warp].hv.cnt_re[m] = 0; s.ws[warp].hv.cnt_im[m] = 0; }
             __syncwarp();
             const uint64_t Ttot = carry;
             uint64_t natt = (Ttot + 0xFFFFFFFFull) >> 32;
@@ -610,18 +623,18 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                         int lo = 0, hi2 = K - 1;
                         while (lo < hi2) {
                             const int mid = (lo + hi2) >> 1;
-                            if (v < s.cum[warp][mid]) hi2 = mid; else lo = mid + 1;
+                            if (v < s.ws[warp].hv.cum[mid]) hi2 = mid; else lo = mid + 1;
                         }
                         uint64_t ck;
                         int gsg;
                         bool jump;
-                        move_key(c, P, hi, hj, s.mv[warp][lo], ck, gsg, jump);
+                        move_key(c, P, hi, hj, s.ws[warp].hv.mv[lo], ck, gsg, jump);
                         if (jump) {
-                            if (part == 0) atomicAdd(&s.cnt_re[warp][lo], sig);
-                            else atomicAdd(&s.cnt_im[warp][lo], sig);
+                            if (part == 0) atomicAdd(&s.ws[warp].hv.cnt_re[lo], sig);
+                            else atomicAdd(&s.ws[warp].hv.cnt_im[lo], sig);
                         } else {
-                            if (part == 0) atomicAdd(&s.cnt_im[warp][lo], sig * gsg);
-                            else atomicAdd(&s.cnt_re[warp][lo], -sig * gsg);
+                            if (part == 0) atomicAdd(&s.ws[warp].hv.cnt_im[lo], sig * gsg);
+                            else atomicAdd(&s.ws[warp].hv.cnt_re[lo], -sig * gsg);
                         }
                     }
                 }
@@ -639,12 +652,12 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
             }
             __syncwarp();
             for (int m = lane; m < K; m += 32) {
-                const int32_t cre = s.cnt_re[warp][m], cim = s.cnt_im[warp][m];
+                const int32_t cre = s.ws[warp].hv.cnt_re[m], cim = s.ws[warp].hv.cnt_im[m];
                 if (cre == 0 && cim == 0) continue;
                 uint64_t ck;
                 int gsg;
                 bool jump;
-                move_key(c, P, hi, hj, s.mv[warp][m], ck, gsg, jump);
+                move_key(c, P, hi, hj, s.ws[warp].hv.mv[m], ck, gsg, jump);
                 emit_counts(s, warp, ck, hinit, cre, cim, out, cap, st, npass);
             }
             flush(s, warp, lane, out, cap, st, npass, SP_FLUSH);
