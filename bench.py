@@ -280,9 +280,11 @@ def gpu_arm(args, world, rank, local, pg):
     value = ws_all / (t_max / 1e3)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / average launch time
-    alg = {"spawn_death": (24 * dM + 16 * dR) / K,
-           "radix_pass": 32 * dR / K,
-           "merge": 16 * (dM + dR + dMn) / K}
+    # spawn records are 8 bytes when 2N <= 32 (packed layout), else 16
+    rb = 8 if 2 * N <= 32 else 16
+    alg = {"spawn_death": (24 * dM + rb * dR) / K,
+           "radix_pass": 2 * rb * dR / K,
+           "merge": (16 * (dM + dMn) + rb * dR) / K}
     per_unit = {"spawn_death": (dM + dR) / K, "radix_pass": dR / K, "merge": (dM + dR) / K}
     kern = {}
     for k, (kms, n) in timing.items():

@@ -32,6 +32,7 @@ struct ddqmc_run {
     uint64_t *lb_radix = nullptr;
     uint64_t *lb_merge = nullptr;
     int64_t *splits = nullptr;
+    int64_t *rem_end = nullptr;
     int64_t mcap = 0, rcap = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -236,6 +237,7 @@ void free_run(ddqmc_run *r) {
     cudaFree(r->lb_radix);
     cudaFree(r->lb_merge);
     cudaFree(r->splits);
+    cudaFree(r->rem_end);
     cudaFree(r->dAnn);
     if (r->own_stream && r->stream) cudaStreamDestroy(r->stream);
     delete r;
@@ -290,11 +292,11 @@ void launch_step(ddqmc_run *r, Rec *Lc, Rec *Ln, const std::function<void(int, i
     mark(1, 1);
     const T *sorted = (P.npass & 1) ? sp1 : sp0;
     mark(2, 0);
-    k_merge_partition<T><<<r->g_part, 256, 0, r->stream>>>(Lc, sorted, r->dS, r->splits, r->rcap);
+    k_merge_partition<T><<<r->g_part, 256, 0, r->stream>>>(Lc, sorted, r->dS, r->splits, r->rem_end, r->rcap);
     mark(2, 1);
     mark(3, 0);
-    k_merge<T><<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits, r->lb_merge,
-                                                           r->rcap, r->mcap);
+    k_merge<T><<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits, r->rem_end,
+                                                           r->lb_merge, r->rcap, r->mcap);
     mark(3, 1);
 }
 
@@ -429,6 +431,7 @@ struct NoAllocScratch {
     uint64_t lb_radix[NA_RTILES * 256];
     uint64_t lb_merge[NA_MTILES];
     int64_t splits[NA_MTILES + 1];
+    int64_t rem_end[NA_MTILES + 1];
     Rec buf[2][NA_MAX_SPAWNS];
 };
 
@@ -535,6 +538,7 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     rc |= dalloc(&r->lb_radix, (size_t)rtiles * 256);
     rc |= dalloc(&r->lb_merge, (size_t)mtiles);
     rc |= dalloc(&r->splits, (size_t)mtiles + 1);
+    rc |= dalloc(&r->rem_end, (size_t)mtiles + 1);
     if (rc != DDQMC_OK) { free_run(r); return DDQMC_ERR_OOM; }
     // kernel shapes
     int sms = 0;
@@ -918,9 +922,9 @@ int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_
                                                                           r->rcap);
         src = dst;
     }
-    k_merge_partition<Rec><<<r->g_part, 256, 0, r->stream>>>(list, src, r->dAnn, r->splits, r->rcap);
+    k_merge_partition<Rec><<<r->g_part, 256, 0, r->stream>>>(list, src, r->dAnn, r->splits, r->rem_end, r->rcap);
     k_merge<Rec><<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, list, src, (Rec *)d_out, r->dAnn, r->splits,
-                                                             r->lb_merge, r->rcap, out_cap);
+                                                             r->rem_end, r->lb_merge, r->rcap, out_cap);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&hs, r->dAnn, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
@@ -972,9 +976,10 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
                                                                            NA_MAX_SPAWNS);
         src = dst;
     }
-    k_merge_partition<Rec><<<g_na_grid[dev][1], 256, 0, stream>>>(list, src, &sc->st, sc->splits, NA_MAX_SPAWNS);
+    k_merge_partition<Rec><<<g_na_grid[dev][1], 256, 0, stream>>>(list, src, &sc->st, sc->splits, sc->rem_end,
+                                                                   NA_MAX_SPAWNS);
     k_merge<Rec><<<g_na_grid[dev][2], MG_TPB, MG_SMEM, stream>>>(&sc->P, list, src, (Rec *)d_out, &sc->st, sc->splits,
-                                                                 sc->lb_merge, NA_MAX_SPAWNS, out_cap);
+                                                                 sc->rem_end, sc->lb_merge, NA_MAX_SPAWNS, out_cap);
     int64_t mo = 0;
     uint32_t status = 0;
     if (cudaGetLastError() != cudaSuccess ||

@@ -42,9 +42,13 @@ __device__ __forceinline__ int64_t merge_split(const Rec *L, int64_t M, const T 
     return lo;
 }
 
+// For every tile boundary t: the merge-path split, and the end of the spawn
+// records that continue the last run of tile t-1 past the boundary (the
+// records S[b, rem_end[t]) share the key of the merged element before the
+// boundary; rem_end[t] = b when the run stops there).
 template <typename T>
 __global__ void k_merge_partition(const Rec *__restrict__ L, const T *__restrict__ S, DevState *__restrict__ st,
-                                  int64_t *__restrict__ splits, int64_t rcap) {
+                                  int64_t *__restrict__ splits, int64_t *__restrict__ rem_end, int64_t rcap) {
     if (st->status) return;
     const int64_t M = st->M;
     int64_t R = st->R;
@@ -54,8 +58,93 @@ __global__ void k_merge_partition(const Rec *__restrict__ L, const T *__restrict
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += (int64_t)gridDim.x * blockDim.x) {
         int64_t diag = t * MG_TILE;
         if (diag > tot) diag = tot;
-        splits[t] = merge_split(L, M, S, R, diag);
+        const int64_t a = merge_split(L, M, S, R, diag);
+        const int64_t b = diag - a;
+        splits[t] = a;
+        int64_t e = b;
+        if (b < R && diag > 0) {
+            uint64_t last = 0;
+            if (a > 0) last = L[a - 1].key;
+            if (b > 0) {
+                const uint64_t k2 = RecTraits<T>::key(S[b - 1]);
+                if (k2 > last) last = k2;
+            }
+            if (RecTraits<T>::key(S[b]) == last) {
+                // first record after b with a larger key
+                int64_t lo = b + 1, hi = R;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (RecTraits<T>::key(S[mid]) == last) lo = mid + 1;
+                    else hi = mid;
+                }
+                e = lo;
+            }
+        }
+        rem_end[t] = e;
     }
+}
+
+// Aggregate of a partial run for the segmented reduction: h = a run head lies
+// in the aggregated range, hasL = that head is the L_t entry, f = L_t
+// population plus initiator records, u = non-initiator records.
+struct SegAgg {
+    int32_t h, hasL;
+    int64_t fre, fim, ure, uim;
+};
+
+__device__ __forceinline__ SegAgg seg_identity() {
+    SegAgg a;
+    a.h = 0; a.hasL = 0; a.fre = 0; a.fim = 0; a.ure = 0; a.uim = 0;
+    return a;
+}
+
+__device__ __forceinline__ SegAgg seg_head(uint32_t fromL) {
+    SegAgg a = seg_identity();
+    a.h = 1;
+    a.hasL = (int32_t)fromL;
+    return a;
+}
+
+__device__ __forceinline__ void seg_add(SegAgg &a, int2 v, uint32_t counted) {
+    if (counted) { a.fre += v.x; a.fim += v.y; }
+    else { a.ure += v.x; a.uim += v.y; }
+}
+
+// a followed by b
+__device__ __forceinline__ SegAgg seg_combine(const SegAgg &a, const SegAgg &b) {
+    if (b.h) return b;
+    SegAgg r;
+    r.h = a.h; r.hasL = a.hasL;
+    r.fre = a.fre + b.fre; r.fim = a.fim + b.fim; r.ure = a.ure + b.ure; r.uim = a.uim + b.uim;
+    return r;
+}
+
+__device__ __forceinline__ SegAgg seg_shfl_up(const SegAgg &a, int off) {
+    SegAgg r;
+    r.h = __shfl_up_sync(0xFFFFFFFFu, a.h, off);
+    r.hasL = __shfl_up_sync(0xFFFFFFFFu, a.hasL, off);
+    r.fre = __shfl_up_sync(0xFFFFFFFFu, a.fre, off);
+    r.fim = __shfl_up_sync(0xFFFFFFFFu, a.fim, off);
+    r.ure = __shfl_up_sync(0xFFFFFFFFu, a.ure, off);
+    r.uim = __shfl_up_sync(0xFFFFFFFFu, a.uim, off);
+    return r;
+}
+
+// Exclusive segmented scan over the threads of the block (tmp: one slot per warp).
+__device__ __forceinline__ SegAgg seg_block_exclusive(const SegAgg &mine, SegAgg *tmp, int lane, int warp) {
+    SegAgg inc = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const SegAgg o = seg_shfl_up(inc, off);
+        if (lane >= off) inc = seg_combine(o, inc);
+    }
+    SegAgg exc = seg_shfl_up(inc, 1);
+    if (lane == 0) exc = seg_identity();
+    if (lane == 31) tmp[warp] = inc;
+    __syncthreads();
+    SegAgg pre = seg_identity();
+    for (int w = 0; w < warp; ++w) pre = seg_combine(pre, tmp[w]);
+    return seg_combine(pre, exc);
 }
 
 struct MergeShared {
@@ -66,7 +155,10 @@ struct MergeShared {
     int8_t bond_a[MAXB], bond_b[MAXB];
     int8_t pair_bond[MAXN * MAXN];
     uint32_t scan_tmp[MG_WARPS];
-    int64_t tile, a0, a1, out_base;
+    SegAgg seg_tmp[MG_WARPS];
+    int32_t first_head[MG_TPB];
+    int64_t rem_f[2], rem_u[2];       // remainder of the tile's last run past the tile end
+    int64_t tile, a0, a1, out_base, rem_e;
     uint64_t prev_key;
     int32_t has_prev;
 };
@@ -110,7 +202,7 @@ template <typename T>
 __global__ void __launch_bounds__(MG_TPB)
 k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__restrict__ S,
         Rec *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
-        uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
+        const int64_t *__restrict__ rem_end, uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
     using TR = RecTraits<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MergeShared &s = *reinterpret_cast<MergeShared *>(smem_raw);
@@ -146,6 +238,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                 const int64_t d0 = tile * MG_TILE;
                 s.a0 = splits[tile];
                 s.a1 = splits[tile + 1];
+                s.rem_e = rem_end[tile + 1];
                 const int64_t b0 = d0 - s.a0;
                 uint64_t pk = 0;
                 int hp = 0;
@@ -178,18 +271,37 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
             s.key[na + q] = TR::key(v) | (TR::flag(v) ? FLAG_BIT : 0ull);
             s.val[na + q] = make_int2(TR::re(v), TR::im(v));
         }
+        if (warp == 0) {
+            // spawn records past the tile end that continue its last run
+            int64_t f0 = 0, f1 = 0, u0 = 0, u1 = 0;
+            for (int64_t q = b1 + lane; q < s.rem_e; q += 32) {
+                const T g = S[q];
+                if (TR::flag(g)) { f0 += TR::re(g); f1 += TR::im(g); }
+                else { u0 += TR::re(g); u1 += TR::im(g); }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                f0 += __shfl_xor_sync(0xFFFFFFFFu, f0, off);
+                f1 += __shfl_xor_sync(0xFFFFFFFFu, f1, off);
+                u0 += __shfl_xor_sync(0xFFFFFFFFu, u0, off);
+                u1 += __shfl_xor_sync(0xFFFFFFFFu, u1, off);
+            }
+            if (lane == 0) { s.rem_f[0] = f0; s.rem_f[1] = f1; s.rem_u[0] = u0; s.rem_u[1] = u1; }
+        }
         __syncthreads();
         const uint64_t *kL = s.key;
         const uint64_t *kS = s.key + na;
         const int2 *vL = s.val;
         const int2 *vS = s.val + na;
 
-        // this thread's merge-path start inside the tile
+        // ---- 1. merge: this thread's MG_IPT merged positions, in registers ----
         const int dloc = tid * MG_IPT;
-        uint64_t okey[MG_IPT];
-        int2 oval[MG_IPT];
-        int nout = 0;
-        if (dloc < na + nb) {
+        const int nt = na + nb;
+        uint64_t ik[MG_IPT];
+        int2 iv[MG_IPT];
+        uint32_t hmask = 0, lmask = 0, fmask = 0;   // run heads, elements of L_t, initiator records
+        int nk = 0;
+        if (dloc < nt) {
             int lo = dloc > nb ? dloc - nb : 0;
             int hi = dloc < na ? dloc : na;
             while (lo < hi) {
@@ -210,52 +322,78 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                     hprev = true;
                 }
             }
-            const int dend = (dloc + MG_IPT < na + nb) ? dloc + MG_IPT : na + nb;
-#pragma unroll 1
-            for (int dpos = dloc; dpos < dend; ++dpos) {
-                bool fromL;
-                if (ia >= na) fromL = false;
-                else if (ib >= nb) fromL = true;
-                else fromL = kL[ia] <= (kS[ib] & KEY_MASK);
-                const uint64_t key = fromL ? kL[ia] : (kS[ib] & KEY_MASK);
-                const bool head = !hprev || key != prev;
-                prev = key;
-                hprev = true;
-                if (head) {
-                    int64_t sre = 0, sim = 0;
-                    if (fromL) { sre = vL[ia].x; sim = vL[ia].y; }
-                    const bool open = fromL || no_init || ((key & nmask) == (key >> N));
-                    // walk the spawn records of this key (may run past the tile)
-                    int64_t q = ib;
-                    for (;;) {
-                        uint64_t kk;
-                        int32_t vr, vi;
-                        if (q < nb) {
-                            kk = kS[q];
-                            vr = vS[q].x;
-                            vi = vS[q].y;
-                        } else if (b0 + q < R) {
-                            const T g = S[b0 + q];
-                            kk = TR::key(g) | (TR::flag(g) ? FLAG_BIT : 0ull);
-                            vr = TR::re(g);
-                            vi = TR::im(g);
-                        } else {
-                            break;
-                        }
-                        if ((kk & KEY_MASK) != key) break;
-                        if (open || (kk & FLAG_BIT)) { sre += vr; sim += vi; }
-                        ++q;
-                    }
-                    if (sre != 0 || sim != 0) {
-                        if (iabs64(sre) > 2147483647ll || iabs64(sim) > 2147483647ll) local_status |= ST_OVERFLOW;
-                        okey[nout] = key;
-                        oval[nout] = make_int2((int32_t)sre, (int32_t)sim);
-                        ++nout;
-                    }
+            nk = nt - dloc < MG_IPT ? nt - dloc : MG_IPT;
+#pragma unroll
+            for (int k = 0; k < MG_IPT; ++k) {
+                ik[k] = 0;
+                iv[k] = make_int2(0, 0);
+                if (k < nk) {
+                    bool fromL;
+                    if (ia >= na) fromL = false;
+                    else if (ib >= nb) fromL = true;
+                    else fromL = kL[ia] <= (kS[ib] & KEY_MASK);
+                    const uint64_t kraw = fromL ? kL[ia] : kS[ib];
+                    const uint64_t key = kraw & KEY_MASK;
+                    ik[k] = key;
+                    iv[k] = fromL ? vL[ia] : vS[ib];
+                    if (!hprev || key != prev) hmask |= 1u << k;
+                    if (fromL) lmask |= 1u << k;
+                    else if (kraw & FLAG_BIT) fmask |= 1u << k;
+                    prev = key;
+                    hprev = true;
+                    if (fromL) ++ia; else ++ib;
                 }
-                if (fromL) ++ia; else ++ib;
             }
         }
+        // ---- 2. segmented reduction of the runs across the block -------------
+        // Per run: sum of its L_t population and initiator records (f), sum of
+        // its non-initiator records (u), and whether its head is in L_t.
+        SegAgg tail = seg_identity();
+#pragma unroll
+        for (int k = 0; k < MG_IPT; ++k) {
+            if (k < nk) {
+                if ((hmask >> k) & 1u) tail = seg_head((lmask >> k) & 1u);
+                seg_add(tail, iv[k], ((lmask | fmask) >> k) & 1u);
+            }
+        }
+        const SegAgg carry = seg_block_exclusive(tail, s.seg_tmp, lane, warp);
+        s.first_head[tid] = nk > 0 ? (int)(hmask & 1u) : 1;
+        __syncthreads();
+        const bool next_thread_head = tid + 1 < MG_TPB ? s.first_head[tid + 1] != 0 : true;
+        SegAgg run = carry;
+        bool owned = carry.h != 0;       // the open run has its head in this tile
+        uint32_t omask = 0;
+        int2 oval[MG_IPT];
+#pragma unroll
+        for (int k = 0; k < MG_IPT; ++k) {
+            oval[k] = make_int2(0, 0);
+            if (k < nk) {
+                if ((hmask >> k) & 1u) { run = seg_head((lmask >> k) & 1u); owned = true; }
+                seg_add(run, iv[k], ((lmask | fmask) >> k) & 1u);
+                bool ends;
+                if (k + 1 < nk) ends = ((hmask >> (k + 1)) & 1u) != 0u;
+                else if (dloc + k + 1 < nt) ends = next_thread_head;
+                else {
+                    // the tile's last run: add its spawn records that follow the tile
+                    ends = true;
+                    run.fre += s.rem_f[0];
+                    run.fim += s.rem_f[1];
+                    run.ure += s.rem_u[0];
+                    run.uim += s.rem_u[1];
+                }
+                if (ends && owned) {
+                    const bool open = run.hasL || no_init || ((ik[k] & nmask) == (ik[k] >> N));
+                    const int64_t sre = run.fre + (open ? run.ure : 0);
+                    const int64_t sim = run.fim + (open ? run.uim : 0);
+                    if (sre != 0 || sim != 0) {
+                        if (iabs64(sre) > 2147483647ll || iabs64(sim) > 2147483647ll) local_status |= ST_OVERFLOW;
+                        omask |= 1u << k;
+                        oval[k] = make_int2((int32_t)sre, (int32_t)sim);
+                    }
+                }
+            }
+        }
+        const int nout = __popc(omask);
         // block scan of output counts
         int x = nout;
 #pragma unroll
@@ -272,10 +410,14 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
             if (w < warp) pre += v;
             total += v;
         }
-        const uint32_t my_off = pre + (uint32_t)(x - nout);
-        for (int q = 0; q < nout; ++q) {
-            s.key[my_off + q] = okey[q];
-            s.val[my_off + q] = oval[q];
+        uint32_t my_off = pre + (uint32_t)(x - nout);
+#pragma unroll
+        for (int k = 0; k < MG_IPT; ++k) {
+            if ((omask >> k) & 1u) {
+                s.key[my_off] = ik[k];
+                s.val[my_off] = oval[k];
+                ++my_off;
+            }
         }
         // output offset of the tile: warp-parallel decoupled look-back
         if (warp == 0) {

@@ -38,6 +38,8 @@
 // pass.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "radix.cuh"
 
@@ -83,6 +85,9 @@ struct SpawnShared {
     uint64_t cross_frac[2 * MAXB + 1];
     uint64_t d_frac[2 * MAXN + 1];
     uint64_t urate8[8];
+    uint32_t urate32[8];
+    float uinv[8];
+    int32_t sgn_h[2];
     uint32_t cross_int[2 * MAXB + 1];
     uint32_t d_int[2 * MAXN + 1];
     int32_t d_sgn[2 * MAXN + 1];
@@ -112,8 +117,19 @@ __device__ __forceinline__ int imp_class(int gk, uint64_t d, uint64_t m, int a, 
 }
 
 // ---- mask formulation -------------------------------------------------------
+// Bond masks are 32-bit words when N <= 16 (2N bond bits) and 64-bit words
+// otherwise; MT is the mask type.
 
-__device__ __forceinline__ uint64_t spread_bits(uint32_t x32) {
+template <typename MT> __device__ __forceinline__ MT spread_bits(uint32_t x32);
+template <> __device__ __forceinline__ uint32_t spread_bits<uint32_t>(uint32_t x) {
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+template <> __device__ __forceinline__ uint64_t spread_bits<uint64_t>(uint32_t x32) {
     uint64_t x = x32;
     x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
     x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
@@ -123,9 +139,13 @@ __device__ __forceinline__ uint64_t spread_bits(uint32_t x32) {
     return x;
 }
 
+__device__ __forceinline__ int popcount(uint32_t x) { return __popc(x); }
+__device__ __forceinline__ int popcount(uint64_t x) { return __popcll(x); }
+
 // bond mask from per-direction site masks: bit 2k <- right bond of k, bit 2k+1 <- lower bond of k
-__device__ __forceinline__ uint64_t bond_mask(uint32_t right, uint32_t down) {
-    return spread_bits(right) | (spread_bits(down) << 1);
+template <typename MT>
+__device__ __forceinline__ MT bond_mask(uint32_t right, uint32_t down) {
+    return spread_bits<MT>(right) | (spread_bits<MT>(down) << 1);
 }
 
 // word whose bit k is the spin of the right (resp. lower) neighbour of site k
@@ -136,53 +156,60 @@ __device__ __forceinline__ uint32_t nb_down(const SpawnCtx &c, uint32_t s) {
     return (s >> c.Lx) | ((s << c.shD) & c.LR);
 }
 
-__device__ __forceinline__ uint64_t anti_mask(const SpawnCtx &c, uint32_t s) {
-    return bond_mask((s ^ nb_right(c, s)) & c.ER, (s ^ nb_down(c, s)) & c.ED);
+template <typename MT>
+__device__ __forceinline__ MT anti_mask(const SpawnCtx &c, uint32_t s) {
+    return bond_mask<MT>((s ^ nb_right(c, s)) & c.ER, (s ^ nb_down(c, s)) & c.ED);
 }
 
 // importance-class masks of configuration (i, j): for the site-product guide
 // X1 / X2 = bonds whose first / second site differs between i and j; for the
 // uniform guide X1 = every bond when i == j, X2 = the bond whose flip makes
 // the child diagonal
-__device__ __forceinline__ void class_masks(const SpawnCtx &c, uint32_t i, uint32_t j, uint64_t &X1,
-                                            uint64_t &X2) {
+template <typename MT>
+__device__ __forceinline__ void class_masks(const SpawnCtx &c, uint32_t i, uint32_t j, MT &X1, MT &X2) {
     const uint32_t d = i ^ j;
     X1 = 0;
     X2 = 0;
     if (c.gk == 1) {
-        if (d == 0) { X1 = c.Emorton; return; }
+        if (d == 0) { X1 = (MT)c.Emorton; return; }
         if (__popc(d) != 2) return;
         const int a = __ffs(d) - 1, b = 31 - __clz(d);
         const SpawnShared &s = *c.sh;
-        if ((c.ER >> a & 1u) && s.rn[a] == b) X2 = 1ull << (2 * a);
-        else if ((c.ED >> a & 1u) && s.dn[a] == b) X2 = 1ull << (2 * a + 1);
-        else if ((c.ER >> b & 1u) && s.rn[b] == a) X2 = 1ull << (2 * b);
-        else if ((c.ED >> b & 1u) && s.dn[b] == a) X2 = 1ull << (2 * b + 1);
+        if ((c.ER >> a & 1u) && s.rn[a] == b) X2 = (MT)1 << (2 * a);
+        else if ((c.ED >> a & 1u) && s.dn[a] == b) X2 = (MT)1 << (2 * a + 1);
+        else if ((c.ER >> b & 1u) && s.rn[b] == a) X2 = (MT)1 << (2 * b);
+        else if ((c.ED >> b & 1u) && s.dn[b] == a) X2 = (MT)1 << (2 * b + 1);
     } else if (c.gk == 2) {
-        X1 = bond_mask(d & c.ER, d & c.ED);
-        X2 = bond_mask(nb_right(c, d) & c.ER, nb_down(c, d) & c.ED);
+        X1 = bond_mask<MT>(d & c.ER, d & c.ED);
+        X2 = bond_mask<MT>(nb_right(c, d) & c.ER, nb_down(c, d) & c.ED);
     }
 }
 
 // bonds of group g = 4*anti + class, given the anti mask A of the flipped word
-__device__ __forceinline__ uint64_t group_mask(const SpawnCtx &c, uint64_t A, uint64_t X1, uint64_t X2, int g) {
+template <typename MT>
+__device__ __forceinline__ MT group_mask(const SpawnCtx &c, MT A, MT X1, MT X2, int g) {
     const int cls = g & 3;
-    uint64_t cm;
-    if (c.gk == 2) cm = ((cls & 2) ? X1 : ~X1) & ((cls & 1) ? X2 : ~X2);
-    else if (c.gk == 1) cm = cls == 0 ? ~(X1 | X2) : (cls == 1 ? X1 : (cls == 2 ? X2 : 0ull));
-    else cm = cls == 0 ? ~0ull : 0ull;
-    return ((g & 4) ? A : ~A) & cm & c.Emorton;
+    MT cm;
+    if (c.gk == 2) cm = ((cls & 2) ? X1 : (MT)~X1) & ((cls & 1) ? X2 : (MT)~X2);
+    else if (c.gk == 1) cm = cls == 0 ? (MT)~(X1 | X2) : (cls == 1 ? X1 : (cls == 2 ? X2 : (MT)0));
+    else cm = cls == 0 ? (MT)~(MT)0 : (MT)0;
+    return ((g & 4) ? A : (MT)~A) & cm & (MT)c.Emorton;
 }
 
 // position of the r-th set bit (r from 0) of m, given r < popcount(m)
-__device__ __forceinline__ int select_bit(uint64_t m, uint32_t r) {
+__device__ __forceinline__ int select_bit(uint32_t m, uint32_t r) {
     int pos = 0;
 #pragma unroll
-    for (int w = 32; w >= 1; w >>= 1) {
-        const uint32_t c = (uint32_t)__popcll((m >> pos) & ((1ull << w) - 1ull));
-        if (r >= c) { r -= c; pos += w; }
+    for (int w = 16; w >= 1; w >>= 1) {
+        const uint32_t c = (uint32_t)__popc(m & ((1u << w) - 1u));
+        if (r >= c) { r -= c; m >>= w; pos += w; }
     }
     return pos;
+}
+__device__ __forceinline__ int select_bit(uint64_t m, uint32_t r) {
+    const uint32_t lo = (uint32_t)m;
+    const uint32_t c = (uint32_t)__popc(lo);
+    return r < c ? select_bit(lo, r) : 32 + select_bit((uint32_t)(m >> 32), r - c);
 }
 
 // floor(v / q) for a quotient below 64, by integer bisection (no division:
@@ -196,15 +223,40 @@ __device__ __forceinline__ uint32_t small_quotient(uint64_t v, uint64_t q) {
 }
 
 // bond bit of the draw v (0 <= v < segment total) in a segment with group counts cnt
+template <typename MT>
 __device__ __forceinline__ int seg_select(const SpawnCtx &c, const uint64_t *rate8, uint64_t cnt,
-                                          uint64_t A, uint64_t X1, uint64_t X2, uint64_t v) {
+                                          MT A, MT X1, MT X2, uint64_t v) {
     int g = 0;
     for (; g < 7; ++g) {
         const uint64_t w = rate8[g] * ((cnt >> (8 * g)) & 0xFFull);
         if (v < w) break;
         v -= w;
     }
-    return select_bit(group_mask(c, A, X1, X2, g), small_quotient(v, rate8[g]));
+    return select_bit(group_mask<MT>(c, A, X1, X2, g), small_quotient(v, rate8[g]));
+}
+
+// Same for a segment whose total is below 2^32 (every group with bonds then
+// has a rate below 2^32): 32-bit arithmetic, and the index inside the group
+// from a float reciprocal estimate corrected to the exact integer quotient.
+template <typename MT>
+__device__ __forceinline__ int seg_select32(const SpawnCtx &c, const uint32_t *rate32, const float *rinv,
+                                            uint64_t cnt, MT A, MT X1, MT X2, uint32_t v) {
+    int g = -1;
+    uint32_t q = 1;
+    float qi = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t w = rate32[k] * (uint32_t)((cnt >> (8 * k)) & 0xFFull);
+        if (g < 0) {
+            if (v < w) { g = k; q = rate32[k]; qi = rinv[k]; }
+            else v -= w;
+        }
+    }
+    uint32_t r = (uint32_t)((float)v * qi);
+    const uint64_t pq = (uint64_t)r * q;
+    if (pq > v) --r;
+    else if (pq + q <= v) ++r;
+    return select_bit(group_mask<MT>(c, A, X1, X2, g), r);
 }
 
 // ---- per-move tables (heavy path) -------------------------------------------
@@ -344,6 +396,8 @@ template <typename T>
 __global__ void __launch_bounds__(SP_TPB, 3)
 k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *__restrict__ L,
               T *__restrict__ out, int64_t cap) {
+    // packed records <=> N <= 16 <=> 32-bit bond masks
+    using MT = typename std::conditional<sizeof(T) == 8, uint32_t, uint64_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SpawnShared &s = *reinterpret_cast<SpawnShared *>(smem_raw);
     const RunParams &P = *Pp;
@@ -358,7 +412,12 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
         s.bond_b[q] = (int8_t)P.bond_b[q];
     }
     for (int q = tid; q < N; q += SP_TPB) { s.rn[q] = P.rn[q]; s.dn[q] = P.dn[q]; }
-    if (tid < 8) s.urate8[tid] = P.urate8[tid];
+    if (tid < 8) {
+        s.urate8[tid] = P.urate8[tid];
+        s.urate32[tid] = (uint32_t)P.urate8[tid];
+        s.uinv[tid] = P.urate8[tid] ? 1.0f / (float)P.urate8[tid] : 0.0f;
+    }
+    if (tid < 2) s.sgn_h[tid] = P.sgn_h[tid];
     for (int q = tid; q <= 2 * B; q += SP_TPB) { s.cross_int[q] = P.cross_int[q]; s.cross_frac[q] = P.cross_frac[q]; }
     for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_frac[q] = st->d_frac[q]; s.d_sgn[q] = st->d_sgn[q]; }
     for (int q = tid; q < MAXPASS * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
@@ -396,14 +455,14 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
         if (light) {
             LightSoA &q = s.ws[warp].le;
             const uint32_t i32 = (uint32_t)i, j32 = (uint32_t)j;
-            const uint64_t Ai = anti_mask(c, i32), Aj = anti_mask(c, j32);
-            uint64_t X1, X2;
-            class_masks(c, i32, j32, X1, X2);
+            const MT Ai = anti_mask<MT>(c, i32), Aj = anti_mask<MT>(c, j32);
+            MT X1, X2;
+            class_masks<MT>(c, i32, j32, X1, X2);
             uint64_t Tket = 0, Tbra = 0, gkp = 0, gbp = 0;
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
-                const int ck = __popcll(group_mask(c, Ai, X1, X2, g));
-                const int cb = __popcll(group_mask(c, Aj, X1, X2, g));
+                const int ck = popcount(group_mask<MT>(c, Ai, X1, X2, g));
+                const int cb = popcount(group_mask<MT>(c, Aj, X1, X2, g));
                 gkp |= (uint64_t)ck << (8 * g);
                 gbp |= (uint64_t)cb << (8 * g);
                 Tket += s.urate8[g] * (uint64_t)ck;
@@ -427,7 +486,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
             q.im[lane] = rec.im;
             q.nre[lane] = (int32_t)nre;
             q.cd[lane] = __popc(i32) + __popc(j32);
-            const int dz = 2 * (__popcll(Aj) - __popcll(Ai));     // zsum(i) - zsum(j)
+            const int dz = 2 * (popcount(Aj) - popcount(Ai));     // zsum(i) - zsum(j)
             q.adz[lane] = dz < 0 ? -dz : dz;
             q.sgn_d[lane] = (dz == 0) ? 0 : -sgn_jz * (dz > 0 ? 1 : -1);
             q.init[lane] = init ? 1 : 0;
@@ -490,13 +549,17 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                     int cre = 0, cim = 0;
                     if (v < qTket + qTbra) {
                         const bool ket = v < qTket;
-                        const uint64_t A = ket ? q.Ai[o] : q.Aj[o];
-                        const int p = seg_select(c, s.urate8, ket ? q.gk[o] : q.gb[o], A, q.X1[o], q.X2[o],
-                                                 ket ? v : v - qTket);
+                        const MT A = (MT)(ket ? q.Ai[o] : q.Aj[o]);
+                        const MT X1 = (MT)q.X1[o], X2 = (MT)q.X2[o];
+                        const uint64_t cnt8 = ket ? q.gk[o] : q.gb[o];
+                        const uint64_t vs = ket ? v : v - qTket;
+                        const int p = qT <= 0xFFFFFFFFull
+                                          ? seg_select32<MT>(c, s.urate32, s.uinv, cnt8, A, X1, X2, (uint32_t)vs)
+                                          : seg_select<MT>(c, s.urate8, cnt8, A, X1, X2, vs);
                         const int k = p >> 1;
                         const int other = (p & 1) ? s.dn[k] : s.rn[k];
                         const uint32_t m = (1u << k) | (1u << other);
-                        const int hs = P.sgn_h[(A >> p) & 1ull];
+                        const int hs = s.sgn_h[(A >> p) & 1u];
                         const int gsg = ket ? -hs : hs;
                         if (ket) ci ^= m; else cj ^= m;
                         if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
