@@ -692,12 +692,16 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                         int gsg;
                         bool jump;
                         move_key(c, P, hi, hj, s.ws[warp].hv.mv[lo], ck, gsg, jump);
-                        if (jump) {
-                            if (part == 0) atomicAdd(&s.ws[warp].hv.cnt_re[lo], sig);
-                            else atomicAdd(&s.ws[warp].hv.cnt_im[lo], sig);
-                        } else {
-                            if (part == 0) atomicAdd(&s.ws[warp].hv.cnt_im[lo], sig * gsg);
-                            else atomicAdd(&s.ws[warp].hv.cnt_re[lo], -sig * gsg);
+                        // child type (0 real, 1 imaginary) and signed unit
+                        const int tgt = jump ? part : 1 - part;
+                        const int val = jump ? sig : (part == 0 ? sig * gsg : -sig * gsg);
+                        // one shared-memory update per distinct (move, type) among the lanes here
+                        const unsigned am = __activemask();
+                        const unsigned peers = __match_any_sync(am, (unsigned)(lo * 2 + tgt));
+                        const unsigned posm = __ballot_sync(am, val > 0);
+                        if (lane == __ffs(peers) - 1) {
+                            const int sum = __popc(peers & posm) - __popc(peers & ~posm);
+                            if (sum) atomicAdd(tgt ? &s.ws[warp].hv.cnt_im[lo] : &s.ws[warp].hv.cnt_re[lo], sum);
                         }
                     }
                 }

@@ -6,9 +6,11 @@ never the CUDA path.  Run from the repository root:
     python tests/golden/make_golden.py
 
 Outputs (JSON, one file per lattice):
-  ness_2x2_open.json       dense SVD null vector, 256 x 256 Liouvillian
-  ness_3x3_periodic.json   Runge-Kutta fixed point, 262144-dim Liouvillian
-Both use the XYZ couplings Jx = 0.9, Jy = 1.0, Jz = 1.0 and gamma = 1 with
+  ness_2x2_open.json            dense SVD null vector, 256 x 256 Liouvillian
+  ness_3x3_periodic.json        Runge-Kutta fixed point, 262144-dim Liouvillian
+  ness_3x3_periodic_weak.json   same, couplings (0.225, 0.335, 0.25)
+The first two use Jx = 0.9, Jy = 1.0, Jz = 1.0, the third the couplings of
+the paper's 3x3 figure (Sec. V.A) as Pauli couplings; all have gamma = 1,
 Pauli matrices in H and sigma^- decay on every site (Nagy & Savona, Sec. V).
 """
 import json
@@ -23,9 +25,9 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 from oracle import exact  # noqa: E402
 
 
-def dump(name, Lx, Ly, periodic, rho, resid, method):
+def dump(name, Lx, Ly, periodic, rho, resid, method, J=(0.9, 1.0, 1.0)):
     ob = exact.observables(rho, Lx, Ly, periodic)
-    rec = dict(lattice=[Lx, Ly, periodic], Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0,
+    rec = dict(lattice=[Lx, Ly, periodic], Jx=J[0], Jy=J[1], Jz=J[2], gamma=1.0,
                method=method, residual=float(resid), mz=ob["mz"],
                z=ob["z"].tolist(), x=ob["x"].tolist(), y=ob["y"].tolist(),
                xx=ob["xx"].tolist(), yy=ob["yy"].tolist(), zz=ob["zz"].tolist(),
@@ -43,6 +45,11 @@ def main():
     L = exact.liouvillian(3, 3, 1, 0.9, 1.0, 1.0, 1.0)
     rho, resid = exact.ness_sparse(L, 512)
     dump("ness_3x3_periodic.json", 3, 3, 1, rho, resid, "RK4 fixed point, sector popcount(i)+popcount(j) even")
+    # the couplings of the paper's 3x3 figure (Jx, Jy, Jz)/gamma = (0.225, 0.335, 0.25), taken as Pauli couplings
+    J = (0.225, 0.335, 0.25)
+    L = exact.liouvillian(3, 3, 1, J[0], J[1], J[2], 1.0)
+    rho, resid = exact.ness_sparse(L, 512)
+    dump("ness_3x3_periodic_weak.json", 3, 3, 1, rho, resid, "RK4 fixed point, sector popcount(i)+popcount(j) even", J)
 
 
 if __name__ == "__main__":

@@ -10,6 +10,11 @@ C1 = dict(Lx=2, Ly=2, periodic=0, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.01, ta
           n_a=0, seed=1, steps=20000)
 C2 = dict(Lx=3, Ly=3, periodic=1, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, target=10 ** 6,
           n_a=3, seed=2, steps=50000)
+# 3x3 periodic with the couplings of the paper's 3x3 figure, (0.225, 0.335, 0.25),
+# taken as Pauli couplings: a regime where the walker population stays near
+# the diagonal target, used for the comparison with the exact steady state
+C2W = dict(Lx=3, Ly=3, periodic=1, Jx=0.225, Jy=0.335, Jz=0.25, gamma=1.0, dt=0.005, target=10 ** 4,
+           n_a=0, seed=2, steps=40000)
 # 4x4 periodic, 10^8 walkers in total (control on the total population), n_a = 3,
 # site-product guide; the all-down mean-field fixed point gives uniform site
 # ratios exp(-1.5).
