@@ -3,19 +3,21 @@
 //
 // The sorted list L_t (unique keys, populations already updated by
 // death/clone) and the sorted spawn records S (repeated keys) are merged
-// along the merge path, L first on equal keys, in tiles of MG_TILE merged
-// positions.  In the merged order every configuration forms one run: its
-// L_t entry (if present) followed by all its spawn records.  The thread that
-// holds the first element of a run sums the run (reading past its own range,
-// and past the tile, when the run continues) under the initiator rule:
-// records whose parent was not an initiator count only when the configuration
-// is occupied in L_t or diagonal.  Non-zero sums are compacted into L_{t+1}
-// in order: a block scan gives offsets inside the tile and a warp-parallel
-// decoupled look-back over earlier tiles gives the tile's output offset.
-// Every kept entry is added to the integer estimator numerators on the way
-// out.  Keys and populations sit in separate shared arrays and every thread
-// merges an odd number of positions, so the threads' merge cursors spread
-// over the shared-memory banks.
+// along the merge path, L first on equal keys.  In the merged order every
+// configuration forms one run: its L_t entry (if present) followed by all its
+// spawn records.  Each run is summed under the initiator rule -- records whose
+// parent was not an initiator count only when the configuration is occupied
+// in L_t or diagonal -- and non-zero sums are compacted into L_{t+1} in order;
+// every kept entry is added to the integer estimator numerators on the way out.
+//
+// Work is cut into tiles of MG_TILE merged positions, one tile per warp at a
+// time, with no block-wide synchronisation: the warp takes a ticket, loads
+// its tile, merges MG_IPT positions per lane, sums runs with a segmented scan
+// over the lanes (the partition kernel has already located the spawn records
+// that continue the tile's last run past its end; the warp sums them with
+// coalesced loads), and finds its output offset by a warp-parallel decoupled
+// look-back over earlier tiles.  Runs whose head lies in an earlier tile are
+// left to that tile.
 #pragma once
 
 #include "common.cuh"
@@ -25,8 +27,9 @@ namespace ddq {
 
 constexpr int MG_TPB = 256;
 constexpr int MG_WARPS = MG_TPB / 32;
-constexpr int MG_IPT = 7;
-constexpr int MG_TILE = MG_TPB * MG_IPT;
+constexpr int MG_IPT = 7;                  // odd: the lanes' merge cursors spread over the banks
+constexpr int MG_TILE = 32 * MG_IPT;       // merged positions per warp tile
+constexpr int MG_PCHUNK = 8;               // tile boundaries per partition thread
 
 // merge-path split of output diagonal `diag`: number of L elements among the
 // first `diag` merged elements (L before S on equal keys)
@@ -55,10 +58,30 @@ __global__ void k_merge_partition(const Rec *__restrict__ L, const T *__restrict
     if (R > rcap) R = rcap;
     const int64_t tot = M + R;
     const int64_t ntiles = (tot + MG_TILE - 1) / MG_TILE;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+    // each thread takes MG_PCHUNK consecutive boundaries: after the first full
+    // search the next split lies within one tile of the previous one
+    const int64_t nchunks = (ntiles + MG_PCHUNK) / MG_PCHUNK;
+    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t t = ch * MG_PCHUNK, aprev = -1; t <= ntiles && t < (ch + 1) * MG_PCHUNK; ++t) {
         int64_t diag = t * MG_TILE;
         if (diag > tot) diag = tot;
-        const int64_t a = merge_split(L, M, S, R, diag);
+        int64_t a;
+        if (aprev < 0) {
+            a = merge_split(L, M, S, R, diag);
+        } else {
+            // merge path split of diag inside [aprev, aprev + MG_TILE]
+            int64_t lo = aprev, hi = aprev + MG_TILE;
+            if (lo < diag - R) lo = diag - R;
+            if (hi > diag) hi = diag;
+            if (hi > M) hi = M;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (L[mid].key <= RecTraits<T>::key(S[diag - 1 - mid])) lo = mid + 1;
+                else hi = mid;
+            }
+            a = lo;
+        }
+        aprev = a;
         const int64_t b = diag - a;
         splits[t] = a;
         int64_t e = b;
@@ -70,8 +93,16 @@ __global__ void k_merge_partition(const Rec *__restrict__ L, const T *__restrict
                 if (k2 > last) last = k2;
             }
             if (RecTraits<T>::key(S[b]) == last) {
-                // first record after b with a larger key
-                int64_t lo = b + 1, hi = R;
+                // first record after b with a larger key: gallop, then bisect
+                // invariant: S[b, lo) all carry the key; the first other key is in [lo, hi]
+                int64_t lo = b + 1, step = 1, hi = R;
+                for (;;) {
+                    if (lo >= R || RecTraits<T>::key(S[lo]) != last) { hi = lo < R ? lo : R; break; }
+                    const int64_t nxt = lo + step;
+                    if (nxt >= R || RecTraits<T>::key(S[nxt]) != last) { hi = nxt < R ? nxt : R; ++lo; break; }
+                    lo = nxt + 1;
+                    step <<= 1;
+                }
                 while (lo < hi) {
                     const int64_t mid = (lo + hi) >> 1;
                     if (RecTraits<T>::key(S[mid]) == last) lo = mid + 1;
@@ -130,8 +161,8 @@ __device__ __forceinline__ SegAgg seg_shfl_up(const SegAgg &a, int off) {
     return r;
 }
 
-// Exclusive segmented scan over the threads of the block (tmp: one slot per warp).
-__device__ __forceinline__ SegAgg seg_block_exclusive(const SegAgg &mine, SegAgg *tmp, int lane, int warp) {
+// Exclusive segmented scan over the lanes of a warp.
+__device__ __forceinline__ SegAgg seg_warp_exclusive(const SegAgg &mine, int lane) {
     SegAgg inc = mine;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -140,27 +171,20 @@ __device__ __forceinline__ SegAgg seg_block_exclusive(const SegAgg &mine, SegAgg
     }
     SegAgg exc = seg_shfl_up(inc, 1);
     if (lane == 0) exc = seg_identity();
-    if (lane == 31) tmp[warp] = inc;
-    __syncthreads();
-    SegAgg pre = seg_identity();
-    for (int w = 0; w < warp; ++w) pre = seg_combine(pre, tmp[w]);
-    return seg_combine(pre, exc);
+    return exc;
 }
 
-struct MergeShared {
+struct MergeWarp {
     uint64_t key[MG_TILE];            // L keys, then S keys with the flag bit; later the output keys
     int2 val[MG_TILE];                // (re, im) of the same elements; later the output populations
+};
+
+struct MergeShared {
+    MergeWarp w[MG_WARPS];
     unsigned long long est[NOBS_MAX];
     uint64_t bond_m[MAXB];
     int8_t bond_a[MAXB], bond_b[MAXB];
     int8_t pair_bond[MAXN * MAXN];
-    uint32_t scan_tmp[MG_WARPS];
-    SegAgg seg_tmp[MG_WARPS];
-    int32_t first_head[MG_TPB];
-    int64_t rem_f[2], rem_u[2];       // remainder of the tile's last run past the tile end
-    int64_t tile, a0, a1, out_base, rem_e;
-    uint64_t prev_key;
-    int32_t has_prev;
 };
 
 __device__ __forceinline__ void add_estimators(MergeShared &s, const RunParams &P, uint64_t key, int32_t re,
@@ -199,7 +223,7 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MG_TPB)
+__global__ void __launch_bounds__(MG_TPB, 4)
 k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__restrict__ S,
         Rec *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
         const int64_t *__restrict__ rem_end, uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
@@ -226,76 +250,69 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
         s.bond_b[q] = (int8_t)P.bond_b[q];
     }
     for (int q = tid; q < N * N; q += MG_TPB) s.pair_bond[q] = P.pair_bond[q];
+    __syncthreads();
+    MergeWarp &ws = s.w[warp];
     int64_t my_w = 0, my_m = 0;
     uint32_t local_status = 0;
 
     for (;;) {
-        __syncthreads();
-        if (tid == 0) {
-            const int64_t tile = (int64_t)atomicAdd(&st->tickets[8], 1u);
-            s.tile = tile;
-            if (tile < ntiles) {
-                const int64_t d0 = tile * MG_TILE;
-                s.a0 = splits[tile];
-                s.a1 = splits[tile + 1];
-                s.rem_e = rem_end[tile + 1];
-                const int64_t b0 = d0 - s.a0;
-                uint64_t pk = 0;
-                int hp = 0;
-                if (s.a0 > 0) { pk = L[s.a0 - 1].key; hp = 1; }
-                if (b0 > 0) {
-                    const uint64_t k2 = TR::key(S[b0 - 1]);
-                    if (!hp || k2 > pk) pk = k2;
-                    hp = 1;
-                }
-                s.prev_key = pk;
-                s.has_prev = hp;
-            }
-        }
-        __syncthreads();
-        const int64_t tile = s.tile;
+        int64_t tile = 0;
+        if (lane == 0) tile = (int64_t)atomicAdd(&st->tickets[8], 1u);
+        tile = __shfl_sync(0xFFFFFFFFu, tile, 0);
         if (tile >= ntiles) break;
         const int64_t d0 = tile * MG_TILE;
         const int64_t d1 = (d0 + MG_TILE < tot) ? d0 + MG_TILE : tot;
-        const int64_t a0 = s.a0, a1 = s.a1;
+        const int64_t a0 = splits[tile], a1 = splits[tile + 1], rem_e = rem_end[tile + 1];
         const int64_t b0 = d0 - a0, b1 = d1 - a1;
         const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
-        // load the tile's L and S elements (S keys keep their flag in bit 63)
-        for (int q = tid; q < na; q += MG_TPB) {
-            const Rec v = L[a0 + q];
-            s.key[q] = v.key;
-            s.val[q] = make_int2(v.re, v.im);
-        }
-        for (int q = tid; q < nb; q += MG_TPB) {
-            const T v = S[b0 + q];
-            s.key[na + q] = TR::key(v) | (TR::flag(v) ? FLAG_BIT : 0ull);
-            s.val[na + q] = make_int2(TR::re(v), TR::im(v));
-        }
-        if (warp == 0) {
-            // spawn records past the tile end that continue its last run
-            int64_t f0 = 0, f1 = 0, u0 = 0, u1 = 0;
-            for (int64_t q = b1 + lane; q < s.rem_e; q += 32) {
-                const T g = S[q];
-                if (TR::flag(g)) { f0 += TR::re(g); f1 += TR::im(g); }
-                else { u0 += TR::re(g); u1 += TR::im(g); }
+        // key of the merged element before the tile
+        uint64_t pk = 0;
+        int hp = 0;
+        if (lane == 0) {
+            if (a0 > 0) { pk = L[a0 - 1].key; hp = 1; }
+            if (b0 > 0) {
+                const uint64_t k2 = TR::key(S[b0 - 1]);
+                if (!hp || k2 > pk) pk = k2;
+                hp = 1;
             }
+        }
+        pk = __shfl_sync(0xFFFFFFFFu, pk, 0);
+        hp = __shfl_sync(0xFFFFFFFFu, hp, 0);
+        // load the tile's L and S elements (S keys keep their flag in bit 63)
+        for (int q = lane; q < na; q += 32) {
+            const Rec v = L[a0 + q];
+            ws.key[q] = v.key;
+            ws.val[q] = make_int2(v.re, v.im);
+        }
+        for (int q = lane; q < nb; q += 32) {
+            const T v = S[b0 + q];
+            ws.key[na + q] = TR::key(v) | (TR::flag(v) ? FLAG_BIT : 0ull);
+            ws.val[na + q] = make_int2(TR::re(v), TR::im(v));
+        }
+        // spawn records past the tile end that continue its last run
+        int64_t rf0 = 0, rf1 = 0, ru0 = 0, ru1 = 0;
+        for (int64_t q = b1 + lane; q < rem_e; q += 32) {
+            const T g = S[q];
+            if (TR::flag(g)) { rf0 += TR::re(g); rf1 += TR::im(g); }
+            else { ru0 += TR::re(g); ru1 += TR::im(g); }
+        }
+        if (rem_e > b1) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                f0 += __shfl_xor_sync(0xFFFFFFFFu, f0, off);
-                f1 += __shfl_xor_sync(0xFFFFFFFFu, f1, off);
-                u0 += __shfl_xor_sync(0xFFFFFFFFu, u0, off);
-                u1 += __shfl_xor_sync(0xFFFFFFFFu, u1, off);
+                rf0 += __shfl_xor_sync(0xFFFFFFFFu, rf0, off);
+                rf1 += __shfl_xor_sync(0xFFFFFFFFu, rf1, off);
+                ru0 += __shfl_xor_sync(0xFFFFFFFFu, ru0, off);
+                ru1 += __shfl_xor_sync(0xFFFFFFFFu, ru1, off);
             }
-            if (lane == 0) { s.rem_f[0] = f0; s.rem_f[1] = f1; s.rem_u[0] = u0; s.rem_u[1] = u1; }
         }
-        __syncthreads();
-        const uint64_t *kL = s.key;
-        const uint64_t *kS = s.key + na;
-        const int2 *vL = s.val;
-        const int2 *vS = s.val + na;
+        __syncwarp();
+        const uint64_t *kL = ws.key;
+        const uint64_t *kS = ws.key + na;
+        const int2 *vL = ws.val;
+        const int2 *vS = ws.val + na;
 
-        // ---- 1. merge: this thread's MG_IPT merged positions, in registers ----
-        const int dloc = tid * MG_IPT;
+        // ---- 1. merge: this lane's MG_IPT merged positions, in registers ----
+        const int dloc = lane * MG_IPT;
         const int nt = na + nb;
         uint64_t ik[MG_IPT];
         int2 iv[MG_IPT];
@@ -310,10 +327,9 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                 else hi = mid;
             }
             int ia = lo, ib = dloc - lo;
-            // key of the merged element just before this thread's range
             uint64_t prev = 0;
             bool hprev = false;
-            if (dloc == 0) { prev = s.prev_key; hprev = s.has_prev != 0; }
+            if (dloc == 0) { prev = pk; hprev = hp != 0; }
             else {
                 if (ia > 0) { prev = kL[ia - 1]; hprev = true; }
                 if (ib > 0) {
@@ -344,10 +360,11 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                     if (fromL) ++ia; else ++ib;
                 }
             }
+        } else {
+#pragma unroll
+            for (int k = 0; k < MG_IPT; ++k) { ik[k] = 0; iv[k] = make_int2(0, 0); }
         }
-        // ---- 2. segmented reduction of the runs across the block -------------
-        // Per run: sum of its L_t population and initiator records (f), sum of
-        // its non-initiator records (u), and whether its head is in L_t.
+        // ---- 2. segmented reduction of the runs over the lanes ---------------
         SegAgg tail = seg_identity();
 #pragma unroll
         for (int k = 0; k < MG_IPT; ++k) {
@@ -356,10 +373,9 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                 seg_add(tail, iv[k], ((lmask | fmask) >> k) & 1u);
             }
         }
-        const SegAgg carry = seg_block_exclusive(tail, s.seg_tmp, lane, warp);
-        s.first_head[tid] = nk > 0 ? (int)(hmask & 1u) : 1;
-        __syncthreads();
-        const bool next_thread_head = tid + 1 < MG_TPB ? s.first_head[tid + 1] != 0 : true;
+        const SegAgg carry = seg_warp_exclusive(tail, lane);
+        const int my_first_head = nk > 0 ? (int)(hmask & 1u) : 1;
+        const int next_first_head = __shfl_down_sync(0xFFFFFFFFu, my_first_head, 1);
         SegAgg run = carry;
         bool owned = carry.h != 0;       // the open run has its head in this tile
         uint32_t omask = 0;
@@ -372,14 +388,14 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                 seg_add(run, iv[k], ((lmask | fmask) >> k) & 1u);
                 bool ends;
                 if (k + 1 < nk) ends = ((hmask >> (k + 1)) & 1u) != 0u;
-                else if (dloc + k + 1 < nt) ends = next_thread_head;
+                else if (dloc + k + 1 < nt) ends = next_first_head != 0;
                 else {
                     // the tile's last run: add its spawn records that follow the tile
                     ends = true;
-                    run.fre += s.rem_f[0];
-                    run.fim += s.rem_f[1];
-                    run.ure += s.rem_u[0];
-                    run.uim += s.rem_u[1];
+                    run.fre += rf0;
+                    run.fim += rf1;
+                    run.ure += ru0;
+                    run.uim += ru1;
                 }
                 if (ends && owned) {
                     const bool open = run.hasL || no_init || ((ik[k] & nmask) == (ik[k] >> N));
@@ -393,67 +409,53 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                 }
             }
         }
+        // ---- 3. compaction: warp scan of the output counts, look-back --------
         const int nout = __popc(omask);
-        // block scan of output counts
         int x = nout;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(0xFFFFFFFFu, x, off);
             if (lane >= off) x += y;
         }
-        __syncthreads();                 // everyone is done reading the tile
-        if (lane == 31) s.scan_tmp[warp] = (uint32_t)x;
-        __syncthreads();
-        uint32_t pre = 0, total = 0;
-        for (int w = 0; w < MG_WARPS; ++w) {
-            const uint32_t v = s.scan_tmp[w];
-            if (w < warp) pre += v;
-            total += v;
-        }
-        uint32_t my_off = pre + (uint32_t)(x - nout);
+        const uint32_t total = (uint32_t)__shfl_sync(0xFFFFFFFFu, x, 31);
+        __syncwarp();                    // every lane is done reading the tile
+        uint32_t my_off = (uint32_t)(x - nout);
 #pragma unroll
         for (int k = 0; k < MG_IPT; ++k) {
             if ((omask >> k) & 1u) {
-                s.key[my_off] = ik[k];
-                s.val[my_off] = oval[k];
+                ws.key[my_off] = ik[k];
+                ws.val[my_off] = oval[k];
                 ++my_off;
             }
         }
-        // output offset of the tile: warp-parallel decoupled look-back
-        if (warp == 0) {
-            uint64_t *myw = lookback + tile;
-            if (lane == 0) lb_store(myw, lb_pack(epoch, tile == 0 ? LB_INC : LB_AGG, total));
-            uint64_t excl = 0;
-            if (tile > 0) {
-                for (int64_t jt = tile - 1;; jt -= 32) {
-                    const int64_t jj = jt - lane;
-                    const uint64_t w = jj >= 0 ? lb_wait(lookback + jj, epoch, &st->status)
-                                               : lb_pack(epoch, LB_INC, 0u);
-                    const unsigned inc = __ballot_sync(0xFFFFFFFFu, ((w >> 32) & 3ull) != LB_AGG);
-                    if (inc) {
-                        const int first = __ffs(inc) - 1;
-                        excl += warp_sum_u64(lane <= first ? (uint64_t)(uint32_t)w : 0ull);
-                        break;
-                    }
-                    excl += warp_sum_u64((uint64_t)(uint32_t)w);
+        uint64_t *myw = lookback + tile;
+        if (lane == 0) lb_store(myw, lb_pack(epoch, tile == 0 ? LB_INC : LB_AGG, total));
+        uint64_t excl = 0;
+        if (tile > 0) {
+            for (int64_t jt = tile - 1;; jt -= 32) {
+                const int64_t jj = jt - lane;
+                const uint64_t w = jj >= 0 ? lb_wait(lookback + jj, epoch, &st->status) : lb_pack(epoch, LB_INC, 0u);
+                const unsigned inc = __ballot_sync(0xFFFFFFFFu, ((w >> 32) & 3ull) != LB_AGG);
+                if (inc) {
+                    const int first = __ffs(inc) - 1;
+                    excl += warp_sum_u64(lane <= first ? (uint64_t)(uint32_t)w : 0ull);
+                    break;
                 }
-                if (lane == 0) lb_store(myw, lb_pack(epoch, LB_INC, (uint32_t)(excl + total)));
+                excl += warp_sum_u64((uint64_t)(uint32_t)w);
             }
-            if (lane == 0) {
-                s.out_base = (int64_t)excl;
-                if (tile == ntiles - 1) st->M_next = (int64_t)(excl + total);
-            }
+            if (lane == 0) lb_store(myw, lb_pack(epoch, LB_INC, (uint32_t)(excl + total)));
         }
-        __syncthreads();
-        const int64_t ob = s.out_base;
+        if (lane == 0 && tile == ntiles - 1) st->M_next = (int64_t)(excl + total);
+        __syncwarp();
+        const int64_t ob = (int64_t)excl;
         if (ob + (int64_t)total > mcap) {
-            if (tid == 0) local_status |= ST_CAPACITY | ST_CAP_LIST;
+            if (lane == 0) local_status |= ST_CAPACITY | ST_CAP_LIST;
         } else {
-            for (uint32_t q = tid; q < total; q += MG_TPB) {
+            for (uint32_t q = lane; q < total; q += 32) {
                 Rec v;
-                v.key = s.key[q];
-                v.re = s.val[q].x;
-                v.im = s.val[q].y;
+                v.key = ws.key[q];
+                v.re = ws.val[q].x;
+                v.im = ws.val[q].y;
                 out[ob + q] = v;
                 my_w += iabs64(v.re) + iabs64(v.im);
                 my_m += 1;
@@ -461,6 +463,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                 if (i == j || __popcll(i ^ j) == 2) add_estimators(s, P, v.key, v.re, v.im);
             }
         }
+        __syncwarp();
     }
     // flush the block's estimator partials
 #pragma unroll

@@ -85,7 +85,7 @@ k_digit_histogram(const T *__restrict__ in, DevState *__restrict__ st, int npass
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RX_TPB)
+__global__ void __launch_bounds__(RX_TPB, 3)
 k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict__ st,
              uint64_t *__restrict__ lookback, int pass, int shift, int64_t cap) {
     using TR = RecTraits<T>;

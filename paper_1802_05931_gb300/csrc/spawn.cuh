@@ -99,6 +99,8 @@ struct SpawnShared {
     WarpScratch ws[SP_WARPS];
     int32_t incl[SP_WARPS][32];
     int32_t dre[SP_WARPS][32], dim[SP_WARPS][32];
+    uint64_t qv[SP_WARPS][64];        // queued spawn draws: scaled uniform v
+    uint32_t qm[SP_WARPS][64];        //   and configuration | part << 5 | negative << 6
 };
 
 struct SpawnCtx {
@@ -392,6 +394,51 @@ __device__ __forceinline__ uint32_t attempt_word(uint4 x0, uint4 &xb, uint32_t &
     }
 }
 
+// Resolve the first n queued spawn draws of the warp, one per lane: the move
+// (ket, bra or jump segment, then the group and the bond inside it), the child
+// configuration and its signed unit, appended as a spawn record.
+template <typename T, typename MT>
+__device__ __forceinline__ void spawn_drain(SpawnShared &s, const SpawnCtx &c, int warp, int lane, int n, int N,
+                                            T *out, int64_t cap, DevState *st, int npass) {
+    if (lane < n) {
+        const uint64_t v = s.qv[warp][lane];
+        const uint32_t meta = s.qm[warp][lane];
+        const int o = (int)(meta & 31u);
+        const int part = (int)((meta >> 5) & 1u);
+        const int sig = (meta & 64u) ? -1 : 1;
+        const LightSoA &q = s.ws[warp].le;
+        const uint32_t qi = q.i[o], qj = q.j[o];
+        const uint64_t qT = q.T[o], qTket = q.Tket[o], qTbra = q.Tbra[o];
+        uint32_t ci = qi, cj = qj;
+        int cre = 0, cim = 0;
+        if (v < qTket + qTbra) {
+            const bool ket = v < qTket;
+            const MT A = (MT)(ket ? q.Ai[o] : q.Aj[o]);
+            const MT X1 = (MT)q.X1[o], X2 = (MT)q.X2[o];
+            const uint64_t cnt8 = ket ? q.gk[o] : q.gb[o];
+            const uint64_t vs = ket ? v : v - qTket;
+            const int p = qT <= 0xFFFFFFFFull ? seg_select32<MT>(c, s.urate32, s.uinv, cnt8, A, X1, X2, (uint32_t)vs)
+                                              : seg_select<MT>(c, s.urate8, cnt8, A, X1, X2, vs);
+            const int k = p >> 1;
+            const int other = (p & 1) ? s.dn[k] : s.rn[k];
+            const uint32_t m = (1u << k) | (1u << other);
+            const int hs = s.sgn_h[(A >> p) & 1u];
+            const int gsg = ket ? -hs : hs;
+            if (ket) ci ^= m; else cj ^= m;
+            if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
+        } else {
+            const uint32_t idx = small_quotient(v - qTket - qTbra, c.jump_q);
+            const int k = select_bit((uint64_t)(qi & qj), idx);
+            ci &= ~(1u << k);
+            cj &= ~(1u << k);
+            if (part == 0) cre = sig; else cim = sig;
+        }
+        emit(s, warp, make_spawn<T>(((uint64_t)cj << N) | (uint64_t)ci, q.init[o] != 0, cre, cim), out, cap, st,
+             npass);
+    }
+    __syncwarp();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SP_TPB, 3)
 k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *__restrict__ L,
@@ -505,30 +552,37 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
         __syncwarp();
 
         // ---- light walkers, spread over the lanes ----------------------------
+        // Death / cloning and the Re <-> Im transfer are applied per walker; a
+        // draw that lands below the total rate is queued, and the move
+        // searches run 32 at a time with every lane busy.
+        int qn = 0;                      // queued spawn draws (same value in every lane)
         for (int base = 0; base < Wl; base += 32) {
             const int g = base + lane;
-            if (g < Wl) {
+            const bool act = g < Wl;
+            int owner = 0, part = 0, sig = 1;
+            uint32_t natt = 0;
+            uint64_t qT = 0;
+            uint4 x = make_uint4(0u, 0u, 0u, 0u), ctr = x;
+            if (act) {
                 int lo = 0, hi = 31;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
                     if (s.incl[warp][mid] > g) hi = mid; else lo = mid + 1;
                 }
-                const int owner = lo;
+                owner = lo;
                 const LightSoA &q = s.ws[warp].le;
-                const int o = owner;
-                const uint32_t qi = q.i[o], qj = q.j[o];
-                const int nre_o = q.nre[o];
+                const int nre_o = q.nre[owner];
                 const int local = g - (owner ? s.incl[warp][owner - 1] : 0);
-                const int part = local < nre_o ? 0 : 1;
+                part = local < nre_o ? 0 : 1;
                 const uint32_t w = (uint32_t)(part ? local - nre_o : local);
-                const int sig = (part ? q.im[o] : q.re[o]) < 0 ? -1 : 1;
-                const uint4 ctr = make_uint4(qi, qj, w, (uint32_t)part << 16);
-                const uint4 x = philox4x32_10(ctr, k0, k1);
-                const int cd = q.cd[o], adz = q.adz[o];
+                sig = (part ? q.im[owner] : q.re[owner]) < 0 ? -1 : 1;
+                ctr = make_uint4(q.i[owner], q.j[owner], w, (uint32_t)part << 16);
+                x = philox4x32_10(ctr, k0, k1);
+                const int cd = q.cd[owner], adz = q.adz[owner];
                 const int cnt = (int)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
                 const int cc = (int)s.cross_int[adz] + ((uint64_t)x.z < s.cross_frac[adz] ? 1 : 0);
                 const int ddeath = -s.d_sgn[cd] * sig * cnt;
-                const int dcross = sig * q.sgn_d[o] * cc;
+                const int dcross = sig * q.sgn_d[owner] * cc;
                 if (part == 0) {
                     if (ddeath) atomicAdd(&s.dre[warp][owner], ddeath);
                     if (dcross) atomicAdd(&s.dim[warp][owner], dcross);
@@ -536,45 +590,45 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                     if (ddeath) atomicAdd(&s.dim[warp][owner], ddeath);
                     if (dcross) atomicAdd(&s.dre[warp][owner], -dcross);
                 }
-                uint4 xb = x;
-                uint32_t blk = 0;
-                const uint64_t natt = q.natt[o];
-                const uint64_t qT = q.T[o], qTket = q.Tket[o], qTbra = q.Tbra[o];
-                const bool qinit = q.init[o] != 0;
-                for (uint64_t a = 0; a < natt; ++a) {
+                natt = q.natt[owner];
+                qT = q.T[owner];
+            }
+            uint32_t nmax = natt;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(0xFFFFFFFFu, nmax, off));
+            uint4 xb = x;
+            uint32_t blk = 0;
+            for (uint32_t a = 0; a < nmax; ++a) {
+                bool ev = false;
+                uint64_t v = 0;
+                if (a < natt) {
                     const uint32_t u = attempt_word(x, xb, blk, a, ctr, k0, k1);
-                    const uint64_t v = (uint64_t)u * natt;
-                    if (v >= qT) continue;
-                    uint32_t ci = qi, cj = qj;
-                    int cre = 0, cim = 0;
-                    if (v < qTket + qTbra) {
-                        const bool ket = v < qTket;
-                        const MT A = (MT)(ket ? q.Ai[o] : q.Aj[o]);
-                        const MT X1 = (MT)q.X1[o], X2 = (MT)q.X2[o];
-                        const uint64_t cnt8 = ket ? q.gk[o] : q.gb[o];
-                        const uint64_t vs = ket ? v : v - qTket;
-                        const int p = qT <= 0xFFFFFFFFull
-                                          ? seg_select32<MT>(c, s.urate32, s.uinv, cnt8, A, X1, X2, (uint32_t)vs)
-                                          : seg_select<MT>(c, s.urate8, cnt8, A, X1, X2, vs);
-                        const int k = p >> 1;
-                        const int other = (p & 1) ? s.dn[k] : s.rn[k];
-                        const uint32_t m = (1u << k) | (1u << other);
-                        const int hs = s.sgn_h[(A >> p) & 1u];
-                        const int gsg = ket ? -hs : hs;
-                        if (ket) ci ^= m; else cj ^= m;
-                        if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
-                    } else {
-                        const uint32_t idx = small_quotient(v - qTket - qTbra, c.jump_q);
-                        const int k = select_bit((uint64_t)(qi & qj), idx);
-                        ci &= ~(1u << k);
-                        cj &= ~(1u << k);
-                        if (part == 0) cre = sig; else cim = sig;
-                    }
-                    emit(s, warp, make_spawn<T>(((uint64_t)cj << N) | (uint64_t)ci, qinit, cre, cim), out,
-                         cap, st, npass);
+                    v = (uint64_t)u * natt;
+                    ev = v < qT;
+                }
+                const unsigned em = __ballot_sync(0xFFFFFFFFu, ev);
+                if (em == 0u) continue;
+                if (ev) {
+                    const int pos = qn + __popc(em & ((1u << lane) - 1u));
+                    s.qv[warp][pos] = v;
+                    s.qm[warp][pos] = (uint32_t)owner | ((uint32_t)part << 5) | (sig < 0 ? 64u : 0u);
+                }
+                qn += __popc(em);
+                __syncwarp();
+                if (qn >= 32) {
+                    spawn_drain<T, MT>(s, c, warp, lane, 32, N, out, cap, st, npass);
+                    qn -= 32;
+                    // move the rest of the queue to the front
+                    uint64_t rv = 0;
+                    uint32_t rm = 0;
+                    if (lane < qn) { rv = s.qv[warp][32 + lane]; rm = s.qm[warp][32 + lane]; }
+                    __syncwarp();
+                    if (lane < qn) { s.qv[warp][lane] = rv; s.qm[warp][lane] = rm; }
+                    __syncwarp();
                 }
             }
         }
+        if (qn > 0) spawn_drain<T, MT>(s, c, warp, lane, qn, N, out, cap, st, npass);
         __syncwarp();
         if (light) {
             const int64_t re2 = (int64_t)rec.re + s.dre[warp][lane], im2 = (int64_t)rec.im + s.dim[warp][lane];
