@@ -36,8 +36,9 @@ METRIC = "walker-steps/s"
 UNIT = "walker-steps/s"
 WORKLOAD = dict(Lx=4, Ly=4, periodic=1, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, n_a=3,
                 guide_kind=2, guide_p=1.5, control=1, seed=3)
-WORKLOAD_NAME = "4x4 periodic XYZ, Jx=0.9 Jy=Jz=1 gamma=1, dt=0.005, n_a=3, site-product guide exp(-1.5), " \
-                "total-walker shift target 1e8, seed 3"
+def workload_name(target=1e8):
+    return ("4x4 periodic XYZ, Jx=0.9 Jy=Jz=1 gamma=1, dt=0.005, n_a=3, site-product guide exp(-1.5), "
+            "total-walker shift target %.0e, seed 3" % target).replace("e+0", "e")
 
 
 def parse():
@@ -154,20 +155,25 @@ def peak_hbm():
         return 6800.0, "fallback"
 
 
-def profile_traffic():
-    """DRAM bytes per unit of work of each kernel from the committed ncu summary
-    (profiles/traffic_per_unit.txt: '<kernel> <bytes per unit> <unit>'), if present."""
+def profile_counters():
+    """Per-unit ncu counters of each kernel from the committed summary
+    profiles/kernel_counters.txt (lines '<kernel> <counter> <value>'); a kernel
+    whose code changed after its capture has no line there."""
     out = {}
-    path = os.path.join(ROOT, "profiles", "traffic_per_unit.txt")
+    path = os.path.join(ROOT, "profiles", "kernel_counters.txt")
     try:
         with open(path) as f:
             for line in f:
                 if line.strip() and not line.startswith("#"):
-                    k, v, u = line.split()[:3]
-                    out[k] = (float(v), u)
+                    k, c, v = line.split()[:3]
+                    out[(k, c)] = float(v)
     except Exception:
         pass
     return out
+
+
+SMS = 152                 # GB300 streaming multiprocessors
+SCHEDULERS_PER_SM = 4     # warp schedulers per SM, one warp instruction issued per cycle each
 
 
 # ----------------------------------------------------------------------------- oracle sample
@@ -216,7 +222,7 @@ def reference_arm(args, world, rank, pg):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": info["steps"], "warmup": args.warmup, "ms_per_step": 1e3 * info["seconds"] / info["steps"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_target": info["target"]},
+            "data": "synthetic", "config": {"workload": workload_name(), "sample_target": info["target"]},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                              "host": cpu_cores_desc()},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -260,10 +266,13 @@ def gpu_arm(args, world, rank, local, pg):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # the profiler range marks the timed steps for ncu --profile-from-start off
+    torch.cuda.profiler.start()
     e0.record(stream)
     run.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     barrier(pg)
     clocks = sampler.stop() if sampler else None
     ms = e0.elapsed_time(e1)
@@ -285,7 +294,6 @@ def gpu_arm(args, world, rank, local, pg):
     alg = {"spawn_death": (24 * dM + rb * dR) / K,
            "radix_pass": 2 * rb * dR / K,
            "merge": (16 * (dM + dMn) + rb * dR) / K}
-    per_unit = {"spawn_death": (dM + dR) / K, "radix_pass": dR / K, "merge": (dM + dR) / K}
     kern = {}
     for k, (kms, n) in timing.items():
         if n:
@@ -295,14 +303,35 @@ def gpu_arm(args, world, rank, local, pg):
                 kern[k]["achieved_gbs"] = alg[k] / (kms / n / 1e3) / 1e9
     dom = max((k for k in kern if k in alg), key=lambda k: timing[k][0])
     peak, peak_src = peak_hbm()
-    achieved = kern[dom]["achieved_gbs"]
-    traffic = None
-    tr = profile_traffic().get(dom)
-    if tr is not None:
-        traffic = tr[0] * per_unit[dom]
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"
-                if peak_src == "measured" else "fallback 6.8 TB/s"}
+    counters = profile_counters()
+    # DRAM traffic per launch: the captured DRAM bytes per algorithmic byte of
+    # the kernel, times this run's algorithmic bytes per launch
+    ratio = counters.get((dom, "dram_bytes_per_alg_byte"))
+    traffic = ratio * alg[dom] if ratio is not None else None
+    for k in kern:
+        r = counters.get((k, "dram_bytes_per_alg_byte"))
+        if r is not None and k in alg:
+            kern[k]["traffic_bytes_per_launch"] = r * alg[k]
+    walkers_per_launch = dws / K
+    if dom == "spawn_death" and (dom, "warp_inst_per_walker") in counters:
+        # issue-bound kernel: warp instructions per second against the issue
+        # rate of every warp scheduler at the SM clock sampled during the run
+        ipw = counters[(dom, "warp_inst_per_walker")]
+        mhz = clocks["sm_mhz"] if clocks else 2070.0
+        ach = ipw * walkers_per_launch / (kern[dom]["ms_per_launch"] / 1e3) / 1e9
+        pk = SMS * SCHEDULERS_PER_SM * mhz * 1e6 / 1e9
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": pk, "unit": "Gwarp-inst/s",
+                    "frac": ach / pk, "traffic": traffic,
+                    "peak_source": "derived: %d SMs x %d schedulers x %.0f MHz (sampled SM clock)"
+                                   % (SMS, SCHEDULERS_PER_SM, mhz),
+                    "warp_inst_per_walker": ipw,
+                    "hbm_achieved_gbs": kern[dom]["achieved_gbs"], "hbm_peak_gbs": peak}
+    else:
+        achieved = kern[dom]["achieved_gbs"]
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                    else "fallback 6.8 TB/s"}
     sortmerge_ms = sum(timing[k][0] for k in ("radix_pass", "merge_partition", "merge")) / K
     sortmerge_bytes = alg["radix_pass"] * (timing["radix_pass"][1] / K) + alg["merge"]
     # end to end through the C-ABI with host buffers: import, step, export, estimators
@@ -345,7 +374,7 @@ def gpu_arm(args, world, rank, local, pg):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "walkers_per_step": dws / K, "entries_per_step": dM / K,
+            "config": {"workload": workload_name(args.target), "walkers_per_step": dws / K, "entries_per_step": dM / K,
                        "spawn_records_per_step": dR / K, "shift": st.shift, "t": st.t,
                        "l2": "inputs larger than L2 (walker list and spawn buffer are GBs)",
                        "parallelism": "replicas x%d" % world},

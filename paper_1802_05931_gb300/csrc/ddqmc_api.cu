@@ -270,7 +270,8 @@ Rec *host_stage(ddqmc_run *r, int64_t n) {
     return r->hstage;
 }
 
-constexpr size_t SP_SMEM = sizeof(SpawnShared);
+constexpr size_t SP_SMEM = sizeof(SpawnShared<Rec>);
+constexpr size_t SPP_SMEM = sizeof(SpawnShared<uint64_t>);
 constexpr size_t RX_SMEM = sizeof(RadixShared<Rec>);
 constexpr size_t RXP_SMEM = sizeof(RadixShared<uint64_t>);
 constexpr size_t MG_SMEM = sizeof(MergeShared);
@@ -283,7 +284,7 @@ void launch_step(ddqmc_run *r, Rec *Lc, Rec *Ln, const std::function<void(int, i
     T *sp1 = reinterpret_cast<T *>(r->Sp[1]);
     const size_t rx_smem = sizeof(RadixShared<T>);
     mark(0, 0);
-    k_spawn_death<T><<<r->g_spawn, SP_TPB, SP_SMEM, r->stream>>>(r->dP, r->dS, Lc, sp0, r->rcap);
+    k_spawn_death<T><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(r->dP, r->dS, Lc, sp0, r->rcap);
     mark(0, 1);
     mark(1, 0);
     for (int p = 0; p < P.npass; ++p)
@@ -546,14 +547,14 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     if (sms < 1) sms = 1;
     r->packed = 2 * r->hp.N <= 32;
     bool ok = cudaFuncSetAttribute(k_spawn_death<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_spawn_death<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_spawn_death<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPP_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_radix_pass<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_radix_pass<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RXP_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_merge<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_merge<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
     if (r->packed) {
-        r->g_spawn = occupancy_grid((const void *)k_spawn_death<uint64_t>, SP_TPB, SP_SMEM, sms);
+        r->g_spawn = occupancy_grid((const void *)k_spawn_death<uint64_t>, SP_TPB, SPP_SMEM, sms);
         r->g_radix = occupancy_grid((const void *)k_radix_pass<uint64_t>, RX_TPB, RXP_SMEM, sms);
         r->g_merge = occupancy_grid((const void *)k_merge<uint64_t>, MG_TPB, MG_SMEM, sms);
     } else {

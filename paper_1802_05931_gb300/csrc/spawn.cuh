@@ -79,8 +79,8 @@ union WarpScratch {
     HeavyTables hv;
 };
 
-struct SpawnShared {
-    uint64_t rate_q[MAXB][2][4];
+// Constant tables of one step, staged in shared memory.
+struct SpawnTables {
     uint64_t bond_m[MAXB];
     uint64_t cross_frac[2 * MAXB + 1];
     uint64_t d_frac[2 * MAXN + 1];
@@ -93,18 +93,25 @@ struct SpawnShared {
     int32_t d_sgn[2 * MAXN + 1];
     int8_t bond_a[MAXB], bond_b[MAXB];
     int8_t rn[MAXN + 1], dn[MAXN + 1];
-    uint32_t hist[MAXPASS][256];
+};
+
+// Shared memory of the spawn kernel for spawn records of type T; packed
+// records (keys of at most 32 bits) need at most four digit passes.
+template <typename T>
+struct SpawnShared : SpawnTables {
+    static constexpr int NP = sizeof(T) == 8 ? 4 : MAXPASS;
+    uint32_t hist[NP][256];
     int32_t stage_n[SP_WARPS];
-    Rec stage[SP_WARPS][SP_STAGE];
+    T stage[SP_WARPS][SP_STAGE];
     WarpScratch ws[SP_WARPS];
-    int32_t incl[SP_WARPS][32];
+    int32_t mark[SP_WARPS][32];       // configuration starting at each walker position of a window
     int32_t dre[SP_WARPS][32], dim[SP_WARPS][32];
     uint64_t qv[SP_WARPS][64];        // queued spawn draws: scaled uniform v
     uint32_t qm[SP_WARPS][64];        //   and configuration | part << 5 | negative << 6
 };
 
 struct SpawnCtx {
-    const SpawnShared *sh;
+    const SpawnTables *sh;
     int N, B, K, gk;
     uint64_t jump_q;
     uint32_t ER, ED, LC, LR;
@@ -176,7 +183,7 @@ __device__ __forceinline__ void class_masks(const SpawnCtx &c, uint32_t i, uint3
         if (d == 0) { X1 = (MT)c.Emorton; return; }
         if (__popc(d) != 2) return;
         const int a = __ffs(d) - 1, b = 31 - __clz(d);
-        const SpawnShared &s = *c.sh;
+        const SpawnTables &s = *c.sh;
         if ((c.ER >> a & 1u) && s.rn[a] == b) X2 = (MT)1 << (2 * a);
         else if ((c.ED >> a & 1u) && s.dn[a] == b) X2 = (MT)1 << (2 * a + 1);
         else if ((c.ER >> b & 1u) && s.rn[b] == a) X2 = (MT)1 << (2 * b);
@@ -268,7 +275,7 @@ __device__ __forceinline__ int seg_select32(const SpawnCtx &c, const uint32_t *r
 // imaginary parent a real child of sign -s*g (bond flips); jumps keep the type.
 __device__ __forceinline__ void move_key(const SpawnCtx &c, const RunParams &P, uint64_t i, uint64_t j, int m,
                                          uint64_t &ckey, int &g, bool &jump) {
-    const SpawnShared &s = *c.sh;
+    const SpawnTables &s = *c.sh;
     uint64_t ci = i, cj = j;
     jump = m >= 2 * c.B;
     g = 1;
@@ -302,15 +309,16 @@ template <> __device__ __forceinline__ uint64_t make_spawn<uint64_t>(uint64_t ke
     return pack_rec(key, flag, re, im);
 }
 
-__device__ __forceinline__ void count_digits(SpawnShared &s, uint64_t key, int npass) {
+template <typename T>
+__device__ __forceinline__ void count_digits(SpawnShared<T> &s, uint64_t key, int npass) {
     for (int p = 0; p < npass; ++p) atomicAdd(&s.hist[p][(key >> (8 * p)) & 0xFFull], 1u);
 }
 
 // Append one record from a (possibly divergent) lane.
 template <typename T>
-__device__ __forceinline__ void emit(SpawnShared &s, int warp, const T &r, T *out, int64_t cap,
+__device__ __forceinline__ void emit(SpawnShared<T> &s, int warp, const T &r, T *out, int64_t cap,
                                      DevState *st, int npass) {
-    T *stage = reinterpret_cast<T *>(&s.stage[warp][0]);
+    T *stage = &s.stage[warp][0];
     // one staging-counter update for all the lanes that emit together
     const unsigned am = __activemask();
     const int lane = threadIdx.x & 31;
@@ -335,7 +343,7 @@ __device__ __forceinline__ void emit(SpawnShared &s, int warp, const T &r, T *ou
 // Append an aggregated child (any int32 counts): packed records carry at most
 // PK_LIM walkers per part, so large counts become several records.
 template <typename T>
-__device__ __forceinline__ void emit_counts(SpawnShared &s, int warp, uint64_t key, bool flag, int cre, int cim,
+__device__ __forceinline__ void emit_counts(SpawnShared<T> &s, int warp, uint64_t key, bool flag, int cre, int cim,
                                             T *out, int64_t cap, DevState *st, int npass) {
     if constexpr (sizeof(T) == sizeof(Rec)) {
         emit(s, warp, make_spawn<T>(key, flag, cre, cim), out, cap, st, npass);
@@ -352,10 +360,10 @@ __device__ __forceinline__ void emit_counts(SpawnShared &s, int warp, uint64_t k
 
 // Warp-uniform flush of the warp's staged records.
 template <typename T>
-__device__ __forceinline__ void flush(SpawnShared &s, int warp, int lane, T *out, int64_t cap,
+__device__ __forceinline__ void flush(SpawnShared<T> &s, int warp, int lane, T *out, int64_t cap,
                                       DevState *st, int npass, int min_n) {
     __syncwarp();
-    const T *stage = reinterpret_cast<const T *>(&s.stage[warp][0]);
+    const T *stage = &s.stage[warp][0];
     int n = s.stage_n[warp];
     if (n > SP_STAGE) n = SP_STAGE;
     if (n >= min_n && n > 0) {
@@ -398,7 +406,7 @@ __device__ __forceinline__ uint32_t attempt_word(uint4 x0, uint4 &xb, uint32_t &
 // (ket, bra or jump segment, then the group and the bond inside it), the child
 // configuration and its signed unit, appended as a spawn record.
 template <typename T, typename MT>
-__device__ __forceinline__ void spawn_drain(SpawnShared &s, const SpawnCtx &c, int warp, int lane, int n, int N,
+__device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c, int warp, int lane, int n, int N,
                                             T *out, int64_t cap, DevState *st, int npass) {
     if (lane < n) {
         const uint64_t v = s.qv[warp][lane];
@@ -446,13 +454,12 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
     // packed records <=> N <= 16 <=> 32-bit bond masks
     using MT = typename std::conditional<sizeof(T) == 8, uint32_t, uint64_t>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SpawnShared &s = *reinterpret_cast<SpawnShared *>(smem_raw);
+    SpawnShared<T> &s = *reinterpret_cast<SpawnShared<T> *>(smem_raw);
     const RunParams &P = *Pp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (block_stopped(st)) return;
     const int N = P.N, B = P.B, K = P.K, npass = P.npass;
     // stage the constant tables
-    for (int q = tid; q < B * 8; q += SP_TPB) (&s.rate_q[0][0][0])[q] = (&P.rate_q[0][0][0])[q];
     for (int q = tid; q < B; q += SP_TPB) {
         s.bond_m[q] = P.bond_m[q];
         s.bond_a[q] = (int8_t)P.bond_a[q];
@@ -467,7 +474,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
     if (tid < 2) s.sgn_h[tid] = P.sgn_h[tid];
     for (int q = tid; q <= 2 * B; q += SP_TPB) { s.cross_int[q] = P.cross_int[q]; s.cross_frac[q] = P.cross_frac[q]; }
     for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_frac[q] = st->d_frac[q]; s.d_sgn[q] = st->d_sgn[q]; }
-    for (int q = tid; q < MAXPASS * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
+    for (int q = tid; q < SpawnShared<T>::NP * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
     if (tid < SP_WARPS) s.stage_n[tid] = 0;
     __syncthreads();
 
@@ -547,7 +554,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
             const int y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
             if (lane >= off) incl += y;
         }
-        s.incl[warp][lane] = incl;
+        const int excl = incl - nl;
         const int Wl = __shfl_sync(0xFFFFFFFFu, incl, 31);
         __syncwarp();
 
@@ -556,23 +563,35 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
         // draw that lands below the total rate is queued, and the move
         // searches run 32 at a time with every lane busy.
         int qn = 0;                      // queued spawn draws (same value in every lane)
+        int carry = 0;                   // configuration of the walker before the window
         for (int base = 0; base < Wl; base += 32) {
+            const bool last_base = base + 32 >= Wl;
             const int g = base + lane;
             const bool act = g < Wl;
-            int owner = 0, part = 0, sig = 1;
+            // owner of walker g: the last configuration starting at or before
+            // g (start marks in the window, then a max-scan over the lanes)
+            __syncwarp();
+            s.mark[warp][lane] = -1;
+            __syncwarp();
+            if (nl > 0 && excl >= base && excl < base + 32) s.mark[warp][excl - base] = lane;
+            __syncwarp();
+            int owner = s.mark[warp][lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, owner, off);
+                if (lane >= off && y > owner) owner = y;
+            }
+            if (carry > owner) owner = carry;
+            carry = __shfl_sync(0xFFFFFFFFu, owner, 31);
+            const int owner_excl = __shfl_sync(0xFFFFFFFFu, excl, owner);
+            int part = 0, sig = 1;
             uint32_t natt = 0;
             uint64_t qT = 0;
             uint4 x = make_uint4(0u, 0u, 0u, 0u), ctr = x;
             if (act) {
-                int lo = 0, hi = 31;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s.incl[warp][mid] > g) hi = mid; else lo = mid + 1;
-                }
-                owner = lo;
                 const LightSoA &q = s.ws[warp].le;
                 const int nre_o = q.nre[owner];
-                const int local = g - (owner ? s.incl[warp][owner - 1] : 0);
+                const int local = g - owner_excl;
                 part = local < nre_o ? 0 : 1;
                 const uint32_t w = (uint32_t)(part ? local - nre_o : local);
                 sig = (part ? q.im[owner] : q.re[owner]) < 0 ? -1 : 1;
@@ -607,28 +626,29 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                     ev = v < qT;
                 }
                 const unsigned em = __ballot_sync(0xFFFFFFFFu, ev);
-                if (em == 0u) continue;
                 if (ev) {
                     const int pos = qn + __popc(em & ((1u << lane) - 1u));
                     s.qv[warp][pos] = v;
                     s.qm[warp][pos] = (uint32_t)owner | ((uint32_t)part << 5) | (sig < 0 ? 64u : 0u);
                 }
                 qn += __popc(em);
-                __syncwarp();
-                if (qn >= 32) {
-                    spawn_drain<T, MT>(s, c, warp, lane, 32, N, out, cap, st, npass);
-                    qn -= 32;
+                // resolve full batches of 32, and what is left after the
+                // chunk's last draw (the one place the draws are resolved)
+                const bool fin = last_base && a + 1 == nmax;
+                while (qn >= 32 || (fin && qn > 0)) {
+                    __syncwarp();
+                    const int nd = qn < 32 ? qn : 32;
+                    spawn_drain<T, MT>(s, c, warp, lane, nd, N, out, cap, st, npass);
+                    qn -= nd;
                     // move the rest of the queue to the front
                     uint64_t rv = 0;
                     uint32_t rm = 0;
                     if (lane < qn) { rv = s.qv[warp][32 + lane]; rm = s.qm[warp][32 + lane]; }
                     __syncwarp();
                     if (lane < qn) { s.qv[warp][lane] = rv; s.qm[warp][lane] = rm; }
-                    __syncwarp();
                 }
             }
         }
-        if (qn > 0) spawn_drain<T, MT>(s, c, warp, lane, qn, N, out, cap, st, npass);
         __syncwarp();
         if (light) {
             const int64_t re2 = (int64_t)rec.re + s.dre[warp][lane], im2 = (int64_t)rec.im + s.dim[warp][lane];
@@ -662,14 +682,14 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                         const int anti = (int)(((w >> a0) ^ (w >> a1)) & 1ull);
                         const int cl = imp_class(c.gk, hd, s.bond_m[lane], a0, a1);
                         g0 = 4 * anti + cl;
-                        r0 = s.rate_q[lane][anti][cl];
+                        r0 = P.rate_q[lane][anti][cl];
                     }
                     if (lane + 32 < B) {
                         const int a0 = s.bond_a[lane + 32], a1 = s.bond_b[lane + 32];
                         const int anti = (int)(((w >> a0) ^ (w >> a1)) & 1ull);
                         const int cl = imp_class(c.gk, hd, s.bond_m[lane + 32], a0, a1);
                         g1 = 4 * anti + cl;
-                        r1 = s.rate_q[lane + 32][anti][cl];
+                        r1 = P.rate_q[lane + 32][anti][cl];
                     }
                     for (int g = 0; g < 8; ++g) {
                         const unsigned m0 = __ballot_sync(0xFFFFFFFFu, g0 == g);
