@@ -147,6 +147,11 @@ __device__ __forceinline__ bool block_stopped(const DevState *st) {
     return stop;
 }
 
+// A look-back word of this epoch with its flag set.
+__device__ __forceinline__ bool lb_ready(uint64_t w, uint32_t epoch) {
+    return (w >> 34) == (uint64_t)(epoch & 0x3FFFFFFFu) && ((w >> 32) & 3ull) != 0ull;
+}
+
 // Bounded spin on a look-back status word; returns the word or 0 on timeout
 // (and records ST_TIMEOUT).
 __device__ __forceinline__ uint64_t lb_wait(const uint64_t *p, uint32_t epoch, uint32_t *status) {

@@ -228,7 +228,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
         Rec *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
         const int64_t *__restrict__ rem_end, uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
     using TR = RecTraits<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     MergeShared &s = *reinterpret_cast<MergeShared *>(smem_raw);
     const RunParams &P = *Pp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

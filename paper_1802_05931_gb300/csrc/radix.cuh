@@ -52,6 +52,7 @@ __device__ __forceinline__ uint64_t pack_rec(uint64_t key, bool flag, int re, in
 constexpr int RX_TPB = 256;                  // one thread per digit value
 constexpr int RX_WARPS = RX_TPB / 32;
 constexpr int RX_TILE_MIN = RX_TPB * 8;      // smallest tile (sizes the look-back words)
+constexpr int LB_BATCH = 8;                  // look-back words read together
 
 template <typename T>
 struct RadixShared {
@@ -91,7 +92,7 @@ k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict
     using TR = RecTraits<T>;
     constexpr int IPT = TR::IPT;
     constexpr int TILE = RX_TPB * IPT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     RadixShared<T> &s = *reinterpret_cast<RadixShared<T> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (block_stopped(st)) return;
@@ -179,12 +180,26 @@ k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict
             for (int w = 0; w < warp; ++w) pre += s.scan_tmp[w];
             s.dstart[tid] = pre + x - cnt;
         }
-        // decoupled look-back for this digit
+        // decoupled look-back for this digit, reading LB_BATCH earlier tiles at a time
         uint64_t excl = 0;
-        for (int64_t jt = tile - 1; jt >= 0; --jt) {
-            const uint64_t w = lb_wait(lookback + (size_t)jt * 256 + tid, epoch, &st->status);
-            excl += (uint32_t)w;
-            if (((w >> 32) & 3ull) != LB_AGG) break;       // inclusive (or timed out)
+        {
+            bool done = tile == 0;
+            for (int64_t jt = tile - 1; !done; jt -= LB_BATCH) {
+                uint64_t w[LB_BATCH];
+#pragma unroll
+                for (int k = 0; k < LB_BATCH; ++k)
+                    w[k] = jt - k >= 0 ? *(volatile const uint64_t *)(lookback + (size_t)(jt - k) * 256 + tid)
+                                       : lb_pack(epoch, LB_INC, 0u);
+#pragma unroll
+                for (int k = 0; k < LB_BATCH; ++k) {
+                    if (!done) {
+                        uint64_t v = w[k];
+                        if (!lb_ready(v, epoch)) v = lb_wait(lookback + (size_t)(jt - k) * 256 + tid, epoch, &st->status);
+                        excl += (uint32_t)v;
+                        if (((v >> 32) & 3ull) != LB_AGG) done = true;     // inclusive (or timed out)
+                    }
+                }
+            }
         }
         if (tile > 0) lb_store(my, lb_pack(epoch, LB_INC, (uint32_t)(excl + cnt)));
         s.gbase[tid] = (int64_t)s.bucket[tid] + (int64_t)excl - (int64_t)s.dstart[tid];

@@ -453,7 +453,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
               T *__restrict__ out, int64_t cap) {
     // packed records <=> N <= 16 <=> 32-bit bond masks
     using MT = typename std::conditional<sizeof(T) == 8, uint32_t, uint64_t>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SpawnShared<T> &s = *reinterpret_cast<SpawnShared<T> *>(smem_raw);
     const RunParams &P = *Pp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
