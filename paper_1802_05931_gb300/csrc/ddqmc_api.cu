@@ -274,7 +274,8 @@ constexpr size_t SP_SMEM = sizeof(SpawnShared<Rec>);
 constexpr size_t SPP_SMEM = sizeof(SpawnShared<uint64_t>);
 constexpr size_t RX_SMEM = sizeof(RadixShared<Rec>);
 constexpr size_t RXP_SMEM = sizeof(RadixShared<uint64_t>);
-constexpr size_t MG_SMEM = sizeof(MergeShared);
+constexpr size_t MG_SMEM = sizeof(MergeShared<Rec>);
+constexpr size_t MGP_SMEM = sizeof(MergeShared<uint64_t>);
 
 // One step's launches for spawn records of type T (16-byte Rec or packed 8-byte).
 template <typename T>
@@ -296,7 +297,7 @@ void launch_step(ddqmc_run *r, Rec *Lc, Rec *Ln, const std::function<void(int, i
     k_merge_partition<T><<<r->g_part, 256, 0, r->stream>>>(Lc, sorted, r->dS, r->splits, r->rem_end, r->rcap);
     mark(2, 1);
     mark(3, 0);
-    k_merge<T><<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits, r->rem_end,
+    k_merge<T><<<r->g_merge, MG_TPB, sizeof(MergeShared<T>), r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits, r->rem_end,
                                                            r->lb_merge, r->rcap, r->mcap);
     mark(3, 1);
 }
@@ -551,12 +552,12 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     ok = ok && cudaFuncSetAttribute(k_radix_pass<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_radix_pass<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RXP_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_merge<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_merge<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_merge<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MGP_SMEM) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
     if (r->packed) {
         r->g_spawn = occupancy_grid((const void *)k_spawn_death<uint64_t>, SP_TPB, SPP_SMEM, sms);
         r->g_radix = occupancy_grid((const void *)k_radix_pass<uint64_t>, RX_TPB, RXP_SMEM, sms);
-        r->g_merge = occupancy_grid((const void *)k_merge<uint64_t>, MG_TPB, MG_SMEM, sms);
+        r->g_merge = occupancy_grid((const void *)k_merge<uint64_t>, MG_TPB, MGP_SMEM, sms);
     } else {
         r->g_spawn = occupancy_grid((const void *)k_spawn_death<Rec>, SP_TPB, SP_SMEM, sms);
         r->g_radix = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);

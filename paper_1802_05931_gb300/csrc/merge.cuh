@@ -174,20 +174,28 @@ __device__ __forceinline__ SegAgg seg_warp_exclusive(const SegAgg &mine, int lan
     return exc;
 }
 
+// Keys of the merge tile: 32-bit when spawn records are packed (2N <= 32).
+template <typename T> struct MergeKey { using type = uint64_t; };
+template <> struct MergeKey<uint64_t> { using type = uint32_t; };
+
+template <typename T>
 struct MergeWarp {
-    uint64_t key[MG_TILE];            // L keys, then S keys with the flag bit; later the output keys
-    int2 val[MG_TILE];                // (re, im) of the same elements; later the output populations
+    typename MergeKey<T>::type key[MG_TILE];   // L keys, then S keys; later the output keys
+    int2 val[MG_TILE];                          // (re, im) of the same elements; later the output populations
+    uint32_t sflag[(MG_TILE + 31) / 32];        // initiator flags of the S elements, bit q of word q/32
 };
 
+template <typename T>
 struct MergeShared {
-    MergeWarp w[MG_WARPS];
+    MergeWarp<T> w[MG_WARPS];
     unsigned long long est[NOBS_MAX];
     uint64_t bond_m[MAXB];
     int8_t bond_a[MAXB], bond_b[MAXB];
     int8_t pair_bond[MAXN * MAXN];
 };
 
-__device__ __forceinline__ void add_estimators(MergeShared &s, const RunParams &P, uint64_t key, int32_t re,
+template <typename T>
+__device__ __forceinline__ void add_estimators(MergeShared<T> &s, const RunParams &P, uint64_t key, int32_t re,
                                                int32_t im) {
     const int N = P.N, B = P.B;
     const uint64_t i = key & P.nmask, j = key >> N;
@@ -228,8 +236,9 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
         Rec *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
         const int64_t *__restrict__ rem_end, uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
     using TR = RecTraits<T>;
+    using KT = typename MergeKey<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    MergeShared &s = *reinterpret_cast<MergeShared *>(smem_raw);
+    MergeShared<T> &s = *reinterpret_cast<MergeShared<T> *>(smem_raw);
     const RunParams &P = *Pp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (block_stopped(st)) return;
@@ -251,7 +260,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
     }
     for (int q = tid; q < N * N; q += MG_TPB) s.pair_bond[q] = P.pair_bond[q];
     __syncthreads();
-    MergeWarp &ws = s.w[warp];
+    MergeWarp<T> &ws = s.w[warp];
     int64_t my_w = 0, my_m = 0;
     uint32_t local_status = 0;
 
@@ -266,28 +275,35 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
         const int64_t b0 = d0 - a0, b1 = d1 - a1;
         const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
         // key of the merged element before the tile
-        uint64_t pk = 0;
+        KT pk = 0;
         int hp = 0;
         if (lane == 0) {
-            if (a0 > 0) { pk = L[a0 - 1].key; hp = 1; }
+            if (a0 > 0) { pk = (KT)L[a0 - 1].key; hp = 1; }
             if (b0 > 0) {
-                const uint64_t k2 = TR::key(S[b0 - 1]);
+                const KT k2 = (KT)TR::key(S[b0 - 1]);
                 if (!hp || k2 > pk) pk = k2;
                 hp = 1;
             }
         }
         pk = __shfl_sync(0xFFFFFFFFu, pk, 0);
         hp = __shfl_sync(0xFFFFFFFFu, hp, 0);
-        // load the tile's L and S elements (S keys keep their flag in bit 63)
+        // load the tile's L and S elements; the S flags go to a bit mask
         for (int q = lane; q < na; q += 32) {
             const Rec v = L[a0 + q];
-            ws.key[q] = v.key;
+            ws.key[q] = (KT)v.key;
             ws.val[q] = make_int2(v.re, v.im);
         }
-        for (int q = lane; q < nb; q += 32) {
-            const T v = S[b0 + q];
-            ws.key[na + q] = TR::key(v) | (TR::flag(v) ? FLAG_BIT : 0ull);
-            ws.val[na + q] = make_int2(TR::re(v), TR::im(v));
+        for (int q0 = 0; q0 < nb; q0 += 32) {
+            const int q = q0 + lane;
+            bool f = false;
+            if (q < nb) {
+                const T v = S[b0 + q];
+                ws.key[na + q] = (KT)TR::key(v);
+                ws.val[na + q] = make_int2(TR::re(v), TR::im(v));
+                f = TR::flag(v);
+            }
+            const unsigned fb = __ballot_sync(0xFFFFFFFFu, f);
+            if (lane == 0) ws.sflag[q0 >> 5] = fb;
         }
         // spawn records past the tile end that continue its last run
         int64_t rf0 = 0, rf1 = 0, ru0 = 0, ru1 = 0;
@@ -306,15 +322,15 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
             }
         }
         __syncwarp();
-        const uint64_t *kL = ws.key;
-        const uint64_t *kS = ws.key + na;
+        const KT *kL = ws.key;
+        const KT *kS = ws.key + na;
         const int2 *vL = ws.val;
         const int2 *vS = ws.val + na;
 
         // ---- 1. merge: this lane's MG_IPT merged positions, in registers ----
         const int dloc = lane * MG_IPT;
         const int nt = na + nb;
-        uint64_t ik[MG_IPT];
+        KT ik[MG_IPT];
         int2 iv[MG_IPT];
         uint32_t hmask = 0, lmask = 0, fmask = 0;   // run heads, elements of L_t, initiator records
         int nk = 0;
@@ -323,17 +339,17 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
             int hi = dloc < na ? dloc : na;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (kL[mid] <= (kS[dloc - 1 - mid] & KEY_MASK)) lo = mid + 1;
+                if (kL[mid] <= kS[dloc - 1 - mid]) lo = mid + 1;
                 else hi = mid;
             }
             int ia = lo, ib = dloc - lo;
-            uint64_t prev = 0;
+            KT prev = 0;
             bool hprev = false;
             if (dloc == 0) { prev = pk; hprev = hp != 0; }
             else {
                 if (ia > 0) { prev = kL[ia - 1]; hprev = true; }
                 if (ib > 0) {
-                    const uint64_t k2 = kS[ib - 1] & KEY_MASK;
+                    const KT k2 = kS[ib - 1];
                     if (!hprev || k2 > prev) prev = k2;
                     hprev = true;
                 }
@@ -347,14 +363,13 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                     bool fromL;
                     if (ia >= na) fromL = false;
                     else if (ib >= nb) fromL = true;
-                    else fromL = kL[ia] <= (kS[ib] & KEY_MASK);
-                    const uint64_t kraw = fromL ? kL[ia] : kS[ib];
-                    const uint64_t key = kraw & KEY_MASK;
+                    else fromL = kL[ia] <= kS[ib];
+                    const KT key = fromL ? kL[ia] : kS[ib];
                     ik[k] = key;
                     iv[k] = fromL ? vL[ia] : vS[ib];
                     if (!hprev || key != prev) hmask |= 1u << k;
                     if (fromL) lmask |= 1u << k;
-                    else if (kraw & FLAG_BIT) fmask |= 1u << k;
+                    else if ((ws.sflag[ib >> 5] >> (ib & 31)) & 1u) fmask |= 1u << k;
                     prev = key;
                     hprev = true;
                     if (fromL) ++ia; else ++ib;
@@ -398,7 +413,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                     run.uim += ru1;
                 }
                 if (ends && owned) {
-                    const bool open = run.hasL || no_init || ((ik[k] & nmask) == (ik[k] >> N));
+                    const bool open = run.hasL || no_init || (((uint64_t)ik[k] & nmask) == ((uint64_t)ik[k] >> N));
                     const int64_t sre = run.fre + (open ? run.ure : 0);
                     const int64_t sim = run.fim + (open ? run.uim : 0);
                     if (sre != 0 || sim != 0) {
@@ -453,7 +468,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
         } else {
             for (uint32_t q = lane; q < total; q += 32) {
                 Rec v;
-                v.key = ws.key[q];
+                v.key = (uint64_t)ws.key[q];
                 v.re = ws.val[q].x;
                 v.im = ws.val[q].y;
                 out[ob + q] = v;
