@@ -468,96 +468,128 @@ static int or_merge_spawns(const or_entry *L, int64_t M, or_spawn *sp, int64_t R
 
 
 
+/* Death/clone table of the current step: p_c = dt ((gamma/2) c + S) for
+ * c = n(i) + n(j); integer part, fixed-point fraction and sign. */
+static void or_death_table(const or_run *r, uint32_t *d_int, uint64_t *d_frac, int *d_sgn) {
+    double g2 = 0.5 * r->gamma;
+    for (int c = 0; c <= 2 * r->N; ++c) {
+        double a = g2 * (double)c;
+        double b = a + r->S;
+        double p = r->dt * b;
+        double ap = fabs(p);
+        double ip = floor(ap);
+        d_int[c] = (uint32_t)ip;
+        d_frac[c] = or_q(ap - ip);
+        d_sgn[c] = (p > 0.0) ? 1 : ((p < 0.0) ? -1 : 0);
+    }
+}
+
+/* Where the children of one entry go: all of them into a spawn vector (sv),
+ * or, with sv NULL, only the sum of those landing on (want_ket, want_bra). */
+typedef struct {
+    or_spawn_vec *sv;
+    uint64_t want_ket, want_bra;
+    int64_t got_re, got_im;
+} or_sink;
+
+/* Steps (i) and (ii) for the walkers of one entry (i, j) with populations
+ * (re, im): the change of the entry's own populations (death/clone and the
+ * on-site transfer) in *dre_p, *dim_p, and its children into the sink. */
+static int or_walk_entry(or_run *r, const uint32_t *d_int, const uint64_t *d_frac, const int *d_sgn,
+                         uint64_t i, uint64_t j, int64_t re, int64_t im, or_move *mv,
+                         int64_t *dre_p, int64_t *dim_p, or_sink *sink) {
+    int err = OR_OK;
+    int64_t nre = re < 0 ? -re : re, nim = im < 0 ? -im : im;
+    int init = (r->n_a == 0) || (i == j) || (nre + nim > (int64_t)r->n_a);
+    int K = or_moves_of(r, i, j, mv);
+    uint64_t T = 0;
+    for (int k = 0; k < K; ++k) T += mv[k].rate;
+    uint64_t natt = (T + 0xFFFFFFFFull) >> 32;
+    if (natt < 1) natt = 1;
+    int cd = or_popc(i) + or_popc(j);
+    int dz = or_zsum(r, i) - or_zsum(r, j);
+    int adz = dz < 0 ? -dz : dz;
+    /* Im part of the diagonal element, d = -(E(i) - E(j)) = -Jz dz */
+    int sgn_d = 0;
+    if (dz != 0 && r->Jz != 0.0) sgn_d = ((r->Jz > 0.0) == (dz > 0)) ? -1 : 1;
+    int64_t dre = 0, dim = 0;
+    for (int part = 0; part < 2 && err == OR_OK; ++part) {
+        int64_t pop = part == 0 ? re : im;
+        int64_t n = pop < 0 ? -pop : pop;
+        int sig = pop < 0 ? -1 : 1;
+        for (int64_t w = 0; w < n && err == OR_OK; ++w) {
+            uint32_t x[4];
+            or_draw_block(r, i, j, (uint32_t)w, part, 0, x);
+            /* death (p > 0) or cloning (p < 0) on the walker's own part */
+            int64_t cnt = (int64_t)d_int[cd] + ((uint64_t)x[1] < d_frac[cd] ? 1 : 0);
+            if (part == 0) dre -= (int64_t)d_sgn[cd] * sig * cnt;
+            else dim -= (int64_t)d_sgn[cd] * sig * cnt;
+            /* on-site transfer from the imaginary part of the diagonal element */
+            int64_t cc = (int64_t)r->cross_int[adz] + ((uint64_t)x[2] < r->cross_frac[adz] ? 1 : 0);
+            if (part == 0) dim += (int64_t)sig * sgn_d * cc;
+            else dre -= (int64_t)sig * sgn_d * cc;
+            /* spawning attempts */
+            uint32_t xb[4];
+            uint32_t cur_block = 0;
+            for (uint64_t a = 0; a < natt; ++a) {
+                uint32_t u;
+                if (a == 0) u = x[0];
+                else if (a == 1) u = x[3];
+                else {
+                    uint32_t blk = 1u + (uint32_t)((a - 2) / 4);
+                    if (blk != cur_block) { or_draw_block(r, i, j, (uint32_t)w, part, blk, xb); cur_block = blk; }
+                    u = xb[(a - 2) % 4];
+                }
+                uint64_t v = (uint64_t)u * natt;
+                if (v >= T) continue;
+                uint64_t cum = 0;
+                int k = 0;
+                for (; k < K; ++k) { cum += mv[k].rate; if (v < cum) break; }
+                /* child type and sign: Delta rho_child = A * rho_parent (Sec. III.C rules) */
+                int32_t cre = 0, cim = 0;
+                double Ar = mv[k].Are, Ai = mv[k].Aim;
+                if (part == 0) {            /* real parent of sign sig */
+                    if (Ar != 0.0) cre = sig * (Ar > 0.0 ? 1 : -1);
+                    else cim = sig * (Ai > 0.0 ? 1 : -1);
+                } else {                    /* imaginary parent i*sig */
+                    if (Ar != 0.0) cim = sig * (Ar > 0.0 ? 1 : -1);
+                    else cre = -sig * (Ai > 0.0 ? 1 : -1);
+                }
+                if (sink->sv) {
+                    err = or_push(sink->sv, mv[k].cket, mv[k].cbra, cre, cim, init);
+                    if (err != OR_OK) break;
+                } else if (mv[k].cket == sink->want_ket && mv[k].cbra == sink->want_bra) {
+                    sink->got_re += cre;
+                    sink->got_im += cim;
+                }
+            }
+        }
+    }
+    *dre_p = dre;
+    *dim_p = dim;
+    return err;
+}
+
 int or_step(or_run *r, int64_t nsteps) {
     or_move mv[2 * OR_MAX_BONDS + OR_MAX_SITES];
     for (int64_t it = 0; it < nsteps; ++it) {
-        /* death/clone table for this step: p_c = dt ((gamma/2) c + S), c = n(i) + n(j) */
         uint32_t d_int[2 * OR_MAX_SITES + 1];
         uint64_t d_frac[2 * OR_MAX_SITES + 1];
         int d_sgn[2 * OR_MAX_SITES + 1];
-        double g2 = 0.5 * r->gamma;
-        for (int c = 0; c <= 2 * r->N; ++c) {
-            double a = g2 * (double)c;
-            double b = a + r->S;
-            double p = r->dt * b;
-            double ap = fabs(p);
-            double ip = floor(ap);
-            d_int[c] = (uint32_t)ip;
-            d_frac[c] = or_q(ap - ip);
-            d_sgn[c] = (p > 0.0) ? 1 : ((p < 0.0) ? -1 : 0);
-        }
+        or_death_table(r, d_int, d_frac, d_sgn);
 
         or_spawn_vec sv = {0, 0, 0};
+        or_sink sink;
+        memset(&sink, 0, sizeof(sink));
+        sink.sv = &sv;
         int err = OR_OK;
         /* (i) spawning and (ii) death/clone, all from rho(t) and S(t) (Euler step) */
         for (int64_t e = 0; e < r->M && err == OR_OK; ++e) {
-            uint64_t i = r->L[e].ket, j = r->L[e].bra;
-            int64_t re = r->L[e].re, im = r->L[e].im;
-            int64_t nre = re < 0 ? -re : re, nim = im < 0 ? -im : im;
-            int init = (r->n_a == 0) || (i == j) || (nre + nim > (int64_t)r->n_a);
-            int K = or_moves_of(r, i, j, mv);
-            uint64_t T = 0;
-            for (int k = 0; k < K; ++k) T += mv[k].rate;
-            uint64_t natt = (T + 0xFFFFFFFFull) >> 32;
-            if (natt < 1) natt = 1;
-            int cd = or_popc(i) + or_popc(j);
-            int dz = or_zsum(r, i) - or_zsum(r, j);
-            int adz = dz < 0 ? -dz : dz;
-            /* Im part of the diagonal element, d = -(E(i) - E(j)) = -Jz dz */
-            int sgn_d = 0;
-            if (dz != 0 && r->Jz != 0.0) sgn_d = ((r->Jz > 0.0) == (dz > 0)) ? -1 : 1;
             int64_t dre = 0, dim = 0;
-            for (int part = 0; part < 2; ++part) {
-                int64_t pop = part == 0 ? re : im;
-                int64_t n = pop < 0 ? -pop : pop;
-                int sig = pop < 0 ? -1 : 1;
-                for (int64_t w = 0; w < n; ++w) {
-                    uint32_t x[4];
-                    or_draw_block(r, i, j, (uint32_t)w, part, 0, x);
-                    /* death (p > 0) or cloning (p < 0) on the walker's own part */
-                    int64_t cnt = (int64_t)d_int[cd] + ((uint64_t)x[1] < d_frac[cd] ? 1 : 0);
-                    if (part == 0) dre -= (int64_t)d_sgn[cd] * sig * cnt;
-                    else dim -= (int64_t)d_sgn[cd] * sig * cnt;
-                    /* on-site transfer from the imaginary part of the diagonal element */
-                    int64_t cc = (int64_t)r->cross_int[adz] + ((uint64_t)x[2] < r->cross_frac[adz] ? 1 : 0);
-                    if (part == 0) dim += (int64_t)sig * sgn_d * cc;
-                    else dre -= (int64_t)sig * sgn_d * cc;
-                    /* spawning attempts */
-                    uint32_t xb[4];
-                    uint32_t cur_block = 0;
-                    for (uint64_t a = 0; a < natt; ++a) {
-                        uint32_t u;
-                        if (a == 0) u = x[0];
-                        else if (a == 1) u = x[3];
-                        else {
-                            uint32_t blk = 1u + (uint32_t)((a - 2) / 4);
-                            if (blk != cur_block) { or_draw_block(r, i, j, (uint32_t)w, part, blk, xb); cur_block = blk; }
-                            u = xb[(a - 2) % 4];
-                        }
-                        uint64_t v = (uint64_t)u * natt;
-                        if (v >= T) continue;
-                        uint64_t cum = 0;
-                        int k = 0;
-                        for (; k < K; ++k) { cum += mv[k].rate; if (v < cum) break; }
-                        /* child type and sign: Delta rho_child = A * rho_parent (Sec. III.C rules) */
-                        int32_t cre = 0, cim = 0;
-                        double Ar = mv[k].Are, Ai = mv[k].Aim;
-                        if (part == 0) {            /* real parent of sign sig */
-                            if (Ar != 0.0) cre = sig * (Ar > 0.0 ? 1 : -1);
-                            else cim = sig * (Ai > 0.0 ? 1 : -1);
-                        } else {                    /* imaginary parent i*sig */
-                            if (Ar != 0.0) cim = sig * (Ar > 0.0 ? 1 : -1);
-                            else cre = -sig * (Ai > 0.0 ? 1 : -1);
-                        }
-                        err = or_push(&sv, mv[k].cket, mv[k].cbra, cre, cim, init);
-                        if (err != OR_OK) break;
-                    }
-                    if (err != OR_OK) break;
-                }
-                if (err != OR_OK) break;
-            }
-            r->L[e].re = re + dre;
-            r->L[e].im = im + dim;
+            err = or_walk_entry(r, d_int, d_frac, d_sgn, r->L[e].ket, r->L[e].bra, r->L[e].re, r->L[e].im, mv,
+                                &dre, &dim, &sink);
+            r->L[e].re += dre;
+            r->L[e].im += dim;
         }
         if (err != OR_OK) { free(sv.v); return err; }
         r->last_spawns = sv.n;
@@ -774,4 +806,79 @@ int64_t or_annihilate(const uint64_t *lket, const uint64_t *lbra, const int32_t 
     }
     free(out);
     return mo;
+}
+
+/* The step of or_step evaluated at chosen configurations only ("gathered"):
+ * for each target c = (tket[q], tbra[q]), its own walkers' death/clone and
+ * on-site transfer (if c is occupied), plus every child that a walker of an
+ * occupied parent sends to c -- the parents that can reach c are c with one
+ * bond flipped in the ket or in the bra, and c with one site raised in both
+ * words (the reverse of a jump) -- summed under the initiator rule of
+ * Sec. IV.A.  Same draws, rates and rules as or_step, so the result equals
+ * the entry of c in the stepped list (0, 0 when c is absent from it).
+ * L_t: m entries sorted by (bra, ket), unique.  The run supplies the lattice,
+ * the rate tables, t and S (its own list is not used). */
+static int64_t or_find(const uint64_t *lket, const uint64_t *lbra, int64_t m, uint64_t ket, uint64_t bra) {
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (or_cmp_key(lket[mid], lbra[mid], ket, bra) < 0) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < m && lket[lo] == ket && lbra[lo] == bra) ? lo : -1;
+}
+
+int or_gather(or_run *r, const uint64_t *lket, const uint64_t *lbra, const int32_t *lre, const int32_t *lim,
+              int64_t m, const uint64_t *tket, const uint64_t *tbra, int64_t nt, int64_t *out_re, int64_t *out_im) {
+    if (r->inj) return OR_ERR_ARG;        /* an injected stream is consumed in list order */
+    or_move mv[2 * OR_MAX_BONDS + OR_MAX_SITES];
+    uint32_t d_int[2 * OR_MAX_SITES + 1];
+    uint64_t d_frac[2 * OR_MAX_SITES + 1];
+    int d_sgn[2 * OR_MAX_SITES + 1];
+    or_death_table(r, d_int, d_frac, d_sgn);
+    uint64_t wmask = (r->N >= 64) ? ~0ull : ((1ull << r->N) - 1ull);
+    for (int64_t q = 0; q < nt; ++q) {
+        uint64_t ci = tket[q], cj = tbra[q];
+        int64_t own_re = 0, own_im = 0, fre = 0, fim = 0, ure = 0, uim = 0;
+        int64_t e = or_find(lket, lbra, m, ci, cj);
+        or_sink sink;
+        memset(&sink, 0, sizeof(sink));
+        sink.want_ket = ci;
+        sink.want_bra = cj;
+        if (e >= 0) {
+            int64_t dre = 0, dim = 0;
+            or_walk_entry(r, d_int, d_frac, d_sgn, ci, cj, lre[e], lim[e], mv, &dre, &dim, &sink);
+            own_re = (int64_t)lre[e] + dre;
+            own_im = (int64_t)lim[e] + dim;
+        }
+        /* candidate parents: 2B bond flips and up to N raised sites */
+        for (int c = 0; c < 2 * r->B + r->N; ++c) {
+            uint64_t pi = ci, pj = cj;
+            if (c < r->B) pi ^= r->bond_m[c];
+            else if (c < 2 * r->B) pj ^= r->bond_m[c - r->B];
+            else {
+                int k = c - 2 * r->B;
+                if (or_bit(ci, k) || or_bit(cj, k)) continue;
+                pi |= 1ull << k;
+                pj |= 1ull << k;
+            }
+            pi &= wmask;
+            pj &= wmask;
+            int64_t pe = or_find(lket, lbra, m, pi, pj);
+            if (pe < 0) continue;
+            int64_t pre = lre[pe], pim = lim[pe];
+            int64_t npop = (pre < 0 ? -pre : pre) + (pim < 0 ? -pim : pim);
+            int init = (r->n_a == 0) || (pi == pj) || (npop > (int64_t)r->n_a);
+            int64_t dre = 0, dim = 0;
+            sink.got_re = 0;
+            sink.got_im = 0;
+            or_walk_entry(r, d_int, d_frac, d_sgn, pi, pj, pre, pim, mv, &dre, &dim, &sink);
+            if (init) { fre += sink.got_re; fim += sink.got_im; }
+            else { ure += sink.got_re; uim += sink.got_im; }
+        }
+        int open = (e >= 0) || (ci == cj) || (r->n_a == 0);
+        out_re[q] = own_re + fre + (open ? ure : 0);
+        out_im[q] = own_im + fim + (open ? uim : 0);
+    }
+    return OR_OK;
 }

@@ -79,6 +79,9 @@ def _load():
         lib.or_annihilate.argtypes = [P(u64), P(u64), P(i32), P(i32), i64, P(u64), P(u64), P(i32), P(i32),
                                       P(i32), i64, i32, P(u64), P(u64), P(i32), P(i32), i64]
         lib.or_annihilate.restype = i64
+        lib.or_gather.argtypes = [C.c_void_p, P(u64), P(u64), P(i32), P(i32), i64, P(u64), P(u64), i64,
+                                  P(i64), P(i64)]
+        lib.or_gather.restype = C.c_int
         lib.or_series_log.argtypes = [dbl]
         lib.or_series_log.restype = dbl
         _lib = lib
@@ -232,6 +235,24 @@ class OracleRun:
         out = np.zeros((max(n, 1), self.nobs), dtype=np.int64)
         self._lib.or_series(self._h, _ptr(out, C.c_int64), n)
         return out[:n]
+
+    def gather(self, ket, bra, re, im, tket, tbra):
+        """One step of the list (ket, bra, re, im) -- sorted by (bra, ket),
+        unique -- evaluated only at the targets (tket, tbra), at this run's t
+        and S: the targets' entries of the stepped list, (0, 0) where a target
+        is absent from it.  The run's own list is not touched."""
+        a = [np.ascontiguousarray(x, dtype=t) for x, t in ((ket, np.uint64), (bra, np.uint64), (re, np.int32),
+                                                         (im, np.int32))]
+        tk = np.ascontiguousarray(tket, dtype=np.uint64)
+        tb = np.ascontiguousarray(tbra, dtype=np.uint64)
+        ore = np.zeros(len(tk), dtype=np.int64)
+        oim = np.zeros(len(tk), dtype=np.int64)
+        rc = self._lib.or_gather(self._h, _ptr(a[0], C.c_uint64), _ptr(a[1], C.c_uint64), _ptr(a[2], C.c_int32),
+                                 _ptr(a[3], C.c_int32), len(a[0]), _ptr(tk, C.c_uint64), _ptr(tb, C.c_uint64),
+                                 len(tk), _ptr(ore, C.c_int64), _ptr(oim, C.c_int64))
+        if rc != 0:
+            raise RuntimeError("oracle gather failed with code %d" % rc)
+        return ore, oim
 
     # --- element access for the Liouvillian pins ----------------------------
     def moves(self, i, j):
