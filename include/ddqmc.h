@@ -36,10 +36,10 @@ extern "C" {
 #define DDQMC_ERR_OVERFLOW (-4)      /* a population left the int32 range (sticky) */
 #define DDQMC_ERR_TIMEOUT (-5)       /* a bounded device wait gave up (sticky) */
 #define DDQMC_ERR_CUDA (-6)          /* a CUDA runtime call failed */
-#define DDQMC_ERR_UNSUPPORTED (-7)   /* valid parameters this build does not handle (N > 31) */
+#define DDQMC_ERR_UNSUPPORTED (-7)   /* valid parameters a call does not handle (see the call) */
 
-#define DDQMC_MAX_SITES 31
-#define DDQMC_MAX_BONDS 64
+#define DDQMC_MAX_SITES 64
+#define DDQMC_MAX_BONDS 128
 
 /* Lattice: Lx x Ly sites; periodic = 1 wraps both directions (then each
  * periodic extent must be 1 or >= 3, since L = 2 would repeat bonds). */
@@ -122,8 +122,11 @@ int ddqmc_default_options(ddqmc_options *opt);
  * importance guide).  Allocates all device memory, writes the initial list
  * of opt->n0 real walkers on |down..down><down..down| and S = opt->shift0.
  * guide and opt may be NULL (no importance sampling / defaults).
+ * Up to 31 sites, ket and bra pack into one 64-bit key (bra << N | ket) and
+ * records are 16 bytes; from 32 to 64 sites (the 6x6 and 8x8 lattices) each
+ * side is one 64-bit word and records are 24 bytes.
  * Errors: INVALID_ARG (N > 64, dt <= 0, gamma < 0, target <= 0, n_a < 0,
- * bad guide), UNSUPPORTED (N > 31), OOM, CUDA.  *out is NULL on error. */
+ * bad guide), OOM, CUDA.  *out is NULL on error. */
 int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz,
                  double gamma, double dt, int64_t target_walkers,
                  int32_t initiator_threshold, const ddqmc_guide *guide,
@@ -204,7 +207,8 @@ int ddqmc_get_timing(ddqmc_run *run, double *ms, int64_t *launches, int32_t cap)
  * rule of Sec. IV.A): sort spawn records by configuration and merge them into
  * a sorted list.  Records are 16 bytes, { uint64 key; int32 re; int32 im; },
  * key = bra << N | ket; in spawn records bit 63 of the key is set when the
- * parent was an initiator.
+ * parent was an initiator.  One-word keys only: runs of more than 31 sites
+ * return UNSUPPORTED.
  *   d_list   m records, strictly increasing keys, no flag bit (device memory);
  *   d_spawns nsp records in any order (device memory, read only);
  *   d_out    room for out_cap records (device memory, must not overlap the
@@ -217,7 +221,8 @@ int ddqmc_get_timing(ddqmc_run *run, double *ms, int64_t *launches, int32_t cap)
  * as scratch (so it must not overlap a ddqmc_step_async of the same run);
  * issued on the run's stream and waited for.  Errors: INVALID_ARG,
  * CAPACITY (nsp above the run's spawn capacity, m above its list capacity,
- * or more than out_cap merged entries), OVERFLOW, TIMEOUT, CUDA. */
+ * or more than out_cap merged entries), OVERFLOW, TIMEOUT, UNSUPPORTED
+ * (more than 31 sites), CUDA. */
 int ddqmc_annihilate(ddqmc_run *run, const void *d_list, int64_t m, const void *d_spawns, int64_t nsp,
                      void *d_out, int64_t out_cap, int64_t *m_out);
 
@@ -229,8 +234,9 @@ int ddqmc_annihilate(ddqmc_run *run, const void *d_list, int64_t m, const void *
  * or they must stay off the driver's allocation path and its implicit
  * synchronisation.  This entry point allocates nothing and needs no run: its
  * scratch is a fixed array inside the library that every GPU loading the
- * library holds until the process exits (about 8.6 MB).
- *   lattice, initiator_threshold: as in ddqmc_create (key layout and rule);
+ * library holds until the process exits (about 8.9 MB).
+ *   lattice, initiator_threshold: as in ddqmc_create (key layout and rule;
+ *     at most 31 sites, else UNSUPPORTED);
  *   d_list, m, d_spawns, nsp, d_out, out_cap, *m_out: as in ddqmc_annihilate,
  *     with m <= 1048576 list entries and nsp <= 262144 spawn records
  *     (larger sizes return DDQMC_ERR_CAPACITY before any work);

@@ -8,12 +8,13 @@
 
 namespace ddq {
 
-constexpr int MAXN = 31;                      // sites: ket and bra words pack into 62 key bits
-constexpr int MAXB = 64;                      // bonds (2N for a periodic 2D lattice)
+constexpr int MAXN = 64;                      // sites: one 64-bit spin word per side
+constexpr int NPACK = 31;                     // up to here ket and bra pack into one 62-bit key
+constexpr int MAXB = 128;                     // bonds (2N for a periodic 2D lattice)
 constexpr int MAXK = 2 * MAXB + MAXN;         // moves per configuration
 constexpr int NOBS_MAX = 5 + MAXN + 3 * MAXB + 4;
 constexpr int LEVELS = 32;                    // blocking levels (block length 2^l)
-constexpr int MAXPASS = 8;                    // radix passes of 8 bits over 2N <= 62 key bits
+constexpr int MAXPASS = 16;                   // radix passes of 8 bits over at most 128 key bits
 
 constexpr uint32_t ST_CAPACITY = 1u, ST_OVERFLOW = 2u, ST_TIMEOUT = 4u;
 constexpr uint32_t ST_CAP_LIST = 8u, ST_CAP_SPAWN = 16u;   // which capacity ran out (with ST_CAPACITY)
@@ -30,6 +31,19 @@ struct __align__(16) Rec {
     int32_t re;
     int32_t im;
 };
+
+// Two-word record for N > 31 sites: lo = ket word, hi = bra word (canonical
+// order: by hi, then lo), 24 bytes.  In a spawn record the re field holds
+// 2 * Delta re + initiator flag; list entries hold plain populations.
+struct __align__(8) RecW {
+    uint64_t lo, hi;
+    int32_t re;
+    int32_t im;
+};
+
+// Walker-list record of each spawn-record type.
+template <typename T> struct ListOf { using type = Rec; };
+template <> struct ListOf<RecW> { using type = RecW; };
 
 // Look-back status words: [epoch:30][flag:2][value:32].
 constexpr uint64_t LB_AGG = 1ull, LB_INC = 2ull;
@@ -62,6 +76,7 @@ struct RunParams {
     int8_t rn[MAXN], dn[MAXN];        // right / lower neighbour of each site
     int32_t uniform;                  // 1 if every bond has the same rate table
     int32_t pad1;
+    int32_t pass_shift[MAXPASS];      // key bit where the digit of each radix pass starts
     uint64_t Emorton;                 // bond-existence mask, bit 2k = right bond of k, 2k+1 = lower
     uint64_t urate8[8];               // rate of group 4*anti + class when every bond has the same table
 };
@@ -78,7 +93,7 @@ struct DevState {
     int64_t R_last;            // spawn records of the last completed step
     uint32_t epoch;            // look-back epoch of the step in progress
     uint32_t pad1;
-    uint32_t tickets[16];      // tile tickets: [0, 8) radix passes, 8 merge
+    uint32_t tickets[MAXPASS + 16];   // tile tickets: [0, MAXPASS) radix passes, MAXPASS merge
     int64_t walker_steps;      // sum over completed steps of the walkers stepped
     int64_t W_cur;             // sum |re| + |im| of the current list
     int64_t n_app;             // samples accumulated for blocking

@@ -27,8 +27,8 @@ struct ddqmc_run {
     RunParams *dP = nullptr;
     DevState *dS = nullptr;
     BlkCell *dBlk = nullptr;
-    Rec *L[2] = {nullptr, nullptr};
-    Rec *Sp[2] = {nullptr, nullptr};
+    void *L[2] = {nullptr, nullptr};     // walker lists: Rec (N <= 31) or RecW records
+    void *Sp[2] = {nullptr, nullptr};    // spawn records (radix ping-pong)
     uint64_t *lb_radix = nullptr;
     uint64_t *lb_merge = nullptr;
     int64_t *splits = nullptr;
@@ -41,6 +41,7 @@ struct ddqmc_run {
     int g_spawn = 0, g_radix = 0, g_part = 0, g_merge = 0;
     int g_radix_wide = 0;        // radix grid of 16-byte records (standalone annihilation)
     bool packed = false;         // 8-byte spawn records (2N <= 32) on the step path
+    bool wide = false;           // two-word keys (N > 31): RecW lists and spawn records
     int guide_kind = 0;
     double w_bond[MAXB];         // importance weight of a configuration differing on bond b only
     int host_status = 0;         // sticky host-visible status
@@ -50,8 +51,8 @@ struct ddqmc_run {
     double kernel_ms[8] = {0};
     int64_t kernel_launches[8] = {0};
     // pinned host staging for import / export, kept between calls
-    Rec *hstage = nullptr;
-    int64_t hstage_cap = 0;
+    unsigned char *hstage = nullptr;
+    size_t hstage_cap = 0;       // bytes
     // counters of standalone annihilation calls (allocated on first use)
     DevState *dAnn = nullptr;
     uint32_t ann_calls = 0;
@@ -107,10 +108,17 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
     P.B = B;
     P.K = 2 * B + N;
     P.nobs = 5 + N + 3 * B + 4;
-    P.npass = (2 * N + 7) / 8;
+    if (N <= NPACK) {
+        P.npass = (2 * N + 7) / 8;                 // digits of the packed key bra << N | ket
+        for (int p = 0; p < P.npass; ++p) P.pass_shift[p] = 8 * p;
+    } else {
+        const int nb = (N + 7) / 8;                // digits of the ket word, then of the bra word
+        P.npass = 2 * nb;
+        for (int p = 0; p < P.npass; ++p) P.pass_shift[p] = p < nb ? 8 * p : 64 + 8 * (p - nb);
+    }
     P.n_a = n_a;
     P.control = o.control;
-    P.nmask = (1ull << N) - 1ull;
+    P.nmask = N >= 64 ? ~0ull : (1ull << N) - 1ull;
     P.seed = o.seed;
     P.target = target;
     const double span_rate = gamma > 0.0 ? gamma : 1.0;
@@ -178,16 +186,22 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
         const int x = k % Lx, y = k / Lx;
         P.rn[k] = (int8_t)((x + 1) % Lx + Lx * y);
         P.dn[k] = (int8_t)(x + Lx * ((y + 1) % Ly));
-        if (Lx > 1 && (x + 1 < Lx || per)) P.ER |= 1u << k;
-        if (Ly > 1 && (y + 1 < Ly || per)) P.ED |= 1u << k;
-        if (x == Lx - 1) P.LC |= 1u << k;
-        if (y == Ly - 1) P.LR |= 1u << k;
     }
-    for (int k = 0; k < N; ++k) {
-        if (P.ER >> k & 1u) P.Emorton |= 1ull << (2 * k);
-        if (P.ED >> k & 1u) P.Emorton |= 1ull << (2 * k + 1);
+    // one-word masks of the popcount formulation (light path, N <= 31 only)
+    if (N <= NPACK) {
+        for (int k = 0; k < N; ++k) {
+            const int x = k % Lx, y = k / Lx;
+            if (Lx > 1 && (x + 1 < Lx || per)) P.ER |= 1u << k;
+            if (Ly > 1 && (y + 1 < Ly || per)) P.ED |= 1u << k;
+            if (x == Lx - 1) P.LC |= 1u << k;
+            if (y == Ly - 1) P.LR |= 1u << k;
+        }
+        for (int k = 0; k < N; ++k) {
+            if (P.ER >> k & 1u) P.Emorton |= 1ull << (2 * k);
+            if (P.ED >> k & 1u) P.Emorton |= 1ull << (2 * k + 1);
+        }
     }
-    bool uni = true;
+    bool uni = N <= NPACK;
     for (int b = 1; b < B; ++b)
         for (int h = 0; h < 2; ++h)
             for (int c = 0; c < 4; ++c) uni = uni && P.rate_q[b][h][c] == P.rate_q[0][h][c];
@@ -207,6 +221,16 @@ template <typename T>
 int dalloc(T **p, size_t n) {
     if (n == 0) n = 1;
     if (cudaMalloc((void **)p, n * sizeof(T)) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return DDQMC_ERR_OOM;
+    }
+    return DDQMC_OK;
+}
+
+int dalloc_bytes(void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
         return DDQMC_ERR_OOM;
@@ -256,12 +280,12 @@ int read_status(ddqmc_run *r) {
     return r->host_status;
 }
 
-// Pinned host staging of at least n records (grown on demand, never shrunk).
-Rec *host_stage(ddqmc_run *r, int64_t n) {
-    if (n <= r->hstage_cap) return r->hstage;
+// Pinned host staging of at least `bytes` bytes (grown on demand, never shrunk).
+unsigned char *host_stage(ddqmc_run *r, size_t bytes) {
+    if (bytes <= r->hstage_cap) return r->hstage;
     if (r->hstage) { cudaFreeHost(r->hstage); r->hstage = nullptr; r->hstage_cap = 0; }
-    const int64_t cap = n + n / 4 + 1024;
-    if (cudaMallocHost((void **)&r->hstage, sizeof(Rec) * (size_t)cap) != cudaSuccess) {
+    const size_t cap = bytes + bytes / 4 + 16384;
+    if (cudaMallocHost((void **)&r->hstage, cap) != cudaSuccess) {
         cudaGetLastError();
         r->hstage = nullptr;
         return nullptr;
@@ -276,10 +300,16 @@ constexpr size_t RX_SMEM = sizeof(RadixShared<Rec>);
 constexpr size_t RXP_SMEM = sizeof(RadixShared<uint64_t>);
 constexpr size_t MG_SMEM = sizeof(MergeShared<Rec>);
 constexpr size_t MGP_SMEM = sizeof(MergeShared<uint64_t>);
+constexpr size_t SPW_SMEM = sizeof(SpawnShared<RecW>);
+constexpr size_t RXW_SMEM = sizeof(RadixShared<RecW>);
+constexpr size_t MGW_SMEM = sizeof(MergeShared<RecW>);
 
-// One step's launches for spawn records of type T (16-byte Rec or packed 8-byte).
+// One step's launches for spawn records of type T (16-byte Rec, packed 8-byte,
+// or two-word RecW), on the list buffers Lc (current) and Ln (next).
 template <typename T>
-void launch_step(ddqmc_run *r, Rec *Lc, Rec *Ln, const std::function<void(int, int)> &mark) {
+void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(int, int)> &mark) {
+    using LT = typename ListOf<T>::type;
+    LT *Lc = reinterpret_cast<LT *>(Lcv), *Ln = reinterpret_cast<LT *>(Lnv);
     const RunParams &P = r->hp;
     T *sp0 = reinterpret_cast<T *>(r->Sp[0]);
     T *sp1 = reinterpret_cast<T *>(r->Sp[1]);
@@ -290,7 +320,7 @@ void launch_step(ddqmc_run *r, Rec *Lc, Rec *Ln, const std::function<void(int, i
     mark(1, 0);
     for (int p = 0; p < P.npass; ++p)
         k_radix_pass<T><<<r->g_radix, RX_TPB, rx_smem, r->stream>>>((p & 1) ? sp1 : sp0, (p & 1) ? sp0 : sp1, r->dS,
-                                                                   r->lb_radix, p, 8 * p, r->rcap);
+                                                                   r->lb_radix, p, P.pass_shift[p], r->rcap);
     mark(1, 1);
     const T *sorted = (P.npass & 1) ? sp1 : sp0;
     mark(2, 0);
@@ -320,8 +350,9 @@ int enqueue_steps(ddqmc_run *r, int64_t nsteps) {
         std::function<void(int, int)> mark = [&](int kc, int edge) {
             if (ev) cudaEventRecord(ev[2 * kc + edge], r->stream);
         };
-        Rec *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
+        void *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
         if (r->packed) launch_step<uint64_t>(r, Lc, Ln, mark);
+        else if (r->wide) launch_step<RecW>(r, Lc, Ln, mark);
         else launch_step<Rec>(r, Lc, Ln, mark);
         mark(KC_FINALIZE, 0);
         k_finalize<<<1, FN_TPB, 0, r->stream>>>(r->dP, r->dS, r->dBlk);
@@ -533,10 +564,13 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     rc |= dalloc(&r->dP, 1);
     rc |= dalloc(&r->dS, 1);
     rc |= dalloc(&r->dBlk, (size_t)NOBS_MAX * LEVELS);
-    rc |= dalloc(&r->L[0], (size_t)mcap);
-    rc |= dalloc(&r->L[1], (size_t)mcap);
-    rc |= dalloc(&r->Sp[0], (size_t)rcap);
-    rc |= dalloc(&r->Sp[1], (size_t)rcap);
+    r->wide = r->hp.N > NPACK;
+    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
+    const size_t ssize = r->wide ? sizeof(RecW) : sizeof(Rec);   // standalone annihilation uses 16-byte Rec
+    rc |= dalloc_bytes(&r->L[0], lsize * (size_t)mcap);
+    rc |= dalloc_bytes(&r->L[1], lsize * (size_t)mcap);
+    rc |= dalloc_bytes(&r->Sp[0], ssize * (size_t)rcap);
+    rc |= dalloc_bytes(&r->Sp[1], ssize * (size_t)rcap);
     rc |= dalloc(&r->lb_radix, (size_t)rtiles * 256);
     rc |= dalloc(&r->lb_merge, (size_t)mtiles);
     rc |= dalloc(&r->splits, (size_t)mtiles + 1);
@@ -553,11 +587,18 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     ok = ok && cudaFuncSetAttribute(k_radix_pass<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RXP_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_merge<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_merge<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MGP_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_spawn_death<RecW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPW_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_radix_pass<RecW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RXW_SMEM) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_merge<RecW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MGW_SMEM) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
     if (r->packed) {
         r->g_spawn = occupancy_grid((const void *)k_spawn_death<uint64_t>, SP_TPB, SPP_SMEM, sms);
         r->g_radix = occupancy_grid((const void *)k_radix_pass<uint64_t>, RX_TPB, RXP_SMEM, sms);
         r->g_merge = occupancy_grid((const void *)k_merge<uint64_t>, MG_TPB, MGP_SMEM, sms);
+    } else if (r->wide) {
+        r->g_spawn = occupancy_grid((const void *)k_spawn_death<RecW>, SP_TPB, SPW_SMEM, sms);
+        r->g_radix = occupancy_grid((const void *)k_radix_pass<RecW>, RX_TPB, RXW_SMEM, sms);
+        r->g_merge = occupancy_grid((const void *)k_merge<RecW>, MG_TPB, MGW_SMEM, sms);
     } else {
         r->g_spawn = occupancy_grid((const void *)k_spawn_death<Rec>, SP_TPB, SP_SMEM, sms);
         r->g_radix = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
@@ -582,12 +623,19 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     first.key = 0;
     first.re = (int32_t)o.n0;
     first.im = 0;
+    RecW firstw;
+    firstw.lo = 0;
+    firstw.hi = 0;
+    firstw.re = (int32_t)o.n0;
+    firstw.im = 0;
     bool okc = cudaMemcpyAsync(r->dP, &r->hp, sizeof(RunParams), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
     okc = okc && cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
     okc = okc && cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * (size_t)NOBS_MAX * LEVELS, r->stream) == cudaSuccess;
     okc = okc && cudaMemsetAsync(r->lb_radix, 0, sizeof(uint64_t) * (size_t)rtiles * 256, r->stream) == cudaSuccess;
     okc = okc && cudaMemsetAsync(r->lb_merge, 0, sizeof(uint64_t) * (size_t)mtiles, r->stream) == cudaSuccess;
-    okc = okc && cudaMemcpyAsync(r->L[0], &first, sizeof(Rec), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    okc = okc && (r->wide ? cudaMemcpyAsync(r->L[0], &firstw, sizeof(RecW), cudaMemcpyHostToDevice, r->stream)
+                          : cudaMemcpyAsync(r->L[0], &first, sizeof(Rec), cudaMemcpyHostToDevice, r->stream)) ==
+                  cudaSuccess;
     okc = okc && cudaStreamSynchronize(r->stream) == cudaSuccess;
     if (!okc) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
     r->cur = 0;
@@ -820,14 +868,24 @@ int ddqmc_export_walkers(ddqmc_run *r, uint64_t *ket, uint64_t *bra, int32_t *re
     *n = M;
     const int64_t m = cap < M ? cap : M;
     if (m <= 0) return DDQMC_OK;
-    Rec *h = host_stage(r, m);
-    if (!h) return DDQMC_ERR_OOM;
+    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
+    unsigned char *hb = host_stage(r, lsize * (size_t)m);
+    if (!hb) return DDQMC_ERR_OOM;
     int rc = DDQMC_OK;
-    if (cudaMemcpyAsync(h, r->L[r->cur], sizeof(Rec) * (size_t)m, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(hb, r->L[r->cur], lsize * (size_t)m, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
         cudaGetLastError();
         rc = DDQMC_ERR_CUDA;
+    } else if (r->wide) {
+        const RecW *h = reinterpret_cast<const RecW *>(hb);
+        for (int64_t q = 0; q < m; ++q) {
+            ket[q] = h[q].lo;
+            bra[q] = h[q].hi;
+            re[q] = h[q].re;
+            im[q] = h[q].im;
+        }
     } else {
+        const Rec *h = reinterpret_cast<const Rec *>(hb);
         const int N = r->hp.N;
         const uint64_t mask = r->hp.nmask;
         for (int64_t q = 0; q < m; ++q) {
@@ -850,15 +908,25 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     const uint64_t mask = r->hp.nmask;
     // make sure no earlier transfer still reads the staging buffer
     if (cudaStreamSynchronize(r->stream) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
-    Rec *h = n > 0 ? host_stage(r, n) : nullptr;
-    if (n > 0 && !h) return DDQMC_ERR_OOM;
+    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
+    unsigned char *hb = n > 0 ? host_stage(r, lsize * (size_t)n) : nullptr;
+    if (n > 0 && !hb) return DDQMC_ERR_OOM;
     for (int64_t q = 0; q < n; ++q) {
         const bool bad = (ket[q] & ~mask) || (bra[q] & ~mask) || (re[q] == 0 && im[q] == 0) ||
                          (q > 0 && (bra[q - 1] > bra[q] || (bra[q - 1] == bra[q] && ket[q - 1] >= ket[q])));
         if (bad) return DDQMC_ERR_INVALID_ARG;
-        h[q].key = (bra[q] << N) | ket[q];
-        h[q].re = re[q];
-        h[q].im = im[q];
+        if (r->wide) {
+            RecW &h = reinterpret_cast<RecW *>(hb)[q];
+            h.lo = ket[q];
+            h.hi = bra[q];
+            h.re = re[q];
+            h.im = im[q];
+        } else {
+            Rec &h = reinterpret_cast<Rec *>(hb)[q];
+            h.key = (bra[q] << N) | ket[q];
+            h.re = re[q];
+            h.im = im[q];
+        }
     }
     // make sure no earlier work of this run is in flight before rewriting its
     // state; the look-back epoch keeps counting so that no status word left
@@ -886,7 +954,7 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     host_death_table(r->hp, S, hs);
     bool ok = true;
     if (n > 0)
-        ok = cudaMemcpyAsync(r->L[r->cur], h, sizeof(Rec) * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+        ok = cudaMemcpyAsync(r->L[r->cur], hb, lsize * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * (size_t)NOBS_MAX * LEVELS, r->stream) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
@@ -900,8 +968,9 @@ int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_
     if (!r || !m_out || m < 0 || nsp < 0 || out_cap < 0 || (m > 0 && !d_list) || (nsp > 0 && !d_spawns) ||
         (out_cap > 0 && !d_out))
         return DDQMC_ERR_INVALID_ARG;
-    if (nsp > r->rcap || m > r->mcap) return DDQMC_ERR_CAPACITY;
     *m_out = 0;
+    if (r->hp.N > NPACK) return DDQMC_ERR_UNSUPPORTED;       // 16-byte records hold one-word keys only
+    if (nsp > r->rcap || m > r->mcap) return DDQMC_ERR_CAPACITY;
     if (!r->dAnn && dalloc(&r->dAnn, 1) != DDQMC_OK) return DDQMC_ERR_OOM;
     const RunParams &P = r->hp;
     DevState hs;
@@ -919,7 +988,7 @@ int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_
     k_digit_histogram<Rec><<<r->g_part, RX_TPB, 0, r->stream>>>(sp, r->dAnn, P.npass);
     const Rec *src = sp;
     for (int p = 0; p < P.npass; ++p) {
-        Rec *dst = r->Sp[p & 1];
+        Rec *dst = reinterpret_cast<Rec *>(r->Sp[p & 1]);
         k_radix_pass<Rec><<<r->g_radix_wide, RX_TPB, RX_SMEM, r->stream>>>(src, dst, r->dAnn, r->lb_radix, p, 8 * p,
                                                                           r->rcap);
         src = dst;
@@ -958,6 +1027,7 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
     rc = build_params(&host_ctx, lattice, 0.0, 0.0, 0.0, 0.0, 1.0, 1, initiator_threshold, nullptr, o);
     if (rc != DDQMC_OK) return rc;
     const RunParams &P = host_ctx.hp;
+    if (P.N > NPACK) return DDQMC_ERR_UNSUPPORTED;           // 16-byte records hold one-word keys only
     DevState hs;
     std::memset(&hs, 0, sizeof(hs));
     hs.M = m;

@@ -81,7 +81,7 @@ k_finalize(const RunParams *__restrict__ Pp, DevState *__restrict__ st, BlkCell 
         st->last_est[q] = s_est[q];
         st->est[q] = 0;
     }
-    for (int q = tid; q < 16; q += FN_TPB) st->tickets[q] = 0u;
+    for (int q = tid; q < MAXPASS + 16; q += FN_TPB) st->tickets[q] = 0u;
     for (int q = tid; q < MAXPASS * 256; q += FN_TPB) (&st->hist[0][0])[q] = 0u;
     if (tid <= 2 * N) death_entry(P, s_S, tid, st);
     if (s_append && tid < nobs) {

@@ -31,15 +31,64 @@ constexpr int MG_IPT = 7;                  // odd: the lanes' merge cursors spre
 constexpr int MG_TILE = 32 * MG_IPT;       // merged positions per warp tile
 constexpr int MG_PCHUNK = 8;               // tile boundaries per partition thread
 
+// ---- keys ----------------------------------------------------------------
+// One-word records compare their packed key (bra << N | ket); two-word
+// records compare (bra, ket) as a 128-bit number.
+struct K128 {
+    uint64_t lo, hi;            // ket word, bra word
+};
+__device__ __forceinline__ bool operator<=(const K128 &a, const K128 &b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
+}
+__device__ __forceinline__ bool operator>(const K128 &a, const K128 &b) { return !(a <= b); }
+__device__ __forceinline__ bool operator==(const K128 &a, const K128 &b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator!=(const K128 &a, const K128 &b) { return !(a == b); }
+
+// Keys of the merge tile: 32-bit when spawn records are packed (2N <= 32).
+template <typename T> struct MergeKey { using type = uint64_t; };
+template <> struct MergeKey<uint64_t> { using type = uint32_t; };
+template <> struct MergeKey<RecW> { using type = K128; };
+
+template <typename KT> __device__ __forceinline__ KT list_key(const Rec &v) { return (KT)v.key; }
+template <typename KT> __device__ __forceinline__ KT list_key(const RecW &v) { return K128{v.lo, v.hi}; }
+template <typename KT, typename T> __device__ __forceinline__ KT spawn_key(const T &v) {
+    return (KT)RecTraits<T>::key(v);
+}
+template <> __device__ __forceinline__ K128 spawn_key<K128, RecW>(const RecW &v) { return K128{v.lo, v.hi}; }
+
+// ket and bra words of a key
+__device__ __forceinline__ void key_words(uint64_t k, uint64_t nmask, int N, uint64_t &i, uint64_t &j) {
+    i = k & nmask;
+    j = k >> N;
+}
+__device__ __forceinline__ void key_words(uint32_t k, uint64_t nmask, int N, uint64_t &i, uint64_t &j) {
+    key_words((uint64_t)k, nmask, N, i, j);
+}
+__device__ __forceinline__ void key_words(const K128 &k, uint64_t, int, uint64_t &i, uint64_t &j) {
+    i = k.lo;
+    j = k.hi;
+}
+
+__device__ __forceinline__ uint64_t shfl_key(uint64_t v, int src) { return __shfl_sync(0xFFFFFFFFu, v, src); }
+__device__ __forceinline__ uint32_t shfl_key(uint32_t v, int src) { return __shfl_sync(0xFFFFFFFFu, v, src); }
+__device__ __forceinline__ K128 shfl_key(const K128 &v, int src) {
+    return K128{__shfl_sync(0xFFFFFFFFu, v.lo, src), __shfl_sync(0xFFFFFFFFu, v.hi, src)};
+}
+
+__device__ __forceinline__ void set_list(Rec &v, uint64_t key) { v.key = key; }
+__device__ __forceinline__ void set_list(Rec &v, uint32_t key) { v.key = (uint64_t)key; }
+__device__ __forceinline__ void set_list(RecW &v, const K128 &key) { v.lo = key.lo; v.hi = key.hi; }
+
 // merge-path split of output diagonal `diag`: number of L elements among the
 // first `diag` merged elements (L before S on equal keys)
-template <typename T>
-__device__ __forceinline__ int64_t merge_split(const Rec *L, int64_t M, const T *S, int64_t R, int64_t diag) {
+template <typename T, typename LT>
+__device__ __forceinline__ int64_t merge_split(const LT *L, int64_t M, const T *S, int64_t R, int64_t diag) {
+    using KT = typename MergeKey<T>::type;
     int64_t lo = diag > R ? diag - R : 0;
     int64_t hi = diag < M ? diag : M;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if (L[mid].key <= RecTraits<T>::key(S[diag - 1 - mid])) lo = mid + 1;
+        if (list_key<KT>(L[mid]) <= spawn_key<KT>(S[diag - 1 - mid])) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -50,8 +99,10 @@ __device__ __forceinline__ int64_t merge_split(const Rec *L, int64_t M, const T 
 // records S[b, rem_end[t]) share the key of the merged element before the
 // boundary; rem_end[t] = b when the run stops there).
 template <typename T>
-__global__ void k_merge_partition(const Rec *__restrict__ L, const T *__restrict__ S, DevState *__restrict__ st,
-                                  int64_t *__restrict__ splits, int64_t *__restrict__ rem_end, int64_t rcap) {
+__global__ void k_merge_partition(const typename ListOf<T>::type *__restrict__ L, const T *__restrict__ S,
+                                  DevState *__restrict__ st, int64_t *__restrict__ splits,
+                                  int64_t *__restrict__ rem_end, int64_t rcap) {
+    using KT = typename MergeKey<T>::type;
     if (st->status) return;
     const int64_t M = st->M;
     int64_t R = st->R;
@@ -76,7 +127,7 @@ __global__ void k_merge_partition(const Rec *__restrict__ L, const T *__restrict
             if (hi > M) hi = M;
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
-                if (L[mid].key <= RecTraits<T>::key(S[diag - 1 - mid])) lo = mid + 1;
+                if (list_key<KT>(L[mid]) <= spawn_key<KT>(S[diag - 1 - mid])) lo = mid + 1;
                 else hi = mid;
             }
             a = lo;
@@ -86,26 +137,26 @@ __global__ void k_merge_partition(const Rec *__restrict__ L, const T *__restrict
         splits[t] = a;
         int64_t e = b;
         if (b < R && diag > 0) {
-            uint64_t last = 0;
-            if (a > 0) last = L[a - 1].key;
+            KT last{};
+            if (a > 0) last = list_key<KT>(L[a - 1]);
             if (b > 0) {
-                const uint64_t k2 = RecTraits<T>::key(S[b - 1]);
-                if (k2 > last) last = k2;
+                const KT k2 = spawn_key<KT>(S[b - 1]);
+                if (a == 0 || k2 > last) last = k2;
             }
-            if (RecTraits<T>::key(S[b]) == last) {
+            if (spawn_key<KT>(S[b]) == last) {
                 // first record after b with a larger key: gallop, then bisect
                 // invariant: S[b, lo) all carry the key; the first other key is in [lo, hi]
                 int64_t lo = b + 1, step = 1, hi = R;
                 for (;;) {
-                    if (lo >= R || RecTraits<T>::key(S[lo]) != last) { hi = lo < R ? lo : R; break; }
+                    if (lo >= R || spawn_key<KT>(S[lo]) != last) { hi = lo < R ? lo : R; break; }
                     const int64_t nxt = lo + step;
-                    if (nxt >= R || RecTraits<T>::key(S[nxt]) != last) { hi = nxt < R ? nxt : R; ++lo; break; }
+                    if (nxt >= R || spawn_key<KT>(S[nxt]) != last) { hi = nxt < R ? nxt : R; ++lo; break; }
                     lo = nxt + 1;
                     step <<= 1;
                 }
                 while (lo < hi) {
                     const int64_t mid = (lo + hi) >> 1;
-                    if (RecTraits<T>::key(S[mid]) == last) lo = mid + 1;
+                    if (spawn_key<KT>(S[mid]) == last) lo = mid + 1;
                     else hi = mid;
                 }
                 e = lo;
@@ -174,10 +225,6 @@ __device__ __forceinline__ SegAgg seg_warp_exclusive(const SegAgg &mine, int lan
     return exc;
 }
 
-// Keys of the merge tile: 32-bit when spawn records are packed (2N <= 32).
-template <typename T> struct MergeKey { using type = uint64_t; };
-template <> struct MergeKey<uint64_t> { using type = uint32_t; };
-
 template <typename T>
 struct MergeWarp {
     typename MergeKey<T>::type key[MG_TILE];   // L keys, then S keys; later the output keys
@@ -195,10 +242,9 @@ struct MergeShared {
 };
 
 template <typename T>
-__device__ __forceinline__ void add_estimators(MergeShared<T> &s, const RunParams &P, uint64_t key, int32_t re,
-                                               int32_t im) {
+__device__ __forceinline__ void add_estimators(MergeShared<T> &s, const RunParams &P, uint64_t i, uint64_t j,
+                                               int32_t re, int32_t im) {
     const int N = P.N, B = P.B;
-    const uint64_t i = key & P.nmask, j = key >> N;
     if (i == j) {
         atomicAdd(&s.est[0], (unsigned long long)(int64_t)re);
         atomicAdd(&s.est[1], (unsigned long long)(int64_t)im);
@@ -232,11 +278,12 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 
 template <typename T>
 __global__ void __launch_bounds__(MG_TPB, 4)
-k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__restrict__ S,
-        Rec *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
+k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__restrict__ L, const T *__restrict__ S,
+        typename ListOf<T>::type *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
         const int64_t *__restrict__ rem_end, uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
     using TR = RecTraits<T>;
     using KT = typename MergeKey<T>::type;
+    using LT = typename ListOf<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MergeShared<T> &s = *reinterpret_cast<MergeShared<T> *>(smem_raw);
     const RunParams &P = *Pp;
@@ -266,7 +313,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
 
     for (;;) {
         int64_t tile = 0;
-        if (lane == 0) tile = (int64_t)atomicAdd(&st->tickets[8], 1u);
+        if (lane == 0) tile = (int64_t)atomicAdd(&st->tickets[MAXPASS], 1u);
         tile = __shfl_sync(0xFFFFFFFFu, tile, 0);
         if (tile >= ntiles) break;
         const int64_t d0 = tile * MG_TILE;
@@ -275,22 +322,22 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
         const int64_t b0 = d0 - a0, b1 = d1 - a1;
         const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
         // key of the merged element before the tile
-        KT pk = 0;
+        KT pk{};
         int hp = 0;
         if (lane == 0) {
-            if (a0 > 0) { pk = (KT)L[a0 - 1].key; hp = 1; }
+            if (a0 > 0) { pk = list_key<KT>(L[a0 - 1]); hp = 1; }
             if (b0 > 0) {
-                const KT k2 = (KT)TR::key(S[b0 - 1]);
+                const KT k2 = spawn_key<KT>(S[b0 - 1]);
                 if (!hp || k2 > pk) pk = k2;
                 hp = 1;
             }
         }
-        pk = __shfl_sync(0xFFFFFFFFu, pk, 0);
+        pk = shfl_key(pk, 0);
         hp = __shfl_sync(0xFFFFFFFFu, hp, 0);
         // load the tile's L and S elements; the S flags go to a bit mask
         for (int q = lane; q < na; q += 32) {
-            const Rec v = L[a0 + q];
-            ws.key[q] = (KT)v.key;
+            const LT v = L[a0 + q];
+            ws.key[q] = list_key<KT>(v);
             ws.val[q] = make_int2(v.re, v.im);
         }
         for (int q0 = 0; q0 < nb; q0 += 32) {
@@ -298,7 +345,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
             bool f = false;
             if (q < nb) {
                 const T v = S[b0 + q];
-                ws.key[na + q] = (KT)TR::key(v);
+                ws.key[na + q] = spawn_key<KT>(v);
                 ws.val[na + q] = make_int2(TR::re(v), TR::im(v));
                 f = TR::flag(v);
             }
@@ -343,7 +390,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                 else hi = mid;
             }
             int ia = lo, ib = dloc - lo;
-            KT prev = 0;
+            KT prev{};
             bool hprev = false;
             if (dloc == 0) { prev = pk; hprev = hp != 0; }
             else {
@@ -357,7 +404,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
             nk = nt - dloc < MG_IPT ? nt - dloc : MG_IPT;
 #pragma unroll
             for (int k = 0; k < MG_IPT; ++k) {
-                ik[k] = 0;
+                ik[k] = KT{};
                 iv[k] = make_int2(0, 0);
                 if (k < nk) {
                     bool fromL;
@@ -377,7 +424,7 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < MG_IPT; ++k) { ik[k] = 0; iv[k] = make_int2(0, 0); }
+            for (int k = 0; k < MG_IPT; ++k) { ik[k] = KT{}; iv[k] = make_int2(0, 0); }
         }
         // ---- 2. segmented reduction of the runs over the lanes ---------------
         SegAgg tail = seg_identity();
@@ -413,7 +460,9 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
                     run.uim += ru1;
                 }
                 if (ends && owned) {
-                    const bool open = run.hasL || no_init || (((uint64_t)ik[k] & nmask) == ((uint64_t)ik[k] >> N));
+                    uint64_t ki, kj;
+                    key_words(ik[k], nmask, N, ki, kj);
+                    const bool open = run.hasL || no_init || ki == kj;
                     const int64_t sre = run.fre + (open ? run.ure : 0);
                     const int64_t sim = run.fim + (open ? run.uim : 0);
                     if (sre != 0 || sim != 0) {
@@ -467,15 +516,16 @@ k_merge(const RunParams *__restrict__ Pp, const Rec *__restrict__ L, const T *__
             if (lane == 0) local_status |= ST_CAPACITY | ST_CAP_LIST;
         } else {
             for (uint32_t q = lane; q < total; q += 32) {
-                Rec v;
-                v.key = (uint64_t)ws.key[q];
+                LT v;
+                set_list(v, ws.key[q]);
                 v.re = ws.val[q].x;
                 v.im = ws.val[q].y;
                 out[ob + q] = v;
                 my_w += iabs64(v.re) + iabs64(v.im);
                 my_m += 1;
-                const uint64_t i = v.key & nmask, j = v.key >> N;
-                if (i == j || __popcll(i ^ j) == 2) add_estimators(s, P, v.key, v.re, v.im);
+                uint64_t i, j;
+                key_words(ws.key[q], nmask, N, i, j);
+                if (i == j || __popcll(i ^ j) == 2) add_estimators(s, P, i, j, v.re, v.im);
             }
         }
         __syncwarp();

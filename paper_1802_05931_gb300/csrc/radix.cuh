@@ -26,17 +26,36 @@ template <typename T> struct RecTraits;
 template <> struct RecTraits<Rec> {
     static constexpr int IPT = 8;      // records per thread in a radix tile
     __device__ __forceinline__ static uint64_t key(const Rec &r) { return r.key & KEY_MASK; }
+    __device__ __forceinline__ static uint32_t digit(const Rec &r, int shift) {
+        return (uint32_t)((r.key & KEY_MASK) >> shift) & 0xFFu;
+    }
     __device__ __forceinline__ static bool flag(const Rec &r) { return (r.key & FLAG_BIT) != 0ull; }
     __device__ __forceinline__ static int32_t re(const Rec &r) { return r.re; }
     __device__ __forceinline__ static int32_t im(const Rec &r) { return r.im; }
     __device__ __forceinline__ static Rec empty() { Rec r; r.key = 0; r.re = 0; r.im = 0; return r; }
 };
 
+// Two-word records: digits of the ket word at shifts 0..63, of the bra word at 64..127.
+template <> struct RecTraits<RecW> {
+    static constexpr int IPT = 6;
+    __device__ __forceinline__ static uint32_t digit(const RecW &r, int shift) {
+        return (uint32_t)(shift < 64 ? (r.lo >> shift) : (r.hi >> (shift - 64))) & 0xFFu;
+    }
+    __device__ __forceinline__ static bool flag(const RecW &r) { return (r.re & 1) != 0; }
+    __device__ __forceinline__ static int32_t re(const RecW &r) { return r.re >> 1; }
+    __device__ __forceinline__ static int32_t im(const RecW &r) { return r.im; }
+    __device__ __forceinline__ static RecW empty() { RecW r; r.lo = 0; r.hi = 0; r.re = 0; r.im = 0; return r; }
+};
+
 constexpr int PK_LIM = 16383;          // largest |Delta| of one packed record
+constexpr int WK_LIM = 1 << 29;        // largest |Delta| of one two-word spawn record
 
 template <> struct RecTraits<uint64_t> {
     static constexpr int IPT = 16;
     __device__ __forceinline__ static uint64_t key(uint64_t r) { return r >> 32; }
+    __device__ __forceinline__ static uint32_t digit(uint64_t r, int shift) {
+        return (uint32_t)((r >> 32) >> shift) & 0xFFu;
+    }
     __device__ __forceinline__ static bool flag(uint64_t r) { return ((r >> 31) & 1ull) != 0ull; }
     __device__ __forceinline__ static int32_t re(uint64_t r) { return ((int32_t)((uint32_t)r << 17)) >> 17; }
     __device__ __forceinline__ static int32_t im(uint64_t r) { return ((int32_t)((uint32_t)(r >> 15) << 17)) >> 17; }
@@ -51,7 +70,7 @@ __device__ __forceinline__ uint64_t pack_rec(uint64_t key, bool flag, int re, in
 
 constexpr int RX_TPB = 256;                  // one thread per digit value
 constexpr int RX_WARPS = RX_TPB / 32;
-constexpr int RX_TILE_MIN = RX_TPB * 8;      // smallest tile (sizes the look-back words)
+constexpr int RX_TILE_MIN = RX_TPB * 6;      // smallest tile (sizes the look-back words)
 constexpr int LB_BATCH = 8;                  // look-back words read together
 
 template <typename T>
@@ -77,8 +96,8 @@ k_digit_histogram(const T *__restrict__ in, DevState *__restrict__ st, int npass
     __syncthreads();
     const int64_t R = st->R;
     for (int64_t q = (int64_t)blockIdx.x * RX_TPB + tid; q < R; q += (int64_t)gridDim.x * RX_TPB) {
-        const uint64_t key = RecTraits<T>::key(in[q]);
-        for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(key >> (8 * p)) & 0xFFull], 1u);
+        const T r = in[q];
+        for (int p = 0; p < npass; ++p) atomicAdd(&h[p][RecTraits<T>::digit(r, 8 * p)], 1u);
     }
     __syncthreads();
     for (int q = tid; q < npass * 256; q += RX_TPB)
@@ -137,7 +156,7 @@ k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict
             const int64_t idx = wbase + q * 32 + lane;
             if (idx < R) {
                 r[q] = in[idx];
-                dg[q] = (uint32_t)((TR::key(r[q]) >> shift) & 0xFFull);
+                dg[q] = TR::digit(r[q], shift);
             } else {
                 r[q] = TR::empty();
                 dg[q] = 0x100u + lane;            // unique sentinel, never counted
@@ -218,7 +237,7 @@ k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict
         if (nvalid > TILE) nvalid = TILE;
         for (int q = tid; q < nvalid; q += RX_TPB) {
             const T v = s.stage[q];
-            const uint32_t d = (uint32_t)((TR::key(v) >> shift) & 0xFFull);
+            const uint32_t d = TR::digit(v, shift);
             out[s.gbase[d] + q] = v;
         }
         __syncthreads();

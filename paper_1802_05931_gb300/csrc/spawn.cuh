@@ -65,18 +65,23 @@ struct LightSoA {
 // Tables of one warp-cooperative configuration: running rate sums of the
 // moves in move order, the move index of each slot (ket b, bra B + b, jump
 // 2B + k) and the children counted per slot.
+template <int KM>
 struct HeavyTables {
-    uint64_t cum[MAXK];
-    int32_t cnt_re[MAXK];
-    int32_t cnt_im[MAXK];
-    int16_t mv[MAXK];
+    uint64_t cum[KM];
+    int32_t cnt_re[KM];
+    int32_t cnt_im[KM];
+    int16_t mv[KM];
 };
+
+// moves per configuration: 2 * 62 bonds + 31 sites for one-word keys
+constexpr int MAXK_PACK = 2 * 2 * NPACK + NPACK + 1;
 
 // A warp's light-configuration parameters are dead before its heavy
 // configurations start, so the two share storage.
+template <typename T>
 union WarpScratch {
     LightSoA le;
-    HeavyTables hv;
+    HeavyTables<std::is_same<T, RecW>::value ? MAXK : MAXK_PACK> hv;
 };
 
 // Constant tables of one step, staged in shared memory.
@@ -93,17 +98,18 @@ struct SpawnTables {
     int32_t d_sgn[2 * MAXN + 1];
     int8_t bond_a[MAXB], bond_b[MAXB];
     int8_t rn[MAXN + 1], dn[MAXN + 1];
+    int32_t pass_shift[MAXPASS];
 };
 
 // Shared memory of the spawn kernel for spawn records of type T; packed
 // records (keys of at most 32 bits) need at most four digit passes.
 template <typename T>
 struct SpawnShared : SpawnTables {
-    static constexpr int NP = sizeof(T) == 8 ? 4 : MAXPASS;
+    static constexpr int NP = sizeof(T) == 8 ? 4 : (std::is_same<T, RecW>::value ? MAXPASS : 8);
     uint32_t hist[NP][256];
     int32_t stage_n[SP_WARPS];
     T stage[SP_WARPS][SP_STAGE];
-    WarpScratch ws[SP_WARPS];
+    WarpScratch<T> ws[SP_WARPS];
     int32_t mark[SP_WARPS][32];       // configuration starting at each walker position of a window
     int32_t dre[SP_WARPS][32], dim[SP_WARPS][32];
     uint64_t qv[SP_WARPS][64];        // queued spawn draws: scaled uniform v
@@ -270,13 +276,15 @@ __device__ __forceinline__ int seg_select32(const SpawnCtx &c, const uint32_t *r
 
 // ---- per-move tables (heavy path) -------------------------------------------
 
-// Child key of move m of configuration (i, j) and the sign factor g of the
-// move: a real parent of sign s makes an imaginary child of sign s*g and an
-// imaginary parent a real child of sign -s*g (bond flips); jumps keep the type.
-__device__ __forceinline__ void move_key(const SpawnCtx &c, const RunParams &P, uint64_t i, uint64_t j, int m,
-                                         uint64_t &ckey, int &g, bool &jump) {
+// Child (ci, cj) of move m of configuration (i, j) and the sign factor g of
+// the move: a real parent of sign s makes an imaginary child of sign s*g and
+// an imaginary parent a real child of sign -s*g (bond flips); jumps keep the
+// type.
+__device__ __forceinline__ void move_child(const SpawnCtx &c, const RunParams &P, uint64_t i, uint64_t j, int m,
+                                           uint64_t &ci, uint64_t &cj, int &g, bool &jump) {
     const SpawnTables &s = *c.sh;
-    uint64_t ci = i, cj = j;
+    ci = i;
+    cj = j;
     jump = m >= 2 * c.B;
     g = 1;
     if (!jump) {
@@ -292,26 +300,37 @@ __device__ __forceinline__ void move_key(const SpawnCtx &c, const RunParams &P, 
         ci &= ~(1ull << k);
         cj &= ~(1ull << k);
     }
-    ckey = (cj << c.N) | ci;
 }
 
 // ---- record output ----------------------------------------------------------
 
-template <typename T> __device__ __forceinline__ T make_spawn(uint64_t key, bool flag, int re, int im);
-template <> __device__ __forceinline__ Rec make_spawn<Rec>(uint64_t key, bool flag, int re, int im) {
+template <typename T>
+__device__ __forceinline__ T make_spawn(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im);
+template <>
+__device__ __forceinline__ Rec make_spawn<Rec>(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im) {
     Rec r;
-    r.key = key | (flag ? FLAG_BIT : 0ull);
+    r.key = ((cj << N) | ci) | (flag ? FLAG_BIT : 0ull);
     r.re = re;
     r.im = im;
     return r;
 }
-template <> __device__ __forceinline__ uint64_t make_spawn<uint64_t>(uint64_t key, bool flag, int re, int im) {
-    return pack_rec(key, flag, re, im);
+template <>
+__device__ __forceinline__ uint64_t make_spawn<uint64_t>(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im) {
+    return pack_rec((cj << N) | ci, flag, re, im);
+}
+template <>
+__device__ __forceinline__ RecW make_spawn<RecW>(uint64_t ci, uint64_t cj, int, bool flag, int re, int im) {
+    RecW r;
+    r.lo = ci;
+    r.hi = cj;
+    r.re = (int32_t)((uint32_t)re << 1) | (flag ? 1 : 0);
+    r.im = im;
+    return r;
 }
 
 template <typename T>
-__device__ __forceinline__ void count_digits(SpawnShared<T> &s, uint64_t key, int npass) {
-    for (int p = 0; p < npass; ++p) atomicAdd(&s.hist[p][(key >> (8 * p)) & 0xFFull], 1u);
+__device__ __forceinline__ void count_digits(SpawnShared<T> &s, const T &r, int npass) {
+    for (int p = 0; p < npass; ++p) atomicAdd(&s.hist[p][RecTraits<T>::digit(r, s.pass_shift[p])], 1u);
 }
 
 // Append one record from a (possibly divergent) lane.
@@ -333,7 +352,7 @@ __device__ __forceinline__ void emit(SpawnShared<T> &s, int warp, const T &r, T 
         const unsigned long long idx = atomicAdd((unsigned long long *)&st->R, 1ull);
         if ((int64_t)idx < cap) {
             out[idx] = r;
-            count_digits(s, RecTraits<T>::key(r), npass);
+            count_digits(s, r, npass);
         } else {
             atomicOr(&st->status, ST_CAPACITY | ST_CAP_SPAWN);
         }
@@ -341,17 +360,19 @@ __device__ __forceinline__ void emit(SpawnShared<T> &s, int warp, const T &r, T 
 }
 
 // Append an aggregated child (any int32 counts): packed records carry at most
-// PK_LIM walkers per part, so large counts become several records.
+// PK_LIM walkers per part and two-word records WK_LIM, so large counts become
+// several records.
 template <typename T>
-__device__ __forceinline__ void emit_counts(SpawnShared<T> &s, int warp, uint64_t key, bool flag, int cre, int cim,
-                                            T *out, int64_t cap, DevState *st, int npass) {
-    if constexpr (sizeof(T) == sizeof(Rec)) {
-        emit(s, warp, make_spawn<T>(key, flag, cre, cim), out, cap, st, npass);
+__device__ __forceinline__ void emit_counts(SpawnShared<T> &s, int warp, uint64_t ci, uint64_t cj, int N, bool flag,
+                                            int cre, int cim, T *out, int64_t cap, DevState *st, int npass) {
+    if constexpr (std::is_same<T, Rec>::value) {
+        emit(s, warp, make_spawn<T>(ci, cj, N, flag, cre, cim), out, cap, st, npass);
     } else {
+        constexpr int LIM = std::is_same<T, RecW>::value ? WK_LIM : PK_LIM;
         while (cre != 0 || cim != 0) {
-            const int pr = cre > PK_LIM ? PK_LIM : (cre < -PK_LIM ? -PK_LIM : cre);
-            const int pi = cim > PK_LIM ? PK_LIM : (cim < -PK_LIM ? -PK_LIM : cim);
-            emit(s, warp, make_spawn<T>(key, flag, pr, pi), out, cap, st, npass);
+            const int pr = cre > LIM ? LIM : (cre < -LIM ? -LIM : cre);
+            const int pi = cim > LIM ? LIM : (cim < -LIM ? -LIM : cim);
+            emit(s, warp, make_spawn<T>(ci, cj, N, flag, pr, pi), out, cap, st, npass);
             cre -= pr;
             cim -= pi;
         }
@@ -374,7 +395,7 @@ __device__ __forceinline__ void flush(SpawnShared<T> &s, int warp, int lane, T *
             const T r = stage[k];
             if ((int64_t)(base + k) < cap) {
                 out[base + k] = r;
-                count_digits(s, RecTraits<T>::key(r), npass);
+                count_digits(s, r, npass);
             }
         }
         if (lane == 0 && (int64_t)(base + n) > cap) atomicOr(&st->status, ST_CAPACITY | ST_CAP_SPAWN);
@@ -441,18 +462,20 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
             cj &= ~(1u << k);
             if (part == 0) cre = sig; else cim = sig;
         }
-        emit(s, warp, make_spawn<T>(((uint64_t)cj << N) | (uint64_t)ci, q.init[o] != 0, cre, cim), out, cap, st,
-             npass);
+        emit(s, warp, make_spawn<T>((uint64_t)ci, (uint64_t)cj, N, q.init[o] != 0, cre, cim), out, cap, st, npass);
     }
     __syncwarp();
 }
 
 template <typename T>
 __global__ void __launch_bounds__(SP_TPB, 3)
-k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *__restrict__ L,
+k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typename ListOf<T>::type *__restrict__ L,
               T *__restrict__ out, int64_t cap) {
-    // packed records <=> N <= 16 <=> 32-bit bond masks
+    // packed records <=> N <= 16 <=> 32-bit bond masks; two-word records: every
+    // configuration on the warp-cooperative path
     using MT = typename std::conditional<sizeof(T) == 8, uint32_t, uint64_t>::type;
+    using LT = typename ListOf<T>::type;
+    constexpr bool WIDE = std::is_same<T, RecW>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SpawnShared<T> &s = *reinterpret_cast<SpawnShared<T> *>(smem_raw);
     const RunParams &P = *Pp;
@@ -466,6 +489,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
         s.bond_b[q] = (int8_t)P.bond_b[q];
     }
     for (int q = tid; q < N; q += SP_TPB) { s.rn[q] = P.rn[q]; s.dn[q] = P.dn[q]; }
+    for (int q = tid; q < MAXPASS; q += SP_TPB) s.pass_shift[q] = P.pass_shift[q];
     if (tid < 8) {
         s.urate8[tid] = P.urate8[tid];
         s.urate32[tid] = (uint32_t)P.urate8[tid];
@@ -493,17 +517,23 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
     const int64_t nwarps = (int64_t)gridDim.x * SP_WARPS;
     for (int64_t chunk = (int64_t)blockIdx.x * SP_WARPS + warp; chunk * 32 < M; chunk += nwarps) {
         const int64_t e = chunk * 32 + lane;
-        Rec rec;
-        rec.key = 0; rec.re = 0; rec.im = 0;
-        if (e < M) rec = L[e];
-        const uint64_t i = rec.key & nmask, j = rec.key >> N;
+        LT rec;
+        uint64_t i = 0, j = 0;
+        rec.re = 0;
+        rec.im = 0;
+        if (e < M) {
+            rec = L[e];
+            if constexpr (WIDE) { i = rec.lo; j = rec.hi; }
+            else { i = rec.key & nmask; j = rec.key >> N; }
+        }
         const int64_t nre = iabs64(rec.re), nim = iabs64(rec.im);
         const int64_t nw = nre + nim;
         const bool valid = e < M;
-        const bool heavy = valid && (nw > SP_HEAVY || !uniform);
+        const bool heavy = valid && (WIDE || nw > SP_HEAVY || !uniform);
         const bool light = valid && !heavy;
         const bool init = (n_a == 0) || (i == j) || (nw > (int64_t)n_a);
 
+        if constexpr (!WIDE) {
         // ---- light configurations: per-configuration setup, one lane each ----
         int nl = 0;
         if (light) {
@@ -655,6 +685,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
             if (iabs64(re2) > 2147483647ll || iabs64(im2) > 2147483647ll) local_status |= ST_OVERFLOW;
             *reinterpret_cast<int2 *>(&L[e].re) = make_int2((int32_t)re2, (int32_t)im2);
         }
+        }    // light configurations
         flush(s, warp, lane, out, cap, st, npass, SP_FLUSH);
 
         // ---- heavy configurations: the whole warp on one configuration -------
@@ -673,43 +704,42 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                 const uint64_t hd = hi ^ hj;
                 const unsigned lt = (1u << lane) - 1u;
                 int base = 0;
+                // bond lane + 32 q of slot q; slots in order keep bond order in a group
+                constexpr int NSLOT = (WIDE ? MAXB : 2 * NPACK + 2) / 32;
                 for (int seg = 0; seg < 2; ++seg) {
                     const uint64_t w = seg == 0 ? hi : hj;
-                    int g0 = -1, g1 = -1;
-                    uint64_t r0 = 0, r1 = 0;
-                    if (lane < B) {
-                        const int a0 = s.bond_a[lane], a1 = s.bond_b[lane];
-                        const int anti = (int)(((w >> a0) ^ (w >> a1)) & 1ull);
-                        const int cl = imp_class(c.gk, hd, s.bond_m[lane], a0, a1);
-                        g0 = 4 * anti + cl;
-                        r0 = P.rate_q[lane][anti][cl];
-                    }
-                    if (lane + 32 < B) {
-                        const int a0 = s.bond_a[lane + 32], a1 = s.bond_b[lane + 32];
-                        const int anti = (int)(((w >> a0) ^ (w >> a1)) & 1ull);
-                        const int cl = imp_class(c.gk, hd, s.bond_m[lane + 32], a0, a1);
-                        g1 = 4 * anti + cl;
-                        r1 = P.rate_q[lane + 32][anti][cl];
+                    int gq[NSLOT];
+                    uint64_t rq[NSLOT];
+#pragma unroll
+                    for (int q = 0; q < NSLOT; ++q) {
+                        const int b = lane + 32 * q;
+                        gq[q] = -1;
+                        rq[q] = 0;
+                        if (b < B) {
+                            const int a0 = s.bond_a[b], a1 = s.bond_b[b];
+                            const int anti = (int)(((w >> a0) ^ (w >> a1)) & 1ull);
+                            const int cl = imp_class(c.gk, hd, s.bond_m[b], a0, a1);
+                            gq[q] = 4 * anti + cl;
+                            rq[q] = P.rate_q[b][anti][cl];
+                        }
                     }
                     for (int g = 0; g < 8; ++g) {
-                        const unsigned m0 = __ballot_sync(0xFFFFFFFFu, g0 == g);
-                        const unsigned m1 = __ballot_sync(0xFFFFFFFFu, g1 == g);
-                        if (g0 == g) {
-                            const int pos = base + __popc(m0 & lt);
-                            s.ws[warp].hv.cum[pos] = r0;
-                            s.ws[warp].hv.mv[pos] = (int16_t)(seg * B + lane);
+#pragma unroll
+                        for (int q = 0; q < NSLOT; ++q) {
+                            if (32 * q >= B) break;
+                            const unsigned mq = __ballot_sync(0xFFFFFFFFu, gq[q] == g);
+                            if (gq[q] == g) {
+                                const int pos = base + __popc(mq & lt);
+                                s.ws[warp].hv.cum[pos] = rq[q];
+                                s.ws[warp].hv.mv[pos] = (int16_t)(seg * B + lane + 32 * q);
+                            }
+                            base += __popc(mq);
                         }
-                        if (g1 == g) {
-                            const int pos = base + __popc(m0) + __popc(m1 & lt);
-                            s.ws[warp].hv.cum[pos] = r1;
-                            s.ws[warp].hv.mv[pos] = (int16_t)(seg * B + lane + 32);
-                        }
-                        base += __popc(m0) + __popc(m1);
                     }
                 }
-                if (lane < N) {
-                    s.ws[warp].hv.cum[2 * B + lane] = (((hi & hj) >> lane) & 1ull) ? c.jump_q : 0ull;
-                    s.ws[warp].hv.mv[2 * B + lane] = (int16_t)(2 * B + lane);
+                for (int k = lane; k < N; k += 32) {
+                    s.ws[warp].hv.cum[2 * B + k] = (((hi & hj) >> k) & 1ull) ? c.jump_q : 0ull;
+                    s.ws[warp].hv.mv[2 * B + k] = (int16_t)(2 * B + k);
                 }
                 __syncwarp();
             }
@@ -745,7 +775,11 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                 const int64_t n = iabs64(pop);
                 const int sig = pop < 0 ? -1 : 1;
                 for (int64_t w = lane; w < n; w += 32) {
-                    const uint4 ctr = make_uint4((uint32_t)hi, (uint32_t)hj, (uint32_t)w, (uint32_t)part << 16);
+                    // counter words: the spin words, their high halves folded in
+                    // (zero for N <= 32)
+                    const uint4 ctr = make_uint4((uint32_t)hi ^ ((uint32_t)(hi >> 32) * 0x9E3779B9u),
+                                                 (uint32_t)hj ^ ((uint32_t)(hj >> 32) * 0x85EBCA6Bu), (uint32_t)w,
+                                                 (uint32_t)part << 16);
                     const uint4 x = philox4x32_10(ctr, k0, k1);
                     const int64_t cnt = (int64_t)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
                     const int64_t cc = (int64_t)s.cross_int[adz] + ((uint64_t)x.z < s.cross_frac[adz] ? 1 : 0);
@@ -762,10 +796,10 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
                             const int mid = (lo + hi2) >> 1;
                             if (v < s.ws[warp].hv.cum[mid]) hi2 = mid; else lo = mid + 1;
                         }
-                        uint64_t ck;
+                        uint64_t ci, cj;
                         int gsg;
                         bool jump;
-                        move_key(c, P, hi, hj, s.ws[warp].hv.mv[lo], ck, gsg, jump);
+                        move_child(c, P, hi, hj, s.ws[warp].hv.mv[lo], ci, cj, gsg, jump);
                         // child type (0 real, 1 imaginary) and signed unit
                         const int tgt = jump ? part : 1 - part;
                         const int val = jump ? sig : (part == 0 ? sig * gsg : -sig * gsg);
@@ -795,11 +829,11 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, Rec *
             for (int m = lane; m < K; m += 32) {
                 const int32_t cre = s.ws[warp].hv.cnt_re[m], cim = s.ws[warp].hv.cnt_im[m];
                 if (cre == 0 && cim == 0) continue;
-                uint64_t ck;
+                uint64_t ci, cj;
                 int gsg;
                 bool jump;
-                move_key(c, P, hi, hj, s.ws[warp].hv.mv[m], ck, gsg, jump);
-                emit_counts(s, warp, ck, hinit, cre, cim, out, cap, st, npass);
+                move_child(c, P, hi, hj, s.ws[warp].hv.mv[m], ci, cj, gsg, jump);
+                emit_counts(s, warp, ci, cj, N, hinit, cre, cim, out, cap, st, npass);
             }
             flush(s, warp, lane, out, cap, st, npass, SP_FLUSH);
         }

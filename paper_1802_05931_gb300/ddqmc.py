@@ -15,8 +15,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libddqmc.so")
 
-MAX_SITES = 31
-MAX_BONDS = 64
+MAX_SITES = 64
+MAX_BONDS = 128
 
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CAPACITY", -4: "OVERFLOW", -5: "TIMEOUT",
           -6: "CUDA", -7: "UNSUPPORTED"}

@@ -84,3 +84,14 @@ def test_annihilate_rejects_too_many_spawns(env):
     with pytest.raises(ddqmc.DDQMCError) as e:
         ddqmc.ddqmc_annihilate(run.h, x.data_ptr(), 0, x.data_ptr(), 8192, x.data_ptr(), 8192)
     assert e.value.code == -3
+
+
+def test_annihilate_rejects_two_word_keys(env):
+    """The 16-byte records of the standalone annihilation hold one-word keys
+    (N <= 31); a run with more sites is refused, not misread."""
+    torch, ddqmc = env
+    run = ddqmc.Run(6, 6, 1, 0.9, 1.0, 1.0, 1.0, 0.005, 100)
+    x = torch.empty(16 * 64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ddqmc.DDQMCError) as e:
+        ddqmc.ddqmc_annihilate(run.h, x.data_ptr(), 1, x.data_ptr(), 1, x.data_ptr(), 64)
+    assert e.value.code == -7          # DDQMC_ERR_UNSUPPORTED

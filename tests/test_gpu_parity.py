@@ -128,6 +128,49 @@ def test_wide_keys_bitexact(ddqmc, Lx, Ly, per):
         _same(gpu, cpu, t)
 
 
+TWO_WORD = [
+    # (Lx, Ly, periodic, Jx, extra options): more than 31 sites
+    (4, 8, 1, 0.9, {}),
+    (5, 7, 0, 0.9, {}),
+    (6, 6, 1, 1.1, {}),
+    (6, 6, 1, 0.9, dict(guide_kind=2, site_ratio=[0.4 + 0.01 * k for k in range(36)])),
+    (8, 8, 1, 0.9, {}),
+]
+
+
+@pytest.mark.parametrize("Lx,Ly,per,Jx,extra", TWO_WORD)
+def test_two_word_keys_bitexact(ddqmc, Lx, Ly, per, Jx, extra):
+    """More than 31 sites (up to the 6x6 and 8x8 lattices): one 64-bit word per
+    side, 24-byte records, radix digits of the ket word then of the bra word,
+    128-bit merge keys, every configuration on the warp-cooperative path."""
+    args = (Lx, Ly, per, Jx, 1.0, 1.0, 1.0, 0.005, 20000)
+    kw = dict(n_a=3, control=1, seed=4)
+    kw.update(extra)
+    # the 8x8 lattice spawns about 2.7 children per walker and step
+    gpu = ddqmc.Run(*args, capacity_entries=1 << 20, capacity_spawns=1 << 21, **kw)
+    cpu = O.OracleRun(*args, **kw)
+    for t in range(100):
+        gpu.step(1)
+        cpu.step(1)
+        if t % 5 == 0 or t >= 97:
+            _same(gpu, cpu, t)
+    assert gpu.export()[0].size > 1000
+
+
+def test_two_word_keys_larger_population(ddqmc):
+    """6x6 periodic grown to 3 x 10^5 walkers, then stepped on both sides."""
+    args = (6, 6, 1, 0.9, 1.0, 1.0, 1.0, 0.005, 300000)
+    kw = dict(n_a=3, control=1, seed=12, n0=20000)
+    gpu = ddqmc.Run(*args, **kw)
+    cpu = O.OracleRun(*args, **kw)
+    for t in range(40):
+        gpu.step(1)
+        cpu.step(1)
+    _same(gpu, cpu, 40)
+    k, b, re, im = gpu.export()
+    assert int(np.abs(re, dtype=np.int64).sum() + np.abs(im, dtype=np.int64).sum()) > 10 ** 5
+
+
 def test_single_step_from_imported_state(ddqmc):
     """Grow a 4x4 population on the GPU, then step the exported state once on
     both sides (the oracle imports the GPU's list and scalar state)."""
@@ -196,8 +239,8 @@ def test_invalid_arguments_rejected(ddqmc):
         ddqmc.Run(2, 2, 1, 0.9, 1.0, 1.0, 1.0, 0.01, 100)       # L = 2 periodic
     assert e.value.code == -1
     with pytest.raises(ddqmc.DDQMCError) as e:
-        ddqmc.Run(8, 4, 0, 0.9, 1.0, 1.0, 1.0, 0.01, 100)       # 32 sites
-    assert e.value.code == -7
+        ddqmc.Run(9, 8, 0, 0.9, 1.0, 1.0, 1.0, 0.01, 100)       # 72 sites: more than one word per side
+    assert e.value.code == -1
     run = ddqmc.Run(2, 2, 0, 0.9, 1.0, 1.0, 1.0, 0.01, 100)
     with pytest.raises(ddqmc.DDQMCError):
         run.import_([1, 0], [0, 0], [1, 1], [0, 0], 0, 0.0)      # not in canonical order
