@@ -71,13 +71,14 @@ struct RunParams {
     int8_t pair_bond[MAXN * MAXN];    // bond index of an (a, b) site pair, -1 if none
     // square-lattice geometry for the mask formulation of the rates
     int32_t Lx, shD;                  // row length; Lx * (Ly - 1)
-    uint32_t ER, ED;                  // sites owning a bond to the right / below
-    uint32_t LC, LR;                  // last column / last row
+    uint64_t ER, ED;                  // sites owning a bond to the right / below
+    uint64_t LC, LR;                  // last column / last row
     int8_t rn[MAXN], dn[MAXN];        // right / lower neighbour of each site
     int32_t uniform;                  // 1 if every bond has the same rate table
     int32_t pad1;
     int32_t pass_shift[MAXPASS];      // key bit where the digit of each radix pass starts
-    uint64_t Emorton;                 // bond-existence mask, bit 2k = right bond of k, 2k+1 = lower
+    uint64_t Emorton;                 // bond-existence mask, bit 2k = right bond of k, 2k+1 = lower (sites < 32)
+    uint64_t Emorton_hi;              // the same for sites 32..63 (bit 2(k-32), 2(k-32)+1)
     uint64_t urate8[8];               // rate of group 4*anti + class when every bond has the same table
 };
 

@@ -187,21 +187,21 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
         P.rn[k] = (int8_t)((x + 1) % Lx + Lx * y);
         P.dn[k] = (int8_t)(x + Lx * ((y + 1) % Ly));
     }
-    // one-word masks of the popcount formulation (light path, N <= 31 only)
-    if (N <= NPACK) {
-        for (int k = 0; k < N; ++k) {
-            const int x = k % Lx, y = k / Lx;
-            if (Lx > 1 && (x + 1 < Lx || per)) P.ER |= 1u << k;
-            if (Ly > 1 && (y + 1 < Ly || per)) P.ED |= 1u << k;
-            if (x == Lx - 1) P.LC |= 1u << k;
-            if (y == Ly - 1) P.LR |= 1u << k;
-        }
-        for (int k = 0; k < N; ++k) {
-            if (P.ER >> k & 1u) P.Emorton |= 1ull << (2 * k);
-            if (P.ED >> k & 1u) P.Emorton |= 1ull << (2 * k + 1);
-        }
+    // site and bond masks of the popcount formulation (light path)
+    for (int k = 0; k < N; ++k) {
+        const int x = k % Lx, y = k / Lx;
+        if (Lx > 1 && (x + 1 < Lx || per)) P.ER |= 1ull << k;
+        if (Ly > 1 && (y + 1 < Ly || per)) P.ED |= 1ull << k;
+        if (x == Lx - 1) P.LC |= 1ull << k;
+        if (y == Ly - 1) P.LR |= 1ull << k;
     }
-    bool uni = N <= NPACK;
+    for (int k = 0; k < N; ++k) {
+        uint64_t &E = k < 32 ? P.Emorton : P.Emorton_hi;
+        const int kk = k & 31;
+        if (P.ER >> k & 1ull) E |= 1ull << (2 * kk);
+        if (P.ED >> k & 1ull) E |= 1ull << (2 * kk + 1);
+    }
+    bool uni = true;
     for (int b = 1; b < B; ++b)
         for (int h = 0; h < 2; ++h)
             for (int c = 0; c < 4; ++c) uni = uni && P.rate_q[b][h][c] == P.rate_q[0][h][c];

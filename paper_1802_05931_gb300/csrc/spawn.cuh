@@ -51,13 +51,30 @@ constexpr int SP_STAGE = 128;      // staged records per warp
 constexpr int SP_FLUSH = 32;       // flush threshold at warp-uniform points
 constexpr int SP_HEAVY = 1024;     // configurations with more walkers use the warp-cooperative path
 
+// 128-bit bond mask (two-word keys: bonds 2k, 2k+1 of sites k < 32 in lo,
+// of sites k >= 32 in hi).
+struct U128 {
+    uint64_t lo, hi;
+};
+__device__ __forceinline__ U128 operator&(const U128 &a, const U128 &b) { return U128{a.lo & b.lo, a.hi & b.hi}; }
+__device__ __forceinline__ U128 operator|(const U128 &a, const U128 &b) { return U128{a.lo | b.lo, a.hi | b.hi}; }
+__device__ __forceinline__ U128 operator~(const U128 &a) { return U128{~a.lo, ~a.hi}; }
+
+// Site-word type SW and bond-mask type MT of the light path for each record
+// type: 2N <= 32 (packed records), N <= 31, N <= 64.
+template <typename T> struct LightTypes { using SW = uint32_t; using MT = uint64_t; };
+template <> struct LightTypes<uint64_t> { using SW = uint32_t; using MT = uint32_t; };
+template <> struct LightTypes<RecW> { using SW = uint64_t; using MT = U128; };
+
 // Parameters of the light configurations of one warp's chunk, one array per
 // field (lanes that read different configurations hit different banks).
+template <typename MT, typename SW>
 struct LightSoA {
-    uint64_t Ai[32], Aj[32], X1[32], X2[32];   // anti-aligned bond masks (ket, bra), importance-class masks
+    MT Ai[32], Aj[32], X1[32], X2[32];         // anti-aligned bond masks (ket, bra), importance-class masks
     uint64_t Tket[32], Tbra[32], T[32];        // rate totals: ket moves, bra moves, all moves
     uint64_t gk[32], gb[32];                   // bonds per group (8 bytes), ket and bra
-    uint32_t i[32], j[32], natt[32];
+    SW i[32], j[32];
+    uint32_t natt[32];
     int32_t re[32], im[32], nre[32];
     int32_t cd[32], adz[32], sgn_d[32], init[32];
 };
@@ -80,7 +97,7 @@ constexpr int MAXK_PACK = 2 * 2 * NPACK + NPACK + 1;
 // configurations start, so the two share storage.
 template <typename T>
 union WarpScratch {
-    LightSoA le;
+    LightSoA<typename LightTypes<T>::MT, typename LightTypes<T>::SW> le;
     HeavyTables<std::is_same<T, RecW>::value ? MAXK : MAXK_PACK> hv;
 };
 
@@ -92,6 +109,7 @@ struct SpawnTables {
     uint64_t urate8[8];
     uint32_t urate32[8];
     float uinv[8];
+    float jinv;                       // 1 / jump rate (0 without jumps)
     int32_t sgn_h[2];
     uint32_t cross_int[2 * MAXB + 1];
     uint32_t d_int[2 * MAXN + 1];
@@ -120,9 +138,9 @@ struct SpawnCtx {
     const SpawnTables *sh;
     int N, B, K, gk;
     uint64_t jump_q;
-    uint32_t ER, ED, LC, LR;
+    uint64_t ER, ED, LC, LR;
     int Lx, shD;
-    uint64_t Emorton;
+    uint64_t Emorton, Emorton_hi;
 };
 
 __device__ __forceinline__ int imp_class(int gk, uint64_t d, uint64_t m, int a, int b) {
@@ -132,19 +150,11 @@ __device__ __forceinline__ int imp_class(int gk, uint64_t d, uint64_t m, int a, 
 }
 
 // ---- mask formulation -------------------------------------------------------
-// Bond masks are 32-bit words when N <= 16 (2N bond bits) and 64-bit words
-// otherwise; MT is the mask type.
+// Bond masks are 32-bit words when N <= 16 (2N bond bits), 64-bit words when
+// N <= 31 and 128-bit pairs up to N = 64; MT is the mask type, SW the type of
+// a spin word (32 bits up to 31 sites, else 64).
 
-template <typename MT> __device__ __forceinline__ MT spread_bits(uint32_t x32);
-template <> __device__ __forceinline__ uint32_t spread_bits<uint32_t>(uint32_t x) {
-    x &= 0xFFFFu;
-    x = (x | (x << 8)) & 0x00FF00FFu;
-    x = (x | (x << 4)) & 0x0F0F0F0Fu;
-    x = (x | (x << 2)) & 0x33333333u;
-    x = (x | (x << 1)) & 0x55555555u;
-    return x;
-}
-template <> __device__ __forceinline__ uint64_t spread_bits<uint64_t>(uint32_t x32) {
+__device__ __forceinline__ uint64_t spread32(uint32_t x32) {
     uint64_t x = x32;
     x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
     x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
@@ -154,49 +164,90 @@ template <> __device__ __forceinline__ uint64_t spread_bits<uint64_t>(uint32_t x
     return x;
 }
 
+template <typename MT, typename SW> __device__ __forceinline__ MT spread_bits(SW x);
+template <> __device__ __forceinline__ uint32_t spread_bits<uint32_t, uint32_t>(uint32_t x) {
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+template <> __device__ __forceinline__ uint64_t spread_bits<uint64_t, uint32_t>(uint32_t x) { return spread32(x); }
+template <> __device__ __forceinline__ U128 spread_bits<U128, uint64_t>(uint64_t x) {
+    return U128{spread32((uint32_t)x), spread32((uint32_t)(x >> 32))};
+}
+
 __device__ __forceinline__ int popcount(uint32_t x) { return __popc(x); }
 __device__ __forceinline__ int popcount(uint64_t x) { return __popcll(x); }
+__device__ __forceinline__ int popcount(const U128 &x) { return __popcll(x.lo) + __popcll(x.hi); }
+
+__device__ __forceinline__ uint32_t shl1(uint32_t x) { return x << 1; }
+__device__ __forceinline__ uint64_t shl1(uint64_t x) { return x << 1; }
+__device__ __forceinline__ U128 shl1(const U128 &x) { return U128{x.lo << 1, x.hi << 1}; }   // even bits to odd
+
+__device__ __forceinline__ uint32_t mask_bit(uint32_t x, int p) { return (x >> p) & 1u; }
+__device__ __forceinline__ uint32_t mask_bit(uint64_t x, int p) { return (uint32_t)(x >> p) & 1u; }
+__device__ __forceinline__ uint32_t mask_bit(const U128 &x, int p) {
+    return (uint32_t)((p < 64 ? (x.lo >> p) : (x.hi >> (p - 64))) & 1ull);
+}
+
+template <typename MT> __device__ __forceinline__ MT zero_mask() { return (MT)0; }
+template <> __device__ __forceinline__ U128 zero_mask<U128>() { return U128{0ull, 0ull}; }
+template <typename MT> __device__ __forceinline__ MT one_bit(int p) { return (MT)1 << p; }
+template <> __device__ __forceinline__ U128 one_bit<U128>(int p) {
+    return p < 64 ? U128{1ull << p, 0ull} : U128{0ull, 1ull << (p - 64)};
+}
+template <typename MT> __device__ __forceinline__ MT bond_exists(const SpawnCtx &c) { return (MT)c.Emorton; }
+template <> __device__ __forceinline__ U128 bond_exists<U128>(const SpawnCtx &c) { return U128{c.Emorton, c.Emorton_hi}; }
+
+__device__ __forceinline__ int low_bit(uint32_t x) { return __ffs(x) - 1; }
+__device__ __forceinline__ int low_bit(uint64_t x) { return __ffsll((long long)x) - 1; }
+__device__ __forceinline__ int high_bit(uint32_t x) { return 31 - __clz(x); }
+__device__ __forceinline__ int high_bit(uint64_t x) { return 63 - __clzll((long long)x); }
 
 // bond mask from per-direction site masks: bit 2k <- right bond of k, bit 2k+1 <- lower bond of k
-template <typename MT>
-__device__ __forceinline__ MT bond_mask(uint32_t right, uint32_t down) {
-    return spread_bits<MT>(right) | (spread_bits<MT>(down) << 1);
+template <typename MT, typename SW>
+__device__ __forceinline__ MT bond_mask(SW right, SW down) {
+    return spread_bits<MT, SW>(right) | shl1(spread_bits<MT, SW>(down));
 }
 
 // word whose bit k is the spin of the right (resp. lower) neighbour of site k
-__device__ __forceinline__ uint32_t nb_right(const SpawnCtx &c, uint32_t s) {
-    return ((s >> 1) & ~c.LC) | ((s << (c.Lx - 1)) & c.LC);
+template <typename SW>
+__device__ __forceinline__ SW nb_right(const SpawnCtx &c, SW s) {
+    return ((s >> 1) & ~(SW)c.LC) | ((s << (c.Lx - 1)) & (SW)c.LC);
 }
-__device__ __forceinline__ uint32_t nb_down(const SpawnCtx &c, uint32_t s) {
-    return (s >> c.Lx) | ((s << c.shD) & c.LR);
+template <typename SW>
+__device__ __forceinline__ SW nb_down(const SpawnCtx &c, SW s) {
+    return (s >> c.Lx) | ((s << c.shD) & (SW)c.LR);
 }
 
-template <typename MT>
-__device__ __forceinline__ MT anti_mask(const SpawnCtx &c, uint32_t s) {
-    return bond_mask<MT>((s ^ nb_right(c, s)) & c.ER, (s ^ nb_down(c, s)) & c.ED);
+template <typename MT, typename SW>
+__device__ __forceinline__ MT anti_mask(const SpawnCtx &c, SW s) {
+    return bond_mask<MT, SW>((s ^ nb_right(c, s)) & (SW)c.ER, (s ^ nb_down(c, s)) & (SW)c.ED);
 }
 
 // importance-class masks of configuration (i, j): for the site-product guide
 // X1 / X2 = bonds whose first / second site differs between i and j; for the
 // uniform guide X1 = every bond when i == j, X2 = the bond whose flip makes
 // the child diagonal
-template <typename MT>
-__device__ __forceinline__ void class_masks(const SpawnCtx &c, uint32_t i, uint32_t j, MT &X1, MT &X2) {
-    const uint32_t d = i ^ j;
-    X1 = 0;
-    X2 = 0;
+template <typename MT, typename SW>
+__device__ __forceinline__ void class_masks(const SpawnCtx &c, SW i, SW j, MT &X1, MT &X2) {
+    const SW d = i ^ j;
+    X1 = zero_mask<MT>();
+    X2 = zero_mask<MT>();
     if (c.gk == 1) {
-        if (d == 0) { X1 = (MT)c.Emorton; return; }
-        if (__popc(d) != 2) return;
-        const int a = __ffs(d) - 1, b = 31 - __clz(d);
+        if (d == 0) { X1 = bond_exists<MT>(c); return; }
+        if (popcount(d) != 2) return;
+        const int a = low_bit(d), b = high_bit(d);
         const SpawnTables &s = *c.sh;
-        if ((c.ER >> a & 1u) && s.rn[a] == b) X2 = (MT)1 << (2 * a);
-        else if ((c.ED >> a & 1u) && s.dn[a] == b) X2 = (MT)1 << (2 * a + 1);
-        else if ((c.ER >> b & 1u) && s.rn[b] == a) X2 = (MT)1 << (2 * b);
-        else if ((c.ED >> b & 1u) && s.dn[b] == a) X2 = (MT)1 << (2 * b + 1);
+        if ((c.ER >> a & 1ull) && s.rn[a] == b) X2 = one_bit<MT>(2 * a);
+        else if ((c.ED >> a & 1ull) && s.dn[a] == b) X2 = one_bit<MT>(2 * a + 1);
+        else if ((c.ER >> b & 1ull) && s.rn[b] == a) X2 = one_bit<MT>(2 * b);
+        else if ((c.ED >> b & 1ull) && s.dn[b] == a) X2 = one_bit<MT>(2 * b + 1);
     } else if (c.gk == 2) {
-        X1 = bond_mask<MT>(d & c.ER, d & c.ED);
-        X2 = bond_mask<MT>(nb_right(c, d) & c.ER, nb_down(c, d) & c.ED);
+        X1 = bond_mask<MT, SW>(d & (SW)c.ER, d & (SW)c.ED);
+        X2 = bond_mask<MT, SW>(nb_right(c, d) & (SW)c.ER, nb_down(c, d) & (SW)c.ED);
     }
 }
 
@@ -206,9 +257,9 @@ __device__ __forceinline__ MT group_mask(const SpawnCtx &c, MT A, MT X1, MT X2, 
     const int cls = g & 3;
     MT cm;
     if (c.gk == 2) cm = ((cls & 2) ? X1 : (MT)~X1) & ((cls & 1) ? X2 : (MT)~X2);
-    else if (c.gk == 1) cm = cls == 0 ? (MT)~(X1 | X2) : (cls == 1 ? X1 : (cls == 2 ? X2 : (MT)0));
-    else cm = cls == 0 ? (MT)~(MT)0 : (MT)0;
-    return ((g & 4) ? A : (MT)~A) & cm & (MT)c.Emorton;
+    else if (c.gk == 1) cm = cls == 0 ? (MT)~(X1 | X2) : (cls == 1 ? X1 : (cls == 2 ? X2 : zero_mask<MT>()));
+    else cm = cls == 0 ? (MT)~zero_mask<MT>() : zero_mask<MT>();
+    return ((g & 4) ? A : (MT)~A) & cm & bond_exists<MT>(c);
 }
 
 // position of the r-th set bit (r from 0) of m, given r < popcount(m)
@@ -225,6 +276,10 @@ __device__ __forceinline__ int select_bit(uint64_t m, uint32_t r) {
     const uint32_t lo = (uint32_t)m;
     const uint32_t c = (uint32_t)__popc(lo);
     return r < c ? select_bit(lo, r) : 32 + select_bit((uint32_t)(m >> 32), r - c);
+}
+__device__ __forceinline__ int select_bit(const U128 &m, uint32_t r) {
+    const uint32_t c = (uint32_t)__popcll(m.lo);
+    return r < c ? select_bit(m.lo, r) : 64 + select_bit(m.hi, r - c);
 }
 
 // floor(v / q) for a quotient below 64, by integer bisection (no division:
@@ -330,7 +385,11 @@ __device__ __forceinline__ RecW make_spawn<RecW>(uint64_t ci, uint64_t cj, int, 
 
 template <typename T>
 __device__ __forceinline__ void count_digits(SpawnShared<T> &s, const T &r, int npass) {
-    for (int p = 0; p < npass; ++p) atomicAdd(&s.hist[p][RecTraits<T>::digit(r, s.pass_shift[p])], 1u);
+    // one-word keys: pass p reads bits 8p..8p+7; two-word keys: per-pass shifts
+    for (int p = 0; p < npass; ++p) {
+        const int shift = std::is_same<T, RecW>::value ? s.pass_shift[p] : 8 * p;
+        atomicAdd(&s.hist[p][RecTraits<T>::digit(r, shift)], 1u);
+    }
 }
 
 // Append one record from a (possibly divergent) lane.
@@ -426,7 +485,7 @@ __device__ __forceinline__ uint32_t attempt_word(uint4 x0, uint4 &xb, uint32_t &
 // Resolve the first n queued spawn draws of the warp, one per lane: the move
 // (ket, bra or jump segment, then the group and the bond inside it), the child
 // configuration and its signed unit, appended as a spawn record.
-template <typename T, typename MT>
+template <typename T, typename MT, typename SW>
 __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c, int warp, int lane, int n, int N,
                                             T *out, int64_t cap, DevState *st, int npass) {
     if (lane < n) {
@@ -435,31 +494,41 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
         const int o = (int)(meta & 31u);
         const int part = (int)((meta >> 5) & 1u);
         const int sig = (meta & 64u) ? -1 : 1;
-        const LightSoA &q = s.ws[warp].le;
-        const uint32_t qi = q.i[o], qj = q.j[o];
+        const auto &q = s.ws[warp].le;
+        const SW qi = q.i[o], qj = q.j[o];
         const uint64_t qT = q.T[o], qTket = q.Tket[o], qTbra = q.Tbra[o];
-        uint32_t ci = qi, cj = qj;
+        SW ci = qi, cj = qj;
         int cre = 0, cim = 0;
         if (v < qTket + qTbra) {
             const bool ket = v < qTket;
-            const MT A = (MT)(ket ? q.Ai[o] : q.Aj[o]);
-            const MT X1 = (MT)q.X1[o], X2 = (MT)q.X2[o];
+            const MT A = ket ? q.Ai[o] : q.Aj[o];
+            const MT X1 = q.X1[o], X2 = q.X2[o];
             const uint64_t cnt8 = ket ? q.gk[o] : q.gb[o];
             const uint64_t vs = ket ? v : v - qTket;
             const int p = qT <= 0xFFFFFFFFull ? seg_select32<MT>(c, s.urate32, s.uinv, cnt8, A, X1, X2, (uint32_t)vs)
                                               : seg_select<MT>(c, s.urate8, cnt8, A, X1, X2, vs);
             const int k = p >> 1;
             const int other = (p & 1) ? s.dn[k] : s.rn[k];
-            const uint32_t m = (1u << k) | (1u << other);
-            const int hs = s.sgn_h[(A >> p) & 1u];
+            const SW m = ((SW)1 << k) | ((SW)1 << other);
+            const int hs = s.sgn_h[mask_bit(A, p)];
             const int gsg = ket ? -hs : hs;
             if (ket) ci ^= m; else cj ^= m;
             if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
         } else {
-            const uint32_t idx = small_quotient(v - qTket - qTbra, c.jump_q);
-            const int k = select_bit((uint64_t)(qi & qj), idx);
-            ci &= ~(1u << k);
-            cj &= ~(1u << k);
+            // jumps share one rate: the site index is the quotient by it
+            const uint64_t vj = v - qTket - qTbra;
+            uint32_t idx;
+            if (qT <= 0xFFFFFFFFull) {
+                idx = (uint32_t)((float)(uint32_t)vj * s.jinv);
+                const uint64_t pq = (uint64_t)idx * c.jump_q;
+                if (pq > vj) --idx;
+                else if (pq + c.jump_q <= vj) ++idx;
+            } else {
+                idx = small_quotient(vj, c.jump_q);
+            }
+            const int k = select_bit((SW)(qi & qj), idx);
+            ci &= ~((SW)1 << k);
+            cj &= ~((SW)1 << k);
             if (part == 0) cre = sig; else cim = sig;
         }
         emit(s, warp, make_spawn<T>((uint64_t)ci, (uint64_t)cj, N, q.init[o] != 0, cre, cim), out, cap, st, npass);
@@ -471,9 +540,10 @@ template <typename T>
 __global__ void __launch_bounds__(SP_TPB, 3)
 k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typename ListOf<T>::type *__restrict__ L,
               T *__restrict__ out, int64_t cap) {
-    // packed records <=> N <= 16 <=> 32-bit bond masks; two-word records: every
-    // configuration on the warp-cooperative path
-    using MT = typename std::conditional<sizeof(T) == 8, uint32_t, uint64_t>::type;
+    // mask and spin-word types of the light path: 32-bit masks for packed
+    // records (2N <= 32), 64-bit up to 31 sites, 128-bit (two words) beyond
+    using MT = typename LightTypes<T>::MT;
+    using SW = typename LightTypes<T>::SW;
     using LT = typename ListOf<T>::type;
     constexpr bool WIDE = std::is_same<T, RecW>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -496,6 +566,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
         s.uinv[tid] = P.urate8[tid] ? 1.0f / (float)P.urate8[tid] : 0.0f;
     }
     if (tid < 2) s.sgn_h[tid] = P.sgn_h[tid];
+    if (tid == 0) s.jinv = P.jump_q ? 1.0f / (float)P.jump_q : 0.0f;
     for (int q = tid; q <= 2 * B; q += SP_TPB) { s.cross_int[q] = P.cross_int[q]; s.cross_frac[q] = P.cross_frac[q]; }
     for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_frac[q] = st->d_frac[q]; s.d_sgn[q] = st->d_sgn[q]; }
     for (int q = tid; q < SpawnShared<T>::NP * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
@@ -504,7 +575,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
 
     SpawnCtx c;
     c.sh = &s; c.N = N; c.B = B; c.K = K; c.gk = P.guide_kind; c.jump_q = P.jump_q;
-    c.ER = P.ER; c.ED = P.ED; c.LC = P.LC; c.LR = P.LR; c.Lx = P.Lx; c.shD = P.shD; c.Emorton = P.Emorton;
+    c.ER = P.ER; c.ED = P.ED; c.LC = P.LC; c.LR = P.LR; c.Lx = P.Lx; c.shD = P.shD;
+    c.Emorton = P.Emorton; c.Emorton_hi = P.Emorton_hi;
     const bool uniform = P.uniform != 0;
     const int64_t M = st->M;
     const uint64_t t = (uint64_t)st->t;
@@ -529,19 +601,18 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
         const int64_t nre = iabs64(rec.re), nim = iabs64(rec.im);
         const int64_t nw = nre + nim;
         const bool valid = e < M;
-        const bool heavy = valid && (WIDE || nw > SP_HEAVY || !uniform);
+        const bool heavy = valid && (nw > SP_HEAVY || !uniform);
         const bool light = valid && !heavy;
         const bool init = (n_a == 0) || (i == j) || (nw > (int64_t)n_a);
 
-        if constexpr (!WIDE) {
         // ---- light configurations: per-configuration setup, one lane each ----
         int nl = 0;
         if (light) {
-            LightSoA &q = s.ws[warp].le;
-            const uint32_t i32 = (uint32_t)i, j32 = (uint32_t)j;
-            const MT Ai = anti_mask<MT>(c, i32), Aj = anti_mask<MT>(c, j32);
+            auto &q = s.ws[warp].le;
+            const SW i32 = (SW)i, j32 = (SW)j;
+            const MT Ai = anti_mask<MT, SW>(c, i32), Aj = anti_mask<MT, SW>(c, j32);
             MT X1, X2;
-            class_masks<MT>(c, i32, j32, X1, X2);
+            class_masks<MT, SW>(c, i32, j32, X1, X2);
             uint64_t Tket = 0, Tbra = 0, gkp = 0, gbp = 0;
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
@@ -552,7 +623,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 Tket += s.urate8[g] * (uint64_t)ck;
                 Tbra += s.urate8[g] * (uint64_t)cb;
             }
-            const uint64_t Tall = Tket + Tbra + (uint64_t)__popc(i32 & j32) * c.jump_q;
+            const uint64_t Tall = Tket + Tbra + (uint64_t)popcount((SW)(i32 & j32)) * c.jump_q;
             const uint64_t natt = (Tall + 0xFFFFFFFFull) >> 32;
             q.Ai[lane] = Ai;
             q.Aj[lane] = Aj;
@@ -569,7 +640,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             q.re[lane] = rec.re;
             q.im[lane] = rec.im;
             q.nre[lane] = (int32_t)nre;
-            q.cd[lane] = __popc(i32) + __popc(j32);
+            q.cd[lane] = popcount(i32) + popcount(j32);
             const int dz = 2 * (popcount(Aj) - popcount(Ai));     // zsum(i) - zsum(j)
             q.adz[lane] = dz < 0 ? -dz : dz;
             q.sgn_d[lane] = (dz == 0) ? 0 : -sgn_jz * (dz > 0 ? 1 : -1);
@@ -619,13 +690,16 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             uint64_t qT = 0;
             uint4 x = make_uint4(0u, 0u, 0u, 0u), ctr = x;
             if (act) {
-                const LightSoA &q = s.ws[warp].le;
+                const auto &q = s.ws[warp].le;
                 const int nre_o = q.nre[owner];
                 const int local = g - owner_excl;
                 part = local < nre_o ? 0 : 1;
                 const uint32_t w = (uint32_t)(part ? local - nre_o : local);
                 sig = (part ? q.im[owner] : q.re[owner]) < 0 ? -1 : 1;
-                ctr = make_uint4(q.i[owner], q.j[owner], w, (uint32_t)part << 16);
+                // counter words: the spin words, high halves folded in (zero up to 32 sites)
+                const uint64_t oi = (uint64_t)q.i[owner], oj = (uint64_t)q.j[owner];
+                ctr = make_uint4((uint32_t)oi ^ ((uint32_t)(oi >> 32) * 0x9E3779B9u),
+                                 (uint32_t)oj ^ ((uint32_t)(oj >> 32) * 0x85EBCA6Bu), w, (uint32_t)part << 16);
                 x = philox4x32_10(ctr, k0, k1);
                 const int cd = q.cd[owner], adz = q.adz[owner];
                 const int cnt = (int)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
@@ -668,7 +742,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 while (qn >= 32 || (fin && qn > 0)) {
                     __syncwarp();
                     const int nd = qn < 32 ? qn : 32;
-                    spawn_drain<T, MT>(s, c, warp, lane, nd, N, out, cap, st, npass);
+                    spawn_drain<T, MT, SW>(s, c, warp, lane, nd, N, out, cap, st, npass);
                     qn -= nd;
                     // move the rest of the queue to the front
                     uint64_t rv = 0;
@@ -685,7 +759,6 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             if (iabs64(re2) > 2147483647ll || iabs64(im2) > 2147483647ll) local_status |= ST_OVERFLOW;
             *reinterpret_cast<int2 *>(&L[e].re) = make_int2((int32_t)re2, (int32_t)im2);
         }
-        }    // light configurations
         flush(s, warp, lane, out, cap, st, npass, SP_FLUSH);
 
         // ---- heavy configurations: the whole warp on one configuration -------
