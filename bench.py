@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-target", type=float, default=2e4, help="shift target of the oracle sample")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve", type=int, default=0,
+                    help="instead: this many synthetic NESS-solve requests through the batching server, "
+                         "then the same requests one at a time")
     return ap.parse_args()
 
 
@@ -388,8 +391,68 @@ def gpu_arm(args, world, rank, local, pg):
     return 0
 
 
+def serve_requests(n, seed=5):
+    """Synthetic solve requests: Poisson arrivals (20/s), lattice 2x2 open, 3x3
+    or 4x4 periodic, Jx ~ U[0.8, 1.1], gamma ~ U[0.5, 2], target log-uniform in
+    [1e4, 2e5] walkers, n_a = 3, samples from 256 steps after the shift switches
+    on, goal: blocked error of M_z below 0.004 within 4096 steps."""
+    import numpy as np
+    from paper_1802_05931_gb300 import serve as S
+    rng = np.random.default_rng(seed)
+    lat = [(2, 2, 0), (3, 3, 1), (4, 4, 1)]
+    out, t = [], 0.0
+    for k in range(n):
+        t += rng.exponential(1.0 / 20.0)
+        Lx, Ly, per = lat[rng.integers(0, 3)]
+        req = S.SolveRequest(Lx, Ly, per, float(rng.uniform(0.8, 1.1)), 1.0, 1.0, float(rng.uniform(0.5, 2.0)),
+                             0.005, int(10 ** rng.uniform(4, math.log10(2e5))), n_a=3, seed=100 + k, control=1,
+                             t_eq=256, tol=0.004, min_samples=512, max_steps=4096)
+        out.append((t, req))
+    return out
+
+
+def serve_arm(args):
+    """Solves/h and latency percentiles of the batching server against the same
+    requests served one at a time (one run on the whole GPU)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1802_05931_gb300 import serve as S
+    torch.cuda.set_device(0)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    reqs = serve_requests(args.serve)
+    out = {}
+    for name, slots in (("batched", 16), ("sequential", 1)):
+        srv = S.NessServer(budget, max_active=slots, chunk=64)
+        t0 = time.perf_counter()
+        for ta, r in reqs:
+            srv.submit(r, t_arrive=t0 + ta)
+        srv.run_until_idle()
+        span = time.perf_counter() - t0
+        lat = [r.latency for r in srv.results.values()]
+        out[name] = {"solves_per_h": len(reqs) / span * 3600.0, "makespan_s": span,
+                     "p50_s": S.percentile(lat, 0.5), "p95_s": S.percentile(lat, 0.95),
+                     "p99_s": S.percentile(lat, 0.99),
+                     "converged": sum(1 for r in srv.results.values() if r.converged),
+                     "errors": sum(1 for r in srv.results.values() if r.error),
+                     "steps": sum(r.steps for r in srv.results.values()), "peak_active": srv.peak_active}
+    b = out["batched"]
+    line = {"metric": "NESS solves/h", "value": b["solves_per_h"], "unit": "solves/h", "n_gpus": 1,
+            "higher_is_better": True, "p50_s": b["p50_s"], "p95_s": b["p95_s"], "p99_s": b["p99_s"],
+            "data": "synthetic", "config": {"workload": "%d requests, Poisson 20/s, 2x2 open / 3x3 / 4x4 periodic, "
+                                                        "Jx U[0.8,1.1], gamma U[0.5,2], target log-U[1e4,2e5], "
+                                                        "n_a 3, M_z error goal 0.004, at most 4096 steps" % len(reqs),
+                                            "slots": 16, "chunk_steps": 64},
+            "batched": b, "sequential": out["sequential"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.serve:
+        return serve_arm(args)
     world, rank, local, pg = dist_setup(args.gpus)
     try:
         if args.impl == "reference":

@@ -75,6 +75,9 @@ typedef struct {
     int64_t capacity_spawns;   /* spawn-record capacity per step; <= 0: 4*target (control 1)
                                   or 64*target (control 0), plus 65536 */
     void *cuda_stream;         /* cudaStream_t to issue work on; NULL: the run creates its own */
+    int32_t sm_limit;          /* > 0: size every kernel grid for at most this many SMs, so that
+                                  several runs stepped on their own streams share the GPU;
+                                  <= 0 (default): the whole GPU */
 } ddqmc_options;
 
 typedef struct ddqmc_run ddqmc_run;

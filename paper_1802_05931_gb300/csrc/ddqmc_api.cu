@@ -516,6 +516,7 @@ int ddqmc_default_options(ddqmc_options *o) {
     o->capacity_entries = 0;
     o->capacity_spawns = 0;
     o->cuda_stream = nullptr;
+    o->sm_limit = 0;
     return DDQMC_OK;
 }
 
@@ -580,6 +581,7 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device);
     if (sms < 1) sms = 1;
+    if (o.sm_limit > 0 && o.sm_limit < sms) sms = o.sm_limit;
     r->packed = 2 * r->hp.N <= 32;
     bool ok = cudaFuncSetAttribute(k_spawn_death<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_spawn_death<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPP_SMEM) == cudaSuccess;

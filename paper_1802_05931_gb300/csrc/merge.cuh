@@ -27,7 +27,7 @@ namespace ddq {
 
 constexpr int MG_TPB = 256;
 constexpr int MG_WARPS = MG_TPB / 32;
-constexpr int MG_IPT = 7;                  // odd: the lanes' merge cursors spread over the banks
+constexpr int MG_IPT = 9;                  // odd: the lanes' merge cursors spread over the banks
 constexpr int MG_TILE = 32 * MG_IPT;       // merged positions per warp tile
 constexpr int MG_PCHUNK = 8;               // tile boundaries per partition thread
 

@@ -40,7 +40,7 @@ class ddqmc_options(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("damping", C.c_double), ("shift0", C.c_double),
                 ("n0", C.c_int64), ("control", C.c_int32), ("t_eq", C.c_int64),
                 ("capacity_entries", C.c_int64), ("capacity_spawns", C.c_int64),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("sm_limit", C.c_int32)]
 
 
 class ddqmc_estimates(C.Structure):
@@ -269,7 +269,7 @@ class Run:
 
     def __init__(self, Lx, Ly, periodic, Jx, Jy, Jz, gamma, dt, target, n_a=0, guide_kind=0,
                  guide_p=0.0, site_ratio=None, seed=1, damping=0.05, shift0=-1.0, n0=1000, control=0,
-                 t_eq=-1, capacity_entries=0, capacity_spawns=0, stream=None):
+                 t_eq=-1, capacity_entries=0, capacity_spawns=0, stream=None, sm_limit=0):
         o = ddqmc_default_options()
         o.seed = int(seed) & ((1 << 64) - 1)
         o.damping = damping
@@ -280,6 +280,7 @@ class Run:
         o.capacity_entries = int(capacity_entries)
         o.capacity_spawns = int(capacity_spawns)
         o.cuda_stream = stream
+        o.sm_limit = int(sm_limit)
         g = ddqmc_guide()
         g.kind = int(guide_kind)
         g.p = float(guide_p)

@@ -1,0 +1,111 @@
+"""Scheduling logic of the NESS-solve server, on the host with stand-in runs:
+admission by slots and by the device-memory budget, first come first served,
+no admission before arrival, retirement on the error goal or the step limit."""
+import math
+import types
+
+import pytest
+
+from paper_1802_05931_gb300 import serve as S
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+class FakeRun:
+    """Blocked error 1/sqrt(samples) with samples = steps - 100."""
+    live = 0
+
+    def __init__(self, req, sm_limit):
+        self.req, self.t, self.closed = req, 0, False
+        FakeRun.live += 1
+
+    def step_async(self, n):
+        self.t += n
+
+    def sync(self):
+        pass
+
+    def estimates(self):
+        ns = max(0, self.t - 100)
+        return types.SimpleNamespace(mz=-0.5, mz_err=(1.0 / math.sqrt(ns)) if ns else float("nan"), n_samples=ns)
+
+    def export(self):
+        return ([self.t], [0], [1], [0])
+
+    def close(self):
+        self.closed = True
+        FakeRun.live -= 1
+
+
+def _req(target=1000, tol=0.05, max_steps=10000):
+    return S.SolveRequest(2, 2, 0, 0.9, 1.0, 1.0, 1.0, 0.01, target, tol=tol, min_samples=64, max_steps=max_steps)
+
+
+def _server(budget, slots, clock, chunk=32):
+    return S.NessServer(budget, max_active=slots, chunk=chunk, make_run=FakeRun, clock=clock, keep_lists=True)
+
+
+def test_retire_on_error_goal_in_whole_chunks():
+    clock = FakeClock()
+    srv = _server(10 ** 12, 4, clock)
+    rid = srv.submit(_req(tol=0.05))          # needs 400 samples: 500 steps, rounded up to chunks
+    srv.run_until_idle()
+    r = srv.results[rid]
+    assert r.converged and r.steps % 32 == 0 and r.n_samples >= 400 and r.steps - 32 < 500 <= r.steps
+    assert r.lists[0] == [r.steps] and FakeRun.live == 0 and srv.bytes_in_use == 0
+
+
+def test_step_limit_retires_unconverged():
+    clock = FakeClock()
+    srv = _server(10 ** 12, 4, clock)
+    rid = srv.submit(_req(tol=1e-9, max_steps=300))
+    srv.run_until_idle()
+    r = srv.results[rid]
+    assert not r.converged and r.steps == 300
+
+
+def test_admission_by_slots_and_budget_first_come_first_served():
+    clock = FakeClock()
+    one = _req().device_bytes()
+    srv = _server(2 * one + 1, 3, clock)       # memory for two runs, three slots
+    ids = [srv.submit(_req(tol=0.05)) for _ in range(5)]
+    starts = []
+    while not srv.idle:
+        srv.cycle()
+        assert len(srv._active) <= 2 and srv.bytes_in_use <= 2 * one + 1
+        starts += [s["id"] for s in srv._active if s["id"] not in starts]
+        clock.t += 1.0
+    assert starts == ids and srv.peak_active == 2
+    assert all(srv.results[i].converged for i in ids)
+
+
+def test_no_admission_before_arrival():
+    clock = FakeClock()
+    srv = _server(10 ** 12, 4, clock)
+    a = srv.submit(_req(tol=0.05), t_arrive=0.0)
+    b = srv.submit(_req(tol=0.05), t_arrive=5.0)
+    srv.cycle()
+    assert [s["id"] for s in srv._active] == [a]
+    clock.t = 5.0
+    srv.cycle()
+    assert sorted(s["id"] for s in srv._active) == [a, b]      # b joins while a runs
+    while not srv.idle:
+        srv.cycle()
+    assert srv.results[b].t_start == 5.0 and srv.results[a].t_start == 0.0
+
+
+def test_request_larger_than_budget_is_refused():
+    srv = _server(1000, 2, FakeClock())
+    with pytest.raises(ValueError):
+        srv.submit(_req())
+
+
+def test_percentile():
+    assert S.percentile([3, 1, 2], 0.5) == 2
+    assert S.percentile([1, 2, 3, 4], 0.99) == pytest.approx(3.97)
