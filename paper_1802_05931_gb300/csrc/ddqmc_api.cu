@@ -56,6 +56,9 @@ struct ddqmc_run {
     // counters of standalone annihilation calls (allocated on first use)
     DevState *dAnn = nullptr;
     uint32_t ann_calls = 0;
+    // CUDA graphs of GRAPH_STEPS steps, one per starting list buffer, captured on first use
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool no_graph = false;       // capture failed once: plain launches from then on
 };
 
 namespace {
@@ -250,6 +253,8 @@ int occupancy_grid(const void *fn, int tpb, size_t smem, int sms) {
 void free_run(ddqmc_run *r) {
     if (!r) return;
     for (cudaEvent_t e : r->ev) cudaEventDestroy(e);
+    for (cudaGraphExec_t g : r->graph)
+        if (g) cudaGraphExecDestroy(g);
     if (r->hstage) cudaFreeHost(r->hstage);
     cudaFree(r->dP);
     cudaFree(r->dS);
@@ -335,7 +340,55 @@ void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(in
 // kernel classes of the per-kernel timing
 enum { KC_SPAWN = 0, KC_RADIX = 1, KC_PARTITION = 2, KC_MERGE = 3, KC_FINALIZE = 4, NKCLASS = 5 };
 
+// Steps replayed from one captured graph: even, so that the list buffers end
+// where they started and one graph per starting buffer suffices.
+constexpr int64_t GRAPH_STEPS = 32;
+
+void launch_one_step(ddqmc_run *r, const std::function<void(int, int)> &mark) {
+    void *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
+    if (r->packed) launch_step<uint64_t>(r, Lc, Ln, mark);
+    else if (r->wide) launch_step<RecW>(r, Lc, Ln, mark);
+    else launch_step<Rec>(r, Lc, Ln, mark);
+    mark(KC_FINALIZE, 0);
+    k_finalize<<<1, FN_TPB, 0, r->stream>>>(r->dP, r->dS, r->dBlk);
+    mark(KC_FINALIZE, 1);
+    r->cur ^= 1;
+}
+
+// Capture GRAPH_STEPS steps starting from the current buffer (launch overhead
+// dominates small runs; the graph replays the same launches).  false if
+// capture is not possible on this stream.
+bool capture_graph(ddqmc_run *r) {
+    const int start = r->cur;
+    std::function<void(int, int)> none = [](int, int) {};
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(r->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    for (int64_t s = 0; s < GRAPH_STEPS; ++s) launch_one_step(r, none);
+    const bool ok = cudaStreamEndCapture(r->stream, &g) == cudaSuccess && g &&
+                    cudaGraphInstantiate(&r->graph[start], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    r->cur = start;
+    if (!ok) {
+        cudaGetLastError();
+        r->graph[start] = nullptr;
+    }
+    return ok;
+}
+
 int enqueue_steps(ddqmc_run *r, int64_t nsteps) {
+    // whole graphs first (not while per-kernel events are recorded)
+    while (!r->timing && !r->no_graph && nsteps >= GRAPH_STEPS) {
+        if (!r->graph[r->cur] && !capture_graph(r)) { r->no_graph = true; break; }
+        if (cudaGraphLaunch(r->graph[r->cur], r->stream) != cudaSuccess) {
+            cudaGetLastError();
+            r->host_status = DDQMC_ERR_CUDA;
+            return r->host_status;
+        }
+        nsteps -= GRAPH_STEPS;
+    }
     for (int64_t s = 0; s < nsteps; ++s) {
         cudaEvent_t *ev = nullptr;
         if (r->timing) {
@@ -350,14 +403,7 @@ int enqueue_steps(ddqmc_run *r, int64_t nsteps) {
         std::function<void(int, int)> mark = [&](int kc, int edge) {
             if (ev) cudaEventRecord(ev[2 * kc + edge], r->stream);
         };
-        void *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
-        if (r->packed) launch_step<uint64_t>(r, Lc, Ln, mark);
-        else if (r->wide) launch_step<RecW>(r, Lc, Ln, mark);
-        else launch_step<Rec>(r, Lc, Ln, mark);
-        mark(KC_FINALIZE, 0);
-        k_finalize<<<1, FN_TPB, 0, r->stream>>>(r->dP, r->dS, r->dBlk);
-        mark(KC_FINALIZE, 1);
-        r->cur ^= 1;
+        launch_one_step(r, mark);
     }
     if (cudaGetLastError() != cudaSuccess) {
         r->host_status = DDQMC_ERR_CUDA;

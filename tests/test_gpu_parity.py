@@ -171,6 +171,26 @@ def test_two_word_keys_larger_population(ddqmc):
     assert int(np.abs(re, dtype=np.int64).sum() + np.abs(im, dtype=np.int64).sum()) > 10 ** 5
 
 
+@pytest.mark.parametrize("cfg", ["C1", "C3"])
+def test_graph_replay_matches_single_steps(ddqmc, cfg):
+    """Multi-step calls replay captured graphs of 32 steps (from either list
+    buffer); they must equal step-by-step launches and the oracle."""
+    over = dict(target=3 * 10 ** 4) if cfg == "C3" else {}
+    args, kw = W.run_kwargs(getattr(W, cfg), **over)
+    a = ddqmc.Run(*args, **kw)
+    b = ddqmc.Run(*args, **kw)
+    cpu = O.OracleRun(*args, **kw)
+    for n in (33, 64, 63, 96, 1, 31):
+        a.step(n)
+        for _ in range(n):
+            b.step(1)
+        cpu.step(n)
+        for x, y in zip(a.export(), b.export()):
+            assert np.array_equal(x, y), n
+        _same(a, cpu, n)
+        assert a.state().t == b.state().t
+
+
 def test_single_step_from_imported_state(ddqmc):
     """Grow a 4x4 population on the GPU, then step the exported state once on
     both sides (the oracle imports the GPU's list and scalar state)."""
