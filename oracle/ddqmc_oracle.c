@@ -26,9 +26,11 @@
  *     a configuration is (ket i, bra j); canonical order is (bra, ket);
  *   - H = sum over bonds of Jx sx sx + Jy sy sy + Jz sz sz (Pauli matrices),
  *     decay gamma * D[sigma^-] on every site (Sec. V, XYZ model);
- *   - moves, in this order: ket bond flips, bra bond flips, then jumps by
- *     site; inside a bond-flip segment grouped by (anti-aligned, importance
- *     class) and in bond order inside a group;
+ *   - moves, in this order: ket bond flips, bra bond flips, ket site flips
+ *     and bra site flips of the in-plane field (only when h != 0), then jumps
+ *     by site; inside a bond-flip segment grouped by (anti-aligned,
+ *     importance class) and in bond order inside a group; inside a site-flip
+ *     segment grouped by importance class, in site order inside a group;
  *   - per-walker categorical draws, which have the joint law of the
  *     binomial + multinomial scheme of Sec. III.B; n_att = ceil(P_tot)
  *     attempts when P_tot > 1;
@@ -45,6 +47,7 @@
 
 #define OR_MAX_SITES 64
 #define OR_MAX_BONDS 128
+#define OR_MAX_MOVES (2 * OR_MAX_BONDS + 3 * OR_MAX_SITES)
 
 /* error codes returned by or_step / or_import */
 #define OR_OK 0
@@ -69,6 +72,8 @@ typedef struct {
     int bond_a[OR_MAX_BONDS], bond_b[OR_MAX_BONDS];
     uint64_t bond_m[OR_MAX_BONDS];
     double Jx, Jy, Jz, gamma, dt;
+    double h;               /* in-plane field strength (Sec. V.B), 0 = none */
+    int field_axis;         /* 0: field along x (theta = 0), 1: along y (theta = pi/2) */
     int64_t target;
     int32_t n_a;
     int control;            /* 0: N_w = sum |Re rho_ii| (paper); 1: sum |re|+|im| */
@@ -82,6 +87,7 @@ typedef struct {
     /* fixed-point rate tables */
     uint64_t rate_q[OR_MAX_BONDS][2][4];   /* [bond][aligned=0/anti=1][ratio class] */
     uint64_t jump_q;
+    uint64_t frate_q[OR_MAX_SITES][4];     /* field flip of site k, [ratio class] */
     uint32_t cross_int[2 * OR_MAX_BONDS + 1];
     uint64_t cross_frac[2 * OR_MAX_BONDS + 1];
     double shift_gain;      /* delta / dt */
@@ -199,6 +205,18 @@ static int or_ratio_class(const or_run *r, uint64_t i, uint64_t j, int b) {
     return 0;
 }
 
+/* ratio class of a site flip of the field at site k applied to (i, j) */
+static int or_site_class(const or_run *r, uint64_t i, uint64_t j, int k) {
+    uint64_t d = i ^ j;
+    if (r->guide_kind == 1) {
+        if (d == 0) return 1;                 /* diagonal parent -> off-diagonal child */
+        if (d == (1ull << k)) return 2;       /* off-diagonal parent -> diagonal child */
+        return 0;
+    }
+    if (r->guide_kind == 2) return or_bit(d, k);   /* 0: site k starts to differ, 1: stops */
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* construction                                                              */
 /* ------------------------------------------------------------------------ */
@@ -256,6 +274,21 @@ static void or_build_rates(or_run *r) {
         }
     }
     r->jump_q = or_q(r->gamma * r->dt);
+    /* field site flips: |A| = |h|, times dt, times the ratio of the flipped site */
+    for (int k = 0; k < r->N; ++k) {
+        double base = fabs(r->h) * r->dt;
+        for (int c = 0; c < 4; ++c) {
+            double x = base;
+            if (r->guide_kind == 1) {
+                if (c == 1) x = base * w_off;
+                else if (c == 2) x = base * w_inv;
+            } else if (r->guide_kind == 2) {
+                if (c == 0) x = base * r->site_r[k];
+                else if (c == 1) x = base * (1.0 / r->site_r[k]);
+            }
+            r->frate_q[k][c] = or_q(x);
+        }
+    }
     /* on-site cross term: q = dt |Jz| |zsum(i) - zsum(j)| */
     double cbase = r->dt * fabs(r->Jz);
     for (int c = 0; c <= 2 * r->B; ++c) {
@@ -278,7 +311,7 @@ or_run *or_create(int Lx, int Ly, int periodic, double Jx, double Jy, double Jz,
                   double gamma, double dt, int64_t target, int32_t n_a,
                   int guide_kind, double guide_p, const double *site_r,
                   uint64_t seed, double delta, double S0, int64_t n0,
-                  int control, int64_t t_eq_override) {
+                  int control, int64_t t_eq_override, double h, int field_axis) {
     or_run *r = (or_run *)calloc(1, sizeof(or_run));
     if (!r) return NULL;
     r->Lx = Lx; r->Ly = Ly; r->periodic = periodic;
@@ -287,9 +320,11 @@ or_run *or_create(int Lx, int Ly, int periodic, double Jx, double Jy, double Jz,
     r->guide_kind = guide_kind; r->guide_p = guide_p;
     r->seed = seed; r->delta = delta; r->S0 = S0; r->n0 = n0;
     r->t_eq_override = t_eq_override;
+    r->h = h;
+    r->field_axis = field_axis;
     if (or_build_lattice(r) != OR_OK || !(dt > 0.0) || gamma < 0.0 || target <= 0 ||
         n_a < 0 || guide_kind < 0 || guide_kind > 2 || n0 < 0 || n0 > 2147483647 ||
-        (control != 0 && control != 1)) {
+        (control != 0 && control != 1) || !isfinite(h) || (field_axis != 0 && field_axis != 1)) {
         free(r);
         return NULL;
     }
@@ -302,7 +337,7 @@ or_run *or_create(int Lx, int Ly, int periodic, double Jx, double Jy, double Jz,
         }
     }
     or_build_rates(r);
-    r->nobs = 5 + r->N + 3 * r->B + 4;
+    r->nobs = 5 + r->N + 3 * r->B + 4 + 2 * r->N + 2;
     r->capL = 1024;
     r->L = (or_entry *)malloc(sizeof(or_entry) * (size_t)r->capL);
     if (!r->L) { free(r); return NULL; }
@@ -384,6 +419,31 @@ static int or_moves_of(const or_run *r, uint64_t i, uint64_t j, or_move *mv) {
             mv[K].rate = r->rate_q[b][al][cl];
             ++K;
         }
+    if (r->h != 0.0) {
+        /* -i H_ext rho and +i rho H_ext, H_ext = h sum_k sigma^x_k (axis 0) or
+         * h sum_k sigma^y_k (axis 1), Sec. V.B: one site flipped in the ket
+         * (A = -i <i'|H_ext|i>) or in the bra (A = +i <j|H_ext|j'>).  With
+         * <up|sy|down> = -i and <down|sy|up> = +i, both give A = h (2 s_k - 1)
+         * for the y axis, s the flipped word before the flip. */
+        for (int seg = 0; seg < 2; ++seg)
+            for (int g = 0; g < 4; ++g)
+                for (int k = 0; k < r->N; ++k) {
+                    if (or_site_class(r, i, j, k) != g) continue;
+                    uint64_t w = seg == 0 ? i : j;
+                    mv[K].cket = seg == 0 ? (i ^ (1ull << k)) : i;
+                    mv[K].cbra = seg == 0 ? j : (j ^ (1ull << k));
+                    mv[K].kind = 3 + seg;
+                    if (r->field_axis == 0) {
+                        mv[K].Are = 0.0;
+                        mv[K].Aim = seg == 0 ? -r->h : r->h;
+                    } else {
+                        mv[K].Are = r->h * (2.0 * (double)or_bit(w, k) - 1.0);
+                        mv[K].Aim = 0.0;
+                    }
+                    mv[K].rate = r->frate_q[k][g];
+                    ++K;
+                }
+    }
     for (int k = 0; k < r->N; ++k) {           /* gamma sigma^- rho sigma^+: needs bit k up on both sides */
         int ok = or_bit(i, k) && or_bit(j, k);
         mv[K].cket = i & ~(1ull << k); mv[K].cbra = j & ~(1ull << k); mv[K].kind = 2;
@@ -571,7 +631,7 @@ static int or_walk_entry(or_run *r, const uint32_t *d_int, const uint64_t *d_fra
 }
 
 int or_step(or_run *r, int64_t nsteps) {
-    or_move mv[2 * OR_MAX_BONDS + OR_MAX_SITES];
+    or_move mv[OR_MAX_MOVES];
     for (int64_t it = 0; it < nsteps; ++it) {
         uint32_t d_int[2 * OR_MAX_SITES + 1];
         uint64_t d_frac[2 * OR_MAX_SITES + 1];
@@ -604,7 +664,7 @@ int or_step(or_run *r, int64_t nsteps) {
         r->L = out; r->M = m; r->capL = m > 0 ? m : 1;
 
         /* estimators on rho(t+1), then the shift update of Sec. III.C */
-        int64_t est[5 + OR_MAX_SITES + 3 * OR_MAX_BONDS + 4];
+        int64_t est[5 + OR_MAX_SITES + 3 * OR_MAX_BONDS + 4 + 2 * OR_MAX_SITES + 2];
         or_estimate(r, est);
         int64_t Q = (r->control == 0) ? est[2] : est[3];
         if (r->variable) {
@@ -641,13 +701,20 @@ int or_step(or_run *r, int64_t nsteps) {
  *   [5+N .. +B)       sum_i z_a z_b Re rho_ii           (per-bond zz)
  *   [.. +B)           sum over i^j == m_b of Re rho_ij  (per-bond xx)
  *   [.. +B)           same with -1 if i is aligned on b, +1 if not (per-bond yy)
- *   [.. +4)           sums over sites / bonds of the four blocks above.
- * Importance weights divide the xx/yy numerators afterwards (Sec. IV.B). */
+ *   [.. +4)           sums over sites / bonds of the four blocks above,
+ *   [.. +N)           sum over i^j == 2^k of Re rho_ij   (per-site sigma^x)
+ *   [.. +N)           same of +Im rho_ij if site k is down in i, -Im if up
+ *                     (per-site sigma^y)
+ *   [.. +2)           sums over sites of the two blocks above.
+ * Importance weights divide the xx/yy/x/y numerators afterwards (Sec. IV.B).
+ * Without a field every move flips an even number of spins, so the sigma^x
+ * and sigma^y blocks stay zero. */
 static void or_estimate(or_run *r, int64_t *est) {
     int N = r->N, B = r->B;
     int nobs = r->nobs;
     for (int k = 0; k < nobs; ++k) est[k] = 0;
     int oz = 5, ozz = 5 + N, oxx = 5 + N + B, oyy = 5 + N + 2 * B, oag = 5 + N + 3 * B;
+    int ox = oag + 4, oy = ox + N, ofa = oy + N;
     for (int64_t e = 0; e < r->M; ++e) {
         uint64_t i = r->L[e].ket, j = r->L[e].bra;
         int64_t re = r->L[e].re, im = r->L[e].im;
@@ -662,6 +729,13 @@ static void or_estimate(or_run *r, int64_t *est) {
                 est[ozz + b] += (or_bit(i, r->bond_a[b]) == or_bit(i, r->bond_b[b])) ? re : -re;
         } else {
             uint64_t d = i ^ j;
+            if (or_popc(d) == 1) {
+                /* sigma^x_k: O_ji = 1; sigma^y_k: O_ji = -i if site k is down in i, +i if up */
+                int k = 0;
+                while (!((d >> k) & 1ull)) ++k;
+                est[ox + k] += re;
+                est[oy + k] += or_bit(i, k) ? -im : im;
+            }
             if (or_popc(d) == 2) {
                 for (int b = 0; b < B; ++b) {
                     if (r->bond_m[b] != d) continue;
@@ -673,6 +747,10 @@ static void or_estimate(or_run *r, int64_t *est) {
         }
     }
     for (int k = 0; k < N; ++k) est[oag + 0] += est[oz + k];
+    for (int k = 0; k < N; ++k) {
+        est[ofa + 0] += est[ox + k];
+        est[ofa + 1] += est[oy + k];
+    }
     for (int b = 0; b < B; ++b) {
         est[oag + 1] += est[ozz + b];
         est[oag + 2] += est[oxx + b];
@@ -753,7 +831,7 @@ int64_t or_series(const or_run *r, int64_t *out, int64_t cap_rows) {
  * A = L~[child, parent] and the fixed-point rate.  Returns the move count. */
 int or_moves(const or_run *r, uint64_t i, uint64_t j, uint64_t *cket, uint64_t *cbra,
              int32_t *kind, double *Are, double *Aim, uint64_t *rate) {
-    or_move mv[2 * OR_MAX_BONDS + OR_MAX_SITES];
+    or_move mv[OR_MAX_MOVES];
     int K = or_moves_of(r, i, j, mv);
     for (int k = 0; k < K; ++k) {
         cket[k] = mv[k].cket; cbra[k] = mv[k].cbra; kind[k] = mv[k].kind;
@@ -831,7 +909,7 @@ static int64_t or_find(const uint64_t *lket, const uint64_t *lbra, int64_t m, ui
 int or_gather(or_run *r, const uint64_t *lket, const uint64_t *lbra, const int32_t *lre, const int32_t *lim,
               int64_t m, const uint64_t *tket, const uint64_t *tbra, int64_t nt, int64_t *out_re, int64_t *out_im) {
     if (r->inj) return OR_ERR_ARG;        /* an injected stream is consumed in list order */
-    or_move mv[2 * OR_MAX_BONDS + OR_MAX_SITES];
+    or_move mv[OR_MAX_MOVES];
     uint32_t d_int[2 * OR_MAX_SITES + 1];
     uint64_t d_frac[2 * OR_MAX_SITES + 1];
     int d_sgn[2 * OR_MAX_SITES + 1];
@@ -851,12 +929,18 @@ int or_gather(or_run *r, const uint64_t *lket, const uint64_t *lbra, const int32
             own_re = (int64_t)lre[e] + dre;
             own_im = (int64_t)lim[e] + dim;
         }
-        /* candidate parents: 2B bond flips and up to N raised sites */
-        for (int c = 0; c < 2 * r->B + r->N; ++c) {
+        /* candidate parents: 2B bond flips, up to N raised sites, and with a
+         * field 2N single-site flips */
+        int ncand = 2 * r->B + r->N + (r->h != 0.0 ? 2 * r->N : 0);
+        for (int c = 0; c < ncand; ++c) {
             uint64_t pi = ci, pj = cj;
             if (c < r->B) pi ^= r->bond_m[c];
             else if (c < 2 * r->B) pj ^= r->bond_m[c - r->B];
-            else {
+            else if (c >= 2 * r->B + r->N) {
+                int k = c - 2 * r->B - r->N;
+                if (k < r->N) pi ^= 1ull << k;
+                else pj ^= 1ull << (k - r->N);
+            } else {
                 int k = c - 2 * r->B;
                 if (or_bit(ci, k) || or_bit(cj, k)) continue;
                 pi |= 1ull << k;

@@ -51,22 +51,27 @@ def site_op(op, k, N):
     return sp.kron(sp.kron(left, sp.csr_matrix(op)), right, format="csr")
 
 
-def hamiltonian(N, bonds, Jx, Jy, Jz):
+def hamiltonian(N, bonds, Jx, Jy, Jz, h=0.0, theta=0.0):
+    """XYZ bonds plus the in-plane field h sum_k (cos theta sx_k + sin theta sy_k) (Sec. V.B)."""
     d = 2 ** N
     H = sp.csr_matrix((d, d), dtype=complex)
     for a, b in bonds:
         H = H + Jx * (site_op(SX, a, N) @ site_op(SX, b, N))
         H = H + Jy * (site_op(SY, a, N) @ site_op(SY, b, N))
         H = H + Jz * (site_op(SZ, a, N) @ site_op(SZ, b, N))
+    if h != 0.0:
+        F = np.cos(theta) * SX + np.sin(theta) * SY
+        for k in range(N):
+            H = H + h * site_op(F, k, N)
     return H.tocsr()
 
 
-def liouvillian(Lx, Ly, periodic, Jx, Jy, Jz, gamma, S=0.0):
+def liouvillian(Lx, Ly, periodic, Jx, Jy, Jz, gamma, S=0.0, h=0.0, theta=0.0):
     """Shifted vectorised Liouvillian (d^2 x d^2, sparse), Kronecker form."""
     N = Lx * Ly
     d = 2 ** N
     bonds = lattice_bonds(Lx, Ly, periodic)
-    H = hamiltonian(N, bonds, Jx, Jy, Jz)
+    H = hamiltonian(N, bonds, Jx, Jy, Jz, h, theta)
     Id = sp.identity(d, dtype=complex, format="csr")
     L = -1j * (sp.kron(Id, H) - sp.kron(H.T, Id)) - S * sp.identity(d * d, dtype=complex)
     for k in range(N):

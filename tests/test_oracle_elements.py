@@ -17,18 +17,22 @@ def test_bonds_match(Lx, Ly, per):
     assert r.bonds() == E.lattice_bonds(Lx, Ly, per)
 
 
+FIELDS = [(0.0, 0), (0.37, 0), (-0.55, 1)]      # (h, axis): none, along x, along y
+
+
 @pytest.mark.parametrize("Lx,Ly,per", LATTICES)
 @pytest.mark.parametrize("J", [(0.9, 1.0, 1.0), (0.3, -1.2, 0.7), (1.1, 1.1, -0.4)])
-def test_every_element_matches_kronecker(Lx, Ly, per, J):
+@pytest.mark.parametrize("h,axis", FIELDS)
+def test_every_element_matches_kronecker(Lx, Ly, per, J, h, axis):
     Jx, Jy, Jz = J
     gamma, S = 0.7, 0.37
-    r = O.OracleRun(Lx, Ly, per, Jx, Jy, Jz, gamma, 0.01, 100, shift0=S)
+    r = O.OracleRun(Lx, Ly, per, Jx, Jy, Jz, gamma, 0.01, 100, shift0=S, field_h=h, field_axis=axis)
     d = 2 ** (Lx * Ly)
-    L = E.liouvillian(Lx, Ly, per, Jx, Jy, Jz, gamma, S=S).toarray()
+    L = E.liouvillian(Lx, Ly, per, Jx, Jy, Jz, gamma, S=S, h=h, theta=axis * np.pi / 2).toarray()
     rebuilt = np.zeros_like(L)
     for i, j in itertools.product(range(d), range(d)):
         ck, cb, kind, A, rate = r.moves(i, j)
-        assert len(A) == 2 * r.B + r.N
+        assert len(A) == 2 * r.B + r.N + (2 * r.N if h else 0)
         p = E.vec_index(i, j, d)
         for a, b, amp in zip(ck, cb, A):
             if amp != 0:
@@ -51,14 +55,15 @@ def _weight(i, j, kind, p, r_site, N):
 
 
 @pytest.mark.parametrize("kind", [0, 1, 2])
-def test_rates_are_truncated_scaled_elements(kind):
+@pytest.mark.parametrize("h,axis", FIELDS)
+def test_rates_are_truncated_scaled_elements(kind, h, axis):
     """Each fixed-point rate is |A| dt w(child)/w(parent) * 2^32 truncated (to within
     the rounding of the product order)."""
     Lx, Ly, per = 2, 2, 0
     dt, p = 0.05, 1.3
     r_site = [0.5, 0.7, 0.9, 0.6]
     r = O.OracleRun(Lx, Ly, per, 0.9, 1.0, 1.0, 1.0, dt, 100, guide_kind=kind, guide_p=p,
-                    site_ratio=r_site if kind == 2 else None)
+                    site_ratio=r_site if kind == 2 else None, field_h=h, field_axis=axis)
     d = 16
     for i, j in itertools.product(range(d), range(d)):
         ck, cb, _, A, rate = r.moves(i, j)

@@ -19,6 +19,8 @@ def _cases():
     yield "2x2 open, n_a=0", dict(W.C1), 400
     yield "3x3 periodic, n_a=3", dict(W.C2, target=3000), 300
     yield "4x4 periodic, guide, n_a=3", dict(W.C3, target=4000), 250
+    yield "2x2 open, field along x", dict(W.C1, field_h=0.3, field_axis=0), 300
+    yield "3x3 periodic, field along y, n_a=3", dict(W.C2, target=3000, field_h=-0.2, field_axis=1), 200
 
 
 @pytest.mark.parametrize("name,cfg,steps", list(_cases()), ids=[c[0] for c in _cases()])

@@ -56,6 +56,14 @@ def test_estimator_numerators_are_traces_with_matrices():
             assert est[lay[name] + b] == round(ref), (name, b)
     assert est[lay["sum_z"]] == est[lay["z"]:lay["z"] + N].sum()
     assert est[lay["sum_xx"]] == est[lay["xx"]:lay["xx"] + B].sum()
+    # single-site sigma^x, sigma^y (non-zero only with entries of odd parity: the field)
+    for k in range(N):
+        for name, op in (("x", E.SX), ("y", E.SY)):
+            ref = E.expect(rho, E.site_op(op, k, N)).real
+            assert est[lay[name] + k] == round(ref), (name, k)
+    assert est[lay["sum_x"]] == est[lay["x"]:lay["x"] + N].sum()
+    assert est[lay["sum_y"]] == est[lay["y"]:lay["y"] + N].sum()
+    assert lay["nobs"] == len(est)
 
 
 def test_shift_follows_log_update():
