@@ -78,6 +78,9 @@ typedef struct {
     int32_t sm_limit;          /* > 0: size every kernel grid for at most this many SMs, so that
                                   several runs stepped on their own streams share the GPU;
                                   <= 0 (default): the whole GPU */
+    double field_h;            /* in-plane field of Sec. V.B, H += h sum_k (cos t sx_k + sin t sy_k);
+                                  default 0 (none) */
+    int32_t field_axis;        /* direction t: 0 along x (t = 0), 1 along y (t = pi/2); default 0 */
 } ddqmc_options;
 
 typedef struct ddqmc_run ddqmc_run;
@@ -102,6 +105,8 @@ typedef struct {
     double xx, xx_err, yy, yy_err, zz, zz_err;     /* bond averages of <s s> */
     double sz[DDQMC_MAX_SITES], sz_err[DDQMC_MAX_SITES];
     double bond_xx[DDQMC_MAX_BONDS], bond_yy[DDQMC_MAX_BONDS], bond_zz[DDQMC_MAX_BONDS];
+    double mx, mx_err, my, my_err;   /* (1/N) sum_k <sigma^x_k>, <sigma^y_k>: non-zero only with a field */
+    double sx[DDQMC_MAX_SITES], sy[DDQMC_MAX_SITES];
 } ddqmc_estimates;
 
 /* Scalar state of a run (for checkpoints and single-step comparisons). */

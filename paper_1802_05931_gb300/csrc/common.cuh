@@ -11,8 +11,8 @@ namespace ddq {
 constexpr int MAXN = 64;                      // sites: one 64-bit spin word per side
 constexpr int NPACK = 31;                     // up to here ket and bra pack into one 62-bit key
 constexpr int MAXB = 128;                     // bonds (2N for a periodic 2D lattice)
-constexpr int MAXK = 2 * MAXB + MAXN;         // moves per configuration
-constexpr int NOBS_MAX = 5 + MAXN + 3 * MAXB + 4;
+constexpr int MAXK = 2 * MAXB + 3 * MAXN;     // moves per configuration (bond flips, field flips, jumps)
+constexpr int NOBS_MAX = 5 + MAXN + 3 * MAXB + 4 + 2 * MAXN + 2;
 constexpr int LEVELS = 32;                    // blocking levels (block length 2^l)
 constexpr int MAXPASS = 16;                   // radix passes of 8 bits over at most 128 key bits
 
@@ -77,6 +77,10 @@ struct RunParams {
     int32_t uniform;                  // 1 if every bond has the same rate table
     int32_t pad1;
     int32_t pass_shift[MAXPASS];      // key bit where the digit of each radix pass starts
+    // in-plane field h sum_k sigma^x_k (axis 0) or sigma^y_k (axis 1)
+    int32_t field_on, field_axis, sgn_hf, pad2;
+    uint64_t frate_q[MAXN][4];        // site flip of site k, [importance class]
+    uint64_t ufrate[4];               // the same when every site has the same table
     uint64_t Emorton;                 // bond-existence mask, bit 2k = right bond of k, 2k+1 = lower (sites < 32)
     uint64_t Emorton_hi;              // the same for sites 32..63 (bit 2(k-32), 2(k-32)+1)
     uint64_t urate8[8];               // rate of group 4*anti + class when every bond has the same table

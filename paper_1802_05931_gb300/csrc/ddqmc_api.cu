@@ -44,6 +44,7 @@ struct ddqmc_run {
     bool wide = false;           // two-word keys (N > 31): RecW lists and spawn records
     int guide_kind = 0;
     double w_bond[MAXB];         // importance weight of a configuration differing on bond b only
+    double w_site[MAXN];         // importance weight of a configuration differing on site k only
     int host_status = 0;         // sticky host-visible status
     // optional per-kernel timing (CUDA events on the run's stream)
     bool timing = false;
@@ -97,6 +98,7 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
     if (!std::isfinite(Jx) || !std::isfinite(Jy) || !std::isfinite(Jz) || !std::isfinite(gamma) || !std::isfinite(dt))
         return DDQMC_ERR_INVALID_ARG;
     if (o.n0 < 0 || o.n0 > 2147483647ll || (o.control != 0 && o.control != 1)) return DDQMC_ERR_INVALID_ARG;
+    if (!std::isfinite(o.field_h) || (o.field_axis != 0 && o.field_axis != 1)) return DDQMC_ERR_INVALID_ARG;
     const int N = Lx * Ly;
     if (N > MAXN) return DDQMC_ERR_UNSUPPORTED;
     P.N = N;
@@ -109,8 +111,11 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
             if (Ly > 1 && (y + 1 < Ly || per)) { P.bond_a[B] = a; P.bond_b[B] = x + Lx * ((y + 1) % Ly); ++B; }
         }
     P.B = B;
-    P.K = 2 * B + N;
-    P.nobs = 5 + N + 3 * B + 4;
+    P.field_on = o.field_h != 0.0 ? 1 : 0;
+    P.field_axis = o.field_axis;
+    P.sgn_hf = o.field_h > 0.0 ? 1 : (o.field_h < 0.0 ? -1 : 0);
+    P.K = 2 * B + N + (P.field_on ? 2 * N : 0);
+    P.nobs = 5 + N + 3 * B + 4 + 2 * N + 2;
     if (N <= NPACK) {
         P.npass = (2 * N + 7) / 8;                 // digits of the packed key bra << N | ket
         for (int p = 0; p < P.npass; ++p) P.pass_shift[p] = 8 * p;
@@ -161,6 +166,7 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
     P.guide_kind = gk;
     r->guide_kind = gk;
     const double hval[2] = {std::fabs(Jx - Jy), std::fabs(Jx + Jy)};
+    for (int k = 0; k < N; ++k) r->w_site[k] = gk == 1 ? w_off : (gk == 2 ? site_r[k] : 1.0);
     for (int b = 0; b < B; ++b) {
         r->w_bond[b] = gk == 1 ? w_off : (gk == 2 ? site_r[P.bond_a[b]] * site_r[P.bond_b[b]] : 1.0);
         for (int h = 0; h < 2; ++h) {
@@ -182,6 +188,21 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
         }
     }
     P.jump_q = fixed_rate(gamma * dt);
+    // field site flips: |A| = |h|, times dt, times the ratio of the flipped site
+    for (int k = 0; k < N; ++k) {
+        const double base = std::fabs(o.field_h) * dt;
+        for (int c = 0; c < 4; ++c) {
+            double x = base;
+            if (gk == 1) {
+                if (c == 1) x = base * w_off;
+                else if (c == 2) x = base * w_inv;
+            } else if (gk == 2) {
+                if (c == 0) x = base * site_r[k];
+                else if (c == 1) x = base * (1.0 / site_r[k]);
+            }
+            P.frate_q[k][c] = fixed_rate(x);
+        }
+    }
     // geometry masks and the bond-uniform rate table of the popcount formulation
     P.Lx = Lx;
     P.shD = Lx * (Ly - 1);
@@ -208,8 +229,11 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
     for (int b = 1; b < B; ++b)
         for (int h = 0; h < 2; ++h)
             for (int c = 0; c < 4; ++c) uni = uni && P.rate_q[b][h][c] == P.rate_q[0][h][c];
+    for (int k = 1; k < N; ++k)
+        for (int c = 0; c < 4; ++c) uni = uni && P.frate_q[k][c] == P.frate_q[0][c];
     P.uniform = uni ? 1 : 0;
     for (int g = 0; g < 8; ++g) P.urate8[g] = P.rate_q[0][g >> 2][g & 3];
+    for (int c = 0; c < 4; ++c) P.ufrate[c] = P.frate_q[0][c];
     const double cbase = dt * std::fabs(Jz);
     for (int c = 0; c <= 2 * B; ++c) {
         const double x = cbase * (double)c;
@@ -563,6 +587,8 @@ int ddqmc_default_options(ddqmc_options *o) {
     o->capacity_spawns = 0;
     o->cuda_stream = nullptr;
     o->sm_limit = 0;
+    o->field_h = 0.0;
+    o->field_axis = 0;
     return DDQMC_OK;
 }
 
@@ -885,6 +911,37 @@ int ddqmc_estimators(ddqmc_run *r, ddqmc_estimates *out) {
     blocked_ratio(cells, core + 3, R, e);
     out->yy = B ? R / (B * w0) : NAN;
     out->yy_err = B ? e / (B * w0) : NAN;
+    // single-site sigma^x, sigma^y (non-zero only with a field): numerators / site weight
+    {
+        const int ox = core + 4, oy = ox + N;
+        double sxs = 0, sys = 0, exs = 0, eys = 0;
+        for (int k = 0; k < N; ++k) {
+            double Rk, ek;
+            blocked_ratio(cells, ox + k, Rk, ek);
+            out->sx[k] = Rk / r->w_site[k];
+            sxs += out->sx[k];
+            exs += (ek / r->w_site[k]) * (ek / r->w_site[k]);
+            blocked_ratio(cells, oy + k, Rk, ek);
+            out->sy[k] = Rk / r->w_site[k];
+            sys += out->sy[k];
+            eys += (ek / r->w_site[k]) * (ek / r->w_site[k]);
+        }
+        bool uniform_s = true;
+        for (int k = 1; k < N; ++k) uniform_s = uniform_s && r->w_site[k] == r->w_site[0];
+        if (uniform_s) {        // the blocked error of the site sum
+            blocked_ratio(cells, oy + N, R, e);
+            out->mx = R / (N * r->w_site[0]);
+            out->mx_err = e / (N * r->w_site[0]);
+            blocked_ratio(cells, oy + N + 1, R, e);
+            out->my = R / (N * r->w_site[0]);
+            out->my_err = e / (N * r->w_site[0]);
+        } else {
+            out->mx = sxs / N;
+            out->my = sys / N;
+            out->mx_err = std::sqrt(exs) / N;
+            out->my_err = std::sqrt(eys) / N;
+        }
+    }
     if (!uniform_w && B) {      // per-bond weights differ: average the per-bond estimates
         double sx = 0, sy = 0, ex = 0, ey = 0;
         for (int b = 0; b < B; ++b) {

@@ -31,21 +31,30 @@ k_finalize(const RunParams *__restrict__ Pp, DevState *__restrict__ st, BlkCell 
     const int tid = threadIdx.x;
     if (block_stopped(st)) return;
     const int N = P.N, B = P.B, nobs = P.nobs;
+    // layout: [0, 5) totals, z per site, zz / xx / yy per bond, their 4 sums,
+    // x and y per site, their 2 sums (the sums are formed here)
     const int core = 5 + N + 3 * B;
-    for (int q = tid; q < core; q += FN_TPB) s_est[q] = st->est[q];
+    const int ox = core + 4, oy = ox + N;
+    for (int q = tid; q < nobs; q += FN_TPB) s_est[q] = st->est[q];
     __syncthreads();
     if (tid == 0) {
-        int64_t sz = 0, szz = 0, sxx = 0, syy = 0;
+        int64_t sz = 0, szz = 0, sxx = 0, syy = 0, sx = 0, sy = 0;
         for (int k = 0; k < N; ++k) sz += s_est[5 + k];
         for (int b = 0; b < B; ++b) {
             szz += s_est[5 + N + b];
             sxx += s_est[5 + N + B + b];
             syy += s_est[5 + N + 2 * B + b];
         }
+        for (int k = 0; k < N; ++k) {
+            sx += s_est[ox + k];
+            sy += s_est[oy + k];
+        }
         s_est[core + 0] = sz;
         s_est[core + 1] = szz;
         s_est[core + 2] = sxx;
         s_est[core + 3] = syy;
+        s_est[oy + N] = sx;
+        s_est[oy + N + 1] = sy;
         // shift update on the controlled weight
         const int64_t Q = P.control == 0 ? s_est[2] : s_est[3];
         double S = st->S;
@@ -84,10 +93,10 @@ k_finalize(const RunParams *__restrict__ Pp, DevState *__restrict__ st, BlkCell 
     for (int q = tid; q < MAXPASS + 16; q += FN_TPB) st->tickets[q] = 0u;
     for (int q = tid; q < MAXPASS * 256; q += FN_TPB) (&st->hist[0][0])[q] = 0u;
     if (tid <= 2 * N) death_entry(P, s_S, tid, st);
-    if (s_append && tid < nobs) {
-        // binary-counter cascade of block sums for observable tid against the trace
-        int64_t x = s_est[tid], y = s_est[0];
-        BlkCell *cells = blk + (size_t)tid * LEVELS;
+    for (int q = tid; s_append && q < nobs; q += FN_TPB) {
+        // binary-counter cascade of block sums for observable q against the trace
+        int64_t x = s_est[q], y = s_est[0];
+        BlkCell *cells = blk + (size_t)q * LEVELS;
         for (int l = 0; l < LEVELS; ++l) {
             BlkCell &c = cells[l];
             c.n += 1;

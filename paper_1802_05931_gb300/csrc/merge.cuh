@@ -257,7 +257,13 @@ __device__ __forceinline__ void add_estimators(MergeShared<T> &s, const RunParam
         }
     } else {
         const uint64_t d = i ^ j;
-        if (__popcll(d) == 2) {
+        if (__popcll(d) == 1) {
+            // sigma^x_k, sigma^y_k (configurations of odd parity: only with a field)
+            const int k = __ffsll((long long)d) - 1;
+            const int ox = 5 + N + 3 * B + 4;
+            atomicAdd(&s.est[ox + k], (unsigned long long)(int64_t)re);
+            atomicAdd(&s.est[ox + N + k], (unsigned long long)(int64_t)(((i >> k) & 1ull) ? -im : im));
+        } else if (__popcll(d) == 2) {
             const int a = __ffsll((long long)d) - 1;
             const int b2 = 63 - __clzll((long long)d);
             const int b = s.pair_bond[a * N + b2];
@@ -525,7 +531,7 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                 my_m += 1;
                 uint64_t i, j;
                 key_words(ws.key[q], nmask, N, i, j);
-                if (i == j || __popcll(i ^ j) == 2) add_estimators(s, P, i, j, v.re, v.im);
+                if (i == j || __popcll(i ^ j) <= 2) add_estimators(s, P, i, j, v.re, v.im);
             }
         }
         __syncwarp();
@@ -542,8 +548,7 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
     }
     if (local_status) atomicOr(&st->status, local_status);
     __syncthreads();
-    const int nobs_core = 5 + N + 3 * P.B;
-    for (int q = tid; q < nobs_core; q += MG_TPB)
+    for (int q = tid; q < P.nobs; q += MG_TPB)
         if (s.est[q]) atomicAdd((unsigned long long *)&st->est[q], s.est[q]);
 }
 

@@ -74,6 +74,8 @@ struct LightSoA {
     uint64_t Tket[32], Tbra[32], T[32];        // rate totals: ket moves, bra moves, all moves
     uint64_t gk[32], gb[32];                   // bonds per group (8 bytes), ket and bra
     SW i[32], j[32];
+    uint64_t Tf[32];                           // field flips: rate total of one segment (ket or bra)
+    uint32_t fc[32];                           // field flips: sites per importance class (8 bits each)
     uint32_t natt[32];
     int32_t re[32], im[32], nre[32];
     int32_t cd[32], adz[32], sgn_d[32], init[32];
@@ -90,8 +92,8 @@ struct HeavyTables {
     int16_t mv[KM];
 };
 
-// moves per configuration: 2 * 62 bonds + 31 sites for one-word keys
-constexpr int MAXK_PACK = 2 * 2 * NPACK + NPACK + 1;
+// moves per configuration for one-word keys: 2 * 62 bonds + 3 * 31 sites
+constexpr int MAXK_PACK = 2 * 2 * NPACK + 3 * NPACK + 1;
 
 // A warp's light-configuration parameters are dead before its heavy
 // configurations start, so the two share storage.
@@ -117,6 +119,10 @@ struct SpawnTables {
     int8_t bond_a[MAXB], bond_b[MAXB];
     int8_t rn[MAXN + 1], dn[MAXN + 1];
     int32_t pass_shift[MAXPASS];
+    uint64_t ufrate[4];               // field flip rate of each importance class (uniform tables)
+    uint32_t ufrate32[4];
+    float ufinv[4];
+    int32_t field_on, field_axis, sgn_hf;
 };
 
 // Shared memory of the spawn kernel for spawn records of type T; packed
@@ -138,6 +144,7 @@ struct SpawnCtx {
     const SpawnTables *sh;
     int N, B, K, gk;
     uint64_t jump_q;
+    uint64_t nmask;
     uint64_t ER, ED, LC, LR;
     int Lx, shD;
     uint64_t Emorton, Emorton_hi;
@@ -251,6 +258,32 @@ __device__ __forceinline__ void class_masks(const SpawnCtx &c, SW i, SW j, MT &X
     }
 }
 
+// sites of each importance class of a field flip of (i, j) (nm: the N site bits):
+// site-product guide: class 0 = sites where i and j agree, 1 = where they
+// differ; uniform guide: class 1 = every site of a diagonal parent, class 2 =
+// the one differing site, class 0 = the rest
+template <typename SW>
+__device__ __forceinline__ void field_masks(const SpawnCtx &c, SW i, SW j, SW (&fm)[4]) {
+    const SW d = i ^ j, nm = (SW)c.nmask;
+    fm[0] = 0; fm[1] = 0; fm[2] = 0; fm[3] = 0;
+    if (c.gk == 2) {
+        fm[0] = ~d & nm;
+        fm[1] = d;
+    } else if (c.gk == 1) {
+        if (d == 0) fm[1] = nm;
+        else if (popcount(d) == 1) { fm[2] = d; fm[0] = ~d & nm; }
+        else fm[0] = nm;
+    } else {
+        fm[0] = nm;
+    }
+}
+
+__device__ __forceinline__ int site_class(int gk, uint64_t d, int k) {
+    if (gk == 1) return d == 0 ? 1 : (d == (1ull << k) ? 2 : 0);
+    if (gk == 2) return (int)((d >> k) & 1ull);
+    return 0;
+}
+
 // bonds of group g = 4*anti + class, given the anti mask A of the flipped word
 template <typename MT>
 __device__ __forceinline__ MT group_mask(const SpawnCtx &c, MT A, MT X1, MT X2, int g) {
@@ -331,29 +364,45 @@ __device__ __forceinline__ int seg_select32(const SpawnCtx &c, const uint32_t *r
 
 // ---- per-move tables (heavy path) -------------------------------------------
 
-// Child (ci, cj) of move m of configuration (i, j) and the sign factor g of
-// the move: a real parent of sign s makes an imaginary child of sign s*g and
-// an imaginary parent a real child of sign -s*g (bond flips); jumps keep the
-// type.
+// Child (ci, cj) of move m of configuration (i, j).  Move ids: ket bond b,
+// bra bond B + b, ket field flip 2B + k, bra field flip 2B + N + k, jump
+// 2B + 2N + k.  same: the child has the parent's type (real / imaginary);
+// a: the sign of the element's non-zero part -- a real parent of sign s makes
+// a child of sign s*a, an imaginary parent one of sign s*a (same type) or
+// -s*a (other type).
 __device__ __forceinline__ void move_child(const SpawnCtx &c, const RunParams &P, uint64_t i, uint64_t j, int m,
-                                           uint64_t &ci, uint64_t &cj, int &g, bool &jump) {
+                                           uint64_t &ci, uint64_t &cj, bool &same, int &a) {
     const SpawnTables &s = *c.sh;
     ci = i;
     cj = j;
-    jump = m >= 2 * c.B;
-    g = 1;
-    if (!jump) {
-        const bool ket = m < c.B;
-        const int b = ket ? m : m - c.B;
+    const int B = c.B, N = c.N;
+    if (m < 2 * B) {                 // bond flip: A = -i h_b (ket) or +i h_b (bra)
+        const bool ket = m < B;
+        const int b = ket ? m : m - B;
         const uint64_t w = ket ? i : j;
         const int anti = (int)(((w >> s.bond_a[b]) ^ (w >> s.bond_b[b])) & 1ull);
         const int hs = P.sgn_h[anti];
         if (ket) ci ^= s.bond_m[b]; else cj ^= s.bond_m[b];
-        g = ket ? -hs : hs;          // A = -i h (ket) or +i h (bra)
-    } else {
-        const int k = m - 2 * c.B;
+        same = false;
+        a = ket ? -hs : hs;
+    } else if (m < 2 * B + 2 * N) {  // field flip: -i h (ket), +i h (bra) along x; h (2 s_k - 1) along y
+        const bool ket = m < 2 * B + N;
+        const int k = ket ? m - 2 * B : m - 2 * B - N;
+        const uint64_t w = ket ? i : j;
+        if (ket) ci ^= 1ull << k; else cj ^= 1ull << k;
+        if (s.field_axis == 0) {
+            same = false;
+            a = ket ? -s.sgn_hf : s.sgn_hf;
+        } else {
+            same = true;
+            a = ((w >> k) & 1ull) ? s.sgn_hf : -s.sgn_hf;
+        }
+    } else {                         // jump: +gamma
+        const int k = m - 2 * B - 2 * N;
         ci &= ~(1ull << k);
         cj &= ~(1ull << k);
+        same = true;
+        a = 1;
     }
 }
 
@@ -514,9 +563,44 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
             const int gsg = ket ? -hs : hs;
             if (ket) ci ^= m; else cj ^= m;
             if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
+        } else if (v - qTket - qTbra < 2 * q.Tf[o]) {
+            // field flip: ket segment, then bra segment; groups by importance class
+            const uint64_t qTf = q.Tf[o];
+            const uint32_t fcp = q.fc[o];
+            const uint64_t vb = v - qTket - qTbra;
+            const bool ket = vb < qTf;
+            uint64_t vf = ket ? vb : vb - qTf;
+            int g = 0;
+            for (; g < 3; ++g) {
+                const uint64_t w = s.ufrate[g] * (uint64_t)((fcp >> (8 * g)) & 0xFFu);
+                if (vf < w) break;
+                vf -= w;
+            }
+            uint32_t idx;
+            if (qT <= 0xFFFFFFFFull) {
+                const uint32_t rq = s.ufrate32[g];
+                idx = (uint32_t)((float)(uint32_t)vf * s.ufinv[g]);
+                const uint64_t pq = (uint64_t)idx * rq;
+                if (pq > vf) --idx;
+                else if (pq + rq <= vf) ++idx;
+            } else {
+                idx = small_quotient(vf, s.ufrate[g]);
+            }
+            SW fm[4];
+            field_masks<SW>(c, qi, qj, fm);
+            const int k = select_bit(fm[g], idx);
+            const SW w = ket ? qi : qj;
+            if (ket) ci ^= (SW)1 << k; else cj ^= (SW)1 << k;
+            if (s.field_axis == 0) {             // -i h (ket), +i h (bra): the other type
+                const int gsg = ket ? -s.sgn_hf : s.sgn_hf;
+                if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
+            } else {                             // h (2 s_k - 1): the same type
+                const int a = ((w >> k) & 1) ? s.sgn_hf : -s.sgn_hf;
+                if (part == 0) cre = sig * a; else cim = sig * a;
+            }
         } else {
             // jumps share one rate: the site index is the quotient by it
-            const uint64_t vj = v - qTket - qTbra;
+            const uint64_t vj = v - qTket - qTbra - 2 * q.Tf[o];
             uint32_t idx;
             if (qT <= 0xFFFFFFFFull) {
                 idx = (uint32_t)((float)(uint32_t)vj * s.jinv);
@@ -567,6 +651,12 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
     }
     if (tid < 2) s.sgn_h[tid] = P.sgn_h[tid];
     if (tid == 0) s.jinv = P.jump_q ? 1.0f / (float)P.jump_q : 0.0f;
+    if (tid < 4) {
+        s.ufrate[tid] = P.ufrate[tid];
+        s.ufrate32[tid] = (uint32_t)P.ufrate[tid];
+        s.ufinv[tid] = P.ufrate[tid] ? 1.0f / (float)P.ufrate[tid] : 0.0f;
+    }
+    if (tid == 0) { s.field_on = P.field_on; s.field_axis = P.field_axis; s.sgn_hf = P.sgn_hf; }
     for (int q = tid; q <= 2 * B; q += SP_TPB) { s.cross_int[q] = P.cross_int[q]; s.cross_frac[q] = P.cross_frac[q]; }
     for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_frac[q] = st->d_frac[q]; s.d_sgn[q] = st->d_sgn[q]; }
     for (int q = tid; q < SpawnShared<T>::NP * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
@@ -574,7 +664,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
     __syncthreads();
 
     SpawnCtx c;
-    c.sh = &s; c.N = N; c.B = B; c.K = K; c.gk = P.guide_kind; c.jump_q = P.jump_q;
+    c.sh = &s; c.N = N; c.B = B; c.K = K; c.gk = P.guide_kind; c.jump_q = P.jump_q; c.nmask = P.nmask;
     c.ER = P.ER; c.ED = P.ED; c.LC = P.LC; c.LR = P.LR; c.Lx = P.Lx; c.shD = P.shD;
     c.Emorton = P.Emorton; c.Emorton_hi = P.Emorton_hi;
     const bool uniform = P.uniform != 0;
@@ -623,7 +713,19 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 Tket += s.urate8[g] * (uint64_t)ck;
                 Tbra += s.urate8[g] * (uint64_t)cb;
             }
-            const uint64_t Tall = Tket + Tbra + (uint64_t)popcount((SW)(i32 & j32)) * c.jump_q;
+            uint64_t Tf = 0;
+            uint32_t fcp = 0;
+            if (P.field_on) {
+                SW fm[4];
+                field_masks<SW>(c, i32, j32, fm);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int cf = popcount(fm[g]);
+                    fcp |= (uint32_t)cf << (8 * g);
+                    Tf += s.ufrate[g] * (uint64_t)cf;
+                }
+            }
+            const uint64_t Tall = Tket + Tbra + 2 * Tf + (uint64_t)popcount((SW)(i32 & j32)) * c.jump_q;
             const uint64_t natt = (Tall + 0xFFFFFFFFull) >> 32;
             q.Ai[lane] = Ai;
             q.Aj[lane] = Aj;
@@ -632,6 +734,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             q.Tket[lane] = Tket;
             q.Tbra[lane] = Tbra;
             q.T[lane] = Tall;
+            q.Tf[lane] = Tf;
+            q.fc[lane] = fcp;
             q.gk[lane] = gkp;
             q.gb[lane] = gbp;
             q.natt[lane] = natt == 0 ? 1u : (uint32_t)natt;
@@ -810,9 +914,39 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                         }
                     }
                 }
+                if (P.field_on) {
+                    // field flips: ket then bra, groups by importance class, sites in order
+                    for (int seg = 0; seg < 2; ++seg) {
+                        int gq[2];
+                        uint64_t rq[2];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int k = lane + 32 * q;
+                            gq[q] = -1;
+                            rq[q] = 0;
+                            if (k < N) {
+                                gq[q] = site_class(c.gk, hd, k);
+                                rq[q] = P.frate_q[k][gq[q]];
+                            }
+                        }
+                        for (int g = 0; g < 4; ++g) {
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                if (32 * q >= N) break;
+                                const unsigned mq = __ballot_sync(0xFFFFFFFFu, gq[q] == g);
+                                if (gq[q] == g) {
+                                    const int pos = base + __popc(mq & lt);
+                                    s.ws[warp].hv.cum[pos] = rq[q];
+                                    s.ws[warp].hv.mv[pos] = (int16_t)(2 * B + seg * N + lane + 32 * q);
+                                }
+                                base += __popc(mq);
+                            }
+                        }
+                    }
+                }
                 for (int k = lane; k < N; k += 32) {
-                    s.ws[warp].hv.cum[2 * B + k] = (((hi & hj) >> k) & 1ull) ? c.jump_q : 0ull;
-                    s.ws[warp].hv.mv[2 * B + k] = (int16_t)(2 * B + k);
+                    s.ws[warp].hv.cum[base + k] = (((hi & hj) >> k) & 1ull) ? c.jump_q : 0ull;
+                    s.ws[warp].hv.mv[base + k] = (int16_t)(2 * B + 2 * N + k);
                 }
                 __syncwarp();
             }
@@ -871,11 +1005,11 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                         }
                         uint64_t ci, cj;
                         int gsg;
-                        bool jump;
-                        move_child(c, P, hi, hj, s.ws[warp].hv.mv[lo], ci, cj, gsg, jump);
+                        bool same;
+                        move_child(c, P, hi, hj, s.ws[warp].hv.mv[lo], ci, cj, same, gsg);
                         // child type (0 real, 1 imaginary) and signed unit
-                        const int tgt = jump ? part : 1 - part;
-                        const int val = jump ? sig : (part == 0 ? sig * gsg : -sig * gsg);
+                        const int tgt = same ? part : 1 - part;
+                        const int val = (same || part == 0) ? sig * gsg : -sig * gsg;
                         // one shared-memory update per distinct (move, type) among the lanes here
                         const unsigned am = __activemask();
                         const unsigned peers = __match_any_sync(am, (unsigned)(lo * 2 + tgt));
@@ -904,8 +1038,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 if (cre == 0 && cim == 0) continue;
                 uint64_t ci, cj;
                 int gsg;
-                bool jump;
-                move_child(c, P, hi, hj, s.ws[warp].hv.mv[m], ci, cj, gsg, jump);
+                bool same;
+                move_child(c, P, hi, hj, s.ws[warp].hv.mv[m], ci, cj, same, gsg);
                 emit_counts(s, warp, ci, cj, N, hinit, cre, cim, out, cap, st, npass);
             }
             flush(s, warp, lane, out, cap, st, npass, SP_FLUSH);

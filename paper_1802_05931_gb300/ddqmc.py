@@ -40,7 +40,8 @@ class ddqmc_options(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("damping", C.c_double), ("shift0", C.c_double),
                 ("n0", C.c_int64), ("control", C.c_int32), ("t_eq", C.c_int64),
                 ("capacity_entries", C.c_int64), ("capacity_spawns", C.c_int64),
-                ("cuda_stream", C.c_void_p), ("sm_limit", C.c_int32)]
+                ("cuda_stream", C.c_void_p), ("sm_limit", C.c_int32), ("field_h", C.c_double),
+                ("field_axis", C.c_int32)]
 
 
 class ddqmc_estimates(C.Structure):
@@ -54,7 +55,9 @@ class ddqmc_estimates(C.Structure):
                 ("zz", C.c_double), ("zz_err", C.c_double),
                 ("sz", C.c_double * MAX_SITES), ("sz_err", C.c_double * MAX_SITES),
                 ("bond_xx", C.c_double * MAX_BONDS), ("bond_yy", C.c_double * MAX_BONDS),
-                ("bond_zz", C.c_double * MAX_BONDS)]
+                ("bond_zz", C.c_double * MAX_BONDS),
+                ("mx", C.c_double), ("mx_err", C.c_double), ("my", C.c_double), ("my_err", C.c_double),
+                ("sx", C.c_double * MAX_SITES), ("sy", C.c_double * MAX_SITES)]
 
 
 class ddqmc_state(C.Structure):
@@ -161,7 +164,7 @@ def ddqmc_estimators(run):
     return rc, e
 
 
-def ddqmc_raw_estimators(run, cap=512):
+def ddqmc_raw_estimators(run, cap=1024):
     out = np.zeros(cap, dtype=np.int64)
     n = C.c_int32()
     _check(load().ddqmc_raw_estimators(run, _p(out, C.c_int64), cap, C.byref(n)), "ddqmc_raw_estimators")
@@ -269,7 +272,8 @@ class Run:
 
     def __init__(self, Lx, Ly, periodic, Jx, Jy, Jz, gamma, dt, target, n_a=0, guide_kind=0,
                  guide_p=0.0, site_ratio=None, seed=1, damping=0.05, shift0=-1.0, n0=1000, control=0,
-                 t_eq=-1, capacity_entries=0, capacity_spawns=0, stream=None, sm_limit=0):
+                 t_eq=-1, capacity_entries=0, capacity_spawns=0, stream=None, sm_limit=0, field_h=0.0,
+                 field_axis=0):
         o = ddqmc_default_options()
         o.seed = int(seed) & ((1 << 64) - 1)
         o.damping = damping
@@ -281,6 +285,8 @@ class Run:
         o.capacity_spawns = int(capacity_spawns)
         o.cuda_stream = stream
         o.sm_limit = int(sm_limit)
+        o.field_h = float(field_h)
+        o.field_axis = int(field_axis)
         g = ddqmc_guide()
         g.kind = int(guide_kind)
         g.p = float(guide_p)

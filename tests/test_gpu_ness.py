@@ -52,3 +52,22 @@ def test_ness_3x3_paper_couplings(ddqmc, golden_dir):
     """3x3 periodic with the couplings of the paper's 3x3 figure (0.225, 0.335, 0.25)
     as Pauli couplings, gamma = 1, dt = 0.005, N_w target 10^4, 4 x 10^4 steps."""
     _check(ddqmc, W.C2W, "ness_3x3_periodic_weak.json", W.C2W["steps"], golden_dir)
+
+
+@pytest.mark.parametrize("axis,golden", [(0, "ness_2x2_open_field_x.json"), (1, "ness_2x2_open_field_y.json")])
+def test_ness_2x2_in_plane_field(ddqmc, golden_dir, axis, golden):
+    """2x2 open with the in-plane field h = 0.3 along x or y (Sec. V.B): the
+    field breaks the parity, so sigma^x and sigma^y no longer vanish; M_x, M_y
+    and M_z within 3.5 blocked errors of the exact steady state."""
+    g = json.load(open(os.path.join(golden_dir, golden)))
+    cfg = dict(W.C1, field_h=0.3, field_axis=axis)
+    args, kw = W.run_kwargs(cfg)
+    run = ddqmc.Run(*args, **kw)
+    run.step(W.C1["steps"])
+    e = run.estimates()
+    assert e.n_samples > W.C1["steps"] // 2
+    for name, val, err, ref in (("mz", e.mz, e.mz_err, g["mz"]), ("mx", e.mx, e.mx_err, np.mean(g["x"])),
+                                ("my", e.my, e.my_err, np.mean(g["y"]))):
+        assert abs(val - ref) < 3.5 * err, (name, val, err, ref)
+    assert abs(np.mean(g["y"] if axis == 0 else g["x"])) > 0.2      # a sizeable in-plane moment
+

@@ -73,6 +73,12 @@ VARIANTS = [
     ("C2", dict(guide_kind=2, guide_p=0.7, n_a=2, dt=0.01, control=1, target=20000)),  # site product
     ("C1", dict(dt=0.05, shift0=25.0, n0=20000, target=10 ** 12)),               # |p_death| > 1
     ("C2", dict(Jx=0.3, Jy=-1.2, Jz=-0.7, gamma=0.6, n_a=1, seed=99, control=1, target=20000)),
+    # in-plane field (Sec. V.B): single-site flips, along x and along y, with each guide
+    ("C1", dict(field_h=0.3, field_axis=0)),
+    ("C2", dict(field_h=-0.25, field_axis=1, guide_kind=2, guide_p=0.7, n_a=2, dt=0.01, control=1, target=20000)),
+    ("C2", dict(field_h=0.4, field_axis=0, guide_kind=1, guide_p=1.5, dt=0.01, control=1, target=20000)),
+    ("C3", dict(field_h=0.1, field_axis=0, target=30000)),
+    ("C3", dict(field_h=-0.2, field_axis=1, target=30000, n0=5000)),
 ]
 
 
@@ -87,13 +93,15 @@ def test_variants_bitexact(ddqmc, base, over):
         _same(gpu, cpu, t)
 
 
-def test_site_dependent_guide_bitexact(ddqmc):
+@pytest.mark.parametrize("field", [0.0, 0.3])
+def test_site_dependent_guide_bitexact(ddqmc, field):
     """Site-product guide with a different ratio on every site: every bond has
     its own rate table, so every configuration takes the warp-per-configuration
-    path with the group-ordered cumulative table."""
+    path with the group-ordered cumulative table (with and without the field's
+    site flips)."""
     r = [0.35 + 0.07 * k for k in range(9)]
     args = (3, 3, 1, 0.9, 1.0, 1.0, 1.0, 0.01, 20000)
-    kw = dict(n_a=2, control=1, seed=5, guide_kind=2, site_ratio=r)
+    kw = dict(n_a=2, control=1, seed=5, guide_kind=2, site_ratio=r, field_h=field, field_axis=1)
     gpu = ddqmc.Run(*args, **kw)
     cpu = O.OracleRun(*args, **kw)
     for t in range(120):
@@ -135,6 +143,7 @@ TWO_WORD = [
     (6, 6, 1, 1.1, {}),
     (6, 6, 1, 0.9, dict(guide_kind=2, site_ratio=[0.4 + 0.01 * k for k in range(36)])),
     (8, 8, 1, 0.9, {}),
+    (6, 6, 1, 0.9, dict(field_h=0.2, field_axis=1)),
 ]
 
 
