@@ -344,7 +344,12 @@ void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(in
     T *sp1 = reinterpret_cast<T *>(r->Sp[1]);
     const size_t rx_smem = sizeof(RadixShared<T>);
     mark(0, 0);
-    k_spawn_death<T><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(r->dP, r->dS, Lc, sp0, r->rcap);
+    if (P.field_on)
+        k_spawn_death<T, true><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(r->dP, r->dS, Lc, sp0,
+                                                                                          r->rcap);
+    else
+        k_spawn_death<T, false><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(r->dP, r->dS, Lc, sp0,
+                                                                                           r->rcap);
     mark(0, 1);
     mark(1, 0);
     for (int p = 0; p < P.npass; ++p)
@@ -655,26 +660,32 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     if (sms < 1) sms = 1;
     if (o.sm_limit > 0 && o.sm_limit < sms) sms = o.sm_limit;
     r->packed = 2 * r->hp.N <= 32;
-    bool ok = cudaFuncSetAttribute(k_spawn_death<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_spawn_death<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPP_SMEM) == cudaSuccess;
+    bool ok = true;
+    for (int f = 0; f < 2; ++f) {
+        const void *fr = f ? (const void *)k_spawn_death<Rec, true> : (const void *)k_spawn_death<Rec, false>;
+        const void *fp = f ? (const void *)k_spawn_death<uint64_t, true> : (const void *)k_spawn_death<uint64_t, false>;
+        const void *fw = f ? (const void *)k_spawn_death<RecW, true> : (const void *)k_spawn_death<RecW, false>;
+        ok = ok && cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
+        ok = ok && cudaFuncSetAttribute(fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPP_SMEM) == cudaSuccess;
+        ok = ok && cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPW_SMEM) == cudaSuccess;
+    }
     ok = ok && cudaFuncSetAttribute(k_radix_pass<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_radix_pass<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RXP_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_merge<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_merge<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MGP_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_spawn_death<RecW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPW_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_radix_pass<RecW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RXW_SMEM) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(k_merge<RecW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MGW_SMEM) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
     if (r->packed) {
-        r->g_spawn = occupancy_grid((const void *)k_spawn_death<uint64_t>, SP_TPB, SPP_SMEM, sms);
+        r->g_spawn = occupancy_grid((const void *)k_spawn_death<uint64_t, false>, SP_TPB, SPP_SMEM, sms);
         r->g_radix = occupancy_grid((const void *)k_radix_pass<uint64_t>, RX_TPB, RXP_SMEM, sms);
         r->g_merge = occupancy_grid((const void *)k_merge<uint64_t>, MG_TPB, MGP_SMEM, sms);
     } else if (r->wide) {
-        r->g_spawn = occupancy_grid((const void *)k_spawn_death<RecW>, SP_TPB, SPW_SMEM, sms);
+        r->g_spawn = occupancy_grid((const void *)k_spawn_death<RecW, false>, SP_TPB, SPW_SMEM, sms);
         r->g_radix = occupancy_grid((const void *)k_radix_pass<RecW>, RX_TPB, RXW_SMEM, sms);
         r->g_merge = occupancy_grid((const void *)k_merge<RecW>, MG_TPB, MGW_SMEM, sms);
     } else {
-        r->g_spawn = occupancy_grid((const void *)k_spawn_death<Rec>, SP_TPB, SP_SMEM, sms);
+        r->g_spawn = occupancy_grid((const void *)k_spawn_death<Rec, false>, SP_TPB, SP_SMEM, sms);
         r->g_radix = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
         r->g_merge = occupancy_grid((const void *)k_merge<Rec>, MG_TPB, MG_SMEM, sms);
     }

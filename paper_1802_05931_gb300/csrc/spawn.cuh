@@ -534,7 +534,7 @@ __device__ __forceinline__ uint32_t attempt_word(uint4 x0, uint4 &xb, uint32_t &
 // Resolve the first n queued spawn draws of the warp, one per lane: the move
 // (ket, bra or jump segment, then the group and the bond inside it), the child
 // configuration and its signed unit, appended as a spawn record.
-template <typename T, typename MT, typename SW>
+template <typename T, typename MT, typename SW, bool FIELD>
 __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c, int warp, int lane, int n, int N,
                                             T *out, int64_t cap, DevState *st, int npass) {
     if (lane < n) {
@@ -563,7 +563,7 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
             const int gsg = ket ? -hs : hs;
             if (ket) ci ^= m; else cj ^= m;
             if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
-        } else if (v - qTket - qTbra < 2 * q.Tf[o]) {
+        } else if (FIELD && v - qTket - qTbra < 2 * q.Tf[o]) {
             // field flip: ket segment, then bra segment; groups by importance class
             const uint64_t qTf = q.Tf[o];
             const uint32_t fcp = q.fc[o];
@@ -600,7 +600,7 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
             }
         } else {
             // jumps share one rate: the site index is the quotient by it
-            const uint64_t vj = v - qTket - qTbra - 2 * q.Tf[o];
+            const uint64_t vj = v - qTket - qTbra - (FIELD ? 2 * q.Tf[o] : 0ull);
             uint32_t idx;
             if (qT <= 0xFFFFFFFFull) {
                 idx = (uint32_t)((float)(uint32_t)vj * s.jinv);
@@ -620,7 +620,9 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
     __syncwarp();
 }
 
-template <typename T>
+// FIELD: the run has the in-plane field's site flips (a separate instantiation
+// keeps them out of the runs without).
+template <typename T, bool FIELD>
 __global__ void __launch_bounds__(SP_TPB, 3)
 k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typename ListOf<T>::type *__restrict__ L,
               T *__restrict__ out, int64_t cap) {
@@ -715,7 +717,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             }
             uint64_t Tf = 0;
             uint32_t fcp = 0;
-            if (P.field_on) {
+            if constexpr (FIELD) {
                 SW fm[4];
                 field_masks<SW>(c, i32, j32, fm);
 #pragma unroll
@@ -734,8 +736,10 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             q.Tket[lane] = Tket;
             q.Tbra[lane] = Tbra;
             q.T[lane] = Tall;
-            q.Tf[lane] = Tf;
-            q.fc[lane] = fcp;
+            if constexpr (FIELD) {
+                q.Tf[lane] = Tf;
+                q.fc[lane] = fcp;
+            }
             q.gk[lane] = gkp;
             q.gb[lane] = gbp;
             q.natt[lane] = natt == 0 ? 1u : (uint32_t)natt;
@@ -846,7 +850,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 while (qn >= 32 || (fin && qn > 0)) {
                     __syncwarp();
                     const int nd = qn < 32 ? qn : 32;
-                    spawn_drain<T, MT, SW>(s, c, warp, lane, nd, N, out, cap, st, npass);
+                    spawn_drain<T, MT, SW, FIELD>(s, c, warp, lane, nd, N, out, cap, st, npass);
                     qn -= nd;
                     // move the rest of the queue to the front
                     uint64_t rv = 0;
@@ -914,7 +918,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                         }
                     }
                 }
-                if (P.field_on) {
+                if (FIELD) {
                     // field flips: ket then bra, groups by importance class, sites in order
                     for (int seg = 0; seg < 2; ++seg) {
                         int gq[2];

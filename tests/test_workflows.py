@@ -1,0 +1,47 @@
+"""Host-side combination of runs: weighted line fits (against numpy's weighted
+polyfit), the initiator extrapolation, the susceptibility tensor from
+magnetisations and its angular average (against the complete elliptic
+integral for a diagonal tensor)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1802_05931_gb300 import workflows as WF
+
+
+def test_weighted_line_matches_polyfit():
+    rng = np.random.default_rng(1)
+    x = np.array([0.0, 1.0, 2.5, 4.0, 7.0])
+    err = rng.uniform(0.1, 0.5, size=5)
+    y = 0.3 - 1.7 * x + rng.normal(0, err)
+    a, sa, b, sb = WF.weighted_line(x, y, err)
+    (pb, pa), cov = np.polyfit(x, y, 1, w=1 / err, cov="unscaled")
+    assert a == pytest.approx(pa, rel=1e-12) and b == pytest.approx(pb, rel=1e-12)
+    assert sa == pytest.approx(math.sqrt(cov[1, 1]), rel=1e-10)
+    assert sb == pytest.approx(math.sqrt(cov[0, 0]), rel=1e-10)
+
+
+def test_initiator_extrapolation_uses_the_lowest_thresholds():
+    vals = {3: (0.5 + 0.01 * 3, 0.01), 6: (0.5 + 0.01 * 6, 0.01), 10: (0.5 + 0.01 * 10, 0.02),
+            40: (9.0, 0.01)}                      # far outlier, not among the three lowest
+    v, e = WF.initiator_extrapolation(vals)
+    assert v == pytest.approx(0.5, abs=1e-12) and e > 0
+
+
+def test_susceptibility_tensor_from_linear_magnetisation():
+    chi = np.array([[0.2, -3.8], [3.4, 2.7]])
+
+    def mag(axis, h):
+        m = chi[:, axis] * h
+        return m[0], 0.01, m[1], 0.01
+    got, err = WF.susceptibility_tensor(mag, [0.0, 0.02, 0.04])
+    assert np.allclose(got, chi, atol=1e-12) and np.all(err > 0)
+
+
+def test_angular_average_of_diagonal_tensor_is_an_elliptic_integral():
+    scipy_special = pytest.importorskip("scipy.special")
+    a, b = 3.0, 1.2
+    ref = (2 / math.pi) * a * scipy_special.ellipe(1 - (b / a) ** 2)
+    assert WF.angular_average(np.diag([a, b])) == pytest.approx(ref, rel=1e-6)
+    assert WF.angular_average(2.5 * np.eye(2)) == pytest.approx(2.5, rel=1e-12)
