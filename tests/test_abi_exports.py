@@ -47,6 +47,27 @@ def test_strerror_and_options_need_no_gpu():
     assert o.seed == 1 and o.damping == 0.05 and o.shift0 == -1.0 and o.n0 == 1000
 
 
+def test_option_defaults_and_parameter_checks_need_no_gpu():
+    """Defaults of the newer option fields, and parameters that ddqmc_create
+    rejects before touching the device."""
+    from paper_1802_05931_gb300 import build as b, ddqmc
+    b.build()
+    o = ddqmc.ddqmc_default_options()
+    assert o.sm_limit == 0 and o.field_h == 0.0 and o.field_axis == 0
+    lat = ddqmc.ddqmc_lattice(2, 2, 0)
+    for lattice, opt in ((ddqmc.ddqmc_lattice(9, 8, 0), None),          # 72 sites
+                         (ddqmc.ddqmc_lattice(2, 2, 1), None),          # L = 2 periodic
+                         (lat, dict(field_axis=2)),                     # no such axis
+                         (lat, dict(field_h=float("nan"))),
+                         (lat, dict(control=3))):
+        oo = ddqmc.ddqmc_default_options()
+        for k, v in (opt or {}).items():
+            setattr(oo, k, v)
+        with pytest.raises(ddqmc.DDQMCError) as e:
+            ddqmc.ddqmc_create(lattice, 0.9, 1.0, 1.0, 1.0, 0.01, 100, 0, None, oo)
+        assert e.value.code == -1
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     from paper_1802_05931_gb300 import ddqmc
     with pytest.raises(RuntimeError):
