@@ -350,8 +350,8 @@ def gpu_arm(args, world, rank, local, pg):
         for _ in range(args.e2e_steps):
             run.import_(ket, bra, re, im, *state)
             h2d += 16 * len(ket)
-            e_ws += int(np.abs(re, dtype=np.int64).sum() + np.abs(im, dtype=np.int64).sum())
             run.step(1)
+            e_ws += ddqmc.ddqmc_get_totals(run.h)["walker_steps"]     # import resets the totals
             ket, bra, re, im = run.export()
             est = run.raw_estimates()
             d2h += 16 * len(ket) + 8 * len(est)

@@ -143,7 +143,11 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz,
 /* Advance nsteps DDQMC steps (Sec. III.C, one step = spawn + death/clone,
  * annihilation under the initiator rule, estimators, shift update), issued
  * on the run's stream; waits for completion and returns the sticky device
- * status.  nsteps = 0 only reports the status. */
+ * status.  nsteps = 0 only reports the status.  Whole blocks of 32 steps are
+ * replayed from a CUDA graph that the first such block captures on the run's
+ * stream (one graph per starting list buffer; plain launches while
+ * per-kernel timing is on, or if the stream cannot be captured); the results
+ * are the same either way. */
 int ddqmc_step(ddqmc_run *run, int64_t nsteps);
 
 /* Same as ddqmc_step but does not wait: returns after enqueueing the work;

@@ -19,7 +19,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 def nvcc_command(out):
     return ["nvcc", "-std=c++17", "-O3", ARCH, "-lineinfo", "--fmad=false",
-            "-Xcompiler", "-fPIC,-ffp-contract=off", "-shared", "-cudart", "static",
+            "-Xcompiler", "-fPIC,-ffp-contract=off", "-shared", "-cudart", "static", "-lpthread",
             "-o", out] + [os.path.join(CSRC, s) for s in SOURCES]
 
 

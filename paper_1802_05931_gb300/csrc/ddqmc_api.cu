@@ -11,6 +11,7 @@
 #include <cstring>
 #include <functional>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/ddqmc.h"
@@ -307,6 +308,26 @@ int read_status(ddqmc_run *r) {
     }
     r->host_status = status_code(st);
     return r->host_status;
+}
+
+// Host loops over list entries (import / export conversion) split over the
+// host's cores; f(begin, end) handles one contiguous range.
+template <typename F>
+void parallel_for(int64_t n, const F &f) {
+    const int64_t grain = 1 << 20;
+    unsigned hw = std::thread::hardware_concurrency();
+    int64_t nt = (n + grain - 1) / grain;
+    if (nt > (int64_t)(hw ? hw : 1)) nt = hw ? hw : 1;
+    if (nt > 32) nt = 32;
+    if (nt <= 1) { f((int64_t)0, n); return; }
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + nt - 1) / nt;
+    for (int64_t t = 1; t < nt; ++t) {
+        const int64_t b = t * chunk, e = b + chunk < n ? b + chunk : n;
+        if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
+    }
+    f((int64_t)0, chunk < n ? chunk : n);
+    for (auto &x : th) x.join();
 }
 
 // Pinned host staging of at least `bytes` bytes (grown on demand, never shrunk).
@@ -994,22 +1015,26 @@ int ddqmc_export_walkers(ddqmc_run *r, uint64_t *ket, uint64_t *bra, int32_t *re
         rc = DDQMC_ERR_CUDA;
     } else if (r->wide) {
         const RecW *h = reinterpret_cast<const RecW *>(hb);
-        for (int64_t q = 0; q < m; ++q) {
-            ket[q] = h[q].lo;
-            bra[q] = h[q].hi;
-            re[q] = h[q].re;
-            im[q] = h[q].im;
-        }
+        parallel_for(m, [&](int64_t b, int64_t e) {
+            for (int64_t q = b; q < e; ++q) {
+                ket[q] = h[q].lo;
+                bra[q] = h[q].hi;
+                re[q] = h[q].re;
+                im[q] = h[q].im;
+            }
+        });
     } else {
         const Rec *h = reinterpret_cast<const Rec *>(hb);
         const int N = r->hp.N;
         const uint64_t mask = r->hp.nmask;
-        for (int64_t q = 0; q < m; ++q) {
-            ket[q] = h[q].key & mask;
-            bra[q] = h[q].key >> N;
-            re[q] = h[q].re;
-            im[q] = h[q].im;
-        }
+        parallel_for(m, [&](int64_t b, int64_t e) {
+            for (int64_t q = b; q < e; ++q) {
+                ket[q] = h[q].key & mask;
+                bra[q] = h[q].key >> N;
+                re[q] = h[q].re;
+                im[q] = h[q].im;
+            }
+        });
     }
     return rc;
 }
@@ -1027,21 +1052,41 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
     unsigned char *hb = n > 0 ? host_stage(r, lsize * (size_t)n) : nullptr;
     if (n > 0 && !hb) return DDQMC_ERR_OOM;
-    for (int64_t q = 0; q < n; ++q) {
-        const bool bad = (ket[q] & ~mask) || (bra[q] & ~mask) || (re[q] == 0 && im[q] == 0) ||
-                         (q > 0 && (bra[q - 1] > bra[q] || (bra[q - 1] == bra[q] && ket[q - 1] >= ket[q])));
-        if (bad) return DDQMC_ERR_INVALID_ARG;
-        if (r->wide) {
-            RecW &h = reinterpret_cast<RecW *>(hb)[q];
-            h.lo = ket[q];
-            h.hi = bra[q];
-            h.re = re[q];
-            h.im = im[q];
-        } else {
-            Rec &h = reinterpret_cast<Rec *>(hb)[q];
-            h.key = (bra[q] << N) | ket[q];
-            h.re = re[q];
-            h.im = im[q];
+    // check and convert in parallel ranges; any bad entry rejects the whole list
+    int64_t W = 0;
+    {
+        const int64_t grain = 1 << 20;
+        const int64_t nr = n > 0 ? (n + grain - 1) / grain : 0;
+        std::vector<int64_t> rw(nr > 0 ? nr : 1, 0);
+        std::vector<char> rb(nr > 0 ? nr : 1, 0);
+        parallel_for(nr, [&](int64_t b, int64_t e) {
+            for (int64_t g = b; g < e; ++g) {
+                const int64_t q0 = g * grain, q1 = q0 + grain < n ? q0 + grain : n;
+                int64_t acc = 0;
+                for (int64_t q = q0; q < q1; ++q) {
+                    const bool bad = (ket[q] & ~mask) || (bra[q] & ~mask) || (re[q] == 0 && im[q] == 0) ||
+                                     (q > 0 && (bra[q - 1] > bra[q] || (bra[q - 1] == bra[q] && ket[q - 1] >= ket[q])));
+                    if (bad) { rb[g] = 1; break; }
+                    acc += (int64_t)std::llabs(re[q]) + (int64_t)std::llabs(im[q]);
+                    if (r->wide) {
+                        RecW &h = reinterpret_cast<RecW *>(hb)[q];
+                        h.lo = ket[q];
+                        h.hi = bra[q];
+                        h.re = re[q];
+                        h.im = im[q];
+                    } else {
+                        Rec &h = reinterpret_cast<Rec *>(hb)[q];
+                        h.key = (bra[q] << N) | ket[q];
+                        h.re = re[q];
+                        h.im = im[q];
+                    }
+                }
+                rw[g] = acc;
+            }
+        });
+        for (int64_t g = 0; g < nr; ++g) {
+            if (rb[g]) return DDQMC_ERR_INVALID_ARG;
+            W += rw[g];
         }
     }
     // make sure no earlier work of this run is in flight before rewriting its
@@ -1063,8 +1108,6 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     hs.t_var = t_var;
     hs.t_eq = t_eq;
     hs.M = n;
-    int64_t W = 0;
-    for (int64_t q = 0; q < n; ++q) W += (int64_t)std::llabs(re[q]) + (int64_t)std::llabs(im[q]);
     hs.W_cur = W;
     hs.epoch = (old_epoch + 16u) & 0x3FFFFFFFu;
     host_death_table(r->hp, S, hs);
