@@ -276,16 +276,22 @@ def gpu_arm(args, world, rank, local, pg):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # one event between steps: per-step durations for the median / p99 (the
+    # total runs from the first event to the last, host gaps included)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps - 1)]
     # the profiler range marks the timed steps for ncu --profile-from-start off
     torch.cuda.profiler.start()
     e0.record(stream)
-    run.step(args.steps)
-    e1.record(stream)
+    for k in range(args.steps):
+        run.step(1)
+        (evs[k] if k < args.steps - 1 else e1).record(stream)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     barrier(pg)
     clocks = sampler.stop() if sampler else None
     ms = e0.elapsed_time(e1)
+    marks = [e0] + evs + [e1]
+    step_ms = sorted(marks[k].elapsed_time(marks[k + 1]) for k in range(args.steps))
     tot1 = ddqmc.ddqmc_get_totals(run.h)
     timing = ddqmc.ddqmc_get_timing(run.h)
     ddqmc.ddqmc_set_timing(run.h, 0)
@@ -395,6 +401,9 @@ def gpu_arm(args, world, rank, local, pg):
             "sort_merge": {"ms_per_step": sortmerge_ms, "alg_bytes_per_step": sortmerge_bytes,
                            "achieved_gbs": sortmerge_bytes / (sortmerge_ms / 1e3) / 1e9,
                            "frac": sortmerge_bytes / (sortmerge_ms / 1e3) / 1e9 / peak},
+            "step_ms": {"median": statistics.median(step_ms), "p99": step_ms[min(len(step_ms) - 1,
+                                                                                   int(0.99 * len(step_ms)))],
+                        "min": step_ms[0], "max": step_ms[-1]},
             "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(sum(v[1] for v in timing.values())), "clocks": clocks}
     print(json.dumps(line), flush=True)
