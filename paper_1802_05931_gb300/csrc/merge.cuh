@@ -282,8 +282,12 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     return v;
 }
 
+// resident blocks per SM the merge is compiled for: 128-bit keys need more registers
+template <typename T> struct MergeBlocks { static constexpr int value = 4; };
+template <> struct MergeBlocks<RecW> { static constexpr int value = 3; };
+
 template <typename T>
-__global__ void __launch_bounds__(MG_TPB, 4)
+__global__ void __launch_bounds__(MG_TPB, MergeBlocks<T>::value)
 k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__restrict__ L, const T *__restrict__ S,
         typename ListOf<T>::type *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
         const int64_t *__restrict__ rem_end, uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
