@@ -263,6 +263,16 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
                              const void *d_list, int64_t m, const void *d_spawns, int64_t nsp,
                              void *d_out, int64_t out_cap, int64_t *m_out, void *cuda_stream);
 
+/* Failure-path check of the device waits (no counterpart in the paper: a
+ * property of this library).  Every spin of a kernel on a status word written
+ * by another block is bounded; when the bound runs out the kernel records a
+ * timeout in the device status and returns, so the context stays usable and
+ * the host call returns DDQMC_ERR_TIMEOUT.  This call spins one thread on a
+ * word that nothing ever sets (about a second on a GB300) and returns what
+ * the host sees: DDQMC_ERR_TIMEOUT when the bound works, CUDA on a launch or
+ * copy error.  cuda_stream: stream to issue on (NULL: the default stream). */
+int ddqmc_wait_selftest(void *cuda_stream);
+
 /* Free every resource of the run (NULL is ignored). */
 void ddqmc_destroy(ddqmc_run *run);
 

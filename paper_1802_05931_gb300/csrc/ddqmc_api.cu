@@ -1224,6 +1224,31 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
     return status_code(status);
 }
 
+// A look-back word that nothing ever publishes, and the status its bounded
+// wait reports: the failure path of every device wait, exercised on purpose.
+static __device__ uint64_t g_wait_word;
+static __device__ uint32_t g_wait_status;
+
+static __global__ void k_wait_selftest(uint32_t epoch) {
+    if (threadIdx.x == 0) {
+        g_wait_status = 0u;
+        lb_wait(&g_wait_word, epoch, &g_wait_status);
+    }
+}
+
+int ddqmc_wait_selftest(void *cuda_stream) {
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    uint32_t st = 0;
+    k_wait_selftest<<<1, 32, 0, stream>>>(12345u);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyFromSymbolAsync(&st, g_wait_status, sizeof(st), 0, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    return status_code(st);
+}
+
 void ddqmc_destroy(ddqmc_run *r) {
     if (!r) return;
     if (r->stream) cudaStreamSynchronize(r->stream);

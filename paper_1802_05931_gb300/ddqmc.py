@@ -70,7 +70,7 @@ EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_as
            "ddqmc_estimators", "ddqmc_raw_estimators", "ddqmc_blocking_moments",
            "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_get_state", "ddqmc_get_counts",
            "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_annihilate",
-           "ddqmc_annihilate_noalloc", "ddqmc_destroy", "ddqmc_strerror"]
+           "ddqmc_annihilate_noalloc", "ddqmc_wait_selftest", "ddqmc_destroy", "ddqmc_strerror"]
 NOALLOC_MAX_SPAWNS = 1 << 18
 NOALLOC_MAX_LIST = 1 << 20
 KERNEL_CLASSES = ["spawn_death", "radix_pass", "merge_partition", "merge", "finalize"]
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
     lib.ddqmc_get_timing.argtypes = [vp, P(dbl), P(i64), i32]
     lib.ddqmc_annihilate.argtypes = [vp, vp, i64, vp, i64, vp, i64, P(i64)]
     lib.ddqmc_annihilate_noalloc.argtypes = [P(ddqmc_lattice), i32, vp, i64, vp, i64, vp, i64, P(i64), vp]
+    lib.ddqmc_wait_selftest.argtypes = [vp]
     lib.ddqmc_destroy.argtypes = [vp]
     lib.ddqmc_destroy.restype = None
     lib.ddqmc_strerror.argtypes = [C.c_int]
@@ -237,6 +238,11 @@ def ddqmc_get_timing(run):
     _check(load().ddqmc_get_timing(run, _p(ms, C.c_double), _p(n, C.c_int64), len(KERNEL_CLASSES)),
            "ddqmc_get_timing")
     return {k: (float(ms[q]), int(n[q])) for q, k in enumerate(KERNEL_CLASSES)}
+
+
+def ddqmc_wait_selftest(stream=None):
+    """Status code of a device wait on a word nothing sets (DDQMC_ERR_TIMEOUT = -5 expected)."""
+    return load().ddqmc_wait_selftest(stream)
 
 
 def ddqmc_annihilate(run, d_list, m, d_spawns, nsp, d_out, out_cap):

@@ -109,3 +109,22 @@ def test_request_larger_than_budget_is_refused():
 def test_percentile():
     assert S.percentile([3, 1, 2], 0.5) == 2
     assert S.percentile([1, 2, 3, 4], 0.99) == pytest.approx(3.97)
+
+
+class FailingRun(FakeRun):
+    """A run whose device reports a capacity error after a few chunks."""
+
+    def sync(self):
+        if self.t > 64:
+            from paper_1802_05931_gb300 import ddqmc
+            raise ddqmc.DDQMCError(-3, "ddqmc_sync")
+
+
+def test_failed_run_is_retired_with_its_error_and_frees_memory():
+    clock = FakeClock()
+    srv = S.NessServer(10 ** 12, max_active=2, chunk=32, make_run=FailingRun, clock=clock)
+    a = srv.submit(_req(tol=1e-9, max_steps=1000))
+    srv.run_until_idle()
+    r = srv.results[a]
+    assert r.error == -3 and not r.converged and math.isnan(r.mz)
+    assert srv.bytes_in_use == 0 and FakeRun.live == 0
