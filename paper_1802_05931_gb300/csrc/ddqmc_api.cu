@@ -11,6 +11,7 @@
 #include <cstring>
 #include <functional>
 #include <new>
+#include <nvtx3/nvToolsExt.h>
 #include <thread>
 #include <vector>
 
@@ -395,6 +396,8 @@ enum { KC_SPAWN = 0, KC_RADIX = 1, KC_PARTITION = 2, KC_MERGE = 3, KC_FINALIZE =
 constexpr int64_t GRAPH_STEPS = 32;
 
 void launch_one_step(ddqmc_run *r, const std::function<void(int, int)> &mark) {
+    // one NVTX range per issued step (free without an attached tool)
+    nvtxRangePushA("ddqmc step");
     void *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
     if (r->packed) launch_step<uint64_t>(r, Lc, Ln, mark);
     else if (r->wide) launch_step<RecW>(r, Lc, Ln, mark);
@@ -402,6 +405,7 @@ void launch_one_step(ddqmc_run *r, const std::function<void(int, int)> &mark) {
     mark(KC_FINALIZE, 0);
     k_finalize<<<1, FN_TPB, 0, r->stream>>>(r->dP, r->dS, r->dBlk);
     mark(KC_FINALIZE, 1);
+    nvtxRangePop();
     r->cur ^= 1;
 }
 

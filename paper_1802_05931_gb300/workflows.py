@@ -86,3 +86,27 @@ def run_magnetisation(make_run: Callable[..., object], steps: int, axis: int, h:
     mx = initiator_extrapolation({k: (v[0], v[1]) for k, v in per.items()})
     my = initiator_extrapolation({k: (v[2], v[3]) for k, v in per.items()})
     return mx[0], mx[1], my[0], my[1]
+
+
+def trace_run(run, steps: int, every: int = 1) -> List[dict]:
+    """Per-step record of a run, every `every` steps: t, shift S, trace of
+    Re rho, N_w, total walkers W, occupied configurations M and the spawn
+    records of the last step (the quantities of Sec. III.C's population
+    control).  Returns one dict per record."""
+    rows = []
+    for _ in range(0, steps, every):
+        run.step(every)
+        st = run.state()
+        est = run.raw_estimates()
+        rec = run.counts()[0]
+        rows.append(dict(t=int(st.t), shift=float(st.shift), trace=int(est[0]), nw=int(est[2]),
+                         walkers=int(est[3]), entries=int(est[4]), spawn_records=int(rec)))
+    return rows
+
+
+def rows_to_csv(rows: List[dict]) -> str:
+    """The records of trace_run as CSV text (header line first)."""
+    if not rows:
+        return ""
+    keys = list(rows[0])
+    return "\n".join([",".join(keys)] + [",".join(str(r[k]) for k in keys) for r in rows]) + "\n"

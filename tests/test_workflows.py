@@ -45,3 +45,29 @@ def test_angular_average_of_diagonal_tensor_is_an_elliptic_integral():
     ref = (2 / math.pi) * a * scipy_special.ellipe(1 - (b / a) ** 2)
     assert WF.angular_average(np.diag([a, b])) == pytest.approx(ref, rel=1e-6)
     assert WF.angular_average(2.5 * np.eye(2)) == pytest.approx(2.5, rel=1e-12)
+
+
+def test_trace_run_records_every_interval():
+    import types
+
+    class Fake:
+        def __init__(self):
+            self.t = 0
+
+        def step(self, n):
+            self.t += n
+
+        def state(self):
+            return types.SimpleNamespace(t=self.t, shift=0.5 * self.t)
+
+        def raw_estimates(self):
+            return [self.t, 0, 2 * self.t, 3 * self.t, 4 * self.t]
+
+        def counts(self):
+            return (5 * self.t, 0, 0)
+
+    rows = WF.trace_run(Fake(), 10, every=5)
+    assert [r["t"] for r in rows] == [5, 10]
+    assert rows[1] == dict(t=10, shift=5.0, trace=10, nw=20, walkers=30, entries=40, spawn_records=50)
+    csv = WF.rows_to_csv(rows).splitlines()
+    assert csv[0] == "t,shift,trace,nw,walkers,entries,spawn_records" and csv[2].startswith("10,5.0,")
