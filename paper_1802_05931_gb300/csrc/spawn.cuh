@@ -10,12 +10,16 @@
 // binomial + multinomial scheme of Sec. III.B.
 //
 // Moves, in order: ket bond flips (child (i ^ m_b, j), A = -i h_b(i)), bra
-// bond flips (child (i, j ^ m_b), A = +i h_b(j)), jumps (child (i - 2^k,
-// j - 2^k), A = gamma, needs spin k up on both sides).  Inside a bond-flip
-// segment the moves are grouped by g = 4*anti + class (anti-aligned bond in
-// the flipped word; importance class of the bond), groups in increasing g and
-// bonds in bond order inside a group.  Rates are fixed-point integers
-// (rate * 2^32, truncated), so the move selection is integer-only.
+// bond flips (child (i, j ^ m_b), A = +i h_b(j)), with the in-plane field of
+// Sec. V.B ket and bra single-site flips (A = -i h / +i h along x, h (2 s_k - 1)
+// along y), then jumps (child (i - 2^k, j - 2^k), A = gamma, needs spin k up
+// on both sides).  Inside a bond-flip segment the moves are grouped by
+// g = 4*anti + class (anti-aligned bond in the flipped word; importance class
+// of the bond), groups in increasing g and bonds in bond order inside a
+// group; site flips are grouped by the importance class of the site, sites in
+// order.  Rates are fixed-point integers (rate * 2^32, truncated), so the
+// move selection is integer-only.  Spin words are 32-bit up to 31 sites and
+// 64-bit up to 64 (then bond masks are 128-bit pairs).
 //
 // Children follow Delta rho_child = A rho_parent (the four sign rules of
 // Sec. III.C); death / clone and the Re <-> Im transfer act on the parent's
