@@ -356,7 +356,10 @@ def gpu_arm(args, world, rank, local, pg):
     # end to end through the C-ABI with host buffers: import, step, export, estimators
     e2e = None
     if args.e2e_steps > 0:
-        ket, bra, re, im = run.export()
+        # host buffers reused from step to step, as a streaming caller would
+        M0 = run.state().entries
+        bufs = tuple(np.empty(int(1.25 * M0) + 1024, dtype=dt) for dt in (np.uint64, np.uint64, np.int32, np.int32))
+        ket, bra, re, im = run.export(out=bufs)
         st = run.state()
         state = (st.t, st.shift, st.variable, st.q_prev, st.t_var, st.t_eq)
         torch.cuda.synchronize()
@@ -368,7 +371,7 @@ def gpu_arm(args, world, rank, local, pg):
             h2d += 16 * len(ket)
             run.step(1)
             e_ws += ddqmc.ddqmc_get_totals(run.h)["walker_steps"]     # import resets the totals
-            ket, bra, re, im = run.export()
+            ket, bra, re, im = run.export(out=bufs)
             est = run.raw_estimates()
             d2h += 16 * len(ket) + 8 * len(est)
             st = run.state()

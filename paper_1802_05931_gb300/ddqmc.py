@@ -185,15 +185,21 @@ def ddqmc_blocking_moments(run, k, levels=32):
     return [dict(n=int(n[l]), sx=int(sx[l]), sxx=i128(sxx, l), sxy=i128(sxy, l)) for l in range(levels)]
 
 
-def ddqmc_export_walkers(run):
+def ddqmc_export_walkers(run, out=None):
+    """(ket, bra, re, im) of the current list; `out` may hold four arrays of
+    those dtypes to write into (reused when long enough, e.g. between steps)."""
     lib = load()
     n = C.c_int64()
     _check(lib.ddqmc_export_walkers(run, None, None, None, None, 0, C.byref(n)), "ddqmc_export_walkers")
     m = n.value
-    ket = np.zeros(max(m, 1), dtype=np.uint64)
-    bra = np.zeros(max(m, 1), dtype=np.uint64)
-    re = np.zeros(max(m, 1), dtype=np.int32)
-    im = np.zeros(max(m, 1), dtype=np.int32)
+    if out is not None and all(len(a) >= m and a.flags.c_contiguous for a in out) and \
+            [a.dtype for a in out] == [np.uint64, np.uint64, np.int32, np.int32]:
+        ket, bra, re, im = out
+    else:
+        ket = np.empty(max(m, 1), dtype=np.uint64)
+        bra = np.empty(max(m, 1), dtype=np.uint64)
+        re = np.empty(max(m, 1), dtype=np.int32)
+        im = np.empty(max(m, 1), dtype=np.int32)
     _check(lib.ddqmc_export_walkers(run, _p(ket, C.c_uint64), _p(bra, C.c_uint64), _p(re, C.c_int32),
                                     _p(im, C.c_int32), m, C.byref(n)), "ddqmc_export_walkers")
     return ket[:m], bra[:m], re[:m], im[:m]
@@ -333,8 +339,8 @@ class Run:
     def raw_estimates(self):
         return ddqmc_raw_estimators(self.h)
 
-    def export(self):
-        return ddqmc_export_walkers(self.h)
+    def export(self, out=None):
+        return ddqmc_export_walkers(self.h, out)
 
     def import_(self, ket, bra, re, im, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-1):
         ddqmc_import_walkers(self.h, ket, bra, re, im, t, S, variable, q_prev, t_var, t_eq)

@@ -273,3 +273,20 @@ def test_invalid_arguments_rejected(ddqmc):
     run = ddqmc.Run(2, 2, 0, 0.9, 1.0, 1.0, 1.0, 0.01, 100)
     with pytest.raises(ddqmc.DDQMCError):
         run.import_([1, 0], [0, 0], [1, 1], [0, 0], 0, 0.0)      # not in canonical order
+
+
+def test_export_into_reused_buffers(ddqmc):
+    """export(out=...) writes into caller buffers that are long enough and
+    gives the same list as a fresh export; short buffers are not used."""
+    args, kw = W.run_kwargs(W.C1)
+    run = ddqmc.Run(*args, **kw)
+    run.step(200)
+    ref = run.export()
+    m = len(ref[0])
+    bufs = tuple(np.full(m + 7, 99, dtype=dt) for dt in (np.uint64, np.uint64, np.int32, np.int32))
+    got = run.export(out=bufs)
+    for a, b, buf in zip(ref, got, bufs):
+        assert np.array_equal(a, b) and np.shares_memory(b, buf)
+    short = tuple(np.zeros(1, dtype=dt) for dt in (np.uint64, np.uint64, np.int32, np.int32))
+    got2 = run.export(out=short)
+    assert all(np.array_equal(a, b) for a, b in zip(ref, got2)) and len(got2[0]) == m
