@@ -57,6 +57,10 @@ def parse():
                          "6x6 and 8x8 use two-word keys)")
     ap.add_argument("--capacity-factor", type=float, default=3.2,
                     help="walker-list capacity per target walker (spawn capacity 1.4 times that)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time N runs stepped as one batch against the same runs one at a time and on "
+                         "concurrent streams (walker-steps/s), instead of the single-run benchmark")
+    ap.add_argument("--batch-target", type=float, default=2e5, help="largest per-run target of --batch")
     ap.add_argument("--serve", type=int, default=0,
                     help="instead: this many synthetic NESS-solve requests through the batching server, "
                          "then the same requests one at a time")
@@ -471,10 +475,105 @@ def serve_arm(args):
     return 0
 
 
+def batch_runs(n, target, seed=40):
+    """n runs of one lattice: Jx spread over [0.8, 1.2], targets log-spaced
+    over [target / 8, target] (uneven sizes), total-population control, n_a 3,
+    shift S0 = -3 so that every run reaches its target within the warm-up."""
+    out = []
+    for k in range(n):
+        f = k / max(n - 1, 1)
+        out.append(dict(Jx=0.8 + 0.4 * f, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005,
+                        target=int(target / 8.0 * 8.0 ** ((k * 7 % n) / max(n - 1, 1))), n_a=3, seed=seed + k,
+                        control=1, shift0=-3.0))
+    return out
+
+
+def batch_arm(args):
+    """Walker-steps/s of n runs stepped as one batch (one walker store, one
+    launch of each kernel per step for all runs) against the same runs one
+    after another and on concurrent streams (each on its share of the SMs).
+    Each arm takes its warm-up steps from t = 0, then the timed steps; the
+    runs are identical in every arm, so each arm steps the same walkers."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1802_05931_gb300 import ddqmc
+    torch.cuda.set_device(0)
+    Lx, Ly = (int(x) for x in args.lattice.split("x"))
+    per = 1 if min(Lx, Ly) >= 3 else 0
+    runs = batch_runs(args.batch, args.batch_target)
+    K = max(32, (args.steps * 16 + 31) // 32 * 32)
+    W = max(512, (args.warmup * 64 + 31) // 32 * 32)
+    # room for the population's overshoot of its target while the shift settles
+    cap = dict(capacity_entries=8 * max(r["target"] for r in runs) + 65536,
+               capacity_spawns=16 * max(r["target"] for r in runs) + 65536)
+    res = {}
+    # one batch
+    b = ddqmc.Batch(Lx, Ly, per, runs, capacity_entries=cap["capacity_entries"] * len(runs),
+                    capacity_spawns=cap["capacity_spawns"] * len(runs))
+    b.step(W)
+    w0 = b.totals()["walker_steps"]
+    t0 = time.perf_counter()
+    b.step(K)
+    res["batch"] = (time.perf_counter() - t0, b.totals()["walker_steps"] - w0)
+    b.close()
+    # one after another, each on the whole GPU
+    dt_seq, ws_seq = 0.0, 0
+    for r in runs:
+        kw = {k: v for k, v in r.items() if k not in ("Jx", "Jy", "Jz", "gamma", "dt", "target")}
+        one = ddqmc.Run(Lx, Ly, per, r["Jx"], r["Jy"], r["Jz"], r["gamma"], r["dt"], r["target"], **cap, **kw)
+        one.step(W)
+        w0 = ddqmc.ddqmc_get_totals(one.h)["walker_steps"]
+        t0 = time.perf_counter()
+        one.step(K)
+        dt_seq += time.perf_counter() - t0
+        ws_seq += ddqmc.ddqmc_get_totals(one.h)["walker_steps"] - w0
+        one.close()
+    res["sequential"] = (dt_seq, ws_seq)
+    # concurrent streams, grids sized for a share of the SMs
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    share = max(1, sms // len(runs))
+    many = []
+    for r in runs:
+        kw = {k: v for k, v in r.items() if k not in ("Jx", "Jy", "Jz", "gamma", "dt", "target")}
+        many.append(ddqmc.Run(Lx, Ly, per, r["Jx"], r["Jy"], r["Jz"], r["gamma"], r["dt"], r["target"],
+                              sm_limit=share, **cap, **kw))
+    for m in many:
+        m.step_async(W)
+    for m in many:
+        m.sync()
+    w0 = sum(ddqmc.ddqmc_get_totals(m.h)["walker_steps"] for m in many)
+    t0 = time.perf_counter()
+    for m in many:
+        m.step_async(K)
+    for m in many:
+        m.sync()
+    res["streams"] = (time.perf_counter() - t0, sum(ddqmc.ddqmc_get_totals(m.h)["walker_steps"] for m in many) - w0)
+    for m in many:
+        m.close()
+    rate = {k: v[1] / v[0] for k, v in res.items()}
+    line = {"metric": "walker-steps/s", "value": rate["batch"], "unit": "walker-steps/s", "n_gpus": 1,
+            "steps": K, "warmup": W, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "batch of %d runs, %s %s, Jx in [0.8, 1.2], targets log-spaced in "
+                                   "[%.3g, %.3g] total walkers, n_a 3, dt 0.005" %
+                                   (len(runs), args.lattice, "periodic" if per else "open",
+                                    args.batch_target / 8, args.batch_target),
+                       "timing": "host clock around the timed steps (each call waits for the device)"},
+            "same_walker_steps": res["batch"][1] == res["sequential"][1] == res["streams"][1],
+            "arms": {k: {"seconds": v[0], "walker_steps": v[1], "walker_steps_per_s": rate[k]}
+                     for k, v in res.items()},
+            "batch_over_sequential": rate["batch"] / rate["sequential"],
+            "batch_over_streams": rate["batch"] / rate["streams"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.serve:
         return serve_arm(args)
+    if args.batch:
+        return batch_arm(args)
     world, rank, local, pg = dist_setup(args.gpus)
     try:
         if args.impl == "reference":

@@ -215,6 +215,73 @@ int ddqmc_set_timing(ddqmc_run *run, int32_t enable);
 /* Accumulated milliseconds and launch counts per kernel class (cap >= 5). */
 int ddqmc_get_timing(ddqmc_run *run, double *ms, int64_t *launches, int32_t cap);
 
+/* ---- batches of runs in one walker store -------------------------------------
+ * The paper averages many independent runs per parameter point (Sec. V: 21
+ * runs per susceptibility point, several hundred per lattice size).  A batch
+ * steps up to DDQMC_MAX_BATCH such runs of one lattice and one guide as a
+ * single DDQMC step: one list sorted by (run, bra, ket) with the run id in
+ * the key's high bits, one spawn + death/clone launch over all runs, one sort
+ * and one merge, one finalize block per run.  Each run keeps its own
+ * couplings, gamma, dt, target, initiator threshold, population control,
+ * shift, seed, field, estimators and blocking accumulators, and its walker
+ * list, estimates and step counts are the same as those of a ddqmc_create
+ * run with the same parameters (every random draw is keyed by the run's
+ * seed, the step and the walker's configuration).
+ * ddqmc_step, ddqmc_step_async, ddqmc_sync, ddqmc_get_counts,
+ * ddqmc_get_totals (sums over the runs), the timing calls and ddqmc_destroy
+ * take a batch like a run; the per-run queries are the ddqmc_batch_* calls
+ * below, and ddqmc_estimators, ddqmc_raw_estimators, ddqmc_blocking_moments,
+ * ddqmc_export_walkers and ddqmc_get_state return INVALID_ARG for a batch
+ * (ddqmc_import_walkers and ddqmc_annihilate: UNSUPPORTED). */
+#define DDQMC_MAX_BATCH 64
+
+/* Parameters of one run of a batch: the arguments of ddqmc_create and the
+ * per-run fields of ddqmc_options, with the same meaning and checks. */
+typedef struct {
+    double Jx, Jy, Jz, gamma, dt;
+    int64_t target_walkers;
+    int32_t initiator_threshold;
+    int32_t control;
+    uint64_t seed;
+    double damping;
+    double shift0;
+    int64_t n0;
+    int64_t t_eq;
+    double field_h;
+    int32_t field_axis;
+    int32_t reserved;          /* set to 0 */
+} ddqmc_run_spec;
+
+/* Create a batch of nruns (1..DDQMC_MAX_BATCH) runs on one lattice and one
+ * guide; runs[k] gives run k's parameters.  From opt only capacity_entries,
+ * capacity_spawns (shared by all runs; <= 0: the sum of the per-run
+ * defaults), cuda_stream and sm_limit are read.  Key layout: up to 31 sites
+ * one 64-bit key run << 2N | bra << N | ket (needs 2N + ceil(log2 nruns) <=
+ * 63; 8-byte spawn records when it is <= 32), from 32 to 63 sites the run id
+ * in the bra word above bit N (needs N + ceil(log2 nruns) <= 64); 64 sites
+ * need an extra key word and return UNSUPPORTED, as does a batch whose
+ * per-block estimator sums (nruns x observables x 8 bytes) do not fit in
+ * shared memory.  Errors: as ddqmc_create, UNSUPPORTED.  *out is NULL on
+ * error. */
+int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_run_spec *runs,
+                       const ddqmc_guide *guide, const ddqmc_options *opt, ddqmc_run **out);
+
+/* Estimates of run `run` of a batch (as ddqmc_estimators). */
+int ddqmc_batch_estimators(ddqmc_run *batch, int32_t run, ddqmc_estimates *out);
+
+/* Estimator numerators of run `run` of a batch (as ddqmc_raw_estimators). */
+int ddqmc_batch_raw_estimators(ddqmc_run *batch, int32_t run, int64_t *host_out, int32_t cap,
+                               int32_t *nobs);
+
+/* Walker list of run `run` of a batch, without the run id (as
+ * ddqmc_export_walkers: *n receives that run's length). */
+int ddqmc_batch_export_walkers(ddqmc_run *batch, int32_t run, uint64_t *ket, uint64_t *bra,
+                               int32_t *re, int32_t *im, int64_t cap, int64_t *n);
+
+/* Scalar state of run `run` of a batch (as ddqmc_get_state; entries counts
+ * that run's configurations, status is the batch's). */
+int ddqmc_batch_get_state(ddqmc_run *batch, int32_t run, ddqmc_state *out);
+
 /* Annihilation stage on its own (Sec. III.C rule (iii) with the initiator
  * rule of Sec. IV.A): sort spawn records by configuration and merge them into
  * a sorted list.  Records are 16 bytes, { uint64 key; int32 re; int32 im; },

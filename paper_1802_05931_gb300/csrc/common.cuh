@@ -84,9 +84,24 @@ struct RunParams {
     uint64_t Emorton;                 // bond-existence mask, bit 2k = right bond of k, 2k+1 = lower (sites < 32)
     uint64_t Emorton_hi;              // the same for sites 32..63 (bit 2(k-32), 2(k-32)+1)
     uint64_t urate8[8];               // rate of group 4*anti + class when every bond has the same table
+    // A batch of runs shares one walker store with the run id in the key's
+    // high bits (bit run_shift up: 2N for one-word keys, N of the bra word for
+    // two-word keys).  nruns = 0 for a single run.
+    int32_t nruns, run_shift;
+    // the uniform tables in the forms the light path reads (a single run
+    // derives them in shared memory; a batch reads each run's copy)
+    uint32_t urate32[8];
+    float uinv[8];
+    uint32_t ufrate32[4];
+    float ufinv[4];
+    float jinv;
+    int32_t pad3;
 };
 
-// Device-resident state of a run, updated by the kernels of each step.
+// Device-resident state of a run, updated by the kernels of each step.  A
+// batch has one for the shared step machinery (list and spawn counts,
+// tickets, histograms, status) and one per run (shift, population control,
+// death table, estimators; M there counts the run's own entries).
 struct DevState {
     int64_t t, t_var, t_eq, q_prev;
     double S;
@@ -187,6 +202,13 @@ __device__ __forceinline__ uint64_t lb_wait(const uint64_t *p, uint32_t epoch, u
 
 __device__ __forceinline__ void lb_store(uint64_t *p, uint64_t w) {
     *(volatile uint64_t *)p = w;
+}
+
+// Run id of a batch key from its high word (the packed key, or the bra word
+// of a two-word key), kept inside [0, nruns).
+__device__ __forceinline__ int batch_run(uint64_t w, int shift, int nruns) {
+    const uint64_t r = w >> shift;
+    return r < (uint64_t)nruns ? (int)r : nruns - 1;
 }
 
 }  // namespace ddq

@@ -42,6 +42,7 @@ struct ddqmc_run {
     int cur = 0;                 // which L buffer holds the current list
     int g_spawn = 0, g_radix = 0, g_part = 0, g_merge = 0;
     int g_radix_wide = 0;        // radix grid of 16-byte records (standalone annihilation)
+    int g_merge_ann = 0;         // merge grid of 16-byte records (standalone annihilation)
     bool packed = false;         // 8-byte spawn records (2N <= 32) on the step path
     bool wide = false;           // two-word keys (N > 31): RecW lists and spawn records
     int guide_kind = 0;
@@ -62,6 +63,14 @@ struct ddqmc_run {
     // CUDA graphs of GRAPH_STEPS steps, one per starting list buffer, captured on first use
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool no_graph = false;       // capture failed once: plain launches from then on
+    // a batch of runs in one walker store (nruns > 0): hp holds the shared
+    // geometry and key layout, hpr / dPr each run's parameters, dRS each
+    // run's state (dS then holds the shared step counters)
+    int nruns = 0;
+    std::vector<RunParams> hpr;
+    RunParams *dPr = nullptr;
+    DevState *dRS = nullptr;
+    size_t mg_smem = 0;          // dynamic shared memory of the merge launch
 };
 
 namespace {
@@ -89,9 +98,10 @@ void host_death_table(const RunParams &P, double S, DevState &st) {
     }
 }
 
-int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, double Jz, double gamma,
-                 double dt, int64_t target, int32_t n_a, const ddqmc_guide *guide, const ddqmc_options &o) {
-    RunParams &P = r->hp;
+// Parameters of one run into P; the guide's weights into r.
+int build_params(ddqmc_run *r, RunParams &P, const ddqmc_lattice *lat, double Jx, double Jy, double Jz,
+                 double gamma, double dt, int64_t target, int32_t n_a, const ddqmc_guide *guide,
+                 const ddqmc_options &o) {
     std::memset(&P, 0, sizeof(P));
     const int Lx = lat->Lx, Ly = lat->Ly, per = lat->periodic ? 1 : 0;
     if (Lx < 1 || Ly < 1 || (int64_t)Lx * Ly > 64) return DDQMC_ERR_INVALID_ARG;
@@ -234,8 +244,17 @@ int build_params(ddqmc_run *r, const ddqmc_lattice *lat, double Jx, double Jy, d
     for (int k = 1; k < N; ++k)
         for (int c = 0; c < 4; ++c) uni = uni && P.frate_q[k][c] == P.frate_q[0][c];
     P.uniform = uni ? 1 : 0;
-    for (int g = 0; g < 8; ++g) P.urate8[g] = P.rate_q[0][g >> 2][g & 3];
-    for (int c = 0; c < 4; ++c) P.ufrate[c] = P.frate_q[0][c];
+    for (int g = 0; g < 8; ++g) {
+        P.urate8[g] = P.rate_q[0][g >> 2][g & 3];
+        P.urate32[g] = (uint32_t)P.urate8[g];
+        P.uinv[g] = P.urate8[g] ? 1.0f / (float)P.urate8[g] : 0.0f;
+    }
+    for (int c = 0; c < 4; ++c) {
+        P.ufrate[c] = P.frate_q[0][c];
+        P.ufrate32[c] = (uint32_t)P.ufrate[c];
+        P.ufinv[c] = P.ufrate[c] ? 1.0f / (float)P.ufrate[c] : 0.0f;
+    }
+    P.jinv = P.jump_q ? 1.0f / (float)P.jump_q : 0.0f;
     const double cbase = dt * std::fabs(Jz);
     for (int c = 0; c <= 2 * B; ++c) {
         const double x = cbase * (double)c;
@@ -284,6 +303,8 @@ void free_run(ddqmc_run *r) {
     if (r->hstage) cudaFreeHost(r->hstage);
     cudaFree(r->dP);
     cudaFree(r->dS);
+    cudaFree(r->dPr);
+    cudaFree(r->dRS);
     cudaFree(r->dBlk);
     cudaFree(r->L[0]);
     cudaFree(r->L[1]);
@@ -356,8 +377,9 @@ constexpr size_t RXW_SMEM = sizeof(RadixShared<RecW>);
 constexpr size_t MGW_SMEM = sizeof(MergeShared<RecW>);
 
 // One step's launches for spawn records of type T (16-byte Rec, packed 8-byte,
-// or two-word RecW), on the list buffers Lc (current) and Ln (next).
-template <typename T>
+// or two-word RecW), on the list buffers Lc (current) and Ln (next); BATCH:
+// the lists hold a batch of runs.
+template <typename T, bool BATCH>
 void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(int, int)> &mark) {
     using LT = typename ListOf<T>::type;
     LT *Lc = reinterpret_cast<LT *>(Lcv), *Ln = reinterpret_cast<LT *>(Lnv);
@@ -365,13 +387,15 @@ void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(in
     T *sp0 = reinterpret_cast<T *>(r->Sp[0]);
     T *sp1 = reinterpret_cast<T *>(r->Sp[1]);
     const size_t rx_smem = sizeof(RadixShared<T>);
+    const RunParams *Pr = BATCH ? r->dPr : r->dP;
+    DevState *rs = BATCH ? r->dRS : r->dS;
     mark(0, 0);
     if (P.field_on)
-        k_spawn_death<T, true><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(r->dP, r->dS, Lc, sp0,
-                                                                                          r->rcap);
+        k_spawn_death<T, true, BATCH><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(
+            r->dP, r->dS, Lc, sp0, r->rcap, Pr, rs);
     else
-        k_spawn_death<T, false><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(r->dP, r->dS, Lc, sp0,
-                                                                                           r->rcap);
+        k_spawn_death<T, false, BATCH><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(
+            r->dP, r->dS, Lc, sp0, r->rcap, Pr, rs);
     mark(0, 1);
     mark(1, 0);
     for (int p = 0; p < P.npass; ++p)
@@ -383,9 +407,152 @@ void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(in
     k_merge_partition<T><<<r->g_part, 256, 0, r->stream>>>(Lc, sorted, r->dS, r->splits, r->rem_end, r->rcap);
     mark(2, 1);
     mark(3, 0);
-    k_merge<T><<<r->g_merge, MG_TPB, sizeof(MergeShared<T>), r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits, r->rem_end,
-                                                           r->lb_merge, r->rcap, r->mcap);
+    k_merge<T, BATCH><<<r->g_merge, MG_TPB, r->mg_smem, r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits,
+                                                                    r->rem_end, r->lb_merge, r->rcap, r->mcap, Pr, rs);
     mark(3, 1);
+}
+
+// Default capacities: with total-population control the list holds at most
+// ~target entries and a step makes up to a few records per walker (P_tot > 1
+// under importance sampling); with diagonal control the off-diagonal
+// population is not held, so leave a wide margin.
+int64_t default_list_capacity(int control, int64_t target) {
+    return (control == 1 ? 2 * target : 64 * target) + 65536;
+}
+int64_t default_spawn_capacity(int control, int64_t target) {
+    return (control == 1 ? 4 * target : 64 * target) + 65536;
+}
+
+// Step state of a run at t = 0: n0 real walkers on |0><0|, fixed shift S0.
+void initial_state(const RunParams &P, double S0, int64_t n0, DevState &hs) {
+    std::memset(&hs, 0, sizeof(hs));
+    hs.t = 0;
+    hs.t_var = -1;
+    hs.t_eq = -1;
+    hs.q_prev = n0;
+    hs.S = S0;
+    hs.variable = 0;
+    hs.M = n0 > 0 ? 1 : 0;
+    hs.W_cur = n0;
+    hs.epoch = 16;
+    host_death_table(P, S0, hs);
+}
+
+// Stream, device buffers (capacities clamped to [4096, 2^31 - 1]), blocking
+// cells, kernel attributes and persistent grid sizes of a run or a batch
+// (r->hp, r->nruns, r->wide and r->packed already set).
+int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rcap, size_t blk_cells) {
+    if (cudaGetDevice(&r->device) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    if (mcap < 4096) mcap = 4096;
+    if (rcap < 4096) rcap = 4096;
+    const int64_t lim = (1ll << 31) - 1;
+    if (mcap > lim) mcap = lim;
+    if (rcap > lim) rcap = lim;
+    r->mcap = mcap;
+    r->rcap = rcap;
+    if (o.cuda_stream) {
+        r->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            r->stream = nullptr;
+            return DDQMC_ERR_CUDA;
+        }
+        r->own_stream = true;
+    }
+    const int64_t rtiles = rcap / RX_TILE_MIN + 2;
+    const int64_t mtiles = (mcap + rcap) / MG_TILE + 2;
+    int rc = DDQMC_OK;
+    rc |= dalloc(&r->dP, 1);
+    rc |= dalloc(&r->dS, 1);
+    rc |= dalloc(&r->dBlk, blk_cells);
+    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
+    const size_t ssize = r->wide ? sizeof(RecW) : sizeof(Rec);   // standalone annihilation uses 16-byte Rec
+    rc |= dalloc_bytes(&r->L[0], lsize * (size_t)mcap);
+    rc |= dalloc_bytes(&r->L[1], lsize * (size_t)mcap);
+    rc |= dalloc_bytes(&r->Sp[0], ssize * (size_t)rcap);
+    rc |= dalloc_bytes(&r->Sp[1], ssize * (size_t)rcap);
+    rc |= dalloc(&r->lb_radix, (size_t)rtiles * 256);
+    rc |= dalloc(&r->lb_merge, (size_t)mtiles);
+    rc |= dalloc(&r->splits, (size_t)mtiles + 1);
+    rc |= dalloc(&r->rem_end, (size_t)mtiles + 1);
+    if (rc != DDQMC_OK) return DDQMC_ERR_OOM;
+    // kernel shapes
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device);
+    if (sms < 1) sms = 1;
+    if (o.sm_limit > 0 && o.sm_limit < sms) sms = o.sm_limit;
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, r->device);
+    bool ok = true;
+    auto attr = [&](const void *fn, size_t bytes) {
+        ok = ok && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+    };
+    attr((const void *)k_spawn_death<Rec, true, false>, SP_SMEM);
+    attr((const void *)k_spawn_death<Rec, false, false>, SP_SMEM);
+    attr((const void *)k_spawn_death<uint64_t, true, false>, SPP_SMEM);
+    attr((const void *)k_spawn_death<uint64_t, false, false>, SPP_SMEM);
+    attr((const void *)k_spawn_death<RecW, true, false>, SPW_SMEM);
+    attr((const void *)k_spawn_death<RecW, false, false>, SPW_SMEM);
+    attr((const void *)k_spawn_death<Rec, true, true>, SP_SMEM);
+    attr((const void *)k_spawn_death<Rec, false, true>, SP_SMEM);
+    attr((const void *)k_spawn_death<uint64_t, true, true>, SPP_SMEM);
+    attr((const void *)k_spawn_death<uint64_t, false, true>, SPP_SMEM);
+    attr((const void *)k_spawn_death<RecW, true, true>, SPW_SMEM);
+    attr((const void *)k_spawn_death<RecW, false, true>, SPW_SMEM);
+    attr((const void *)k_radix_pass<Rec>, RX_SMEM);
+    attr((const void *)k_radix_pass<uint64_t>, RXP_SMEM);
+    attr((const void *)k_radix_pass<RecW>, RXW_SMEM);
+    attr((const void *)k_merge<Rec, false>, MG_SMEM);
+    attr((const void *)k_merge<uint64_t, false>, MGP_SMEM);
+    attr((const void *)k_merge<RecW, false>, MGW_SMEM);
+    // batch merges: per-run estimator sums past MergeShared, up to what the
+    // device allows next to the kernel's static shared memory
+    auto dyn_max = [&](const void *fn) -> size_t {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) { ok = false; return 0; }
+        return (size_t)smem_max > fa.sharedSizeBytes ? (size_t)smem_max - fa.sharedSizeBytes : 0;
+    };
+    const size_t bmax_rec = dyn_max((const void *)k_merge<Rec, true>);
+    const size_t bmax_pk = dyn_max((const void *)k_merge<uint64_t, true>);
+    const size_t bmax_w = dyn_max((const void *)k_merge<RecW, true>);
+    attr((const void *)k_merge<Rec, true>, bmax_rec);
+    attr((const void *)k_merge<uint64_t, true>, bmax_pk);
+    attr((const void *)k_merge<RecW, true>, bmax_w);
+    if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    const bool B = r->nruns > 0;
+    const size_t est_bytes = B ? sizeof(unsigned long long) * (size_t)r->nruns * (size_t)r->hp.nobs : 0;
+    const void *fs, *fr, *fm;
+    size_t ss, sr, sm, bmax;
+    if (r->packed) {
+        fs = B ? (const void *)k_spawn_death<uint64_t, false, true> : (const void *)k_spawn_death<uint64_t, false, false>;
+        fr = (const void *)k_radix_pass<uint64_t>;
+        fm = B ? (const void *)k_merge<uint64_t, true> : (const void *)k_merge<uint64_t, false>;
+        ss = SPP_SMEM; sr = RXP_SMEM; sm = MGP_SMEM; bmax = bmax_pk;
+    } else if (r->wide) {
+        fs = B ? (const void *)k_spawn_death<RecW, false, true> : (const void *)k_spawn_death<RecW, false, false>;
+        fr = (const void *)k_radix_pass<RecW>;
+        fm = B ? (const void *)k_merge<RecW, true> : (const void *)k_merge<RecW, false>;
+        ss = SPW_SMEM; sr = RXW_SMEM; sm = MGW_SMEM; bmax = bmax_w;
+    } else {
+        fs = B ? (const void *)k_spawn_death<Rec, false, true> : (const void *)k_spawn_death<Rec, false, false>;
+        fr = (const void *)k_radix_pass<Rec>;
+        fm = B ? (const void *)k_merge<Rec, true> : (const void *)k_merge<Rec, false>;
+        ss = SP_SMEM; sr = RX_SMEM; sm = MG_SMEM; bmax = bmax_rec;
+    }
+    r->mg_smem = sm + est_bytes;
+    if (B && r->mg_smem > bmax) return DDQMC_ERR_UNSUPPORTED;   // too many runs x observables
+    r->g_spawn = occupancy_grid(fs, SP_TPB, ss, sms);
+    r->g_radix = occupancy_grid(fr, RX_TPB, sr, sms);
+    r->g_merge = occupancy_grid(fm, MG_TPB, r->mg_smem, sms);
+    r->g_merge_ann = occupancy_grid((const void *)k_merge<Rec, false>, MG_TPB, MG_SMEM, sms);
+    r->g_radix_wide = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
+    r->g_part = 4 * sms;
+    bool okc = cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * blk_cells, r->stream) == cudaSuccess;
+    okc = okc && cudaMemsetAsync(r->lb_radix, 0, sizeof(uint64_t) * (size_t)rtiles * 256, r->stream) == cudaSuccess;
+    okc = okc && cudaMemsetAsync(r->lb_merge, 0, sizeof(uint64_t) * (size_t)mtiles, r->stream) == cudaSuccess;
+    if (!okc) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    return DDQMC_OK;
 }
 
 // kernel classes of the per-kernel timing
@@ -399,11 +566,18 @@ void launch_one_step(ddqmc_run *r, const std::function<void(int, int)> &mark) {
     // one NVTX range per issued step (free without an attached tool)
     nvtxRangePushA("ddqmc step");
     void *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
-    if (r->packed) launch_step<uint64_t>(r, Lc, Ln, mark);
-    else if (r->wide) launch_step<RecW>(r, Lc, Ln, mark);
-    else launch_step<Rec>(r, Lc, Ln, mark);
+    if (r->nruns) {
+        if (r->packed) launch_step<uint64_t, true>(r, Lc, Ln, mark);
+        else if (r->wide) launch_step<RecW, true>(r, Lc, Ln, mark);
+        else launch_step<Rec, true>(r, Lc, Ln, mark);
+    } else {
+        if (r->packed) launch_step<uint64_t, false>(r, Lc, Ln, mark);
+        else if (r->wide) launch_step<RecW, false>(r, Lc, Ln, mark);
+        else launch_step<Rec, false>(r, Lc, Ln, mark);
+    }
     mark(KC_FINALIZE, 0);
-    k_finalize<<<1, FN_TPB, 0, r->stream>>>(r->dP, r->dS, r->dBlk);
+    if (r->nruns) k_finalize<true><<<r->nruns, FN_TPB, 0, r->stream>>>(r->dPr, r->dS, r->dBlk, r->dRS);
+    else k_finalize<false><<<1, FN_TPB, 0, r->stream>>>(r->dP, r->dS, r->dBlk, r->dS);
     mark(KC_FINALIZE, 1);
     nvtxRangePop();
     r->cur ^= 1;
@@ -590,14 +764,115 @@ int noalloc_setup(int dev) {
         return DDQMC_ERR_CUDA;
     }
     if (cudaFuncSetAttribute(k_radix_pass<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) != cudaSuccess ||
-        cudaFuncSetAttribute(k_merge<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) != cudaSuccess) {
+        cudaFuncSetAttribute(k_merge<Rec, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) !=
+            cudaSuccess) {
         cudaGetLastError();
         return DDQMC_ERR_CUDA;
     }
     g_na_grid[dev][0] = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
     g_na_grid[dev][1] = 4 * sms;
-    g_na_grid[dev][2] = occupancy_grid((const void *)k_merge<Rec>, MG_TPB, MG_SMEM, sms);
+    g_na_grid[dev][2] = occupancy_grid((const void *)k_merge<Rec, false>, MG_TPB, MG_SMEM, sms);
     g_na_ptr[dev] = (NoAllocScratch *)ptr;
+    return DDQMC_OK;
+}
+
+// Run k of a batch, or the run itself (k ignored) when not a batch.
+DevState *run_state(ddqmc_run *r, int k) { return r->nruns ? r->dRS + k : r->dS; }
+const RunParams &run_params(const ddqmc_run *r, int k) { return r->nruns ? r->hpr[(size_t)k] : r->hp; }
+BlkCell *run_cells(ddqmc_run *r, int k) {
+    return r->dBlk + (r->nruns ? (size_t)k * (size_t)r->hp.nobs * LEVELS : (size_t)0);
+}
+
+int state_of(ddqmc_run *r, int k, ddqmc_state *out);
+int estimates_of(ddqmc_run *r, int k, ddqmc_estimates *out);
+
+int raw_estimators_of(ddqmc_run *r, int k, int64_t *host_out, int32_t cap, int32_t *nobs) {
+    const int n = run_params(r, k).nobs;
+    if (nobs) *nobs = n;
+    const int m = cap < n ? cap : n;
+    if (m > 0) {
+        if (cudaMemcpyAsync(host_out, run_state(r, k)->last_est, sizeof(int64_t) * (size_t)m,
+                            cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+            cudaStreamSynchronize(r->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return DDQMC_ERR_CUDA;
+        }
+    }
+    return DDQMC_OK;
+}
+
+// Canonical (ket, bra, re, im) of the current list: the whole list (k < 0),
+// or the entries of batch run k (a contiguous range: the run id is the key's
+// most significant part).  *n = the entries of that list or run.
+int export_of(ddqmc_run *r, int k, uint64_t *ket, uint64_t *bra, int32_t *re, int32_t *im, int64_t cap,
+              int64_t *n) {
+    int64_t M = 0;
+    if (cudaMemcpyAsync(&M, &r->dS->M, sizeof(M), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    if (k < 0) {
+        *n = M;
+        if (cap < M) M = cap;       // only what the caller can take
+    }
+    if (M <= 0) {
+        if (k >= 0) *n = 0;
+        return DDQMC_OK;
+    }
+    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
+    unsigned char *hb = host_stage(r, lsize * (size_t)M);
+    if (!hb) return DDQMC_ERR_OOM;
+    if (cudaMemcpyAsync(hb, r->L[r->cur], lsize * (size_t)M, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    const int N = r->hp.N, rs = r->hp.run_shift;
+    const uint64_t mask = r->hp.nmask;
+    const RecW *hw = reinterpret_cast<const RecW *>(hb);
+    const Rec *h1 = reinterpret_cast<const Rec *>(hb);
+    // [b0, b1): the exported range
+    int64_t b0 = 0, b1 = M;
+    if (k >= 0) {
+        auto run_of = [&](int64_t q) -> uint64_t { return r->wide ? (hw[q].hi >> rs) : (h1[q].key >> rs); };
+        int64_t lo = 0, hi = M;
+        while (lo < hi) {           // first entry of a run >= k
+            const int64_t mid = (lo + hi) / 2;
+            if (run_of(mid) < (uint64_t)k) lo = mid + 1; else hi = mid;
+        }
+        b0 = lo;
+        hi = M;
+        while (lo < hi) {           // first entry of a run > k
+            const int64_t mid = (lo + hi) / 2;
+            if (run_of(mid) <= (uint64_t)k) lo = mid + 1; else hi = mid;
+        }
+        b1 = lo;
+        *n = b1 - b0;
+        if (b1 - b0 > cap) b1 = b0 + (cap > 0 ? cap : 0);
+    }
+    const int64_t m = b1 - b0;
+    if (r->wide) {
+        parallel_for(m, [&](int64_t b, int64_t e) {
+            for (int64_t q = b; q < e; ++q) {
+                const RecW &v = hw[b0 + q];
+                ket[q] = v.lo;
+                bra[q] = v.hi & mask;
+                re[q] = v.re;
+                im[q] = v.im;
+            }
+        });
+    } else {
+        parallel_for(m, [&](int64_t b, int64_t e) {
+            for (int64_t q = b; q < e; ++q) {
+                const Rec &v = h1[b0 + q];
+                ket[q] = v.key & mask;
+                bra[q] = (v.key >> N) & mask;
+                re[q] = v.re;
+                im[q] = v.im;
+            }
+        });
+    }
     return DDQMC_OK;
 }
 
@@ -633,102 +908,19 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     if (opt) o = *opt;
     ddqmc_run *r = new (std::nothrow) ddqmc_run();
     if (!r) return DDQMC_ERR_OOM;
-    int rc = build_params(r, lattice, Jx, Jy, Jz, gamma, dt, target_walkers, initiator_threshold, guide, o);
+    int rc = build_params(r, r->hp, lattice, Jx, Jy, Jz, gamma, dt, target_walkers, initiator_threshold, guide, o);
     if (rc != DDQMC_OK) { delete r; return rc; }
-    if (cudaGetDevice(&r->device) != cudaSuccess) { cudaGetLastError(); delete r; return DDQMC_ERR_CUDA; }
     // capacities
     int64_t mcap = o.capacity_entries, rcap = o.capacity_spawns;
-    // defaults: with total-population control the list holds at most ~target
-    // entries and a step makes up to a few records per walker (P_tot > 1 under
-    // importance sampling); with diagonal control the off-diagonal population
-    // is not held, so leave a wide margin
-    if (mcap <= 0) mcap = (o.control == 1 ? 2 * target_walkers : 64 * target_walkers) + 65536;
-    if (rcap <= 0) rcap = (o.control == 1 ? 4 * target_walkers : 64 * target_walkers) + 65536;
-    if (mcap < 4096) mcap = 4096;
-    if (rcap < 4096) rcap = 4096;
-    const int64_t lim = (1ll << 31) - 1;
-    if (mcap > lim) mcap = lim;
-    if (rcap > lim) rcap = lim;
-    r->mcap = mcap;
-    r->rcap = rcap;
-    if (o.cuda_stream) {
-        r->stream = (cudaStream_t)o.cuda_stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            delete r;
-            return DDQMC_ERR_CUDA;
-        }
-        r->own_stream = true;
-    }
-    const int64_t rtiles = rcap / RX_TILE_MIN + 2;
-    const int64_t mtiles = (mcap + rcap) / MG_TILE + 2;
-    rc = DDQMC_OK;
-    rc |= dalloc(&r->dP, 1);
-    rc |= dalloc(&r->dS, 1);
-    rc |= dalloc(&r->dBlk, (size_t)NOBS_MAX * LEVELS);
+    if (mcap <= 0) mcap = default_list_capacity(o.control, target_walkers);
+    if (rcap <= 0) rcap = default_spawn_capacity(o.control, target_walkers);
     r->wide = r->hp.N > NPACK;
-    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
-    const size_t ssize = r->wide ? sizeof(RecW) : sizeof(Rec);   // standalone annihilation uses 16-byte Rec
-    rc |= dalloc_bytes(&r->L[0], lsize * (size_t)mcap);
-    rc |= dalloc_bytes(&r->L[1], lsize * (size_t)mcap);
-    rc |= dalloc_bytes(&r->Sp[0], ssize * (size_t)rcap);
-    rc |= dalloc_bytes(&r->Sp[1], ssize * (size_t)rcap);
-    rc |= dalloc(&r->lb_radix, (size_t)rtiles * 256);
-    rc |= dalloc(&r->lb_merge, (size_t)mtiles);
-    rc |= dalloc(&r->splits, (size_t)mtiles + 1);
-    rc |= dalloc(&r->rem_end, (size_t)mtiles + 1);
-    if (rc != DDQMC_OK) { free_run(r); return DDQMC_ERR_OOM; }
-    // kernel shapes
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device);
-    if (sms < 1) sms = 1;
-    if (o.sm_limit > 0 && o.sm_limit < sms) sms = o.sm_limit;
     r->packed = 2 * r->hp.N <= 32;
-    bool ok = true;
-    for (int f = 0; f < 2; ++f) {
-        const void *fr = f ? (const void *)k_spawn_death<Rec, true> : (const void *)k_spawn_death<Rec, false>;
-        const void *fp = f ? (const void *)k_spawn_death<uint64_t, true> : (const void *)k_spawn_death<uint64_t, false>;
-        const void *fw = f ? (const void *)k_spawn_death<RecW, true> : (const void *)k_spawn_death<RecW, false>;
-        ok = ok && cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SP_SMEM) == cudaSuccess;
-        ok = ok && cudaFuncSetAttribute(fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPP_SMEM) == cudaSuccess;
-        ok = ok && cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPW_SMEM) == cudaSuccess;
-    }
-    ok = ok && cudaFuncSetAttribute(k_radix_pass<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RX_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_radix_pass<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RXP_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_merge<Rec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MG_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_merge<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MGP_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_radix_pass<RecW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RXW_SMEM) == cudaSuccess;
-    ok = ok && cudaFuncSetAttribute(k_merge<RecW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MGW_SMEM) == cudaSuccess;
-    if (!ok) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
-    if (r->packed) {
-        r->g_spawn = occupancy_grid((const void *)k_spawn_death<uint64_t, false>, SP_TPB, SPP_SMEM, sms);
-        r->g_radix = occupancy_grid((const void *)k_radix_pass<uint64_t>, RX_TPB, RXP_SMEM, sms);
-        r->g_merge = occupancy_grid((const void *)k_merge<uint64_t>, MG_TPB, MGP_SMEM, sms);
-    } else if (r->wide) {
-        r->g_spawn = occupancy_grid((const void *)k_spawn_death<RecW, false>, SP_TPB, SPW_SMEM, sms);
-        r->g_radix = occupancy_grid((const void *)k_radix_pass<RecW>, RX_TPB, RXW_SMEM, sms);
-        r->g_merge = occupancy_grid((const void *)k_merge<RecW>, MG_TPB, MGW_SMEM, sms);
-    } else {
-        r->g_spawn = occupancy_grid((const void *)k_spawn_death<Rec, false>, SP_TPB, SP_SMEM, sms);
-        r->g_radix = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
-        r->g_merge = occupancy_grid((const void *)k_merge<Rec>, MG_TPB, MG_SMEM, sms);
-    }
-    r->g_radix_wide = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
-    r->g_part = 4 * sms;
+    rc = setup_device(r, o, mcap, rcap, (size_t)NOBS_MAX * LEVELS);
+    if (rc != DDQMC_OK) { free_run(r); return rc; }
     // initial state
     DevState hs;
-    std::memset(&hs, 0, sizeof(hs));
-    hs.t = 0;
-    hs.t_var = -1;
-    hs.t_eq = -1;
-    hs.q_prev = o.n0;
-    hs.S = o.shift0;
-    hs.variable = 0;
-    hs.M = o.n0 > 0 ? 1 : 0;
-    hs.W_cur = o.n0;
-    hs.epoch = 16;
-    host_death_table(r->hp, o.shift0, hs);
+    initial_state(r->hp, o.shift0, o.n0, hs);
     Rec first;
     first.key = 0;
     first.re = (int32_t)o.n0;
@@ -740,12 +932,121 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     firstw.im = 0;
     bool okc = cudaMemcpyAsync(r->dP, &r->hp, sizeof(RunParams), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
     okc = okc && cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
-    okc = okc && cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * (size_t)NOBS_MAX * LEVELS, r->stream) == cudaSuccess;
-    okc = okc && cudaMemsetAsync(r->lb_radix, 0, sizeof(uint64_t) * (size_t)rtiles * 256, r->stream) == cudaSuccess;
-    okc = okc && cudaMemsetAsync(r->lb_merge, 0, sizeof(uint64_t) * (size_t)mtiles, r->stream) == cudaSuccess;
     okc = okc && (r->wide ? cudaMemcpyAsync(r->L[0], &firstw, sizeof(RecW), cudaMemcpyHostToDevice, r->stream)
                           : cudaMemcpyAsync(r->L[0], &first, sizeof(Rec), cudaMemcpyHostToDevice, r->stream)) ==
                   cudaSuccess;
+    okc = okc && cudaStreamSynchronize(r->stream) == cudaSuccess;
+    if (!okc) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
+    r->cur = 0;
+    *out = r;
+    return DDQMC_OK;
+}
+
+int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_run_spec *runs,
+                       const ddqmc_guide *guide, const ddqmc_options *opt, ddqmc_run **out) {
+    if (!out) return DDQMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!lattice || !runs || nruns < 1 || nruns > DDQMC_MAX_BATCH) return DDQMC_ERR_INVALID_ARG;
+    ddqmc_options o;
+    ddqmc_default_options(&o);
+    if (opt) o = *opt;
+    ddqmc_run *r = new (std::nothrow) ddqmc_run();
+    if (!r) return DDQMC_ERR_OOM;
+    r->nruns = nruns;
+    r->hpr.resize((size_t)nruns);
+    int64_t mdef = 0, rdef = 0;
+    for (int k = 0; k < nruns; ++k) {
+        const ddqmc_run_spec &q = runs[k];
+        ddqmc_options ok = o;
+        ok.seed = q.seed;
+        ok.damping = q.damping;
+        ok.shift0 = q.shift0;
+        ok.n0 = q.n0;
+        ok.control = q.control;
+        ok.t_eq = q.t_eq;
+        ok.field_h = q.field_h;
+        ok.field_axis = q.field_axis;
+        const int rc = build_params(r, r->hpr[k], lattice, q.Jx, q.Jy, q.Jz, q.gamma, q.dt, q.target_walkers,
+                                    q.initiator_threshold, guide, ok);
+        if (rc != DDQMC_OK) { delete r; return rc; }
+        if (!std::isfinite(q.shift0) || !std::isfinite(q.damping)) { delete r; return DDQMC_ERR_INVALID_ARG; }
+        mdef += default_list_capacity(q.control, q.target_walkers);
+        rdef += default_spawn_capacity(q.control, q.target_walkers);
+    }
+    // key layout: the run id above the spin bits (2N of a one-word key, N of the bra word)
+    RunParams &H = r->hp;
+    H = r->hpr[0];
+    const int N = H.N, B = H.B;
+    int rbits = 0;
+    while ((1ll << rbits) < (int64_t)nruns) ++rbits;
+    r->wide = N > NPACK;
+    if (r->wide) {
+        if (N + rbits > 64 || N >= 64) { delete r; return DDQMC_ERR_UNSUPPORTED; }
+        const int nb = (N + 7) / 8, nbb = (N + rbits + 7) / 8;
+        H.npass = nb + nbb;
+        for (int p = 0; p < H.npass; ++p) H.pass_shift[p] = p < nb ? 8 * p : 64 + 8 * (p - nb);
+        H.run_shift = N;
+    } else {
+        if (2 * N + rbits > 63) { delete r; return DDQMC_ERR_UNSUPPORTED; }
+        H.npass = (2 * N + rbits + 7) / 8;
+        for (int p = 0; p < H.npass; ++p) H.pass_shift[p] = 8 * p;
+        H.run_shift = 2 * N;
+    }
+    r->packed = 2 * N + rbits <= 32;
+    H.nruns = nruns;
+    H.field_on = 0;
+    for (int k = 0; k < nruns; ++k) H.field_on |= r->hpr[k].field_on;
+    H.K = 2 * B + N + (H.field_on ? 2 * N : 0);
+    for (int k = 0; k < nruns; ++k) {
+        r->hpr[k].nruns = nruns;
+        r->hpr[k].run_shift = H.run_shift;
+        r->hpr[k].npass = H.npass;
+        r->hpr[k].K = H.K;
+    }
+    int64_t mcap = o.capacity_entries > 0 ? o.capacity_entries : mdef;
+    int64_t rcap = o.capacity_spawns > 0 ? o.capacity_spawns : rdef;
+    int rc = setup_device(r, o, mcap, rcap, (size_t)nruns * H.nobs * LEVELS);
+    if (rc != DDQMC_OK) { free_run(r); return rc; }
+    rc |= dalloc(&r->dPr, (size_t)nruns);
+    rc |= dalloc(&r->dRS, (size_t)nruns);
+    if (rc != DDQMC_OK) { free_run(r); return DDQMC_ERR_OOM; }
+    // per-run states, the shared counters and the first list (one entry per run with walkers, in run order)
+    std::vector<DevState> rs((size_t)nruns);
+    DevState ms;
+    std::memset(&ms, 0, sizeof(ms));
+    ms.epoch = 16;
+    std::vector<Rec> first;
+    std::vector<RecW> firstw;
+    for (int k = 0; k < nruns; ++k) {
+        initial_state(r->hpr[k], runs[k].shift0, runs[k].n0, rs[k]);
+        if (runs[k].n0 > 0) {
+            ms.M += 1;
+            ms.W_cur += runs[k].n0;
+            Rec e;
+            e.key = (uint64_t)k << H.run_shift;
+            e.re = (int32_t)runs[k].n0;
+            e.im = 0;
+            first.push_back(e);
+            RecW w;
+            w.lo = 0;
+            w.hi = r->wide ? (uint64_t)k << H.run_shift : 0ull;
+            w.re = (int32_t)runs[k].n0;
+            w.im = 0;
+            firstw.push_back(w);
+        }
+    }
+    if (ms.M > r->mcap) { free_run(r); return DDQMC_ERR_CAPACITY; }
+    bool okc = cudaMemcpyAsync(r->dP, &H, sizeof(RunParams), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    okc = okc && cudaMemcpyAsync(r->dPr, r->hpr.data(), sizeof(RunParams) * (size_t)nruns, cudaMemcpyHostToDevice,
+                                 r->stream) == cudaSuccess;
+    okc = okc && cudaMemcpyAsync(r->dRS, rs.data(), sizeof(DevState) * (size_t)nruns, cudaMemcpyHostToDevice,
+                                 r->stream) == cudaSuccess;
+    okc = okc && cudaMemcpyAsync(r->dS, &ms, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    if (ms.M > 0)
+        okc = okc && (r->wide ? cudaMemcpyAsync(r->L[0], firstw.data(), sizeof(RecW) * firstw.size(),
+                                                cudaMemcpyHostToDevice, r->stream)
+                              : cudaMemcpyAsync(r->L[0], first.data(), sizeof(Rec) * first.size(),
+                                                cudaMemcpyHostToDevice, r->stream)) == cudaSuccess;
     okc = okc && cudaStreamSynchronize(r->stream) == cudaSuccess;
     if (!okc) { cudaGetLastError(); free_run(r); return DDQMC_ERR_CUDA; }
     r->cur = 0;
@@ -811,13 +1112,31 @@ int ddqmc_get_totals(ddqmc_run *r, int64_t *walker_steps, int64_t *entry_steps, 
 }
 
 int ddqmc_get_state(ddqmc_run *r, ddqmc_state *out) {
-    if (!r || !out) return DDQMC_ERR_INVALID_ARG;
+    if (!r || !out || r->nruns) return DDQMC_ERR_INVALID_ARG;
+    return state_of(r, 0, out);
+}
+
+int ddqmc_batch_get_state(ddqmc_run *r, int32_t run, ddqmc_state *out) {
+    if (!r || !out || run < 0 || run >= r->nruns) return DDQMC_ERR_INVALID_ARG;
+    return state_of(r, run, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// State of run k (the run itself when not a batch); the status word is the
+// shared one.
+int state_of(ddqmc_run *r, int k, ddqmc_state *out) {
     DevState hs;
-    if (cudaMemcpyAsync(&hs, r->dS, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+    uint32_t status = 0;
+    if (cudaMemcpyAsync(&hs, run_state(r, k), sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&status, &r->dS->status, sizeof(status), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
         cudaGetLastError();
         return DDQMC_ERR_CUDA;
     }
+    hs.status = status;
     out->t = hs.t;
     out->shift = hs.S;
     out->variable = hs.variable;
@@ -829,6 +1148,10 @@ int ddqmc_get_state(ddqmc_run *r, ddqmc_state *out) {
     out->status_bits = (int32_t)hs.status;
     return DDQMC_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int ddqmc_get_counts(ddqmc_run *r, int64_t *spawn_records, int64_t *capacity_entries, int64_t *capacity_spawns) {
     if (!r) return DDQMC_ERR_INVALID_ARG;
@@ -845,24 +1168,18 @@ int ddqmc_get_counts(ddqmc_run *r, int64_t *spawn_records, int64_t *capacity_ent
 }
 
 int ddqmc_raw_estimators(ddqmc_run *r, int64_t *host_out, int32_t cap, int32_t *nobs) {
-    if (!r || (cap > 0 && !host_out)) return DDQMC_ERR_INVALID_ARG;
-    const int n = r->hp.nobs;
-    if (nobs) *nobs = n;
-    const int m = cap < n ? cap : n;
-    if (m > 0) {
-        if (cudaMemcpyAsync(host_out, r->dS->last_est, sizeof(int64_t) * (size_t)m, cudaMemcpyDeviceToHost,
-                            r->stream) != cudaSuccess ||
-            cudaStreamSynchronize(r->stream) != cudaSuccess) {
-            cudaGetLastError();
-            return DDQMC_ERR_CUDA;
-        }
-    }
-    return DDQMC_OK;
+    if (!r || (cap > 0 && !host_out) || r->nruns) return DDQMC_ERR_INVALID_ARG;
+    return raw_estimators_of(r, 0, host_out, cap, nobs);
+}
+
+int ddqmc_batch_raw_estimators(ddqmc_run *r, int32_t run, int64_t *host_out, int32_t cap, int32_t *nobs) {
+    if (!r || (cap > 0 && !host_out) || run < 0 || run >= r->nruns) return DDQMC_ERR_INVALID_ARG;
+    return raw_estimators_of(r, run, host_out, cap, nobs);
 }
 
 int ddqmc_blocking_moments(ddqmc_run *r, int32_t k, int32_t levels, int64_t *hn, int64_t *hsx, int64_t *hsxx,
                            int64_t *hsxy) {
-    if (!r || k < 0 || k >= r->hp.nobs || levels < 0 || levels > LEVELS) return DDQMC_ERR_INVALID_ARG;
+    if (!r || k < 0 || k >= r->hp.nobs || levels < 0 || levels > LEVELS || r->nruns) return DDQMC_ERR_INVALID_ARG;
     std::vector<BlkCell> cells(LEVELS);
     if (cudaMemcpyAsync(cells.data(), r->dBlk + (size_t)k * LEVELS, sizeof(BlkCell) * LEVELS,
                         cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
@@ -886,17 +1203,34 @@ int ddqmc_blocking_moments(ddqmc_run *r, int32_t k, int32_t levels, int64_t *hn,
 }
 
 int ddqmc_estimators(ddqmc_run *r, ddqmc_estimates *out) {
-    if (!r || !out) return DDQMC_ERR_INVALID_ARG;
-    const RunParams &P = r->hp;
+    if (!r || !out || r->nruns) return DDQMC_ERR_INVALID_ARG;
+    return estimates_of(r, 0, out);
+}
+
+int ddqmc_batch_estimators(ddqmc_run *r, int32_t run, ddqmc_estimates *out) {
+    if (!r || !out || run < 0 || run >= r->nruns) return DDQMC_ERR_INVALID_ARG;
+    return estimates_of(r, run, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Estimates of run k (the run itself when not a batch).
+int estimates_of(ddqmc_run *r, int k, ddqmc_estimates *out) {
+    const RunParams &P = run_params(r, k);
     DevState hs;
+    uint32_t status = 0;
     std::vector<BlkCell> cells((size_t)P.nobs * LEVELS);
-    if (cudaMemcpyAsync(&hs, r->dS, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
-        cudaMemcpyAsync(cells.data(), r->dBlk, sizeof(BlkCell) * cells.size(), cudaMemcpyDeviceToHost,
+    if (cudaMemcpyAsync(&hs, run_state(r, k), sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaMemcpyAsync(cells.data(), run_cells(r, k), sizeof(BlkCell) * cells.size(), cudaMemcpyDeviceToHost,
                         r->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&status, &r->dS->status, sizeof(status), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
         cudaGetLastError();
         return DDQMC_ERR_CUDA;
     }
+    hs.status = status;
     std::memset(out, 0, sizeof(*out));
     const int N = P.N, B = P.B, core = 5 + N + 3 * B;
     out->t = hs.t;
@@ -997,50 +1331,21 @@ int ddqmc_estimators(ddqmc_run *r, ddqmc_estimates *out) {
     return r->host_status ? r->host_status : status_code(hs.status);
 }
 
+}  // namespace
+
+extern "C" {
+
 int ddqmc_export_walkers(ddqmc_run *r, uint64_t *ket, uint64_t *bra, int32_t *re, int32_t *im, int64_t cap,
                          int64_t *n) {
-    if (!r || !n || (cap > 0 && (!ket || !bra || !re || !im))) return DDQMC_ERR_INVALID_ARG;
-    int64_t M = 0;
-    if (cudaMemcpyAsync(&M, &r->dS->M, sizeof(M), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
-        cudaStreamSynchronize(r->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return DDQMC_ERR_CUDA;
-    }
-    *n = M;
-    const int64_t m = cap < M ? cap : M;
-    if (m <= 0) return DDQMC_OK;
-    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
-    unsigned char *hb = host_stage(r, lsize * (size_t)m);
-    if (!hb) return DDQMC_ERR_OOM;
-    int rc = DDQMC_OK;
-    if (cudaMemcpyAsync(hb, r->L[r->cur], lsize * (size_t)m, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
-        cudaStreamSynchronize(r->stream) != cudaSuccess) {
-        cudaGetLastError();
-        rc = DDQMC_ERR_CUDA;
-    } else if (r->wide) {
-        const RecW *h = reinterpret_cast<const RecW *>(hb);
-        parallel_for(m, [&](int64_t b, int64_t e) {
-            for (int64_t q = b; q < e; ++q) {
-                ket[q] = h[q].lo;
-                bra[q] = h[q].hi;
-                re[q] = h[q].re;
-                im[q] = h[q].im;
-            }
-        });
-    } else {
-        const Rec *h = reinterpret_cast<const Rec *>(hb);
-        const int N = r->hp.N;
-        const uint64_t mask = r->hp.nmask;
-        parallel_for(m, [&](int64_t b, int64_t e) {
-            for (int64_t q = b; q < e; ++q) {
-                ket[q] = h[q].key & mask;
-                bra[q] = h[q].key >> N;
-                re[q] = h[q].re;
-                im[q] = h[q].im;
-            }
-        });
-    }
-    return rc;
+    if (!r || !n || (cap > 0 && (!ket || !bra || !re || !im)) || r->nruns) return DDQMC_ERR_INVALID_ARG;
+    return export_of(r, -1, ket, bra, re, im, cap, n);
+}
+
+int ddqmc_batch_export_walkers(ddqmc_run *r, int32_t run, uint64_t *ket, uint64_t *bra, int32_t *re, int32_t *im,
+                               int64_t cap, int64_t *n) {
+    if (!r || !n || (cap > 0 && (!ket || !bra || !re || !im)) || run < 0 || run >= r->nruns)
+        return DDQMC_ERR_INVALID_ARG;
+    return export_of(r, run, ket, bra, re, im, cap, n);
 }
 
 int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra, const int32_t *re,
@@ -1048,6 +1353,7 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
                          int64_t t_var, int64_t t_eq) {
     if (!r || n < 0 || (n > 0 && (!ket || !bra || !re || !im)) || t < 0 || !std::isfinite(S))
         return DDQMC_ERR_INVALID_ARG;
+    if (r->nruns) return DDQMC_ERR_UNSUPPORTED;
     if (n > r->mcap) return DDQMC_ERR_CAPACITY;
     const int N = r->hp.N;
     const uint64_t mask = r->hp.nmask;
@@ -1132,7 +1438,7 @@ int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_
         (out_cap > 0 && !d_out))
         return DDQMC_ERR_INVALID_ARG;
     *m_out = 0;
-    if (r->hp.N > NPACK) return DDQMC_ERR_UNSUPPORTED;       // 16-byte records hold one-word keys only
+    if (r->hp.N > NPACK || r->nruns) return DDQMC_ERR_UNSUPPORTED;   // one-word keys of a single run only
     if (nsp > r->rcap || m > r->mcap) return DDQMC_ERR_CAPACITY;
     if (!r->dAnn && dalloc(&r->dAnn, 1) != DDQMC_OK) return DDQMC_ERR_OOM;
     const RunParams &P = r->hp;
@@ -1157,8 +1463,9 @@ int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_
         src = dst;
     }
     k_merge_partition<Rec><<<r->g_part, 256, 0, r->stream>>>(list, src, r->dAnn, r->splits, r->rem_end, r->rcap);
-    k_merge<Rec><<<r->g_merge, MG_TPB, MG_SMEM, r->stream>>>(r->dP, list, src, (Rec *)d_out, r->dAnn, r->splits,
-                                                             r->rem_end, r->lb_merge, r->rcap, out_cap);
+    k_merge<Rec, false><<<r->g_merge_ann, MG_TPB, MG_SMEM, r->stream>>>(r->dP, list, src, (Rec *)d_out, r->dAnn,
+                                                                        r->splits, r->rem_end, r->lb_merge, r->rcap,
+                                                                        out_cap, r->dP, r->dAnn);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&hs, r->dAnn, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
@@ -1187,7 +1494,7 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
     ddqmc_run host_ctx;
     ddqmc_options o;
     ddqmc_default_options(&o);
-    rc = build_params(&host_ctx, lattice, 0.0, 0.0, 0.0, 0.0, 1.0, 1, initiator_threshold, nullptr, o);
+    rc = build_params(&host_ctx, host_ctx.hp, lattice, 0.0, 0.0, 0.0, 0.0, 1.0, 1, initiator_threshold, nullptr, o);
     if (rc != DDQMC_OK) return rc;
     const RunParams &P = host_ctx.hp;
     if (P.N > NPACK) return DDQMC_ERR_UNSUPPORTED;           // 16-byte records hold one-word keys only
@@ -1213,8 +1520,9 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
     }
     k_merge_partition<Rec><<<g_na_grid[dev][1], 256, 0, stream>>>(list, src, &sc->st, sc->splits, sc->rem_end,
                                                                    NA_MAX_SPAWNS);
-    k_merge<Rec><<<g_na_grid[dev][2], MG_TPB, MG_SMEM, stream>>>(&sc->P, list, src, (Rec *)d_out, &sc->st, sc->splits,
-                                                                 sc->rem_end, sc->lb_merge, NA_MAX_SPAWNS, out_cap);
+    k_merge<Rec, false><<<g_na_grid[dev][2], MG_TPB, MG_SMEM, stream>>>(&sc->P, list, src, (Rec *)d_out, &sc->st,
+                                                                        sc->splits, sc->rem_end, sc->lb_merge,
+                                                                        NA_MAX_SPAWNS, out_cap, &sc->P, &sc->st);
     int64_t mo = 0;
     uint32_t status = 0;
     if (cudaGetLastError() != cudaSuccess ||

@@ -75,6 +75,11 @@ __device__ __forceinline__ K128 shfl_key(const K128 &v, int src) {
     return K128{__shfl_sync(0xFFFFFFFFu, v.lo, src), __shfl_sync(0xFFFFFFFFu, v.hi, src)};
 }
 
+// high word of a key, where a batch keeps the run id
+__device__ __forceinline__ uint64_t key_high(uint64_t k) { return k; }
+__device__ __forceinline__ uint64_t key_high(uint32_t k) { return (uint64_t)k; }
+__device__ __forceinline__ uint64_t key_high(const K128 &k) { return k.hi; }
+
 __device__ __forceinline__ void set_list(Rec &v, uint64_t key) { v.key = key; }
 __device__ __forceinline__ void set_list(Rec &v, uint32_t key) { v.key = (uint64_t)key; }
 __device__ __forceinline__ void set_list(RecW &v, const K128 &key) { v.lo = key.lo; v.hi = key.hi; }
@@ -241,19 +246,20 @@ struct MergeShared {
     int8_t pair_bond[MAXN * MAXN];
 };
 
+// est: the block's shared-memory numerators of the entry's run
 template <typename T>
-__device__ __forceinline__ void add_estimators(MergeShared<T> &s, const RunParams &P, uint64_t i, uint64_t j,
-                                               int32_t re, int32_t im) {
+__device__ __forceinline__ void add_estimators(MergeShared<T> &s, unsigned long long *est, const RunParams &P,
+                                               uint64_t i, uint64_t j, int32_t re, int32_t im) {
     const int N = P.N, B = P.B;
     if (i == j) {
-        atomicAdd(&s.est[0], (unsigned long long)(int64_t)re);
-        atomicAdd(&s.est[1], (unsigned long long)(int64_t)im);
-        atomicAdd(&s.est[2], (unsigned long long)(int64_t)(re < 0 ? -re : re));
+        atomicAdd(&est[0], (unsigned long long)(int64_t)re);
+        atomicAdd(&est[1], (unsigned long long)(int64_t)im);
+        atomicAdd(&est[2], (unsigned long long)(int64_t)(re < 0 ? -re : re));
         for (int k = 0; k < N; ++k)
-            atomicAdd(&s.est[5 + k], (unsigned long long)(int64_t)(((i >> k) & 1ull) ? re : -re));
+            atomicAdd(&est[5 + k], (unsigned long long)(int64_t)(((i >> k) & 1ull) ? re : -re));
         for (int b = 0; b < B; ++b) {
             const bool al = ((i >> s.bond_a[b]) & 1ull) == ((i >> s.bond_b[b]) & 1ull);
-            atomicAdd(&s.est[5 + N + b], (unsigned long long)(int64_t)(al ? re : -re));
+            atomicAdd(&est[5 + N + b], (unsigned long long)(int64_t)(al ? re : -re));
         }
     } else {
         const uint64_t d = i ^ j;
@@ -261,16 +267,16 @@ __device__ __forceinline__ void add_estimators(MergeShared<T> &s, const RunParam
             // sigma^x_k, sigma^y_k (configurations of odd parity: only with a field)
             const int k = __ffsll((long long)d) - 1;
             const int ox = 5 + N + 3 * B + 4;
-            atomicAdd(&s.est[ox + k], (unsigned long long)(int64_t)re);
-            atomicAdd(&s.est[ox + N + k], (unsigned long long)(int64_t)(((i >> k) & 1ull) ? -im : im));
+            atomicAdd(&est[ox + k], (unsigned long long)(int64_t)re);
+            atomicAdd(&est[ox + N + k], (unsigned long long)(int64_t)(((i >> k) & 1ull) ? -im : im));
         } else if (__popcll(d) == 2) {
             const int a = __ffsll((long long)d) - 1;
             const int b2 = 63 - __clzll((long long)d);
             const int b = s.pair_bond[a * N + b2];
             if (b >= 0) {
                 const bool al = ((i >> s.bond_a[b]) & 1ull) == ((i >> s.bond_b[b]) & 1ull);
-                atomicAdd(&s.est[5 + N + B + b], (unsigned long long)(int64_t)re);
-                atomicAdd(&s.est[5 + N + 2 * B + b], (unsigned long long)(int64_t)(al ? -re : re));
+                atomicAdd(&est[5 + N + B + b], (unsigned long long)(int64_t)re);
+                atomicAdd(&est[5 + N + 2 * B + b], (unsigned long long)(int64_t)(al ? -re : re));
             }
         }
     }
@@ -286,11 +292,16 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 template <typename T> struct MergeBlocks { static constexpr int value = 4; };
 template <> struct MergeBlocks<RecW> { static constexpr int value = 3; };
 
-template <typename T>
+// BATCH: the lists hold several runs (run id in the key's high bits); each
+// run has its own initiator threshold (Pr[r]) and estimator numerators
+// (rs[r]), summed per block in dynamic shared memory past MergeShared (nruns
+// x nobs words).  A single run passes Pr = Pp and rs = st (unread).
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(MG_TPB, MergeBlocks<T>::value)
 k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__restrict__ L, const T *__restrict__ S,
         typename ListOf<T>::type *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
-        const int64_t *__restrict__ rem_end, uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
+        const int64_t *__restrict__ rem_end, uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap,
+        const RunParams *__restrict__ Pr, DevState *__restrict__ rs) {
     using TR = RecTraits<T>;
     using KT = typename MergeKey<T>::type;
     using LT = typename ListOf<T>::type;
@@ -308,8 +319,12 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
     const int N = P.N;
     const uint64_t nmask = P.nmask;
     const bool no_init = P.n_a == 0;
+    const int nruns = P.nruns, run_shift = P.run_shift, nobs = P.nobs;
+    unsigned long long *best = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(MergeShared<T>));
 
     for (int q = tid; q < NOBS_MAX; q += MG_TPB) s.est[q] = 0ull;
+    if (BATCH)
+        for (int q = tid; q < nruns * nobs; q += MG_TPB) best[q] = 0ull;
     for (int q = tid; q < P.B; q += MG_TPB) {
         s.bond_m[q] = P.bond_m[q];
         s.bond_a[q] = (int8_t)P.bond_a[q];
@@ -472,7 +487,12 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                 if (ends && owned) {
                     uint64_t ki, kj;
                     key_words(ik[k], nmask, N, ki, kj);
-                    const bool open = run.hasL || no_init || ki == kj;
+                    bool ni = no_init;
+                    if constexpr (BATCH) {
+                        kj &= nmask;
+                        ni = Pr[batch_run(key_high(ik[k]), run_shift, nruns)].n_a == 0;
+                    }
+                    const bool open = run.hasL || ni || ki == kj;
                     const int64_t sre = run.fre + (open ? run.ure : 0);
                     const int64_t sim = run.fim + (open ? run.uim : 0);
                     if (sre != 0 || sim != 0) {
@@ -531,11 +551,19 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                 v.re = ws.val[q].x;
                 v.im = ws.val[q].y;
                 out[ob + q] = v;
-                my_w += iabs64(v.re) + iabs64(v.im);
-                my_m += 1;
                 uint64_t i, j;
                 key_words(ws.key[q], nmask, N, i, j);
-                if (i == j || __popcll(i ^ j) <= 2) add_estimators(s, P, i, j, v.re, v.im);
+                unsigned long long *est = s.est;
+                if constexpr (BATCH) {
+                    j &= nmask;
+                    est = best + (size_t)batch_run(key_high(ws.key[q]), run_shift, nruns) * nobs;
+                    atomicAdd(&est[3], (unsigned long long)(iabs64(v.re) + iabs64(v.im)));
+                    atomicAdd(&est[4], 1ull);
+                } else {
+                    my_w += iabs64(v.re) + iabs64(v.im);
+                    my_m += 1;
+                }
+                if (i == j || __popcll(i ^ j) <= 2) add_estimators(s, est, P, i, j, v.re, v.im);
             }
         }
         __syncwarp();
@@ -552,8 +580,13 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
     }
     if (local_status) atomicOr(&st->status, local_status);
     __syncthreads();
-    for (int q = tid; q < P.nobs; q += MG_TPB)
-        if (s.est[q]) atomicAdd((unsigned long long *)&st->est[q], s.est[q]);
+    if (BATCH) {
+        for (int q = tid; q < nruns * nobs; q += MG_TPB)
+            if (best[q]) atomicAdd((unsigned long long *)&rs[q / nobs].est[q % nobs], best[q]);
+    } else {
+        for (int q = tid; q < P.nobs; q += MG_TPB)
+            if (s.est[q]) atomicAdd((unsigned long long *)&st->est[q], s.est[q]);
+    }
 }
 
 }  // namespace ddq

@@ -373,10 +373,14 @@ __device__ __forceinline__ int seg_select32(const SpawnCtx &c, const uint32_t *r
 // 2B + 2N + k.  same: the child has the parent's type (real / imaginary);
 // a: the sign of the element's non-zero part -- a real parent of sign s makes
 // a child of sign s*a, an imaginary parent one of sign s*a (same type) or
-// -s*a (other type).
+// -s*a (other type).  P: the run's parameters (a single run reads its field
+// settings from the shared-memory copy, a batch from P).
+template <bool BATCH>
 __device__ __forceinline__ void move_child(const SpawnCtx &c, const RunParams &P, uint64_t i, uint64_t j, int m,
                                            uint64_t &ci, uint64_t &cj, bool &same, int &a) {
     const SpawnTables &s = *c.sh;
+    const int field_axis = BATCH ? P.field_axis : s.field_axis;
+    const int sgn_hf = BATCH ? P.sgn_hf : s.sgn_hf;
     ci = i;
     cj = j;
     const int B = c.B, N = c.N;
@@ -394,12 +398,12 @@ __device__ __forceinline__ void move_child(const SpawnCtx &c, const RunParams &P
         const int k = ket ? m - 2 * B : m - 2 * B - N;
         const uint64_t w = ket ? i : j;
         if (ket) ci ^= 1ull << k; else cj ^= 1ull << k;
-        if (s.field_axis == 0) {
+        if (field_axis == 0) {
             same = false;
-            a = ket ? -s.sgn_hf : s.sgn_hf;
+            a = ket ? -sgn_hf : sgn_hf;
         } else {
             same = true;
-            a = ((w >> k) & 1ull) ? s.sgn_hf : -s.sgn_hf;
+            a = ((w >> k) & 1ull) ? sgn_hf : -sgn_hf;
         }
     } else {                         // jump: +gamma
         const int k = m - 2 * B - 2 * N;
@@ -412,25 +416,29 @@ __device__ __forceinline__ void move_child(const SpawnCtx &c, const RunParams &P
 
 // ---- record output ----------------------------------------------------------
 
+// kp: the batch run id already shifted into place (0 for a single run)
 template <typename T>
-__device__ __forceinline__ T make_spawn(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im);
+__device__ __forceinline__ T make_spawn(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im, uint64_t kp);
 template <>
-__device__ __forceinline__ Rec make_spawn<Rec>(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im) {
+__device__ __forceinline__ Rec make_spawn<Rec>(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im,
+                                               uint64_t kp) {
     Rec r;
-    r.key = ((cj << N) | ci) | (flag ? FLAG_BIT : 0ull);
+    r.key = (kp | (cj << N) | ci) | (flag ? FLAG_BIT : 0ull);
     r.re = re;
     r.im = im;
     return r;
 }
 template <>
-__device__ __forceinline__ uint64_t make_spawn<uint64_t>(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im) {
-    return pack_rec((cj << N) | ci, flag, re, im);
+__device__ __forceinline__ uint64_t make_spawn<uint64_t>(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im,
+                                                         uint64_t kp) {
+    return pack_rec(kp | (cj << N) | ci, flag, re, im);
 }
 template <>
-__device__ __forceinline__ RecW make_spawn<RecW>(uint64_t ci, uint64_t cj, int, bool flag, int re, int im) {
+__device__ __forceinline__ RecW make_spawn<RecW>(uint64_t ci, uint64_t cj, int, bool flag, int re, int im,
+                                                 uint64_t kp) {
     RecW r;
     r.lo = ci;
-    r.hi = cj;
+    r.hi = cj | kp;
     r.re = (int32_t)((uint32_t)re << 1) | (flag ? 1 : 0);
     r.im = im;
     return r;
@@ -476,15 +484,16 @@ __device__ __forceinline__ void emit(SpawnShared<T> &s, int warp, const T &r, T 
 // several records.
 template <typename T>
 __device__ __forceinline__ void emit_counts(SpawnShared<T> &s, int warp, uint64_t ci, uint64_t cj, int N, bool flag,
-                                            int cre, int cim, T *out, int64_t cap, DevState *st, int npass) {
+                                            int cre, int cim, T *out, int64_t cap, DevState *st, int npass,
+                                            uint64_t kp) {
     if constexpr (std::is_same<T, Rec>::value) {
-        emit(s, warp, make_spawn<T>(ci, cj, N, flag, cre, cim), out, cap, st, npass);
+        emit(s, warp, make_spawn<T>(ci, cj, N, flag, cre, cim, kp), out, cap, st, npass);
     } else {
         constexpr int LIM = std::is_same<T, RecW>::value ? WK_LIM : PK_LIM;
         while (cre != 0 || cim != 0) {
             const int pr = cre > LIM ? LIM : (cre < -LIM ? -LIM : cre);
             const int pi = cim > LIM ? LIM : (cim < -LIM ? -LIM : cim);
-            emit(s, warp, make_spawn<T>(ci, cj, N, flag, pr, pi), out, cap, st, npass);
+            emit(s, warp, make_spawn<T>(ci, cj, N, flag, pr, pi, kp), out, cap, st, npass);
             cre -= pr;
             cim -= pi;
         }
@@ -537,10 +546,13 @@ __device__ __forceinline__ uint32_t attempt_word(uint4 x0, uint4 &xb, uint32_t &
 
 // Resolve the first n queued spawn draws of the warp, one per lane: the move
 // (ket, bra or jump segment, then the group and the bond inside it), the child
-// configuration and its signed unit, appended as a spawn record.
-template <typename T, typename MT, typename SW, bool FIELD>
-__device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c, int warp, int lane, int n, int N,
-                                            T *out, int64_t cap, DevState *st, int npass) {
+// configuration and its signed unit, appended as a spawn record.  A single
+// run reads its rate tables from shared memory; in a batch (BATCH) each
+// configuration carries its run id and the tables are that run's (Pr).
+template <typename T, typename MT, typename SW, bool FIELD, bool BATCH>
+__device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c, const RunParams *__restrict__ Pr,
+                                            int run_shift, int warp, int lane, int n, int N, T *out, int64_t cap,
+                                            DevState *st, int npass) {
     if (lane < n) {
         const uint64_t v = s.qv[warp][lane];
         const uint32_t meta = s.qm[warp][lane];
@@ -550,6 +562,10 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
         const auto &q = s.ws[warp].le;
         const SW qi = q.i[o], qj = q.j[o];
         const uint64_t qT = q.T[o], qTket = q.Tket[o], qTbra = q.Tbra[o];
+        // initiator flag in bit 0, batch run id above it
+        const int qinit = q.init[o];
+        const int orun = BATCH ? (qinit >> 1) : 0;
+        const RunParams &R = Pr[orun];
         SW ci = qi, cj = qj;
         int cre = 0, cim = 0;
         if (v < qTket + qTbra) {
@@ -558,12 +574,17 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
             const MT X1 = q.X1[o], X2 = q.X2[o];
             const uint64_t cnt8 = ket ? q.gk[o] : q.gb[o];
             const uint64_t vs = ket ? v : v - qTket;
-            const int p = qT <= 0xFFFFFFFFull ? seg_select32<MT>(c, s.urate32, s.uinv, cnt8, A, X1, X2, (uint32_t)vs)
-                                              : seg_select<MT>(c, s.urate8, cnt8, A, X1, X2, vs);
+            int p;
+            if constexpr (BATCH)
+                p = qT <= 0xFFFFFFFFull ? seg_select32<MT>(c, R.urate32, R.uinv, cnt8, A, X1, X2, (uint32_t)vs)
+                                        : seg_select<MT>(c, R.urate8, cnt8, A, X1, X2, vs);
+            else
+                p = qT <= 0xFFFFFFFFull ? seg_select32<MT>(c, s.urate32, s.uinv, cnt8, A, X1, X2, (uint32_t)vs)
+                                        : seg_select<MT>(c, s.urate8, cnt8, A, X1, X2, vs);
             const int k = p >> 1;
             const int other = (p & 1) ? s.dn[k] : s.rn[k];
             const SW m = ((SW)1 << k) | ((SW)1 << other);
-            const int hs = s.sgn_h[mask_bit(A, p)];
+            const int hs = BATCH ? R.sgn_h[mask_bit(A, p)] : s.sgn_h[mask_bit(A, p)];
             const int gsg = ket ? -hs : hs;
             if (ket) ci ^= m; else cj ^= m;
             if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
@@ -576,60 +597,69 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
             uint64_t vf = ket ? vb : vb - qTf;
             int g = 0;
             for (; g < 3; ++g) {
-                const uint64_t w = s.ufrate[g] * (uint64_t)((fcp >> (8 * g)) & 0xFFu);
+                const uint64_t w = (BATCH ? R.ufrate[g] : s.ufrate[g]) * (uint64_t)((fcp >> (8 * g)) & 0xFFu);
                 if (vf < w) break;
                 vf -= w;
             }
             uint32_t idx;
             if (qT <= 0xFFFFFFFFull) {
-                const uint32_t rq = s.ufrate32[g];
-                idx = (uint32_t)((float)(uint32_t)vf * s.ufinv[g]);
+                const uint32_t rq = BATCH ? R.ufrate32[g] : s.ufrate32[g];
+                idx = (uint32_t)((float)(uint32_t)vf * (BATCH ? R.ufinv[g] : s.ufinv[g]));
                 const uint64_t pq = (uint64_t)idx * rq;
                 if (pq > vf) --idx;
                 else if (pq + rq <= vf) ++idx;
             } else {
-                idx = small_quotient(vf, s.ufrate[g]);
+                idx = small_quotient(vf, BATCH ? R.ufrate[g] : s.ufrate[g]);
             }
             SW fm[4];
             field_masks<SW>(c, qi, qj, fm);
             const int k = select_bit(fm[g], idx);
             const SW w = ket ? qi : qj;
+            const int axis = BATCH ? R.field_axis : s.field_axis;
+            const int shf = BATCH ? R.sgn_hf : s.sgn_hf;
             if (ket) ci ^= (SW)1 << k; else cj ^= (SW)1 << k;
-            if (s.field_axis == 0) {             // -i h (ket), +i h (bra): the other type
-                const int gsg = ket ? -s.sgn_hf : s.sgn_hf;
+            if (axis == 0) {                     // -i h (ket), +i h (bra): the other type
+                const int gsg = ket ? -shf : shf;
                 if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
             } else {                             // h (2 s_k - 1): the same type
-                const int a = ((w >> k) & 1) ? s.sgn_hf : -s.sgn_hf;
+                const int a = ((w >> k) & 1) ? shf : -shf;
                 if (part == 0) cre = sig * a; else cim = sig * a;
             }
         } else {
             // jumps share one rate: the site index is the quotient by it
             const uint64_t vj = v - qTket - qTbra - (FIELD ? 2 * q.Tf[o] : 0ull);
+            const uint64_t jq = BATCH ? R.jump_q : c.jump_q;
             uint32_t idx;
             if (qT <= 0xFFFFFFFFull) {
-                idx = (uint32_t)((float)(uint32_t)vj * s.jinv);
-                const uint64_t pq = (uint64_t)idx * c.jump_q;
+                idx = (uint32_t)((float)(uint32_t)vj * (BATCH ? R.jinv : s.jinv));
+                const uint64_t pq = (uint64_t)idx * jq;
                 if (pq > vj) --idx;
-                else if (pq + c.jump_q <= vj) ++idx;
+                else if (pq + jq <= vj) ++idx;
             } else {
-                idx = small_quotient(vj, c.jump_q);
+                idx = small_quotient(vj, jq);
             }
             const int k = select_bit((SW)(qi & qj), idx);
             ci &= ~((SW)1 << k);
             cj &= ~((SW)1 << k);
             if (part == 0) cre = sig; else cim = sig;
         }
-        emit(s, warp, make_spawn<T>((uint64_t)ci, (uint64_t)cj, N, q.init[o] != 0, cre, cim), out, cap, st, npass);
+        const uint64_t kp = BATCH ? (uint64_t)orun << run_shift : 0ull;
+        emit(s, warp, make_spawn<T>((uint64_t)ci, (uint64_t)cj, N, (qinit & 1) != 0, cre, cim, kp), out, cap, st,
+             npass);
     }
     __syncwarp();
 }
 
 // FIELD: the run has the in-plane field's site flips (a separate instantiation
-// keeps them out of the runs without).
-template <typename T, bool FIELD>
+// keeps them out of the runs without).  BATCH: the list holds several runs
+// (run id in the key's high bits, see RunParams::nruns); Pp then holds the
+// batch's shared geometry, Pr[r] and rs[r] run r's rates, shift and death
+// table, and st the shared step counters.  A single run passes Pr = Pp and
+// rs = st (unread).
+template <typename T, bool FIELD, bool BATCH>
 __global__ void __launch_bounds__(SP_TPB, 3)
 k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typename ListOf<T>::type *__restrict__ L,
-              T *__restrict__ out, int64_t cap) {
+              T *__restrict__ out, int64_t cap, const RunParams *__restrict__ Pr, const DevState *__restrict__ rs) {
     // mask and spin-word types of the light path: 32-bit masks for packed
     // records (2N <= 32), 64-bit up to 31 sites, 128-bit (two words) beyond
     using MT = typename LightTypes<T>::MT;
@@ -680,6 +710,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
     const uint64_t nmask = P.nmask;
     const int n_a = P.n_a;
     const int sgn_jz = P.sgn_jz;
+    const int nruns = P.nruns, run_shift = P.run_shift;
     uint32_t local_status = 0;
 
     const int64_t nwarps = (int64_t)gridDim.x * SP_WARPS;
@@ -687,19 +718,26 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
         const int64_t e = chunk * 32 + lane;
         LT rec;
         uint64_t i = 0, j = 0;
+        int crun = 0;                    // batch run of this lane's configuration
         rec.re = 0;
         rec.im = 0;
         if (e < M) {
             rec = L[e];
             if constexpr (WIDE) { i = rec.lo; j = rec.hi; }
             else { i = rec.key & nmask; j = rec.key >> N; }
+            if constexpr (BATCH) {
+                crun = batch_run(j, N, nruns);   // j holds the run id above its N spin bits
+                j &= nmask;
+            }
         }
+        const RunParams &CR = Pr[crun];
         const int64_t nre = iabs64(rec.re), nim = iabs64(rec.im);
         const int64_t nw = nre + nim;
         const bool valid = e < M;
-        const bool heavy = valid && (nw > SP_HEAVY || !uniform);
+        const bool heavy = valid && (nw > SP_HEAVY || !(BATCH ? CR.uniform != 0 : uniform));
         const bool light = valid && !heavy;
-        const bool init = (n_a == 0) || (i == j) || (nw > (int64_t)n_a);
+        const int na_r = BATCH ? CR.n_a : n_a;
+        const bool init = (na_r == 0) || (i == j) || (nw > (int64_t)na_r);
 
         // ---- light configurations: per-configuration setup, one lane each ----
         int nl = 0;
@@ -716,8 +754,9 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 const int cb = popcount(group_mask<MT>(c, Aj, X1, X2, g));
                 gkp |= (uint64_t)ck << (8 * g);
                 gbp |= (uint64_t)cb << (8 * g);
-                Tket += s.urate8[g] * (uint64_t)ck;
-                Tbra += s.urate8[g] * (uint64_t)cb;
+                const uint64_t rg = BATCH ? CR.urate8[g] : s.urate8[g];
+                Tket += rg * (uint64_t)ck;
+                Tbra += rg * (uint64_t)cb;
             }
             uint64_t Tf = 0;
             uint32_t fcp = 0;
@@ -728,10 +767,10 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 for (int g = 0; g < 4; ++g) {
                     const int cf = popcount(fm[g]);
                     fcp |= (uint32_t)cf << (8 * g);
-                    Tf += s.ufrate[g] * (uint64_t)cf;
+                    Tf += (BATCH ? CR.ufrate[g] : s.ufrate[g]) * (uint64_t)cf;
                 }
             }
-            const uint64_t Tall = Tket + Tbra + 2 * Tf + (uint64_t)popcount((SW)(i32 & j32)) * c.jump_q;
+            const uint64_t Tall = Tket + Tbra + 2 * Tf + (uint64_t)popcount((SW)(i32 & j32)) * (BATCH ? CR.jump_q : c.jump_q);
             const uint64_t natt = (Tall + 0xFFFFFFFFull) >> 32;
             q.Ai[lane] = Ai;
             q.Aj[lane] = Aj;
@@ -755,8 +794,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             q.cd[lane] = popcount(i32) + popcount(j32);
             const int dz = 2 * (popcount(Aj) - popcount(Ai));     // zsum(i) - zsum(j)
             q.adz[lane] = dz < 0 ? -dz : dz;
-            q.sgn_d[lane] = (dz == 0) ? 0 : -sgn_jz * (dz > 0 ? 1 : -1);
-            q.init[lane] = init ? 1 : 0;
+            q.sgn_d[lane] = (dz == 0) ? 0 : -(BATCH ? CR.sgn_jz : sgn_jz) * (dz > 0 ? 1 : -1);
+            q.init[lane] = (crun << 1) | (init ? 1 : 0);
             nl = (int)nw;
         }
         s.dre[warp][lane] = 0;
@@ -801,6 +840,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             uint32_t natt = 0;
             uint64_t qT = 0;
             uint4 x = make_uint4(0u, 0u, 0u, 0u), ctr = x;
+            uint32_t wk0 = k0, wk1 = k1;     // Philox key of the owner's run
             if (act) {
                 const auto &q = s.ws[warp].le;
                 const int nre_o = q.nre[owner];
@@ -812,11 +852,25 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 const uint64_t oi = (uint64_t)q.i[owner], oj = (uint64_t)q.j[owner];
                 ctr = make_uint4((uint32_t)oi ^ ((uint32_t)(oi >> 32) * 0x9E3779B9u),
                                  (uint32_t)oj ^ ((uint32_t)(oj >> 32) * 0x85EBCA6Bu), w, (uint32_t)part << 16);
-                x = philox4x32_10(ctr, k0, k1);
                 const int cd = q.cd[owner], adz = q.adz[owner];
-                const int cnt = (int)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
-                const int cc = (int)s.cross_int[adz] + ((uint64_t)x.z < s.cross_frac[adz] ? 1 : 0);
-                const int ddeath = -s.d_sgn[cd] * sig * cnt;
+                int cnt, cc, dsg;
+                if constexpr (BATCH) {
+                    const int orun = q.init[owner] >> 1;
+                    const RunParams &OR = Pr[orun];
+                    const DevState &OS = rs[orun];
+                    wk0 = (uint32_t)OR.seed;
+                    wk1 = (uint32_t)(OR.seed >> 32) ^ (uint32_t)t;
+                    x = philox4x32_10(ctr, wk0, wk1);
+                    cnt = (int)OS.d_int[cd] + ((uint64_t)x.y < OS.d_frac[cd] ? 1 : 0);
+                    cc = (int)OR.cross_int[adz] + ((uint64_t)x.z < OR.cross_frac[adz] ? 1 : 0);
+                    dsg = OS.d_sgn[cd];
+                } else {
+                    x = philox4x32_10(ctr, k0, k1);
+                    cnt = (int)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
+                    cc = (int)s.cross_int[adz] + ((uint64_t)x.z < s.cross_frac[adz] ? 1 : 0);
+                    dsg = s.d_sgn[cd];
+                }
+                const int ddeath = -dsg * sig * cnt;
                 const int dcross = sig * q.sgn_d[owner] * cc;
                 if (part == 0) {
                     if (ddeath) atomicAdd(&s.dre[warp][owner], ddeath);
@@ -837,7 +891,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 bool ev = false;
                 uint64_t v = 0;
                 if (a < natt) {
-                    const uint32_t u = attempt_word(x, xb, blk, a, ctr, k0, k1);
+                    const uint32_t u = BATCH ? attempt_word(x, xb, blk, a, ctr, wk0, wk1)
+                                             : attempt_word(x, xb, blk, a, ctr, k0, k1);
                     v = (uint64_t)u * natt;
                     ev = v < qT;
                 }
@@ -854,7 +909,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 while (qn >= 32 || (fin && qn > 0)) {
                     __syncwarp();
                     const int nd = qn < 32 ? qn : 32;
-                    spawn_drain<T, MT, SW, FIELD>(s, c, warp, lane, nd, N, out, cap, st, npass);
+                    spawn_drain<T, MT, SW, FIELD, BATCH>(s, c, Pr, run_shift, warp, lane, nd, N, out, cap, st, npass);
                     qn -= nd;
                     // move the rest of the queue to the front
                     uint64_t rv = 0;
@@ -883,6 +938,12 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             const int32_t hre = __shfl_sync(0xFFFFFFFFu, rec.re, h);
             const int32_t him = __shfl_sync(0xFFFFFFFFu, rec.im, h);
             const bool hinit = __shfl_sync(0xFFFFFFFFu, init, h);
+            const int hrun = BATCH ? __shfl_sync(0xFFFFFFFFu, crun, h) : 0;
+            const RunParams &HP = BATCH ? Pr[hrun] : P;         // the configuration's run
+            const uint64_t hjump = BATCH ? HP.jump_q : c.jump_q;
+            const uint64_t hkp = BATCH ? (uint64_t)hrun << run_shift : 0ull;
+            const uint32_t hk0 = BATCH ? (uint32_t)HP.seed : k0;
+            const uint32_t hk1 = BATCH ? ((uint32_t)(HP.seed >> 32) ^ (uint32_t)t) : k1;
             // rates of the K moves in move order (group-major inside each bond
             // segment, via ballots over the bonds), then their running sums
             {
@@ -905,7 +966,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                             const int anti = (int)(((w >> a0) ^ (w >> a1)) & 1ull);
                             const int cl = imp_class(c.gk, hd, s.bond_m[b], a0, a1);
                             gq[q] = 4 * anti + cl;
-                            rq[q] = P.rate_q[b][anti][cl];
+                            rq[q] = HP.rate_q[b][anti][cl];
                         }
                     }
                     for (int g = 0; g < 8; ++g) {
@@ -934,7 +995,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                             rq[q] = 0;
                             if (k < N) {
                                 gq[q] = site_class(c.gk, hd, k);
-                                rq[q] = P.frate_q[k][gq[q]];
+                                rq[q] = HP.frate_q[k][gq[q]];
                             }
                         }
                         for (int g = 0; g < 4; ++g) {
@@ -953,7 +1014,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                     }
                 }
                 for (int k = lane; k < N; k += 32) {
-                    s.ws[warp].hv.cum[base + k] = (((hi & hj) >> k) & 1ull) ? c.jump_q : 0ull;
+                    s.ws[warp].hv.cum[base + k] = (((hi & hj) >> k) & 1ull) ? hjump : 0ull;
                     s.ws[warp].hv.mv[base + k] = (int16_t)(2 * B + 2 * N + k);
                 }
                 __syncwarp();
@@ -983,7 +1044,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             const int cd = __popcll(hi) + __popcll(hj);
             const int dz = 2 * (na_j - na_i);
             const int adz = dz < 0 ? -dz : dz;
-            const int sgn_d = (dz == 0) ? 0 : -sgn_jz * (dz > 0 ? 1 : -1);
+            const int sgn_d = (dz == 0) ? 0 : -(BATCH ? HP.sgn_jz : sgn_jz) * (dz > 0 ? 1 : -1);
             int64_t dre = 0, dim = 0;
             for (int part = 0; part < 2; ++part) {
                 const int64_t pop = part == 0 ? hre : him;
@@ -995,15 +1056,24 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                     const uint4 ctr = make_uint4((uint32_t)hi ^ ((uint32_t)(hi >> 32) * 0x9E3779B9u),
                                                  (uint32_t)hj ^ ((uint32_t)(hj >> 32) * 0x85EBCA6Bu), (uint32_t)w,
                                                  (uint32_t)part << 16);
-                    const uint4 x = philox4x32_10(ctr, k0, k1);
-                    const int64_t cnt = (int64_t)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
-                    const int64_t cc = (int64_t)s.cross_int[adz] + ((uint64_t)x.z < s.cross_frac[adz] ? 1 : 0);
-                    if (part == 0) { dre -= (int64_t)s.d_sgn[cd] * sig * cnt; dim += (int64_t)sig * sgn_d * cc; }
-                    else { dim -= (int64_t)s.d_sgn[cd] * sig * cnt; dre -= (int64_t)sig * sgn_d * cc; }
+                    const uint4 x = philox4x32_10(ctr, hk0, hk1);
+                    int64_t cnt, cc, dsg;
+                    if constexpr (BATCH) {
+                        const DevState &HS = rs[hrun];
+                        cnt = (int64_t)HS.d_int[cd] + ((uint64_t)x.y < HS.d_frac[cd] ? 1 : 0);
+                        cc = (int64_t)HP.cross_int[adz] + ((uint64_t)x.z < HP.cross_frac[adz] ? 1 : 0);
+                        dsg = HS.d_sgn[cd];
+                    } else {
+                        cnt = (int64_t)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
+                        cc = (int64_t)s.cross_int[adz] + ((uint64_t)x.z < s.cross_frac[adz] ? 1 : 0);
+                        dsg = s.d_sgn[cd];
+                    }
+                    if (part == 0) { dre -= dsg * sig * cnt; dim += (int64_t)sig * sgn_d * cc; }
+                    else { dim -= dsg * sig * cnt; dre -= (int64_t)sig * sgn_d * cc; }
                     uint4 xb = x;
                     uint32_t blk = 0;
                     for (uint64_t a = 0; a < natt; ++a) {
-                        const uint32_t u = attempt_word(x, xb, blk, a, ctr, k0, k1);
+                        const uint32_t u = attempt_word(x, xb, blk, a, ctr, hk0, hk1);
                         const uint64_t v = (uint64_t)u * natt;
                         if (v >= Ttot) continue;
                         int lo = 0, hi2 = K - 1;
@@ -1014,7 +1084,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                         uint64_t ci, cj;
                         int gsg;
                         bool same;
-                        move_child(c, P, hi, hj, s.ws[warp].hv.mv[lo], ci, cj, same, gsg);
+                        move_child<BATCH>(c, HP, hi, hj, s.ws[warp].hv.mv[lo], ci, cj, same, gsg);
                         // child type (0 real, 1 imaginary) and signed unit
                         const int tgt = same ? part : 1 - part;
                         const int val = (same || part == 0) ? sig * gsg : -sig * gsg;
@@ -1047,8 +1117,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 uint64_t ci, cj;
                 int gsg;
                 bool same;
-                move_child(c, P, hi, hj, s.ws[warp].hv.mv[m], ci, cj, same, gsg);
-                emit_counts(s, warp, ci, cj, N, hinit, cre, cim, out, cap, st, npass);
+                move_child<BATCH>(c, HP, hi, hj, s.ws[warp].hv.mv[m], ci, cj, same, gsg);
+                emit_counts(s, warp, ci, cj, N, hinit, cre, cim, out, cap, st, npass, hkp);
             }
             flush(s, warp, lane, out, cap, st, npass, SP_FLUSH);
         }

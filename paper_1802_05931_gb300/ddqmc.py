@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libddqmc.so")
 
 MAX_SITES = 64
 MAX_BONDS = 128
+MAX_BATCH = 64
 
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CAPACITY", -4: "OVERFLOW", -5: "TIMEOUT",
           -6: "CUDA", -7: "UNSUPPORTED"}
@@ -60,6 +61,14 @@ class ddqmc_estimates(C.Structure):
                 ("sx", C.c_double * MAX_SITES), ("sy", C.c_double * MAX_SITES)]
 
 
+class ddqmc_run_spec(C.Structure):
+    _fields_ = [("Jx", C.c_double), ("Jy", C.c_double), ("Jz", C.c_double), ("gamma", C.c_double),
+                ("dt", C.c_double), ("target_walkers", C.c_int64), ("initiator_threshold", C.c_int32),
+                ("control", C.c_int32), ("seed", C.c_uint64), ("damping", C.c_double), ("shift0", C.c_double),
+                ("n0", C.c_int64), ("t_eq", C.c_int64), ("field_h", C.c_double), ("field_axis", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class ddqmc_state(C.Structure):
     _fields_ = [("t", C.c_int64), ("shift", C.c_double), ("variable", C.c_int32),
                 ("q_prev", C.c_int64), ("t_var", C.c_int64), ("t_eq", C.c_int64),
@@ -70,7 +79,9 @@ EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_as
            "ddqmc_estimators", "ddqmc_raw_estimators", "ddqmc_blocking_moments",
            "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_get_state", "ddqmc_get_counts",
            "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_annihilate",
-           "ddqmc_annihilate_noalloc", "ddqmc_wait_selftest", "ddqmc_destroy", "ddqmc_strerror"]
+           "ddqmc_annihilate_noalloc", "ddqmc_wait_selftest", "ddqmc_create_batch", "ddqmc_batch_estimators",
+           "ddqmc_batch_raw_estimators", "ddqmc_batch_export_walkers", "ddqmc_batch_get_state", "ddqmc_destroy",
+           "ddqmc_strerror"]
 NOALLOC_MAX_SPAWNS = 1 << 18
 NOALLOC_MAX_LIST = 1 << 20
 KERNEL_CLASSES = ["spawn_death", "radix_pass", "merge_partition", "merge", "finalize"]
@@ -109,6 +120,12 @@ def load(path: str = LIB_PATH):
     lib.ddqmc_annihilate.argtypes = [vp, vp, i64, vp, i64, vp, i64, P(i64)]
     lib.ddqmc_annihilate_noalloc.argtypes = [P(ddqmc_lattice), i32, vp, i64, vp, i64, vp, i64, P(i64), vp]
     lib.ddqmc_wait_selftest.argtypes = [vp]
+    lib.ddqmc_create_batch.argtypes = [P(ddqmc_lattice), i32, P(ddqmc_run_spec), P(ddqmc_guide), P(ddqmc_options),
+                                       P(vp)]
+    lib.ddqmc_batch_estimators.argtypes = [vp, i32, P(ddqmc_estimates)]
+    lib.ddqmc_batch_raw_estimators.argtypes = [vp, i32, P(i64), i32, P(i32)]
+    lib.ddqmc_batch_export_walkers.argtypes = [vp, i32, P(u64), P(u64), P(i32), P(i32), i64, P(i64)]
+    lib.ddqmc_batch_get_state.argtypes = [vp, i32, P(ddqmc_state)]
     lib.ddqmc_destroy.argtypes = [vp]
     lib.ddqmc_destroy.restype = None
     lib.ddqmc_strerror.argtypes = [C.c_int]
@@ -189,8 +206,18 @@ def ddqmc_export_walkers(run, out=None):
     """(ket, bra, re, im) of the current list; `out` may hold four arrays of
     those dtypes to write into (reused when long enough, e.g. between steps)."""
     lib = load()
+    return _export(lambda *a: lib.ddqmc_export_walkers(run, *a), out, "ddqmc_export_walkers")
+
+
+def ddqmc_batch_export_walkers(batch, k, out=None):
+    """(ket, bra, re, im) of run k of a batch (as ddqmc_export_walkers)."""
+    lib = load()
+    return _export(lambda *a: lib.ddqmc_batch_export_walkers(batch, int(k), *a), out, "ddqmc_batch_export_walkers")
+
+
+def _export(call, out, what):
     n = C.c_int64()
-    _check(lib.ddqmc_export_walkers(run, None, None, None, None, 0, C.byref(n)), "ddqmc_export_walkers")
+    _check(call(None, None, None, None, 0, C.byref(n)), what)
     m = n.value
     if out is not None and all(len(a) >= m and a.flags.c_contiguous for a in out) and \
             [a.dtype for a in out] == [np.uint64, np.uint64, np.int32, np.int32]:
@@ -200,8 +227,8 @@ def ddqmc_export_walkers(run, out=None):
         bra = np.empty(max(m, 1), dtype=np.uint64)
         re = np.empty(max(m, 1), dtype=np.int32)
         im = np.empty(max(m, 1), dtype=np.int32)
-    _check(lib.ddqmc_export_walkers(run, _p(ket, C.c_uint64), _p(bra, C.c_uint64), _p(re, C.c_int32),
-                                    _p(im, C.c_int32), m, C.byref(n)), "ddqmc_export_walkers")
+    _check(call(_p(ket, C.c_uint64), _p(bra, C.c_uint64), _p(re, C.c_int32), _p(im, C.c_int32), m, C.byref(n)),
+           what)
     return ket[:m], bra[:m], re[:m], im[:m]
 
 
@@ -269,6 +296,37 @@ def ddqmc_annihilate_noalloc(lattice, initiator_threshold, d_list, m, d_spawns, 
                                            C.byref(n), C.c_void_p(stream) if stream else None),
            "ddqmc_annihilate_noalloc")
     return n.value
+
+
+def ddqmc_create_batch(lattice, specs, guide=None, options=None):
+    """specs: a sequence of ddqmc_run_spec (one per run)."""
+    lib = load()
+    arr = (ddqmc_run_spec * len(specs))(*specs)
+    h = C.c_void_p()
+    rc = lib.ddqmc_create_batch(C.byref(lattice), len(specs), arr, C.byref(guide) if guide is not None else None,
+                                C.byref(options) if options is not None else None, C.byref(h))
+    _check(rc, "ddqmc_create_batch")
+    return h
+
+
+def ddqmc_batch_estimators(batch, k):
+    e = ddqmc_estimates()
+    rc = load().ddqmc_batch_estimators(batch, int(k), C.byref(e))
+    return rc, e
+
+
+def ddqmc_batch_raw_estimators(batch, k, cap=1024):
+    out = np.zeros(cap, dtype=np.int64)
+    n = C.c_int32()
+    _check(load().ddqmc_batch_raw_estimators(batch, int(k), _p(out, C.c_int64), cap, C.byref(n)),
+           "ddqmc_batch_raw_estimators")
+    return out[: n.value]
+
+
+def ddqmc_batch_get_state(batch, k):
+    s = ddqmc_state()
+    _check(load().ddqmc_batch_get_state(batch, int(k), C.byref(s)), "ddqmc_batch_get_state")
+    return s
 
 
 def ddqmc_destroy(run):
@@ -350,3 +408,84 @@ class Run:
 
     def counts(self):
         return ddqmc_get_counts(self.h)
+
+
+def run_spec(Jx, Jy, Jz, gamma, dt, target, n_a=0, seed=1, damping=0.05, shift0=-1.0, n0=1000, control=0,
+             t_eq=-1, field_h=0.0, field_axis=0):
+    """A ddqmc_run_spec with the keyword names of ``Run``."""
+    q = ddqmc_run_spec()
+    q.Jx, q.Jy, q.Jz, q.gamma, q.dt = float(Jx), float(Jy), float(Jz), float(gamma), float(dt)
+    q.target_walkers = int(target)
+    q.initiator_threshold = int(n_a)
+    q.control = int(control)
+    q.seed = int(seed) & ((1 << 64) - 1)
+    q.damping = float(damping)
+    q.shift0 = float(shift0)
+    q.n0 = int(n0)
+    q.t_eq = int(t_eq)
+    q.field_h = float(field_h)
+    q.field_axis = int(field_axis)
+    q.reserved = 0
+    return q
+
+
+class Batch:
+    """Several DDQMC runs of one lattice stepped together in one walker store
+    (run id in the key's high bits); runs[k] are the keyword arguments of
+    ``run_spec`` for run k."""
+
+    def __init__(self, Lx, Ly, periodic, runs, guide_kind=0, guide_p=0.0, site_ratio=None,
+                 capacity_entries=0, capacity_spawns=0, stream=None, sm_limit=0):
+        o = ddqmc_default_options()
+        o.capacity_entries = int(capacity_entries)
+        o.capacity_spawns = int(capacity_spawns)
+        o.cuda_stream = stream
+        o.sm_limit = int(sm_limit)
+        g = ddqmc_guide()
+        g.kind = int(guide_kind)
+        g.p = float(guide_p)
+        self._site_r = None
+        if site_ratio is not None:
+            self._site_r = np.ascontiguousarray(site_ratio, dtype=np.float64)
+            g.site_ratio = _p(self._site_r, C.c_double)
+        specs = [run_spec(**r) for r in runs]
+        self.h = ddqmc_create_batch(ddqmc_lattice(int(Lx), int(Ly), int(periodic)), specs, g, o)
+        self.nruns = len(specs)
+        self.N = Lx * Ly
+
+    def close(self):
+        if getattr(self, "h", None):
+            ddqmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        _check(ddqmc_step(self.h, n), "ddqmc_step")
+
+    def step_async(self, n=1):
+        _check(ddqmc_step_async(self.h, n), "ddqmc_step_async")
+
+    def sync(self):
+        _check(ddqmc_sync(self.h), "ddqmc_sync")
+
+    def estimates(self, k):
+        rc, e = ddqmc_batch_estimators(self.h, k)
+        _check(rc, "ddqmc_batch_estimators")
+        return e
+
+    def raw_estimates(self, k):
+        return ddqmc_batch_raw_estimators(self.h, k)
+
+    def export(self, k, out=None):
+        return ddqmc_batch_export_walkers(self.h, k, out)
+
+    def state(self, k):
+        return ddqmc_batch_get_state(self.h, k)
+
+    def totals(self):
+        return ddqmc_get_totals(self.h)

@@ -82,3 +82,23 @@ def _fresh_load(path):
         ddqmc.load(path)
     finally:
         ddqmc._lib = saved
+
+
+def test_batch_parameter_checks_need_no_gpu():
+    """ddqmc_create_batch rejects what it cannot run before touching the
+    device: no runs, too many runs, a bad run parameter, 64 sites (the run id
+    would need an extra key word), and 31 sites with 3 runs (62 spin bits +
+    2 run bits do not fit below the flag bit of a one-word key)."""
+    from paper_1802_05931_gb300 import build as b, ddqmc
+    b.build()
+    base = ddqmc.run_spec(0.9, 1.0, 1.0, 1.0, 0.01, 1000)
+    bad = ddqmc.run_spec(0.9, 1.0, 1.0, 1.0, 0.0, 1000)
+    lat = ddqmc.ddqmc_lattice(2, 2, 0)
+    for lattice, specs, code in ((lat, [], -1),
+                                 (lat, [base] * (ddqmc.MAX_BATCH + 1), -1),
+                                 (lat, [base, bad], -1),
+                                 (ddqmc.ddqmc_lattice(8, 8, 1), [base, base], -7),
+                                 (ddqmc.ddqmc_lattice(31, 1, 0), [base] * 3, -7)):
+        with pytest.raises(ddqmc.DDQMCError) as e:
+            ddqmc.ddqmc_create_batch(lattice, specs)
+        assert e.value.code == code
