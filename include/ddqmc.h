@@ -86,9 +86,10 @@ typedef struct {
 typedef struct ddqmc_run ddqmc_run;
 
 /* Steady-state estimates (ratios of time averages, Sec. III.A) with blocked
- * standard errors, over the steps t >= t_eq.  Sigma^x and sigma^y are zero by
- * the Z2 parity of the dynamics (every move flips an even number of spins
- * across ket and bra), so they are not reported separately. */
+ * standard errors, over the steps t >= t_eq.  Without a field, sigma^x and
+ * sigma^y are zero by the Z2 parity of the dynamics (every move flips an even
+ * number of spins across ket and bra); with the in-plane field of Sec. V.B
+ * they are reported per site and as the magnetisations mx, my. */
 typedef struct {
     int64_t t;                 /* completed steps */
     double shift;              /* current S */
