@@ -516,7 +516,15 @@ def batch_arm(args):
     t0 = time.perf_counter()
     b.step(K)
     res["batch"] = (time.perf_counter() - t0, b.totals()["walker_steps"] - w0)
+    # per-kernel split of the batch step: 32 more steps with CUDA events around
+    # each kernel class (plain launches instead of graph replay)
+    ddqmc.ddqmc_set_timing(b.h, 1)
+    b.step(32)
+    tm = ddqmc.ddqmc_get_timing(b.h)
+    ddqmc.ddqmc_set_timing(b.h, 0)
     b.close()
+    launches_per_step = sum(v[1] for v in tm.values()) / 32.0
+    kern = {k: {"ms_per_step": v[0] / 32.0, "launches_per_step": v[1] / 32.0} for k, v in tm.items()}
     # one after another, each on the whole GPU
     dt_seq, ws_seq = 0.0, 0
     for r in runs:
@@ -552,6 +560,22 @@ def batch_arm(args):
     for m in many:
         m.close()
     rate = {k: v[1] / v[0] for k, v in res.items()}
+    # the oracle beside it: run 0 of the batch (its smallest target), grown
+    # untimed for the warm-up steps, then timed for a bounded sample
+    from oracle import oracle as O
+    r0 = runs[0]
+    cpu = O.OracleRun(Lx, Ly, per, r0["Jx"], r0["Jy"], r0["Jz"], r0["gamma"], r0["dt"], r0["target"],
+                      **{k: v for k, v in r0.items() if k not in ("Jx", "Jy", "Jz", "gamma", "dt", "target")})
+    cpu.step(W)
+    cws, cn, c0 = 0, 0, time.perf_counter()
+    while time.perf_counter() - c0 < args.cpu_seconds / 3.0:
+        cws += int(cpu.estimates_now()[3])
+        cpu.step(1)
+        cn += 1
+    cel = time.perf_counter() - c0
+    cpu_line = {"value": cws / cel, "unit": "walker-steps/s", "cores": 1, "kind": "oracle",
+                "sample": "run 0 of the batch (target %d) alone, %d steps after %d untimed, %.1f s" %
+                          (r0["target"], cn, W, cel)}
     line = {"metric": "walker-steps/s", "value": rate["batch"], "unit": "walker-steps/s", "n_gpus": 1,
             "steps": K, "warmup": W, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "batch of %d runs, %s %s, Jx in [0.8, 1.2], targets log-spaced in "
@@ -560,6 +584,8 @@ def batch_arm(args):
                                     args.batch_target / 8, args.batch_target),
                        "timing": "host clock around the timed steps (each call waits for the device)"},
             "same_walker_steps": res["batch"][1] == res["sequential"][1] == res["streams"][1],
+            "gpu_launches": int(round(launches_per_step * K)),
+            "kernels": kern, "cpu_baseline": cpu_line,
             "arms": {k: {"seconds": v[0], "walker_steps": v[1], "walker_steps_per_s": rate[k]}
                      for k, v in res.items()},
             "batch_over_sequential": rate["batch"] / rate["sequential"],
