@@ -169,16 +169,17 @@ def peak_hbm():
 
 def profile_counters():
     """Per-unit ncu counters of each kernel from the committed summary
-    profiles/kernel_counters.txt (lines '<kernel> <counter> <value>'); a kernel
-    whose code changed after its capture has no line there."""
+    profiles/kernel_counters.txt (lines '<kernel> <counter> <value>', with a
+    fourth word 'previous-build' when the kernel's code changed after the
+    capture).  Returns {(kernel, counter): (value, current)}."""
     out = {}
     path = os.path.join(ROOT, "profiles", "kernel_counters.txt")
     try:
         with open(path) as f:
             for line in f:
                 if line.strip() and not line.startswith("#"):
-                    k, c, v = line.split()[:3]
-                    out[(k, c)] = float(v)
+                    w = line.split()
+                    out[(w[0], w[1])] = (float(w[2]), len(w) < 4 or w[3] != "previous-build")
     except Exception:
         pass
     return out
@@ -328,18 +329,19 @@ def gpu_arm(args, world, rank, local, pg):
     # the committed counters were captured on the 4x4 benchmark workload
     counters = profile_counters() if args.lattice.lower() == "4x4" else {}
     # DRAM traffic per launch: the captured DRAM bytes per algorithmic byte of
-    # the kernel, times this run's algorithmic bytes per launch
-    ratio = counters.get((dom, "dram_bytes_per_alg_byte"))
-    traffic = ratio * alg[dom] if ratio is not None else None
+    # the kernel, times this run's algorithmic bytes per launch (none when the
+    # kernel changed after the capture)
+    ratio, cur = counters.get((dom, "dram_bytes_per_alg_byte"), (None, False))
+    traffic = ratio * alg[dom] if ratio is not None and cur else None
     for k in kern:
-        r = counters.get((k, "dram_bytes_per_alg_byte"))
-        if r is not None and k in alg:
+        r, rc = counters.get((k, "dram_bytes_per_alg_byte"), (None, False))
+        if r is not None and rc and k in alg:
             kern[k]["traffic_bytes_per_launch"] = r * alg[k]
     walkers_per_launch = dws / K
     if dom == "spawn_death" and (dom, "warp_inst_per_walker") in counters:
         # issue-bound kernel: warp instructions per second against the issue
         # rate of every warp scheduler at the SM clock sampled during the run
-        ipw = counters[(dom, "warp_inst_per_walker")]
+        ipw, ipw_cur = counters[(dom, "warp_inst_per_walker")]
         mhz = clocks["sm_mhz"] if clocks else 2070.0
         ach = ipw * walkers_per_launch / (kern[dom]["ms_per_launch"] / 1e3) / 1e9
         pk = SMS * SCHEDULERS_PER_SM * mhz * 1e6 / 1e9
@@ -348,6 +350,9 @@ def gpu_arm(args, world, rank, local, pg):
                     "peak_source": "derived: %d SMs x %d schedulers x %.0f MHz (sampled SM clock)"
                                    % (SMS, SCHEDULERS_PER_SM, mhz),
                     "warp_inst_per_walker": ipw,
+                    "counters": "ncu capture of this build" if ipw_cur else
+                                "warp instructions per walker from the ncu capture of the previous build of the "
+                                "kernel (its code changed since); no traffic until re-captured",
                     "hbm_achieved_gbs": kern[dom]["achieved_gbs"], "hbm_peak_gbs": peak}
     else:
         achieved = kern[dom]["achieved_gbs"]
