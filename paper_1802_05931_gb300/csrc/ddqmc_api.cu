@@ -783,9 +783,6 @@ BlkCell *run_cells(ddqmc_run *r, int k) {
     return r->dBlk + (r->nruns ? (size_t)k * (size_t)r->hp.nobs * LEVELS : (size_t)0);
 }
 
-int state_of(ddqmc_run *r, int k, ddqmc_state *out);
-int estimates_of(ddqmc_run *r, int k, ddqmc_estimates *out);
-
 int raw_estimators_of(ddqmc_run *r, int k, int64_t *host_out, int32_t cap, int32_t *nobs) {
     const int n = run_params(r, k).nobs;
     if (nobs) *nobs = n;
@@ -874,6 +871,145 @@ int export_of(ddqmc_run *r, int k, uint64_t *ket, uint64_t *bra, int32_t *re, in
         });
     }
     return DDQMC_OK;
+}
+
+// State of run k (the run itself when not a batch); the status word is the
+// shared one.
+int state_of(ddqmc_run *r, int k, ddqmc_state *out) {
+    DevState hs;
+    uint32_t status = 0;
+    if (cudaMemcpyAsync(&hs, run_state(r, k), sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&status, &r->dS->status, sizeof(status), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    hs.status = status;
+    out->t = hs.t;
+    out->shift = hs.S;
+    out->variable = hs.variable;
+    out->q_prev = hs.q_prev;
+    out->t_var = hs.t_var;
+    out->t_eq = hs.t_eq;
+    out->entries = hs.M;
+    out->status = r->host_status ? r->host_status : status_code(hs.status);
+    out->status_bits = (int32_t)hs.status;
+    return DDQMC_OK;
+}
+
+// Estimates of run k (the run itself when not a batch).
+int estimates_of(ddqmc_run *r, int k, ddqmc_estimates *out) {
+    const RunParams &P = run_params(r, k);
+    DevState hs;
+    uint32_t status = 0;
+    std::vector<BlkCell> cells((size_t)P.nobs * LEVELS);
+    if (cudaMemcpyAsync(&hs, run_state(r, k), sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaMemcpyAsync(cells.data(), run_cells(r, k), sizeof(BlkCell) * cells.size(), cudaMemcpyDeviceToHost,
+                        r->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&status, &r->dS->status, sizeof(status), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    hs.status = status;
+    std::memset(out, 0, sizeof(*out));
+    const int N = P.N, B = P.B, core = 5 + N + 3 * B;
+    out->t = hs.t;
+    out->shift = hs.S;
+    out->variable = hs.variable;
+    out->t_var = hs.t_var;
+    out->t_eq = hs.t_eq;
+    out->n_samples = hs.n_app;
+    out->walkers = hs.last_est[3];
+    out->entries = hs.M;
+    out->nw = hs.last_est[2];
+    out->trace_re = hs.last_est[0];
+    out->trace_im = hs.last_est[1];
+    out->nsites = N;
+    out->nbonds = B;
+    out->walker_steps = (double)hs.walker_steps;
+    if (hs.t == 0) {            // nothing stepped yet: report the initial list
+        out->walkers = hs.W_cur;
+        out->nw = hs.W_cur;
+        out->trace_re = hs.W_cur;
+    }
+    double R, e;
+    blocked_ratio(cells, core + 0, R, e);
+    out->mz = R / N;
+    out->mz_err = e / N;
+    for (int k = 0; k < N; ++k) {
+        blocked_ratio(cells, 5 + k, R, e);
+        out->sz[k] = R;
+        out->sz_err[k] = e;
+    }
+    bool uniform_w = true;
+    for (int b = 1; b < B; ++b) uniform_w = uniform_w && r->w_bond[b] == r->w_bond[0];
+    for (int b = 0; b < B; ++b) {
+        blocked_ratio(cells, 5 + N + b, R, e);
+        out->bond_zz[b] = R;
+        blocked_ratio(cells, 5 + N + B + b, R, e);
+        out->bond_xx[b] = R / r->w_bond[b];
+        blocked_ratio(cells, 5 + N + 2 * B + b, R, e);
+        out->bond_yy[b] = R / r->w_bond[b];
+    }
+    blocked_ratio(cells, core + 1, R, e);
+    out->zz = B ? R / B : NAN;
+    out->zz_err = B ? e / B : NAN;
+    const double w0 = B ? r->w_bond[0] : 1.0;
+    blocked_ratio(cells, core + 2, R, e);
+    out->xx = B ? R / (B * w0) : NAN;
+    out->xx_err = B ? e / (B * w0) : NAN;
+    blocked_ratio(cells, core + 3, R, e);
+    out->yy = B ? R / (B * w0) : NAN;
+    out->yy_err = B ? e / (B * w0) : NAN;
+    // single-site sigma^x, sigma^y (non-zero only with a field): numerators / site weight
+    {
+        const int ox = core + 4, oy = ox + N;
+        double sxs = 0, sys = 0, exs = 0, eys = 0;
+        for (int k = 0; k < N; ++k) {
+            double Rk, ek;
+            blocked_ratio(cells, ox + k, Rk, ek);
+            out->sx[k] = Rk / r->w_site[k];
+            sxs += out->sx[k];
+            exs += (ek / r->w_site[k]) * (ek / r->w_site[k]);
+            blocked_ratio(cells, oy + k, Rk, ek);
+            out->sy[k] = Rk / r->w_site[k];
+            sys += out->sy[k];
+            eys += (ek / r->w_site[k]) * (ek / r->w_site[k]);
+        }
+        bool uniform_s = true;
+        for (int k = 1; k < N; ++k) uniform_s = uniform_s && r->w_site[k] == r->w_site[0];
+        if (uniform_s) {        // the blocked error of the site sum
+            blocked_ratio(cells, oy + N, R, e);
+            out->mx = R / (N * r->w_site[0]);
+            out->mx_err = e / (N * r->w_site[0]);
+            blocked_ratio(cells, oy + N + 1, R, e);
+            out->my = R / (N * r->w_site[0]);
+            out->my_err = e / (N * r->w_site[0]);
+        } else {
+            out->mx = sxs / N;
+            out->my = sys / N;
+            out->mx_err = std::sqrt(exs) / N;
+            out->my_err = std::sqrt(eys) / N;
+        }
+    }
+    if (!uniform_w && B) {      // per-bond weights differ: average the per-bond estimates
+        double sx = 0, sy = 0, ex = 0, ey = 0;
+        for (int b = 0; b < B; ++b) {
+            sx += out->bond_xx[b];
+            sy += out->bond_yy[b];
+            double Rb, eb;
+            blocked_ratio(cells, 5 + N + B + b, Rb, eb);
+            ex += (eb / r->w_bond[b]) * (eb / r->w_bond[b]);
+            blocked_ratio(cells, 5 + N + 2 * B + b, Rb, eb);
+            ey += (eb / r->w_bond[b]) * (eb / r->w_bond[b]);
+        }
+        out->xx = sx / B;
+        out->yy = sy / B;
+        out->xx_err = std::sqrt(ex) / B;
+        out->yy_err = std::sqrt(ey) / B;
+    }
+    return r->host_status ? r->host_status : status_code(hs.status);
 }
 
 }  // namespace
@@ -1121,37 +1257,6 @@ int ddqmc_batch_get_state(ddqmc_run *r, int32_t run, ddqmc_state *out) {
     return state_of(r, run, out);
 }
 
-}  // extern "C"
-
-namespace {
-
-// State of run k (the run itself when not a batch); the status word is the
-// shared one.
-int state_of(ddqmc_run *r, int k, ddqmc_state *out) {
-    DevState hs;
-    uint32_t status = 0;
-    if (cudaMemcpyAsync(&hs, run_state(r, k), sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
-        cudaMemcpyAsync(&status, &r->dS->status, sizeof(status), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
-        cudaStreamSynchronize(r->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return DDQMC_ERR_CUDA;
-    }
-    hs.status = status;
-    out->t = hs.t;
-    out->shift = hs.S;
-    out->variable = hs.variable;
-    out->q_prev = hs.q_prev;
-    out->t_var = hs.t_var;
-    out->t_eq = hs.t_eq;
-    out->entries = hs.M;
-    out->status = r->host_status ? r->host_status : status_code(hs.status);
-    out->status_bits = (int32_t)hs.status;
-    return DDQMC_OK;
-}
-
-}  // namespace
-
-extern "C" {
 
 int ddqmc_get_counts(ddqmc_run *r, int64_t *spawn_records, int64_t *capacity_entries, int64_t *capacity_spawns) {
     if (!r) return DDQMC_ERR_INVALID_ARG;
@@ -1212,128 +1317,6 @@ int ddqmc_batch_estimators(ddqmc_run *r, int32_t run, ddqmc_estimates *out) {
     return estimates_of(r, run, out);
 }
 
-}  // extern "C"
-
-namespace {
-
-// Estimates of run k (the run itself when not a batch).
-int estimates_of(ddqmc_run *r, int k, ddqmc_estimates *out) {
-    const RunParams &P = run_params(r, k);
-    DevState hs;
-    uint32_t status = 0;
-    std::vector<BlkCell> cells((size_t)P.nobs * LEVELS);
-    if (cudaMemcpyAsync(&hs, run_state(r, k), sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
-        cudaMemcpyAsync(cells.data(), run_cells(r, k), sizeof(BlkCell) * cells.size(), cudaMemcpyDeviceToHost,
-                        r->stream) != cudaSuccess ||
-        cudaMemcpyAsync(&status, &r->dS->status, sizeof(status), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
-        cudaStreamSynchronize(r->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return DDQMC_ERR_CUDA;
-    }
-    hs.status = status;
-    std::memset(out, 0, sizeof(*out));
-    const int N = P.N, B = P.B, core = 5 + N + 3 * B;
-    out->t = hs.t;
-    out->shift = hs.S;
-    out->variable = hs.variable;
-    out->t_var = hs.t_var;
-    out->t_eq = hs.t_eq;
-    out->n_samples = hs.n_app;
-    out->walkers = hs.last_est[3];
-    out->entries = hs.M;
-    out->nw = hs.last_est[2];
-    out->trace_re = hs.last_est[0];
-    out->trace_im = hs.last_est[1];
-    out->nsites = N;
-    out->nbonds = B;
-    out->walker_steps = (double)hs.walker_steps;
-    if (hs.t == 0) {            // nothing stepped yet: report the initial list
-        out->walkers = hs.W_cur;
-        out->nw = hs.W_cur;
-        out->trace_re = hs.W_cur;
-    }
-    double R, e;
-    blocked_ratio(cells, core + 0, R, e);
-    out->mz = R / N;
-    out->mz_err = e / N;
-    for (int k = 0; k < N; ++k) {
-        blocked_ratio(cells, 5 + k, R, e);
-        out->sz[k] = R;
-        out->sz_err[k] = e;
-    }
-    bool uniform_w = true;
-    for (int b = 1; b < B; ++b) uniform_w = uniform_w && r->w_bond[b] == r->w_bond[0];
-    for (int b = 0; b < B; ++b) {
-        blocked_ratio(cells, 5 + N + b, R, e);
-        out->bond_zz[b] = R;
-        blocked_ratio(cells, 5 + N + B + b, R, e);
-        out->bond_xx[b] = R / r->w_bond[b];
-        blocked_ratio(cells, 5 + N + 2 * B + b, R, e);
-        out->bond_yy[b] = R / r->w_bond[b];
-    }
-    blocked_ratio(cells, core + 1, R, e);
-    out->zz = B ? R / B : NAN;
-    out->zz_err = B ? e / B : NAN;
-    const double w0 = B ? r->w_bond[0] : 1.0;
-    blocked_ratio(cells, core + 2, R, e);
-    out->xx = B ? R / (B * w0) : NAN;
-    out->xx_err = B ? e / (B * w0) : NAN;
-    blocked_ratio(cells, core + 3, R, e);
-    out->yy = B ? R / (B * w0) : NAN;
-    out->yy_err = B ? e / (B * w0) : NAN;
-    // single-site sigma^x, sigma^y (non-zero only with a field): numerators / site weight
-    {
-        const int ox = core + 4, oy = ox + N;
-        double sxs = 0, sys = 0, exs = 0, eys = 0;
-        for (int k = 0; k < N; ++k) {
-            double Rk, ek;
-            blocked_ratio(cells, ox + k, Rk, ek);
-            out->sx[k] = Rk / r->w_site[k];
-            sxs += out->sx[k];
-            exs += (ek / r->w_site[k]) * (ek / r->w_site[k]);
-            blocked_ratio(cells, oy + k, Rk, ek);
-            out->sy[k] = Rk / r->w_site[k];
-            sys += out->sy[k];
-            eys += (ek / r->w_site[k]) * (ek / r->w_site[k]);
-        }
-        bool uniform_s = true;
-        for (int k = 1; k < N; ++k) uniform_s = uniform_s && r->w_site[k] == r->w_site[0];
-        if (uniform_s) {        // the blocked error of the site sum
-            blocked_ratio(cells, oy + N, R, e);
-            out->mx = R / (N * r->w_site[0]);
-            out->mx_err = e / (N * r->w_site[0]);
-            blocked_ratio(cells, oy + N + 1, R, e);
-            out->my = R / (N * r->w_site[0]);
-            out->my_err = e / (N * r->w_site[0]);
-        } else {
-            out->mx = sxs / N;
-            out->my = sys / N;
-            out->mx_err = std::sqrt(exs) / N;
-            out->my_err = std::sqrt(eys) / N;
-        }
-    }
-    if (!uniform_w && B) {      // per-bond weights differ: average the per-bond estimates
-        double sx = 0, sy = 0, ex = 0, ey = 0;
-        for (int b = 0; b < B; ++b) {
-            sx += out->bond_xx[b];
-            sy += out->bond_yy[b];
-            double Rb, eb;
-            blocked_ratio(cells, 5 + N + B + b, Rb, eb);
-            ex += (eb / r->w_bond[b]) * (eb / r->w_bond[b]);
-            blocked_ratio(cells, 5 + N + 2 * B + b, Rb, eb);
-            ey += (eb / r->w_bond[b]) * (eb / r->w_bond[b]);
-        }
-        out->xx = sx / B;
-        out->yy = sy / B;
-        out->xx_err = std::sqrt(ex) / B;
-        out->yy_err = std::sqrt(ey) / B;
-    }
-    return r->host_status ? r->host_status : status_code(hs.status);
-}
-
-}  // namespace
-
-extern "C" {
 
 int ddqmc_export_walkers(ddqmc_run *r, uint64_t *ket, uint64_t *bra, int32_t *re, int32_t *im, int64_t cap,
                          int64_t *n) {
