@@ -4,7 +4,9 @@
 // which needs a host round trip: spawn + death/clone, npass onesweep radix
 // passes, merge-path partition, merge + annihilation + estimators, finalize
 // (shift update, blocking, resets).  Every size a kernel needs is read from
-// the device-resident DevState.
+// the device-resident DevState.  A batch of runs (ddqmc_create_batch) issues
+// the same launches once per step for all its runs, with the batch
+// instantiations of the kernels and one finalize block per run.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
