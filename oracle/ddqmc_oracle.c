@@ -30,7 +30,11 @@
  *     and bra site flips of the in-plane field (only when h != 0), then jumps
  *     by site; inside a bond-flip segment grouped by (anti-aligned,
  *     importance class) and in bond order inside a group; inside a site-flip
- *     segment grouped by importance class, in site order inside a group;
+ *     segment grouped by importance class, in site order inside a group.  A
+ *     field at a general angle (axis 2) has an element with a real and an
+ *     imaginary part, so each site flip becomes two moves, one per part: a
+ *     site-flip segment then holds the imaginary-part (cos) moves, then the
+ *     real-part (sin) moves, each grouped as above;
  *   - per-walker categorical draws, which have the joint law of the
  *     binomial + multinomial scheme of Sec. III.B; n_att = ceil(P_tot)
  *     attempts when P_tot > 1;
@@ -47,7 +51,7 @@
 
 #define OR_MAX_SITES 64
 #define OR_MAX_BONDS 128
-#define OR_MAX_MOVES (2 * OR_MAX_BONDS + 3 * OR_MAX_SITES)
+#define OR_MAX_MOVES (2 * OR_MAX_BONDS + 5 * OR_MAX_SITES)
 
 /* error codes returned by or_step / or_import */
 #define OR_OK 0
@@ -73,7 +77,8 @@ typedef struct {
     uint64_t bond_m[OR_MAX_BONDS];
     double Jx, Jy, Jz, gamma, dt;
     double h;               /* in-plane field strength (Sec. V.B), 0 = none */
-    int field_axis;         /* 0: field along x (theta = 0), 1: along y (theta = pi/2) */
+    int field_axis;         /* 0: field along x (theta = 0), 1: along y (theta = pi/2), 2: angle theta */
+    double theta;           /* field angle for axis 2 */
     int64_t target;
     int32_t n_a;
     int control;            /* 0: N_w = sum |Re rho_ii| (paper); 1: sum |re|+|im| */
@@ -88,6 +93,8 @@ typedef struct {
     uint64_t rate_q[OR_MAX_BONDS][2][4];   /* [bond][aligned=0/anti=1][ratio class] */
     uint64_t jump_q;
     uint64_t frate_q[OR_MAX_SITES][4];     /* field flip of site k, [ratio class] */
+    uint64_t frate_c[OR_MAX_SITES][4];     /* axis 2: the imaginary part, |h cos theta| */
+    uint64_t frate_s[OR_MAX_SITES][4];     /* axis 2: the real part, |h sin theta| */
     uint32_t cross_int[2 * OR_MAX_BONDS + 1];
     uint64_t cross_frac[2 * OR_MAX_BONDS + 1];
     double shift_gain;      /* delta / dt */
@@ -274,19 +281,27 @@ static void or_build_rates(or_run *r) {
         }
     }
     r->jump_q = or_q(r->gamma * r->dt);
-    /* field site flips: |A| = |h|, times dt, times the ratio of the flipped site */
+    /* field site flips: |A| = |h|, times dt, times the ratio of the flipped site;
+     * at a general angle the two parts |h cos theta| and |h sin theta| */
     for (int k = 0; k < r->N; ++k) {
-        double base = fabs(r->h) * r->dt;
-        for (int c = 0; c < 4; ++c) {
-            double x = base;
-            if (r->guide_kind == 1) {
-                if (c == 1) x = base * w_off;
-                else if (c == 2) x = base * w_inv;
-            } else if (r->guide_kind == 2) {
-                if (c == 0) x = base * r->site_r[k];
-                else if (c == 1) x = base * (1.0 / r->site_r[k]);
+        for (int part = 0; part < 3; ++part) {
+            double amp = fabs(r->h);
+            if (part == 1) amp = fabs(r->h * cos(r->theta));
+            if (part == 2) amp = fabs(r->h * sin(r->theta));
+            double base = amp * r->dt;
+            for (int c = 0; c < 4; ++c) {
+                double x = base;
+                if (r->guide_kind == 1) {
+                    if (c == 1) x = base * w_off;
+                    else if (c == 2) x = base * w_inv;
+                } else if (r->guide_kind == 2) {
+                    if (c == 0) x = base * r->site_r[k];
+                    else if (c == 1) x = base * (1.0 / r->site_r[k]);
+                }
+                if (part == 0) r->frate_q[k][c] = or_q(x);
+                else if (part == 1) r->frate_c[k][c] = or_q(x);
+                else r->frate_s[k][c] = or_q(x);
             }
-            r->frate_q[k][c] = or_q(x);
         }
     }
     /* on-site cross term: q = dt |Jz| |zsum(i) - zsum(j)| */
@@ -311,7 +326,7 @@ or_run *or_create(int Lx, int Ly, int periodic, double Jx, double Jy, double Jz,
                   double gamma, double dt, int64_t target, int32_t n_a,
                   int guide_kind, double guide_p, const double *site_r,
                   uint64_t seed, double delta, double S0, int64_t n0,
-                  int control, int64_t t_eq_override, double h, int field_axis) {
+                  int control, int64_t t_eq_override, double h, int field_axis, double theta) {
     or_run *r = (or_run *)calloc(1, sizeof(or_run));
     if (!r) return NULL;
     r->Lx = Lx; r->Ly = Ly; r->periodic = periodic;
@@ -322,9 +337,11 @@ or_run *or_create(int Lx, int Ly, int periodic, double Jx, double Jy, double Jz,
     r->t_eq_override = t_eq_override;
     r->h = h;
     r->field_axis = field_axis;
+    r->theta = theta;
     if (or_build_lattice(r) != OR_OK || !(dt > 0.0) || gamma < 0.0 || target <= 0 ||
         n_a < 0 || guide_kind < 0 || guide_kind > 2 || n0 < 0 || n0 > 2147483647 ||
-        (control != 0 && control != 1) || !isfinite(h) || (field_axis != 0 && field_axis != 1)) {
+        (control != 0 && control != 1) || !isfinite(h) || field_axis < 0 || field_axis > 2 ||
+        !isfinite(theta)) {
         free(r);
         return NULL;
     }
@@ -419,7 +436,36 @@ static int or_moves_of(const or_run *r, uint64_t i, uint64_t j, or_move *mv) {
             mv[K].rate = r->rate_q[b][al][cl];
             ++K;
         }
-    if (r->h != 0.0) {
+    if (r->h != 0.0 && r->field_axis == 2) {
+        /* H_ext = h sum_k (cos theta sigma^x_k + sin theta sigma^y_k), Sec. V.B.
+         * Ket flip: A = -i h (cos theta + i sin theta (2 s - 1))
+         *             = -i h cos theta + h sin theta (2 s - 1);
+         * bra flip: A = +i h (cos theta - i sin theta (2 s - 1))
+         *             = +i h cos theta + h sin theta (2 s - 1)
+         * (s the flipped word's bit before the flip).  Each flip is two moves:
+         * the imaginary part, then (after all of them) the real part. */
+        double hc = r->h * cos(r->theta), hs = r->h * sin(r->theta);
+        for (int seg = 0; seg < 2; ++seg)
+            for (int part = 0; part < 2; ++part)
+                for (int g = 0; g < 4; ++g)
+                    for (int k = 0; k < r->N; ++k) {
+                        if (or_site_class(r, i, j, k) != g) continue;
+                        uint64_t w = seg == 0 ? i : j;
+                        mv[K].cket = seg == 0 ? (i ^ (1ull << k)) : i;
+                        mv[K].cbra = seg == 0 ? j : (j ^ (1ull << k));
+                        mv[K].kind = 3 + seg;
+                        if (part == 0) {
+                            mv[K].Are = 0.0;
+                            mv[K].Aim = seg == 0 ? -hc : hc;
+                            mv[K].rate = r->frate_c[k][g];
+                        } else {
+                            mv[K].Are = hs * (2.0 * (double)or_bit(w, k) - 1.0);
+                            mv[K].Aim = 0.0;
+                            mv[K].rate = r->frate_s[k][g];
+                        }
+                        ++K;
+                    }
+    } else if (r->h != 0.0) {
         /* -i H_ext rho and +i rho H_ext, H_ext = h sum_k sigma^x_k (axis 0) or
          * h sum_k sigma^y_k (axis 1), Sec. V.B: one site flipped in the ket
          * (A = -i <i'|H_ext|i>) or in the bra (A = +i <j|H_ext|j'>).  With

@@ -50,7 +50,7 @@ def _load():
         lib.or_create.restype = C.c_void_p
         lib.or_create.argtypes = [C.c_int, C.c_int, C.c_int, dbl, dbl, dbl, dbl, dbl,
                                   i64, i32, C.c_int, dbl, P(dbl), u64, dbl, dbl, i64,
-                                  C.c_int, i64, dbl, C.c_int]
+                                  C.c_int, i64, dbl, C.c_int, dbl]
         lib.or_destroy.argtypes = [C.c_void_p]
         lib.or_step.argtypes = [C.c_void_p, i64]
         lib.or_step.restype = C.c_int
@@ -131,7 +131,7 @@ class OracleRun:
 
     def __init__(self, Lx, Ly, periodic, Jx, Jy, Jz, gamma, dt, target, n_a=0,
                  guide_kind=0, guide_p=0.0, site_ratio=None, seed=1, damping=0.05,
-                 shift0=-1.0, n0=1000, control=0, t_eq=-1, field_h=0.0, field_axis=0):
+                 shift0=-1.0, n0=1000, control=0, t_eq=-1, field_h=0.0, field_axis=0, field_theta=0.0):
         lib = _load()
         self._lib = lib
         self._site_r = None
@@ -142,7 +142,8 @@ class OracleRun:
         h = lib.or_create(int(Lx), int(Ly), int(periodic), float(Jx), float(Jy), float(Jz),
                           float(gamma), float(dt), int(target), int(n_a), int(guide_kind),
                           float(guide_p), rp, int(seed) & ((1 << 64) - 1), float(damping),
-                          float(shift0), int(n0), int(control), int(t_eq), float(field_h), int(field_axis))
+                          float(shift0), int(n0), int(control), int(t_eq), float(field_h), int(field_axis),
+                          float(field_theta))
         if not h:
             raise ValueError("oracle rejected the parameters")
         self._h = C.c_void_p(h)
@@ -257,7 +258,7 @@ class OracleRun:
 
     # --- element access for the Liouvillian pins ----------------------------
     def moves(self, i, j):
-        K = 2 * self.B + 3 * self.N
+        K = 2 * self.B + 5 * self.N
         ck = np.zeros(K, dtype=np.uint64)
         cb = np.zeros(K, dtype=np.uint64)
         kind = np.zeros(K, dtype=np.int32)

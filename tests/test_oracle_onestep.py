@@ -49,7 +49,10 @@ CASES = [
     (0.1, 0.5, 0, 0.0, None, 0.8, 0, 2500),      # in-plane field along x
     (0.1, 0.5, 2, 0.0, [0.5, 0.7, 0.9, 0.6], -0.6, 1, 2500),   # along y, site-product guide
     (0.1, 0.2, 1, 1.2, None, 0.5, 1, 2500),
+    (0.1, 0.5, 0, 0.0, None, 0.7, 2, 2500),      # general angle 0.7: real and imaginary parts
+    (0.1, 0.5, 2, 0.0, [0.5, 0.7, 0.9, 0.6], -0.6, 2, 2500),
 ]
+THETA = 0.7                                     # the angle of the axis-2 cases
 
 
 @pytest.mark.parametrize("dt,S,kind,p,r_site,h,axis,ns", CASES)
@@ -57,7 +60,8 @@ def test_one_step_is_unbiased(dt, S, kind, p, r_site, h, axis, ns):
     Jx, Jy, Jz, gamma = 0.9, 1.0, 1.3, 1.0
     d = 16
     run = O.OracleRun(2, 2, 0, Jx, Jy, Jz, gamma, dt, 10 ** 15, n_a=0, guide_kind=kind,
-                      guide_p=p, site_ratio=r_site, seed=11, shift0=S, field_h=h, field_axis=axis)
+                      guide_p=p, site_ratio=r_site, seed=11, shift0=S, field_h=h, field_axis=axis,
+                      field_theta=THETA)
     st = _sorted(STATE)
     ket = [e[0] for e in st]; bra = [e[1] for e in st]; re = [e[2] for e in st]; im = [e[3] for e in st]
     acc = np.zeros((d, d), dtype=complex)
@@ -74,7 +78,8 @@ def test_one_step_is_unbiased(dt, S, kind, p, r_site, h, axis, ns):
         acc2r += rho.real ** 2
         acc2i += rho.imag ** 2
     mean = acc / ns
-    L = E.liouvillian(2, 2, 0, Jx, Jy, Jz, gamma, S=S, h=h, theta=axis * np.pi / 2).toarray()
+    L = E.liouvillian(2, 2, 0, Jx, Jy, Jz, gamma, S=S, h=h,
+                      theta=THETA if axis == 2 else axis * np.pi / 2).toarray()
     if kind:
         w = _weights(d, kind, p, r_site, 4).reshape(-1, order="F")
         off = ~np.eye(d * d, dtype=bool)

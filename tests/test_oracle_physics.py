@@ -154,3 +154,28 @@ def test_ness_2x2_within_blocked_errors(golden_dir):
         assert abs(R - np.mean(g[name])) < 4 * err, (name, R, err)
     # the shift settles at the steady-state eigenvalue 0 (Sec. III.A)
     assert abs(run.state()["S"]) < 0.2
+
+
+@pytest.mark.slow
+def test_ness_2x2_field_at_a_general_angle():
+    """2x2 open with the in-plane field h = 0.3 at theta = 0.7 (Sec. V.B: both
+    sigma^x and sigma^y in H_ext, so every field flip has a real and an
+    imaginary part): M_x, M_y and M_z within 3.5 blocked errors of the exact
+    null vector of the same Liouvillian (dense SVD, computed here).  N_w
+    target 3000, seed 7, 1.5 x 10^4 steps."""
+    h, theta = 0.3, 0.7
+    L = E.liouvillian(2, 2, 0, 0.9, 1.0, 1.0, 1.0, h=h, theta=theta)
+    rho, _, _ = E.ness_dense(L, 16)
+    ref = {name: np.mean([E.expect(rho, E.site_op(op, k, 4)).real for k in range(4)])
+           for name, op in (("x", E.SX), ("y", E.SY), ("z", E.SZ))}
+    run = O.OracleRun(2, 2, 0, 0.9, 1.0, 1.0, 1.0, 0.01, 3000, seed=7, field_h=h, field_axis=2,
+                      field_theta=theta)
+    run.step(15000)
+    ser = run.series()
+    assert len(ser) > 12000
+    lay = O.observable_layout(4, 4)
+    for name in ("x", "y", "z"):
+        R, err, _ = Bk.blocked_ratio(ser[:, lay["sum_" + name]], ser[:, 0] * 4)
+        assert abs(R - ref[name]) < 3.5 * err, (name, R, err, ref[name])
+    # both in-plane components are sizeable at this angle
+    assert abs(ref["x"]) > 0.05 and abs(ref["y"]) > 0.05
