@@ -71,3 +71,29 @@ def test_trace_run_records_every_interval():
     assert rows[1] == dict(t=10, shift=5.0, trace=10, nw=20, walkers=30, entries=40, spawn_records=50)
     csv = WF.rows_to_csv(rows).splitlines()
     assert csv[0] == "t,shift,trace,nw,walkers,entries,spawn_records" and csv[2].startswith("10,5.0,")
+
+
+def test_angular_average_from_the_tensor_equals_the_direct_average():
+    """chi_av of Sec. V.B read as the angle average of the response to a
+    field at each angle (reading 22 takes it from the 2 x 2 tensor of the x
+    and y responses).  On the exact 2x2 steady state (dense null vectors of
+    the Liouvillian with the field at each angle) both agree to O(h)."""
+    from oracle import exact as E
+    h = 1e-3
+
+    def mag(theta):
+        L = E.liouvillian(2, 2, 0, 0.9, 1.0, 1.0, 1.0, h=h, theta=theta)
+        rho, _, _ = E.ness_dense(L, 16)
+        return np.array([np.mean([E.expect(rho, E.site_op(op, k, 4)).real for k in range(4)])
+                          for op in (E.SX, E.SY)])
+
+    chi = np.column_stack([mag(0.0) / h, mag(np.pi / 2) / h])
+    n = 48
+    thetas = (np.arange(n) + 0.5) * (2 * np.pi / n)
+    direct = [np.hypot(*mag(t)) / h for t in thetas]
+    # the tensor predicts the response at every angle (linear response)
+    for t, d in zip(thetas[::8], direct[::8]):
+        pred = chi @ np.array([np.cos(t), np.sin(t)])
+        assert np.hypot(*pred) == pytest.approx(d, rel=5e-3, abs=1e-6)
+    assert WF.angular_average(chi, n=n) == pytest.approx(float(np.mean(direct)), rel=5e-3)
+    assert WF.angular_average(chi) > 0.05          # a finite in-plane susceptibility
