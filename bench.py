@@ -350,8 +350,8 @@ def gpu_arm(args, world, rank, local, pg):
                     "peak_source": "derived: %d SMs x %d schedulers x %.0f MHz (sampled SM clock)"
                                    % (SMS, SCHEDULERS_PER_SM, mhz),
                     "warp_inst_per_walker": ipw,
-                    "counters": "ncu capture of this build" if ipw_cur else
-                                "warp instructions per walker from the ncu capture of the previous build of the "
+                    "counters": "ncu capture of the current kernel code" if ipw_cur else
+                                "warp instructions per walker from the ncu capture of the previous version of the "
                                 "kernel (its code changed since); no traffic until re-captured",
                     "hbm_achieved_gbs": kern[dom]["achieved_gbs"], "hbm_peak_gbs": peak}
     else:
