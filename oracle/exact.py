@@ -115,19 +115,21 @@ def ness_sparse(L, d, tol=1e-11, dt=None, max_time=2000.0, check_every=50):
     Classical fourth-order Runge-Kutta propagation of d rho/dt = L~ rho from
     |down..down><down..down|.  Its step map is a polynomial p(dt L~) with
     p(0) = 1, so the null vector is an exact fixed point and every other mode
-    (Re lambda < 0) decays when dt |lambda| is inside the stability region;
-    propagation stops when ||L~ rho|| / ||rho|| < tol."""
+    (Re lambda < 0) decays when dt lambda is inside the stability region;
+    propagation stops when ||L~ rho|| / ||rho|| < tol.
+
+    Step: the eigenvalues of a Lindblad generator lie in the closed left
+    half-plane, every eigenvalue is bounded by the largest absolute row sum
+    (Gershgorin), and the left half-disc of radius 2.5 lies inside the
+    classical RK4 stability region, so dt = 2.5 / max_row_sum |L~| is stable
+    for every mode.  (An estimate of the spectral radius by power iteration
+    is not a bound: on a three-site ring it came out at half the true radius
+    and the propagation diverged.)"""
     keep = sector_indices(d)
     Ls = L[keep][:, keep].tocsr()
     n = len(keep)
     if dt is None:
-        v = np.ones(n, dtype=complex)
-        nv = 1.0
-        for _ in range(40):
-            v = Ls @ v
-            nv = np.linalg.norm(v)
-            v /= nv
-        dt = 2.0 / (1.25 * nv)
+        dt = 2.5 / float(abs(Ls).sum(axis=1).max())
     x = np.zeros(n, dtype=complex)
     x[0] = 1.0                          # vec index 0 is |0><0| = all down
     t = 0.0
