@@ -6,9 +6,10 @@ initiator rule, estimators, shift update) on the 4x4 periodic XYZ lattice.
 Workload: 4x4 periodic XYZ lattice (N = 16, 32 bonds), Jx = 0.9, Jy = Jz = 1,
 gamma = 1, dt = 0.005, initiator threshold n_a = 3, site-product importance
 guide with uniform site ratio exp(-1.5), the shift switched on when the total
-population sum |re|+|im| first reaches 10^8, seed 3.  The run is grown from
-1000 walkers on |down..down><down..down| (untimed), settles, then W warm-up
-steps and K timed steps follow.  Every input is synthetic: the dynamics
+population sum |re|+|im| first reaches 1.75x10^7, after which the population
+overshoots and is held near 10^8 walkers, seed 3.  The run is grown from
+1000 walkers on |down..down><down..down| (untimed), settles for 1000 steps
+after the shift switches on, then W warm-up steps and K timed steps follow.  Every input is synthetic: the dynamics
 generate the walker lists.
 
 One JSON line on stdout (rank 0).  ``--impl reference`` times the CPU oracle
@@ -36,9 +37,12 @@ METRIC = "walker-steps/s"
 UNIT = "walker-steps/s"
 WORKLOAD = dict(Lx=4, Ly=4, periodic=1, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, n_a=3,
                 guide_kind=2, guide_p=1.5, control=1, seed=3)
-def workload_name(target=1e8, lattice="4x4"):
+SWITCH_ON = 1.75e7       # total walkers at which the shift switches on (held population ~1e8)
+
+
+def workload_name(target=SWITCH_ON, lattice="4x4"):
     return ("%s periodic XYZ, Jx=0.9 Jy=Jz=1 gamma=1, dt=0.005, n_a=3, site-product guide exp(-1.5), "
-            "total-walker shift target %.0e, seed 3" % (lattice, target)).replace("e+0", "e")
+            "shift switched on at %.3g total walkers, seed 3" % (lattice, target))
 
 
 def parse():
@@ -47,16 +51,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--target", type=float, default=1e8, help="total walkers at which the shift switches on")
-    ap.add_argument("--settle", type=int, default=150, help="untimed steps after the shift switches on")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--target", type=float, default=SWITCH_ON,
+                    help="total walkers at which the shift switches on (the population then overshoots to "
+                         "about 5.7 times this and is held there)")
+    ap.add_argument("--settle", type=int, default=1000, help="untimed steps after the shift switches on")
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-target", type=float, default=2e4, help="shift target of the oracle sample")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--lattice", default="4x4",
                     help="Lx x Ly periodic lattice of the same workload (the benchmark line is 4x4; "
                          "6x6 and 8x8 use two-word keys)")
     ap.add_argument("--capacity-factor", type=float, default=3.2,
-                    help="walker-list capacity per target walker (spawn capacity 1.4 times that)")
+                    help="walker-list capacity per switch-on walker (spawn capacity 1.4 times that)")
     ap.add_argument("--batch", type=int, default=0,
                     help="time N runs stepped as one batch against the same runs one at a time and on "
                          "concurrent streams (walker-steps/s), instead of the single-run benchmark")
@@ -171,7 +177,10 @@ def profile_counters():
     """Per-unit ncu counters of each kernel from the committed summary
     profiles/kernel_counters.txt (lines '<kernel> <counter> <value>', with a
     fourth word 'previous-build' when the kernel's code changed after the
-    capture).  Returns {(kernel, counter): (value, current)}."""
+    capture): warp_inst_per_walker, dram_bytes_per_kernel_byte (DRAM bytes
+    over the bytes the kernel must move in its layout) and, for the
+    partition, dram_bytes_per_position (per merged position, entries +
+    records).  Returns {(kernel, counter): (value, current)}."""
     out = {}
     path = os.path.join(ROOT, "profiles", "kernel_counters.txt")
     try:
@@ -264,12 +273,15 @@ def gpu_arm(args, world, rank, local, pg):
                     site_ratio=[math.exp(-w["guide_p"])] * N, seed=w["seed"] + rank, control=w["control"],
                     capacity_entries=int(cf * target) + (1 << 20),
                     capacity_spawns=int(1.4 * cf * target) + (1 << 20), stream=stream.cuda_stream)
-    # grow and settle (untimed)
+    # grow and settle (untimed; whole blocks of 32 steps replay a CUDA graph)
     while True:
-        run.step(25)
+        run.step(32)
         st = run.state()
-        if st.variable and st.t >= st.t_var + args.settle:
+        if st.variable:
             break
+    left = st.t_var + args.settle - st.t
+    if left > 0:
+        run.step(left)
     run.step(max(args.warmup, 3))
     tot0 = ddqmc.ddqmc_get_totals(run.h)
     ddqmc.ddqmc_set_timing(run.h, 1)
@@ -309,59 +321,92 @@ def gpu_arm(args, world, rank, local, pg):
     ws_all = reduce_sum(pg, dws)
     value = ws_all / (t_max / 1e3)
 
-    # roofline of the dominant kernel: algorithmic bytes per launch / average launch time
-    # spawn records are 8 bytes when 2N <= 32 (packed layout), 16 up to 31
-    # sites, 24 beyond; list entries 16 bytes up to 31 sites, 24 beyond
+    # Bytes per launch.  "kernel": what each kernel must move in the layout it
+    # uses (8-byte packed spawn records when 2N <= 32, 16-byte records up to 31
+    # sites, 24-byte beyond; list entries 16 bytes up to 31 sites, 24 beyond).
+    # "alg": the method's algorithmic minimum with 16-byte records (24 above
+    # 31 sites): spawn/death reads the list, writes the populations back and
+    # writes the spawns; annihilation reads the spawns and the list once and
+    # writes the merged list once.
     rb = 8 if 2 * N <= 32 else (16 if N <= 31 else 24)
     lb = 16 if N <= 31 else 24
-    alg = {"spawn_death": ((lb + 8) * dM + rb * dR) / K,
-           "radix_pass": 2 * rb * dR / K,
-           "merge": (lb * (dM + dMn) + rb * dR) / K}
+    kb = {"spawn_death": ((lb + 8) * dM + rb * dR) / K,
+          "radix_pass": 2 * rb * dR / K,
+          "merge": (lb * (dM + dMn) + rb * dR) / K}
+    spawn_alg = ((lb + 8) * dM + lb * dR) / K
+    ann_alg = lb * (dR + dM + dMn) / K
+    positions = (dM + dR) / K
     kern = {}
+    tot_ms = max(sum(v[0] for v in timing.values()), 1e-30)
+    peak, peak_src = peak_hbm()
     for k, (kms, n) in timing.items():
         if n:
-            kern[k] = {"ms_per_launch": kms / n, "launches": n, "share": kms / max(sum(v[0] for v in timing.values()), 1e-30)}
-            if k in alg:
-                kern[k]["alg_bytes_per_launch"] = alg[k]
-                kern[k]["achieved_gbs"] = alg[k] / (kms / n / 1e3) / 1e9
-    dom = max((k for k in kern if k in alg), key=lambda k: timing[k][0])
-    peak, peak_src = peak_hbm()
-    # the committed counters were captured on the 4x4 benchmark workload
+            kern[k] = {"ms_per_launch": kms / n, "launches": n, "share": kms / tot_ms}
+            if k in kb:
+                kern[k]["kernel_bytes_per_launch"] = kb[k]
+                kern[k]["kernel_gbs"] = kb[k] / (kms / n / 1e3) / 1e9
+                kern[k]["kernel_frac"] = kern[k]["kernel_gbs"] / peak
+    dom = max((k for k in kern if k in kb), key=lambda k: timing[k][0])
+    # committed per-unit ncu counters of the 4x4 benchmark workload
     counters = profile_counters() if args.lattice.lower() == "4x4" else {}
-    # DRAM traffic per launch: the captured DRAM bytes per algorithmic byte of
-    # the kernel, times this run's algorithmic bytes per launch (none when the
-    # kernel changed after the capture)
-    ratio, cur = counters.get((dom, "dram_bytes_per_alg_byte"), (None, False))
-    traffic = ratio * alg[dom] if ratio is not None and cur else None
+
+    def dram(k):
+        """DRAM bytes per launch of kernel k from the committed counters (None if absent or stale)."""
+        if k == "merge_partition":
+            r, cur = counters.get((k, "dram_bytes_per_position"), (None, False))
+            return r * positions if r is not None and cur else None
+        r, cur = counters.get((k, "dram_bytes_per_kernel_byte"), (None, False))
+        return r * kb[k] if r is not None and cur and k in kb else None
+
     for k in kern:
-        r, rc = counters.get((k, "dram_bytes_per_alg_byte"), (None, False))
-        if r is not None and rc and k in alg:
-            kern[k]["traffic_bytes_per_launch"] = r * alg[k]
+        d = dram(k)
+        if d is not None:
+            kern[k]["dram_bytes_per_launch"] = d
+            kern[k]["dram_frac"] = d / (kern[k]["ms_per_launch"] / 1e3) / 1e9 / peak
     walkers_per_launch = dws / K
-    if dom == "spawn_death" and (dom, "warp_inst_per_walker") in counters:
+    dms = kern[dom]["ms_per_launch"]
+    traffic = dram(dom)
+    hbm_src = ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s")
+    ipw, ipw_cur = counters.get((dom, "warp_inst_per_walker"), (None, False))
+    if dom == "spawn_death" and ipw is not None and ipw_cur:
         # issue-bound kernel: warp instructions per second against the issue
         # rate of every warp scheduler at the SM clock sampled during the run
-        ipw, ipw_cur = counters[(dom, "warp_inst_per_walker")]
         mhz = clocks["sm_mhz"] if clocks else 2070.0
-        ach = ipw * walkers_per_launch / (kern[dom]["ms_per_launch"] / 1e3) / 1e9
+        ach = ipw * walkers_per_launch / (dms / 1e3) / 1e9
         pk = SMS * SCHEDULERS_PER_SM * mhz * 1e6 / 1e9
         roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": pk, "unit": "Gwarp-inst/s",
                     "frac": ach / pk, "traffic": traffic,
                     "peak_source": "derived: %d SMs x %d schedulers x %.0f MHz (sampled SM clock)"
                                    % (SMS, SCHEDULERS_PER_SM, mhz),
-                    "warp_inst_per_walker": ipw,
-                    "counters": "ncu capture of the current kernel code" if ipw_cur else
-                                "warp instructions per walker from the ncu capture of the previous version of the "
-                                "kernel (its code changed since); no traffic until re-captured",
-                    "hbm_achieved_gbs": kern[dom]["achieved_gbs"], "hbm_peak_gbs": peak}
+                    "warp_inst_per_walker": ipw, "thread_inst_per_walker": 32.0 * ipw,
+                    "counters": "ncu capture of the current kernel code (profiles/kernel_counters.txt)",
+                    "alg_bytes_per_launch": spawn_alg,
+                    "hbm_alg_gbs": spawn_alg / (dms / 1e3) / 1e9, "hbm_peak_gbs": peak,
+                    "hbm_alg_frac": spawn_alg / (dms / 1e3) / 1e9 / peak}
     else:
-        achieved = kern[dom]["achieved_gbs"]
+        alg_dom = spawn_alg if dom == "spawn_death" else kb[dom]
+        achieved = alg_dom / (dms / 1e3) / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": traffic,
-                    "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
-                    else "fallback 6.8 TB/s"}
-    sortmerge_ms = sum(timing[k][0] for k in ("radix_pass", "merge_partition", "merge")) / K
-    sortmerge_bytes = alg["radix_pass"] * (timing["radix_pass"][1] / K) + alg["merge"]
+                    "frac": achieved / peak, "traffic": traffic, "peak_source": hbm_src,
+                    "alg_bytes_per_launch": alg_dom,
+                    "counters": "no current instruction count for this kernel" if dom == "spawn_death" else None}
+    sm_keys = ("radix_pass", "merge_partition", "merge")
+    sortmerge_ms = sum(timing[k][0] for k in sm_keys if k in timing) / K
+    sm_s = sortmerge_ms / 1e3
+    moved = kb["radix_pass"] * (timing["radix_pass"][1] / K) + kb["merge"]
+    sm_dram = [dram(k) for k in sm_keys]
+    sm_dram_bytes = (sum(d * timing[k][1] / K for d, k in zip(sm_dram, sm_keys))
+                     if all(d is not None for d in sm_dram) else None)
+    sort_merge = {"ms_per_step": sortmerge_ms,
+                  "alg_min_bytes_per_step": ann_alg,
+                  "frac_alg_min": ann_alg / sm_s / 1e9 / peak,
+                  "kernel_bytes_per_step": moved,
+                  "frac_kernel_bytes": moved / sm_s / 1e9 / peak,
+                  "dram_bytes_per_step": sm_dram_bytes,
+                  "frac_dram": sm_dram_bytes / sm_s / 1e9 / peak if sm_dram_bytes else None,
+                  "note": "frac_dram: DRAM bytes of the radix passes, the partition and the merge (committed ncu "
+                          "counters per unit x this run's units) over their CUDA-event time; frac_alg_min: "
+                          "16 B x (spawn records + entries read + entries written) over the same time"}
     # end to end through the C-ABI with host buffers: import, step, export, estimators
     e2e = None
     if args.e2e_steps > 0:
@@ -410,9 +455,7 @@ def gpu_arm(args, world, rank, local, pg):
                        "l2": "inputs larger than L2 (walker list and spawn buffer are GBs)",
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline,
-            "sort_merge": {"ms_per_step": sortmerge_ms, "alg_bytes_per_step": sortmerge_bytes,
-                           "achieved_gbs": sortmerge_bytes / (sortmerge_ms / 1e3) / 1e9,
-                           "frac": sortmerge_bytes / (sortmerge_ms / 1e3) / 1e9 / peak},
+            "sort_merge": sort_merge,
             "step_ms": {"median": statistics.median(step_ms), "p99": step_ms[min(len(step_ms) - 1,
                                                                                    int(0.99 * len(step_ms)))],
                         "min": step_ms[0], "max": step_ms[-1]},

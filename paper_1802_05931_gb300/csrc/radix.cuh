@@ -134,9 +134,19 @@ k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict
         }
         if (lane == 31) s.scan_tmp[warp] = x;
         __syncthreads();
-        uint32_t pre = 0;
-        for (int w = 0; w < warp; ++w) pre += s.scan_tmp[w];
+        uint32_t pre = 0, all = 0;
+        for (int w = 0; w < RX_WARPS; ++w) {
+            if (w < warp) pre += s.scan_tmp[w];
+            all += s.scan_tmp[w];
+        }
         s.bucket[tid] = pre + x - v;
+        // the counted records must be exactly the records to sort; otherwise
+        // the bucket offsets would point outside the output (every block reads
+        // the same histogram, so every block leaves here together)
+        if ((int64_t)all != R) {
+            if (blockIdx.x == 0 && tid == 0) atomicOr(&st->status, ST_CAPACITY | ST_CAP_SPAWN);
+            return;
+        }
         __syncthreads();
     }
 
@@ -238,11 +248,18 @@ k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict
         __syncthreads();
         int64_t nvalid = R - t0;
         if (nvalid > TILE) nvalid = TILE;
+        bool bad = false;
         for (int q = tid; q < nvalid; q += RX_TPB) {
             const T v = s.stage[q];
             const uint32_t d = TR::digit(v, shift);
-            out[s.gbase[d] + q] = v;
+            const int64_t o = s.gbase[d] + q;
+            // offsets come from the histograms and the look-back; one that
+            // falls outside [0, R) (inconsistent counts, or a timed-out wait)
+            // is reported, never written
+            if ((uint64_t)o < (uint64_t)R) out[o] = v;
+            else bad = true;
         }
+        if (bad) atomicOr(&st->status, ST_CAPACITY | ST_CAP_SPAWN);
         __syncthreads();
     }
 }

@@ -137,8 +137,13 @@ def test_single_run_line_has_every_key(fake_gpu, capsys, monkeypatch):
     assert r["bound"] in ("alu", "hbm") and r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     # counters marked previous-build give no traffic
     c = bench.profile_counters()
-    if not c.get(("spawn_death", "dram_bytes_per_alg_byte"), (0, False))[1]:
+    if not c.get((r["kernel"], "dram_bytes_per_kernel_byte"), (0, False))[1]:
         assert r["traffic"] is None
+    sm = line["sort_merge"]
+    for k in ("ms_per_step", "alg_min_bytes_per_step", "frac_alg_min", "kernel_bytes_per_step",
+              "frac_kernel_bytes", "dram_bytes_per_step", "frac_dram"):
+        assert k in sm, k
+    assert sm["frac_alg_min"] <= sm["frac_kernel_bytes"]
     cpu = line["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and "sample" in cpu
     e2e = line["e2e"]

@@ -95,3 +95,43 @@ def test_annihilate_rejects_two_word_keys(env):
     with pytest.raises(ddqmc.DDQMCError) as e:
         ddqmc.ddqmc_annihilate(run.h, x.data_ptr(), 1, x.data_ptr(), 1, x.data_ptr(), 64)
     assert e.value.code == -7          # DDQMC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("part,sign", [("re", 1), ("re", -1), ("im", 1)])
+def test_annihilate_int32_overflow_is_reported(env, part, sign):
+    """A list entry 10 walkers short of the int32 limit that receives 20 more
+    through its spawn records leaves the int32 range: the call reports
+    DDQMC_ERR_OVERFLOW instead of a wrapped population, and the oracle's
+    annihilation reports its overflow code on the same arrays.  A following
+    call on the same run with valid records succeeds."""
+    torch, ddqmc = env
+    N = 16
+    run = ddqmc.Run(4, 4, 1, 0.9, 1.0, 1.0, 1.0, 0.005, 10 ** 6, n_a=3, control=1,
+                    capacity_entries=1 << 16, capacity_spawns=1 << 16)
+    L = np.zeros(3, dtype=RC.REC)
+    L["key"] = np.array([5, (7 << N) | 3, (9 << N) | 9], dtype=np.uint64)
+    L["re"] = [1, 0, -2]
+    L["im"] = [0, 0, 1]
+    L[part][1] = sign * (2 ** 31 - 10)
+    S = np.zeros(6, dtype=RC.REC)
+    S["key"] = np.uint64((7 << N) | 3) | RC.FLAG
+    S[part] = sign * 4
+    S["key"][5] = np.uint64(11 << N | 2)         # an unrelated record
+    S[part][5] = 0
+    S["re"][5] = 1
+    dl, ds = _dev(torch, L), _dev(torch, S)
+    out = torch.empty(16 * 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ddqmc.DDQMCError) as e:
+        ddqmc.ddqmc_annihilate(run.h, dl.data_ptr(), len(L), ds.data_ptr(), len(S), out.data_ptr(), 16)
+    assert e.value.code == -4                     # DDQMC_ERR_OVERFLOW
+    lk, lb, lr, li, _ = RC.split(L, N)
+    sk, sb, sr, si, sf = RC.split(S, N)
+    with pytest.raises(RuntimeError, match=r"\(-4\)"):
+        O.annihilate(lk, lb, lr, li, sk, sb, sr, si, sf, 3)
+    # the same entry with records summing to +4 stays in range
+    S[part][3] = -sign * 4
+    S[part][4] = -sign * 4
+    got, ref = run_case(env, run, N, 3, L, S)
+    assert np.array_equal(got, ref)
+    k = np.nonzero(got["key"] == np.uint64((7 << N) | 3))[0][0]
+    assert int(got[part][k]) == sign * (2 ** 31 - 6)
