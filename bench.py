@@ -6,7 +6,7 @@ initiator rule, estimators, shift update) on the 4x4 periodic XYZ lattice.
 Workload: 4x4 periodic XYZ lattice (N = 16, 32 bonds), Jx = 0.9, Jy = Jz = 1,
 gamma = 1, dt = 0.005, initiator threshold n_a = 3, site-product importance
 guide with uniform site ratio exp(-1.5), the shift switched on when the total
-population sum |re|+|im| first reaches 1.75x10^7, after which the population
+population sum |re|+|im| first reaches 1.5x10^7, after which the population
 overshoots and is held near 10^8 walkers, seed 3.  The run is grown from
 1000 walkers on |down..down><down..down| (untimed), settles for 1000 steps
 after the shift switches on, then W warm-up steps and K timed steps follow.  Every input is synthetic: the dynamics
@@ -37,7 +37,7 @@ METRIC = "walker-steps/s"
 UNIT = "walker-steps/s"
 WORKLOAD = dict(Lx=4, Ly=4, periodic=1, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, n_a=3,
                 guide_kind=2, guide_p=1.5, control=1, seed=3)
-SWITCH_ON = 1.75e7       # total walkers at which the shift switches on (held population ~1e8)
+SWITCH_ON = 1.5e7        # total walkers at which the shift switches on (held population ~1e8)
 
 
 def workload_name(target=SWITCH_ON, lattice="4x4"):
