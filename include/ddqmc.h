@@ -289,6 +289,7 @@ int ddqmc_batch_get_state(ddqmc_run *batch, int32_t run, ddqmc_state *out);
  * key = bra << N | ket; in spawn records bit 63 of the key is set when the
  * parent was an initiator.  One-word keys only: runs of more than 31 sites
  * return UNSUPPORTED.
+ * Every record pointer must be 16-byte aligned (INVALID_ARG otherwise).
  *   d_list   m records, strictly increasing keys, no flag bit (device memory);
  *   d_spawns nsp records in any order (device memory, read only);
  *   d_out    room for out_cap records (device memory, must not overlap the
@@ -299,8 +300,8 @@ int ddqmc_batch_get_state(ddqmc_run *batch, int32_t run, ddqmc_state *out);
  *            are dropped.
  * Uses the run's lattice and initiator threshold and the run's spawn buffers
  * as scratch (so it must not overlap a ddqmc_step_async of the same run);
- * issued on the run's stream and waited for.  Errors: INVALID_ARG,
- * CAPACITY (nsp above the run's spawn capacity, m above its list capacity,
+ * issued on the run's stream and waited for.  Errors: INVALID_ARG (a null
+ * or misaligned pointer, a negative size), CAPACITY (nsp above the run's spawn capacity, m above its list capacity,
  * or more than out_cap merged entries), OVERFLOW, TIMEOUT, UNSUPPORTED
  * (more than 31 sites), CUDA. */
 int ddqmc_annihilate(ddqmc_run *run, const void *d_list, int64_t m, const void *d_spawns, int64_t nsp,

@@ -77,6 +77,12 @@ struct ddqmc_run {
 
 namespace {
 
+// 16-byte records are moved with 16-byte vector accesses and bulk copies:
+// every record pointer a caller passes must be 16-byte aligned.
+bool records_aligned(const void *a, const void *b, const void *c) {
+    return (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 15u) == 0u;
+}
+
 int status_code(uint32_t st) {
     if (st & ST_TIMEOUT) return DDQMC_ERR_TIMEOUT;
     if (st & ST_OVERFLOW) return DDQMC_ERR_OVERFLOW;
@@ -470,10 +476,12 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     rc |= dalloc(&r->dBlk, blk_cells);
     const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
     const size_t ssize = r->wide ? sizeof(RecW) : sizeof(Rec);   // standalone annihilation uses 16-byte Rec
-    rc |= dalloc_bytes(&r->L[0], lsize * (size_t)mcap);
-    rc |= dalloc_bytes(&r->L[1], lsize * (size_t)mcap);
-    rc |= dalloc_bytes(&r->Sp[0], ssize * (size_t)rcap);
-    rc |= dalloc_bytes(&r->Sp[1], ssize * (size_t)rcap);
+    // 64 bytes past the last record: the merge's bulk copies widen each range
+    // to 16-byte boundaries, so 24-byte records are read up to 15 bytes past it
+    rc |= dalloc_bytes(&r->L[0], lsize * (size_t)mcap + 64);
+    rc |= dalloc_bytes(&r->L[1], lsize * (size_t)mcap + 64);
+    rc |= dalloc_bytes(&r->Sp[0], ssize * (size_t)rcap + 64);
+    rc |= dalloc_bytes(&r->Sp[1], ssize * (size_t)rcap + 64);
     rc |= dalloc(&r->lb_radix, (size_t)rtiles * 256);
     rc |= dalloc(&r->lb_merge, (size_t)mtiles);
     rc |= dalloc(&r->splits, (size_t)mtiles + 1);
@@ -1420,7 +1428,7 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
 int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_spawns, int64_t nsp, void *d_out,
                      int64_t out_cap, int64_t *m_out) {
     if (!r || !m_out || m < 0 || nsp < 0 || out_cap < 0 || (m > 0 && !d_list) || (nsp > 0 && !d_spawns) ||
-        (out_cap > 0 && !d_out))
+        (out_cap > 0 && !d_out) || !records_aligned(d_list, d_spawns, d_out))
         return DDQMC_ERR_INVALID_ARG;
     *m_out = 0;
     if (r->hp.N > NPACK || r->nruns) return DDQMC_ERR_UNSUPPORTED;   // one-word keys of a single run only
@@ -1465,7 +1473,7 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
                              int64_t m, const void *d_spawns, int64_t nsp, void *d_out, int64_t out_cap,
                              int64_t *m_out, void *cuda_stream) {
     if (!lattice || !m_out || m < 0 || nsp < 0 || out_cap < 0 || (m > 0 && !d_list) || (nsp > 0 && !d_spawns) ||
-        (out_cap > 0 && !d_out))
+        (out_cap > 0 && !d_out) || !records_aligned(d_list, d_spawns, d_out))
         return DDQMC_ERR_INVALID_ARG;
     *m_out = 0;
     if (nsp > NA_MAX_SPAWNS || m > NA_MAX_LIST) return DDQMC_ERR_CAPACITY;

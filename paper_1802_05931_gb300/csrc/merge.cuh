@@ -11,13 +11,14 @@
 // every kept entry is added to the integer estimator numerators on the way out.
 //
 // Work is cut into tiles of MG_TILE merged positions, one tile per warp at a
-// time, with no block-wide synchronisation: the warp takes a ticket, loads
-// its tile, merges MG_IPT positions per lane, sums runs with a segmented scan
-// over the lanes (the partition kernel has already located the spawn records
-// that continue the tile's last run past its end; the warp sums them with
-// coalesced loads), and finds its output offset by a warp-parallel decoupled
-// look-back over earlier tiles.  Runs whose head lies in an earlier tile are
-// left to that tile.
+// time, with no block-wide synchronisation: the warp takes a ticket, brings
+// its tile's list and spawn ranges into shared memory with two bulk copies,
+// merges MG_IPT positions per lane in registers, sums runs as differences of
+// a warp-wide prefix sum (the partition kernel has already located the spawn
+// records that continue the tile's last run past its end; the warp sums them
+// with coalesced loads), and finds its output offset by a warp-parallel
+// decoupled look-back over earlier tiles.  Runs whose head lies in an earlier
+// tile are left to that tile.
 #pragma once
 
 #include "common.cuh"
@@ -171,75 +172,24 @@ __global__ void k_merge_partition(const typename ListOf<T>::type *__restrict__ L
     }
 }
 
-// Aggregate of a partial run for the segmented reduction: h = a run head lies
-// in the aggregated range, hasL = that head is the L_t entry, f = L_t
-// population plus initiator records, u = non-initiator records.
-struct SegAgg {
-    int32_t h, hasL;
-    int64_t fre, fim, ure, uim;
-};
 
-__device__ __forceinline__ SegAgg seg_identity() {
-    SegAgg a;
-    a.h = 0; a.hasL = 0; a.fre = 0; a.fim = 0; a.ure = 0; a.uim = 0;
-    return a;
-}
-
-__device__ __forceinline__ SegAgg seg_head(uint32_t fromL) {
-    SegAgg a = seg_identity();
-    a.h = 1;
-    a.hasL = (int32_t)fromL;
-    return a;
-}
-
-__device__ __forceinline__ void seg_add(SegAgg &a, int2 v, uint32_t counted) {
-    if (counted) { a.fre += v.x; a.fim += v.y; }
-    else { a.ure += v.x; a.uim += v.y; }
-}
-
-// a followed by b
-__device__ __forceinline__ SegAgg seg_combine(const SegAgg &a, const SegAgg &b) {
-    if (b.h) return b;
-    SegAgg r;
-    r.h = a.h; r.hasL = a.hasL;
-    r.fre = a.fre + b.fre; r.fim = a.fim + b.fim; r.ure = a.ure + b.ure; r.uim = a.uim + b.uim;
-    return r;
-}
-
-__device__ __forceinline__ SegAgg seg_shfl_up(const SegAgg &a, int off) {
-    SegAgg r;
-    r.h = __shfl_up_sync(0xFFFFFFFFu, a.h, off);
-    r.hasL = __shfl_up_sync(0xFFFFFFFFu, a.hasL, off);
-    r.fre = __shfl_up_sync(0xFFFFFFFFu, a.fre, off);
-    r.fim = __shfl_up_sync(0xFFFFFFFFu, a.fim, off);
-    r.ure = __shfl_up_sync(0xFFFFFFFFu, a.ure, off);
-    r.uim = __shfl_up_sync(0xFFFFFFFFu, a.uim, off);
-    return r;
-}
-
-// Exclusive segmented scan over the lanes of a warp.
-__device__ __forceinline__ SegAgg seg_warp_exclusive(const SegAgg &mine, int lane) {
-    SegAgg inc = mine;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const SegAgg o = seg_shfl_up(inc, off);
-        if (lane >= off) inc = seg_combine(o, inc);
-    }
-    SegAgg exc = seg_shfl_up(inc, 1);
-    if (lane == 0) exc = seg_identity();
-    return exc;
-}
-
+// Shared memory of one warp tile: the tile's list and spawn ranges as raw
+// records (one bulk copy each, the element before each range included), later
+// the tile's output entries.
 template <typename T>
-struct MergeWarp {
-    typename MergeKey<T>::type key[MG_TILE];   // L keys, then S keys; later the output keys
-    int2 val[MG_TILE];                          // (re, im) of the same elements; later the output populations
-    uint32_t sflag[(MG_TILE + 31) / 32];        // initiator flags of the S elements, bit q of word q/32
+struct MergeTile {
+    using LT = typename ListOf<T>::type;
+    static constexpr int LS = (int)sizeof(LT), SS = (int)sizeof(T);
+    static constexpr int MAXS = LS > SS ? LS : SS;
+    // two ranges of at most MG_TILE + 1 records in all, each widened by at most 30 bytes
+    static constexpr int BYTES = ((MG_TILE + 2) * MAXS + 64 + 15) & ~15;
 };
 
 template <typename T>
 struct MergeShared {
-    MergeWarp<T> w[MG_WARPS];
+    alignas(128) unsigned char buf[MG_WARPS][MergeTile<T>::BYTES];
+    uint64_t bar[MG_WARPS];
+    int64_t rem[MG_WARPS][4];         // sums of the records past the tile: initiator re, im; others re, im
     unsigned long long est[NOBS_MAX];
     uint64_t bond_m[MAXB];
     int8_t bond_a[MAXB], bond_b[MAXB];
@@ -287,15 +237,39 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
     return v;
 }
+// resident blocks per SM the merge is compiled for (85 registers a thread at
+// 3; 128-bit keys need more)
+template <typename T> struct MergeBlocks { static constexpr int value = 3; };
+template <> struct MergeBlocks<RecW> { static constexpr int value = 2; };
 
-// resident blocks per SM the merge is compiled for: 128-bit keys need more registers
-template <typename T> struct MergeBlocks { static constexpr int value = 4; };
-template <> struct MergeBlocks<RecW> { static constexpr int value = 3; };
+__device__ __forceinline__ int64_t shfl_up_i64(int64_t v, int off) {
+    return (int64_t)__shfl_up_sync(0xFFFFFFFFu, (long long)v, off);
+}
+
+// configuration (ket, bra) of a merge key, the batch run id stripped
+template <typename KT, bool BATCH>
+__device__ __forceinline__ bool key_diagonal(const KT &k, uint64_t nmask, int N) {
+    uint64_t i, j;
+    key_words(k, nmask, N, i, j);
+    if (BATCH) j &= nmask;
+    return i == j;
+}
 
 // BATCH: the lists hold several runs (run id in the key's high bits); each
 // run has its own initiator threshold (Pr[r]) and estimator numerators
 // (rs[r]), summed per block in dynamic shared memory past MergeShared (nruns
 // x nobs words).  A single run passes Pr = Pp and rs = st (unread).
+//
+// One warp tile of MG_TILE merged positions: lane 0 takes a ticket and
+// issues two bulk copies (list range [a0 - 1, a1), spawn range [b0 - 1, b1),
+// each widened to 16-byte boundaries) completing on the warp's mbarrier; each
+// lane merges its MG_IPT positions in registers; whether a run holds its L_t
+// entry travels from the lane of its head by ballot and shuffle; run sums are
+// differences of one warp-wide int64 prefix sum of the counted contributions
+// (L_t entries and initiator records always, other records when the run is
+// open: L_t entry present, diagonal, or no initiator rule).  The outputs are
+// staged in the tile buffer and written with one bulk store (16-byte list
+// records) after the output offset is found by decoupled look-back.
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(MG_TPB, MergeBlocks<T>::value)
 k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__restrict__ L, const T *__restrict__ S,
@@ -305,6 +279,8 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
     using TR = RecTraits<T>;
     using KT = typename MergeKey<T>::type;
     using LT = typename ListOf<T>::type;
+    constexpr int LS = MergeTile<T>::LS, SS = MergeTile<T>::SS;
+    constexpr bool BULK_OUT = LS == 16;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MergeShared<T> &s = *reinterpret_cast<MergeShared<T> *>(smem_raw);
     const RunParams &P = *Pp;
@@ -331,8 +307,12 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
         s.bond_b[q] = (int8_t)P.bond_b[q];
     }
     for (int q = tid; q < N * N; q += MG_TPB) s.pair_bond[q] = P.pair_bond[q];
+    if (lane == 0) mbar_init(&s.bar[warp], 1);
     __syncthreads();
-    MergeWarp<T> &ws = s.w[warp];
+    unsigned char *buf = s.buf[warp];
+    uint64_t *bar = &s.bar[warp];
+    uint32_t phase = 0;
+    bool store_pending = false;          // lane 0: a bulk store still reads buf
     int64_t my_w = 0, my_m = 0;
     uint32_t local_status = 0;
 
@@ -345,39 +325,20 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
         const int64_t d1 = (d0 + MG_TILE < tot) ? d0 + MG_TILE : tot;
         const int64_t a0 = splits[tile], a1 = splits[tile + 1], rem_e = rem_end[tile + 1];
         const int64_t b0 = d0 - a0, b1 = d1 - a1;
-        const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
-        // key of the merged element before the tile
-        KT pk{};
-        int hp = 0;
+        const int na = (int)(a1 - a0), nb = (int)(b1 - b0), nt = na + nb;
+        // byte ranges of the two copies (from the element before each range)
+        const int64_t gl0 = ((a0 > 0 ? a0 - 1 : 0) * LS) & ~15ll, gl1 = (a1 * LS + 15) & ~15ll;
+        const int64_t gs0 = ((b0 > 0 ? b0 - 1 : 0) * SS) & ~15ll, gs1 = (b1 * SS + 15) & ~15ll;
+        const uint32_t lbytes = (uint32_t)(gl1 - gl0), sbytes = (uint32_t)(gs1 - gs0);
+        __syncwarp();                    // every lane is done with the previous tile's buffer
         if (lane == 0) {
-            if (a0 > 0) { pk = list_key<KT>(L[a0 - 1]); hp = 1; }
-            if (b0 > 0) {
-                const KT k2 = spawn_key<KT>(S[b0 - 1]);
-                if (!hp || k2 > pk) pk = k2;
-                hp = 1;
-            }
+            if (store_pending) { bulk_wait_read(); store_pending = false; }
+            fence_proxy_async();
+            mbar_arrive_expect_tx(bar, lbytes + sbytes);
+            if (lbytes) bulk_load(buf, reinterpret_cast<const unsigned char *>(L) + gl0, lbytes, bar);
+            if (sbytes) bulk_load(buf + lbytes, reinterpret_cast<const unsigned char *>(S) + gs0, sbytes, bar);
         }
-        pk = shfl_key(pk, 0);
-        hp = __shfl_sync(0xFFFFFFFFu, hp, 0);
-        // load the tile's L and S elements; the S flags go to a bit mask
-        for (int q = lane; q < na; q += 32) {
-            const LT v = L[a0 + q];
-            ws.key[q] = list_key<KT>(v);
-            ws.val[q] = make_int2(v.re, v.im);
-        }
-        for (int q0 = 0; q0 < nb; q0 += 32) {
-            const int q = q0 + lane;
-            bool f = false;
-            if (q < nb) {
-                const T v = S[b0 + q];
-                ws.key[na + q] = spawn_key<KT>(v);
-                ws.val[na + q] = make_int2(TR::re(v), TR::im(v));
-                f = TR::flag(v);
-            }
-            const unsigned fb = __ballot_sync(0xFFFFFFFFu, f);
-            if (lane == 0) ws.sflag[q0 >> 5] = fb;
-        }
-        // spawn records past the tile end that continue its last run
+        // spawn records past the tile end that continue its last run (plain loads, overlapping the copies)
         int64_t rf0 = 0, rf1 = 0, ru0 = 0, ru1 = 0;
         for (int64_t q = b1 + lane; q < rem_e; q += 32) {
             const T g = S[q];
@@ -393,117 +354,169 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                 ru1 += __shfl_xor_sync(0xFFFFFFFFu, ru1, off);
             }
         }
-        __syncwarp();
-        const KT *kL = ws.key;
-        const KT *kS = ws.key + na;
-        const int2 *vL = ws.val;
-        const int2 *vS = ws.val + na;
+        if (lane == 0) {
+            s.rem[warp][0] = rf0;
+            s.rem[warp][1] = rf1;
+            s.rem[warp][2] = ru0;
+            s.rem[warp][3] = ru1;
+        }
+        const bool has_lprev = a0 > 0, has_sprev = b0 > 0;
+        const bool arrived = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        if (!__all_sync(0xFFFFFFFFu, arrived)) {
+            // the copies did not complete: report, give them one more bounded
+            // wait (the buffer must not be left while they may still land), stop
+            if (lane == 0) atomicOr(&st->status, ST_TIMEOUT);
+            mbar_wait_bounded(bar, phase ^ 1u);
+            break;
+        }
+        // Lt[q] = L[a0 + q], St[q] = S[b0 + q] for q >= -1
+        const LT *Lt = reinterpret_cast<const LT *>(buf + (a0 * LS - gl0));
+        const T *St = reinterpret_cast<const T *>(buf + lbytes + (b0 * SS - gs0));
 
         // ---- 1. merge: this lane's MG_IPT merged positions, in registers ----
         const int dloc = lane * MG_IPT;
-        const int nt = na + nb;
         KT ik[MG_IPT];
         int2 iv[MG_IPT];
         uint32_t hmask = 0, lmask = 0, fmask = 0;   // run heads, elements of L_t, initiator records
         int nk = 0;
+#pragma unroll
+        for (int k = 0; k < MG_IPT; ++k) { ik[k] = KT{}; iv[k] = make_int2(0, 0); }
         if (dloc < nt) {
             int lo = dloc > nb ? dloc - nb : 0;
             int hi = dloc < na ? dloc : na;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (kL[mid] <= kS[dloc - 1 - mid]) lo = mid + 1;
+                if (list_key<KT>(Lt[mid]) <= spawn_key<KT, T>(St[dloc - 1 - mid])) lo = mid + 1;
                 else hi = mid;
             }
             int ia = lo, ib = dloc - lo;
+            // the merged element before this lane's first position
             KT prev{};
             bool hprev = false;
-            if (dloc == 0) { prev = pk; hprev = hp != 0; }
-            else {
-                if (ia > 0) { prev = kL[ia - 1]; hprev = true; }
-                if (ib > 0) {
-                    const KT k2 = kS[ib - 1];
-                    if (!hprev || k2 > prev) prev = k2;
-                    hprev = true;
-                }
+            if (ia > 0 || has_lprev) { prev = list_key<KT>(Lt[ia - 1]); hprev = true; }
+            if (ib > 0 || has_sprev) {
+                const KT k2 = spawn_key<KT, T>(St[ib - 1]);
+                if (!hprev || k2 > prev) prev = k2;
+                hprev = true;
             }
             nk = nt - dloc < MG_IPT ? nt - dloc : MG_IPT;
 #pragma unroll
             for (int k = 0; k < MG_IPT; ++k) {
-                ik[k] = KT{};
-                iv[k] = make_int2(0, 0);
                 if (k < nk) {
                     bool fromL;
                     if (ia >= na) fromL = false;
                     else if (ib >= nb) fromL = true;
-                    else fromL = kL[ia] <= kS[ib];
-                    const KT key = fromL ? kL[ia] : kS[ib];
+                    else fromL = list_key<KT>(Lt[ia]) <= spawn_key<KT, T>(St[ib]);
+                    KT key;
+                    if (fromL) {
+                        const LT v = Lt[ia];
+                        key = list_key<KT>(v);
+                        iv[k] = make_int2(v.re, v.im);
+                        lmask |= 1u << k;
+                        ++ia;
+                    } else {
+                        const T v = St[ib];
+                        key = spawn_key<KT, T>(v);
+                        iv[k] = make_int2(TR::re(v), TR::im(v));
+                        if (TR::flag(v)) fmask |= 1u << k;
+                        ++ib;
+                    }
                     ik[k] = key;
-                    iv[k] = fromL ? vL[ia] : vS[ib];
                     if (!hprev || key != prev) hmask |= 1u << k;
-                    if (fromL) lmask |= 1u << k;
-                    else if ((ws.sflag[ib >> 5] >> (ib & 31)) & 1u) fmask |= 1u << k;
                     prev = key;
                     hprev = true;
-                    if (fromL) ++ia; else ++ib;
                 }
             }
-        } else {
-#pragma unroll
-            for (int k = 0; k < MG_IPT; ++k) { ik[k] = KT{}; iv[k] = make_int2(0, 0); }
         }
-        // ---- 2. segmented reduction of the runs over the lanes ---------------
-        SegAgg tail = seg_identity();
+        // ---- 2. runs: L_t entry of the open run, counted contributions ------
+        // the run open at this lane's start has its head in the nearest
+        // earlier lane with a head (none: it began in an earlier tile and is
+        // that tile's to finish)
+        const int last_head = hmask ? 31 - __clz(hmask) : 0;
+        const uint32_t last_head_L = (lmask >> last_head) & 1u;
+        const unsigned heads = __ballot_sync(0xFFFFFFFFu, hmask != 0u);
+        const unsigned below = heads & ((1u << lane) - 1u);
+        const int src = below ? 31 - __clz(below) : 0;
+        const uint32_t carry_L = __shfl_sync(0xFFFFFFFFu, last_head_L, src);
+        const bool carry_owned = below != 0u;
+        uint32_t cmask = 0;              // counted contributions
+        int64_t lre = 0, lim = 0;        // lane sums of the counted contributions
+        int64_t hre = 0, him = 0;        // lane prefix before its last head
+        {
+            uint32_t hasL = carry_L;
 #pragma unroll
-        for (int k = 0; k < MG_IPT; ++k) {
-            if (k < nk) {
-                if ((hmask >> k) & 1u) tail = seg_head((lmask >> k) & 1u);
-                seg_add(tail, iv[k], ((lmask | fmask) >> k) & 1u);
+            for (int k = 0; k < MG_IPT; ++k) {
+                if (k < nk) {
+                    if ((hmask >> k) & 1u) { hasL = (lmask >> k) & 1u; hre = lre; him = lim; }
+                    bool counted = (((lmask | fmask) >> k) & 1u) || hasL;
+                    if (!counted) {
+                        bool ni = no_init;
+                        if constexpr (BATCH) ni = Pr[batch_run(key_high(ik[k]), run_shift, nruns)].n_a == 0;
+                        counted = ni || key_diagonal<KT, BATCH>(ik[k], nmask, N);
+                    }
+                    if (counted) {
+                        cmask |= 1u << k;
+                        lre += iv[k].x;
+                        lim += iv[k].y;
+                    }
+                }
             }
         }
-        const SegAgg carry = seg_warp_exclusive(tail, lane);
+        // exclusive warp prefix of the lane sums
+        int64_t ere = lre, eim = lim;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t yr = shfl_up_i64(ere, off), yi = shfl_up_i64(eim, off);
+            if (lane >= off) { ere += yr; eim += yi; }
+        }
+        ere -= lre;
+        eim -= lim;
+        // prefix before the head of the run open at this lane's start
+        const int64_t cb_re = (int64_t)__shfl_sync(0xFFFFFFFFu, (long long)(ere + hre), src);
+        const int64_t cb_im = (int64_t)__shfl_sync(0xFFFFFFFFu, (long long)(eim + him), src);
         const int my_first_head = nk > 0 ? (int)(hmask & 1u) : 1;
         const int next_first_head = __shfl_down_sync(0xFFFFFFFFu, my_first_head, 1);
-        SegAgg run = carry;
-        bool owned = carry.h != 0;       // the open run has its head in this tile
+
+        // ---- 3. run ends: sums and the initiator rule; outputs replace iv ----
         uint32_t omask = 0;
-        int2 oval[MG_IPT];
+        {
+            int64_t pre = ere, pim = eim, bre = cb_re, bim = cb_im;
+            uint32_t hasL = carry_L;
+            bool owned = carry_owned;
 #pragma unroll
-        for (int k = 0; k < MG_IPT; ++k) {
-            oval[k] = make_int2(0, 0);
-            if (k < nk) {
-                if ((hmask >> k) & 1u) { run = seg_head((lmask >> k) & 1u); owned = true; }
-                seg_add(run, iv[k], ((lmask | fmask) >> k) & 1u);
-                bool ends;
-                if (k + 1 < nk) ends = ((hmask >> (k + 1)) & 1u) != 0u;
-                else if (dloc + k + 1 < nt) ends = next_first_head != 0;
-                else {
-                    // the tile's last run: add its spawn records that follow the tile
-                    ends = true;
-                    run.fre += rf0;
-                    run.fim += rf1;
-                    run.ure += ru0;
-                    run.uim += ru1;
-                }
-                if (ends && owned) {
-                    uint64_t ki, kj;
-                    key_words(ik[k], nmask, N, ki, kj);
-                    bool ni = no_init;
-                    if constexpr (BATCH) {
-                        kj &= nmask;
-                        ni = Pr[batch_run(key_high(ik[k]), run_shift, nruns)].n_a == 0;
-                    }
-                    const bool open = run.hasL || ni || ki == kj;
-                    const int64_t sre = run.fre + (open ? run.ure : 0);
-                    const int64_t sim = run.fim + (open ? run.uim : 0);
-                    if (sre != 0 || sim != 0) {
-                        if (iabs64(sre) > 2147483647ll || iabs64(sim) > 2147483647ll) local_status |= ST_OVERFLOW;
-                        omask |= 1u << k;
-                        oval[k] = make_int2((int32_t)sre, (int32_t)sim);
+            for (int k = 0; k < MG_IPT; ++k) {
+                if (k < nk) {
+                    if ((hmask >> k) & 1u) { bre = pre; bim = pim; hasL = (lmask >> k) & 1u; owned = true; }
+                    if ((cmask >> k) & 1u) { pre += iv[k].x; pim += iv[k].y; }
+                    const bool tile_last = dloc + k + 1 == nt;
+                    bool ends;
+                    if (k + 1 < nk) ends = ((hmask >> (k + 1)) & 1u) != 0u;
+                    else ends = tile_last || next_first_head != 0;
+                    if (ends && owned) {
+                        int64_t sre = pre - bre, sim = pim - bim;
+                        if (tile_last) {
+                            // the records of the last run that lie past the tile
+                            sre += s.rem[warp][0];
+                            sim += s.rem[warp][1];
+                            bool open = hasL != 0u;
+                            if (!open) {
+                                bool ni = no_init;
+                                if constexpr (BATCH) ni = Pr[batch_run(key_high(ik[k]), run_shift, nruns)].n_a == 0;
+                                open = ni || key_diagonal<KT, BATCH>(ik[k], nmask, N);
+                            }
+                            if (open) { sre += s.rem[warp][2]; sim += s.rem[warp][3]; }
+                        }
+                        if (sre != 0 || sim != 0) {
+                            if (iabs64(sre) > 2147483647ll || iabs64(sim) > 2147483647ll) local_status |= ST_OVERFLOW;
+                            omask |= 1u << k;
+                            iv[k] = make_int2((int32_t)sre, (int32_t)sim);
+                        }
                     }
                 }
             }
         }
-        // ---- 3. compaction: warp scan of the output counts, look-back --------
+        // ---- 4. compaction: warp scan of the output counts, staging ---------
         const int nout = __popc(omask);
         int x = nout;
 #pragma unroll
@@ -513,15 +526,60 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
         }
         const uint32_t total = (uint32_t)__shfl_sync(0xFFFFFFFFu, x, 31);
         __syncwarp();                    // every lane is done reading the tile
-        uint32_t my_off = (uint32_t)(x - nout);
+        LT *stage = reinterpret_cast<LT *>(buf);
+        {
+            uint32_t my_off = (uint32_t)(x - nout);
 #pragma unroll
-        for (int k = 0; k < MG_IPT; ++k) {
-            if ((omask >> k) & 1u) {
-                ws.key[my_off] = ik[k];
-                ws.val[my_off] = oval[k];
-                ++my_off;
+            for (int k = 0; k < MG_IPT; ++k) {
+                if ((omask >> k) & 1u) {
+                    LT v;
+                    set_list(v, ik[k]);
+                    v.re = iv[k].x;
+                    v.im = iv[k].y;
+                    stage[my_off++] = v;
+                }
             }
         }
+        __syncwarp();
+        // estimator numerators of the outputs (walkers, entries; diagonal and
+        // nearest-neighbour terms); a batch sums walkers and entries per run
+        // in registers while consecutive entries stay in one run
+        {
+            int brun = -1;
+            int64_t bw = 0, bm = 0;
+            for (uint32_t q = lane; q < total; q += 32) {
+                const LT v = stage[q];
+                uint64_t i, j;
+                key_words(list_key<KT>(v), nmask, N, i, j);
+                const int64_t w = iabs64(v.re) + iabs64(v.im);
+                unsigned long long *est = s.est;
+                if constexpr (BATCH) {
+                    const int rr = batch_run(key_high(list_key<KT>(v)), run_shift, nruns);
+                    j &= nmask;
+                    if (rr != brun) {
+                        if (brun >= 0) {
+                            atomicAdd(&best[(size_t)brun * nobs + 3], (unsigned long long)bw);
+                            atomicAdd(&best[(size_t)brun * nobs + 4], (unsigned long long)bm);
+                        }
+                        brun = rr;
+                        bw = 0;
+                        bm = 0;
+                    }
+                    bw += w;
+                    bm += 1;
+                    est = best + (size_t)rr * nobs;
+                } else {
+                    my_w += w;
+                    my_m += 1;
+                }
+                if (i == j || __popcll(i ^ j) <= 2) add_estimators(s, est, P, i, j, v.re, v.im);
+            }
+            if (BATCH && brun >= 0) {
+                atomicAdd(&best[(size_t)brun * nobs + 3], (unsigned long long)bw);
+                atomicAdd(&best[(size_t)brun * nobs + 4], (unsigned long long)bm);
+            }
+        }
+        // ---- 5. output offset by decoupled look-back, then the write ---------
         uint64_t *myw = lookback + tile;
         if (lane == 0) lb_store(myw, lb_pack(epoch, tile == 0 ? LB_INC : LB_AGG, total));
         uint64_t excl = 0;
@@ -540,34 +598,23 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
             if (lane == 0) lb_store(myw, lb_pack(epoch, LB_INC, (uint32_t)(excl + total)));
         }
         if (lane == 0 && tile == ntiles - 1) st->M_next = (int64_t)(excl + total);
-        __syncwarp();
         const int64_t ob = (int64_t)excl;
         if (ob + (int64_t)total > mcap) {
             if (lane == 0) local_status |= ST_CAPACITY | ST_CAP_LIST;
-        } else {
-            for (uint32_t q = lane; q < total; q += 32) {
-                LT v;
-                set_list(v, ws.key[q]);
-                v.re = ws.val[q].x;
-                v.im = ws.val[q].y;
-                out[ob + q] = v;
-                uint64_t i, j;
-                key_words(ws.key[q], nmask, N, i, j);
-                unsigned long long *est = s.est;
-                if constexpr (BATCH) {
-                    j &= nmask;
-                    est = best + (size_t)batch_run(key_high(ws.key[q]), run_shift, nruns) * nobs;
-                    atomicAdd(&est[3], (unsigned long long)(iabs64(v.re) + iabs64(v.im)));
-                    atomicAdd(&est[4], 1ull);
-                } else {
-                    my_w += iabs64(v.re) + iabs64(v.im);
-                    my_m += 1;
-                }
-                if (i == j || __popcll(i ^ j) <= 2) add_estimators(s, est, P, i, j, v.re, v.im);
+        } else if constexpr (BULK_OUT) {
+            fence_proxy_async();         // the staged entries, before the async proxy reads them
+            __syncwarp();
+            if (lane == 0 && total > 0) {
+                bulk_store(out + ob, buf, total * (uint32_t)LS);
+                bulk_commit();
+                store_pending = true;
             }
+        } else {
+            for (uint32_t q = lane; q < total; q += 32) out[ob + q] = stage[q];
         }
-        __syncwarp();
     }
+    if (lane == 0 && store_pending) bulk_wait_all();
+    __syncwarp();
     // flush the block's estimator partials
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

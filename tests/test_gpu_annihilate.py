@@ -135,3 +135,18 @@ def test_annihilate_int32_overflow_is_reported(env, part, sign):
     assert np.array_equal(got, ref)
     k = np.nonzero(got["key"] == np.uint64((7 << N) | 3))[0][0]
     assert int(got[part][k]) == sign * (2 ** 31 - 6)
+
+
+def test_annihilate_rejects_misaligned_records(env):
+    """16-byte records are moved with 16-byte accesses and bulk copies: a
+    record pointer that is not 16-byte aligned is refused on the host before
+    any launch."""
+    torch, ddqmc = env
+    run = ddqmc.Run(4, 4, 1, 0.9, 1.0, 1.0, 1.0, 0.005, 10 ** 4, capacity_entries=4096, capacity_spawns=4096)
+    x = torch.zeros(16 * 64 + 64, dtype=torch.uint8, device="cuda")
+    p = x.data_ptr()
+    assert p % 16 == 0
+    for args in ((p + 8, 1, p, 1, p + 512, 8), (p, 1, p + 4, 1, p + 512, 8), (p, 1, p, 1, p + 520, 8)):
+        with pytest.raises(ddqmc.DDQMCError) as e:
+            ddqmc.ddqmc_annihilate(run.h, *args)
+        assert e.value.code == -1      # DDQMC_ERR_INVALID_ARG
