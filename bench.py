@@ -70,7 +70,80 @@ def parse():
     ap.add_argument("--serve", type=int, default=0,
                     help="instead: this many synthetic NESS-solve requests through the batching server, "
                          "then the same requests one at a time")
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"],
+                    help="c3: the 4x4 benchmark (default); c1: 2x2 open, N_w target 1e4, timed after the shift "
+                         "settles; c2: 3x3 periodic, N_w target 1e6, n_a 3, its first 200 steps (the window the "
+                         "parity tests compare bit for bit); c1 and c2 time the GPU and the oracle on the same steps")
     return ap.parse_args()
+
+
+# the small configurations: (parameters, untimed steps after the shift switches on or None, timed steps)
+SMALL_WORKLOADS = {
+    "c1": (dict(Lx=2, Ly=2, periodic=0, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.01, target=10 ** 4, n_a=0, seed=1,
+                control=0), 1000, 2048),
+    "c2": (dict(Lx=3, Ly=3, periodic=1, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, target=10 ** 6, n_a=3, seed=2,
+                control=0), None, 200),
+}
+
+
+def small_arm(args):
+    """Walker-steps/s of c1 or c2 on the GPU (CUDA events around the timed
+    steps, graph replay in blocks of 32) and of the oracle on the same steps
+    (single-threaded; c1 times its first 256 of them)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1802_05931_gb300 import ddqmc
+    from oracle import oracle as O
+    torch.cuda.set_device(0)
+    prm, settle, K = SMALL_WORKLOADS[args.workload]
+    pos = (prm["Lx"], prm["Ly"], prm["periodic"], prm["Jx"], prm["Jy"], prm["Jz"], prm["gamma"], prm["dt"],
+           prm["target"])
+    kw = dict(n_a=prm["n_a"], seed=prm["seed"], control=prm["control"])
+    stream = torch.cuda.Stream()
+
+    def advance(run, cpu):
+        if settle is None:
+            return
+        while True:
+            run.step(32)
+            st = run.state()
+            if st.variable:
+                break
+        run.step(st.t_var + settle - st.t)
+        # the oracle continues from the GPU's state (list, step, shift)
+        s = run.state()
+        cpu.import_(*run.export())
+        cpu.set_state(s.t, s.shift, s.variable, s.q_prev, s.t_var, s.t_eq)
+
+    gpu = ddqmc.Run(*pos, stream=stream.cuda_stream, **kw)
+    cpu = O.OracleRun(*pos, **kw)
+    advance(gpu, cpu)
+    w0 = ddqmc.ddqmc_get_totals(gpu.h)["walker_steps"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    gpu.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ws = ddqmc.ddqmc_get_totals(gpu.h)["walker_steps"] - w0
+    Kc = K if args.workload == "c2" else 256
+    cws, t0 = 0, time.perf_counter()
+    for _ in range(Kc):
+        cws += int(cpu.estimates_now()[3])
+        cpu.step(1)
+    cel = time.perf_counter() - t0
+    line = {"metric": METRIC, "value": ws / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": 0,
+            "ms_per_step": ms / K, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "parameters": prm,
+                       "timed": "steps [%d, %d)" % (gpu.state().t - K, gpu.state().t),
+                       "walkers_per_step": ws / K},
+            "cpu_baseline": {"value": cws / cel, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "the first %d of the same steps, %.1f s" % (Kc, cel), "host": cpu_cores_desc()}}
+    gpu.close()
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -192,6 +265,15 @@ def profile_counters():
     except Exception:
         pass
     return out
+
+
+def pinned_list_buffers(n):
+    """Four page-locked host arrays (ket, bra, re, im) of n entries."""
+    import numpy as np
+    import torch
+    b = tuple(torch.empty(n, dtype=dt, pin_memory=True).numpy()
+              for dt in (torch.int64, torch.int64, torch.int32, torch.int32))
+    return b[0].view(np.uint64), b[1].view(np.uint64), b[2], b[3]
 
 
 SMS = 152                 # GB300 streaming multiprocessors
@@ -332,7 +414,8 @@ def gpu_arm(args, world, rank, local, pg):
     lb = 16 if N <= 31 else 24
     kb = {"spawn_death": ((lb + 8) * dM + rb * dR) / K,
           "radix_pass": 2 * rb * dR / K,
-          "merge": (lb * (dM + dMn) + rb * dR) / K}
+          "merge": (lb * (dM + dMn) + rb * dR) / K,
+          "merge_compact": 2 * lb * dMn / K}
     spawn_alg = ((lb + 8) * dM + lb * dR) / K
     ann_alg = lb * (dR + dM + dMn) / K
     positions = (dM + dR) / K
@@ -390,12 +473,12 @@ def gpu_arm(args, world, rank, local, pg):
                     "frac": achieved / peak, "traffic": traffic, "peak_source": hbm_src,
                     "alg_bytes_per_launch": alg_dom,
                     "counters": "no current instruction count for this kernel" if dom == "spawn_death" else None}
-    sm_keys = ("radix_pass", "merge_partition", "merge")
+    sm_keys = ("radix_pass", "merge_partition", "merge", "merge_compact")
     sortmerge_ms = sum(timing[k][0] for k in sm_keys if k in timing) / K
     sm_s = sortmerge_ms / 1e3
-    moved = kb["radix_pass"] * (timing["radix_pass"][1] / K) + kb["merge"]
+    moved = kb["radix_pass"] * (timing["radix_pass"][1] / K) + kb["merge"] + kb["merge_compact"]
     sm_dram = [dram(k) for k in sm_keys]
-    sm_dram_bytes = (sum(d * timing[k][1] / K for d, k in zip(sm_dram, sm_keys))
+    sm_dram_bytes = (sum(d * timing[k][1] / K for d, k in zip(sm_dram, sm_keys) if k in timing)
                      if all(d is not None for d in sm_dram) else None)
     sort_merge = {"ms_per_step": sortmerge_ms,
                   "alg_min_bytes_per_step": ann_alg,
@@ -404,15 +487,15 @@ def gpu_arm(args, world, rank, local, pg):
                   "frac_kernel_bytes": moved / sm_s / 1e9 / peak,
                   "dram_bytes_per_step": sm_dram_bytes,
                   "frac_dram": sm_dram_bytes / sm_s / 1e9 / peak if sm_dram_bytes else None,
-                  "note": "frac_dram: DRAM bytes of the radix passes, the partition and the merge (committed ncu "
-                          "counters per unit x this run's units) over their CUDA-event time; frac_alg_min: "
-                          "16 B x (spawn records + entries read + entries written) over the same time"}
+                  "note": "frac_dram: DRAM bytes of the radix passes, the partition, the merge and its compaction "
+                          "(committed ncu counters per unit x this run's units) over their CUDA-event time; "
+                          "frac_alg_min: 16 B x (spawn records + entries read + entries written) over the same time"}
     # end to end through the C-ABI with host buffers: import, step, export, estimators
     e2e = None
     if args.e2e_steps > 0:
-        # host buffers reused from step to step, as a streaming caller would
+        # pinned host buffers reused from step to step, as a streaming caller would
         M0 = run.state().entries
-        bufs = tuple(np.empty(int(1.25 * M0) + 1024, dtype=dt) for dt in (np.uint64, np.uint64, np.int32, np.int32))
+        bufs = pinned_list_buffers(int(1.25 * M0) + 1024)
         ket, bra, re, im = run.export(out=bufs)
         st = run.state()
         state = (st.t, st.shift, st.variable, st.q_prev, st.t_var, st.t_eq)
@@ -422,12 +505,12 @@ def gpu_arm(args, world, rank, local, pg):
         e_ws, h2d, d2h = 0, 0, 0
         for _ in range(args.e2e_steps):
             run.import_(ket, bra, re, im, *state)
-            h2d += 16 * len(ket)
+            h2d += 24 * len(ket)                 # ket, bra (8 B each), re, im (4 B each)
             run.step(1)
             e_ws += ddqmc.ddqmc_get_totals(run.h)["walker_steps"]     # import resets the totals
             ket, bra, re, im = run.export(out=bufs)
             est = run.raw_estimates()
-            d2h += 16 * len(ket) + 8 * len(est)
+            d2h += 24 * len(ket) + 8 * len(est)
             st = run.state()
             state = (st.t, st.shift, st.variable, st.q_prev, st.t_var, st.t_eq)
         el = time.perf_counter() - t0
@@ -648,6 +731,8 @@ def main():
         return serve_arm(args)
     if args.batch:
         return batch_arm(args)
+    if args.workload != "c3":
+        return small_arm(args)
     world, rank, local, pg = dist_setup(args.gpus)
     try:
         if args.impl == "reference":

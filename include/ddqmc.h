@@ -177,7 +177,11 @@ int ddqmc_blocking_moments(ddqmc_run *run, int32_t k, int32_t levels, int64_t *h
                            int64_t *host_sx, int64_t *host_sxx, int64_t *host_sxy);
 
 /* Copy the current walker list (canonical order) to host arrays of capacity
- * cap; *n receives the list length (call with cap = 0 to query it). */
+ * cap; *n receives the list length (call with cap = 0 to query it).  The list
+ * is unpacked into the four arrays on the device and each array crosses the
+ * host link in one copy (at the link's speed when the host arrays are pinned,
+ * e.g. from cudaMallocHost); device scratch of 24 bytes per entry is kept
+ * by the run after the first call.  Waits for the run's stream. */
 int ddqmc_export_walkers(ddqmc_run *run, uint64_t *ket, uint64_t *bra, int32_t *re,
                          int32_t *im, int64_t cap, int64_t *n);
 
@@ -185,7 +189,10 @@ int ddqmc_export_walkers(ddqmc_run *run, uint64_t *ket, uint64_t *bra, int32_t *
  * order, no all-zero entry, spin words within N bits) and set the step
  * counter t and shift S; the shift stays in its variable phase iff
  * variable != 0, with q_prev as the last controlled weight.  Clears the
- * accumulated estimates and any sticky error. */
+ * accumulated estimates and any sticky error.  Each array crosses the host
+ * link in one copy (pinned arrays at the link's speed); the entries are
+ * checked and packed on the device into the run's spare list buffer, so a
+ * list that fails a check (INVALID_ARG) leaves the run as it was. */
 int ddqmc_import_walkers(ddqmc_run *run, const uint64_t *ket, const uint64_t *bra,
                          const int32_t *re, const int32_t *im, int64_t n, int64_t t,
                          double S, int32_t variable, int64_t q_prev, int64_t t_var,
@@ -315,7 +322,7 @@ int ddqmc_annihilate(ddqmc_run *run, const void *d_list, int64_t m, const void *
  * or they must stay off the driver's allocation path and its implicit
  * synchronisation.  This entry point allocates nothing and needs no run: its
  * scratch is a fixed array inside the library that every GPU loading the
- * library holds until the process exits (about 8.9 MB).
+ * library holds until the process exits (about 30 MB).
  *   lattice, initiator_threshold: as in ddqmc_create (key layout and rule;
  *     at most 31 sites, else UNSUPPORTED);
  *   d_list, m, d_spawns, nsp, d_out, out_cap, *m_out: as in ddqmc_annihilate,

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libddqmc.so")
 SOURCES = ["ddqmc_api.cu"]
-DEPS = ["ddqmc_api.cu", "common.cuh", "spawn.cuh", "radix.cuh", "merge.cuh", "finalize.cuh"]
+DEPS = ["ddqmc_api.cu", "common.cuh", "spawn.cuh", "radix.cuh", "merge.cuh", "finalize.cuh", "transfer.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

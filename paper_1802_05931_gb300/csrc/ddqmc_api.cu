@@ -14,7 +14,6 @@
 #include <functional>
 #include <new>
 #include <nvtx3/nvToolsExt.h>
-#include <thread>
 #include <vector>
 
 #include "../../include/ddqmc.h"
@@ -23,6 +22,7 @@
 #include "merge.cuh"
 #include "radix.cuh"
 #include "spawn.cuh"
+#include "transfer.cuh"
 
 using namespace ddq;
 
@@ -37,14 +37,17 @@ struct ddqmc_run {
     uint64_t *lb_merge = nullptr;
     int64_t *splits = nullptr;
     int64_t *rem_end = nullptr;
+    void *slots = nullptr;               // the merge's per-tile output slots (list records)
+    uint32_t *tile_counts = nullptr;     // entries in each slot
     int64_t mcap = 0, rcap = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
     int cur = 0;                 // which L buffer holds the current list
-    int g_spawn = 0, g_radix = 0, g_part = 0, g_merge = 0;
+    int g_spawn = 0, g_radix = 0, g_part = 0, g_merge = 0, g_scan = 0, g_copy = 0;
     int g_radix_wide = 0;        // radix grid of 16-byte records (standalone annihilation)
     int g_merge_ann = 0;         // merge grid of 16-byte records (standalone annihilation)
+    int g_copy_ann = 0;          // compaction copy grid of 16-byte records (standalone annihilation)
     bool packed = false;         // 8-byte spawn records (2N <= 32) on the step path
     bool wide = false;           // two-word keys (N > 31): RecW lists and spawn records
     int guide_kind = 0;
@@ -56,9 +59,11 @@ struct ddqmc_run {
     std::vector<cudaEvent_t> ev;     // 2 * NKCLASS events per step
     double kernel_ms[8] = {0};
     int64_t kernel_launches[8] = {0};
-    // pinned host staging for import / export, kept between calls
-    unsigned char *hstage = nullptr;
-    size_t hstage_cap = 0;       // bytes
+    // device arrays of the caller's layout for import / export (ket, bra
+    // words, re, im), allocated on first use; small device scratch
+    unsigned char *soa = nullptr;
+    int64_t soa_cap = 0;         // entries
+    unsigned long long *dxfer = nullptr;   // [0] walkers, [1] bad entry, [2..3] run bounds
     // counters of standalone annihilation calls (allocated on first use)
     DevState *dAnn = nullptr;
     uint32_t ann_calls = 0;
@@ -308,7 +313,8 @@ void free_run(ddqmc_run *r) {
     for (cudaEvent_t e : r->ev) cudaEventDestroy(e);
     for (cudaGraphExec_t g : r->graph)
         if (g) cudaGraphExecDestroy(g);
-    if (r->hstage) cudaFreeHost(r->hstage);
+    cudaFree(r->soa);
+    cudaFree(r->dxfer);
     cudaFree(r->dP);
     cudaFree(r->dS);
     cudaFree(r->dPr);
@@ -322,6 +328,8 @@ void free_run(ddqmc_run *r) {
     cudaFree(r->lb_merge);
     cudaFree(r->splits);
     cudaFree(r->rem_end);
+    cudaFree(r->slots);
+    cudaFree(r->tile_counts);
     cudaFree(r->dAnn);
     if (r->own_stream && r->stream) cudaStreamDestroy(r->stream);
     delete r;
@@ -340,38 +348,23 @@ int read_status(ddqmc_run *r) {
     return r->host_status;
 }
 
-// Host loops over list entries (import / export conversion) split over the
-// host's cores; f(begin, end) handles one contiguous range.
-template <typename F>
-void parallel_for(int64_t n, const F &f) {
-    const int64_t grain = 1 << 20;
-    unsigned hw = std::thread::hardware_concurrency();
-    int64_t nt = (n + grain - 1) / grain;
-    if (nt > (int64_t)(hw ? hw : 1)) nt = hw ? hw : 1;
-    if (nt > 32) nt = 32;
-    if (nt <= 1) { f((int64_t)0, n); return; }
-    std::vector<std::thread> th;
-    const int64_t chunk = (n + nt - 1) / nt;
-    for (int64_t t = 1; t < nt; ++t) {
-        const int64_t b = t * chunk, e = b + chunk < n ? b + chunk : n;
-        if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
-    }
-    f((int64_t)0, chunk < n ? chunk : n);
-    for (auto &x : th) x.join();
+// Device arrays of the caller's layout for n entries (24 bytes each), grown
+// on demand; nullptr when the allocation fails.
+unsigned char *soa_scratch(ddqmc_run *r, int64_t n) {
+    if (!r->dxfer && dalloc(&r->dxfer, 4) != DDQMC_OK) return nullptr;
+    if (n <= r->soa_cap && r->soa) return r->soa;
+    cudaFree(r->soa);
+    r->soa = nullptr;
+    r->soa_cap = 0;
+    const int64_t cap = n > 4096 ? n : 4096;
+    if (dalloc_bytes((void **)&r->soa, 24 * (size_t)cap) != DDQMC_OK) return nullptr;
+    r->soa_cap = cap;
+    return r->soa;
 }
 
-// Pinned host staging of at least `bytes` bytes (grown on demand, never shrunk).
-unsigned char *host_stage(ddqmc_run *r, size_t bytes) {
-    if (bytes <= r->hstage_cap) return r->hstage;
-    if (r->hstage) { cudaFreeHost(r->hstage); r->hstage = nullptr; r->hstage_cap = 0; }
-    const size_t cap = bytes + bytes / 4 + 16384;
-    if (cudaMallocHost((void **)&r->hstage, cap) != cudaSuccess) {
-        cudaGetLastError();
-        r->hstage = nullptr;
-        return nullptr;
-    }
-    r->hstage_cap = cap;
-    return r->hstage;
+int grid_for(int64_t n) {
+    const int64_t g = (n + TX_TPB - 1) / TX_TPB;
+    return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
 }
 
 constexpr size_t SP_SMEM = sizeof(SpawnShared<Rec>);
@@ -415,9 +408,17 @@ void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(in
     k_merge_partition<T><<<r->g_part, 256, 0, r->stream>>>(Lc, sorted, r->dS, r->splits, r->rem_end, r->rcap);
     mark(2, 1);
     mark(3, 0);
-    k_merge<T, BATCH><<<r->g_merge, MG_TPB, r->mg_smem, r->stream>>>(r->dP, Lc, sorted, Ln, r->dS, r->splits,
-                                                                    r->rem_end, r->lb_merge, r->rcap, r->mcap, Pr, rs);
+    k_merge<T, BATCH><<<r->g_merge, MG_TPB, r->mg_smem, r->stream>>>(
+        r->dP, Lc, sorted, reinterpret_cast<LT *>(r->slots), r->tile_counts, r->dS, r->splits, r->rem_end, r->rcap,
+        Pr, rs);
     mark(3, 1);
+    // compaction: tile offsets (into splits, free once the merge has run), then the copy
+    mark(5, 0);
+    k_merge_scan<<<r->g_scan, MC_TPB, 0, r->stream>>>(r->tile_counts, r->splits, r->dS, r->lb_merge, r->rcap,
+                                                      r->mcap);
+    k_merge_copy<LT><<<r->g_copy, MC_TPB, 0, r->stream>>>(reinterpret_cast<const LT *>(r->slots), r->tile_counts,
+                                                          r->splits, Ln, r->dS, r->rcap);
+    mark(5, 1);
 }
 
 // Default capacities: with total-population control the list holds at most
@@ -486,6 +487,8 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     rc |= dalloc(&r->lb_merge, (size_t)mtiles);
     rc |= dalloc(&r->splits, (size_t)mtiles + 1);
     rc |= dalloc(&r->rem_end, (size_t)mtiles + 1);
+    rc |= dalloc_bytes(&r->slots, lsize * (size_t)mtiles * MG_TILE + 64);
+    rc |= dalloc(&r->tile_counts, (size_t)mtiles);
     if (rc != DDQMC_OK) return DDQMC_ERR_OOM;
     // kernel shapes
     int sms = 0;
@@ -557,7 +560,11 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     r->g_merge = occupancy_grid(fm, MG_TPB, r->mg_smem, sms);
     r->g_merge_ann = occupancy_grid((const void *)k_merge<Rec, false>, MG_TPB, MG_SMEM, sms);
     r->g_radix_wide = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
+    r->g_copy_ann = occupancy_grid((const void *)k_merge_copy<Rec>, MC_TPB, 0, sms);
     r->g_part = 4 * sms;
+    r->g_scan = occupancy_grid((const void *)k_merge_scan, MC_TPB, 0, sms);
+    r->g_copy = occupancy_grid(r->wide ? (const void *)k_merge_copy<RecW> : (const void *)k_merge_copy<Rec>, MC_TPB,
+                               0, sms);
     bool okc = cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * blk_cells, r->stream) == cudaSuccess;
     okc = okc && cudaMemsetAsync(r->lb_radix, 0, sizeof(uint64_t) * (size_t)rtiles * 256, r->stream) == cudaSuccess;
     okc = okc && cudaMemsetAsync(r->lb_merge, 0, sizeof(uint64_t) * (size_t)mtiles, r->stream) == cudaSuccess;
@@ -566,7 +573,7 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
 }
 
 // kernel classes of the per-kernel timing
-enum { KC_SPAWN = 0, KC_RADIX = 1, KC_PARTITION = 2, KC_MERGE = 3, KC_FINALIZE = 4, NKCLASS = 5 };
+enum { KC_SPAWN = 0, KC_RADIX = 1, KC_PARTITION = 2, KC_MERGE = 3, KC_FINALIZE = 4, KC_COMPACT = 5, NKCLASS = 6 };
 
 // Steps replayed from one captured graph: even, so that the list buffers end
 // where they started and one graph per starting buffer suffices.
@@ -660,7 +667,7 @@ void collect_timing(ddqmc_run *r, int64_t nsteps) {
             const size_t b = (size_t)s * 2 * NKCLASS + 2 * kc;
             if (cudaEventElapsedTime(&ms, r->ev[b], r->ev[b + 1]) == cudaSuccess) {
                 r->kernel_ms[kc] += ms;
-                r->kernel_launches[kc] += (kc == KC_RADIX) ? r->hp.npass : 1;
+                r->kernel_launches[kc] += (kc == KC_RADIX) ? r->hp.npass : (kc == KC_COMPACT ? 2 : 1);
             } else {
                 cudaGetLastError();
             }
@@ -749,14 +756,16 @@ struct NoAllocScratch {
     uint64_t lb_merge[NA_MTILES];
     int64_t splits[NA_MTILES + 1];
     int64_t rem_end[NA_MTILES + 1];
+    uint32_t counts[NA_MTILES];
     Rec buf[2][NA_MAX_SPAWNS];
+    Rec slots[NA_MTILES * MG_TILE];
 };
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
 constexpr int NA_MAX_DEVICES = 64;
 NoAllocScratch *g_na_ptr[NA_MAX_DEVICES] = {nullptr};
-int g_na_grid[NA_MAX_DEVICES][3];       // radix, partition, merge grids
+int g_na_grid[NA_MAX_DEVICES][4];       // radix, partition (and tile-offset scan), merge, copy grids
 
 // Once per device, with that device current: device address of the scratch
 // array and the launch shapes.
@@ -782,6 +791,7 @@ int noalloc_setup(int dev) {
     g_na_grid[dev][0] = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
     g_na_grid[dev][1] = 4 * sms;
     g_na_grid[dev][2] = occupancy_grid((const void *)k_merge<Rec, false>, MG_TPB, MG_SMEM, sms);
+    g_na_grid[dev][3] = occupancy_grid((const void *)k_merge_copy<Rec>, MC_TPB, 0, sms);
     g_na_ptr[dev] = (NoAllocScratch *)ptr;
     return DDQMC_OK;
 }
@@ -811,76 +821,54 @@ int raw_estimators_of(ddqmc_run *r, int k, int64_t *host_out, int32_t cap, int32
 // Canonical (ket, bra, re, im) of the current list: the whole list (k < 0),
 // or the entries of batch run k (a contiguous range: the run id is the key's
 // most significant part).  *n = the entries of that list or run.
-int export_of(ddqmc_run *r, int k, uint64_t *ket, uint64_t *bra, int32_t *re, int32_t *im, int64_t cap,
-              int64_t *n) {
+template <typename LT>
+int export_list(ddqmc_run *r, int k, uint64_t *ket, uint64_t *bra, int32_t *re, int32_t *im, int64_t cap,
+                int64_t *n) {
     int64_t M = 0;
     if (cudaMemcpyAsync(&M, &r->dS->M, sizeof(M), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
         cudaGetLastError();
         return DDQMC_ERR_CUDA;
     }
-    if (k < 0) {
-        *n = M;
-        if (cap < M) M = cap;       // only what the caller can take
-    }
-    if (M <= 0) {
-        if (k >= 0) *n = 0;
-        return DDQMC_OK;
-    }
-    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
-    unsigned char *hb = host_stage(r, lsize * (size_t)M);
-    if (!hb) return DDQMC_ERR_OOM;
-    if (cudaMemcpyAsync(hb, r->L[r->cur], lsize * (size_t)M, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
-        cudaStreamSynchronize(r->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return DDQMC_ERR_CUDA;
-    }
-    const int N = r->hp.N, rs = r->hp.run_shift;
-    const uint64_t mask = r->hp.nmask;
-    const RecW *hw = reinterpret_cast<const RecW *>(hb);
-    const Rec *h1 = reinterpret_cast<const Rec *>(hb);
-    // [b0, b1): the exported range
+    const LT *L = reinterpret_cast<const LT *>(r->L[r->cur]);
+    // [b0, b1): the exported range (run k's entries of a batch)
     int64_t b0 = 0, b1 = M;
-    if (k >= 0) {
-        auto run_of = [&](int64_t q) -> uint64_t { return r->wide ? (hw[q].hi >> rs) : (h1[q].key >> rs); };
-        int64_t lo = 0, hi = M;
-        while (lo < hi) {           // first entry of a run >= k
-            const int64_t mid = (lo + hi) / 2;
-            if (run_of(mid) < (uint64_t)k) lo = mid + 1; else hi = mid;
+    if (k >= 0 && M > 0) {
+        if (!soa_scratch(r, 1)) return DDQMC_ERR_OOM;
+        int64_t hb[2] = {0, 0};
+        k_run_bounds<LT><<<1, 32, 0, r->stream>>>(L, r->dS, r->hp.run_shift, (uint64_t)k, (int64_t *)(r->dxfer + 2));
+        if (cudaMemcpyAsync(hb, r->dxfer + 2, sizeof(hb), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+            cudaStreamSynchronize(r->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return DDQMC_ERR_CUDA;
         }
-        b0 = lo;
-        hi = M;
-        while (lo < hi) {           // first entry of a run > k
-            const int64_t mid = (lo + hi) / 2;
-            if (run_of(mid) <= (uint64_t)k) lo = mid + 1; else hi = mid;
-        }
-        b1 = lo;
-        *n = b1 - b0;
-        if (b1 - b0 > cap) b1 = b0 + (cap > 0 ? cap : 0);
+        b0 = hb[0];
+        b1 = hb[1];
     }
-    const int64_t m = b1 - b0;
-    if (r->wide) {
-        parallel_for(m, [&](int64_t b, int64_t e) {
-            for (int64_t q = b; q < e; ++q) {
-                const RecW &v = hw[b0 + q];
-                ket[q] = v.lo;
-                bra[q] = v.hi & mask;
-                re[q] = v.re;
-                im[q] = v.im;
-            }
-        });
-    } else {
-        parallel_for(m, [&](int64_t b, int64_t e) {
-            for (int64_t q = b; q < e; ++q) {
-                const Rec &v = h1[b0 + q];
-                ket[q] = v.key & mask;
-                bra[q] = (v.key >> N) & mask;
-                re[q] = v.re;
-                im[q] = v.im;
-            }
-        });
-    }
+    *n = b1 - b0;
+    int64_t m = b1 - b0;
+    if (m > cap) m = cap > 0 ? cap : 0;     // only what the caller can take
+    if (m <= 0) return DDQMC_OK;
+    unsigned char *d = soa_scratch(r, m);
+    if (!d) return DDQMC_ERR_OOM;
+    uint64_t *dk = reinterpret_cast<uint64_t *>(d), *db = dk + m;
+    int32_t *dr = reinterpret_cast<int32_t *>(db + m), *di = dr + m;
+    k_export_unpack<LT><<<grid_for(m), TX_TPB, 0, r->stream>>>(L + b0, m, r->hp.N, r->hp.nmask, dk, db, dr, di);
+    bool ok = cudaGetLastError() == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(ket, dk, 8 * (size_t)m, cudaMemcpyDeviceToHost, r->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(bra, db, 8 * (size_t)m, cudaMemcpyDeviceToHost, r->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(re, dr, 4 * (size_t)m, cudaMemcpyDeviceToHost, r->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(im, di, 4 * (size_t)m, cudaMemcpyDeviceToHost, r->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
     return DDQMC_OK;
+}
+
+// Walker list of run k (k < 0: the whole list of a single run) into the
+// caller's arrays: unpacked on the device, then one copy per array.
+int export_of(ddqmc_run *r, int k, uint64_t *ket, uint64_t *bra, int32_t *re, int32_t *im, int64_t cap,
+              int64_t *n) {
+    return r->wide ? export_list<RecW>(r, k, ket, bra, re, im, cap, n) : export_list<Rec>(r, k, ket, bra, re, im, cap, n);
 }
 
 // State of run k (the run itself when not a batch); the status word is the
@@ -1350,58 +1338,44 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     if (n > r->mcap) return DDQMC_ERR_CAPACITY;
     const int N = r->hp.N;
     const uint64_t mask = r->hp.nmask;
-    // make sure no earlier transfer still reads the staging buffer
+    // the caller's arrays go over the link as they are, one copy each; the
+    // device checks and packs them into the spare list buffer, so a rejected
+    // list leaves the run as it was
     if (cudaStreamSynchronize(r->stream) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
-    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
-    unsigned char *hb = n > 0 ? host_stage(r, lsize * (size_t)n) : nullptr;
-    if (n > 0 && !hb) return DDQMC_ERR_OOM;
-    // check and convert in parallel ranges; any bad entry rejects the whole list
+    unsigned char *d = soa_scratch(r, n > 0 ? n : 1);
+    if (!d) return DDQMC_ERR_OOM;
     int64_t W = 0;
-    {
-        const int64_t grain = 1 << 20;
-        const int64_t nr = n > 0 ? (n + grain - 1) / grain : 0;
-        std::vector<int64_t> rw(nr > 0 ? nr : 1, 0);
-        std::vector<char> rb(nr > 0 ? nr : 1, 0);
-        parallel_for(nr, [&](int64_t b, int64_t e) {
-            for (int64_t g = b; g < e; ++g) {
-                const int64_t q0 = g * grain, q1 = q0 + grain < n ? q0 + grain : n;
-                int64_t acc = 0;
-                for (int64_t q = q0; q < q1; ++q) {
-                    const bool bad = (ket[q] & ~mask) || (bra[q] & ~mask) || (re[q] == 0 && im[q] == 0) ||
-                                     (q > 0 && (bra[q - 1] > bra[q] || (bra[q - 1] == bra[q] && ket[q - 1] >= ket[q])));
-                    if (bad) { rb[g] = 1; break; }
-                    acc += (int64_t)std::llabs(re[q]) + (int64_t)std::llabs(im[q]);
-                    if (r->wide) {
-                        RecW &h = reinterpret_cast<RecW *>(hb)[q];
-                        h.lo = ket[q];
-                        h.hi = bra[q];
-                        h.re = re[q];
-                        h.im = im[q];
-                    } else {
-                        Rec &h = reinterpret_cast<Rec *>(hb)[q];
-                        h.key = (bra[q] << N) | ket[q];
-                        h.re = re[q];
-                        h.im = im[q];
-                    }
-                }
-                rw[g] = acc;
-            }
-        });
-        for (int64_t g = 0; g < nr; ++g) {
-            if (rb[g]) return DDQMC_ERR_INVALID_ARG;
-            W += rw[g];
-        }
-    }
-    // make sure no earlier work of this run is in flight before rewriting its
-    // state; the look-back epoch keeps counting so that no status word left
-    // by an earlier step can match a later one
     uint32_t old_epoch = 0;
-    if (cudaMemcpyAsync(&old_epoch, &r->dS->epoch, sizeof(old_epoch), cudaMemcpyDeviceToHost, r->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(r->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return DDQMC_ERR_CUDA;
+    {
+        const int64_t m = n > 0 ? n : 1;
+        uint64_t *dk = reinterpret_cast<uint64_t *>(d), *db = dk + m;
+        int32_t *dr = reinterpret_cast<int32_t *>(db + m), *di = dr + m;
+        unsigned long long acc[2] = {0ull, 0ull};
+        bool ok = cudaMemsetAsync(r->dxfer, 0, 2 * sizeof(unsigned long long), r->stream) == cudaSuccess;
+        if (n > 0) {
+            ok = ok && cudaMemcpyAsync(dk, ket, 8 * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+            ok = ok && cudaMemcpyAsync(db, bra, 8 * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+            ok = ok && cudaMemcpyAsync(dr, re, 4 * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+            ok = ok && cudaMemcpyAsync(di, im, 4 * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+            if (r->wide)
+                k_import_pack<RecW><<<grid_for(n), TX_TPB, 0, r->stream>>>(
+                    dk, db, dr, di, n, N, mask, reinterpret_cast<RecW *>(r->L[r->cur ^ 1]), r->dxfer);
+            else
+                k_import_pack<Rec><<<grid_for(n), TX_TPB, 0, r->stream>>>(
+                    dk, db, dr, di, n, N, mask, reinterpret_cast<Rec *>(r->L[r->cur ^ 1]), r->dxfer);
+            ok = ok && cudaGetLastError() == cudaSuccess;
+        }
+        // the look-back epoch keeps counting, so that no status word left by
+        // an earlier step can match a later one
+        ok = ok && cudaMemcpyAsync(acc, r->dxfer, sizeof(acc), cudaMemcpyDeviceToHost, r->stream) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(&old_epoch, &r->dS->epoch, sizeof(old_epoch), cudaMemcpyDeviceToHost,
+                                   r->stream) == cudaSuccess;
+        ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
+        if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+        if (acc[1]) return DDQMC_ERR_INVALID_ARG;
+        W = (int64_t)acc[0];
     }
+    r->cur ^= 1;
     DevState hs;
     std::memset(&hs, 0, sizeof(hs));
     hs.t = t;
@@ -1414,10 +1388,7 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     hs.W_cur = W;
     hs.epoch = (old_epoch + 16u) & 0x3FFFFFFFu;
     host_death_table(r->hp, S, hs);
-    bool ok = true;
-    if (n > 0)
-        ok = cudaMemcpyAsync(r->L[r->cur], hb, lsize * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    bool ok = cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * (size_t)NOBS_MAX * LEVELS, r->stream) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
     if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
@@ -1456,9 +1427,13 @@ int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_
         src = dst;
     }
     k_merge_partition<Rec><<<r->g_part, 256, 0, r->stream>>>(list, src, r->dAnn, r->splits, r->rem_end, r->rcap);
-    k_merge<Rec, false><<<r->g_merge_ann, MG_TPB, MG_SMEM, r->stream>>>(r->dP, list, src, (Rec *)d_out, r->dAnn,
-                                                                        r->splits, r->rem_end, r->lb_merge, r->rcap,
-                                                                        out_cap, r->dP, r->dAnn);
+    k_merge<Rec, false><<<r->g_merge_ann, MG_TPB, MG_SMEM, r->stream>>>(r->dP, list, src, (Rec *)r->slots,
+                                                                        r->tile_counts, r->dAnn, r->splits,
+                                                                        r->rem_end, r->rcap, r->dP, r->dAnn);
+    k_merge_scan<<<r->g_scan, MC_TPB, 0, r->stream>>>(r->tile_counts, r->splits, r->dAnn, r->lb_merge, r->rcap,
+                                                      out_cap);
+    k_merge_copy<Rec><<<r->g_copy_ann, MC_TPB, 0, r->stream>>>((const Rec *)r->slots, r->tile_counts, r->splits,
+                                                               (Rec *)d_out, r->dAnn, r->rcap);
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&hs, r->dAnn, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaStreamSynchronize(r->stream) != cudaSuccess) {
@@ -1513,9 +1488,13 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
     }
     k_merge_partition<Rec><<<g_na_grid[dev][1], 256, 0, stream>>>(list, src, &sc->st, sc->splits, sc->rem_end,
                                                                    NA_MAX_SPAWNS);
-    k_merge<Rec, false><<<g_na_grid[dev][2], MG_TPB, MG_SMEM, stream>>>(&sc->P, list, src, (Rec *)d_out, &sc->st,
-                                                                        sc->splits, sc->rem_end, sc->lb_merge,
-                                                                        NA_MAX_SPAWNS, out_cap, &sc->P, &sc->st);
+    k_merge<Rec, false><<<g_na_grid[dev][2], MG_TPB, MG_SMEM, stream>>>(&sc->P, list, src, sc->slots, sc->counts,
+                                                                        &sc->st, sc->splits, sc->rem_end,
+                                                                        NA_MAX_SPAWNS, &sc->P, &sc->st);
+    k_merge_scan<<<g_na_grid[dev][1], MC_TPB, 0, stream>>>(sc->counts, sc->splits, &sc->st, sc->lb_merge,
+                                                           NA_MAX_SPAWNS, out_cap);
+    k_merge_copy<Rec><<<g_na_grid[dev][3], MC_TPB, 0, stream>>>(sc->slots, sc->counts, sc->splits, (Rec *)d_out,
+                                                                &sc->st, NA_MAX_SPAWNS);
     int64_t mo = 0;
     uint32_t status = 0;
     if (cudaGetLastError() != cudaSuccess ||

@@ -11,14 +11,16 @@
 // every kept entry is added to the integer estimator numerators on the way out.
 //
 // Work is cut into tiles of MG_TILE merged positions, one tile per warp at a
-// time, with no block-wide synchronisation: the warp takes a ticket, brings
-// its tile's list and spawn ranges into shared memory with two bulk copies,
-// merges MG_IPT positions per lane in registers, sums runs as differences of
-// a warp-wide prefix sum (the partition kernel has already located the spawn
-// records that continue the tile's last run past its end; the warp sums them
-// with coalesced loads), and finds its output offset by a warp-parallel
-// decoupled look-back over earlier tiles.  Runs whose head lies in an earlier
-// tile are left to that tile.
+// time, assigned statically (tiles never wait for one another): the warp
+// brings its tile's list and spawn ranges into shared memory with two bulk
+// copies, merges MG_IPT positions per lane in registers, sums runs as
+// differences of a warp-wide prefix sum (the partition kernel has already
+// located the spawn records that continue the tile's last run past its end;
+// the warp sums them with coalesced loads) and writes its output entries,
+// uncompacted, into the tile's own slot of a scratch array with their count.
+// Runs whose head lies in an earlier tile are left to that tile.  Then one
+// kernel scans the tile counts (decoupled look-back over chunks of MC_TILES
+// tiles) and another copies every tile's entries to their place in L_{t+1}.
 #pragma once
 
 #include "common.cuh"
@@ -30,7 +32,6 @@ constexpr int MG_TPB = 256;
 constexpr int MG_WARPS = MG_TPB / 32;
 constexpr int MG_IPT = 9;                  // odd: the lanes' merge cursors spread over the banks
 constexpr int MG_TILE = 32 * MG_IPT;       // merged positions per warp tile
-constexpr int MG_PCHUNK = 8;               // tile boundaries per partition thread
 
 // ---- keys ----------------------------------------------------------------
 // One-word records compare their packed key (bra << N | ket); two-word
@@ -103,7 +104,12 @@ __device__ __forceinline__ int64_t merge_split(const LT *L, int64_t M, const T *
 // For every tile boundary t: the merge-path split, and the end of the spawn
 // records that continue the last run of tile t-1 past the boundary (the
 // records S[b, rem_end[t]) share the key of the merged element before the
-// boundary; rem_end[t] = b when the run stops there).
+// boundary; rem_end[t] = b when the run stops there).  One thread per
+// boundary in groups of MG_PGROUP consecutive boundaries: the first thread of
+// a group searches the whole path, the others then search in parallel inside
+// the window that bound gives (a split moves by at most MG_TILE per
+// boundary), so each thread makes about one full and one short search.
+constexpr int MG_PGROUP = 8;
 template <typename T>
 __global__ void k_merge_partition(const typename ListOf<T>::type *__restrict__ L, const T *__restrict__ S,
                                   DevState *__restrict__ st, int64_t *__restrict__ splits,
@@ -115,19 +121,22 @@ __global__ void k_merge_partition(const typename ListOf<T>::type *__restrict__ L
     if (R > rcap) R = rcap;
     const int64_t tot = M + R;
     const int64_t ntiles = (tot + MG_TILE - 1) / MG_TILE;
-    // each thread takes MG_PCHUNK consecutive boundaries: after the first full
-    // search the next split lies within one tile of the previous one
-    const int64_t nchunks = (ntiles + MG_PCHUNK) / MG_PCHUNK;
-    for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += (int64_t)gridDim.x * blockDim.x)
-    for (int64_t t = ch * MG_PCHUNK, aprev = -1; t <= ntiles && t < (ch + 1) * MG_PCHUNK; ++t) {
+    const int lane = threadIdx.x & 31, g = lane & (MG_PGROUP - 1);
+    // the grid strides in whole warps, so the lanes of a group stay together
+    const int64_t span = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 <= ntiles; t0 += span) {
+        const int64_t t = t0 + lane;
+        const int64_t tg = t - g;                         // first boundary of the group
         int64_t diag = t * MG_TILE;
         if (diag > tot) diag = tot;
-        int64_t a;
-        if (aprev < 0) {
-            a = merge_split(L, M, S, R, diag);
-        } else {
-            // merge path split of diag inside [aprev, aprev + MG_TILE]
-            int64_t lo = aprev, hi = aprev + MG_TILE;
+        int64_t a0 = 0;
+        if (g == 0 && t <= ntiles) a0 = merge_split(L, M, S, R, diag);
+        a0 = __shfl_sync(0xFFFFFFFFu, a0, lane & ~(MG_PGROUP - 1));
+        if (t > ntiles) continue;
+        int64_t a = a0;
+        if (g != 0) {
+            const int64_t dg = tg * MG_TILE;
+            int64_t lo = a0, hi = a0 + (diag - dg);
             if (lo < diag - R) lo = diag - R;
             if (hi > diag) hi = diag;
             if (hi > M) hi = M;
@@ -138,7 +147,6 @@ __global__ void k_merge_partition(const typename ListOf<T>::type *__restrict__ L
             }
             a = lo;
         }
-        aprev = a;
         const int64_t b = diag - a;
         splits[t] = a;
         int64_t e = b;
@@ -171,7 +179,6 @@ __global__ void k_merge_partition(const typename ListOf<T>::type *__restrict__ L
         rem_end[t] = e;
     }
 }
-
 
 // Shared memory of one warp tile: the tile's list and spawn ranges as raw
 // records (one bulk copy each, the element before each range included), later
@@ -260,27 +267,26 @@ __device__ __forceinline__ bool key_diagonal(const KT &k, uint64_t nmask, int N)
 // (rs[r]), summed per block in dynamic shared memory past MergeShared (nruns
 // x nobs words).  A single run passes Pr = Pp and rs = st (unread).
 //
-// One warp tile of MG_TILE merged positions: lane 0 takes a ticket and
-// issues two bulk copies (list range [a0 - 1, a1), spawn range [b0 - 1, b1),
-// each widened to 16-byte boundaries) completing on the warp's mbarrier; each
-// lane merges its MG_IPT positions in registers; whether a run holds its L_t
-// entry travels from the lane of its head by ballot and shuffle; run sums are
-// differences of one warp-wide int64 prefix sum of the counted contributions
-// (L_t entries and initiator records always, other records when the run is
-// open: L_t entry present, diagonal, or no initiator rule).  The outputs are
-// staged in the tile buffer and written with one bulk store (16-byte list
-// records) after the output offset is found by decoupled look-back.
+// One warp tile of MG_TILE merged positions: lane 0 issues two bulk copies
+// (list range [a0 - 1, a1), spawn range [b0 - 1, b1), each widened to 16-byte
+// boundaries) completing on the warp's mbarrier; each lane merges its MG_IPT
+// positions in registers; whether a run holds its L_t entry travels from the
+// lane of its head by ballot and shuffle; run sums are differences of one
+// warp-wide int64 prefix sum of the counted contributions (L_t entries and
+// initiator records always, other records when the run is open: L_t entry
+// present, diagonal, or no initiator rule).  The outputs are staged in the
+// tile buffer and leave with one bulk store into the tile's slot
+// (slots + tile * MG_TILE), their number into counts[tile].
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(MG_TPB, MergeBlocks<T>::value)
 k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__restrict__ L, const T *__restrict__ S,
-        typename ListOf<T>::type *__restrict__ out, DevState *__restrict__ st, const int64_t *__restrict__ splits,
-        const int64_t *__restrict__ rem_end, uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap,
+        typename ListOf<T>::type *__restrict__ slots, uint32_t *__restrict__ counts, DevState *__restrict__ st,
+        const int64_t *__restrict__ splits, const int64_t *__restrict__ rem_end, int64_t rcap,
         const RunParams *__restrict__ Pr, DevState *__restrict__ rs) {
     using TR = RecTraits<T>;
     using KT = typename MergeKey<T>::type;
     using LT = typename ListOf<T>::type;
     constexpr int LS = MergeTile<T>::LS, SS = MergeTile<T>::SS;
-    constexpr bool BULK_OUT = LS == 16;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MergeShared<T> &s = *reinterpret_cast<MergeShared<T> *>(smem_raw);
     const RunParams &P = *Pp;
@@ -291,7 +297,6 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
     if (R > rcap) R = rcap;
     const int64_t tot = M + R;
     const int64_t ntiles = (tot + MG_TILE - 1) / MG_TILE;
-    const uint32_t epoch = st->epoch + (uint32_t)MAXPASS;
     const int N = P.N;
     const uint64_t nmask = P.nmask;
     const bool no_init = P.n_a == 0;
@@ -316,14 +321,15 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
     int64_t my_w = 0, my_m = 0;
     uint32_t local_status = 0;
 
-    for (;;) {
-        int64_t tile = 0;
-        if (lane == 0) tile = (int64_t)atomicAdd(&st->tickets[MAXPASS], 1u);
-        tile = __shfl_sync(0xFFFFFFFFu, tile, 0);
-        if (tile >= ntiles) break;
+    const int64_t nwarps = (int64_t)gridDim.x * MG_WARPS;
+    int64_t tile = (int64_t)blockIdx.x * MG_WARPS + warp;
+    // bounds of the next tile, loaded one tile ahead
+    int64_t na0 = 0, na1 = 0, nrem = 0;
+    if (tile < ntiles) { na0 = splits[tile]; na1 = splits[tile + 1]; nrem = rem_end[tile + 1]; }
+    for (; tile < ntiles; tile += nwarps) {
         const int64_t d0 = tile * MG_TILE;
         const int64_t d1 = (d0 + MG_TILE < tot) ? d0 + MG_TILE : tot;
-        const int64_t a0 = splits[tile], a1 = splits[tile + 1], rem_e = rem_end[tile + 1];
+        const int64_t a0 = na0, a1 = na1, rem_e = nrem;
         const int64_t b0 = d0 - a0, b1 = d1 - a1;
         const int na = (int)(a1 - a0), nb = (int)(b1 - b0), nt = na + nb;
         // byte ranges of the two copies (from the element before each range)
@@ -337,6 +343,11 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
             mbar_arrive_expect_tx(bar, lbytes + sbytes);
             if (lbytes) bulk_load(buf, reinterpret_cast<const unsigned char *>(L) + gl0, lbytes, bar);
             if (sbytes) bulk_load(buf + lbytes, reinterpret_cast<const unsigned char *>(S) + gs0, sbytes, bar);
+        }
+        if (tile + nwarps < ntiles) {
+            na0 = splits[tile + nwarps];
+            na1 = splits[tile + nwarps + 1];
+            nrem = rem_end[tile + nwarps + 1];
         }
         // spawn records past the tile end that continue its last run (plain loads, overlapping the copies)
         int64_t rf0 = 0, rf1 = 0, ru0 = 0, ru1 = 0;
@@ -579,38 +590,18 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                 atomicAdd(&best[(size_t)brun * nobs + 4], (unsigned long long)bm);
             }
         }
-        // ---- 5. output offset by decoupled look-back, then the write ---------
-        uint64_t *myw = lookback + tile;
-        if (lane == 0) lb_store(myw, lb_pack(epoch, tile == 0 ? LB_INC : LB_AGG, total));
-        uint64_t excl = 0;
-        if (tile > 0) {
-            for (int64_t jt = tile - 1;; jt -= 32) {
-                const int64_t jj = jt - lane;
-                const uint64_t w = jj >= 0 ? lb_wait(lookback + jj, epoch, &st->status) : lb_pack(epoch, LB_INC, 0u);
-                const unsigned inc = __ballot_sync(0xFFFFFFFFu, ((w >> 32) & 3ull) != LB_AGG);
-                if (inc) {
-                    const int first = __ffs(inc) - 1;
-                    excl += warp_sum_u64(lane <= first ? (uint64_t)(uint32_t)w : 0ull);
-                    break;
-                }
-                excl += warp_sum_u64((uint64_t)(uint32_t)w);
-            }
-            if (lane == 0) lb_store(myw, lb_pack(epoch, LB_INC, (uint32_t)(excl + total)));
-        }
-        if (lane == 0 && tile == ntiles - 1) st->M_next = (int64_t)(excl + total);
-        const int64_t ob = (int64_t)excl;
-        if (ob + (int64_t)total > mcap) {
-            if (lane == 0) local_status |= ST_CAPACITY | ST_CAP_LIST;
-        } else if constexpr (BULK_OUT) {
-            fence_proxy_async();         // the staged entries, before the async proxy reads them
-            __syncwarp();
-            if (lane == 0 && total > 0) {
-                bulk_store(out + ob, buf, total * (uint32_t)LS);
+        // ---- 5. the tile's slot: one bulk store, the count ------------------
+        fence_proxy_async();             // the staged entries, before the async proxy reads them
+        __syncwarp();
+        if (lane == 0) {
+            counts[tile] = total;
+            if (total > 0) {
+                // rounded up to 16 bytes: an odd number of 24-byte entries
+                // carries 8 more bytes, inside the buffer and inside the slot
+                bulk_store(slots + tile * MG_TILE, buf, (total * (uint32_t)LS + 15u) & ~15u);
                 bulk_commit();
                 store_pending = true;
             }
-        } else {
-            for (uint32_t q = lane; q < total; q += 32) out[ob + q] = stage[q];
         }
     }
     if (lane == 0 && store_pending) bulk_wait_all();
@@ -633,6 +624,119 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
     } else {
         for (int q = tid; q < P.nobs; q += MG_TPB)
             if (s.est[q]) atomicAdd((unsigned long long *)&st->est[q], s.est[q]);
+    }
+}
+
+constexpr int MC_TPB = 256;
+constexpr int MC_PER_THREAD = 4;
+constexpr int MC_TILES = MC_TPB * MC_PER_THREAD;   // merge tiles per scan chunk
+
+// Output offsets of the merge's tiles: a persistent grid takes chunks of
+// MC_TILES tile counts in order from a ticket, scans each chunk in the
+// block, finds the chunk's offset by decoupled look-back over earlier chunks
+// (bounded waits) and writes every tile's offset into tile_off.  The last
+// chunk records the merged length; one longer than mcap sets the capacity
+// status (and the copy kernel then writes nothing).
+__global__ void __launch_bounds__(MC_TPB)
+k_merge_scan(const uint32_t *__restrict__ counts, int64_t *__restrict__ tile_off, DevState *__restrict__ st,
+             uint64_t *__restrict__ lookback, int64_t rcap, int64_t mcap) {
+    __shared__ uint32_t warp_sum[MC_TPB / 32];
+    __shared__ int64_t s_base, s_chunk;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (block_stopped(st)) return;
+    const int64_t M = st->M;
+    int64_t R = st->R;
+    if (R > rcap) R = rcap;
+    const int64_t ntiles = (M + R + MG_TILE - 1) / MG_TILE;
+    const int64_t nchunks = (ntiles + MC_TILES - 1) / MC_TILES;
+    const uint32_t epoch = st->epoch + (uint32_t)MAXPASS;
+    for (;;) {
+        if (tid == 0) s_chunk = (int64_t)atomicAdd(&st->tickets[MAXPASS], 1u);
+        __syncthreads();
+        const int64_t chunk = s_chunk;
+        if (chunk >= nchunks) break;
+        const int64_t t0 = chunk * MC_TILES + (int64_t)tid * MC_PER_THREAD;
+        uint32_t c[MC_PER_THREAD], sum = 0;
+#pragma unroll
+        for (int k = 0; k < MC_PER_THREAD; ++k) {
+            c[k] = t0 + k < ntiles ? counts[t0 + k] : 0u;
+            sum += c[k];
+        }
+        uint32_t x = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        uint32_t pre = 0, all = 0;
+        for (int w = 0; w < MC_TPB / 32; ++w) {
+            if (w < warp) pre += warp_sum[w];
+            all += warp_sum[w];
+        }
+        if (warp == 0) {
+            uint64_t *myw = lookback + chunk;
+            if (lane == 0) lb_store(myw, lb_pack(epoch, chunk == 0 ? LB_INC : LB_AGG, all));
+            uint64_t excl = 0;
+            if (chunk > 0) {
+                for (int64_t jt = chunk - 1;; jt -= 32) {
+                    const int64_t jj = jt - lane;
+                    const uint64_t w = jj >= 0 ? lb_wait(lookback + jj, epoch, &st->status) : lb_pack(epoch, LB_INC, 0u);
+                    const unsigned inc = __ballot_sync(0xFFFFFFFFu, ((w >> 32) & 3ull) != LB_AGG);
+                    if (inc) {
+                        const int first = __ffs(inc) - 1;
+                        excl += warp_sum_u64(lane <= first ? (uint64_t)(uint32_t)w : 0ull);
+                        break;
+                    }
+                    excl += warp_sum_u64((uint64_t)(uint32_t)w);
+                }
+                if (lane == 0) lb_store(myw, lb_pack(epoch, LB_INC, (uint32_t)(excl + all)));
+            }
+            if (lane == 0) {
+                s_base = (int64_t)excl;
+                if (chunk == nchunks - 1) {
+                    st->M_next = (int64_t)(excl + all);
+                    if ((int64_t)(excl + all) > mcap) atomicOr(&st->status, ST_CAPACITY | ST_CAP_LIST);
+                }
+            }
+        }
+        __syncthreads();
+        int64_t o = s_base + (int64_t)(pre + x - sum);
+#pragma unroll
+        for (int k = 0; k < MC_PER_THREAD; ++k) {
+            if (t0 + k < ntiles) tile_off[t0 + k] = o;
+            o += c[k];
+        }
+        __syncthreads();
+    }
+}
+
+// Copy of every tile's entries from its slot to its place in L_{t+1}: one
+// tile per warp at a time, grid-strided, every lane's loads of the tile
+// issued before its stores.
+template <typename LT>
+__global__ void __launch_bounds__(MC_TPB)
+k_merge_copy(const LT *__restrict__ slots, const uint32_t *__restrict__ counts, const int64_t *__restrict__ tile_off,
+             LT *__restrict__ out, const DevState *__restrict__ st, int64_t rcap) {
+    const int lane = threadIdx.x & 31;
+    if (*(volatile const uint32_t *)&st->status) return;
+    const int64_t M = st->M;
+    int64_t R = st->R;
+    if (R > rcap) R = rcap;
+    const int64_t ntiles = (M + R + MG_TILE - 1) / MG_TILE;
+    const int64_t nwarps = (int64_t)gridDim.x * (MC_TPB / 32);
+    for (int64_t t = (int64_t)blockIdx.x * (MC_TPB / 32) + (threadIdx.x >> 5); t < ntiles; t += nwarps) {
+        const uint32_t n = counts[t];
+        const int64_t o = tile_off[t];
+        const LT *src = slots + t * MG_TILE;
+        LT v[MG_IPT];
+#pragma unroll
+        for (int k = 0; k < MG_IPT; ++k)
+            if ((uint32_t)(lane + 32 * k) < n) v[k] = src[lane + 32 * k];
+#pragma unroll
+        for (int k = 0; k < MG_IPT; ++k)
+            if ((uint32_t)(lane + 32 * k) < n) out[o + lane + 32 * k] = v[k];
     }
 }
 

@@ -299,6 +299,29 @@ __device__ __forceinline__ MT group_mask(const SpawnCtx &c, MT A, MT X1, MT X2, 
     return ((g & 4) ? A : (MT)~A) & cm & bond_exists<MT>(c);
 }
 
+// the four importance-class masks of group_mask (class k: bonds of class k
+// that exist), computed once per configuration
+template <typename MT>
+__device__ __forceinline__ void class_group_masks(const SpawnCtx &c, MT X1, MT X2, MT (&cm)[4]) {
+    const MT E = bond_exists<MT>(c);
+    if (c.gk == 2) {
+        cm[0] = ~X1 & ~X2 & E;
+        cm[1] = ~X1 & X2 & E;
+        cm[2] = X1 & ~X2 & E;
+        cm[3] = X1 & X2 & E;
+    } else if (c.gk == 1) {
+        cm[0] = ~(X1 | X2) & E;
+        cm[1] = X1 & E;
+        cm[2] = X2 & E;
+        cm[3] = zero_mask<MT>();
+    } else {
+        cm[0] = E;
+        cm[1] = zero_mask<MT>();
+        cm[2] = zero_mask<MT>();
+        cm[3] = zero_mask<MT>();
+    }
+}
+
 // position of the r-th set bit (r from 0) of m, given r < popcount(m)
 __device__ __forceinline__ int select_bit(uint32_t m, uint32_t r) {
     int pos = 0;
@@ -747,11 +770,13 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             const MT Ai = anti_mask<MT, SW>(c, i32), Aj = anti_mask<MT, SW>(c, j32);
             MT X1, X2;
             class_masks<MT, SW>(c, i32, j32, X1, X2);
+            MT cm[4];
+            class_group_masks<MT>(c, X1, X2, cm);
             uint64_t Tket = 0, Tbra = 0, gkp = 0, gbp = 0;
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
-                const int ck = popcount(group_mask<MT>(c, Ai, X1, X2, g));
-                const int cb = popcount(group_mask<MT>(c, Aj, X1, X2, g));
+                const int ck = popcount(((g & 4) ? Ai : (MT)~Ai) & cm[g & 3]);
+                const int cb = popcount(((g & 4) ? Aj : (MT)~Aj) & cm[g & 3]);
                 gkp |= (uint64_t)ck << (8 * g);
                 gbp |= (uint64_t)cb << (8 * g);
                 const uint64_t rg = BATCH ? CR.urate8[g] : s.urate8[g];
@@ -908,6 +933,10 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 const bool fin = last_base && a + 1 == nmax;
                 while (qn >= 32 || (fin && qn > 0)) {
                     __syncwarp();
+                    // a drain adds up to 32 records: flush first when they
+                    // might not fit, so that no record takes the one-by-one
+                    // path through the global record counter
+                    flush(s, warp, lane, out, cap, st, npass, SP_STAGE - 32 + 1);
                     const int nd = qn < 32 ? qn : 32;
                     spawn_drain<T, MT, SW, FIELD, BATCH>(s, c, Pr, run_shift, warp, lane, nd, N, out, cap, st, npass);
                     qn -= nd;

@@ -84,7 +84,7 @@ EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_as
            "ddqmc_strerror"]
 NOALLOC_MAX_SPAWNS = 1 << 18
 NOALLOC_MAX_LIST = 1 << 20
-KERNEL_CLASSES = ["spawn_death", "radix_pass", "merge_partition", "merge", "finalize"]
+KERNEL_CLASSES = ["spawn_death", "radix_pass", "merge_partition", "merge", "finalize", "merge_compact"]
 
 _lib = None
 

@@ -58,11 +58,14 @@ class SolveRequest:
         return m, 2 * m
 
     def device_bytes(self) -> int:
-        """Device memory of the run: two lists and two spawn buffers, plus
-        look-back words and fixed tables."""
+        """Device memory of the run: two lists and two spawn buffers, the
+        merge's tile slots (one list record per merged position), plus
+        look-back words, tile bounds and fixed tables."""
         m, r = self.capacities()
         rec = 24 if self.sites > 31 else 16
-        return 2 * m * rec + 2 * r * rec + (r // 1536 + 2) * 256 * 8 + 3 * ((m + r) // 288 + 3) * 8 + (1 << 21)
+        tiles = (m + r) // 288 + 3
+        return (2 * m * rec + 2 * r * rec + tiles * 288 * rec + (r // 1536 + 2) * 256 * 8 + 3 * tiles * 8
+                + 4 * tiles + (1 << 21))
 
 
 @dataclasses.dataclass

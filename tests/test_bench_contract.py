@@ -104,8 +104,11 @@ def fake_gpu(monkeypatch):
     monkeypatch.setattr(ddqmc, "ddqmc_set_timing", lambda h, e: None)
     monkeypatch.setattr(ddqmc, "ddqmc_get_timing",
                         lambda h: {"spawn_death": (10.0, 2), "radix_pass": (5.0, 8), "merge_partition": (0.5, 2),
-                                   "merge": (4.0, 2), "finalize": (0.1, 2)})
+                                   "merge": (4.0, 2), "finalize": (0.1, 2),
+                                   "merge_compact": (0.4, 2)})
     monkeypatch.setattr(bench, "ClockSampler", _Sampler)
+    monkeypatch.setattr(bench, "pinned_list_buffers",
+                        lambda n: tuple(np.empty(n, dtype=d) for d in (np.uint64, np.uint64, np.int32, np.int32)))
     monkeypatch.setattr(bench, "oracle_sample",
                         lambda target, seconds, warmup, steps=None: (1.5e6, dict(target=int(target), walkers=1000,
                                                                                   steps=10, seconds=1.0)))
@@ -148,7 +151,7 @@ def test_single_run_line_has_every_key(fake_gpu, capsys, monkeypatch):
     assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and "sample" in cpu
     e2e = line["e2e"]
     assert e2e["unit"] == line["unit"] and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
-    assert line["gpu_launches"] == 16
+    assert line["gpu_launches"] == 18
     assert set(line["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
 
 
@@ -164,4 +167,4 @@ def test_batch_line_has_every_key(fake_gpu, capsys, monkeypatch):
         assert k in line, k
     assert set(line["arms"]) == {"batch", "sequential", "streams"}
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] > 0
-    assert line["gpu_launches"] == int(round(16 / 32.0 * line["steps"]))
+    assert line["gpu_launches"] == int(round(18 / 32.0 * line["steps"]))
