@@ -74,7 +74,7 @@ __device__ __forceinline__ uint64_t pack_rec(uint64_t key, bool flag, int re, in
 constexpr int RX_TPB = 256;                  // one thread per digit value
 constexpr int RX_WARPS = RX_TPB / 32;
 constexpr int RX_TILE_MIN = RX_TPB * 6;      // smallest tile (sizes the look-back words)
-constexpr int LB_BATCH = 8;                  // look-back words read together
+constexpr int LB_BATCH = 16;                 // look-back words read together
 
 template <typename T>
 struct RadixShared {
@@ -212,6 +212,16 @@ k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict
             for (int w = 0; w < warp; ++w) pre += s.scan_tmp[w];
             s.dstart[tid] = pre + x - cnt;
         }
+        __syncthreads();
+        // stage in digit order (tile-local positions need no look-back; the
+        // records' registers are free again before it)
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            if (dg[q] < 256u) {
+                const uint32_t pos = s.dstart[dg[q]] + s.whist[warp][dg[q]] + rk[q];
+                s.stage[pos] = r[q];
+            }
+        }
         // decoupled look-back for this digit, reading LB_BATCH earlier tiles at a time
         uint64_t excl = 0;
         {
@@ -235,16 +245,6 @@ k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict
         }
         if (tile > 0) lb_store(my, lb_pack(epoch, LB_INC, (uint32_t)(excl + cnt)));
         s.gbase[tid] = (int64_t)s.bucket[tid] + (int64_t)excl - (int64_t)s.dstart[tid];
-        __syncthreads();
-
-        // stage in digit order
-#pragma unroll
-        for (int q = 0; q < IPT; ++q) {
-            if (dg[q] < 256u) {
-                const uint32_t pos = s.dstart[dg[q]] + s.whist[warp][dg[q]] + rk[q];
-                s.stage[pos] = r[q];
-            }
-        }
         __syncthreads();
         int64_t nvalid = R - t0;
         if (nvalid > TILE) nvalid = TILE;
