@@ -69,7 +69,12 @@ def parse():
     ap.add_argument("--batch-target", type=float, default=2e5, help="largest per-run target of --batch")
     ap.add_argument("--serve", type=int, default=0,
                     help="instead: this many synthetic NESS-solve requests through the batching server, "
-                         "then the same requests one at a time")
+                         "then the same requests on streams and one at a time")
+    ap.add_argument("--serve-target", type=float, default=2e5, help="largest request target of --serve")
+    ap.add_argument("--serve-default", type=int, default=32,
+                    help="requests of the serving measurement added to the default line (targets up to 3e5, "
+                         "about 40 s for its three arms; 0: none)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuning)")
     ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"],
                     help="c3: the 4x4 benchmark (default); c1: 2x2 open, N_w target 1e4, timed after the shift "
                          "settles; c2: 3x3 periodic, N_w target 1e6, n_a 3, its first 200 steps (the window the "
@@ -364,6 +369,8 @@ def gpu_arm(args, world, rank, local, pg):
     left = st.t_var + args.settle - st.t
     if left > 0:
         run.step(left)
+    # launch shapes tuned on this list (the run's state is restored after the trials)
+    tuning = run.tune() if not args.no_tune else run.tuning()
     run.step(max(args.warmup, 3))
     tot0 = ddqmc.ddqmc_get_totals(run.h)
     ddqmc.ddqmc_set_timing(run.h, 1)
@@ -530,6 +537,14 @@ def gpu_arm(args, world, rank, local, pg):
                "sample": "oracle on the bench workload with shift target %d (about %d walkers), %d steps in %.1f s"
                          % (info["target"], info["walkers"], info["steps"], info["seconds"]),
                "host": cpu_cores_desc()}
+    serving = None
+    if args.serve_default > 0 and world == 1:
+        out, workload = serve_measure(args.serve_default, 3e5)
+        b, q = out["batched"], out["sequential"]
+        serving = {"metric": "NESS solves/h", "unit": "solves/h", "workload": workload,
+                   "value": b["solves_per_h"], "p50_s": b["p50_s"], "p95_s": b["p95_s"], "p99_s": b["p99_s"],
+                   "vs_sequential": b["solves_per_h"] / q["solves_per_h"],
+                   "vs_streams": b["solves_per_h"] / out["streams"]["solves_per_h"], "arms": out}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
@@ -542,17 +557,17 @@ def gpu_arm(args, world, rank, local, pg):
             "step_ms": {"median": statistics.median(step_ms), "p99": step_ms[min(len(step_ms) - 1,
                                                                                    int(0.99 * len(step_ms)))],
                         "min": step_ms[0], "max": step_ms[-1]},
-            "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
+            "kernels": kern, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "tuning": tuning,
             "gpu_launches": int(sum(v[1] for v in timing.values())), "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def serve_requests(n, seed=5):
+def serve_requests(n, max_target=2e5, seed=5):
     """Synthetic solve requests: Poisson arrivals (20/s), lattice 2x2 open, 3x3
     or 4x4 periodic, Jx ~ U[0.8, 1.1], gamma ~ U[0.5, 2], target log-uniform in
-    [1e4, 2e5] walkers, n_a = 3, samples from 256 steps after the shift switches
-    on, goal: blocked error of M_z below 0.004 within 4096 steps."""
+    [1e4, max_target] walkers, n_a = 3, samples from 256 steps after the shift
+    switches on, goal: blocked error of M_z below 0.004 within 4096 steps."""
     import numpy as np
     from paper_1802_05931_gb300 import serve as S
     rng = np.random.default_rng(seed)
@@ -562,26 +577,28 @@ def serve_requests(n, seed=5):
         t += rng.exponential(1.0 / 20.0)
         Lx, Ly, per = lat[rng.integers(0, 3)]
         req = S.SolveRequest(Lx, Ly, per, float(rng.uniform(0.8, 1.1)), 1.0, 1.0, float(rng.uniform(0.5, 2.0)),
-                             0.005, int(10 ** rng.uniform(4, math.log10(2e5))), n_a=3, seed=100 + k, control=1,
-                             t_eq=256, tol=0.004, min_samples=512, max_steps=4096)
+                             0.005, int(10 ** rng.uniform(4, math.log10(max_target))), n_a=3, seed=100 + k,
+                             control=1, t_eq=256, tol=0.004, min_samples=512, max_steps=4096)
         out.append((t, req))
     return out
 
 
-def serve_arm(args):
-    """Solves/h and latency percentiles of the batching server against the same
-    requests served one at a time (one run on the whole GPU)."""
+SERVE_ARMS = (("batched", 16, True), ("streams", 16, False), ("sequential", 1, False))
+
+
+def serve_measure(n, max_target):
+    """The same requests through the server three ways: packed into batches
+    on 16 concurrent units, on 16 concurrent streams without packing, and one
+    at a time on the whole GPU.  Solves/h over the makespan (first arrival to
+    last retirement) and latency percentiles (arrival to retirement)."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1802_05931_gb300 import serve as S
-    torch.cuda.set_device(0)
     free, total = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
-    reqs = serve_requests(args.serve)
+    reqs = serve_requests(n, max_target)
     out = {}
-    for name, slots in (("batched", 16), ("sequential", 1)):
-        srv = S.NessServer(budget, max_active=slots, chunk=64)
+    for name, slots, pack in SERVE_ARMS:
+        srv = S.NessServer(budget, max_active=slots, chunk=64, pack=pack)
         t0 = time.perf_counter()
         for ta, r in reqs:
             srv.submit(r, t_arrive=t0 + ta)
@@ -593,15 +610,26 @@ def serve_arm(args):
                      "p99_s": S.percentile(lat, 0.99),
                      "converged": sum(1 for r in srv.results.values() if r.converged),
                      "errors": sum(1 for r in srv.results.values() if r.error),
-                     "steps": sum(r.steps for r in srv.results.values()), "peak_active": srv.peak_active}
+                     "steps": sum(r.steps for r in srv.results.values()), "peak_active": srv.peak_active,
+                     "batches": srv.batches_made}
+    workload = ("%d requests, Poisson 20/s, 2x2 open / 3x3 / 4x4 periodic, Jx U[0.8,1.1], gamma U[0.5,2], "
+                "target log-U[1e4,%.0e], n_a 3, M_z error goal 0.004, at most 4096 steps" % (n, max_target))
+    return out, workload
+
+
+def serve_arm(args):
+    """Solves/h and latency percentiles of the batching server against the same
+    requests served on streams without packing and one at a time."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    out, workload = serve_measure(args.serve, args.serve_target)
     b = out["batched"]
     line = {"metric": "NESS solves/h", "value": b["solves_per_h"], "unit": "solves/h", "n_gpus": 1,
             "higher_is_better": True, "p50_s": b["p50_s"], "p95_s": b["p95_s"], "p99_s": b["p99_s"],
-            "data": "synthetic", "config": {"workload": "%d requests, Poisson 20/s, 2x2 open / 3x3 / 4x4 periodic, "
-                                                        "Jx U[0.8,1.1], gamma U[0.5,2], target log-U[1e4,2e5], "
-                                                        "n_a 3, M_z error goal 0.004, at most 4096 steps" % len(reqs),
-                                            "slots": 16, "chunk_steps": 64},
-            "batched": b, "sequential": out["sequential"]}
+            "data": "synthetic", "config": {"workload": workload, "units": 16, "chunk_steps": 64},
+            "batched": b, "streams": out["streams"], "sequential": out["sequential"]}
     print(json.dumps(line), flush=True)
     return 0
 

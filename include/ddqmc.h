@@ -216,12 +216,47 @@ int ddqmc_get_totals(ddqmc_run *run, int64_t *walker_steps, int64_t *entry_steps
 /* Per-kernel timing: with enable != 0 every later ddqmc_step brackets each
  * kernel class with CUDA events on the run's stream (classes: 0 spawn+death,
  * 1 radix passes, 2 merge partition, 3 merge+annihilation+estimators,
- * 4 finalize) and accumulates the elapsed times; enabling or disabling resets
- * the sums.  ddqmc_step_async does not record events. */
+ * 4 finalize, 5 compaction of the merged list: tile-offset scan and copy)
+ * and accumulates the elapsed times; enabling or disabling resets the sums.
+ * ddqmc_step_async does not record events. */
 int ddqmc_set_timing(ddqmc_run *run, int32_t enable);
 
-/* Accumulated milliseconds and launch counts per kernel class (cap >= 5). */
+/* Accumulated milliseconds and launch counts per kernel class (cap >= 6). */
 int ddqmc_get_timing(ddqmc_run *run, double *ms, int64_t *launches, int32_t cap);
+
+/* Launch shapes of a run's kernels (no counterpart in the paper: they change
+ * how fast a step runs, never what it computes).  Blocks per SM of each
+ * persistent kernel, the partition's blocks per SM, the walker count above
+ * which a configuration takes the spawn kernel's warp-cooperative path, and
+ * the radix tile of 8-byte packed records (12, 16 or 24 records per thread;
+ * 0 for other record types).  step_ms_default and step_ms_tuned are filled
+ * by ddqmc_tune: the kernel time of one step with the default shapes and with
+ * the chosen ones, on the same list. */
+typedef struct {
+    int32_t spawn_blocks_per_sm, radix_blocks_per_sm, merge_blocks_per_sm;
+    int32_t copy_blocks_per_sm, scan_blocks_per_sm, partition_blocks_per_sm;
+    int32_t heavy_walkers;
+    int32_t radix_records_per_thread;
+    double step_ms_default, step_ms_tuned;
+} ddqmc_tuning;
+
+/* Autotune the launch shapes on the run's current walker list: the list and
+ * every piece of device state are saved, each candidate shape is timed over
+ * one step (CUDA events per kernel class), the state is restored after each
+ * trial and at the end, and each kernel class gets its fastest shape (the
+ * classes do not depend on each other's shapes).  The run then continues
+ * exactly as if the call had not been made, with the chosen shapes, which are
+ * also kept for later runs of the same lattice size, record type and batch
+ * kind in this process.  Needs a non-empty list and no sticky error; takes
+ * temporary device memory of one list and the blocking cells; waits for the
+ * run's stream.  out may be NULL.  Errors: INVALID_ARG, OOM, CUDA, and the
+ * run's sticky status. */
+int ddqmc_tune(ddqmc_run *run, ddqmc_tuning *out);
+
+/* Use the given launch shapes (each clamped to what its kernel can hold;
+ * step_ms_* are ignored) or read the shapes in use. */
+int ddqmc_set_tuning(ddqmc_run *run, const ddqmc_tuning *in);
+int ddqmc_get_tuning(ddqmc_run *run, ddqmc_tuning *out);
 
 /* ---- batches of runs in one walker store -------------------------------------
  * The paper averages many independent runs per parameter point (Sec. V: 21
@@ -273,6 +308,15 @@ typedef struct {
  * error. */
 int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_run_spec *runs,
                        const ddqmc_guide *guide, const ddqmc_options *opt, ddqmc_run **out);
+
+/* Retire run `run` of a batch (no counterpart in the paper: it lets a
+ * server stop paying for a run whose answer it already has).  From the next
+ * step on, the run's configurations spawn nothing and the merge drops them,
+ * so the run's list is empty after one step; the other runs of the batch are
+ * unaffected (runs never interact).  Issued on the batch's stream, ordered
+ * before the steps enqueued after it; not undone.  Errors: INVALID_ARG (not a
+ * batch, or run out of range), CUDA. */
+int ddqmc_batch_retire(ddqmc_run *batch, int32_t run);
 
 /* Estimates of run `run` of a batch (as ddqmc_estimators). */
 int ddqmc_batch_estimators(ddqmc_run *batch, int32_t run, ddqmc_estimates *out);

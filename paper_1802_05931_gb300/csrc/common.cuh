@@ -95,7 +95,9 @@ struct RunParams {
     uint32_t ufrate32[4];
     float ufinv[4];
     float jinv;
-    int32_t pad3;
+    // a run of a batch that was retired (0): its configurations spawn nothing
+    // and leave the list at the next merge; the other runs do not notice
+    int32_t active;
 };
 
 // Device-resident state of a run, updated by the kernels of each step.  A

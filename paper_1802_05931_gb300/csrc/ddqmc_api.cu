@@ -45,6 +45,13 @@ struct ddqmc_run {
     int device = 0;
     int cur = 0;                 // which L buffer holds the current list
     int g_spawn = 0, g_radix = 0, g_part = 0, g_merge = 0, g_scan = 0, g_copy = 0;
+    // launch shapes: SMs the grids are sized for, the most blocks per SM each
+    // persistent kernel can hold (radix: per tile size of packed records),
+    // and the shapes in use (defaults, a cached tuning, or ddqmc_tune's)
+    int sms = 1;
+    int occ_spawn = 1, occ_radix[3] = {1, 1, 1}, occ_merge = 1, occ_copy = 1, occ_scan = 1;
+    ddqmc_tuning tune;
+    size_t blk_cells = 0;        // blocking cells held in dBlk
     int g_radix_wide = 0;        // radix grid of 16-byte records (standalone annihilation)
     int g_merge_ann = 0;         // merge grid of 16-byte records (standalone annihilation)
     int g_copy_ann = 0;          // compaction copy grid of 16-byte records (standalone annihilation)
@@ -116,6 +123,7 @@ int build_params(ddqmc_run *r, RunParams &P, const ddqmc_lattice *lat, double Jx
                  double gamma, double dt, int64_t target, int32_t n_a, const ddqmc_guide *guide,
                  const ddqmc_options &o) {
     std::memset(&P, 0, sizeof(P));
+    P.active = 1;
     const int Lx = lat->Lx, Ly = lat->Ly, per = lat->periodic ? 1 : 0;
     if (Lx < 1 || Ly < 1 || (int64_t)Lx * Ly > 64) return DDQMC_ERR_INVALID_ARG;
     if (per && (Lx == 2 || Ly == 2)) return DDQMC_ERR_INVALID_ARG;
@@ -299,6 +307,15 @@ int dalloc_bytes(void **p, size_t bytes) {
     return DDQMC_OK;
 }
 
+int occupancy(const void *fn, int tpb, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tpb, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm;
+}
+
 int occupancy_grid(const void *fn, int tpb, size_t smem, int sms) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tpb, smem) != cudaSuccess || per_sm < 1) {
@@ -375,6 +392,15 @@ constexpr size_t MG_SMEM = sizeof(MergeShared<Rec>);
 constexpr size_t MGP_SMEM = sizeof(MergeShared<uint64_t>);
 constexpr size_t SPW_SMEM = sizeof(SpawnShared<RecW>);
 constexpr size_t RXW_SMEM = sizeof(RadixShared<RecW>);
+// radix tile sizes (records per thread) of packed records the tuner chooses from
+constexpr int RX_PK_IPT[3] = {12, 16, 24};
+constexpr size_t RXP_SMEM_V[3] = {sizeof(RadixShared<uint64_t, 12>), sizeof(RadixShared<uint64_t, 16>),
+                                  sizeof(RadixShared<uint64_t, 24>)};
+const void *radix_packed_fn(int v) {
+    return v == 0 ? (const void *)k_radix_pass<uint64_t, 12>
+                  : (v == 2 ? (const void *)k_radix_pass<uint64_t, 24> : (const void *)k_radix_pass<uint64_t, 16>);
+}
+int radix_variant(int ipt) { return ipt == 12 ? 0 : (ipt == 24 ? 2 : 1); }
 constexpr size_t MGW_SMEM = sizeof(MergeShared<RecW>);
 
 // One step's launches for spawn records of type T (16-byte Rec, packed 8-byte,
@@ -393,15 +419,31 @@ void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(in
     mark(0, 0);
     if (P.field_on)
         k_spawn_death<T, true, BATCH><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(
-            r->dP, r->dS, Lc, sp0, r->rcap, Pr, rs);
+            r->dP, r->dS, Lc, sp0, r->rcap, Pr, rs, (int64_t)r->tune.heavy_walkers);
     else
         k_spawn_death<T, false, BATCH><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(
-            r->dP, r->dS, Lc, sp0, r->rcap, Pr, rs);
+            r->dP, r->dS, Lc, sp0, r->rcap, Pr, rs, (int64_t)r->tune.heavy_walkers);
     mark(0, 1);
     mark(1, 0);
-    for (int p = 0; p < P.npass; ++p)
-        k_radix_pass<T><<<r->g_radix, RX_TPB, rx_smem, r->stream>>>((p & 1) ? sp1 : sp0, (p & 1) ? sp0 : sp1, r->dS,
-                                                                   r->lb_radix, p, P.pass_shift[p], r->rcap);
+    for (int p = 0; p < P.npass; ++p) {
+        const T *in = (p & 1) ? sp1 : sp0;
+        T *outp = (p & 1) ? sp0 : sp1;
+        if constexpr (std::is_same<T, uint64_t>::value) {
+            const int v = radix_variant(r->tune.radix_records_per_thread);
+            if (v == 0)
+                k_radix_pass<T, 12><<<r->g_radix, RX_TPB, RXP_SMEM_V[0], r->stream>>>(in, outp, r->dS, r->lb_radix, p,
+                                                                                    P.pass_shift[p], r->rcap);
+            else if (v == 2)
+                k_radix_pass<T, 24><<<r->g_radix, RX_TPB, RXP_SMEM_V[2], r->stream>>>(in, outp, r->dS, r->lb_radix, p,
+                                                                                    P.pass_shift[p], r->rcap);
+            else
+                k_radix_pass<T, 16><<<r->g_radix, RX_TPB, RXP_SMEM_V[1], r->stream>>>(in, outp, r->dS, r->lb_radix, p,
+                                                                                    P.pass_shift[p], r->rcap);
+        } else {
+            k_radix_pass<T><<<r->g_radix, RX_TPB, rx_smem, r->stream>>>(in, outp, r->dS, r->lb_radix, p,
+                                                                       P.pass_shift[p], r->rcap);
+        }
+    }
     mark(1, 1);
     const T *sorted = (P.npass & 1) ? sp1 : sp0;
     mark(2, 0);
@@ -447,6 +489,82 @@ void initial_state(const RunParams &P, double S0, int64_t n0, DevState &hs) {
     host_death_table(P, S0, hs);
 }
 
+// ---- launch shapes --------------------------------------------------------
+// Results never depend on the launch shapes (every draw is keyed by the
+// configuration, tiles are taken by ticket and reduced in key order), so
+// the shapes only change the time a step takes.
+
+ddqmc_tuning default_tuning(const ddqmc_run *r) {
+    ddqmc_tuning t;
+    std::memset(&t, 0, sizeof(t));
+    t.spawn_blocks_per_sm = r->occ_spawn;
+    t.radix_blocks_per_sm = r->occ_radix[1];
+    t.merge_blocks_per_sm = r->occ_merge;
+    t.copy_blocks_per_sm = r->occ_copy;
+    t.scan_blocks_per_sm = r->occ_scan;
+    t.partition_blocks_per_sm = 4;
+    t.heavy_walkers = SP_HEAVY;
+    t.radix_records_per_thread = r->packed ? 16 : 0;
+    return t;
+}
+
+int clamp_bps(int v, int hi) { return v < 1 ? 1 : (v > hi ? hi : v); }
+
+// Grids of the shapes t, each clamped to what the kernel can hold; records
+// the clamped shapes in r->tune and drops captured step graphs (they hold the
+// old grids).
+void apply_tuning(ddqmc_run *r, const ddqmc_tuning &t) {
+    ddqmc_tuning c = t;
+    if (!r->packed) c.radix_records_per_thread = 0;
+    else if (c.radix_records_per_thread != 12 && c.radix_records_per_thread != 24) c.radix_records_per_thread = 16;
+    const int rv = radix_variant(c.radix_records_per_thread);
+    c.spawn_blocks_per_sm = clamp_bps(c.spawn_blocks_per_sm, r->occ_spawn);
+    c.radix_blocks_per_sm = clamp_bps(c.radix_blocks_per_sm, r->occ_radix[rv]);
+    c.merge_blocks_per_sm = clamp_bps(c.merge_blocks_per_sm, r->occ_merge);
+    c.copy_blocks_per_sm = clamp_bps(c.copy_blocks_per_sm, r->occ_copy);
+    c.scan_blocks_per_sm = clamp_bps(c.scan_blocks_per_sm, r->occ_scan);
+    c.partition_blocks_per_sm = clamp_bps(c.partition_blocks_per_sm, 8);
+    if (c.heavy_walkers < 32) c.heavy_walkers = 32;
+    r->tune = c;
+    r->g_spawn = c.spawn_blocks_per_sm * r->sms;
+    r->g_radix = c.radix_blocks_per_sm * r->sms;
+    r->g_merge = c.merge_blocks_per_sm * r->sms;
+    r->g_copy = c.copy_blocks_per_sm * r->sms;
+    r->g_scan = c.scan_blocks_per_sm * r->sms;
+    r->g_part = c.partition_blocks_per_sm * r->sms;
+    for (int k = 0; k < 2; ++k)
+        if (r->graph[k]) {
+            cudaGraphExecDestroy(r->graph[k]);
+            r->graph[k] = nullptr;
+        }
+}
+
+// Tunings found by ddqmc_tune in this process, by (sites, record kind, batch,
+// SMs): a later run of the same kind starts with the last one found.
+struct TuneKey {
+    int N, kind, batch, sms;
+    bool operator==(const TuneKey &o) const { return N == o.N && kind == o.kind && batch == o.batch && sms == o.sms; }
+};
+std::vector<std::pair<TuneKey, ddqmc_tuning>> g_tune_cache;
+
+TuneKey tune_key(const ddqmc_run *r) {
+    return TuneKey{r->hp.N, r->packed ? 1 : (r->wide ? 2 : 0), r->nruns > 0 ? 1 : 0, r->sms};
+}
+
+bool cached_tuning(const ddqmc_run *r, ddqmc_tuning *out) {
+    const TuneKey k = tune_key(r);
+    for (const auto &e : g_tune_cache)
+        if (e.first == k) { *out = e.second; return true; }
+    return false;
+}
+
+void cache_tuning(const ddqmc_run *r, const ddqmc_tuning &t) {
+    const TuneKey k = tune_key(r);
+    for (auto &e : g_tune_cache)
+        if (e.first == k) { e.second = t; return; }
+    g_tune_cache.push_back({k, t});
+}
+
 // Stream, device buffers (capacities clamped to [4096, 2^31 - 1]), blocking
 // cells, kernel attributes and persistent grid sizes of a run or a batch
 // (r->hp, r->nruns, r->wide and r->packed already set).
@@ -475,6 +593,7 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     rc |= dalloc(&r->dP, 1);
     rc |= dalloc(&r->dS, 1);
     rc |= dalloc(&r->dBlk, blk_cells);
+    r->blk_cells = blk_cells;
     const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
     const size_t ssize = r->wide ? sizeof(RecW) : sizeof(Rec);   // standalone annihilation uses 16-byte Rec
     // 64 bytes past the last record: the merge's bulk copies widen each range
@@ -515,6 +634,7 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     attr((const void *)k_spawn_death<RecW, false, true>, SPW_SMEM);
     attr((const void *)k_radix_pass<Rec>, RX_SMEM);
     attr((const void *)k_radix_pass<uint64_t>, RXP_SMEM);
+    for (int v = 0; v < 3; ++v) attr(radix_packed_fn(v), RXP_SMEM_V[v]);
     attr((const void *)k_radix_pass<RecW>, RXW_SMEM);
     attr((const void *)k_merge<Rec, false>, MG_SMEM);
     attr((const void *)k_merge<uint64_t, false>, MGP_SMEM);
@@ -555,16 +675,19 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     }
     r->mg_smem = sm + est_bytes;
     if (B && r->mg_smem > bmax) return DDQMC_ERR_UNSUPPORTED;   // too many runs x observables
-    r->g_spawn = occupancy_grid(fs, SP_TPB, ss, sms);
-    r->g_radix = occupancy_grid(fr, RX_TPB, sr, sms);
-    r->g_merge = occupancy_grid(fm, MG_TPB, r->mg_smem, sms);
+    r->sms = sms;
+    r->occ_spawn = occupancy(fs, SP_TPB, ss);
+    for (int v = 0; v < 3; ++v)
+        r->occ_radix[v] = r->packed ? occupancy(radix_packed_fn(v), RX_TPB, RXP_SMEM_V[v]) : occupancy(fr, RX_TPB, sr);
+    r->occ_merge = occupancy(fm, MG_TPB, r->mg_smem);
     r->g_merge_ann = occupancy_grid((const void *)k_merge<Rec, false>, MG_TPB, MG_SMEM, sms);
     r->g_radix_wide = occupancy_grid((const void *)k_radix_pass<Rec>, RX_TPB, RX_SMEM, sms);
     r->g_copy_ann = occupancy_grid((const void *)k_merge_copy<Rec>, MC_TPB, 0, sms);
-    r->g_part = 4 * sms;
-    r->g_scan = occupancy_grid((const void *)k_merge_scan, MC_TPB, 0, sms);
-    r->g_copy = occupancy_grid(r->wide ? (const void *)k_merge_copy<RecW> : (const void *)k_merge_copy<Rec>, MC_TPB,
-                               0, sms);
+    r->occ_scan = occupancy((const void *)k_merge_scan, MC_TPB, 0);
+    r->occ_copy = occupancy(r->wide ? (const void *)k_merge_copy<RecW> : (const void *)k_merge_copy<Rec>, MC_TPB, 0);
+    r->tune = default_tuning(r);
+    cached_tuning(r, &r->tune);
+    apply_tuning(r, r->tune);
     bool okc = cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * blk_cells, r->stream) == cudaSuccess;
     okc = okc && cudaMemsetAsync(r->lb_radix, 0, sizeof(uint64_t) * (size_t)rtiles * 256, r->stream) == cudaSuccess;
     okc = okc && cudaMemsetAsync(r->lb_merge, 0, sizeof(uint64_t) * (size_t)mtiles, r->stream) == cudaSuccess;
@@ -1012,6 +1135,82 @@ int estimates_of(ddqmc_run *r, int k, ddqmc_estimates *out) {
 
 }  // namespace
 
+namespace {
+
+// Device state of a run saved for the tuning trials.
+struct TuneBackup {
+    DevState st;
+    std::vector<DevState> rs;
+    void *list = nullptr;
+    BlkCell *blk = nullptr;
+    int cur = 0;
+    int64_t M = 0;
+};
+
+// Put the saved state back; the look-back epoch moves past every epoch the
+// trials used, so no status word they left can match a later step.
+int tune_restore(ddqmc_run *r, const TuneBackup &b) {
+    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
+    uint32_t ep = 0;
+    bool ok = cudaMemcpyAsync(&ep, &r->dS->epoch, sizeof(ep), cudaMemcpyDeviceToHost, r->stream) == cudaSuccess &&
+              cudaStreamSynchronize(r->stream) == cudaSuccess;
+    DevState h = b.st;
+    h.epoch = (ep + 16u) & 0x3FFFFFFFu;
+    r->cur = b.cur;
+    ok = ok && cudaMemcpyAsync(r->L[b.cur], b.list, lsize * (size_t)b.M, cudaMemcpyDeviceToDevice, r->stream) ==
+                   cudaSuccess;
+    ok = ok && cudaMemcpyAsync(r->dS, &h, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    if (r->nruns)
+        ok = ok && cudaMemcpyAsync(r->dRS, b.rs.data(), sizeof(DevState) * b.rs.size(), cudaMemcpyHostToDevice,
+                                   r->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(r->dBlk, b.blk, sizeof(BlkCell) * r->blk_cells, cudaMemcpyDeviceToDevice,
+                               r->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    r->host_status = 0;
+    return DDQMC_OK;
+}
+
+// One step with the shapes t from the saved state; kernel-class times into ms.
+int tune_trial(ddqmc_run *r, const TuneBackup &b, const ddqmc_tuning &t, double *ms) {
+    int rc = tune_restore(r, b);
+    if (rc != DDQMC_OK) return rc;
+    apply_tuning(r, t);
+    for (int k = 0; k < 8; ++k) { r->kernel_ms[k] = 0.0; r->kernel_launches[k] = 0; }
+    rc = enqueue_steps(r, 1);
+    if (rc != DDQMC_OK) return rc;
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    collect_timing(r, 1);
+    rc = read_status(r);
+    if (rc != DDQMC_OK) return rc;
+    for (int k = 0; k < NKCLASS; ++k) ms[k] = r->kernel_ms[k];
+    return DDQMC_OK;
+}
+
+// Candidate shapes: every (blocks per SM, heavy threshold) of the spawn
+// kernel and every (blocks per SM, tile) of the radix passes once, paired
+// in one trial each, with the merge, partition and compaction shapes cycling.
+std::vector<ddqmc_tuning> tune_candidates(const ddqmc_run *r) {
+    std::vector<ddqmc_tuning> c;
+    c.push_back(r->tune);
+    const int heavy[3] = {256, 1024, 4096}, part[3] = {2, 4, 8};
+    for (int i = 0; i < 9; ++i) {
+        ddqmc_tuning t = r->tune;
+        t.spawn_blocks_per_sm = 1 + i % 3;
+        t.heavy_walkers = heavy[i / 3];
+        t.radix_blocks_per_sm = 1 + i / 3;
+        t.radix_records_per_thread = r->packed ? RX_PK_IPT[i % 3] : 0;
+        t.merge_blocks_per_sm = 1 + (i + 1) % 3;
+        t.partition_blocks_per_sm = part[i % 3];
+        t.copy_blocks_per_sm = 2 + 2 * (i % 3);
+        t.scan_blocks_per_sm = 1 + (i + 2) % 3;
+        c.push_back(t);
+    }
+    return c;
+}
+
+}  // namespace
+
 extern "C" {
 
 int ddqmc_default_options(ddqmc_options *o) {
@@ -1308,6 +1507,116 @@ int ddqmc_blocking_moments(ddqmc_run *r, int32_t k, int32_t levels, int64_t *hn,
 int ddqmc_estimators(ddqmc_run *r, ddqmc_estimates *out) {
     if (!r || !out || r->nruns) return DDQMC_ERR_INVALID_ARG;
     return estimates_of(r, 0, out);
+}
+
+int ddqmc_get_tuning(ddqmc_run *r, ddqmc_tuning *out) {
+    if (!r || !out) return DDQMC_ERR_INVALID_ARG;
+    *out = r->tune;
+    return DDQMC_OK;
+}
+
+int ddqmc_set_tuning(ddqmc_run *r, const ddqmc_tuning *in) {
+    if (!r || !in) return DDQMC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    apply_tuning(r, *in);
+    return DDQMC_OK;
+}
+
+int ddqmc_tune(ddqmc_run *r, ddqmc_tuning *out) {
+    if (!r) return DDQMC_ERR_INVALID_ARG;
+    int rc = read_status(r);
+    if (rc != DDQMC_OK) return rc;
+    TuneBackup b;
+    if (cudaMemcpyAsync(&b.st, r->dS, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    if (r->nruns) {
+        b.rs.resize((size_t)r->nruns);
+        if (cudaMemcpyAsync(b.rs.data(), r->dRS, sizeof(DevState) * (size_t)r->nruns, cudaMemcpyDeviceToHost,
+                            r->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return DDQMC_ERR_CUDA;
+        }
+    }
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    b.M = b.st.M;
+    b.cur = r->cur;
+    if (b.M <= 0) return DDQMC_ERR_INVALID_ARG;
+    const size_t lsize = r->wide ? sizeof(RecW) : sizeof(Rec);
+    if (dalloc_bytes(&b.list, lsize * (size_t)b.M) != DDQMC_OK) return DDQMC_ERR_OOM;
+    if (dalloc(&b.blk, r->blk_cells) != DDQMC_OK) { cudaFree(b.list); return DDQMC_ERR_OOM; }
+    bool ok = cudaMemcpyAsync(b.list, r->L[b.cur], lsize * (size_t)b.M, cudaMemcpyDeviceToDevice, r->stream) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(b.blk, r->dBlk, sizeof(BlkCell) * r->blk_cells, cudaMemcpyDeviceToDevice, r->stream) ==
+                  cudaSuccess &&
+              cudaStreamSynchronize(r->stream) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(b.list);
+        cudaFree(b.blk);
+        return DDQMC_ERR_CUDA;
+    }
+    const bool timing0 = r->timing;
+    r->timing = true;
+    const std::vector<ddqmc_tuning> cand = tune_candidates(r);
+    // per kernel class: best time and the shape that gave it
+    const int cls[5] = {KC_SPAWN, KC_RADIX, KC_PARTITION, KC_MERGE, KC_COMPACT};
+    double best[5] = {1e300, 1e300, 1e300, 1e300, 1e300};
+    ddqmc_tuning pick[5];
+    double def_ms = 1e300;
+    for (int rep = 0; rep < 2 && rc == DDQMC_OK; ++rep)
+        for (size_t i = 0; i < cand.size() && rc == DDQMC_OK; ++i) {
+            double ms[NKCLASS] = {0};
+            rc = tune_trial(r, b, cand[i], ms);
+            if (rc != DDQMC_OK) break;
+            double tot = 0.0;                   // the tuned classes (finalize has no shape to tune)
+            for (int q = 0; q < 5; ++q) tot += ms[cls[q]];
+            if (i == 0 && tot < def_ms) def_ms = tot;
+            for (int q = 0; q < 5; ++q)
+                if (ms[cls[q]] < best[q]) { best[q] = ms[cls[q]]; pick[q] = r->tune; }
+        }
+    ddqmc_tuning t = r->tune;
+    if (rc == DDQMC_OK) {
+        t.spawn_blocks_per_sm = pick[0].spawn_blocks_per_sm;
+        t.heavy_walkers = pick[0].heavy_walkers;
+        t.radix_blocks_per_sm = pick[1].radix_blocks_per_sm;
+        t.radix_records_per_thread = pick[1].radix_records_per_thread;
+        t.partition_blocks_per_sm = pick[2].partition_blocks_per_sm;
+        t.merge_blocks_per_sm = pick[3].merge_blocks_per_sm;
+        t.copy_blocks_per_sm = pick[4].copy_blocks_per_sm;
+        t.scan_blocks_per_sm = pick[4].scan_blocks_per_sm;
+    } else {
+        t = cand[0];
+    }
+    const int rrc = tune_restore(r, b);
+    apply_tuning(r, t);
+    r->timing = timing0;
+    for (int k = 0; k < 8; ++k) { r->kernel_ms[k] = 0.0; r->kernel_launches[k] = 0; }
+    cudaFree(b.list);
+    cudaFree(b.blk);
+    if (rc != DDQMC_OK) return rc;
+    if (rrc != DDQMC_OK) return rrc;
+    double tuned = 0.0;
+    for (int q = 0; q < 5; ++q) tuned += best[q];
+    r->tune.step_ms_default = def_ms;
+    r->tune.step_ms_tuned = tuned;
+    cache_tuning(r, r->tune);
+    if (out) *out = r->tune;
+    return DDQMC_OK;
+}
+
+int ddqmc_batch_retire(ddqmc_run *r, int32_t run) {
+    if (!r || r->nruns == 0 || run < 0 || run >= r->nruns) return DDQMC_ERR_INVALID_ARG;
+    r->hpr[(size_t)run].active = 0;
+    // ordered on the batch's stream before every later step (the captured
+    // graphs read the parameters from device memory when they run)
+    if (cudaMemcpyAsync(&r->dPr[run].active, &r->hpr[(size_t)run].active, sizeof(int32_t), cudaMemcpyHostToDevice,
+                        r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    return DDQMC_OK;
 }
 
 int ddqmc_batch_estimators(ddqmc_run *r, int32_t run, ddqmc_estimates *out) {

@@ -239,6 +239,42 @@ __device__ __forceinline__ void add_estimators(MergeShared<T> &s, unsigned long 
     }
 }
 
+// Exact warp sum of int32 values (two 32-bit reductions of the 16-bit
+// halves, so no partial sum leaves the int32 range).
+__device__ __forceinline__ int64_t warp_sum_i32(int32_t v) {
+    const uint32_t lo = (uint32_t)v & 0xFFFFu;
+    const int32_t hi = v >> 16;
+    const uint32_t slo = __reduce_add_sync(0xFFFFFFFFu, lo);
+    const int32_t shi = (int32_t)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)hi);
+    return (int64_t)shi * 65536 + (int64_t)slo;
+}
+
+// The diagonal numerators (Tr re, Tr im, N_w, sigma^z per site, zz per bond)
+// of the warp's diagonal entries, all of one run (entries elsewhere give 0):
+// summed over the warp, then one shared-memory atomic per observable.
+template <typename T>
+__device__ __forceinline__ void add_diagonal_warp(MergeShared<T> &s, unsigned long long *est, const RunParams &P,
+                                                  bool diag, uint64_t i, int32_t re, int32_t im, int lane) {
+    const int N = P.N, B = P.B;
+    const int32_t x = diag ? re : 0;
+    int64_t t;
+    t = warp_sum_i32(x);
+    if (lane == 0 && t) atomicAdd(&est[0], (unsigned long long)t);
+    t = warp_sum_i32(diag ? im : 0);
+    if (lane == 0 && t) atomicAdd(&est[1], (unsigned long long)t);
+    t = warp_sum_i32(x < 0 ? -x : x);
+    if (lane == 0 && t) atomicAdd(&est[2], (unsigned long long)t);
+    for (int k = 0; k < N; ++k) {
+        t = warp_sum_i32(((i >> k) & 1ull) ? x : -x);
+        if (lane == 0 && t) atomicAdd(&est[5 + k], (unsigned long long)t);
+    }
+    for (int b = 0; b < B; ++b) {
+        const bool al = ((i >> s.bond_a[b]) & 1ull) == ((i >> s.bond_b[b]) & 1ull);
+        t = warp_sum_i32(al ? x : -x);
+        if (lane == 0 && t) atomicAdd(&est[5 + N + b], (unsigned long long)t);
+    }
+}
+
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
@@ -518,7 +554,9 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                             }
                             if (open) { sre += s.rem[warp][2]; sim += s.rem[warp][3]; }
                         }
-                        if (sre != 0 || sim != 0) {
+                        bool keep = sre != 0 || sim != 0;
+                        if constexpr (BATCH) keep = keep && Pr[batch_run(key_high(ik[k]), run_shift, nruns)].active != 0;
+                        if (keep) {
                             if (iabs64(sre) > 2147483647ll || iabs64(sim) > 2147483647ll) local_status |= ST_OVERFLOW;
                             omask |= 1u << k;
                             iv[k] = make_int2((int32_t)sre, (int32_t)sim);
@@ -554,36 +592,58 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
         __syncwarp();
         // estimator numerators of the outputs (walkers, entries; diagonal and
         // nearest-neighbour terms); a batch sums walkers and entries per run
-        // in registers while consecutive entries stay in one run
+        // in registers while consecutive entries stay in one run.  When many
+        // lanes hold diagonal entries of one run (small runs: most entries),
+        // their diagonal terms are summed over the warp first.
         {
             int brun = -1;
             int64_t bw = 0, bm = 0;
-            for (uint32_t q = lane; q < total; q += 32) {
-                const LT v = stage[q];
+            for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                const bool valid = q < total;
+                LT v;
+                set_list(v, KT{});
+                v.re = 0;
+                v.im = 0;
+                if (valid) v = stage[q];
                 uint64_t i, j;
                 key_words(list_key<KT>(v), nmask, N, i, j);
-                const int64_t w = iabs64(v.re) + iabs64(v.im);
                 unsigned long long *est = s.est;
+                int rr = 0;
                 if constexpr (BATCH) {
-                    const int rr = batch_run(key_high(list_key<KT>(v)), run_shift, nruns);
+                    rr = batch_run(key_high(list_key<KT>(v)), run_shift, nruns);
                     j &= nmask;
-                    if (rr != brun) {
-                        if (brun >= 0) {
-                            atomicAdd(&best[(size_t)brun * nobs + 3], (unsigned long long)bw);
-                            atomicAdd(&best[(size_t)brun * nobs + 4], (unsigned long long)bm);
-                        }
-                        brun = rr;
-                        bw = 0;
-                        bm = 0;
-                    }
-                    bw += w;
-                    bm += 1;
                     est = best + (size_t)rr * nobs;
-                } else {
-                    my_w += w;
-                    my_m += 1;
                 }
-                if (i == j || __popcll(i ^ j) <= 2) add_estimators(s, est, P, i, j, v.re, v.im);
+                if (valid) {
+                    const int64_t w = iabs64(v.re) + iabs64(v.im);
+                    if constexpr (BATCH) {
+                        if (rr != brun) {
+                            if (brun >= 0) {
+                                atomicAdd(&best[(size_t)brun * nobs + 3], (unsigned long long)bw);
+                                atomicAdd(&best[(size_t)brun * nobs + 4], (unsigned long long)bm);
+                            }
+                            brun = rr;
+                            bw = 0;
+                            bm = 0;
+                        }
+                        bw += w;
+                        bm += 1;
+                    } else {
+                        my_w += w;
+                        my_m += 1;
+                    }
+                }
+                const bool diag = valid && i == j;
+                const unsigned dm = __ballot_sync(0xFFFFFFFFu, diag);
+                bool warp_diag = false;
+                if (__popc(dm) >= 4) {
+                    const int r0 = __shfl_sync(0xFFFFFFFFu, rr, __ffs(dm) - 1);
+                    warp_diag = __all_sync(0xFFFFFFFFu, !diag || rr == r0);
+                    if (warp_diag)
+                        add_diagonal_warp(s, BATCH ? best + (size_t)r0 * nobs : s.est, P, diag, i, v.re, v.im, lane);
+                }
+                if (valid && (diag ? !warp_diag : __popcll(i ^ j) <= 2)) add_estimators(s, est, P, i, j, v.re, v.im);
             }
             if (BATCH && brun >= 0) {
                 atomicAdd(&best[(size_t)brun * nobs + 3], (unsigned long long)bw);

@@ -76,9 +76,11 @@ constexpr int RX_WARPS = RX_TPB / 32;
 constexpr int RX_TILE_MIN = RX_TPB * 6;      // smallest tile (sizes the look-back words)
 constexpr int LB_BATCH = 16;                 // look-back words read together
 
-template <typename T>
+// IPT: records per thread of a tile (default the record type's; the tuner
+// picks among the instantiated alternatives)
+template <typename T, int IPT = RecTraits<T>::IPT>
 struct RadixShared {
-    T stage[RX_TPB * RecTraits<T>::IPT];
+    T stage[RX_TPB * IPT];
     uint32_t whist[RX_WARPS][256];
     uint32_t bucket[256];      // start of each digit's bucket in the output
     uint32_t dstart[256];      // start of each digit inside the staged tile
@@ -107,15 +109,19 @@ k_digit_histogram(const T *__restrict__ in, DevState *__restrict__ st, int npass
         if ((&h[0][0])[q]) atomicAdd(&st->hist[q >> 8][q & 255], (&h[0][0])[q]);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(RX_TPB, RecTraits<T>::MINB)
+// blocks per SM a tile size is compiled for: more records per thread need more registers
+template <typename T, int IPT> struct RadixBlocks {
+    static constexpr int value = IPT > RecTraits<T>::IPT ? 2 : RecTraits<T>::MINB;
+};
+
+template <typename T, int IPT = RecTraits<T>::IPT>
+__global__ void __launch_bounds__(RX_TPB, (RadixBlocks<T, IPT>::value))
 k_radix_pass(const T *__restrict__ in, T *__restrict__ out, DevState *__restrict__ st,
              uint64_t *__restrict__ lookback, int pass, int shift, int64_t cap) {
     using TR = RecTraits<T>;
-    constexpr int IPT = TR::IPT;
     constexpr int TILE = RX_TPB * IPT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    RadixShared<T> &s = *reinterpret_cast<RadixShared<T> *>(smem_raw);
+    RadixShared<T, IPT> &s = *reinterpret_cast<RadixShared<T, IPT> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (block_stopped(st)) return;
     int64_t R = st->R;

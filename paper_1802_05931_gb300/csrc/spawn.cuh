@@ -53,7 +53,7 @@ constexpr int SP_TPB = 256;
 constexpr int SP_WARPS = SP_TPB / 32;
 constexpr int SP_STAGE = 128;      // staged records per warp
 constexpr int SP_FLUSH = 32;       // flush threshold at warp-uniform points
-constexpr int SP_HEAVY = 1024;     // configurations with more walkers use the warp-cooperative path
+constexpr int SP_HEAVY = 1024;     // default: configurations with more walkers use the warp-cooperative path
 
 // 128-bit bond mask (two-word keys: bonds 2k, 2k+1 of sites k < 32 in lo,
 // of sites k >= 32 in hi).
@@ -682,7 +682,8 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
 template <typename T, bool FIELD, bool BATCH>
 __global__ void __launch_bounds__(SP_TPB, 3)
 k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typename ListOf<T>::type *__restrict__ L,
-              T *__restrict__ out, int64_t cap, const RunParams *__restrict__ Pr, const DevState *__restrict__ rs) {
+              T *__restrict__ out, int64_t cap, const RunParams *__restrict__ Pr, const DevState *__restrict__ rs,
+              int64_t heavy_walkers) {
     // mask and spin-word types of the light path: 32-bit masks for packed
     // records (2N <= 32), 64-bit up to 31 sites, 128-bit (two words) beyond
     using MT = typename LightTypes<T>::MT;
@@ -756,8 +757,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
         const RunParams &CR = Pr[crun];
         const int64_t nre = iabs64(rec.re), nim = iabs64(rec.im);
         const int64_t nw = nre + nim;
-        const bool valid = e < M;
-        const bool heavy = valid && (nw > SP_HEAVY || !(BATCH ? CR.uniform != 0 : uniform));
+        const bool valid = e < M && (!BATCH || CR.active != 0);
+        const bool heavy = valid && (nw > heavy_walkers || !(BATCH ? CR.uniform != 0 : uniform));
         const bool light = valid && !heavy;
         const int na_r = BATCH ? CR.n_a : n_a;
         const bool init = (na_r == 0) || (i == j) || (nw > (int64_t)na_r);

@@ -29,6 +29,17 @@ class DDQMCError(RuntimeError):
         super().__init__("%s failed: %s (%d)" % (what, ERRORS.get(code, "?"), code))
 
 
+class ddqmc_tuning(C.Structure):
+    _fields_ = [("spawn_blocks_per_sm", C.c_int32), ("radix_blocks_per_sm", C.c_int32),
+                ("merge_blocks_per_sm", C.c_int32), ("copy_blocks_per_sm", C.c_int32),
+                ("scan_blocks_per_sm", C.c_int32), ("partition_blocks_per_sm", C.c_int32),
+                ("heavy_walkers", C.c_int32), ("radix_records_per_thread", C.c_int32),
+                ("step_ms_default", C.c_double), ("step_ms_tuned", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ddqmc_lattice(C.Structure):
     _fields_ = [("Lx", C.c_int32), ("Ly", C.c_int32), ("periodic", C.c_int32)]
 
@@ -78,9 +89,11 @@ class ddqmc_state(C.Structure):
 EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_async", "ddqmc_sync",
            "ddqmc_estimators", "ddqmc_raw_estimators", "ddqmc_blocking_moments",
            "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_get_state", "ddqmc_get_counts",
-           "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_annihilate",
+           "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_tune", "ddqmc_set_tuning",
+           "ddqmc_get_tuning", "ddqmc_annihilate",
            "ddqmc_annihilate_noalloc", "ddqmc_wait_selftest", "ddqmc_create_batch", "ddqmc_batch_estimators",
-           "ddqmc_batch_raw_estimators", "ddqmc_batch_export_walkers", "ddqmc_batch_get_state", "ddqmc_destroy",
+           "ddqmc_batch_raw_estimators", "ddqmc_batch_export_walkers", "ddqmc_batch_get_state", "ddqmc_batch_retire",
+           "ddqmc_destroy",
            "ddqmc_strerror"]
 NOALLOC_MAX_SPAWNS = 1 << 18
 NOALLOC_MAX_LIST = 1 << 20
@@ -126,6 +139,10 @@ def load(path: str = LIB_PATH):
     lib.ddqmc_batch_raw_estimators.argtypes = [vp, i32, P(i64), i32, P(i32)]
     lib.ddqmc_batch_export_walkers.argtypes = [vp, i32, P(u64), P(u64), P(i32), P(i32), i64, P(i64)]
     lib.ddqmc_batch_get_state.argtypes = [vp, i32, P(ddqmc_state)]
+    lib.ddqmc_batch_retire.argtypes = [vp, i32]
+    lib.ddqmc_tune.argtypes = [vp, P(ddqmc_tuning)]
+    lib.ddqmc_set_tuning.argtypes = [vp, P(ddqmc_tuning)]
+    lib.ddqmc_get_tuning.argtypes = [vp, P(ddqmc_tuning)]
     lib.ddqmc_destroy.argtypes = [vp]
     lib.ddqmc_destroy.restype = None
     lib.ddqmc_strerror.argtypes = [C.c_int]
@@ -323,6 +340,33 @@ def ddqmc_batch_raw_estimators(batch, k, cap=1024):
     return out[: n.value]
 
 
+def ddqmc_tune(run):
+    """Autotune the launch shapes on the run's current list (state restored); returns the chosen shapes."""
+    t = ddqmc_tuning()
+    _check(load().ddqmc_tune(run, C.byref(t)), "ddqmc_tune")
+    return t.as_dict()
+
+
+def ddqmc_get_tuning(run):
+    t = ddqmc_tuning()
+    _check(load().ddqmc_get_tuning(run, C.byref(t)), "ddqmc_get_tuning")
+    return t.as_dict()
+
+
+def ddqmc_set_tuning(run, **shapes):
+    """Change some launch shapes (keyword names of ddqmc_tuning), keeping the others."""
+    t = ddqmc_tuning()
+    _check(load().ddqmc_get_tuning(run, C.byref(t)), "ddqmc_get_tuning")
+    for k, v in shapes.items():
+        setattr(t, k, v)
+    _check(load().ddqmc_set_tuning(run, C.byref(t)), "ddqmc_set_tuning")
+
+
+def ddqmc_batch_retire(batch, k):
+    """Stop run k of a batch: its walkers leave the list at the next step."""
+    _check(load().ddqmc_batch_retire(batch, int(k)), "ddqmc_batch_retire")
+
+
 def ddqmc_batch_get_state(batch, k):
     s = ddqmc_state()
     _check(load().ddqmc_batch_get_state(batch, int(k), C.byref(s)), "ddqmc_batch_get_state")
@@ -409,6 +453,12 @@ class Run:
     def counts(self):
         return ddqmc_get_counts(self.h)
 
+    def tune(self):
+        return ddqmc_tune(self.h)
+
+    def tuning(self):
+        return ddqmc_get_tuning(self.h)
+
 
 def run_spec(Jx, Jy, Jz, gamma, dt, target, n_a=0, seed=1, damping=0.05, shift0=-1.0, n0=1000, control=0,
              t_eq=-1, field_h=0.0, field_axis=0):
@@ -486,6 +536,12 @@ class Batch:
 
     def state(self, k):
         return ddqmc_batch_get_state(self.h, k)
+
+    def retire(self, k):
+        ddqmc_batch_retire(self.h, k)
+
+    def tune(self):
+        return ddqmc_tune(self.h)
 
     def totals(self):
         return ddqmc_get_totals(self.h)

@@ -64,6 +64,12 @@ class _FakeRun:
     def raw_estimates(self, k=0):
         return np.zeros(8, dtype=np.int64)
 
+    def tune(self):
+        return {"spawn_blocks_per_sm": 3, "step_ms_default": 1.0, "step_ms_tuned": 0.9}
+
+    def tuning(self):
+        return {"spawn_blocks_per_sm": 3}
+
     def totals(self):
         return dict(walker_steps=self.ws, entry_steps=100 * self.t, spawn_records=300 * self.t,
                     merged_entries=100 * self.t)
@@ -107,6 +113,10 @@ def fake_gpu(monkeypatch):
                                    "merge": (4.0, 2), "finalize": (0.1, 2),
                                    "merge_compact": (0.4, 2)})
     monkeypatch.setattr(bench, "ClockSampler", _Sampler)
+    arm = {"solves_per_h": 100.0, "makespan_s": 1.0, "p50_s": 0.1, "p95_s": 0.2, "p99_s": 0.3, "converged": 1,
+           "errors": 0, "steps": 10, "peak_active": 1, "batches": 0}
+    monkeypatch.setattr(bench, "serve_measure",
+                        lambda n, t: ({k: dict(arm) for k in ("batched", "streams", "sequential")}, "fake"))
     monkeypatch.setattr(bench, "pinned_list_buffers",
                         lambda n: tuple(np.empty(n, dtype=d) for d in (np.uint64, np.uint64, np.int32, np.int32)))
     monkeypatch.setattr(bench, "oracle_sample",
@@ -153,6 +163,9 @@ def test_single_run_line_has_every_key(fake_gpu, capsys, monkeypatch):
     assert e2e["unit"] == line["unit"] and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     assert line["gpu_launches"] == 18
     assert set(line["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
+    sv = line["serving"]
+    assert sv["unit"] == "solves/h" and set(sv["arms"]) == {"batched", "streams", "sequential"}
+    assert sv["vs_sequential"] == pytest.approx(1.0)
 
 
 def test_batch_line_has_every_key(fake_gpu, capsys, monkeypatch):

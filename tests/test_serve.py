@@ -1,6 +1,8 @@
-"""Scheduling logic of the NESS-solve server, on the host with stand-in runs:
-admission by slots and by the device-memory budget, first come first served,
-no admission before arrival, retirement on the error goal or the step limit."""
+"""Scheduling logic of the NESS-solve server, on the host with stand-in runs
+and batches: admission by slots and by the device-memory budget, first come
+first served, no admission before arrival, retirement on the error goal or
+the step limit, packing of compatible requests into one batch, retirement of
+batch members at their own check points."""
 import math
 import types
 
@@ -47,8 +49,9 @@ def _req(target=1000, tol=0.05, max_steps=10000):
     return S.SolveRequest(2, 2, 0, 0.9, 1.0, 1.0, 1.0, 0.01, target, tol=tol, min_samples=64, max_steps=max_steps)
 
 
-def _server(budget, slots, clock, chunk=32):
-    return S.NessServer(budget, max_active=slots, chunk=chunk, make_run=FakeRun, clock=clock, keep_lists=True)
+def _server(budget, slots, clock, chunk=32, pack=False):
+    return S.NessServer(budget, max_active=slots, chunk=chunk, make_run=FakeRun, clock=clock, keep_lists=True,
+                        pack=pack, make_batch=FakeBatch)
 
 
 def test_retire_on_error_goal_in_whole_chunks():
@@ -78,8 +81,8 @@ def test_admission_by_slots_and_budget_first_come_first_served():
     starts = []
     while not srv.idle:
         srv.cycle()
-        assert len(srv._active) <= 2 and srv.bytes_in_use <= 2 * one + 1
-        starts += [s["id"] for s in srv._active if s["id"] not in starts]
+        assert len(srv.active_ids()) <= 2 and srv.bytes_in_use <= 2 * one + 1
+        starts += [i for i in srv.active_ids() if i not in starts]
         clock.t += 1.0
     assert starts == ids and srv.peak_active == 2
     assert all(srv.results[i].converged for i in ids)
@@ -91,13 +94,82 @@ def test_no_admission_before_arrival():
     a = srv.submit(_req(tol=0.05), t_arrive=0.0)
     b = srv.submit(_req(tol=0.05), t_arrive=5.0)
     srv.cycle()
-    assert [s["id"] for s in srv._active] == [a]
+    assert srv.active_ids() == [a]
     clock.t = 5.0
     srv.cycle()
-    assert sorted(s["id"] for s in srv._active) == [a, b]      # b joins while a runs
+    assert sorted(srv.active_ids()) == [a, b]      # b joins while a runs
     while not srv.idle:
         srv.cycle()
     assert srv.results[b].t_start == 5.0 and srv.results[a].t_start == 0.0
+
+
+class FakeBatch:
+    """Members behave as FakeRun would alone: error 1/sqrt(steps - 100)."""
+    made = []
+
+    def __init__(self, reqs, sm_limit):
+        self.reqs, self.t, self.retired, self.closed = list(reqs), 0, [], False
+        FakeBatch.made.append(self)
+
+    def step_async(self, n):
+        self.t += n
+
+    def sync(self):
+        pass
+
+    def estimates(self, k):
+        ns = max(0, self.t - 100)
+        return types.SimpleNamespace(mz=-0.5, mz_err=(1.0 / math.sqrt(ns)) if ns else float("nan"), n_samples=ns)
+
+    def export(self, k):
+        return ([self.t], [k], [1], [0])
+
+    def retire(self, k):
+        assert k not in self.retired
+        self.retired.append(k)
+
+    def close(self):
+        self.closed = True
+
+
+def test_compatible_requests_share_one_batch_and_retire_at_their_own_check_points():
+    FakeBatch.made = []
+    clock = FakeClock()
+    srv = _server(10 ** 12, 4, clock, pack=True)
+    tols = [0.05, 0.1, 0.2]                      # converge at different chunks
+    ids = [srv.submit(_req(tol=t)) for t in tols]
+    other = srv.submit(S.SolveRequest(3, 3, 1, 0.9, 1.0, 1.0, 1.0, 0.005, 1000, tol=0.05, min_samples=64))
+    limited = srv.submit(_req(tol=1e-9, max_steps=200))   # step limit between two check points
+    srv.cycle()
+    assert len(FakeBatch.made) == 1 and len(FakeBatch.made[0].reqs) == 4   # the 2x2 requests
+    assert FakeRun.live == 1                                             # the 3x3 one alone
+    srv.run_until_idle()
+    b = FakeBatch.made[0]
+    assert b.closed and FakeRun.live == 0 and srv.bytes_in_use == 0
+    # every member but the last is retired in the batch; the last one closes it
+    assert len(b.retired) == 3 and set(b.retired) <= {0, 1, 2, 3}
+    # each member's result is what it would be alone
+    for rid, t in zip(ids, tols):
+        alone = _server(10 ** 12, 1, FakeClock())
+        a = alone.submit(_req(tol=t))
+        alone.run_until_idle()
+        assert srv.results[rid].steps == alone.results[a].steps
+        assert srv.results[rid].n_samples == alone.results[a].n_samples and srv.results[rid].converged
+    assert srv.results[limited].steps == 200 and not srv.results[limited].converged
+    assert srv.results[other].converged and srv.batches_made == 1
+
+
+def test_batches_respect_max_batch_and_the_unit_slots():
+    FakeBatch.made = []
+    clock = FakeClock()
+    srv = S.NessServer(10 ** 12, max_active=2, chunk=32, make_run=FakeRun, clock=clock, pack=True, max_batch=3,
+                       make_batch=FakeBatch)
+    ids = [srv.submit(_req(tol=0.05)) for _ in range(8)]
+    srv.cycle()
+    assert [len(b.reqs) for b in FakeBatch.made] == [3, 3]     # two units, two left waiting
+    assert len(srv.active_ids()) == 6
+    srv.run_until_idle()
+    assert all(srv.results[i].converged for i in ids) and srv.bytes_in_use == 0
 
 
 def test_request_larger_than_budget_is_refused():
