@@ -422,7 +422,9 @@ def gpu_arm(args, world, rank, local, pg):
     kb = {"spawn_death": ((lb + 8) * dM + rb * dR) / K,
           "radix_pass": 2 * rb * dR / K,
           "merge": (lb * (dM + dMn) + rb * dR) / K,
-          "merge_compact": 2 * lb * dMn / K}
+          # two launches a step (tile-offset scan, copy): the copy's read and
+          # write of the merged list averaged over both
+          "merge_compact": lb * dMn / K}
     spawn_alg = ((lb + 8) * dM + lb * dR) / K
     ann_alg = lb * (dR + dM + dMn) / K
     positions = (dM + dR) / K
@@ -483,7 +485,8 @@ def gpu_arm(args, world, rank, local, pg):
     sm_keys = ("radix_pass", "merge_partition", "merge", "merge_compact")
     sortmerge_ms = sum(timing[k][0] for k in sm_keys if k in timing) / K
     sm_s = sortmerge_ms / 1e3
-    moved = kb["radix_pass"] * (timing["radix_pass"][1] / K) + kb["merge"] + kb["merge_compact"]
+    # kernel bytes a step: per-launch bytes x launches a step
+    moved = sum(kb[k] * timing[k][1] / K for k in ("radix_pass", "merge", "merge_compact") if k in timing)
     sm_dram = [dram(k) for k in sm_keys]
     sm_dram_bytes = (sum(d * timing[k][1] / K for d, k in zip(sm_dram, sm_keys) if k in timing)
                      if all(d is not None for d in sm_dram) else None)

@@ -591,11 +591,21 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
         }
         __syncwarp();
         // estimator numerators of the outputs (walkers, entries; diagonal and
-        // nearest-neighbour terms); a batch sums walkers and entries per run
-        // in registers while consecutive entries stay in one run.  When many
-        // lanes hold diagonal entries of one run (small runs: most entries),
-        // their diagonal terms are summed over the warp first.
-        {
+        // nearest-neighbour terms).  A single run sums walkers and entries in
+        // registers; a batch sums them per run while consecutive entries stay
+        // in one run, and when many lanes hold diagonal entries of one run
+        // (the small runs batches are made of: most entries) it sums their
+        // diagonal terms over the warp before the shared-memory atomics.
+        if constexpr (!BATCH) {
+            for (uint32_t q = lane; q < total; q += 32) {
+                const LT v = stage[q];
+                uint64_t i, j;
+                key_words(list_key<KT>(v), nmask, N, i, j);
+                my_w += iabs64(v.re) + iabs64(v.im);
+                my_m += 1;
+                if (i == j || __popcll(i ^ j) <= 2) add_estimators(s, s.est, P, i, j, v.re, v.im);
+            }
+        } else {
             int brun = -1;
             int64_t bw = 0, bm = 0;
             for (uint32_t q0 = 0; q0 < total; q0 += 32) {
@@ -608,31 +618,21 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                 if (valid) v = stage[q];
                 uint64_t i, j;
                 key_words(list_key<KT>(v), nmask, N, i, j);
-                unsigned long long *est = s.est;
-                int rr = 0;
-                if constexpr (BATCH) {
-                    rr = batch_run(key_high(list_key<KT>(v)), run_shift, nruns);
-                    j &= nmask;
-                    est = best + (size_t)rr * nobs;
-                }
+                const int rr = batch_run(key_high(list_key<KT>(v)), run_shift, nruns);
+                j &= nmask;
+                unsigned long long *est = best + (size_t)rr * nobs;
                 if (valid) {
-                    const int64_t w = iabs64(v.re) + iabs64(v.im);
-                    if constexpr (BATCH) {
-                        if (rr != brun) {
-                            if (brun >= 0) {
-                                atomicAdd(&best[(size_t)brun * nobs + 3], (unsigned long long)bw);
-                                atomicAdd(&best[(size_t)brun * nobs + 4], (unsigned long long)bm);
-                            }
-                            brun = rr;
-                            bw = 0;
-                            bm = 0;
+                    if (rr != brun) {
+                        if (brun >= 0) {
+                            atomicAdd(&best[(size_t)brun * nobs + 3], (unsigned long long)bw);
+                            atomicAdd(&best[(size_t)brun * nobs + 4], (unsigned long long)bm);
                         }
-                        bw += w;
-                        bm += 1;
-                    } else {
-                        my_w += w;
-                        my_m += 1;
+                        brun = rr;
+                        bw = 0;
+                        bm = 0;
                     }
+                    bw += iabs64(v.re) + iabs64(v.im);
+                    bm += 1;
                 }
                 const bool diag = valid && i == j;
                 const unsigned dm = __ballot_sync(0xFFFFFFFFu, diag);
@@ -640,12 +640,11 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                 if (__popc(dm) >= 4) {
                     const int r0 = __shfl_sync(0xFFFFFFFFu, rr, __ffs(dm) - 1);
                     warp_diag = __all_sync(0xFFFFFFFFu, !diag || rr == r0);
-                    if (warp_diag)
-                        add_diagonal_warp(s, BATCH ? best + (size_t)r0 * nobs : s.est, P, diag, i, v.re, v.im, lane);
+                    if (warp_diag) add_diagonal_warp(s, best + (size_t)r0 * nobs, P, diag, i, v.re, v.im, lane);
                 }
                 if (valid && (diag ? !warp_diag : __popcll(i ^ j) <= 2)) add_estimators(s, est, P, i, j, v.re, v.im);
             }
-            if (BATCH && brun >= 0) {
+            if (brun >= 0) {
                 atomicAdd(&best[(size_t)brun * nobs + 3], (unsigned long long)bw);
                 atomicAdd(&best[(size_t)brun * nobs + 4], (unsigned long long)bm);
             }
