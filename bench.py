@@ -674,6 +674,8 @@ def batch_arm(args):
     b = ddqmc.Batch(Lx, Ly, per, runs, capacity_entries=cap["capacity_entries"] * len(runs),
                     capacity_spawns=cap["capacity_spawns"] * len(runs))
     b.step(W)
+    # every arm's runs take tuned launch shapes (state restored after the trials)
+    batch_tuning = b.tune() if not args.no_tune else None
     w0 = b.totals()["walker_steps"]
     t0 = time.perf_counter()
     b.step(K)
@@ -693,6 +695,8 @@ def batch_arm(args):
         kw = {k: v for k, v in r.items() if k not in ("Jx", "Jy", "Jz", "gamma", "dt", "target")}
         one = ddqmc.Run(Lx, Ly, per, r["Jx"], r["Jy"], r["Jz"], r["gamma"], r["dt"], r["target"], **cap, **kw)
         one.step(W)
+        if not args.no_tune:
+            one.tune()
         w0 = ddqmc.ddqmc_get_totals(one.h)["walker_steps"]
         t0 = time.perf_counter()
         one.step(K)
@@ -712,6 +716,9 @@ def batch_arm(args):
         m.step_async(W)
     for m in many:
         m.sync()
+    if not args.no_tune:
+        for m in many:
+            m.tune()
     w0 = sum(ddqmc.ddqmc_get_totals(m.h)["walker_steps"] for m in many)
     t0 = time.perf_counter()
     for m in many:
@@ -746,6 +753,7 @@ def batch_arm(args):
                                     args.batch_target / 8, args.batch_target),
                        "timing": "host clock around the timed steps (each call waits for the device)"},
             "same_walker_steps": res["batch"][1] == res["sequential"][1] == res["streams"][1],
+            "batch_tuning": batch_tuning,
             "gpu_launches": int(round(launches_per_step * K)),
             "kernels": kern, "cpu_baseline": cpu_line,
             "arms": {k: {"seconds": v[0], "walker_steps": v[1], "walker_steps_per_s": rate[k]}

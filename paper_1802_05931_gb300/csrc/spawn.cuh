@@ -371,17 +371,22 @@ __device__ __forceinline__ int seg_select(const SpawnCtx &c, const uint64_t *rat
 template <typename MT>
 __device__ __forceinline__ int seg_select32(const SpawnCtx &c, const uint32_t *rate32, const float *rinv,
                                             uint64_t cnt, MT A, MT X1, MT X2, uint32_t v) {
-    int g = -1;
-    uint32_t q = 1;
-    float qi = 0.f;
+    // inclusive prefix P of the eight group totals; the group is the number
+    // of prefixes at or below v, found by a three-level search of selects
+    // (no serial subtract chain, no divergence)
+    uint32_t P[8], acc = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const uint32_t w = rate32[k] * (uint32_t)((cnt >> (8 * k)) & 0xFFull);
-        if (g < 0) {
-            if (v < w) { g = k; q = rate32[k]; qi = rinv[k]; }
-            else v -= w;
-        }
+        acc += rate32[k] * (uint32_t)((cnt >> (8 * k)) & 0xFFull);
+        P[k] = acc;
     }
+    const bool h4 = v >= P[3];
+    const bool h2 = v >= (h4 ? P[5] : P[1]);
+    const bool h1 = v >= (h4 ? (h2 ? P[6] : P[4]) : (h2 ? P[2] : P[0]));
+    const int g = (h4 ? 4 : 0) + (h2 ? 2 : 0) + (h1 ? 1 : 0);
+    v -= h4 ? (h2 ? (h1 ? P[6] : P[5]) : (h1 ? P[4] : P[3])) : (h2 ? (h1 ? P[2] : P[1]) : (h1 ? P[0] : 0u));
+    const uint32_t q = rate32[g];
+    const float qi = rinv[g];
     uint32_t r = (uint32_t)((float)v * qi);
     const uint64_t pq = (uint64_t)r * q;
     if (pq > v) --r;
@@ -908,9 +913,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 natt = q.natt[owner];
                 qT = q.T[owner];
             }
-            uint32_t nmax = natt;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(0xFFFFFFFFu, nmax, off));
+            const uint32_t nmax = __reduce_max_sync(0xFFFFFFFFu, natt);
             uint4 xb = x;
             uint32_t blk = 0;
             for (uint32_t a = 0; a < nmax; ++a) {
