@@ -313,6 +313,27 @@ __device__ __forceinline__ bool key_diagonal(const KT &k, uint64_t nmask, int N)
 // present, diagonal, or no initiator rule).  The outputs are staged in the
 // tile buffer and leave with one bulk store into the tile's slot
 // (slots + tile * MG_TILE), their number into counts[tile].
+// Sums of the spawn records S[b1, rem_e) (initiator re, im, other re, im)
+// over one warp, into out (lane 0 writes).
+template <typename T>
+__device__ __noinline__ void rem_sums(const T *__restrict__ S, int64_t b1, int64_t rem_e, int lane, int64_t *out) {
+    using TR = RecTraits<T>;
+    int64_t f0 = 0, f1 = 0, u0 = 0, u1 = 0;
+    for (int64_t q = b1 + lane; q < rem_e; q += 32) {
+        const T g = S[q];
+        if (TR::flag(g)) { f0 += TR::re(g); f1 += TR::im(g); }
+        else { u0 += TR::re(g); u1 += TR::im(g); }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        f0 += __shfl_xor_sync(0xFFFFFFFFu, f0, off);
+        f1 += __shfl_xor_sync(0xFFFFFFFFu, f1, off);
+        u0 += __shfl_xor_sync(0xFFFFFFFFu, u0, off);
+        u1 += __shfl_xor_sync(0xFFFFFFFFu, u1, off);
+    }
+    if (lane == 0) { out[0] = f0; out[1] = f1; out[2] = u0; out[3] = u1; }
+}
+
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(MG_TPB, MergeBlocks<T>::value)
 k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__restrict__ L, const T *__restrict__ S,
@@ -385,28 +406,14 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
             na1 = splits[tile + nwarps + 1];
             nrem = rem_end[tile + nwarps + 1];
         }
-        // spawn records past the tile end that continue its last run (plain loads, overlapping the copies)
-        int64_t rf0 = 0, rf1 = 0, ru0 = 0, ru1 = 0;
-        for (int64_t q = b1 + lane; q < rem_e; q += 32) {
-            const T g = S[q];
-            if (TR::flag(g)) { rf0 += TR::re(g); rf1 += TR::im(g); }
-            else { ru0 += TR::re(g); ru1 += TR::im(g); }
-        }
-        if (rem_e > b1) {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                rf0 += __shfl_xor_sync(0xFFFFFFFFu, rf0, off);
-                rf1 += __shfl_xor_sync(0xFFFFFFFFu, rf1, off);
-                ru0 += __shfl_xor_sync(0xFFFFFFFFu, ru0, off);
-                ru1 += __shfl_xor_sync(0xFFFFFFFFu, ru1, off);
-            }
-        }
-        if (lane == 0) {
-            s.rem[warp][0] = rf0;
-            s.rem[warp][1] = rf1;
-            s.rem[warp][2] = ru0;
-            s.rem[warp][3] = ru1;
-        }
+        // spawn records past the tile end that continue its last run.  Up to
+        // 32 (the usual case): one per lane, loaded now so that the load
+        // overlaps the copies and the merge, and summed just before the run
+        // ends.  More: summed here.
+        const bool rem_any = rem_e > b1, rem_long = rem_e - b1 > 32;
+        T g0 = TR::empty();
+        if (rem_long) rem_sums<T>(S, b1, rem_e, lane, s.rem[warp]);
+        else if (b1 + lane < rem_e) g0 = S[b1 + lane];
         const bool has_lprev = a0 > 0, has_sprev = b0 > 0;
         const bool arrived = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
@@ -525,6 +532,23 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
         const int my_first_head = nk > 0 ? (int)(hmask & 1u) : 1;
         const int next_first_head = __shfl_down_sync(0xFFFFFFFFu, my_first_head, 1);
 
+        // sums of those records (initiator and other), for the tile's last run
+        if (!rem_long) {
+            const bool f = TR::flag(g0);
+            int64_t f0 = f ? TR::re(g0) : 0, f1 = f ? TR::im(g0) : 0;
+            int64_t u0 = f ? 0 : TR::re(g0), u1 = f ? 0 : TR::im(g0);
+            if (rem_any) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    f0 += __shfl_xor_sync(0xFFFFFFFFu, f0, off);
+                    f1 += __shfl_xor_sync(0xFFFFFFFFu, f1, off);
+                    u0 += __shfl_xor_sync(0xFFFFFFFFu, u0, off);
+                    u1 += __shfl_xor_sync(0xFFFFFFFFu, u1, off);
+                }
+            }
+            if (lane == 0) { s.rem[warp][0] = f0; s.rem[warp][1] = f1; s.rem[warp][2] = u0; s.rem[warp][3] = u1; }
+        }
+        __syncwarp();
         // ---- 3. run ends: sums and the initiator rule; outputs replace iv ----
         uint32_t omask = 0;
         {
