@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--lattice", default="4x4",
                     help="Lx x Ly periodic lattice of the same workload (the benchmark line is 4x4; "
                          "6x6 and 8x8 use two-word keys)")
+    ap.add_argument("--wide-sort-bits", type=int, default=64,
+                    help="two-word keys: hash bits of the sort order (-1: plain order on every key bit)")
     ap.add_argument("--capacity-factor", type=float, default=3.2,
                     help="walker-list capacity per switch-on walker (spawn capacity 1.4 times that)")
     ap.add_argument("--batch", type=int, default=0,
@@ -74,6 +76,9 @@ def parse():
     ap.add_argument("--serve-default", type=int, default=32,
                     help="requests of the serving measurement added to the default line (targets up to 3e5, "
                          "about 40 s for its three arms; 0: none)")
+    ap.add_argument("--batch-default", type=int, default=16,
+                    help="runs of the 4x4 batch measurement added to the default line (targets up to "
+                         "--batch-target; batch against one at a time and streams; 0: none)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuning)")
     ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"],
                     help="c3: the 4x4 benchmark (default); c1: 2x2 open, N_w target 1e4, timed after the shift "
@@ -359,7 +364,8 @@ def gpu_arm(args, world, rank, local, pg):
                     n_a=w["n_a"], guide_kind=w["guide_kind"], guide_p=w["guide_p"],
                     site_ratio=[math.exp(-w["guide_p"])] * N, seed=w["seed"] + rank, control=w["control"],
                     capacity_entries=int(cf * target) + (1 << 20),
-                    capacity_spawns=int(1.4 * cf * target) + (1 << 20), stream=stream.cuda_stream)
+                    capacity_spawns=int(1.4 * cf * target) + (1 << 20), stream=stream.cuda_stream,
+                    wide_sort_bits=args.wide_sort_bits)
     # grow and settle (untimed; whole blocks of 32 steps replay a CUDA graph)
     while True:
         run.step(32)
@@ -548,6 +554,22 @@ def gpu_arm(args, world, rank, local, pg):
                    "value": b["solves_per_h"], "p50_s": b["p50_s"], "p95_s": b["p95_s"], "p99_s": b["p99_s"],
                    "vs_sequential": b["solves_per_h"] / q["solves_per_h"],
                    "vs_streams": b["solves_per_h"] / out["streams"]["solves_per_h"], "arms": out}
+    batch = None
+    if args.batch_default > 0 and world == 1:
+        t_b = time.perf_counter()
+        bruns = batch_runs(args.batch_default, args.batch_target)
+        res, btune, _, _ = batch_measure(ddqmc, 4, 4, bruns, 128, 512, not args.no_tune)
+        rate = {k: v[1] / v[0] for k, v in res.items()}
+        batch = {"metric": METRIC, "unit": UNIT,
+                 "workload": "batch of %d runs, 4x4 periodic, Jx in [0.8, 1.2], targets log-spaced in "
+                             "[%.3g, %.3g] total walkers, n_a 3, dt 0.005; 128 steps timed after 512"
+                             % (len(bruns), args.batch_target / 8, args.batch_target),
+                 "value": rate["batch"], "sequential": rate["sequential"], "streams": rate["streams"],
+                 "batch_over_sequential": rate["batch"] / rate["sequential"],
+                 "batch_over_streams": rate["batch"] / rate["streams"],
+                 "same_walker_steps": res["batch"][1] == res["sequential"][1] == res["streams"][1],
+                 "timing": "host clock around the timed steps (each call waits for the device)",
+                 "seconds": time.perf_counter() - t_b}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
@@ -560,7 +582,7 @@ def gpu_arm(args, world, rank, local, pg):
             "step_ms": {"median": statistics.median(step_ms), "p99": step_ms[min(len(step_ms) - 1,
                                                                                    int(0.99 * len(step_ms)))],
                         "min": step_ms[0], "max": step_ms[-1]},
-            "kernels": kern, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "tuning": tuning,
+            "kernels": kern, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "batch": batch, "tuning": tuning,
             "gpu_launches": int(sum(v[1] for v in timing.values())), "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
@@ -650,22 +672,14 @@ def batch_runs(n, target, seed=40):
     return out
 
 
-def batch_arm(args):
-    """Walker-steps/s of n runs stepped as one batch (one walker store, one
+def batch_measure(ddqmc, Lx, Ly, runs, K, W, tune):
+    """Walker-steps/s of the runs stepped as one batch (one walker store, one
     launch of each kernel per step for all runs) against the same runs one
     after another and on concurrent streams (each on its share of the SMs).
-    Each arm takes its warm-up steps from t = 0, then the timed steps; the
-    runs are identical in every arm, so each arm steps the same walkers."""
+    Each arm takes W warm-up steps from t = 0, then K timed steps; the runs
+    are identical in every arm, so each arm steps the same walkers."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_1802_05931_gb300 import ddqmc
-    torch.cuda.set_device(0)
-    Lx, Ly = (int(x) for x in args.lattice.split("x"))
     per = 1 if min(Lx, Ly) >= 3 else 0
-    runs = batch_runs(args.batch, args.batch_target)
-    K = max(32, (args.steps * 16 + 31) // 32 * 32)
-    W = max(512, (args.warmup * 64 + 31) // 32 * 32)
     # room for the population's overshoot of its target while the shift settles
     cap = dict(capacity_entries=8 * max(r["target"] for r in runs) + 65536,
                capacity_spawns=16 * max(r["target"] for r in runs) + 65536)
@@ -675,7 +689,7 @@ def batch_arm(args):
                     capacity_spawns=cap["capacity_spawns"] * len(runs))
     b.step(W)
     # every arm's runs take tuned launch shapes (state restored after the trials)
-    batch_tuning = b.tune() if not args.no_tune else None
+    batch_tuning = b.tune() if tune else None
     w0 = b.totals()["walker_steps"]
     t0 = time.perf_counter()
     b.step(K)
@@ -695,7 +709,7 @@ def batch_arm(args):
         kw = {k: v for k, v in r.items() if k not in ("Jx", "Jy", "Jz", "gamma", "dt", "target")}
         one = ddqmc.Run(Lx, Ly, per, r["Jx"], r["Jy"], r["Jz"], r["gamma"], r["dt"], r["target"], **cap, **kw)
         one.step(W)
-        if not args.no_tune:
+        if tune:
             one.tune()
         w0 = ddqmc.ddqmc_get_totals(one.h)["walker_steps"]
         t0 = time.perf_counter()
@@ -716,7 +730,7 @@ def batch_arm(args):
         m.step_async(W)
     for m in many:
         m.sync()
-    if not args.no_tune:
+    if tune:
         for m in many:
             m.tune()
     w0 = sum(ddqmc.ddqmc_get_totals(m.h)["walker_steps"] for m in many)
@@ -728,6 +742,23 @@ def batch_arm(args):
     res["streams"] = (time.perf_counter() - t0, sum(ddqmc.ddqmc_get_totals(m.h)["walker_steps"] for m in many) - w0)
     for m in many:
         m.close()
+    return res, batch_tuning, kern, launches_per_step
+
+
+def batch_arm(args):
+    """The batch measurement (batch_measure) of --batch runs as its own line,
+    with the oracle timed beside it on run 0."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1802_05931_gb300 import ddqmc
+    torch.cuda.set_device(0)
+    Lx, Ly = (int(x) for x in args.lattice.split("x"))
+    per = 1 if min(Lx, Ly) >= 3 else 0
+    runs = batch_runs(args.batch, args.batch_target)
+    K = max(32, (args.steps * 16 + 31) // 32 * 32)
+    W = max(512, (args.warmup * 64 + 31) // 32 * 32)
+    res, batch_tuning, kern, launches_per_step = batch_measure(ddqmc, Lx, Ly, runs, K, W, not args.no_tune)
     rate = {k: v[1] / v[0] for k, v in res.items()}
     # the oracle beside it: run 0 of the batch (its smallest target), grown
     # untimed for the warm-up steps, then timed for a bounded sample

@@ -81,6 +81,17 @@ typedef struct {
     double field_h;            /* in-plane field of Sec. V.B, H += h sum_k (cos t sx_k + sin t sy_k);
                                   default 0 (none) */
     int32_t field_axis;        /* direction t: 0 along x (t = 0), 1 along y (t = pi/2); default 0 */
+    int32_t wide_sort_bits;    /* lattices of more than 31 sites (two-word keys), single runs:
+                                  the list and the spawn records are kept in the hashed order
+                                  (stored bra word = bra ^ (64-bit hash of ket, low
+                                  wide_sort_bits bits), then ket); a step sorts the spawn
+                                  records on the stored bra word only and puts records that
+                                  share it in ket order.  0..64, default 64 (8 digit passes
+                                  instead of up to 16); -1: plain (bra, ket) order on every
+                                  key bit.  Results do not depend on it; fewer bits make equal
+                                  stored words common (a test of their repair).  Import and
+                                  export stay in (bra, ket) order and then need
+                                  entries <= capacity_spawns.  Batches keep the plain order. */
 } ddqmc_options;
 
 typedef struct ddqmc_run ddqmc_run;
@@ -181,7 +192,10 @@ int ddqmc_blocking_moments(ddqmc_run *run, int32_t k, int32_t levels, int64_t *h
  * is unpacked into the four arrays on the device and each array crosses the
  * host link in one copy (at the link's speed when the host arrays are pinned,
  * e.g. from cudaMallocHost); device scratch of 24 bytes per entry is kept
- * by the run after the first call.  Waits for the run's stream. */
+ * by the run after the first call.  A run in the hashed order of two-word
+ * keys (wide_sort_bits >= 0) is first sorted into the canonical order on
+ * the device, in its spawn buffers: CAPACITY if the list has more entries
+ * than capacity_spawns.  Waits for the run's stream. */
 int ddqmc_export_walkers(ddqmc_run *run, uint64_t *ket, uint64_t *bra, int32_t *re,
                          int32_t *im, int64_t cap, int64_t *n);
 
@@ -192,7 +206,9 @@ int ddqmc_export_walkers(ddqmc_run *run, uint64_t *ket, uint64_t *bra, int32_t *
  * accumulated estimates and any sticky error.  Each array crosses the host
  * link in one copy (pinned arrays at the link's speed); the entries are
  * checked and packed on the device into the run's spare list buffer, so a
- * list that fails a check (INVALID_ARG) leaves the run as it was. */
+ * list that fails a check (INVALID_ARG) leaves the run as it was.  A run in
+ * the hashed order of two-word keys sorts the entries into it on the device,
+ * in its spawn buffers (CAPACITY if n > capacity_spawns). */
 int ddqmc_import_walkers(ddqmc_run *run, const uint64_t *ket, const uint64_t *bra,
                          const int32_t *re, const int32_t *im, int64_t n, int64_t t,
                          double S, int32_t variable, int64_t q_prev, int64_t t_var,

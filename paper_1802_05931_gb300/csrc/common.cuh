@@ -41,6 +41,23 @@ struct __align__(8) RecW {
     int32_t im;
 };
 
+// Mixing function of the hashed order of two-word keys: the 64-bit
+// finalizer of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014), a bijection
+// of 64-bit words whose every output bit depends on every input bit.
+__host__ __device__ __forceinline__ uint64_t ket_mix(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Stored bra word of a two-word key in the hashed order, and back (the same
+// xor): the pair (ket, stored bra) still determines the key, so the list
+// keeps 24-byte records and sorts the stored bra word as its leading word.
+__host__ __device__ __forceinline__ uint64_t bra_swap(uint64_t ket, uint64_t bra, uint64_t hash_mask) {
+    return hash_mask ? bra ^ (ket_mix(ket) & hash_mask) : bra;
+}
+
 // Walker-list record of each spawn-record type.
 template <typename T> struct ListOf { using type = Rec; };
 template <> struct ListOf<RecW> { using type = RecW; };
@@ -98,6 +115,12 @@ struct RunParams {
     // a run of a batch that was retired (0): its configurations spawn nothing
     // and leave the list at the next merge; the other runs do not notice
     int32_t active;
+    // Hashed order of two-word keys (single runs): the stored bra word is
+    // bra ^ (ket_mix(ket) & hash_mask), the digit passes cover the stored bra
+    // word only, and a repair kernel puts records with equal stored bra words
+    // in ket order (hashed = 1).  hash_mask = 0, hashed = 0: the plain order.
+    int32_t hashed;
+    uint64_t hash_mask;
 };
 
 // Device-resident state of a run, updated by the kernels of each step.  A
@@ -114,7 +137,7 @@ struct DevState {
     int64_t R;                 // spawn records of the step in progress
     int64_t R_last;            // spawn records of the last completed step
     uint32_t epoch;            // look-back epoch of the step in progress
-    uint32_t pad1;
+    uint32_t hviol;            // hashed order: out-of-order neighbours found after the digit passes
     uint32_t tickets[MAXPASS + 16];   // tile tickets: [0, MAXPASS) radix passes, MAXPASS merge
     int64_t walker_steps;      // sum over completed steps of the walkers stepped
     int64_t W_cur;             // sum |re| + |im| of the current list

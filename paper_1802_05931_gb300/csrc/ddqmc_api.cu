@@ -19,6 +19,7 @@
 #include "../../include/ddqmc.h"
 #include "common.cuh"
 #include "finalize.cuh"
+#include "hashorder.cuh"
 #include "merge.cuh"
 #include "radix.cuh"
 #include "spawn.cuh"
@@ -85,6 +86,10 @@ struct ddqmc_run {
     RunParams *dPr = nullptr;
     DevState *dRS = nullptr;
     size_t mg_smem = 0;          // dynamic shared memory of the merge launch
+    // hashed order of two-word keys: positions of out-of-order neighbours
+    // found after the digit passes (HO_MAXV), grids of the check and repair
+    int64_t *hviol = nullptr;
+    int g_hcheck = 0, g_hrepair = 0;
 };
 
 namespace {
@@ -132,6 +137,7 @@ int build_params(ddqmc_run *r, RunParams &P, const ddqmc_lattice *lat, double Jx
         return DDQMC_ERR_INVALID_ARG;
     if (o.n0 < 0 || o.n0 > 2147483647ll || (o.control != 0 && o.control != 1)) return DDQMC_ERR_INVALID_ARG;
     if (!std::isfinite(o.field_h) || (o.field_axis != 0 && o.field_axis != 1)) return DDQMC_ERR_INVALID_ARG;
+    if (o.wide_sort_bits < -1 || o.wide_sort_bits > 64) return DDQMC_ERR_INVALID_ARG;
     const int N = Lx * Ly;
     if (N > MAXN) return DDQMC_ERR_UNSUPPORTED;
     P.N = N;
@@ -152,6 +158,15 @@ int build_params(ddqmc_run *r, RunParams &P, const ddqmc_lattice *lat, double Jx
     if (N <= NPACK) {
         P.npass = (2 * N + 7) / 8;                 // digits of the packed key bra << N | ket
         for (int p = 0; p < P.npass; ++p) P.pass_shift[p] = 8 * p;
+    } else if (o.wide_sort_bits >= 0) {
+        // hashed order: digits of the stored bra word bra ^ (hash of ket), whose
+        // low wide_sort_bits bits carry the hash; equal stored words are put
+        // in ket order after the passes
+        const int hb = o.wide_sort_bits;
+        P.hashed = 1;
+        P.hash_mask = hb >= 64 ? ~0ull : (1ull << hb) - 1ull;
+        P.npass = ((hb > N ? hb : N) + 7) / 8;
+        for (int p = 0; p < P.npass; ++p) P.pass_shift[p] = 64 + 8 * p;
     } else {
         const int nb = (N + 7) / 8;                // digits of the ket word, then of the bra word
         P.npass = 2 * nb;
@@ -348,6 +363,7 @@ void free_run(ddqmc_run *r) {
     cudaFree(r->slots);
     cudaFree(r->tile_counts);
     cudaFree(r->dAnn);
+    cudaFree(r->hviol);
     if (r->own_stream && r->stream) cudaStreamDestroy(r->stream);
     delete r;
 }
@@ -444,6 +460,14 @@ void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(in
                                                                        P.pass_shift[p], r->rcap);
         }
     }
+    if constexpr (std::is_same<T, RecW>::value && !BATCH) {
+        if (P.hashed) {
+            // equal stored bra words into ket order
+            RecW *srt = (P.npass & 1) ? sp1 : sp0;
+            k_hash_check<<<r->g_hcheck, HO_TPB, 0, r->stream>>>(srt, r->dS, r->hviol, r->rcap);
+            k_hash_repair<<<r->g_hrepair, HO_TPB, 0, r->stream>>>(srt, r->dS, r->hviol, r->rcap);
+        }
+    }
     mark(1, 1);
     const T *sorted = (P.npass & 1) ? sp1 : sp0;
     mark(2, 0);
@@ -532,6 +556,8 @@ void apply_tuning(ddqmc_run *r, const ddqmc_tuning &t) {
     r->g_copy = c.copy_blocks_per_sm * r->sms;
     r->g_scan = c.scan_blocks_per_sm * r->sms;
     r->g_part = c.partition_blocks_per_sm * r->sms;
+    r->g_hcheck = 4 * r->sms;
+    r->g_hrepair = r->sms;
     for (int k = 0; k < 2; ++k)
         if (r->graph[k]) {
             cudaGraphExecDestroy(r->graph[k]);
@@ -608,6 +634,7 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     rc |= dalloc(&r->rem_end, (size_t)mtiles + 1);
     rc |= dalloc_bytes(&r->slots, lsize * (size_t)mtiles * MG_TILE + 64);
     rc |= dalloc(&r->tile_counts, (size_t)mtiles);
+    if (r->wide) rc |= dalloc(&r->hviol, (size_t)HO_MAXV);
     if (rc != DDQMC_OK) return DDQMC_ERR_OOM;
     // kernel shapes
     int sms = 0;
@@ -790,7 +817,8 @@ void collect_timing(ddqmc_run *r, int64_t nsteps) {
             const size_t b = (size_t)s * 2 * NKCLASS + 2 * kc;
             if (cudaEventElapsedTime(&ms, r->ev[b], r->ev[b + 1]) == cudaSuccess) {
                 r->kernel_ms[kc] += ms;
-                r->kernel_launches[kc] += (kc == KC_RADIX) ? r->hp.npass : (kc == KC_COMPACT ? 2 : 1);
+                r->kernel_launches[kc] += (kc == KC_RADIX) ? r->hp.npass + (r->hp.hashed ? 2 : 0)
+                                                           : (kc == KC_COMPACT ? 2 : 1);
             } else {
                 cudaGetLastError();
             }
@@ -941,6 +969,39 @@ int raw_estimators_of(ddqmc_run *r, int k, int64_t *host_out, int32_t cap, int32
     return DDQMC_OK;
 }
 
+// Sort n two-word records in Sp[0] with the step's digit passes and the
+// standalone counters (dAnn): npass passes of 8 bits, the first nlo over the
+// ket word, the rest over the bra word; hashed: then equal bra words into ket
+// order.  *sorted = the buffer holding the result.  Synchronises the stream.
+int sort_records_wide(ddqmc_run *r, int64_t n, int npass, int nlo, bool hashed, RecW **sorted) {
+    RecW *sp0 = reinterpret_cast<RecW *>(r->Sp[0]), *sp1 = reinterpret_cast<RecW *>(r->Sp[1]);
+    *sorted = (npass & 1) ? sp1 : sp0;
+    if (n > r->rcap) return DDQMC_ERR_CAPACITY;
+    if (!r->dAnn && dalloc(&r->dAnn, 1) != DDQMC_OK) return DDQMC_ERR_OOM;
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.R = n;
+    // epochs of standalone calls carry bit 29, those of the run's steps do not
+    hs.epoch = (1u << 29) | ((r->ann_calls++ * 16u) & ((1u << 29) - 1u));
+    bool ok = cudaMemcpyAsync(r->dAnn, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    if (n > 0) {
+        k_digit_histogram<RecW><<<r->g_part, RX_TPB, 0, r->stream>>>(sp0, r->dAnn, npass, nlo);
+        for (int p = 0; p < npass; ++p)
+            k_radix_pass<RecW><<<r->g_radix, RX_TPB, RXW_SMEM, r->stream>>>(
+                (p & 1) ? sp1 : sp0, (p & 1) ? sp0 : sp1, r->dAnn, r->lb_radix, p,
+                p < nlo ? 8 * p : 64 + 8 * (p - nlo), r->rcap);
+        if (hashed) {
+            k_hash_check<<<r->g_hcheck, HO_TPB, 0, r->stream>>>(*sorted, r->dAnn, r->hviol, r->rcap);
+            k_hash_repair<<<r->g_hrepair, HO_TPB, 0, r->stream>>>(*sorted, r->dAnn, r->hviol, r->rcap);
+        }
+        ok = ok && cudaGetLastError() == cudaSuccess;
+    }
+    ok = ok && cudaMemcpyAsync(&hs, r->dAnn, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    return hs.status ? status_code(hs.status) : DDQMC_OK;
+}
+
 // Canonical (ket, bra, re, im) of the current list: the whole list (k < 0),
 // or the entries of batch run k (a contiguous range: the run id is the key's
 // most significant part).  *n = the entries of that list or run.
@@ -972,6 +1033,19 @@ int export_list(ddqmc_run *r, int k, uint64_t *ket, uint64_t *bra, int32_t *re, 
     int64_t m = b1 - b0;
     if (m > cap) m = cap > 0 ? cap : 0;     // only what the caller can take
     if (m <= 0) return DDQMC_OK;
+    if constexpr (std::is_same<LT, RecW>::value) {
+        if (r->hp.hashed) {
+            // the hashed order is not the caller's: plain bra words, then a
+            // sort on both words (Sp[0] holds the copy)
+            if (M > r->rcap) return DDQMC_ERR_CAPACITY;
+            k_unhash<<<grid_for(M), TX_TPB, 0, r->stream>>>(L, M, r->hp.hash_mask, reinterpret_cast<RecW *>(r->Sp[0]));
+            const int nb = (r->hp.N + 7) / 8;
+            RecW *srt = nullptr;
+            const int rc = sort_records_wide(r, M, 2 * nb, nb, false, &srt);
+            if (rc != DDQMC_OK) return rc;
+            L = srt;
+        }
+    }
     unsigned char *d = soa_scratch(r, m);
     if (!d) return DDQMC_ERR_OOM;
     uint64_t *dk = reinterpret_cast<uint64_t *>(d), *db = dk + m;
@@ -1227,6 +1301,7 @@ int ddqmc_default_options(ddqmc_options *o) {
     o->sm_limit = 0;
     o->field_h = 0.0;
     o->field_axis = 0;
+    o->wide_sort_bits = 64;
     return DDQMC_OK;
 }
 
@@ -1260,7 +1335,7 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     first.im = 0;
     RecW firstw;
     firstw.lo = 0;
-    firstw.hi = 0;
+    firstw.hi = bra_swap(0ull, 0ull, r->hp.hash_mask);
     firstw.re = (int32_t)o.n0;
     firstw.im = 0;
     bool okc = cudaMemcpyAsync(r->dP, &r->hp, sizeof(RunParams), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
@@ -1330,11 +1405,16 @@ int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_
     H.field_on = 0;
     for (int k = 0; k < nruns; ++k) H.field_on |= r->hpr[k].field_on;
     H.K = 2 * B + N + (H.field_on ? 2 * N : 0);
+    // a batch keeps the plain key order (its run id leads the bra word)
+    H.hashed = 0;
+    H.hash_mask = 0;
     for (int k = 0; k < nruns; ++k) {
         r->hpr[k].nruns = nruns;
         r->hpr[k].run_shift = H.run_shift;
         r->hpr[k].npass = H.npass;
         r->hpr[k].K = H.K;
+        r->hpr[k].hashed = 0;
+        r->hpr[k].hash_mask = 0;
     }
     int64_t mcap = o.capacity_entries > 0 ? o.capacity_entries : mdef;
     int64_t rcap = o.capacity_spawns > 0 ? o.capacity_spawns : rdef;
@@ -1644,7 +1724,7 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
     if (!r || n < 0 || (n > 0 && (!ket || !bra || !re || !im)) || t < 0 || !std::isfinite(S))
         return DDQMC_ERR_INVALID_ARG;
     if (r->nruns) return DDQMC_ERR_UNSUPPORTED;
-    if (n > r->mcap) return DDQMC_ERR_CAPACITY;
+    if (n > r->mcap || (r->hp.hashed && n > r->rcap)) return DDQMC_ERR_CAPACITY;
     const int N = r->hp.N;
     const uint64_t mask = r->hp.nmask;
     // the caller's arrays go over the link as they are, one copy each; the
@@ -1666,12 +1746,14 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
             ok = ok && cudaMemcpyAsync(db, bra, 8 * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
             ok = ok && cudaMemcpyAsync(dr, re, 4 * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
             ok = ok && cudaMemcpyAsync(di, im, 4 * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+            // a hashed-order list is packed into Sp[0] and sorted into the spare buffer below
             if (r->wide)
                 k_import_pack<RecW><<<grid_for(n), TX_TPB, 0, r->stream>>>(
-                    dk, db, dr, di, n, N, mask, reinterpret_cast<RecW *>(r->L[r->cur ^ 1]), r->dxfer);
+                    dk, db, dr, di, n, N, mask, r->hp.hash_mask,
+                    reinterpret_cast<RecW *>(r->hp.hashed ? r->Sp[0] : r->L[r->cur ^ 1]), r->dxfer);
             else
                 k_import_pack<Rec><<<grid_for(n), TX_TPB, 0, r->stream>>>(
-                    dk, db, dr, di, n, N, mask, reinterpret_cast<Rec *>(r->L[r->cur ^ 1]), r->dxfer);
+                    dk, db, dr, di, n, N, mask, 0ull, reinterpret_cast<Rec *>(r->L[r->cur ^ 1]), r->dxfer);
             ok = ok && cudaGetLastError() == cudaSuccess;
         }
         // the look-back epoch keeps counting, so that no status word left by
@@ -1683,6 +1765,16 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
         if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
         if (acc[1]) return DDQMC_ERR_INVALID_ARG;
         W = (int64_t)acc[0];
+        if (r->hp.hashed && n > 0) {
+            RecW *srt = nullptr;
+            const int rc = sort_records_wide(r, n, r->hp.npass, 0, true, &srt);
+            if (rc != DDQMC_OK) return rc;
+            if (cudaMemcpyAsync(r->L[r->cur ^ 1], srt, sizeof(RecW) * (size_t)n, cudaMemcpyDeviceToDevice,
+                                r->stream) != cudaSuccess) {
+                cudaGetLastError();
+                return DDQMC_ERR_CUDA;
+            }
+        }
     }
     r->cur ^= 1;
     DevState hs;
@@ -1727,7 +1819,7 @@ int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_
     }
     const Rec *list = (const Rec *)d_list;
     const Rec *sp = (const Rec *)d_spawns;
-    k_digit_histogram<Rec><<<r->g_part, RX_TPB, 0, r->stream>>>(sp, r->dAnn, P.npass);
+    k_digit_histogram<Rec><<<r->g_part, RX_TPB, 0, r->stream>>>(sp, r->dAnn, P.npass, P.npass);
     const Rec *src = sp;
     for (int p = 0; p < P.npass; ++p) {
         Rec *dst = reinterpret_cast<Rec *>(r->Sp[p & 1]);
@@ -1788,7 +1880,7 @@ int ddqmc_annihilate_noalloc(const ddqmc_lattice *lattice, int32_t initiator_thr
     if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
     const Rec *list = (const Rec *)d_list;
     const Rec *src = (const Rec *)d_spawns;
-    k_digit_histogram<Rec><<<g_na_grid[dev][1], RX_TPB, 0, stream>>>(src, &sc->st, P.npass);
+    k_digit_histogram<Rec><<<g_na_grid[dev][1], RX_TPB, 0, stream>>>(src, &sc->st, P.npass, P.npass);
     for (int p = 0; p < P.npass; ++p) {
         Rec *dst = sc->buf[p & 1];
         k_radix_pass<Rec><<<g_na_grid[dev][0], RX_TPB, RX_SMEM, stream>>>(src, dst, &sc->st, sc->lb_radix, p, 8 * p,

@@ -98,6 +98,7 @@ k_finalize(const RunParams *__restrict__ Pp, DevState *__restrict__ st, BlkCell 
             st->M_next = 0;
             st->R_last = st->R;
             st->R = 0;
+            st->hviol = 0;
             st->epoch = (st->epoch + 16u) & 0x3FFFFFFFu;
         }
         s_S = S;

@@ -59,16 +59,21 @@ template <typename KT, typename T> __device__ __forceinline__ KT spawn_key(const
 template <> __device__ __forceinline__ K128 spawn_key<K128, RecW>(const RecW &v) { return K128{v.lo, v.hi}; }
 
 // ket and bra words of a key
-__device__ __forceinline__ void key_words(uint64_t k, uint64_t nmask, int N, uint64_t &i, uint64_t &j) {
+// (hmask: the hashed order's mask of the ket hash in a two-word key's stored
+// bra word; 0 for one-word keys and batches)
+__device__ __forceinline__ void key_words(uint64_t k, uint64_t nmask, int N, uint64_t &i, uint64_t &j,
+                                          uint64_t = 0) {
     i = k & nmask;
     j = k >> N;
 }
-__device__ __forceinline__ void key_words(uint32_t k, uint64_t nmask, int N, uint64_t &i, uint64_t &j) {
+__device__ __forceinline__ void key_words(uint32_t k, uint64_t nmask, int N, uint64_t &i, uint64_t &j,
+                                          uint64_t = 0) {
     key_words((uint64_t)k, nmask, N, i, j);
 }
-__device__ __forceinline__ void key_words(const K128 &k, uint64_t, int, uint64_t &i, uint64_t &j) {
+__device__ __forceinline__ void key_words(const K128 &k, uint64_t, int, uint64_t &i, uint64_t &j,
+                                          uint64_t hmask = 0) {
     i = k.lo;
-    j = k.hi;
+    j = bra_swap(k.lo, k.hi, hmask);
 }
 
 __device__ __forceinline__ uint64_t shfl_key(uint64_t v, int src) { return __shfl_sync(0xFFFFFFFFu, v, src); }
@@ -291,9 +296,9 @@ __device__ __forceinline__ int64_t shfl_up_i64(int64_t v, int off) {
 
 // configuration (ket, bra) of a merge key, the batch run id stripped
 template <typename KT, bool BATCH>
-__device__ __forceinline__ bool key_diagonal(const KT &k, uint64_t nmask, int N) {
+__device__ __forceinline__ bool key_diagonal(const KT &k, uint64_t nmask, int N, uint64_t hmask) {
     uint64_t i, j;
-    key_words(k, nmask, N, i, j);
+    key_words(k, nmask, N, i, j, hmask);
     if (BATCH) j &= nmask;
     return i == j;
 }
@@ -356,6 +361,7 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
     const int64_t ntiles = (tot + MG_TILE - 1) / MG_TILE;
     const int N = P.N;
     const uint64_t nmask = P.nmask;
+    const uint64_t xmask = BATCH ? 0ull : P.hash_mask;     // hashed order of two-word keys
     const bool no_init = P.n_a == 0;
     const int nruns = P.nruns, run_shift = P.run_shift, nobs = P.nobs;
     unsigned long long *best = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(MergeShared<T>));
@@ -507,7 +513,7 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                     if (!counted) {
                         bool ni = no_init;
                         if constexpr (BATCH) ni = Pr[batch_run(key_high(ik[k]), run_shift, nruns)].n_a == 0;
-                        counted = ni || key_diagonal<KT, BATCH>(ik[k], nmask, N);
+                        counted = ni || key_diagonal<KT, BATCH>(ik[k], nmask, N, xmask);
                     }
                     if (counted) {
                         cmask |= 1u << k;
@@ -574,7 +580,7 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                             if (!open) {
                                 bool ni = no_init;
                                 if constexpr (BATCH) ni = Pr[batch_run(key_high(ik[k]), run_shift, nruns)].n_a == 0;
-                                open = ni || key_diagonal<KT, BATCH>(ik[k], nmask, N);
+                                open = ni || key_diagonal<KT, BATCH>(ik[k], nmask, N, xmask);
                             }
                             if (open) { sre += s.rem[warp][2]; sim += s.rem[warp][3]; }
                         }
@@ -624,7 +630,7 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
             for (uint32_t q = lane; q < total; q += 32) {
                 const LT v = stage[q];
                 uint64_t i, j;
-                key_words(list_key<KT>(v), nmask, N, i, j);
+                key_words(list_key<KT>(v), nmask, N, i, j, xmask);
                 my_w += iabs64(v.re) + iabs64(v.im);
                 my_m += 1;
                 if (i == j || __popcll(i ^ j) <= 2) add_estimators(s, s.est, P, i, j, v.re, v.im);

@@ -90,10 +90,12 @@ struct RadixShared {
 };
 
 // Digit histograms of every pass over st->R records (used when the records do
-// not come from the spawn kernel, which counts them as it writes them).
+// not come from the spawn kernel, which counts them as it writes them).  Pass
+// p reads bits 8p.. of the key for p < nlo, and bits 64 + 8(p - nlo).. after
+// (two-word records: the ket word, then the bra word).
 template <typename T>
 __global__ void __launch_bounds__(RX_TPB)
-k_digit_histogram(const T *__restrict__ in, DevState *__restrict__ st, int npass) {
+k_digit_histogram(const T *__restrict__ in, DevState *__restrict__ st, int npass, int nlo) {
     __shared__ uint32_t h[MAXPASS][256];
     const int tid = threadIdx.x;
     if (block_stopped(st)) return;
@@ -102,7 +104,8 @@ k_digit_histogram(const T *__restrict__ in, DevState *__restrict__ st, int npass
     const int64_t R = st->R;
     for (int64_t q = (int64_t)blockIdx.x * RX_TPB + tid; q < R; q += (int64_t)gridDim.x * RX_TPB) {
         const T r = in[q];
-        for (int p = 0; p < npass; ++p) atomicAdd(&h[p][RecTraits<T>::digit(r, 8 * p)], 1u);
+        for (int p = 0; p < npass; ++p)
+            atomicAdd(&h[p][RecTraits<T>::digit(r, p < nlo ? 8 * p : 64 + 8 * (p - nlo))], 1u);
     }
     __syncthreads();
     for (int q = tid; q < npass * 256; q += RX_TPB)

@@ -152,6 +152,7 @@ struct SpawnCtx {
     uint64_t ER, ED, LC, LR;
     int Lx, shD;
     uint64_t Emorton, Emorton_hi;
+    uint64_t hmask;                 // hashed order of two-word keys: mask of the ket hash in the stored bra word
 };
 
 __device__ __forceinline__ int imp_class(int gk, uint64_t d, uint64_t m, int a, int b) {
@@ -672,8 +673,9 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
             if (part == 0) cre = sig; else cim = sig;
         }
         const uint64_t kp = BATCH ? (uint64_t)orun << run_shift : 0ull;
-        emit(s, warp, make_spawn<T>((uint64_t)ci, (uint64_t)cj, N, (qinit & 1) != 0, cre, cim, kp), out, cap, st,
-             npass);
+        uint64_t cjs = (uint64_t)cj;
+        if constexpr (std::is_same<T, RecW>::value && !BATCH) cjs = bra_swap((uint64_t)ci, cjs, c.hmask);
+        emit(s, warp, make_spawn<T>((uint64_t)ci, cjs, N, (qinit & 1) != 0, cre, cim, kp), out, cap, st, npass);
     }
     __syncwarp();
 }
@@ -732,6 +734,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
     c.sh = &s; c.N = N; c.B = B; c.K = K; c.gk = P.guide_kind; c.jump_q = P.jump_q; c.nmask = P.nmask;
     c.ER = P.ER; c.ED = P.ED; c.LC = P.LC; c.LR = P.LR; c.Lx = P.Lx; c.shD = P.shD;
     c.Emorton = P.Emorton; c.Emorton_hi = P.Emorton_hi;
+    c.hmask = P.hash_mask;
     const bool uniform = P.uniform != 0;
     const int64_t M = st->M;
     const uint64_t t = (uint64_t)st->t;
@@ -752,7 +755,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
         rec.im = 0;
         if (e < M) {
             rec = L[e];
-            if constexpr (WIDE) { i = rec.lo; j = rec.hi; }
+            if constexpr (WIDE) { i = rec.lo; j = BATCH ? rec.hi : bra_swap(rec.lo, rec.hi, c.hmask); }
             else { i = rec.key & nmask; j = rec.key >> N; }
             if constexpr (BATCH) {
                 crun = batch_run(j, N, nruns);   // j holds the run id above its N spin bits
@@ -1151,6 +1154,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 int gsg;
                 bool same;
                 move_child<BATCH>(c, HP, hi, hj, s.ws[warp].hv.mv[m], ci, cj, same, gsg);
+                if constexpr (WIDE && !BATCH) cj = bra_swap(ci, cj, c.hmask);
                 emit_counts(s, warp, ci, cj, N, hinit, cre, cim, out, cap, st, npass, hkp);
             }
             flush(s, warp, lane, out, cap, st, npass, SP_FLUSH);

@@ -10,10 +10,14 @@ namespace ddq {
 
 constexpr int TX_TPB = 256;
 
-__device__ __forceinline__ void put_list(Rec &v, uint64_t ket, uint64_t bra, int N) { v.key = (bra << N) | ket; }
-__device__ __forceinline__ void put_list(RecW &v, uint64_t ket, uint64_t bra, int) {
+// hmask: the hashed order's mask of the ket hash in the stored bra word
+// (two-word keys of a single run; 0 otherwise)
+__device__ __forceinline__ void put_list(Rec &v, uint64_t ket, uint64_t bra, int N, uint64_t) {
+    v.key = (bra << N) | ket;
+}
+__device__ __forceinline__ void put_list(RecW &v, uint64_t ket, uint64_t bra, int, uint64_t hmask) {
     v.lo = ket;
-    v.hi = bra;
+    v.hi = bra_swap(ket, bra, hmask);
 }
 __device__ __forceinline__ void get_list(const Rec &v, int N, uint64_t mask, uint64_t &ket, uint64_t &bra) {
     ket = v.key & mask;
@@ -27,10 +31,12 @@ __device__ __forceinline__ void get_list(const RecW &v, int, uint64_t mask, uint
 // Pack n caller entries into list records and check them: every word within
 // the lattice's N bits, no empty entry, keys strictly increasing in (bra,
 // ket) order.  acc[0] += sum |re| + |im|; acc[1] != 0 when any entry fails.
+// With hmask != 0 the records carry the stored bra words of the hashed order
+// and still need sorting in it.
 template <typename LT>
 __global__ void __launch_bounds__(TX_TPB)
 k_import_pack(const uint64_t *__restrict__ ket, const uint64_t *__restrict__ bra, const int32_t *__restrict__ re,
-              const int32_t *__restrict__ im, int64_t n, int N, uint64_t mask, LT *__restrict__ out,
+              const int32_t *__restrict__ im, int64_t n, int N, uint64_t mask, uint64_t hmask, LT *__restrict__ out,
               unsigned long long *__restrict__ acc) {
     __shared__ unsigned long long s_w[TX_TPB / 32];
     int64_t w = 0;
@@ -45,7 +51,7 @@ k_import_pack(const uint64_t *__restrict__ ket, const uint64_t *__restrict__ bra
         }
         w += (int64_t)(x < 0 ? -(int64_t)x : x) + (int64_t)(y < 0 ? -(int64_t)y : y);
         LT v;
-        put_list(v, k, b, N);
+        put_list(v, k, b, N, hmask);
         v.re = x;
         v.im = y;
         out[q] = v;
@@ -76,6 +82,17 @@ k_export_unpack(const LT *__restrict__ L, int64_t m, int N, uint64_t mask, uint6
         bra[q] = b;
         re[q] = v.re;
         im[q] = v.im;
+    }
+}
+
+// Copy of a hashed-order list with its plain bra words (to be sorted in the
+// (bra, ket) order of the caller's layout).
+__global__ void __launch_bounds__(TX_TPB)
+k_unhash(const RecW *__restrict__ L, int64_t m, uint64_t hmask, RecW *__restrict__ out) {
+    for (int64_t q = (int64_t)blockIdx.x * TX_TPB + threadIdx.x; q < m; q += (int64_t)gridDim.x * TX_TPB) {
+        RecW v = L[q];
+        v.hi = bra_swap(v.lo, v.hi, hmask);
+        out[q] = v;
     }
 }
 

@@ -166,6 +166,9 @@ def test_single_run_line_has_every_key(fake_gpu, capsys, monkeypatch):
     sv = line["serving"]
     assert sv["unit"] == "solves/h" and set(sv["arms"]) == {"batched", "streams", "sequential"}
     assert sv["vs_sequential"] == pytest.approx(1.0)
+    bt = line["batch"]
+    assert bt["unit"] == line["unit"] and bt["value"] > 0 and "same_walker_steps" in bt
+    assert bt["batch_over_streams"] == pytest.approx(bt["value"] / bt["streams"])
 
 
 def test_batch_line_has_every_key(fake_gpu, capsys, monkeypatch):
