@@ -112,6 +112,8 @@ struct SpawnTables {
     uint64_t bond_m[MAXB];
     uint64_t cross_frac[2 * MAXB + 1];
     uint64_t d_frac[2 * MAXN + 1];
+    uint32_t cross_frac32[2 * MAXB + 1];  // the same fractions in 32 bits (each is below 2^32)
+    uint32_t d_frac32[2 * MAXN + 1];
     uint64_t urate8[8];
     uint32_t urate32[8];
     float uinv[8];
@@ -138,7 +140,7 @@ struct SpawnShared : SpawnTables {
     int32_t stage_n[SP_WARPS];
     T stage[SP_WARPS][SP_STAGE];
     WarpScratch<T> ws[SP_WARPS];
-    int32_t mark[SP_WARPS][32];       // configuration starting at each walker position of a window
+    int32_t mark[SP_WARPS][32];       // first walker position of each configuration of the chunk
     int32_t dre[SP_WARPS][32], dim[SP_WARPS][32];
     uint64_t qv[SP_WARPS][64];        // queued spawn draws: scaled uniform v
     uint32_t qm[SP_WARPS][64];        //   and configuration | part << 5 | negative << 6
@@ -726,6 +728,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
     if (tid == 0) { s.field_on = P.field_on; s.field_axis = P.field_axis; s.sgn_hf = P.sgn_hf; }
     for (int q = tid; q <= 2 * B; q += SP_TPB) { s.cross_int[q] = P.cross_int[q]; s.cross_frac[q] = P.cross_frac[q]; }
     for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_frac[q] = st->d_frac[q]; s.d_sgn[q] = st->d_sgn[q]; }
+    for (int q = tid; q <= 2 * B; q += SP_TPB) s.cross_frac32[q] = (uint32_t)P.cross_frac[q];
+    for (int q = tid; q <= 2 * N; q += SP_TPB) s.d_frac32[q] = (uint32_t)st->d_frac[q];
     for (int q = tid; q < SpawnShared<T>::NP * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
     if (tid < SP_WARPS) s.stage_n[tid] = 0;
     __syncthreads();
@@ -849,26 +853,20 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
         // draw that lands below the total rate is queued, and the move
         // searches run 32 at a time with every lane busy.
         int qn = 0;                      // queued spawn draws (same value in every lane)
-        int carry = 0;                   // configuration of the walker before the window
+        // the configurations' first walker positions, for the owner search
+        __syncwarp();
+        s.mark[warp][lane] = excl;
+        __syncwarp();
         for (int base = 0; base < Wl; base += 32) {
             const bool last_base = base + 32 >= Wl;
             const int g = base + lane;
             const bool act = g < Wl;
             // owner of walker g: the last configuration starting at or before
-            // g (start marks in the window, then a max-scan over the lanes)
-            __syncwarp();
-            s.mark[warp][lane] = -1;
-            __syncwarp();
-            if (nl > 0 && excl >= base && excl < base + 32) s.mark[warp][excl - base] = lane;
-            __syncwarp();
-            int owner = s.mark[warp][lane];
+            // g (binary search of the non-decreasing first positions)
+            int owner = 0;
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xFFFFFFFFu, owner, off);
-                if (lane >= off && y > owner) owner = y;
-            }
-            if (carry > owner) owner = carry;
-            carry = __shfl_sync(0xFFFFFFFFu, owner, 31);
+            for (int sft = 16; sft >= 1; sft >>= 1)
+                if (s.mark[warp][owner + sft] <= g) owner += sft;
             const int owner_excl = __shfl_sync(0xFFFFFFFFu, excl, owner);
             int part = 0, sig = 1;
             uint32_t natt = 0;
@@ -900,8 +898,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                     dsg = OS.d_sgn[cd];
                 } else {
                     x = philox4x32_10(ctr, k0, k1);
-                    cnt = (int)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
-                    cc = (int)s.cross_int[adz] + ((uint64_t)x.z < s.cross_frac[adz] ? 1 : 0);
+                    cnt = (int)s.d_int[cd] + (x.y < s.d_frac32[cd] ? 1 : 0);
+                    cc = (int)s.cross_int[adz] + (x.z < s.cross_frac32[adz] ? 1 : 0);
                     dsg = s.d_sgn[cd];
                 }
                 const int ddeath = -dsg * sig * cnt;
@@ -1072,11 +1070,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
             const uint64_t Ttot = carry;
             uint64_t natt = (Ttot + 0xFFFFFFFFull) >> 32;
             if (natt == 0) natt = 1;
-            int na_i = 0, na_j = 0;
-            for (int b = 0; b < B; ++b) {
-                na_i += (int)(((hi >> s.bond_a[b]) ^ (hi >> s.bond_b[b])) & 1ull);
-                na_j += (int)(((hj >> s.bond_a[b]) ^ (hj >> s.bond_b[b])) & 1ull);
-            }
+            // anti-aligned bonds of each side (one bit per bond of the mask formulation)
+            const int na_i = popcount(anti_mask<MT, SW>(c, (SW)hi)), na_j = popcount(anti_mask<MT, SW>(c, (SW)hj));
             const int cd = __popcll(hi) + __popcll(hj);
             const int dz = 2 * (na_j - na_i);
             const int adz = dz < 0 ? -dz : dz;
