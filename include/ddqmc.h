@@ -80,7 +80,8 @@ typedef struct {
                                   <= 0 (default): the whole GPU */
     double field_h;            /* in-plane field of Sec. V.B, H += h sum_k (cos t sx_k + sin t sy_k);
                                   default 0 (none) */
-    int32_t field_axis;        /* direction t: 0 along x (t = 0), 1 along y (t = pi/2); default 0 */
+    int32_t field_axis;        /* direction t: 0 along x (t = 0), 1 along y (t = pi/2), 2 the
+                                  angle field_theta; default 0 */
     int32_t wide_sort_bits;    /* lattices of more than 31 sites (two-word keys), single runs:
                                   the list and the spawn records are kept in the hashed order
                                   (stored bra word = bra ^ (64-bit hash of ket, low
@@ -92,6 +93,11 @@ typedef struct {
                                   stored words common (a test of their repair).  Import and
                                   export stay in (bra, ket) order and then need
                                   entries <= capacity_spawns.  Batches keep the plain order. */
+    double field_theta;        /* field_axis 2: the angle t (radians); each site flip is then two
+                                  moves, |h cos t| (the x part) and |h sin t| (the y part), so
+                                  2B + 5N moves per configuration must fit the move table
+                                  (UNSUPPORTED otherwise: up to 24 sites of a periodic lattice
+                                  with one-word keys, 6x6 with two-word keys); default 0 */
 } ddqmc_options;
 
 typedef struct ddqmc_run ddqmc_run;
@@ -309,6 +315,7 @@ typedef struct {
     double field_h;
     int32_t field_axis;
     int32_t reserved;          /* set to 0 */
+    double field_theta;        /* as in ddqmc_options */
 } ddqmc_run_spec;
 
 /* Create a batch of nruns (1..DDQMC_MAX_BATCH) runs on one lattice and one

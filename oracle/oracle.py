@@ -128,8 +128,7 @@ def series_log(x: float) -> float:
 
 class OracleRun:
     """One DDQMC run on the CPU.  Parameters mirror the C-ABI ``ddqmc_create``;
-    field_axis = 2 takes the field angle field_theta (the C-ABI takes the axes
-    0 and 1 only)."""
+    field_axis = 2 takes the field angle field_theta."""
 
     def __init__(self, Lx, Ly, periodic, Jx, Jy, Jz, gamma, dt, target, n_a=0,
                  guide_kind=0, guide_p=0.0, site_ratio=None, seed=1, damping=0.05,

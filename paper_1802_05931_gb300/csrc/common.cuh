@@ -94,8 +94,11 @@ struct RunParams {
     int32_t uniform;                  // 1 if every bond has the same rate table
     int32_t pad1;
     int32_t pass_shift[MAXPASS];      // key bit where the digit of each radix pass starts
-    // in-plane field h sum_k sigma^x_k (axis 0) or sigma^y_k (axis 1)
-    int32_t field_on, field_axis, sgn_hf, pad2;
+    // in-plane field h sum_k sigma^x_k (axis 0), sigma^y_k (axis 1), or
+    // (cos t sigma^x_k + sin t sigma^y_k) (axis 2: each flip is two moves, the
+    // x part with the tables frate_q / ufrate.. and sign sgn_hf, then the y
+    // part with frate_q2 / ufrate..2 and sign sgn_hf2)
+    int32_t field_on, field_axis, sgn_hf, sgn_hf2;
     uint64_t frate_q[MAXN][4];        // site flip of site k, [importance class]
     uint64_t ufrate[4];               // the same when every site has the same table
     uint64_t Emorton;                 // bond-existence mask, bit 2k = right bond of k, 2k+1 = lower (sites < 32)
@@ -121,6 +124,10 @@ struct RunParams {
     // in ket order (hashed = 1).  hash_mask = 0, hashed = 0: the plain order.
     int32_t hashed;
     uint64_t hash_mask;
+    uint64_t frate_q2[MAXN][4];       // axis 2: the y part of a site flip, [importance class]
+    uint64_t ufrate2[4];
+    uint32_t ufrate32_2[4];
+    float ufinv2[4];
 };
 
 // Device-resident state of a run, updated by the kernels of each step.  A

@@ -136,7 +136,8 @@ int build_params(ddqmc_run *r, RunParams &P, const ddqmc_lattice *lat, double Jx
     if (!std::isfinite(Jx) || !std::isfinite(Jy) || !std::isfinite(Jz) || !std::isfinite(gamma) || !std::isfinite(dt))
         return DDQMC_ERR_INVALID_ARG;
     if (o.n0 < 0 || o.n0 > 2147483647ll || (o.control != 0 && o.control != 1)) return DDQMC_ERR_INVALID_ARG;
-    if (!std::isfinite(o.field_h) || (o.field_axis != 0 && o.field_axis != 1)) return DDQMC_ERR_INVALID_ARG;
+    if (!std::isfinite(o.field_h) || o.field_axis < 0 || o.field_axis > 2 || !std::isfinite(o.field_theta))
+        return DDQMC_ERR_INVALID_ARG;
     if (o.wide_sort_bits < -1 || o.wide_sort_bits > 64) return DDQMC_ERR_INVALID_ARG;
     const int N = Lx * Ly;
     if (N > MAXN) return DDQMC_ERR_UNSUPPORTED;
@@ -152,8 +153,14 @@ int build_params(ddqmc_run *r, RunParams &P, const ddqmc_lattice *lat, double Jx
     P.B = B;
     P.field_on = o.field_h != 0.0 ? 1 : 0;
     P.field_axis = o.field_axis;
-    P.sgn_hf = o.field_h > 0.0 ? 1 : (o.field_h < 0.0 ? -1 : 0);
-    P.K = 2 * B + N + (P.field_on ? 2 * N : 0);
+    // amplitudes of the field's parts: h (axes 0, 1); h cos t and h sin t (axis 2)
+    const double hx = o.field_axis == 2 ? o.field_h * std::cos(o.field_theta) : o.field_h;
+    const double hy = o.field_axis == 2 ? o.field_h * std::sin(o.field_theta) : 0.0;
+    P.sgn_hf = hx > 0.0 ? 1 : (hx < 0.0 ? -1 : 0);
+    P.sgn_hf2 = hy > 0.0 ? 1 : (hy < 0.0 ? -1 : 0);
+    P.K = 2 * B + N + (P.field_on ? (P.field_axis == 2 ? 4 * N : 2 * N) : 0);
+    // the warp-cooperative path's move table
+    if (P.K > (N > NPACK ? MAXK : MAXK_PACK)) return DDQMC_ERR_UNSUPPORTED;
     P.nobs = 5 + N + 3 * B + 4 + 2 * N + 2;
     if (N <= NPACK) {
         P.npass = (2 * N + 7) / 8;                 // digits of the packed key bra << N | ket
@@ -236,21 +243,26 @@ int build_params(ddqmc_run *r, RunParams &P, const ddqmc_lattice *lat, double Jx
         }
     }
     P.jump_q = fixed_rate(gamma * dt);
-    // field site flips: |A| = |h|, times dt, times the ratio of the flipped site
-    for (int k = 0; k < N; ++k) {
-        const double base = std::fabs(o.field_h) * dt;
-        for (int c = 0; c < 4; ++c) {
-            double x = base;
-            if (gk == 1) {
-                if (c == 1) x = base * w_off;
-                else if (c == 2) x = base * w_inv;
-            } else if (gk == 2) {
-                if (c == 0) x = base * site_r[k];
-                else if (c == 1) x = base * (1.0 / site_r[k]);
+    // field site flips: |A| times dt times the ratio of the flipped site;
+    // |A| = |h| along an axis, |h cos t| and |h sin t| for the two parts at an angle
+    auto field_rates = [&](double amp, uint64_t (*q)[4]) {
+        for (int k = 0; k < N; ++k) {
+            const double base = amp * dt;
+            for (int c = 0; c < 4; ++c) {
+                double x = base;
+                if (gk == 1) {
+                    if (c == 1) x = base * w_off;
+                    else if (c == 2) x = base * w_inv;
+                } else if (gk == 2) {
+                    if (c == 0) x = base * site_r[k];
+                    else if (c == 1) x = base * (1.0 / site_r[k]);
+                }
+                q[k][c] = fixed_rate(x);
             }
-            P.frate_q[k][c] = fixed_rate(x);
         }
-    }
+    };
+    field_rates(o.field_axis == 2 ? std::fabs(o.field_h * std::cos(o.field_theta)) : std::fabs(o.field_h), P.frate_q);
+    if (o.field_axis == 2) field_rates(std::fabs(o.field_h * std::sin(o.field_theta)), P.frate_q2);
     // geometry masks and the bond-uniform rate table of the popcount formulation
     P.Lx = Lx;
     P.shD = Lx * (Ly - 1);
@@ -278,7 +290,8 @@ int build_params(ddqmc_run *r, RunParams &P, const ddqmc_lattice *lat, double Jx
         for (int h = 0; h < 2; ++h)
             for (int c = 0; c < 4; ++c) uni = uni && P.rate_q[b][h][c] == P.rate_q[0][h][c];
     for (int k = 1; k < N; ++k)
-        for (int c = 0; c < 4; ++c) uni = uni && P.frate_q[k][c] == P.frate_q[0][c];
+        for (int c = 0; c < 4; ++c)
+            uni = uni && P.frate_q[k][c] == P.frate_q[0][c] && P.frate_q2[k][c] == P.frate_q2[0][c];
     P.uniform = uni ? 1 : 0;
     for (int g = 0; g < 8; ++g) {
         P.urate8[g] = P.rate_q[0][g >> 2][g & 3];
@@ -289,6 +302,9 @@ int build_params(ddqmc_run *r, RunParams &P, const ddqmc_lattice *lat, double Jx
         P.ufrate[c] = P.frate_q[0][c];
         P.ufrate32[c] = (uint32_t)P.ufrate[c];
         P.ufinv[c] = P.ufrate[c] ? 1.0f / (float)P.ufrate[c] : 0.0f;
+        P.ufrate2[c] = P.frate_q2[0][c];
+        P.ufrate32_2[c] = (uint32_t)P.ufrate2[c];
+        P.ufinv2[c] = P.ufrate2[c] ? 1.0f / (float)P.ufrate2[c] : 0.0f;
     }
     P.jinv = P.jump_q ? 1.0f / (float)P.jump_q : 0.0f;
     const double cbase = dt * std::fabs(Jz);
@@ -1302,6 +1318,7 @@ int ddqmc_default_options(ddqmc_options *o) {
     o->field_h = 0.0;
     o->field_axis = 0;
     o->wide_sort_bits = 64;
+    o->field_theta = 0.0;
     return DDQMC_OK;
 }
 
@@ -1374,6 +1391,7 @@ int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_
         ok.t_eq = q.t_eq;
         ok.field_h = q.field_h;
         ok.field_axis = q.field_axis;
+        ok.field_theta = q.field_theta;
         const int rc = build_params(r, r->hpr[k], lattice, q.Jx, q.Jy, q.Jz, q.gamma, q.dt, q.target_walkers,
                                     q.initiator_threshold, guide, ok);
         if (rc != DDQMC_OK) { delete r; return rc; }
@@ -1404,7 +1422,10 @@ int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_
     H.nruns = nruns;
     H.field_on = 0;
     for (int k = 0; k < nruns; ++k) H.field_on |= r->hpr[k].field_on;
-    H.K = 2 * B + N + (H.field_on ? 2 * N : 0);
+    bool axis2 = false;
+    for (int k = 0; k < nruns; ++k) axis2 = axis2 || (r->hpr[k].field_on && r->hpr[k].field_axis == 2);
+    H.K = 2 * B + N + (H.field_on ? (axis2 ? 4 * N : 2 * N) : 0);
+    if (H.K > (N > NPACK ? MAXK : MAXK_PACK)) { delete r; return DDQMC_ERR_UNSUPPORTED; }
     // a batch keeps the plain key order (its run id leads the bra word)
     H.hashed = 0;
     H.hash_mask = 0;

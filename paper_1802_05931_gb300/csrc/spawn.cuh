@@ -128,7 +128,11 @@ struct SpawnTables {
     uint64_t ufrate[4];               // field flip rate of each importance class (uniform tables)
     uint32_t ufrate32[4];
     float ufinv[4];
-    int32_t field_on, field_axis, sgn_hf;
+    uint64_t ufrate2[4];              // the same for the y part of a flip at an angle (axis 2)
+    uint32_t ufrate32_2[4];
+    float ufinv2[4];
+    int32_t field_on, field_axis, sgn_hf, sgn_hf2;
+    int32_t fparts;                   // moves per site flip and segment: 2 when a run has axis 2
 };
 
 // Shared memory of the spawn kernel for spawn records of type T; packed
@@ -400,8 +404,9 @@ __device__ __forceinline__ int seg_select32(const SpawnCtx &c, const uint32_t *r
 // ---- per-move tables (heavy path) -------------------------------------------
 
 // Child (ci, cj) of move m of configuration (i, j).  Move ids: ket bond b,
-// bra bond B + b, ket field flip 2B + k, bra field flip 2B + N + k, jump
-// 2B + 2N + k.  same: the child has the parent's type (real / imaginary);
+// bra bond B + b, ket field flip 2B + k, bra field flip 2B + N + k (at an
+// angle: their x parts), jump 2B + 2N + k, and at an angle the y parts of the
+// ket and bra flips 2B + 3N + k, 2B + 4N + k.  same: the child has the parent's type (real / imaginary);
 // a: the sign of the element's non-zero part -- a real parent of sign s makes
 // a child of sign s*a, an imaginary parent one of sign s*a (same type) or
 // -s*a (other type).  P: the run's parameters (a single run reads its field
@@ -412,6 +417,7 @@ __device__ __forceinline__ void move_child(const SpawnCtx &c, const RunParams &P
     const SpawnTables &s = *c.sh;
     const int field_axis = BATCH ? P.field_axis : s.field_axis;
     const int sgn_hf = BATCH ? P.sgn_hf : s.sgn_hf;
+    const int sgn_hf2 = BATCH ? P.sgn_hf2 : s.sgn_hf2;
     ci = i;
     cj = j;
     const int B = c.B, N = c.N;
@@ -429,19 +435,26 @@ __device__ __forceinline__ void move_child(const SpawnCtx &c, const RunParams &P
         const int k = ket ? m - 2 * B : m - 2 * B - N;
         const uint64_t w = ket ? i : j;
         if (ket) ci ^= 1ull << k; else cj ^= 1ull << k;
-        if (field_axis == 0) {
+        if (field_axis != 1) {
             same = false;
             a = ket ? -sgn_hf : sgn_hf;
         } else {
             same = true;
             a = ((w >> k) & 1ull) ? sgn_hf : -sgn_hf;
         }
-    } else {                         // jump: +gamma
+    } else if (m < 2 * B + 3 * N) {  // jump: +gamma
         const int k = m - 2 * B - 2 * N;
         ci &= ~(1ull << k);
         cj &= ~(1ull << k);
         same = true;
         a = 1;
+    } else {                         // y part of a flip at an angle: h sin t (2 s_k - 1)
+        const bool ket = m < 2 * B + 4 * N;
+        const int k = ket ? m - 2 * B - 3 * N : m - 2 * B - 4 * N;
+        const uint64_t w = ket ? i : j;
+        if (ket) ci ^= 1ull << k; else cj ^= 1ull << k;
+        same = true;
+        a = ((w >> k) & 1ull) ? sgn_hf2 : -sgn_hf2;
     }
 }
 
@@ -626,30 +639,47 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c
             const uint64_t vb = v - qTket - qTbra;
             const bool ket = vb < qTf;
             uint64_t vf = ket ? vb : vb - qTf;
+            // at an angle: the x part of the segment's flips, then the y part
+            const uint64_t *fr = BATCH ? R.ufrate : s.ufrate;
+            const uint32_t *fr32 = BATCH ? R.ufrate32 : s.ufrate32;
+            const float *fri = BATCH ? R.ufinv : s.ufinv;
+            bool ypart = false;
+            if (s.fparts == 2) {
+                uint64_t tx = 0;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) tx += fr[g] * (uint64_t)((fcp >> (8 * g)) & 0xFFu);
+                if (vf >= tx) {
+                    vf -= tx;
+                    ypart = true;
+                    fr = BATCH ? R.ufrate2 : s.ufrate2;
+                    fr32 = BATCH ? R.ufrate32_2 : s.ufrate32_2;
+                    fri = BATCH ? R.ufinv2 : s.ufinv2;
+                }
+            }
             int g = 0;
             for (; g < 3; ++g) {
-                const uint64_t w = (BATCH ? R.ufrate[g] : s.ufrate[g]) * (uint64_t)((fcp >> (8 * g)) & 0xFFu);
+                const uint64_t w = fr[g] * (uint64_t)((fcp >> (8 * g)) & 0xFFu);
                 if (vf < w) break;
                 vf -= w;
             }
             uint32_t idx;
             if (qT <= 0xFFFFFFFFull) {
-                const uint32_t rq = BATCH ? R.ufrate32[g] : s.ufrate32[g];
-                idx = (uint32_t)((float)(uint32_t)vf * (BATCH ? R.ufinv[g] : s.ufinv[g]));
+                const uint32_t rq = fr32[g];
+                idx = (uint32_t)((float)(uint32_t)vf * fri[g]);
                 const uint64_t pq = (uint64_t)idx * rq;
                 if (pq > vf) --idx;
                 else if (pq + rq <= vf) ++idx;
             } else {
-                idx = small_quotient(vf, BATCH ? R.ufrate[g] : s.ufrate[g]);
+                idx = small_quotient(vf, fr[g]);
             }
             SW fm[4];
             field_masks<SW>(c, qi, qj, fm);
             const int k = select_bit(fm[g], idx);
             const SW w = ket ? qi : qj;
             const int axis = BATCH ? R.field_axis : s.field_axis;
-            const int shf = BATCH ? R.sgn_hf : s.sgn_hf;
+            const int shf = ypart ? (BATCH ? R.sgn_hf2 : s.sgn_hf2) : (BATCH ? R.sgn_hf : s.sgn_hf);
             if (ket) ci ^= (SW)1 << k; else cj ^= (SW)1 << k;
-            if (axis == 0) {                     // -i h (ket), +i h (bra): the other type
+            if (!ypart && axis != 1) {           // -i h (ket), +i h (bra): the other type
                 const int gsg = ket ? -shf : shf;
                 if (part == 0) cim = sig * gsg; else cre = -sig * gsg;
             } else {                             // h (2 s_k - 1): the same type
@@ -725,7 +755,18 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
         s.ufrate32[tid] = (uint32_t)P.ufrate[tid];
         s.ufinv[tid] = P.ufrate[tid] ? 1.0f / (float)P.ufrate[tid] : 0.0f;
     }
-    if (tid == 0) { s.field_on = P.field_on; s.field_axis = P.field_axis; s.sgn_hf = P.sgn_hf; }
+    if (tid < 4) {
+        s.ufrate2[tid] = P.ufrate2[tid];
+        s.ufrate32_2[tid] = (uint32_t)P.ufrate2[tid];
+        s.ufinv2[tid] = P.ufrate2[tid] ? 1.0f / (float)P.ufrate2[tid] : 0.0f;
+    }
+    if (tid == 0) {
+        s.field_on = P.field_on;
+        s.field_axis = P.field_axis;
+        s.sgn_hf = P.sgn_hf;
+        s.sgn_hf2 = P.sgn_hf2;
+        s.fparts = P.K == 2 * P.B + 5 * P.N ? 2 : 1;
+    }
     for (int q = tid; q <= 2 * B; q += SP_TPB) { s.cross_int[q] = P.cross_int[q]; s.cross_frac[q] = P.cross_frac[q]; }
     for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_frac[q] = st->d_frac[q]; s.d_sgn[q] = st->d_sgn[q]; }
     for (int q = tid; q <= 2 * B; q += SP_TPB) s.cross_frac32[q] = (uint32_t)P.cross_frac[q];
@@ -805,7 +846,9 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 for (int g = 0; g < 4; ++g) {
                     const int cf = popcount(fm[g]);
                     fcp |= (uint32_t)cf << (8 * g);
-                    Tf += (BATCH ? CR.ufrate[g] : s.ufrate[g]) * (uint64_t)cf;
+                    // both parts of a flip at an angle (the y part's rates are 0 otherwise)
+                    Tf += ((BATCH ? CR.ufrate[g] : s.ufrate[g]) + (BATCH ? CR.ufrate2[g] : s.ufrate2[g])) *
+                          (uint64_t)cf;
                 }
             }
             const uint64_t Tall = Tket + Tbra + 2 * Tf + (uint64_t)popcount((SW)(i32 & j32)) * (BATCH ? CR.jump_q : c.jump_q);
@@ -1018,8 +1061,10 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                     }
                 }
                 if (FIELD) {
-                    // field flips: ket then bra, groups by importance class, sites in order
-                    for (int seg = 0; seg < 2; ++seg) {
+                    // field flips: ket then bra; at an angle the x part of the
+                    // segment, then its y part; groups by importance class, sites in order
+                    for (int sp = 0; sp < 2 * s.fparts; ++sp) {
+                        const int seg = sp / s.fparts, fp = sp % s.fparts;
                         int gq[2];
                         uint64_t rq[2];
 #pragma unroll
@@ -1029,9 +1074,11 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                             rq[q] = 0;
                             if (k < N) {
                                 gq[q] = site_class(c.gk, hd, k);
-                                rq[q] = HP.frate_q[k][gq[q]];
+                                rq[q] = fp ? HP.frate_q2[k][gq[q]] : HP.frate_q[k][gq[q]];
                             }
                         }
+                        // move ids: x part (or the axis) 2B + seg N + k, y part 2B + (3 + seg) N + k
+                        const int mv0 = 2 * B + (fp ? 3 + seg : seg) * N;
                         for (int g = 0; g < 4; ++g) {
 #pragma unroll
                             for (int q = 0; q < 2; ++q) {
@@ -1040,7 +1087,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                                 if (gq[q] == g) {
                                     const int pos = base + __popc(mq & lt);
                                     s.ws[warp].hv.cum[pos] = rq[q];
-                                    s.ws[warp].hv.mv[pos] = (int16_t)(2 * B + seg * N + lane + 32 * q);
+                                    s.ws[warp].hv.mv[pos] = (int16_t)(mv0 + lane + 32 * q);
                                 }
                                 base += __popc(mq);
                             }

@@ -53,7 +53,7 @@ class ddqmc_options(C.Structure):
                 ("n0", C.c_int64), ("control", C.c_int32), ("t_eq", C.c_int64),
                 ("capacity_entries", C.c_int64), ("capacity_spawns", C.c_int64),
                 ("cuda_stream", C.c_void_p), ("sm_limit", C.c_int32), ("field_h", C.c_double),
-                ("field_axis", C.c_int32), ("wide_sort_bits", C.c_int32)]
+                ("field_axis", C.c_int32), ("wide_sort_bits", C.c_int32), ("field_theta", C.c_double)]
 
 
 class ddqmc_estimates(C.Structure):
@@ -77,7 +77,7 @@ class ddqmc_run_spec(C.Structure):
                 ("dt", C.c_double), ("target_walkers", C.c_int64), ("initiator_threshold", C.c_int32),
                 ("control", C.c_int32), ("seed", C.c_uint64), ("damping", C.c_double), ("shift0", C.c_double),
                 ("n0", C.c_int64), ("t_eq", C.c_int64), ("field_h", C.c_double), ("field_axis", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("field_theta", C.c_double)]
 
 
 class ddqmc_state(C.Structure):
@@ -387,7 +387,7 @@ class Run:
     def __init__(self, Lx, Ly, periodic, Jx, Jy, Jz, gamma, dt, target, n_a=0, guide_kind=0,
                  guide_p=0.0, site_ratio=None, seed=1, damping=0.05, shift0=-1.0, n0=1000, control=0,
                  t_eq=-1, capacity_entries=0, capacity_spawns=0, stream=None, sm_limit=0, field_h=0.0,
-                 field_axis=0, wide_sort_bits=64):
+                 field_axis=0, wide_sort_bits=64, field_theta=0.0):
         o = ddqmc_default_options()
         o.seed = int(seed) & ((1 << 64) - 1)
         o.damping = damping
@@ -402,6 +402,7 @@ class Run:
         o.field_h = float(field_h)
         o.field_axis = int(field_axis)
         o.wide_sort_bits = int(wide_sort_bits)
+        o.field_theta = float(field_theta)
         g = ddqmc_guide()
         g.kind = int(guide_kind)
         g.p = float(guide_p)
@@ -462,7 +463,7 @@ class Run:
 
 
 def run_spec(Jx, Jy, Jz, gamma, dt, target, n_a=0, seed=1, damping=0.05, shift0=-1.0, n0=1000, control=0,
-             t_eq=-1, field_h=0.0, field_axis=0):
+             t_eq=-1, field_h=0.0, field_axis=0, field_theta=0.0):
     """A ddqmc_run_spec with the keyword names of ``Run``."""
     q = ddqmc_run_spec()
     q.Jx, q.Jy, q.Jz, q.gamma, q.dt = float(Jx), float(Jy), float(Jz), float(gamma), float(dt)
@@ -477,6 +478,7 @@ def run_spec(Jx, Jy, Jz, gamma, dt, target, n_a=0, seed=1, damping=0.05, shift0=
     q.field_h = float(field_h)
     q.field_axis = int(field_axis)
     q.reserved = 0
+    q.field_theta = float(field_theta)
     return q
 
 

@@ -53,12 +53,15 @@ def test_option_defaults_and_parameter_checks_need_no_gpu():
     from paper_1802_05931_gb300 import build as b, ddqmc
     b.build()
     o = ddqmc.ddqmc_default_options()
-    assert o.sm_limit == 0 and o.field_h == 0.0 and o.field_axis == 0
+    assert o.sm_limit == 0 and o.field_h == 0.0 and o.field_axis == 0 and o.field_theta == 0.0
+    assert o.wide_sort_bits == 64
     lat = ddqmc.ddqmc_lattice(2, 2, 0)
     for lattice, opt in ((ddqmc.ddqmc_lattice(9, 8, 0), None),          # 72 sites
                          (ddqmc.ddqmc_lattice(2, 2, 1), None),          # L = 2 periodic
-                         (lat, dict(field_axis=2)),                     # no such axis
+                         (lat, dict(field_axis=3)),                     # no such axis
                          (lat, dict(field_h=float("nan"))),
+                         (lat, dict(field_axis=2, field_theta=float("inf"))),
+                         (lat, dict(wide_sort_bits=65)),
                          (lat, dict(control=3))):
         oo = ddqmc.ddqmc_default_options()
         for k, v in (opt or {}).items():

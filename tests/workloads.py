@@ -34,7 +34,7 @@ def run_kwargs(cfg, **over):
         kw["guide_p"] = c.get("guide_p", 0.0)
         if gk == 2:
             kw["site_ratio"] = [math.exp(-c.get("guide_p", 0.0))] * (c["Lx"] * c["Ly"])
-    for k in ("n0", "shift0", "damping", "t_eq", "field_h", "field_axis"):
+    for k in ("n0", "shift0", "damping", "t_eq", "field_h", "field_axis", "field_theta"):
         if k in c:
             kw[k] = c[k]
     args = (c["Lx"], c["Ly"], c["periodic"], c["Jx"], c["Jy"], c["Jz"], c["gamma"], c["dt"], c["target"])
