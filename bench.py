@@ -286,6 +286,13 @@ def pinned_list_buffers(n):
     return b[0].view(np.uint64), b[1].view(np.uint64), b[2], b[3]
 
 
+def pinned_record_buffer(n):
+    """A page-locked host array of n 16-byte list records (RECORD_DTYPE)."""
+    import torch
+    from paper_1802_05931_gb300 import ddqmc
+    return torch.empty(16 * n, dtype=torch.uint8, pin_memory=True).numpy().view(ddqmc.RECORD_DTYPE)
+
+
 SMS = 152                 # GB300 streaming multiprocessors
 SCHEDULERS_PER_SM = 4     # warp schedulers per SM, one warp instruction issued per cycle each
 
@@ -506,34 +513,55 @@ def gpu_arm(args, world, rank, local, pg):
                   "note": "frac_dram: DRAM bytes of the radix passes, the partition, the merge and its compaction "
                           "(committed ncu counters per unit x this run's units) over their CUDA-event time; "
                           "frac_alg_min: 16 B x (spawn records + entries read + entries written) over the same time"}
-    # end to end through the C-ABI with host buffers: import, step, export, estimators
-    e2e = None
+    # end to end through the C-ABI with host buffers: import, step, export,
+    # estimators, every step; the list in the run's own 16-byte records (the
+    # e2e key, one-word keys) and in the four caller arrays (e2e_arrays)
+    e2e, e2e_arrays = None, None
     if args.e2e_steps > 0:
-        # pinned host buffers reused from step to step, as a streaming caller would
         M0 = run.state().entries
-        bufs = pinned_list_buffers(int(1.25 * M0) + 1024)
-        ket, bra, re, im = run.export(out=bufs)
         st = run.state()
         state = (st.t, st.shift, st.variable, st.q_prev, st.t_var, st.t_eq)
-        torch.cuda.synchronize()
-        barrier(pg)
-        t0 = time.perf_counter()
-        e_ws, h2d, d2h = 0, 0, 0
-        for _ in range(args.e2e_steps):
-            run.import_(ket, bra, re, im, *state)
-            h2d += 24 * len(ket)                 # ket, bra (8 B each), re, im (4 B each)
-            run.step(1)
-            e_ws += ddqmc.ddqmc_get_totals(run.h)["walker_steps"]     # import resets the totals
-            ket, bra, re, im = run.export(out=bufs)
-            est = run.raw_estimates()
-            d2h += 24 * len(ket) + 8 * len(est)
-            st = run.state()
-            state = (st.t, st.shift, st.variable, st.q_prev, st.t_var, st.t_eq)
-        el = time.perf_counter() - t0
-        el = reduce_max(pg, el)
-        e_all = reduce_sum(pg, e_ws)
-        e2e = {"value": e_all / el, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
-               "d2h_bytes_per_step": d2h // args.e2e_steps, "steps": args.e2e_steps}
+
+        def leg(records):
+            nonlocal state
+            if records:
+                rbuf = pinned_record_buffer(int(1.25 * M0) + 1024)
+                lst = run.export_records(out=rbuf)
+            else:
+                bufs = pinned_list_buffers(int(1.25 * M0) + 1024)
+                lst = run.export(out=bufs)
+            torch.cuda.synchronize()
+            barrier(pg)
+            t0 = time.perf_counter()
+            e_ws, h2d, d2h = 0, 0, 0
+            for _ in range(args.e2e_steps):
+                if records:
+                    run.import_records(lst, *state)
+                    h2d += 16 * len(lst)             # key (8 B), re, im (4 B each)
+                else:
+                    run.import_(*lst, *state)
+                    h2d += 24 * len(lst[0])          # ket, bra (8 B each), re, im (4 B each)
+                run.step(1)
+                e_ws += ddqmc.ddqmc_get_totals(run.h)["walker_steps"]     # import resets the totals
+                if records:
+                    lst = run.export_records(out=rbuf)
+                    d2h += 16 * len(lst)
+                else:
+                    lst = run.export(out=bufs)
+                    d2h += 24 * len(lst[0])
+                est = run.raw_estimates()
+                d2h += 8 * len(est)
+                st = run.state()
+                state = (st.t, st.shift, st.variable, st.q_prev, st.t_var, st.t_eq)
+            el = reduce_max(pg, time.perf_counter() - t0)
+            e_all = reduce_sum(pg, e_ws)
+            return {"value": e_all / el, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
+                    "d2h_bytes_per_step": d2h // args.e2e_steps, "steps": args.e2e_steps,
+                    "api": "ddqmc_import_records / ddqmc_export_records (16-byte records)" if records else
+                           "ddqmc_import_walkers / ddqmc_export_walkers (ket, bra, re, im arrays)"}
+        wide = w["Lx"] * w["Ly"] > 31
+        e2e_arrays = leg(False)
+        e2e = e2e_arrays if wide else leg(True)
     st = run.state()
     est = run.raw_estimates()
     run.close()
@@ -582,7 +610,7 @@ def gpu_arm(args, world, rank, local, pg):
             "step_ms": {"median": statistics.median(step_ms), "p99": step_ms[min(len(step_ms) - 1,
                                                                                    int(0.99 * len(step_ms)))],
                         "min": step_ms[0], "max": step_ms[-1]},
-            "kernels": kern, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "batch": batch, "tuning": tuning,
+            "kernels": kern, "cpu_baseline": cpu, "e2e": e2e, "e2e_arrays": e2e_arrays, "serving": serving, "batch": batch, "tuning": tuning,
             "gpu_launches": int(sum(v[1] for v in timing.values())), "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0

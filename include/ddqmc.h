@@ -220,6 +220,26 @@ int ddqmc_import_walkers(ddqmc_run *run, const uint64_t *ket, const uint64_t *br
                          double S, int32_t variable, int64_t q_prev, int64_t t_var,
                          int64_t t_eq);
 
+/* The walker list in the run's own record layout, for callers that stream it
+ * through host memory every step: 16-byte records
+ *     { uint64_t key = bra << N | ket; int32_t re; int32_t im; }
+ * in canonical order (strictly increasing key), a third fewer bytes than the
+ * four arrays above and no conversion on either side.  Single runs of at most
+ * 31 sites (UNSUPPORTED otherwise).  host_records must be 8-byte aligned; the
+ * copy runs at the link's speed when it is pinned. */
+
+/* Copy the current list into host_records (capacity cap records); *n
+ * receives the list length (cap = 0 queries it).  One copy over the link.
+ * Waits for the run's stream. */
+int ddqmc_export_records(ddqmc_run *run, void *host_records, int64_t cap, int64_t *n);
+
+/* Replace the list with n host records and set the state as
+ * ddqmc_import_walkers does (same checks: keys strictly increasing and within
+ * 2N bits, no all-zero entry; INVALID_ARG leaves the run as it was).  One copy
+ * over the link into the run's spare list buffer, checked there. */
+int ddqmc_import_records(ddqmc_run *run, const void *host_records, int64_t n, int64_t t, double S,
+                         int32_t variable, int64_t q_prev, int64_t t_var, int64_t t_eq);
+
 /* Scalar state (waits for the stream). */
 int ddqmc_get_state(ddqmc_run *run, ddqmc_state *out);
 

@@ -1739,6 +1739,32 @@ int ddqmc_batch_export_walkers(ddqmc_run *r, int32_t run, uint64_t *ket, uint64_
     return export_of(r, run, ket, bra, re, im, cap, n);
 }
 
+// The imported list (n entries, W walkers) in the spare buffer becomes the
+// current one, with the given step state; the look-back epoch keeps counting,
+// so that no status word left by an earlier step can match a later one.
+int finish_import(ddqmc_run *r, int64_t n, int64_t W, uint32_t old_epoch, int64_t t, double S, int32_t variable,
+                  int64_t q_prev, int64_t t_var, int64_t t_eq) {
+    r->cur ^= 1;
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.t = t;
+    hs.S = S;
+    hs.variable = variable ? 1 : 0;
+    hs.q_prev = q_prev;
+    hs.t_var = t_var;
+    hs.t_eq = t_eq;
+    hs.M = n;
+    hs.W_cur = W;
+    hs.epoch = (old_epoch + 16u) & 0x3FFFFFFFu;
+    host_death_table(r->hp, S, hs);
+    bool ok = cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * (size_t)NOBS_MAX * LEVELS, r->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    r->host_status = 0;
+    return DDQMC_OK;
+}
+
 int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra, const int32_t *re,
                          const int32_t *im, int64_t n, int64_t t, double S, int32_t variable, int64_t q_prev,
                          int64_t t_var, int64_t t_eq) {
@@ -1797,25 +1823,59 @@ int ddqmc_import_walkers(ddqmc_run *r, const uint64_t *ket, const uint64_t *bra,
             }
         }
     }
-    r->cur ^= 1;
-    DevState hs;
-    std::memset(&hs, 0, sizeof(hs));
-    hs.t = t;
-    hs.S = S;
-    hs.variable = variable ? 1 : 0;
-    hs.q_prev = q_prev;
-    hs.t_var = t_var;
-    hs.t_eq = t_eq;
-    hs.M = n;
-    hs.W_cur = W;
-    hs.epoch = (old_epoch + 16u) & 0x3FFFFFFFu;
-    host_death_table(r->hp, S, hs);
-    bool ok = cudaMemcpyAsync(r->dS, &hs, sizeof(DevState), cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
-    ok = ok && cudaMemsetAsync(r->dBlk, 0, sizeof(BlkCell) * (size_t)NOBS_MAX * LEVELS, r->stream) == cudaSuccess;
+    return finish_import(r, n, W, old_epoch, t, S, variable, q_prev, t_var, t_eq);
+}
+
+int ddqmc_export_records(ddqmc_run *r, void *host_records, int64_t cap, int64_t *n) {
+    if (!r || !n || cap < 0 || (cap > 0 && !host_records) || ((uintptr_t)host_records & 7u)) return DDQMC_ERR_INVALID_ARG;
+    if (r->nruns || r->wide) return DDQMC_ERR_UNSUPPORTED;
+    int64_t M = 0;
+    if (cudaMemcpyAsync(&M, &r->dS->M, sizeof(M), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    *n = M;
+    const int64_t m = M < cap ? M : cap;
+    if (m <= 0) return DDQMC_OK;
+    if (cudaMemcpyAsync(host_records, r->L[r->cur], sizeof(Rec) * (size_t)m, cudaMemcpyDeviceToHost, r->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    return DDQMC_OK;
+}
+
+int ddqmc_import_records(ddqmc_run *r, const void *host_records, int64_t n, int64_t t, double S, int32_t variable,
+                         int64_t q_prev, int64_t t_var, int64_t t_eq) {
+    if (!r || n < 0 || (n > 0 && !host_records) || ((uintptr_t)host_records & 7u) || t < 0 || !std::isfinite(S))
+        return DDQMC_ERR_INVALID_ARG;
+    if (r->nruns || r->wide) return DDQMC_ERR_UNSUPPORTED;
+    if (n > r->mcap) return DDQMC_ERR_CAPACITY;
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    if (!soa_scratch(r, 1)) return DDQMC_ERR_OOM;
+    // straight into the spare list buffer, checked there (a rejected list
+    // leaves the run as it was)
+    unsigned long long acc[2] = {0ull, 0ull};
+    uint32_t old_epoch = 0;
+    const int kbits = 2 * r->hp.N;
+    bool ok = cudaMemsetAsync(r->dxfer, 0, 2 * sizeof(unsigned long long), r->stream) == cudaSuccess;
+    if (n > 0) {
+        ok = ok && cudaMemcpyAsync(r->L[r->cur ^ 1], host_records, sizeof(Rec) * (size_t)n, cudaMemcpyHostToDevice,
+                                   r->stream) == cudaSuccess;
+        k_check_records<<<grid_for(n), TX_TPB, 0, r->stream>>>(reinterpret_cast<const Rec *>(r->L[r->cur ^ 1]), n,
+                                                                kbits >= 64 ? ~0ull : (1ull << kbits) - 1ull,
+                                                                r->dxfer);
+        ok = ok && cudaGetLastError() == cudaSuccess;
+    }
+    ok = ok && cudaMemcpyAsync(acc, r->dxfer, sizeof(acc), cudaMemcpyDeviceToHost, r->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(&old_epoch, &r->dS->epoch, sizeof(old_epoch), cudaMemcpyDeviceToHost, r->stream) ==
+                   cudaSuccess;
     ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
     if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
-    r->host_status = 0;
-    return DDQMC_OK;
+    if (acc[1]) return DDQMC_ERR_INVALID_ARG;
+    return finish_import(r, n, (int64_t)acc[0], old_epoch, t, S, variable, q_prev, t_var, t_eq);
 }
 
 int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_spawns, int64_t nsp, void *d_out,

@@ -68,6 +68,31 @@ k_import_pack(const uint64_t *__restrict__ ket, const uint64_t *__restrict__ bra
     }
 }
 
+// Check n list records already in place (the caller's 16-byte records): key
+// within kmask, no empty entry, keys strictly increasing.  acc as k_import_pack.
+__global__ void __launch_bounds__(TX_TPB)
+k_check_records(const Rec *__restrict__ L, int64_t n, uint64_t kmask, unsigned long long *__restrict__ acc) {
+    __shared__ unsigned long long s_w[TX_TPB / 32];
+    int64_t w = 0;
+    bool bad = false;
+    for (int64_t q = (int64_t)blockIdx.x * TX_TPB + threadIdx.x; q < n; q += (int64_t)gridDim.x * TX_TPB) {
+        const Rec v = L[q];
+        bad |= (v.key & ~kmask) != 0ull || (v.re == 0 && v.im == 0);
+        if (q > 0) bad |= L[q - 1].key >= v.key;
+        w += (int64_t)(v.re < 0 ? -(int64_t)v.re : v.re) + (int64_t)(v.im < 0 ? -(int64_t)v.im : v.im);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xFFFFFFFFu, w, off);
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(&acc[1], 1ull);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = (unsigned long long)w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int k = 0; k < TX_TPB / 32; ++k) t += s_w[k];
+        if (t) atomicAdd(&acc[0], t);
+    }
+}
+
 // Unpack list records [0, m) into the caller's layout (the batch run id, if
 // any, dropped from the bra word).
 template <typename LT>

@@ -88,7 +88,8 @@ class ddqmc_state(C.Structure):
 
 EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_async", "ddqmc_sync",
            "ddqmc_estimators", "ddqmc_raw_estimators", "ddqmc_blocking_moments",
-           "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_get_state", "ddqmc_get_counts",
+           "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_export_records", "ddqmc_import_records",
+           "ddqmc_get_state", "ddqmc_get_counts",
            "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_tune", "ddqmc_set_tuning",
            "ddqmc_get_tuning", "ddqmc_annihilate",
            "ddqmc_annihilate_noalloc", "ddqmc_wait_selftest", "ddqmc_create_batch", "ddqmc_batch_estimators",
@@ -123,6 +124,8 @@ def load(path: str = LIB_PATH):
     lib.ddqmc_raw_estimators.argtypes = [vp, P(i64), i32, P(i32)]
     lib.ddqmc_blocking_moments.argtypes = [vp, i32, i32, P(i64), P(i64), P(i64), P(i64)]
     lib.ddqmc_export_walkers.argtypes = [vp, P(u64), P(u64), P(i32), P(i32), i64, P(i64)]
+    lib.ddqmc_export_records.argtypes = [vp, vp, i64, P(i64)]
+    lib.ddqmc_import_records.argtypes = [vp, vp, i64, i64, dbl, i32, i64, i64, i64]
     lib.ddqmc_import_walkers.argtypes = [vp, P(u64), P(u64), P(i32), P(i32), i64, i64, dbl, i32, i64,
                                          i64, i64]
     lib.ddqmc_get_state.argtypes = [vp, P(ddqmc_state)]
@@ -224,6 +227,30 @@ def ddqmc_export_walkers(run, out=None):
     those dtypes to write into (reused when long enough, e.g. between steps)."""
     lib = load()
     return _export(lambda *a: lib.ddqmc_export_walkers(run, *a), out, "ddqmc_export_walkers")
+
+
+# the run's own 16-byte list records (ddqmc_export_records / ddqmc_import_records)
+RECORD_DTYPE = np.dtype([("key", "<u8"), ("re", "<i4"), ("im", "<i4")])
+
+
+def ddqmc_export_records(run, out=None):
+    """The current list as RECORD_DTYPE records (key = bra << N | ket); `out`
+    (a RECORD_DTYPE array, e.g. pinned) is written into when long enough."""
+    lib = load()
+    n = C.c_int64()
+    _check(lib.ddqmc_export_records(run, None, 0, C.byref(n)), "ddqmc_export_records")
+    m = n.value
+    if out is None or len(out) < m or out.dtype != RECORD_DTYPE or not out.flags.c_contiguous:
+        out = np.empty(max(m, 1), dtype=RECORD_DTYPE)
+    _check(lib.ddqmc_export_records(run, out.ctypes.data_as(C.c_void_p), len(out), C.byref(n)),
+           "ddqmc_export_records")
+    return out[:m]
+
+
+def ddqmc_import_records(run, recs, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-1):
+    recs = np.ascontiguousarray(recs, dtype=RECORD_DTYPE)
+    _check(load().ddqmc_import_records(run, recs.ctypes.data_as(C.c_void_p), len(recs), int(t), float(S),
+                                       int(variable), int(q_prev), int(t_var), int(t_eq)), "ddqmc_import_records")
 
 
 def ddqmc_batch_export_walkers(batch, k, out=None):
@@ -448,6 +475,12 @@ class Run:
 
     def import_(self, ket, bra, re, im, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-1):
         ddqmc_import_walkers(self.h, ket, bra, re, im, t, S, variable, q_prev, t_var, t_eq)
+
+    def export_records(self, out=None):
+        return ddqmc_export_records(self.h, out)
+
+    def import_records(self, recs, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-1):
+        ddqmc_import_records(self.h, recs, t, S, variable, q_prev, t_var, t_eq)
 
     def state(self):
         return ddqmc_get_state(self.h)

@@ -290,3 +290,48 @@ def test_export_into_reused_buffers(ddqmc):
     short = tuple(np.zeros(1, dtype=dt) for dt in (np.uint64, np.uint64, np.int32, np.int32))
     got2 = run.export(out=short)
     assert all(np.array_equal(a, b) for a, b in zip(ref, got2)) and len(got2[0]) == m
+
+
+def test_records_import_export(ddqmc):
+    """The 16-byte record layout: export_records equals export (key = bra << N
+    | ket); a list imported as records steps exactly as the same list imported
+    as arrays and as the oracle; bad records are rejected and leave the run
+    as it was; two-word keys and batches are refused."""
+    args, kw = W.run_kwargs(W.C2, target=30000)
+    run = ddqmc.Run(*args, **kw)
+    run.step(150)
+    ket, bra, re, im = run.export()
+    recs = run.export_records()
+    N = 9
+    assert np.array_equal(recs["key"], (bra << np.uint64(N)) | ket)
+    assert np.array_equal(recs["re"], re) and np.array_equal(recs["im"], im)
+    s = run.state()
+    st = (s.t, s.shift, s.variable, s.q_prev, s.t_var, s.t_eq)
+    a = ddqmc.Run(*args, **kw)
+    b = ddqmc.Run(*args, **kw)
+    a.import_records(recs, *st)
+    b.import_(ket, bra, re, im, *st)
+    cpu = O.OracleRun(*args, **kw)
+    cpu.import_(ket, bra, re, im)
+    cpu.set_state(*st)
+    for t in range(20):
+        a.step(1)
+        b.step(1)
+        cpu.step(1)
+        _same(a, cpu, ("records", t))
+        assert np.array_equal(a.export_records(), b.export_records())
+    before = a.export_records().copy()
+    for bad in (recs[::-1], np.concatenate([recs, recs[-1:]])):
+        with pytest.raises(ddqmc.DDQMCError) as e:
+            a.import_records(bad, *st)
+        assert e.value.code == -1
+    zero = recs.copy()
+    zero["re"][3] = 0
+    zero["im"][3] = 0
+    with pytest.raises(ddqmc.DDQMCError):
+        a.import_records(zero, *st)
+    assert np.array_equal(a.export_records(), before)
+    wide = ddqmc.Run(6, 6, 1, 0.9, 1.0, 1.0, 1.0, 0.005, 1000)
+    with pytest.raises(ddqmc.DDQMCError) as e:
+        wide.export_records()
+    assert e.value.code == -7
