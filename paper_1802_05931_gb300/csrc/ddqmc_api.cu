@@ -416,13 +416,14 @@ int grid_for(int64_t n) {
     return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
 }
 
-constexpr size_t SP_SMEM = sizeof(SpawnShared<Rec>);
-constexpr size_t SPP_SMEM = sizeof(SpawnShared<uint64_t>);
+// spawn kernel shared memory, without / with the field's moves
+constexpr size_t SP_SMEM = sizeof(SpawnShared<Rec, false>), SP_SMEM_F = sizeof(SpawnShared<Rec, true>);
+constexpr size_t SPP_SMEM = sizeof(SpawnShared<uint64_t, false>), SPP_SMEM_F = sizeof(SpawnShared<uint64_t, true>);
 constexpr size_t RX_SMEM = sizeof(RadixShared<Rec>);
 constexpr size_t RXP_SMEM = sizeof(RadixShared<uint64_t>);
 constexpr size_t MG_SMEM = sizeof(MergeShared<Rec>);
 constexpr size_t MGP_SMEM = sizeof(MergeShared<uint64_t>);
-constexpr size_t SPW_SMEM = sizeof(SpawnShared<RecW>);
+constexpr size_t SPW_SMEM = sizeof(SpawnShared<RecW, false>), SPW_SMEM_F = sizeof(SpawnShared<RecW, true>);
 constexpr size_t RXW_SMEM = sizeof(RadixShared<RecW>);
 // radix tile sizes (records per thread) of packed records the tuner chooses from
 constexpr int RX_PK_IPT[3] = {12, 16, 24};
@@ -450,10 +451,10 @@ void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(in
     DevState *rs = BATCH ? r->dRS : r->dS;
     mark(0, 0);
     if (P.field_on)
-        k_spawn_death<T, true, BATCH><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(
+        k_spawn_death<T, true, BATCH><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T, true>), r->stream>>>(
             r->dP, r->dS, Lc, sp0, r->rcap, Pr, rs, (int64_t)r->tune.heavy_walkers);
     else
-        k_spawn_death<T, false, BATCH><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T>), r->stream>>>(
+        k_spawn_death<T, false, BATCH><<<r->g_spawn, SP_TPB, sizeof(SpawnShared<T, false>), r->stream>>>(
             r->dP, r->dS, Lc, sp0, r->rcap, Pr, rs, (int64_t)r->tune.heavy_walkers);
     mark(0, 1);
     mark(1, 0);
@@ -663,17 +664,17 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     auto attr = [&](const void *fn, size_t bytes) {
         ok = ok && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
     };
-    attr((const void *)k_spawn_death<Rec, true, false>, SP_SMEM);
+    attr((const void *)k_spawn_death<Rec, true, false>, SP_SMEM_F);
     attr((const void *)k_spawn_death<Rec, false, false>, SP_SMEM);
-    attr((const void *)k_spawn_death<uint64_t, true, false>, SPP_SMEM);
+    attr((const void *)k_spawn_death<uint64_t, true, false>, SPP_SMEM_F);
     attr((const void *)k_spawn_death<uint64_t, false, false>, SPP_SMEM);
-    attr((const void *)k_spawn_death<RecW, true, false>, SPW_SMEM);
+    attr((const void *)k_spawn_death<RecW, true, false>, SPW_SMEM_F);
     attr((const void *)k_spawn_death<RecW, false, false>, SPW_SMEM);
-    attr((const void *)k_spawn_death<Rec, true, true>, SP_SMEM);
+    attr((const void *)k_spawn_death<Rec, true, true>, SP_SMEM_F);
     attr((const void *)k_spawn_death<Rec, false, true>, SP_SMEM);
-    attr((const void *)k_spawn_death<uint64_t, true, true>, SPP_SMEM);
+    attr((const void *)k_spawn_death<uint64_t, true, true>, SPP_SMEM_F);
     attr((const void *)k_spawn_death<uint64_t, false, true>, SPP_SMEM);
-    attr((const void *)k_spawn_death<RecW, true, true>, SPW_SMEM);
+    attr((const void *)k_spawn_death<RecW, true, true>, SPW_SMEM_F);
     attr((const void *)k_spawn_death<RecW, false, true>, SPW_SMEM);
     attr((const void *)k_radix_pass<Rec>, RX_SMEM);
     attr((const void *)k_radix_pass<uint64_t>, RXP_SMEM);
@@ -700,21 +701,25 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     const size_t est_bytes = B ? sizeof(unsigned long long) * (size_t)r->nruns * (size_t)r->hp.nobs : 0;
     const void *fs, *fr, *fm;
     size_t ss, sr, sm, bmax;
+    const bool F = r->hp.field_on != 0;
     if (r->packed) {
-        fs = B ? (const void *)k_spawn_death<uint64_t, false, true> : (const void *)k_spawn_death<uint64_t, false, false>;
+        fs = F ? (B ? (const void *)k_spawn_death<uint64_t, true, true> : (const void *)k_spawn_death<uint64_t, true, false>)
+               : (B ? (const void *)k_spawn_death<uint64_t, false, true> : (const void *)k_spawn_death<uint64_t, false, false>);
         fr = (const void *)k_radix_pass<uint64_t>;
         fm = B ? (const void *)k_merge<uint64_t, true> : (const void *)k_merge<uint64_t, false>;
-        ss = SPP_SMEM; sr = RXP_SMEM; sm = MGP_SMEM; bmax = bmax_pk;
+        ss = F ? SPP_SMEM_F : SPP_SMEM; sr = RXP_SMEM; sm = MGP_SMEM; bmax = bmax_pk;
     } else if (r->wide) {
-        fs = B ? (const void *)k_spawn_death<RecW, false, true> : (const void *)k_spawn_death<RecW, false, false>;
+        fs = F ? (B ? (const void *)k_spawn_death<RecW, true, true> : (const void *)k_spawn_death<RecW, true, false>)
+               : (B ? (const void *)k_spawn_death<RecW, false, true> : (const void *)k_spawn_death<RecW, false, false>);
         fr = (const void *)k_radix_pass<RecW>;
         fm = B ? (const void *)k_merge<RecW, true> : (const void *)k_merge<RecW, false>;
-        ss = SPW_SMEM; sr = RXW_SMEM; sm = MGW_SMEM; bmax = bmax_w;
+        ss = F ? SPW_SMEM_F : SPW_SMEM; sr = RXW_SMEM; sm = MGW_SMEM; bmax = bmax_w;
     } else {
-        fs = B ? (const void *)k_spawn_death<Rec, false, true> : (const void *)k_spawn_death<Rec, false, false>;
+        fs = F ? (B ? (const void *)k_spawn_death<Rec, true, true> : (const void *)k_spawn_death<Rec, true, false>)
+               : (B ? (const void *)k_spawn_death<Rec, false, true> : (const void *)k_spawn_death<Rec, false, false>);
         fr = (const void *)k_radix_pass<Rec>;
         fm = B ? (const void *)k_merge<Rec, true> : (const void *)k_merge<Rec, false>;
-        ss = SP_SMEM; sr = RX_SMEM; sm = MG_SMEM; bmax = bmax_rec;
+        ss = F ? SP_SMEM_F : SP_SMEM; sr = RX_SMEM; sm = MG_SMEM; bmax = bmax_rec;
     }
     r->mg_smem = sm + est_bytes;
     if (B && r->mg_smem > bmax) return DDQMC_ERR_UNSUPPORTED;   // too many runs x observables

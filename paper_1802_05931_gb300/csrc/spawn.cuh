@@ -99,12 +99,20 @@ struct HeavyTables {
 // moves per configuration for one-word keys: 2 * 62 bonds + 3 * 31 sites
 constexpr int MAXK_PACK = 2 * 2 * NPACK + 3 * NPACK + 1;
 
+// Moves a warp's table holds: without the field's site flips a
+// configuration has at most 2B + N moves (two-word keys: 320 against 448),
+// which is what lets the two-word kernel keep two blocks per SM.
+template <typename T, bool FIELD> struct HeavyCap {
+    static constexpr int value = std::is_same<T, RecW>::value ? (FIELD ? MAXK : 2 * MAXB + MAXN)
+                                                              : (FIELD ? MAXK_PACK : 2 * 2 * NPACK + NPACK);
+};
+
 // A warp's light-configuration parameters are dead before its heavy
 // configurations start, so the two share storage.
-template <typename T>
+template <typename T, bool FIELD>
 union WarpScratch {
     LightSoA<typename LightTypes<T>::MT, typename LightTypes<T>::SW> le;
-    HeavyTables<std::is_same<T, RecW>::value ? MAXK : MAXK_PACK> hv;
+    HeavyTables<HeavyCap<T, FIELD>::value> hv;
 };
 
 // Constant tables of one step, staged in shared memory.
@@ -135,15 +143,16 @@ struct SpawnTables {
     int32_t fparts;                   // moves per site flip and segment: 2 when a run has axis 2
 };
 
-// Shared memory of the spawn kernel for spawn records of type T; packed
-// records (keys of at most 32 bits) need at most four digit passes.
-template <typename T>
+// Shared memory of the spawn kernel for spawn records of type T, with or
+// without the field's moves; packed records (keys of at most 32 bits) need at
+// most four digit passes.
+template <typename T, bool FIELD>
 struct SpawnShared : SpawnTables {
     static constexpr int NP = sizeof(T) == 8 ? 4 : (std::is_same<T, RecW>::value ? MAXPASS : 8);
     uint32_t hist[NP][256];
     int32_t stage_n[SP_WARPS];
     T stage[SP_WARPS][SP_STAGE];
-    WarpScratch<T> ws[SP_WARPS];
+    WarpScratch<T, FIELD> ws[SP_WARPS];
     int32_t mark[SP_WARPS][32];       // first walker position of each configuration of the chunk
     int32_t dre[SP_WARPS][32], dim[SP_WARPS][32];
     uint64_t qv[SP_WARPS][64];        // queued spawn draws: scaled uniform v
@@ -488,8 +497,8 @@ __device__ __forceinline__ RecW make_spawn<RecW>(uint64_t ci, uint64_t cj, int, 
     return r;
 }
 
-template <typename T>
-__device__ __forceinline__ void count_digits(SpawnShared<T> &s, const T &r, int npass) {
+template <typename T, bool F>
+__device__ __forceinline__ void count_digits(SpawnShared<T, F> &s, const T &r, int npass) {
     // one-word keys: pass p reads bits 8p..8p+7; two-word keys: per-pass shifts
     for (int p = 0; p < npass; ++p) {
         const int shift = std::is_same<T, RecW>::value ? s.pass_shift[p] : 8 * p;
@@ -498,8 +507,8 @@ __device__ __forceinline__ void count_digits(SpawnShared<T> &s, const T &r, int 
 }
 
 // Append one record from a (possibly divergent) lane.
-template <typename T>
-__device__ __forceinline__ void emit(SpawnShared<T> &s, int warp, const T &r, T *out, int64_t cap,
+template <typename T, bool F>
+__device__ __forceinline__ void emit(SpawnShared<T, F> &s, int warp, const T &r, T *out, int64_t cap,
                                      DevState *st, int npass) {
     T *stage = &s.stage[warp][0];
     // one staging-counter update for all the lanes that emit together
@@ -526,8 +535,8 @@ __device__ __forceinline__ void emit(SpawnShared<T> &s, int warp, const T &r, T 
 // Append an aggregated child (any int32 counts): packed records carry at most
 // PK_LIM walkers per part and two-word records WK_LIM, so large counts become
 // several records.
-template <typename T>
-__device__ __forceinline__ void emit_counts(SpawnShared<T> &s, int warp, uint64_t ci, uint64_t cj, int N, bool flag,
+template <typename T, bool F>
+__device__ __forceinline__ void emit_counts(SpawnShared<T, F> &s, int warp, uint64_t ci, uint64_t cj, int N, bool flag,
                                             int cre, int cim, T *out, int64_t cap, DevState *st, int npass,
                                             uint64_t kp) {
     if constexpr (std::is_same<T, Rec>::value) {
@@ -545,8 +554,8 @@ __device__ __forceinline__ void emit_counts(SpawnShared<T> &s, int warp, uint64_
 }
 
 // Warp-uniform flush of the warp's staged records.
-template <typename T>
-__device__ __forceinline__ void flush(SpawnShared<T> &s, int warp, int lane, T *out, int64_t cap,
+template <typename T, bool F>
+__device__ __forceinline__ void flush(SpawnShared<T, F> &s, int warp, int lane, T *out, int64_t cap,
                                       DevState *st, int npass, int min_n) {
     __syncwarp();
     const T *stage = &s.stage[warp][0];
@@ -594,7 +603,7 @@ __device__ __forceinline__ uint32_t attempt_word(uint4 x0, uint4 &xb, uint32_t &
 // run reads its rate tables from shared memory; in a batch (BATCH) each
 // configuration carries its run id and the tables are that run's (Pr).
 template <typename T, typename MT, typename SW, bool FIELD, bool BATCH>
-__device__ __forceinline__ void spawn_drain(SpawnShared<T> &s, const SpawnCtx &c, const RunParams *__restrict__ Pr,
+__device__ __forceinline__ void spawn_drain(SpawnShared<T, FIELD> &s, const SpawnCtx &c, const RunParams *__restrict__ Pr,
                                             int run_shift, int warp, int lane, int n, int N, T *out, int64_t cap,
                                             DevState *st, int npass) {
     if (lane < n) {
@@ -730,7 +739,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
     using LT = typename ListOf<T>::type;
     constexpr bool WIDE = std::is_same<T, RecW>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SpawnShared<T> &s = *reinterpret_cast<SpawnShared<T> *>(smem_raw);
+    SpawnShared<T, FIELD> &s = *reinterpret_cast<SpawnShared<T, FIELD> *>(smem_raw);
     const RunParams &P = *Pp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (block_stopped(st)) return;
@@ -771,7 +780,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
     for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_frac[q] = st->d_frac[q]; s.d_sgn[q] = st->d_sgn[q]; }
     for (int q = tid; q <= 2 * B; q += SP_TPB) s.cross_frac32[q] = (uint32_t)P.cross_frac[q];
     for (int q = tid; q <= 2 * N; q += SP_TPB) s.d_frac32[q] = (uint32_t)st->d_frac[q];
-    for (int q = tid; q < SpawnShared<T>::NP * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
+    for (int q = tid; q < SpawnShared<T, FIELD>::NP * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
     if (tid < SP_WARPS) s.stage_n[tid] = 0;
     __syncthreads();
 
