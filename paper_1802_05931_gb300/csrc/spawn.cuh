@@ -118,9 +118,7 @@ union WarpScratch {
 // Constant tables of one step, staged in shared memory.
 struct SpawnTables {
     uint64_t bond_m[MAXB];
-    uint64_t cross_frac[2 * MAXB + 1];
-    uint64_t d_frac[2 * MAXN + 1];
-    uint32_t cross_frac32[2 * MAXB + 1];  // the same fractions in 32 bits (each is below 2^32)
+    uint32_t cross_frac32[2 * MAXB + 1];  // fractional parts of the cross and death counts, x 2^32
     uint32_t d_frac32[2 * MAXN + 1];
     uint64_t urate8[8];
     uint32_t urate32[8];
@@ -141,6 +139,15 @@ struct SpawnTables {
     float ufinv2[4];
     int32_t field_on, field_axis, sgn_hf, sgn_hf2;
     int32_t fparts;                   // moves per site flip and segment: 2 when a run has axis 2
+};
+
+// Resident blocks per SM the spawn kernel is compiled for: four for a single
+// run with packed records (64 registers a thread: a few spills, measured
+// faster than three blocks at 80); two for two-word keys, whose shared memory
+// allows no more (so up to 128 registers a thread); else three.
+template <typename T, bool BATCH> struct SpawnBlocks {
+    static constexpr int value = std::is_same<T, RecW>::value ? 2
+                                 : ((std::is_same<T, uint64_t>::value && !BATCH) ? 4 : 3);
 };
 
 // Shared memory of the spawn kernel for spawn records of type T, with or
@@ -728,7 +735,7 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T, FIELD> &s, const Spaw
 // table, and st the shared step counters.  A single run passes Pr = Pp and
 // rs = st (unread).
 template <typename T, bool FIELD, bool BATCH>
-__global__ void __launch_bounds__(SP_TPB, 3)
+__global__ void __launch_bounds__(SP_TPB, (SpawnBlocks<T, BATCH>::value))
 k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typename ListOf<T>::type *__restrict__ L,
               T *__restrict__ out, int64_t cap, const RunParams *__restrict__ Pr, const DevState *__restrict__ rs,
               int64_t heavy_walkers) {
@@ -776,8 +783,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
         s.sgn_hf2 = P.sgn_hf2;
         s.fparts = P.K == 2 * P.B + 5 * P.N ? 2 : 1;
     }
-    for (int q = tid; q <= 2 * B; q += SP_TPB) { s.cross_int[q] = P.cross_int[q]; s.cross_frac[q] = P.cross_frac[q]; }
-    for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_frac[q] = st->d_frac[q]; s.d_sgn[q] = st->d_sgn[q]; }
+    for (int q = tid; q <= 2 * B; q += SP_TPB) s.cross_int[q] = P.cross_int[q];
+    for (int q = tid; q <= 2 * N; q += SP_TPB) { s.d_int[q] = st->d_int[q]; s.d_sgn[q] = st->d_sgn[q]; }
     for (int q = tid; q <= 2 * B; q += SP_TPB) s.cross_frac32[q] = (uint32_t)P.cross_frac[q];
     for (int q = tid; q <= 2 * N; q += SP_TPB) s.d_frac32[q] = (uint32_t)st->d_frac[q];
     for (int q = tid; q < SpawnShared<T, FIELD>::NP * 256; q += SP_TPB) (&s.hist[0][0])[q] = 0u;
@@ -1151,8 +1158,8 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                         cc = (int64_t)HP.cross_int[adz] + ((uint64_t)x.z < HP.cross_frac[adz] ? 1 : 0);
                         dsg = HS.d_sgn[cd];
                     } else {
-                        cnt = (int64_t)s.d_int[cd] + ((uint64_t)x.y < s.d_frac[cd] ? 1 : 0);
-                        cc = (int64_t)s.cross_int[adz] + ((uint64_t)x.z < s.cross_frac[adz] ? 1 : 0);
+                        cnt = (int64_t)s.d_int[cd] + (x.y < s.d_frac32[cd] ? 1 : 0);
+                        cc = (int64_t)s.cross_int[adz] + (x.z < s.cross_frac32[adz] ? 1 : 0);
                         dsg = s.d_sgn[cd];
                     }
                     if (part == 0) { dre -= dsg * sig * cnt; dim += (int64_t)sig * sgn_d * cc; }
