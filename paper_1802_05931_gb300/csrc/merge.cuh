@@ -285,10 +285,13 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
     return v;
 }
-// resident blocks per SM the merge is compiled for (85 registers a thread at
-// 3; 128-bit keys need more)
-template <typename T> struct MergeBlocks { static constexpr int value = 3; };
-template <> struct MergeBlocks<RecW> { static constexpr int value = 2; };
+// resident blocks per SM the merge is compiled for: 4 for a single run with
+// packed records (64 registers a thread: a few spills, measured faster than
+// 3 at 80), 2 for 128-bit keys, else 3
+template <typename T, bool BATCH> struct MergeBlocks {
+    static constexpr int value = std::is_same<T, RecW>::value ? 2
+                                 : ((std::is_same<T, uint64_t>::value && !BATCH) ? 4 : 3);
+};
 
 __device__ __forceinline__ int64_t shfl_up_i64(int64_t v, int off) {
     return (int64_t)__shfl_up_sync(0xFFFFFFFFu, (long long)v, off);
@@ -340,7 +343,7 @@ __device__ __noinline__ void rem_sums(const T *__restrict__ S, int64_t b1, int64
 }
 
 template <typename T, bool BATCH>
-__global__ void __launch_bounds__(MG_TPB, MergeBlocks<T>::value)
+__global__ void __launch_bounds__(MG_TPB, (MergeBlocks<T, BATCH>::value))
 k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__restrict__ L, const T *__restrict__ S,
         typename ListOf<T>::type *__restrict__ slots, uint32_t *__restrict__ counts, DevState *__restrict__ st,
         const int64_t *__restrict__ splits, const int64_t *__restrict__ rem_end, int64_t rcap,
