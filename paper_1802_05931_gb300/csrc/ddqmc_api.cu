@@ -58,6 +58,7 @@ struct ddqmc_run {
     int g_copy_ann = 0;          // compaction copy grid of 16-byte records (standalone annihilation)
     bool packed = false;         // 8-byte spawn records (2N <= 32) on the step path
     bool wide = false;           // two-word keys (N > 31): RecW lists and spawn records
+    bool p40 = false;            // 8-byte spawn records of 33- to 40-bit keys (P40) on the step path
     int guide_kind = 0;
     double w_bond[MAXB];         // importance weight of a configuration differing on bond b only
     double w_site[MAXN];         // importance weight of a configuration differing on site k only
@@ -424,6 +425,9 @@ constexpr size_t RXP_SMEM = sizeof(RadixShared<uint64_t>);
 constexpr size_t MG_SMEM = sizeof(MergeShared<Rec>);
 constexpr size_t MGP_SMEM = sizeof(MergeShared<uint64_t>);
 constexpr size_t SPW_SMEM = sizeof(SpawnShared<RecW, false>), SPW_SMEM_F = sizeof(SpawnShared<RecW, true>);
+constexpr size_t SP4_SMEM = sizeof(SpawnShared<P40, false>), SP4_SMEM_F = sizeof(SpawnShared<P40, true>);
+constexpr size_t RX4_SMEM = sizeof(RadixShared<P40>);
+constexpr size_t MG4_SMEM = sizeof(MergeShared<P40>);
 constexpr size_t RXW_SMEM = sizeof(RadixShared<RecW>);
 // radix tile sizes (records per thread) of packed records the tuner chooses from
 constexpr int RX_PK_IPT[3] = {12, 16, 24};
@@ -591,7 +595,7 @@ struct TuneKey {
 std::vector<std::pair<TuneKey, ddqmc_tuning>> g_tune_cache;
 
 TuneKey tune_key(const ddqmc_run *r) {
-    return TuneKey{r->hp.N, r->packed ? 1 : (r->wide ? 2 : 0), r->nruns > 0 ? 1 : 0, r->sms};
+    return TuneKey{r->hp.N, r->packed ? 1 : (r->wide ? 2 : (r->p40 ? 3 : 0)), r->nruns > 0 ? 1 : 0, r->sms};
 }
 
 bool cached_tuning(const ddqmc_run *r, ddqmc_tuning *out) {
@@ -675,6 +679,12 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     attr((const void *)k_spawn_death<uint64_t, true, true>, SPP_SMEM_F);
     attr((const void *)k_spawn_death<uint64_t, false, true>, SPP_SMEM);
     attr((const void *)k_spawn_death<RecW, true, true>, SPW_SMEM_F);
+    attr((const void *)k_spawn_death<P40, true, false>, SP4_SMEM_F);
+    attr((const void *)k_spawn_death<P40, false, false>, SP4_SMEM);
+    attr((const void *)k_spawn_death<P40, true, true>, SP4_SMEM_F);
+    attr((const void *)k_spawn_death<P40, false, true>, SP4_SMEM);
+    attr((const void *)k_radix_pass<P40>, RX4_SMEM);
+    attr((const void *)k_merge<P40, false>, MG4_SMEM);
     attr((const void *)k_spawn_death<RecW, false, true>, SPW_SMEM);
     attr((const void *)k_radix_pass<Rec>, RX_SMEM);
     attr((const void *)k_radix_pass<uint64_t>, RXP_SMEM);
@@ -693,9 +703,11 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
     const size_t bmax_rec = dyn_max((const void *)k_merge<Rec, true>);
     const size_t bmax_pk = dyn_max((const void *)k_merge<uint64_t, true>);
     const size_t bmax_w = dyn_max((const void *)k_merge<RecW, true>);
+    const size_t bmax_p4 = dyn_max((const void *)k_merge<P40, true>);
     attr((const void *)k_merge<Rec, true>, bmax_rec);
     attr((const void *)k_merge<uint64_t, true>, bmax_pk);
     attr((const void *)k_merge<RecW, true>, bmax_w);
+    attr((const void *)k_merge<P40, true>, bmax_p4);
     if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
     const bool B = r->nruns > 0;
     const size_t est_bytes = B ? sizeof(unsigned long long) * (size_t)r->nruns * (size_t)r->hp.nobs : 0;
@@ -708,6 +720,12 @@ int setup_device(ddqmc_run *r, const ddqmc_options &o, int64_t mcap, int64_t rca
         fr = (const void *)k_radix_pass<uint64_t>;
         fm = B ? (const void *)k_merge<uint64_t, true> : (const void *)k_merge<uint64_t, false>;
         ss = F ? SPP_SMEM_F : SPP_SMEM; sr = RXP_SMEM; sm = MGP_SMEM; bmax = bmax_pk;
+    } else if (r->p40) {
+        fs = F ? (B ? (const void *)k_spawn_death<P40, true, true> : (const void *)k_spawn_death<P40, true, false>)
+               : (B ? (const void *)k_spawn_death<P40, false, true> : (const void *)k_spawn_death<P40, false, false>);
+        fr = (const void *)k_radix_pass<P40>;
+        fm = B ? (const void *)k_merge<P40, true> : (const void *)k_merge<P40, false>;
+        ss = F ? SP4_SMEM_F : SP4_SMEM; sr = RX4_SMEM; sm = MG4_SMEM; bmax = bmax_p4;
     } else if (r->wide) {
         fs = F ? (B ? (const void *)k_spawn_death<RecW, true, true> : (const void *)k_spawn_death<RecW, true, false>)
                : (B ? (const void *)k_spawn_death<RecW, false, true> : (const void *)k_spawn_death<RecW, false, false>);
@@ -756,10 +774,12 @@ void launch_one_step(ddqmc_run *r, const std::function<void(int, int)> &mark) {
     void *Lc = r->L[r->cur], *Ln = r->L[r->cur ^ 1];
     if (r->nruns) {
         if (r->packed) launch_step<uint64_t, true>(r, Lc, Ln, mark);
+        else if (r->p40) launch_step<P40, true>(r, Lc, Ln, mark);
         else if (r->wide) launch_step<RecW, true>(r, Lc, Ln, mark);
         else launch_step<Rec, true>(r, Lc, Ln, mark);
     } else {
         if (r->packed) launch_step<uint64_t, false>(r, Lc, Ln, mark);
+        else if (r->p40) launch_step<P40, false>(r, Lc, Ln, mark);
         else if (r->wide) launch_step<RecW, false>(r, Lc, Ln, mark);
         else launch_step<Rec, false>(r, Lc, Ln, mark);
     }
@@ -1346,6 +1366,7 @@ int ddqmc_create(const ddqmc_lattice *lattice, double Jx, double Jy, double Jz, 
     if (rcap <= 0) rcap = default_spawn_capacity(o.control, target_walkers);
     r->wide = r->hp.N > NPACK;
     r->packed = 2 * r->hp.N <= 32;
+    r->p40 = !r->wide && !r->packed && 2 * r->hp.N <= 40;
     rc = setup_device(r, o, mcap, rcap, (size_t)NOBS_MAX * LEVELS);
     if (rc != DDQMC_OK) { free_run(r); return rc; }
     // initial state
@@ -1424,6 +1445,7 @@ int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_
         H.run_shift = 2 * N;
     }
     r->packed = 2 * N + rbits <= 32;
+    r->p40 = !r->wide && !r->packed && 2 * N + rbits <= 40;
     H.nruns = nruns;
     H.field_on = 0;
     for (int k = 0; k < nruns; ++k) H.field_on |= r->hpr[k].field_on;

@@ -49,6 +49,7 @@ __device__ __forceinline__ bool operator!=(const K128 &a, const K128 &b) { retur
 // Keys of the merge tile: 32-bit when spawn records are packed (2N <= 32).
 template <typename T> struct MergeKey { using type = uint64_t; };
 template <> struct MergeKey<uint64_t> { using type = uint32_t; };
+template <> struct MergeKey<P40> { using type = uint64_t; };
 template <> struct MergeKey<RecW> { using type = K128; };
 
 template <typename KT> __device__ __forceinline__ KT list_key(const Rec &v) { return (KT)v.key; }

@@ -71,6 +71,35 @@ __device__ __forceinline__ uint64_t pack_rec(uint64_t key, bool flag, int re, in
            (uint64_t)((uint32_t)re & 0x7FFFu);
 }
 
+// 8-byte record for keys of 33 to 40 bits (lattices of 17 to 20 sites, and
+// batches whose run id takes the key past 32 bits):
+//   bits 63..24 key, bit 23 initiator flag, bits 22..12 Delta im, 11..0 Delta re
+// (11- and 12-bit two's complement); larger aggregated counts become several
+// records.
+struct P40 {
+    uint64_t v;
+};
+constexpr int P40_LIM = 1023;          // largest |Delta| of one such record
+
+template <> struct RecTraits<P40> {
+    static constexpr int IPT = 16;
+    static constexpr int MINB = 3;
+    __device__ __forceinline__ static uint64_t key(P40 r) { return r.v >> 24; }
+    __device__ __forceinline__ static uint32_t digit(P40 r, int shift) {
+        return (uint32_t)((r.v >> 24) >> shift) & 0xFFu;
+    }
+    __device__ __forceinline__ static bool flag(P40 r) { return ((r.v >> 23) & 1ull) != 0ull; }
+    __device__ __forceinline__ static int32_t re(P40 r) { return ((int32_t)((uint32_t)r.v << 20)) >> 20; }
+    __device__ __forceinline__ static int32_t im(P40 r) { return ((int32_t)((uint32_t)(r.v >> 12) << 21)) >> 21; }
+    __device__ __forceinline__ static P40 empty() { return P40{0ull}; }
+};
+
+// |re|, |im| <= P40_LIM
+__device__ __forceinline__ P40 pack_p40(uint64_t key, bool flag, int re, int im) {
+    return P40{(key << 24) | (flag ? (1ull << 23) : 0ull) | ((uint64_t)((uint32_t)im & 0x7FFu) << 12) |
+               (uint64_t)((uint32_t)re & 0xFFFu)};
+}
+
 constexpr int RX_TPB = 256;                  // one thread per digit value
 constexpr int RX_WARPS = RX_TPB / 32;
 constexpr int RX_TILE_MIN = RX_TPB * 6;      // smallest tile (sizes the look-back words)

@@ -68,6 +68,7 @@ __device__ __forceinline__ U128 operator~(const U128 &a) { return U128{~a.lo, ~a
 // type: 2N <= 32 (packed records), N <= 31, N <= 64.
 template <typename T> struct LightTypes { using SW = uint32_t; using MT = uint64_t; };
 template <> struct LightTypes<uint64_t> { using SW = uint32_t; using MT = uint32_t; };
+template <> struct LightTypes<P40> { using SW = uint32_t; using MT = uint64_t; };
 template <> struct LightTypes<RecW> { using SW = uint64_t; using MT = U128; };
 
 // Parameters of the light configurations of one warp's chunk, one array per
@@ -155,7 +156,8 @@ template <typename T, bool BATCH> struct SpawnBlocks {
 // most four digit passes.
 template <typename T, bool FIELD>
 struct SpawnShared : SpawnTables {
-    static constexpr int NP = sizeof(T) == 8 ? 4 : (std::is_same<T, RecW>::value ? MAXPASS : 8);
+    static constexpr int NP = std::is_same<T, uint64_t>::value ? 4
+                              : (std::is_same<T, P40>::value ? 5 : (std::is_same<T, RecW>::value ? MAXPASS : 8));
     uint32_t hist[NP][256];
     int32_t stage_n[SP_WARPS];
     T stage[SP_WARPS][SP_STAGE];
@@ -494,6 +496,10 @@ __device__ __forceinline__ uint64_t make_spawn<uint64_t>(uint64_t ci, uint64_t c
     return pack_rec(kp | (cj << N) | ci, flag, re, im);
 }
 template <>
+__device__ __forceinline__ P40 make_spawn<P40>(uint64_t ci, uint64_t cj, int N, bool flag, int re, int im, uint64_t kp) {
+    return pack_p40(kp | (cj << N) | ci, flag, re, im);
+}
+template <>
 __device__ __forceinline__ RecW make_spawn<RecW>(uint64_t ci, uint64_t cj, int, bool flag, int re, int im,
                                                  uint64_t kp) {
     RecW r;
@@ -549,7 +555,7 @@ __device__ __forceinline__ void emit_counts(SpawnShared<T, F> &s, int warp, uint
     if constexpr (std::is_same<T, Rec>::value) {
         emit(s, warp, make_spawn<T>(ci, cj, N, flag, cre, cim, kp), out, cap, st, npass);
     } else {
-        constexpr int LIM = std::is_same<T, RecW>::value ? WK_LIM : PK_LIM;
+        constexpr int LIM = std::is_same<T, RecW>::value ? WK_LIM : (std::is_same<T, P40>::value ? P40_LIM : PK_LIM);
         while (cre != 0 || cim != 0) {
             const int pr = cre > LIM ? LIM : (cre < -LIM ? -LIM : cre);
             const int pi = cim > LIM ? LIM : (cim < -LIM ? -LIM : cim);

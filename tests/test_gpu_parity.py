@@ -335,3 +335,22 @@ def test_records_import_export(ddqmc):
     with pytest.raises(ddqmc.DDQMCError) as e:
         wide.export_records()
     assert e.value.code == -7
+
+
+def test_p40_records_split_large_counts(ddqmc):
+    """4x5 open (40-bit keys: 8-byte records with 11/12-bit Delta fields):
+    2x10^5 walkers on one configuration take the warp-cooperative path, whose
+    per-move child counts (thousands: |Jx - Jy| = 0.7, dt = 0.02) exceed the
+    fields and are split over several records; bit-exact with the oracle."""
+    args = (4, 5, 0, 0.3, 1.0, 1.0, 1.0, 0.02, 10 ** 6)
+    kw = dict(n_a=3, control=1, seed=21, n0=200000)
+    gpu = ddqmc.Run(*args, capacity_entries=1 << 22, capacity_spawns=1 << 23, **kw)
+    cpu = O.OracleRun(*args, **kw)
+    for t in range(6):
+        gpu.step(1)
+        cpu.step(1)
+        _same(gpu, cpu, t)
+        if t == 0:
+            ket, bra, re, im = gpu.export()
+            off = (ket != 0) | (bra != 0)
+            assert int(np.abs(im[off]).max()) > 1023
