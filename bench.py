@@ -286,11 +286,12 @@ def pinned_list_buffers(n):
     return b[0].view(np.uint64), b[1].view(np.uint64), b[2], b[3]
 
 
-def pinned_record_buffer(n):
-    """A page-locked host array of n 16-byte list records (RECORD_DTYPE)."""
+def pinned_record_buffer(n, dtype=None):
+    """A page-locked host array of n list records (RECORD_DTYPE, or the given dtype)."""
     import torch
     from paper_1802_05931_gb300 import ddqmc
-    return torch.empty(16 * n, dtype=torch.uint8, pin_memory=True).numpy().view(ddqmc.RECORD_DTYPE)
+    dt = ddqmc.RECORD_DTYPE if dtype is None else dtype
+    return torch.empty(dt.itemsize * n, dtype=torch.uint8, pin_memory=True).numpy().view(dt)
 
 
 SMS = 152                 # GB300 streaming multiprocessors
@@ -514,41 +515,47 @@ def gpu_arm(args, world, rank, local, pg):
                           "(committed ncu counters per unit x this run's units) over their CUDA-event time; "
                           "frac_alg_min: 16 B x (spawn records + entries read + entries written) over the same time"}
     # end to end through the C-ABI with host buffers: import, step, export,
-    # estimators, every step; the list in the run's own 16-byte records (the
-    # e2e key, one-word keys) and in the four caller arrays (e2e_arrays)
+    # estimators, every step; the list in the most compact record layout the
+    # lattice allows (the e2e key: 12-byte records up to 16 sites, 16-byte
+    # records up to 31) and in the four caller arrays (e2e_arrays)
     e2e, e2e_arrays = None, None
     if args.e2e_steps > 0:
         M0 = run.state().entries
         st = run.state()
         state = (st.t, st.shift, st.variable, st.q_prev, st.t_var, st.t_eq)
 
-        def leg(records):
+        def leg(mode):
             nonlocal state
-            if records:
-                rbuf = pinned_record_buffer(int(1.25 * M0) + 1024)
-                lst = run.export_records(out=rbuf)
+            if mode == "records32":
+                buf = pinned_record_buffer(int(1.25 * M0) + 1024, ddqmc.RECORD32_DTYPE)
+                get = lambda: run.export_records32(out=buf)
+                put = lambda lst: run.import_records32(lst, *state)
+                nbytes = lambda lst: 12 * len(lst)        # key (4 B), re, im (4 B each)
+                api = "ddqmc_import_records32 / ddqmc_export_records32 (12-byte records)"
+            elif mode == "records":
+                buf = pinned_record_buffer(int(1.25 * M0) + 1024)
+                get = lambda: run.export_records(out=buf)
+                put = lambda lst: run.import_records(lst, *state)
+                nbytes = lambda lst: 16 * len(lst)        # key (8 B), re, im (4 B each)
+                api = "ddqmc_import_records / ddqmc_export_records (16-byte records)"
             else:
-                bufs = pinned_list_buffers(int(1.25 * M0) + 1024)
-                lst = run.export(out=bufs)
+                buf = pinned_list_buffers(int(1.25 * M0) + 1024)
+                get = lambda: run.export(out=buf)
+                put = lambda lst: run.import_(*lst, *state)
+                nbytes = lambda lst: 24 * len(lst[0])     # ket, bra (8 B each), re, im (4 B each)
+                api = "ddqmc_import_walkers / ddqmc_export_walkers (ket, bra, re, im arrays)"
+            lst = get()
             torch.cuda.synchronize()
             barrier(pg)
             t0 = time.perf_counter()
             e_ws, h2d, d2h = 0, 0, 0
             for _ in range(args.e2e_steps):
-                if records:
-                    run.import_records(lst, *state)
-                    h2d += 16 * len(lst)             # key (8 B), re, im (4 B each)
-                else:
-                    run.import_(*lst, *state)
-                    h2d += 24 * len(lst[0])          # ket, bra (8 B each), re, im (4 B each)
+                put(lst)
+                h2d += nbytes(lst)
                 run.step(1)
                 e_ws += ddqmc.ddqmc_get_totals(run.h)["walker_steps"]     # import resets the totals
-                if records:
-                    lst = run.export_records(out=rbuf)
-                    d2h += 16 * len(lst)
-                else:
-                    lst = run.export(out=bufs)
-                    d2h += 24 * len(lst[0])
+                lst = get()
+                d2h += nbytes(lst)
                 est = run.raw_estimates()
                 d2h += 8 * len(est)
                 st = run.state()
@@ -556,12 +563,10 @@ def gpu_arm(args, world, rank, local, pg):
             el = reduce_max(pg, time.perf_counter() - t0)
             e_all = reduce_sum(pg, e_ws)
             return {"value": e_all / el, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
-                    "d2h_bytes_per_step": d2h // args.e2e_steps, "steps": args.e2e_steps,
-                    "api": "ddqmc_import_records / ddqmc_export_records (16-byte records)" if records else
-                           "ddqmc_import_walkers / ddqmc_export_walkers (ket, bra, re, im arrays)"}
-        wide = w["Lx"] * w["Ly"] > 31
-        e2e_arrays = leg(False)
-        e2e = e2e_arrays if wide else leg(True)
+                    "d2h_bytes_per_step": d2h // args.e2e_steps, "steps": args.e2e_steps, "api": api}
+        nsites = w["Lx"] * w["Ly"]
+        e2e_arrays = leg("arrays")
+        e2e = leg("records32") if nsites <= 16 else (leg("records") if nsites <= 31 else e2e_arrays)
     st = run.state()
     est = run.raw_estimates()
     run.close()

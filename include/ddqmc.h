@@ -240,6 +240,15 @@ int ddqmc_export_records(ddqmc_run *run, void *host_records, int64_t cap, int64_
 int ddqmc_import_records(ddqmc_run *run, const void *host_records, int64_t n, int64_t t, double S,
                          int32_t variable, int64_t q_prev, int64_t t_var, int64_t t_eq);
 
+/* The same for lattices of at most 16 sites (keys of at most 32 bits) in
+ * 12-byte records { uint32_t key = bra << N | ket; int32_t re; int32_t im; }
+ * (packed, 4-byte aligned), a quarter fewer bytes over the link than the
+ * 16-byte records; packed and unpacked on the device (UNSUPPORTED for more
+ * sites or a batch). */
+int ddqmc_export_records32(ddqmc_run *run, void *host_records, int64_t cap, int64_t *n);
+int ddqmc_import_records32(ddqmc_run *run, const void *host_records, int64_t n, int64_t t, double S,
+                           int32_t variable, int64_t q_prev, int64_t t_var, int64_t t_eq);
+
 /* Scalar state (waits for the stream). */
 int ddqmc_get_state(ddqmc_run *run, ddqmc_state *out);
 

@@ -1905,6 +1905,63 @@ int ddqmc_import_records(ddqmc_run *r, const void *host_records, int64_t n, int6
     return finish_import(r, n, (int64_t)acc[0], old_epoch, t, S, variable, q_prev, t_var, t_eq);
 }
 
+int ddqmc_export_records32(ddqmc_run *r, void *host_records, int64_t cap, int64_t *n) {
+    if (!r || !n || cap < 0 || (cap > 0 && !host_records) || ((uintptr_t)host_records & 3u)) return DDQMC_ERR_INVALID_ARG;
+    if (r->nruns || 2 * r->hp.N > 32) return DDQMC_ERR_UNSUPPORTED;
+    int64_t M = 0;
+    if (cudaMemcpyAsync(&M, &r->dS->M, sizeof(M), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    *n = M;
+    const int64_t m = M < cap ? M : cap;
+    if (m <= 0) return DDQMC_OK;
+    unsigned char *d = soa_scratch(r, m);
+    if (!d) return DDQMC_ERR_OOM;
+    k_pack_records32<<<grid_for(m), TX_TPB, 0, r->stream>>>(reinterpret_cast<const Rec *>(r->L[r->cur]), m,
+                                                             reinterpret_cast<uint32_t *>(d));
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(host_records, d, 12 * (size_t)m, cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaStreamSynchronize(r->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return DDQMC_ERR_CUDA;
+    }
+    return DDQMC_OK;
+}
+
+int ddqmc_import_records32(ddqmc_run *r, const void *host_records, int64_t n, int64_t t, double S, int32_t variable,
+                           int64_t q_prev, int64_t t_var, int64_t t_eq) {
+    if (!r || n < 0 || (n > 0 && !host_records) || ((uintptr_t)host_records & 3u) || t < 0 || !std::isfinite(S))
+        return DDQMC_ERR_INVALID_ARG;
+    if (r->nruns || 2 * r->hp.N > 32) return DDQMC_ERR_UNSUPPORTED;
+    if (n > r->mcap) return DDQMC_ERR_CAPACITY;
+    if (cudaStreamSynchronize(r->stream) != cudaSuccess) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    unsigned char *d = soa_scratch(r, n > 0 ? n : 1);
+    if (!d) return DDQMC_ERR_OOM;
+    // over the link into scratch, unpacked and checked into the spare list
+    // buffer (a rejected list leaves the run as it was)
+    unsigned long long acc[2] = {0ull, 0ull};
+    uint32_t old_epoch = 0;
+    const int kbits = 2 * r->hp.N;
+    bool ok = cudaMemsetAsync(r->dxfer, 0, 2 * sizeof(unsigned long long), r->stream) == cudaSuccess;
+    if (n > 0) {
+        ok = ok && cudaMemcpyAsync(d, host_records, 12 * (size_t)n, cudaMemcpyHostToDevice, r->stream) == cudaSuccess;
+        k_unpack_records32<<<grid_for(n), TX_TPB, 0, r->stream>>>(reinterpret_cast<const uint32_t *>(d), n,
+                                                                   kbits >= 64 ? ~0ull : (1ull << kbits) - 1ull,
+                                                                   reinterpret_cast<Rec *>(r->L[r->cur ^ 1]),
+                                                                   r->dxfer);
+        ok = ok && cudaGetLastError() == cudaSuccess;
+    }
+    ok = ok && cudaMemcpyAsync(acc, r->dxfer, sizeof(acc), cudaMemcpyDeviceToHost, r->stream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(&old_epoch, &r->dS->epoch, sizeof(old_epoch), cudaMemcpyDeviceToHost, r->stream) ==
+                   cudaSuccess;
+    ok = ok && cudaStreamSynchronize(r->stream) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); return DDQMC_ERR_CUDA; }
+    if (acc[1]) return DDQMC_ERR_INVALID_ARG;
+    return finish_import(r, n, (int64_t)acc[0], old_epoch, t, S, variable, q_prev, t_var, t_eq);
+}
+
 int ddqmc_annihilate(ddqmc_run *r, const void *d_list, int64_t m, const void *d_spawns, int64_t nsp, void *d_out,
                      int64_t out_cap, int64_t *m_out) {
     if (!r || !m_out || m < 0 || nsp < 0 || out_cap < 0 || (m > 0 && !d_list) || (nsp > 0 && !d_spawns) ||

@@ -93,6 +93,47 @@ k_check_records(const Rec *__restrict__ L, int64_t n, uint64_t kmask, unsigned l
     }
 }
 
+// The list records [0, m) as 12-byte records {u32 key, i32 re, i32 im} (keys
+// of at most 32 bits), three words per entry.
+__global__ void __launch_bounds__(TX_TPB)
+k_pack_records32(const Rec *__restrict__ L, int64_t m, uint32_t *__restrict__ out) {
+    for (int64_t q = (int64_t)blockIdx.x * TX_TPB + threadIdx.x; q < m; q += (int64_t)gridDim.x * TX_TPB) {
+        const Rec v = L[q];
+        out[3 * q] = (uint32_t)v.key;
+        out[3 * q + 1] = (uint32_t)v.re;
+        out[3 * q + 2] = (uint32_t)v.im;
+    }
+}
+
+// 12-byte records back into list records, with the checks of k_check_records.
+__global__ void __launch_bounds__(TX_TPB)
+k_unpack_records32(const uint32_t *__restrict__ in, int64_t n, uint64_t kmask, Rec *__restrict__ L,
+                   unsigned long long *__restrict__ acc) {
+    __shared__ unsigned long long s_w[TX_TPB / 32];
+    int64_t w = 0;
+    bool bad = false;
+    for (int64_t q = (int64_t)blockIdx.x * TX_TPB + threadIdx.x; q < n; q += (int64_t)gridDim.x * TX_TPB) {
+        Rec v;
+        v.key = in[3 * q];
+        v.re = (int32_t)in[3 * q + 1];
+        v.im = (int32_t)in[3 * q + 2];
+        bad |= (v.key & ~kmask) != 0ull || (v.re == 0 && v.im == 0);
+        if (q > 0) bad |= (uint64_t)in[3 * (q - 1)] >= v.key;
+        w += (int64_t)(v.re < 0 ? -(int64_t)v.re : v.re) + (int64_t)(v.im < 0 ? -(int64_t)v.im : v.im);
+        L[q] = v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xFFFFFFFFu, w, off);
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(&acc[1], 1ull);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = (unsigned long long)w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int k = 0; k < TX_TPB / 32; ++k) t += s_w[k];
+        if (t) atomicAdd(&acc[0], t);
+    }
+}
+
 // Unpack list records [0, m) into the caller's layout (the batch run id, if
 // any, dropped from the bra word).
 template <typename LT>

@@ -89,6 +89,7 @@ class ddqmc_state(C.Structure):
 EXPORTS = ["ddqmc_default_options", "ddqmc_create", "ddqmc_step", "ddqmc_step_async", "ddqmc_sync",
            "ddqmc_estimators", "ddqmc_raw_estimators", "ddqmc_blocking_moments",
            "ddqmc_export_walkers", "ddqmc_import_walkers", "ddqmc_export_records", "ddqmc_import_records",
+           "ddqmc_export_records32", "ddqmc_import_records32",
            "ddqmc_get_state", "ddqmc_get_counts",
            "ddqmc_get_totals", "ddqmc_set_timing", "ddqmc_get_timing", "ddqmc_tune", "ddqmc_set_tuning",
            "ddqmc_get_tuning", "ddqmc_annihilate",
@@ -126,6 +127,8 @@ def load(path: str = LIB_PATH):
     lib.ddqmc_export_walkers.argtypes = [vp, P(u64), P(u64), P(i32), P(i32), i64, P(i64)]
     lib.ddqmc_export_records.argtypes = [vp, vp, i64, P(i64)]
     lib.ddqmc_import_records.argtypes = [vp, vp, i64, i64, dbl, i32, i64, i64, i64]
+    lib.ddqmc_export_records32.argtypes = [vp, vp, i64, P(i64)]
+    lib.ddqmc_import_records32.argtypes = [vp, vp, i64, i64, dbl, i32, i64, i64, i64]
     lib.ddqmc_import_walkers.argtypes = [vp, P(u64), P(u64), P(i32), P(i32), i64, i64, dbl, i32, i64,
                                          i64, i64]
     lib.ddqmc_get_state.argtypes = [vp, P(ddqmc_state)]
@@ -231,6 +234,8 @@ def ddqmc_export_walkers(run, out=None):
 
 # the run's own 16-byte list records (ddqmc_export_records / ddqmc_import_records)
 RECORD_DTYPE = np.dtype([("key", "<u8"), ("re", "<i4"), ("im", "<i4")])
+# 12-byte records of keys of at most 32 bits (ddqmc_export_records32 / ddqmc_import_records32)
+RECORD32_DTYPE = np.dtype([("key", "<u4"), ("re", "<i4"), ("im", "<i4")])
 
 
 def ddqmc_export_records(run, out=None):
@@ -251,6 +256,26 @@ def ddqmc_import_records(run, recs, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-
     recs = np.ascontiguousarray(recs, dtype=RECORD_DTYPE)
     _check(load().ddqmc_import_records(run, recs.ctypes.data_as(C.c_void_p), len(recs), int(t), float(S),
                                        int(variable), int(q_prev), int(t_var), int(t_eq)), "ddqmc_import_records")
+
+
+def ddqmc_export_records32(run, out=None):
+    """The current list as RECORD32_DTYPE records (lattices of at most 16 sites)."""
+    lib = load()
+    n = C.c_int64()
+    _check(lib.ddqmc_export_records32(run, None, 0, C.byref(n)), "ddqmc_export_records32")
+    m = n.value
+    if out is None or len(out) < m or out.dtype != RECORD32_DTYPE or not out.flags.c_contiguous:
+        out = np.empty(max(m, 1), dtype=RECORD32_DTYPE)
+    _check(lib.ddqmc_export_records32(run, out.ctypes.data_as(C.c_void_p), len(out), C.byref(n)),
+           "ddqmc_export_records32")
+    return out[:m]
+
+
+def ddqmc_import_records32(run, recs, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-1):
+    recs = np.ascontiguousarray(recs, dtype=RECORD32_DTYPE)
+    _check(load().ddqmc_import_records32(run, recs.ctypes.data_as(C.c_void_p), len(recs), int(t), float(S),
+                                         int(variable), int(q_prev), int(t_var), int(t_eq)),
+           "ddqmc_import_records32")
 
 
 def ddqmc_batch_export_walkers(batch, k, out=None):
@@ -481,6 +506,12 @@ class Run:
 
     def import_records(self, recs, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-1):
         ddqmc_import_records(self.h, recs, t, S, variable, q_prev, t_var, t_eq)
+
+    def export_records32(self, out=None):
+        return ddqmc_export_records32(self.h, out)
+
+    def import_records32(self, recs, t, S, variable=0, q_prev=1, t_var=-1, t_eq=-1):
+        ddqmc_import_records32(self.h, recs, t, S, variable, q_prev, t_var, t_eq)
 
     def state(self):
         return ddqmc_get_state(self.h)

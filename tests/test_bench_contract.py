@@ -67,6 +67,12 @@ class _FakeRun:
     def import_records(self, *a):
         pass
 
+    def export_records32(self, out=None):
+        return np.zeros(100, dtype=[("key", "<u4"), ("re", "<i4"), ("im", "<i4")])
+
+    def import_records32(self, *a):
+        pass
+
     def raw_estimates(self, k=0):
         return np.zeros(8, dtype=np.int64)
 
@@ -123,8 +129,7 @@ def fake_gpu(monkeypatch):
            "errors": 0, "steps": 10, "peak_active": 1, "batches": 0}
     monkeypatch.setattr(bench, "serve_measure",
                         lambda n, t: ({k: dict(arm) for k in ("batched", "streams", "sequential")}, "fake"))
-    monkeypatch.setattr(bench, "pinned_record_buffer",
-                        lambda n: np.empty(n, dtype=[("key", "<u8"), ("re", "<i4"), ("im", "<i4")]))
+    monkeypatch.setattr(bench, "pinned_record_buffer", lambda n, dtype=None: np.empty(n, dtype=dtype or np.uint8))
     monkeypatch.setattr(bench, "pinned_list_buffers",
                         lambda n: tuple(np.empty(n, dtype=d) for d in (np.uint64, np.uint64, np.int32, np.int32)))
     monkeypatch.setattr(bench, "oracle_sample",
@@ -169,7 +174,7 @@ def test_single_run_line_has_every_key(fake_gpu, capsys, monkeypatch):
     assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and "sample" in cpu
     e2e = line["e2e"]
     assert e2e["unit"] == line["unit"] and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
-    assert e2e["h2d_bytes_per_step"] == 1600 and line["e2e_arrays"]["h2d_bytes_per_step"] == 2400
+    assert e2e["h2d_bytes_per_step"] == 1200 and line["e2e_arrays"]["h2d_bytes_per_step"] == 2400
     assert line["gpu_launches"] == 18
     assert set(line["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
     sv = line["serving"]

@@ -335,6 +335,30 @@ def test_records_import_export(ddqmc):
     with pytest.raises(ddqmc.DDQMCError) as e:
         wide.export_records()
     assert e.value.code == -7
+    # the 12-byte records of keys of at most 32 bits
+    r32 = run.export_records32()
+    assert np.array_equal(r32["key"].astype(np.uint64), recs["key"])
+    assert np.array_equal(r32["re"], recs["re"]) and np.array_equal(r32["im"], recs["im"])
+    c = ddqmc.Run(*args, **kw)
+    c.import_records32(r32, *st)
+    d = ddqmc.Run(*args, **kw)
+    d.import_records(recs, *st)
+    for t in range(10):
+        c.step(1)
+        d.step(1)
+        assert np.array_equal(c.export_records32(), d.export_records32()), t
+        assert np.array_equal(c.raw_estimates(), d.raw_estimates()), t
+    before = c.export_records32().copy()
+    with pytest.raises(ddqmc.DDQMCError) as e:
+        c.import_records32(r32[::-1], *st)
+    assert e.value.code == -1
+    assert np.array_equal(c.export_records32(), before)
+    empty = ddqmc.Run(*args, **kw)
+    empty.import_records32(r32[:0], *st)
+    assert len(empty.export_records32()) == 0 and len(empty.export_records()) == 0
+    with pytest.raises(ddqmc.DDQMCError) as e:
+        ddqmc.Run(4, 5, 0, 0.9, 1.0, 1.0, 1.0, 0.005, 1000).export_records32()
+    assert e.value.code == -7
 
 
 def test_p40_records_split_large_counts(ddqmc):
