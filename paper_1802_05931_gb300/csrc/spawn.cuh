@@ -546,8 +546,8 @@ __device__ __forceinline__ void emit(SpawnShared<T, F> &s, int warp, const T &r,
 }
 
 // Append an aggregated child (any int32 counts): packed records carry at most
-// PK_LIM walkers per part and two-word records WK_LIM, so large counts become
-// several records.
+// PK_LIM walkers per part, 40-bit-key records P40_LIM and two-word records
+// WK_LIM, so large counts become several records.
 template <typename T, bool F>
 __device__ __forceinline__ void emit_counts(SpawnShared<T, F> &s, int warp, uint64_t ci, uint64_t cj, int N, bool flag,
                                             int cre, int cim, T *out, int64_t cap, DevState *st, int npass,
