@@ -51,7 +51,7 @@ namespace ddq {
 
 constexpr int SP_TPB = 256;
 constexpr int SP_WARPS = SP_TPB / 32;
-constexpr int SP_STAGE = 128;      // staged records per warp
+constexpr int SP_STAGE = 128;      // staged records per warp (default)
 constexpr int SP_FLUSH = 32;       // flush threshold at warp-uniform points
 constexpr int SP_HEAVY = 1024;     // default: configurations with more walkers use the warp-cooperative path
 
@@ -143,12 +143,14 @@ struct SpawnTables {
 };
 
 // Resident blocks per SM the spawn kernel is compiled for: four for a single
-// run with packed records (64 registers a thread: a few spills, measured
-// faster than three blocks at 80); two for two-word keys, whose shared memory
-// allows no more (so up to 128 registers a thread); else three.
+// run with packed records and for 40-bit-key records (64 registers a thread:
+// a few spills, measured faster than three blocks at 80); two for two-word
+// keys, whose shared memory allows no more (so up to 128 registers a thread);
+// else three.
 template <typename T, bool BATCH> struct SpawnBlocks {
     static constexpr int value = std::is_same<T, RecW>::value ? 2
-                                 : ((std::is_same<T, uint64_t>::value && !BATCH) ? 4 : 3);
+                                 : (((std::is_same<T, uint64_t>::value && !BATCH) || std::is_same<T, P40>::value)
+                                        ? 4 : 3);
 };
 
 // Shared memory of the spawn kernel for spawn records of type T, with or
@@ -160,7 +162,9 @@ struct SpawnShared : SpawnTables {
                               : (std::is_same<T, P40>::value ? 5 : (std::is_same<T, RecW>::value ? MAXPASS : 8));
     uint32_t hist[NP][256];
     int32_t stage_n[SP_WARPS];
-    T stage[SP_WARPS][SP_STAGE];
+    // staged records per warp (40-bit-key records: 64, for four blocks per SM)
+    static constexpr int STAGE = std::is_same<T, P40>::value ? 64 : SP_STAGE;
+    T stage[SP_WARPS][STAGE];
     WarpScratch<T, FIELD> ws[SP_WARPS];
     int32_t mark[SP_WARPS][32];       // first walker position of each configuration of the chunk
     int32_t dre[SP_WARPS][32], dim[SP_WARPS][32];
@@ -532,7 +536,7 @@ __device__ __forceinline__ void emit(SpawnShared<T, F> &s, int warp, const T &r,
     if (lane == leader) base = atomicAdd(&s.stage_n[warp], __popc(am));
     base = __shfl_sync(am, base, leader);
     const int pos = base + __popc(am & ((1u << lane) - 1u));
-    if (pos < SP_STAGE) {
+    if (pos < SpawnShared<T, F>::STAGE) {
         stage[pos] = r;
     } else {
         const unsigned long long idx = atomicAdd((unsigned long long *)&st->R, 1ull);
@@ -573,7 +577,7 @@ __device__ __forceinline__ void flush(SpawnShared<T, F> &s, int warp, int lane, 
     __syncwarp();
     const T *stage = &s.stage[warp][0];
     int n = s.stage_n[warp];
-    if (n > SP_STAGE) n = SP_STAGE;
+    if (n > SpawnShared<T, F>::STAGE) n = SpawnShared<T, F>::STAGE;
     if (n >= min_n && n > 0) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd((unsigned long long *)&st->R, (unsigned long long)n);
@@ -1006,7 +1010,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                     // a drain adds up to 32 records: flush first when they
                     // might not fit, so that no record takes the one-by-one
                     // path through the global record counter
-                    flush(s, warp, lane, out, cap, st, npass, SP_STAGE - 32 + 1);
+                    flush(s, warp, lane, out, cap, st, npass, SpawnShared<T, FIELD>::STAGE - 32 + 1);
                     const int nd = qn < 32 ? qn : 32;
                     spawn_drain<T, MT, SW, FIELD, BATCH>(s, c, Pr, run_shift, warp, lane, nd, N, out, cap, st, npass);
                     qn -= nd;
