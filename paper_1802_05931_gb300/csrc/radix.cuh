@@ -38,8 +38,8 @@ template <> struct RecTraits<Rec> {
 
 // Two-word records: digits of the ket word at shifts 0..63, of the bra word at 64..127.
 template <> struct RecTraits<RecW> {
-    static constexpr int IPT = 10;     // larger tiles at 2 blocks per SM (measured faster than 6 at 3)
-    static constexpr int MINB = 2;
+    static constexpr int IPT = 8;      // at 3 blocks per SM: measured faster than 10 at 2 and 6 at 3
+    static constexpr int MINB = 3;
     __device__ __forceinline__ static uint32_t digit(const RecW &r, int shift) {
         return (uint32_t)(shift < 64 ? (r.lo >> shift) : (r.hi >> (shift - 64))) & 0xFFu;
     }

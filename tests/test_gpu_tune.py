@@ -34,7 +34,8 @@ def test_tuned_run_continues_as_untuned(ddqmc, cfg, target):
     a.step(300)
     b.step(300)
     t = a.tune()
-    assert 1 <= t["spawn_blocks_per_sm"] <= 3 and 1 <= t["radix_blocks_per_sm"] <= 3
+    # within what each kernel can hold: spawn of packed single runs 4 blocks per SM, radix 3
+    assert 1 <= t["spawn_blocks_per_sm"] <= 4 and 1 <= t["radix_blocks_per_sm"] <= 3
     assert t["heavy_walkers"] in (256, 1024, 4096)
     assert t["step_ms_tuned"] <= t["step_ms_default"] * 1.0001
     assert a.tuning()["merge_blocks_per_sm"] == t["merge_blocks_per_sm"]
