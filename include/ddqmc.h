@@ -82,17 +82,25 @@ typedef struct {
                                   default 0 (none) */
     int32_t field_axis;        /* direction t: 0 along x (t = 0), 1 along y (t = pi/2), 2 the
                                   angle field_theta; default 0 */
-    int32_t wide_sort_bits;    /* lattices of more than 31 sites (two-word keys), single runs:
-                                  the list and the spawn records are kept in the hashed order
-                                  (stored bra word = bra ^ (64-bit hash of ket, low
-                                  wide_sort_bits bits), then ket); a step sorts the spawn
-                                  records on the stored bra word only and puts records that
-                                  share it in ket order.  0..64, default 64 (8 digit passes
-                                  instead of up to 16); -1: plain (bra, ket) order on every
-                                  key bit.  Results do not depend on it; fewer bits make equal
-                                  stored words common (a test of their repair).  Import and
-                                  export stay in (bra, ket) order and then need
-                                  entries <= capacity_spawns.  Batches keep the plain order. */
+    int32_t wide_sort_bits;    /* lattices of more than 31 sites (two-word keys): the list and
+                                  the spawn records are kept in the hashed order (stored bra
+                                  word = bra ^ (64-bit hash of ket, low wide_sort_bits bits),
+                                  then ket); a step sorts the spawn records on the stored bra
+                                  word only and puts records that share it in ket order.
+                                  0..64, default 64 (8 digit passes instead of up to 16);
+                                  -1: plain (bra, ket) order on every key bit.  Results do not
+                                  depend on it; fewer bits make equal stored words common (a
+                                  test of their repair).  Import and export stay in (bra, ket)
+                                  order and then need entries <= capacity_spawns (a batch: the
+                                  exported run's entries).  A batch puts its run id above
+                                  max(N, hash bits) in the bra word, hashes at most 64 minus
+                                  the run id's bits, and sorts digit passes up to the run id's
+                                  top bit: a 6x6 batch of up to 16 runs takes 8 passes at the
+                                  default, 10 in the plain order, and 5 with wide_sort_bits =
+                                  36, for small runs: D distinct keys spawned in a run then
+                                  share stored bra words in about D^2 / 2^37 pairs per step,
+                                  and past 16,384 out-of-order neighbours in all runs the step
+                                  stops with CAPACITY. */
     double field_theta;        /* field_axis 2: the angle t (radians); each site flip is then two
                                   moves, |h cos t| (the x part) and |h sin t| (the y part), so
                                   2B + 5N moves per configuration must fit the move table

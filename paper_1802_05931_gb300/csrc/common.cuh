@@ -105,8 +105,9 @@ struct RunParams {
     uint64_t Emorton_hi;              // the same for sites 32..63 (bit 2(k-32), 2(k-32)+1)
     uint64_t urate8[8];               // rate of group 4*anti + class when every bond has the same table
     // A batch of runs shares one walker store with the run id in the key's
-    // high bits (bit run_shift up: 2N for one-word keys, N of the bra word for
-    // two-word keys).  nruns = 0 for a single run.
+    // high bits (bit run_shift up: 2N for one-word keys; for two-word keys
+    // N of the bra word, or in the hashed order above the hash bits if they
+    // reach past N).  nruns = 0 for a single run.
     int32_t nruns, run_shift;
     // the uniform tables in the forms the light path reads (a single run
     // derives them in shared memory; a batch reads each run's copy)

@@ -481,7 +481,7 @@ void launch_step(ddqmc_run *r, void *Lcv, void *Lnv, const std::function<void(in
                                                                        P.pass_shift[p], r->rcap);
         }
     }
-    if constexpr (std::is_same<T, RecW>::value && !BATCH) {
+    if constexpr (std::is_same<T, RecW>::value) {
         if (P.hashed) {
             // equal stored bra words into ket order
             RecW *srt = (P.npass & 1) ? sp1 : sp0;
@@ -1076,15 +1076,20 @@ int export_list(ddqmc_run *r, int k, uint64_t *ket, uint64_t *bra, int32_t *re, 
     if (m <= 0) return DDQMC_OK;
     if constexpr (std::is_same<LT, RecW>::value) {
         if (r->hp.hashed) {
-            // the hashed order is not the caller's: plain bra words, then a
-            // sort on both words (Sp[0] holds the copy)
-            if (M > r->rcap) return DDQMC_ERR_CAPACITY;
-            k_unhash<<<grid_for(M), TX_TPB, 0, r->stream>>>(L, M, r->hp.hash_mask, reinterpret_cast<RecW *>(r->Sp[0]));
+            // the hashed order is not the caller's: the exported range with
+            // its plain bra words, then a sort on both words (Sp[0] holds the
+            // copy; the entries of a batch run share their run bits, so the
+            // bra word's digits need not reach them)
+            const int64_t me = b1 - b0;
+            if (me > r->rcap) return DDQMC_ERR_CAPACITY;
+            k_unhash<<<grid_for(me), TX_TPB, 0, r->stream>>>(L + b0, me, r->hp.hash_mask,
+                                                               reinterpret_cast<RecW *>(r->Sp[0]));
             const int nb = (r->hp.N + 7) / 8;
             RecW *srt = nullptr;
-            const int rc = sort_records_wide(r, M, 2 * nb, nb, false, &srt);
+            const int rc = sort_records_wide(r, me, 2 * nb, nb, false, &srt);
             if (rc != DDQMC_OK) return rc;
             L = srt;
+            b0 = 0;
         }
     }
     unsigned char *d = soa_scratch(r, m);
@@ -1432,12 +1437,29 @@ int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_
     int rbits = 0;
     while ((1ll << rbits) < (int64_t)nruns) ++rbits;
     r->wide = N > NPACK;
+    // two-word keys in the hashed order (wide_sort_bits >= 0): the hash takes
+    // the low bits of the stored bra word up to the run id, which sits above
+    // both the N spin bits and the hash bits, so the runs stay contiguous;
+    // the passes cover the stored bra word up to the run id's top bit.  The
+    // plain order's passes cover the ket word, then the bra word.
+    H.hashed = 0;
+    H.hash_mask = 0;
     if (r->wide) {
         if (N + rbits > 64 || N >= 64) { delete r; return DDQMC_ERR_UNSUPPORTED; }
         const int nb = (N + 7) / 8, nbb = (N + rbits + 7) / 8;
-        H.npass = nb + nbb;
-        for (int p = 0; p < H.npass; ++p) H.pass_shift[p] = p < nb ? 8 * p : 64 + 8 * (p - nb);
-        H.run_shift = N;
+        if (o.wide_sort_bits >= 0) {
+            const int room = 64 - (rbits > 0 ? rbits : 1);      // the run id's shift stays below 64
+            const int hb = o.wide_sort_bits < room ? o.wide_sort_bits : room;
+            H.hashed = 1;
+            H.hash_mask = (1ull << hb) - 1ull;
+            H.run_shift = hb > N ? hb : N;
+            H.npass = (H.run_shift + rbits + 7) / 8;
+            for (int p = 0; p < H.npass; ++p) H.pass_shift[p] = 64 + 8 * p;
+        } else {
+            H.npass = nb + nbb;
+            for (int p = 0; p < H.npass; ++p) H.pass_shift[p] = p < nb ? 8 * p : 64 + 8 * (p - nb);
+            H.run_shift = N;
+        }
     } else {
         if (2 * N + rbits > 63) { delete r; return DDQMC_ERR_UNSUPPORTED; }
         H.npass = (2 * N + rbits + 7) / 8;
@@ -1453,16 +1475,13 @@ int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_
     for (int k = 0; k < nruns; ++k) axis2 = axis2 || (r->hpr[k].field_on && r->hpr[k].field_axis == 2);
     H.K = 2 * B + N + (H.field_on ? (axis2 ? 4 * N : 2 * N) : 0);
     if (H.K > (N > NPACK ? MAXK : MAXK_PACK)) { delete r; return DDQMC_ERR_UNSUPPORTED; }
-    // a batch keeps the plain key order (its run id leads the bra word)
-    H.hashed = 0;
-    H.hash_mask = 0;
     for (int k = 0; k < nruns; ++k) {
         r->hpr[k].nruns = nruns;
         r->hpr[k].run_shift = H.run_shift;
         r->hpr[k].npass = H.npass;
         r->hpr[k].K = H.K;
-        r->hpr[k].hashed = 0;
-        r->hpr[k].hash_mask = 0;
+        r->hpr[k].hashed = H.hashed;
+        r->hpr[k].hash_mask = H.hash_mask;
     }
     int64_t mcap = o.capacity_entries > 0 ? o.capacity_entries : mdef;
     int64_t rcap = o.capacity_spawns > 0 ? o.capacity_spawns : rdef;
@@ -1490,7 +1509,7 @@ int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_
             first.push_back(e);
             RecW w;
             w.lo = 0;
-            w.hi = r->wide ? (uint64_t)k << H.run_shift : 0ull;
+            w.hi = r->wide ? bra_swap(0ull, (uint64_t)k << H.run_shift, H.hash_mask) : 0ull;
             w.re = (int32_t)runs[k].n0;
             w.im = 0;
             firstw.push_back(w);

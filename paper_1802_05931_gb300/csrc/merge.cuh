@@ -61,7 +61,7 @@ template <> __device__ __forceinline__ K128 spawn_key<K128, RecW>(const RecW &v)
 
 // ket and bra words of a key
 // (hmask: the hashed order's mask of the ket hash in a two-word key's stored
-// bra word; 0 for one-word keys and batches)
+// bra word; 0 for one-word keys; a batch's covers the N spin bits at most)
 __device__ __forceinline__ void key_words(uint64_t k, uint64_t nmask, int N, uint64_t &i, uint64_t &j,
                                           uint64_t = 0) {
     i = k & nmask;
@@ -365,7 +365,7 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
     const int64_t ntiles = (tot + MG_TILE - 1) / MG_TILE;
     const int N = P.N;
     const uint64_t nmask = P.nmask;
-    const uint64_t xmask = BATCH ? 0ull : P.hash_mask;     // hashed order of two-word keys
+    const uint64_t xmask = P.hash_mask;     // hashed order of two-word keys
     const bool no_init = P.n_a == 0;
     const int nruns = P.nruns, run_shift = P.run_shift, nobs = P.nobs;
     unsigned long long *best = reinterpret_cast<unsigned long long *>(smem_raw + sizeof(MergeShared<T>));
@@ -651,7 +651,7 @@ k_merge(const RunParams *__restrict__ Pp, const typename ListOf<T>::type *__rest
                 v.im = 0;
                 if (valid) v = stage[q];
                 uint64_t i, j;
-                key_words(list_key<KT>(v), nmask, N, i, j);
+                key_words(list_key<KT>(v), nmask, N, i, j, xmask);
                 const int rr = batch_run(key_high(list_key<KT>(v)), run_shift, nruns);
                 j &= nmask;
                 unsigned long long *est = best + (size_t)rr * nobs;

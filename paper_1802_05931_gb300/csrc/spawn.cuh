@@ -732,7 +732,7 @@ __device__ __forceinline__ void spawn_drain(SpawnShared<T, FIELD> &s, const Spaw
         }
         const uint64_t kp = BATCH ? (uint64_t)orun << run_shift : 0ull;
         uint64_t cjs = (uint64_t)cj;
-        if constexpr (std::is_same<T, RecW>::value && !BATCH) cjs = bra_swap((uint64_t)ci, cjs, c.hmask);
+        if constexpr (std::is_same<T, RecW>::value) cjs = bra_swap((uint64_t)ci, cjs, c.hmask);
         emit(s, warp, make_spawn<T>((uint64_t)ci, cjs, N, (qinit & 1) != 0, cre, cim, kp), out, cap, st, npass);
     }
     __syncwarp();
@@ -826,10 +826,12 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
         rec.im = 0;
         if (e < M) {
             rec = L[e];
-            if constexpr (WIDE) { i = rec.lo; j = BATCH ? rec.hi : bra_swap(rec.lo, rec.hi, c.hmask); }
+            if constexpr (WIDE) { i = rec.lo; j = bra_swap(rec.lo, rec.hi, c.hmask); }
             else { i = rec.key & nmask; j = rec.key >> N; }
             if constexpr (BATCH) {
-                crun = batch_run(j, N, nruns);   // j holds the run id above its N spin bits
+                // the run id: from bit run_shift of a two-word key's bra word
+                // (above the spin and hash bits), from bit N of key >> N
+                crun = batch_run(j, WIDE ? run_shift : N, nruns);
                 j &= nmask;
             }
         }
@@ -1222,7 +1224,7 @@ k_spawn_death(const RunParams *__restrict__ Pp, DevState *__restrict__ st, typen
                 int gsg;
                 bool same;
                 move_child<BATCH>(c, HP, hi, hj, s.ws[warp].hv.mv[m], ci, cj, same, gsg);
-                if constexpr (WIDE && !BATCH) cj = bra_swap(ci, cj, c.hmask);
+                if constexpr (WIDE) cj = bra_swap(ci, cj, c.hmask);
                 emit_counts(s, warp, ci, cj, N, hinit, cre, cim, out, cap, st, npass, hkp);
             }
             flush(s, warp, lane, out, cap, st, npass, SP_FLUSH);

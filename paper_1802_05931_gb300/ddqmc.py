@@ -549,13 +549,15 @@ def run_spec(Jx, Jy, Jz, gamma, dt, target, n_a=0, seed=1, damping=0.05, shift0=
 class Batch:
     """Several DDQMC runs of one lattice stepped together in one walker store
     (run id in the key's high bits); runs[k] are the keyword arguments of
-    ``run_spec`` for run k."""
+    ``run_spec`` for run k.  ``wide_sort_bits``: the key order of two-word
+    keys, as for ``Run`` (the run id sits above the hash bits)."""
 
     def __init__(self, Lx, Ly, periodic, runs, guide_kind=0, guide_p=0.0, site_ratio=None,
-                 capacity_entries=0, capacity_spawns=0, stream=None, sm_limit=0):
+                 capacity_entries=0, capacity_spawns=0, stream=None, sm_limit=0, wide_sort_bits=64):
         o = ddqmc_default_options()
         o.capacity_entries = int(capacity_entries)
         o.capacity_spawns = int(capacity_spawns)
+        o.wide_sort_bits = int(wide_sort_bits)
         o.cuda_stream = stream
         o.sm_limit = int(sm_limit)
         g = ddqmc_guide()

@@ -2,8 +2,8 @@
 are sorted on the stored bra word only (bra xor a hash of the ket), and a
 repair kernel puts records that share it in ket order.  The order is internal:
 lists, estimators and the step must equal the oracle's bit for bit whatever
-the number of hash bits, and import / export keep the caller's (bra, ket)
-order."""
+the number of hash bits, for single runs and batches, and import / export
+keep the caller's (bra, ket) order."""
 import numpy as np
 import pytest
 
@@ -99,6 +99,41 @@ def test_import_export_roundtrip(ddqmc, bits, nbra, nket):
         for a, b in zip(plain.export(), run2.export()):
             assert np.array_equal(a, b)
         assert np.array_equal(plain.raw_estimates(), run2.raw_estimates())
+
+
+@pytest.mark.parametrize("bits", [0, 3, 50])
+def test_batch_hashed_order_against_the_oracle(ddqmc, bits):
+    """A 6x6 batch in the hashed order, against the oracle run by run, after
+    single steps and after graph blocks; then a retired run.  Few hash bits
+    leave many groups of equal stored bra words to repair in every step (the
+    run id above the 36 spin bits keeps the runs' groups apart); 50 bits put
+    the run id above the hash, at bit 50."""
+    # at most about 9,000 spawn records per step in all: fewer out-of-order
+    # neighbours than the repair records, whatever the order
+    runs = [dict(Jx=(0.8, 0.9, 1.15)[k], Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, target=1500 + 500 * k, n_a=3,
+                 seed=40 + k, control=1) for k in range(3)]
+    batch = ddqmc.Batch(6, 6, 1, runs, capacity_entries=1 << 18, capacity_spawns=1 << 19, wide_sort_bits=bits)
+    cpus = [O.OracleRun(6, 6, 1, r["Jx"], r["Jy"], r["Jz"], r["gamma"], r["dt"], r["target"], n_a=r["n_a"],
+                        seed=r["seed"], control=r["control"]) for r in runs]
+    for t in (1, 2, 3, 10, 40, 73):
+        done = batch.state(0).t
+        batch.step(t - done)
+        for k, cpu in enumerate(cpus):
+            cpu.step(t - done)
+            g, c = batch.export(k), cpu.export()
+            assert len(g[0]) == len(c[0]), (bits, t, k)
+            for name, a, b in zip(("ket", "bra", "re", "im"), g, c):
+                assert np.array_equal(a, b), (bits, t, k, name)
+            assert np.array_equal(batch.raw_estimates(k), cpu.estimates_now()), (bits, t, k)
+    assert all(batch.export(k)[0].size > 1000 for k in range(len(runs)))
+    # run 1 retires: its entries leave at the next merge, the others go on
+    batch.retire(1)
+    batch.step(5)
+    assert batch.export(1)[0].size == 0
+    for k in (0, 2):
+        cpus[k].step(5)
+        for a, b in zip(batch.export(k), cpus[k].export()):
+            assert np.array_equal(a, b), (bits, "retired", k)
 
 
 def test_invalid_sort_bits(ddqmc):
