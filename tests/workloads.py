@@ -16,8 +16,8 @@ C2 = dict(Lx=3, Ly=3, periodic=1, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, t
 C2W = dict(Lx=3, Ly=3, periodic=1, Jx=0.225, Jy=0.335, Jz=0.25, gamma=1.0, dt=0.005, target=10 ** 4,
            n_a=0, seed=2, steps=40000)
 # 4x4 periodic, 10^8 walkers in total (control on the total population), n_a = 3,
-# site-product guide; the all-down mean-field fixed point gives uniform site
-# ratios exp(-1.5).
+# site-product guide with every site ratio exp(-1.5) (the paper's uniform
+# weight per flipped site, through the site-product code path).
 C3 = dict(Lx=4, Ly=4, periodic=1, Jx=0.9, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, target=10 ** 8,
           n_a=3, seed=3, steps=10000, control=1, guide_kind=2, guide_p=1.5)
 
