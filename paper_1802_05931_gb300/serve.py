@@ -55,6 +55,8 @@ class SolveRequest:
     min_samples: int = 256      # accumulated steps before convergence is judged
     max_steps: int = 20000      # give up (unconverged) after this many steps
     capacity_factor: float = 8.0   # list capacity = factor * target; spawn capacity twice that
+    # (6x6 and larger lattices grow to millions of walkers whatever the target
+    # before the shift holds them: their requests need a far larger factor)
 
     @property
     def sites(self) -> int:
