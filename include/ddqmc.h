@@ -358,10 +358,11 @@ typedef struct {
 /* Create a batch of nruns (1..DDQMC_MAX_BATCH) runs on one lattice and one
  * guide; runs[k] gives run k's parameters.  From opt only capacity_entries,
  * capacity_spawns (shared by all runs; <= 0: the sum of the per-run
- * defaults), cuda_stream and sm_limit are read.  Key layout: up to 31 sites
- * one 64-bit key run << 2N | bra << N | ket (needs 2N + ceil(log2 nruns) <=
- * 63; 8-byte spawn records when it is <= 32), from 32 to 63 sites the run id
- * in the bra word above bit N (needs N + ceil(log2 nruns) <= 64); 64 sites
+ * defaults), cuda_stream, sm_limit and wide_sort_bits are read.  Key
+ * layout: up to 31 sites one 64-bit key run << 2N | bra << N | ket (needs
+ * 2N + ceil(log2 nruns) <= 63; 8-byte spawn records when it is <= 40), from
+ * 32 to 63 sites the run id in the bra word above bit N, or above the hash
+ * bits in the hashed order (needs N + ceil(log2 nruns) <= 64); 64 sites
  * need an extra key word and return UNSUPPORTED, as does a batch whose
  * per-block estimator sums (nruns x observables x 8 bytes) do not fit in
  * shared memory.  Errors: as ddqmc_create, UNSUPPORTED.  *out is NULL on

@@ -119,10 +119,11 @@ struct RunParams {
     // a run of a batch that was retired (0): its configurations spawn nothing
     // and leave the list at the next merge; the other runs do not notice
     int32_t active;
-    // Hashed order of two-word keys (single runs): the stored bra word is
-    // bra ^ (ket_mix(ket) & hash_mask), the digit passes cover the stored bra
-    // word only, and a repair kernel puts records with equal stored bra words
-    // in ket order (hashed = 1).  hash_mask = 0, hashed = 0: the plain order.
+    // Hashed order of two-word keys: the stored bra word is
+    // bra ^ (ket_mix(ket) & hash_mask) (a batch's run id above the mask's
+    // bits), the digit passes cover the stored bra word only, and a repair
+    // kernel puts records with equal stored bra words in ket order
+    // (hashed = 1).  hash_mask = 0, hashed = 0: the plain order.
     int32_t hashed;
     uint64_t hash_mask;
     uint64_t frate_q2[MAXN][4];       // axis 2: the y part of a site flip, [importance class]

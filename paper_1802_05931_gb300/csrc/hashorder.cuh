@@ -4,9 +4,10 @@
 // spawn records share it).
 //
 // The stored bra word of a key is bra ^ (ket_mix(ket) & hash_mask); the list
-// and the spawn records are ordered by (stored bra word, ket).  The digit
-// passes sort the spawn records on the stored bra word only (8 passes of 8
-// bits instead of up to 16 over both words).  Records with equal stored bra
+// and the spawn records are ordered by (stored bra word, ket); a batch keeps
+// its run id above the hash bits of that word.  The digit passes sort the
+// spawn records on the stored bra word only (8 passes of 8 bits instead of
+// up to 16 over both words).  Records with equal stored bra
 // words are then in the order the passes left them; with a 64-bit hash two
 // different keys share a stored bra word with probability about
 // n^2 / 2^65 per step (n distinct keys).  Afterwards:
