@@ -90,8 +90,9 @@ def _fresh_load(path):
 def test_batch_parameter_checks_need_no_gpu():
     """ddqmc_create_batch rejects what it cannot run before touching the
     device: no runs, too many runs, a bad run parameter, 64 sites (the run id
-    would need an extra key word), and 31 sites with 3 runs (62 spin bits +
-    2 run bits do not fit below the flag bit of a one-word key)."""
+    would need an extra key word), 31 sites with 3 runs (62 spin bits + 2
+    run bits do not fit below the flag bit of a one-word key), 63 sites with
+    3 runs (63 + 2 bits do not fit in the bra word), and a bad sort order."""
     from paper_1802_05931_gb300 import build as b, ddqmc
     b.build()
     base = ddqmc.run_spec(0.9, 1.0, 1.0, 1.0, 0.01, 1000)
@@ -101,7 +102,14 @@ def test_batch_parameter_checks_need_no_gpu():
                                  (lat, [base] * (ddqmc.MAX_BATCH + 1), -1),
                                  (lat, [base, bad], -1),
                                  (ddqmc.ddqmc_lattice(8, 8, 1), [base, base], -7),
-                                 (ddqmc.ddqmc_lattice(31, 1, 0), [base] * 3, -7)):
+                                 (ddqmc.ddqmc_lattice(31, 1, 0), [base] * 3, -7),
+                                 (ddqmc.ddqmc_lattice(7, 9, 0), [base] * 3, -7)):
         with pytest.raises(ddqmc.DDQMCError) as e:
             ddqmc.ddqmc_create_batch(lattice, specs)
         assert e.value.code == code
+    for bits in (-2, 65):
+        o = ddqmc.ddqmc_default_options()
+        o.wide_sort_bits = bits
+        with pytest.raises(ddqmc.DDQMCError) as e:
+            ddqmc.ddqmc_create_batch(ddqmc.ddqmc_lattice(6, 6, 1), [base, base], options=o)
+        assert e.value.code == -1
