@@ -93,14 +93,15 @@ typedef struct {
                                   test of their repair).  Import and export stay in (bra, ket)
                                   order and then need entries <= capacity_spawns (a batch: the
                                   exported run's entries).  A batch puts its run id above
-                                  max(N, hash bits) in the bra word, hashes at most 64 minus
-                                  the run id's bits, and sorts digit passes up to the run id's
-                                  top bit: a 6x6 batch of up to 16 runs takes 8 passes at the
-                                  default, 10 in the plain order, and 5 with wide_sort_bits =
-                                  36, for small runs: D distinct keys spawned in a run then
-                                  share stored bra words in about D^2 / 2^37 pairs per step,
-                                  and past 16,384 out-of-order neighbours in all runs the step
-                                  stops with CAPACITY. */
+                                  max(N, hash bits) in the bra word and sorts digit passes up
+                                  to the run id's top bit; it hashes at most one digit byte
+                                  more than its spin and run-id bits fill, and at most 64
+                                  minus the run id's bits.  A 6x6 batch of up to 16 runs takes
+                                  6 passes at the default, 10 in the plain order, and 5 with
+                                  wide_sort_bits = 36, for small runs: D distinct keys spawned
+                                  in a run then share stored bra words in about D^2 / 2^37
+                                  pairs per step, and past 16,384 out-of-order neighbours in
+                                  all runs the step stops with CAPACITY. */
     double field_theta;        /* field_axis 2: the angle t (radians); each site flip is then two
                                   moves, |h cos t| (the x part) and |h sin t| (the y part), so
                                   2B + 5N moves per configuration must fit the move table

@@ -1441,7 +1441,11 @@ int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_
     // the low bits of the stored bra word up to the run id, which sits above
     // both the N spin bits and the hash bits, so the runs stay contiguous;
     // the passes cover the stored bra word up to the run id's top bit.  The
-    // plain order's passes cover the ket word, then the bra word.
+    // hash takes at most hb = one digit byte more than the spin and run-id
+    // bits fill, for one pass more than the minimum: at the default,
+    // hb >= min(N + 8, 64 - run-id bits), and different keys of a run share
+    // a stored bra word in about D^2 / 2^(hb + 1) pairs a step for D distinct
+    // keys.  The plain order's passes cover the ket word, then the bra word.
     H.hashed = 0;
     H.hash_mask = 0;
     if (r->wide) {
@@ -1449,7 +1453,10 @@ int ddqmc_create_batch(const ddqmc_lattice *lattice, int32_t nruns, const ddqmc_
         const int nb = (N + 7) / 8, nbb = (N + rbits + 7) / 8;
         if (o.wide_sort_bits >= 0) {
             const int room = 64 - (rbits > 0 ? rbits : 1);      // the run id's shift stays below 64
-            const int hb = o.wide_sort_bits < room ? o.wide_sort_bits : room;
+            const int byte_more = 8 * nbb + 8 - rbits;
+            int hb = o.wide_sort_bits;
+            if (hb > byte_more) hb = byte_more;
+            if (hb > room) hb = room;
             H.hashed = 1;
             H.hash_mask = (1ull << hb) - 1ull;
             H.run_shift = hb > N ? hb : N;

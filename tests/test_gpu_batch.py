@@ -126,10 +126,11 @@ def test_batch_site_dependent_guide_matches_single_runs(ddqmc):
 
 @pytest.mark.parametrize("bits", [64, 36, -1])
 def test_batch_two_word_keys_match_single_runs(ddqmc, bits):
-    """6x6 periodic (36 sites): the batch in the hashed order with 62 hash
-    bits (run id from bit 62, 8 digit passes), with 36 (run id from bit 36,
-    5 passes) and in the plain order (10 passes), against single runs in the
-    hashed order."""
+    """6x6 periodic (36 sites): the batch in the hashed order at the default
+    (for three runs 46 hash bits, one digit byte past the 36 spin and 2
+    run-id bits: run id from bit 46, 6 digit passes), with 36 (run id from
+    bit 36, 5 passes) and in the plain order (10 passes), against single runs
+    in the hashed order."""
     runs = [dict(Jx=0.8 + 0.2 * k, Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, target=3 * 10 ** 4, n_a=3, seed=30 + k,
                  control=1) for k in range(3)]
     batch = ddqmc.Batch(6, 6, 1, runs, capacity_entries=10 ** 7, capacity_spawns=2 * 10 ** 7, wide_sort_bits=bits)

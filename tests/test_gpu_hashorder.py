@@ -106,8 +106,9 @@ def test_batch_hashed_order_against_the_oracle(ddqmc, bits):
     """A 6x6 batch in the hashed order, against the oracle run by run, after
     single steps and after graph blocks; then a retired run.  Few hash bits
     leave many groups of equal stored bra words to repair in every step (the
-    run id above the 36 spin bits keeps the runs' groups apart); 50 bits put
-    the run id above the hash, at bit 50."""
+    run id above the 36 spin bits keeps the runs' groups apart); 50 bits are
+    capped at 46 (one digit byte past the spin and run-id bits), which puts
+    the run id above the hash, at bit 46."""
     # at most about 9,000 spawn records per step in all: fewer out-of-order
     # neighbours than the repair records, whatever the order
     runs = [dict(Jx=(0.8, 0.9, 1.15)[k], Jy=1.0, Jz=1.0, gamma=1.0, dt=0.005, target=1500 + 500 * k, n_a=3,
